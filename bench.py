@@ -1,0 +1,375 @@
+"""Benchmark: eigenpairs/s of the SS / shifted-CG eigensolver on one GB300.
+
+Workload (one "step" = one full eigen-solve through the C ABI: quadrature
+setup, shifted CG for every quadrature point and source, moments,
+Rayleigh-Ritz, acceptance, eigenpair readback):
+
+  8^4 lattice (n = 49152), kappa = 0.125, antiperiodic time, smooth SU(3)
+  links proj(exp(i 0.3 G)) (seed 2), L = 4 Gaussian sources, N = 32
+  quadrature points on the line pair L+- (beta = 0.3, N' = 16) around the
+  interval [0.105, 0.120] -- the lowest positive cluster of the spectrum
+  (12 eigenpairs) -- M = 8 moments, FP64 throughout, tol 1e-12.
+
+``value`` counts accepted eigenpairs with residual <= 1e-8 per second of
+device time (inputs resident, CUDA events on the library's stream, L2
+flushed between steps).  ``e2e`` is the same metric with host inputs
+(gauge field and sources copied in, eigenvectors copied out) timed on the
+host.  Under torchrun every rank solves an independent replica (its own
+sources): the path has no data exchange, so scaling is weak and there is no
+collective on the data path.
+
+``--impl reference`` times the FP64 numpy oracle on the host cores on a
+bounded sample of the same workload (shifted-CG iterations of one source and
+one Rayleigh-Ritz pass), extrapolated to a full step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "eigenpairs/s at resid<=1e-8 (plain FP64 SS-RR, shifted CG)"
+UNIT = "eigenpairs/s"
+RES_TOL = 1e-8
+
+WORKLOAD = dict(
+    name="8^4 smooth eps=0.3 kappa=0.125 L=4 N=32 M=8 [0.105,0.120] FP64",
+    dims=(8, 8, 8, 8), kappa=0.125, bc_t=-1, kind="smooth", gauge_seed=2, eps=0.3,
+    L=4, src_seed=200, N=32, M=8, interval=(0.105, 0.120), beta=0.3, nprime=16, tol=1e-12,
+)
+
+# ---- FP64 pipe peak (alu roofline of the FP64 kernels) ---------------------------------
+# 152 SMs x 2 FP64 FMA / clock / SM x 2 flop x 2.07 GHz (GB300 FP64 runs at 1/64 of
+# FP32); a throughput probe measured 1.19-1.20 TFLOP/s at ~1.98 GHz.
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+# algorithmic cost of one element-shift update of the fused kernel (FP64):
+#   y += a p_hat (4 FMA), p_hat = r + b p_hat (4 FMA) -> 16 flop;
+#   y, p_hat read and written once -> 64 B.
+UPDATE_FLOP_PER_UNIT = 16
+UPDATE_BYTES_PER_UNIT = 64
+# stencil: 8 hops x (12 projection adds + 6 x 12 link FMA/MUL + 24 reconstruction adds)
+# + 24 = 888 FP64 instructions; counted as 1368 flop/site/rhs (FMA = 2); bytes:
+# spinor in 192 B + out 192 B + links 576 B (shared by the rhs) per site.
+STENCIL_FLOP_PER_SITE = 1368
+
+
+def _measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        return json.load(open(p))
+    return {"hbm_gbs": 6800.0, "fallback": True}
+
+
+class ClockSampler:
+    """nvidia-smi SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def make_inputs(rank=0):
+    import synthetic
+    w = WORKLOAD
+    U = synthetic.gauge_field(w["dims"], w["kind"], seed=w["gauge_seed"], eps=w["eps"])
+    src = synthetic.gaussian_sources(w["dims"], w["L"], seed=w["src_seed"] + 1000 * rank)
+    return U, src
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_1004_0292_gb300 as ss
+    from paper_1004_0292_gb300 import build as ssbuild
+
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    ssbuild.build()
+    w = WORKLOAD
+    U, src = make_inputs(rank)
+    stream = torch.cuda.current_stream()
+    lat = ss.create_lattice(w["dims"], w["kappa"], w["bc_t"], stream=stream)
+    U_d = torch.from_numpy(U).cuda()
+    src_d = torch.from_numpy(src).cuda()
+    ss.upload_gauge(lat, U_d)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
+
+    def step(timing=False):
+        res = ss.ss_solve(lat, w["interval"], w["N"], w["M"], src_d, beta=w["beta"], nprime=w["nprime"],
+                          tol=w["tol"])
+        if res.status != ss.OK:
+            raise RuntimeError(f"solve failed with status {res.status}")
+        ev, _, rs, st = ss.ss_eigpairs(res, want_vectors=False)
+        return ev, rs, st
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ss.set_kernel_timing(True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    launches0 = ss.kernel_launches()
+    times, counts, stats = [], [], []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        ev, rs, st = step()
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+        counts.append(int(np.sum(rs <= RES_TOL)))
+        stats.append(st)
+    torch.cuda.synchronize()
+    launches = ss.kernel_launches() - launches0
+    clk = clocks.stop()
+    ss.set_kernel_timing(False)
+    total_ms = float(sum(times))
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        c = torch.tensor([float(sum(counts))], dtype=torch.float64, device="cuda")
+        dist.all_reduce(c, op=dist.ReduceOp.SUM)
+        total_ms, total_pairs = float(t.item()), float(c.item())
+    else:
+        total_pairs = float(sum(counts))
+    value = total_pairs / (total_ms / 1e3)
+
+    # ---- roofline of the dominant kernel (fused multi-shift update) ----
+    n = 12 * int(np.prod(w["dims"]))
+    ms_upd = sum(s["ms_k_update"] for s in stats)
+    units = sum(s["shift_updates"] for s in stats) * n
+    launches_upd = sum(s["launches_update"] for s in stats)
+    flops = UPDATE_FLOP_PER_UNIT * units
+    achieved_tf = flops / (ms_upd / 1e3) / 1e12
+    bytes_upd = UPDATE_BYTES_PER_UNIT * units
+    peaks = _measured_peaks()
+    ms_sten = sum(s["ms_k_stencil"] for s in stats)
+    it_tot = sum(s["iterations"] for s in stats)
+    V = int(np.prod(w["dims"]))
+    sten_bytes = it_tot * V * (w["L"] * 2 * 192 + 576)
+    sten_flops = it_tot * V * w["L"] * STENCIL_FLOP_PER_SITE
+
+    # ---- end to end through the C ABI with host buffers ----
+    e2e = None
+    if rank == 0 or world > 1:
+        e2e_times, e2e_pairs = [], []
+        h2d = U.nbytes + src.nbytes
+        d2h = 0
+        for _ in range(max(1, min(3, args.steps))):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            lat2 = ss.create_lattice(w["dims"], w["kappa"], w["bc_t"], stream=stream)
+            ss.upload_gauge(lat2, U)
+            res = ss.ss_solve(lat2, w["interval"], w["N"], w["M"], src, beta=w["beta"], nprime=w["nprime"],
+                              tol=w["tol"])
+            ev, vec, rs, st = ss.ss_eigpairs(res, want_vectors=True)
+            torch.cuda.synchronize()
+            e2e_times.append(time.perf_counter() - t0)
+            e2e_pairs.append(int(np.sum(rs <= RES_TOL)))
+            d2h = ev.nbytes + rs.nbytes + vec.nbytes
+            del res, lat2
+        e2e = {"value": float(sum(e2e_pairs) / sum(e2e_times)), "unit": UNIT,
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(stats[-1], counts[-1], budget_s=args.cpu_budget)
+
+    if rank == 0:
+        lat_sorted = sorted(times)
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded smooth SU(3) links, Gaussian sources)",
+            "config": {"workload": WORKLOAD["name"], "lattice": list(w["dims"]), "kappa": w["kappa"],
+                       "sources": w["L"], "quad_points": w["N"], "moments": w["M"],
+                       "interval": list(w["interval"]), "beta": w["beta"], "nprime": w["nprime"],
+                       "tol": w["tol"], "parallelism": f"replicas x{world}",
+                       "l2": "flushed between steps (256 MB write)"},
+            "eigenpairs_per_step": counts[-1], "iterations_per_step": stats[-1]["iterations"],
+            "latency_ms": {"p50": float(np.percentile(lat_sorted, 50)), "p99": float(np.percentile(lat_sorted, 99))},
+            "phase_ms": {"cg": stats[-1]["ms_cg"], "moments": stats[-1]["ms_moments"], "rr": stats[-1]["ms_rr"]},
+            "roofline": {
+                "kernel": "shift_update_kernel (fused multi-shift update, FP64)",
+                "bound": "alu", "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved_tf / FP64_PEAK_TFLOPS, "traffic": None,
+                "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz",
+                "hbm_achieved_gbs": bytes_upd / (ms_upd / 1e3) / 1e9,
+                "hbm_frac_of_measured": bytes_upd / (ms_upd / 1e3) / 1e9 / peaks["hbm_gbs"],
+                "avg_launch_us": 1e3 * ms_upd / max(1, launches_upd),
+                "share_of_step": ms_upd / total_ms * world,
+            },
+            "stencil": {"bound": "alu", "achieved_tflops": sten_flops / (ms_sten / 1e3) / 1e12,
+                        "frac_fp64_peak": sten_flops / (ms_sten / 1e3) / 1e12 / FP64_PEAK_TFLOPS,
+                        "hbm_gbs": sten_bytes / (ms_sten / 1e3) / 1e9,
+                        "avg_launch_us": 1e3 * ms_sten / max(1, it_tot)},
+            "kernel_ms_per_step": {"stencil": ms_sten / args.steps, "seed_update": sum(s["ms_k_seed"] for s in stats) / args.steps,
+                                   "shift_scalars": sum(s["ms_k_scalars"] for s in stats) / args.steps,
+                                   "shift_update": ms_upd / args.steps},
+            "e2e": e2e, "cpu_baseline": cpu, "clocks": clk, "gpu_launches": int(launches),
+        }
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def cpu_baseline(gpu_stats, pairs, budget_s=20.0, sample_iters=None):
+    """Time the oracle on a bounded sample of the workload and extrapolate a
+    full step: (shifted-CG iterations of one source) x iterations x L plus one
+    Rayleigh-Ritz pass on a random moment block of the same shape."""
+    import synthetic
+    from oracle import contour, rayleigh_ritz, shifted_cg, wilson
+    w = WORKLOAD
+    U, src = make_inputs(0)
+    dims = w["dims"]
+    A = lambda x: wilson.apply_H(U, x, w["kappa"], dims, w["bc_t"])
+    gamma, rho = contour.window_from_interval(*w["interval"], w["N"], w["nprime"])
+    z = contour.line_nodes(gamma, rho, w["beta"], w["N"])
+    # calibrate: a few iterations, then as many as fit in half the budget
+    t0 = time.perf_counter()
+    k_cal = 4
+    try:
+        shifted_cg.shifted_cg(A, src[0], z, tol=1e-12, max_iter=k_cal)
+    except shifted_cg.NoConvergence:
+        pass
+    t_it = (time.perf_counter() - t0) / k_cal
+    k = sample_iters or max(4, int(0.5 * budget_s / max(t_it, 1e-6)))
+    t0 = time.perf_counter()
+    try:
+        shifted_cg.shifted_cg(A, src[0], z, tol=1e-12, max_iter=k)
+    except shifted_cg.NoConvergence:
+        pass
+    t_iter = (time.perf_counter() - t0) / k
+    V = synthetic.volume(dims)
+    m = w["M"] * w["L"]
+    g = synthetic.rng(7)
+    S = g.standard_normal((12 * V, m)) + 1j * g.standard_normal((12 * V, m))
+    t0 = time.perf_counter()
+    rayleigh_ritz.rayleigh_ritz(lambda X: A(X.T.reshape(X.shape[1], V, 4, 3)).reshape(X.shape[1], -1).T, S)
+    t_rr = time.perf_counter() - t0
+    iters = gpu_stats["iterations"]
+    t_step = t_iter * iters * w["L"] + t_rr
+    try:
+        import threadpoolctl
+        info = threadpoolctl.threadpool_info()
+        cores = max([i.get("num_threads", 1) for i in info] + [1])
+    except Exception:
+        cores = os.cpu_count() or 1
+    return {"value": pairs / t_step, "unit": UNIT, "cores": int(cores), "kind": "oracle",
+            "sample": (f"{k} shifted-CG iterations of 1 source (all {w['N']} shifts, {t_iter*1e3:.1f} ms/iter) "
+                       f"+ 1 Rayleigh-Ritz pass on a {12*V}x{m} block ({t_rr:.2f} s); extrapolated to "
+                       f"{iters} iterations x {w['L']} sources = {t_step:.1f} s per step"),
+            "extrapolated": True}
+
+
+def run_reference(args):
+    world, rank, local = _dist()
+    if rank != 0:
+        return
+    # each step: a bounded sample of the workload timed on the host cores
+    iters_full = 500  # the FP64 solve needs ~500 seed iterations on this workload
+    pairs = 12
+    fake_stats = {"iterations": iters_full}
+    vals = []
+    for i in range(args.warmup + args.steps):
+        cb = cpu_baseline(fake_stats, pairs, budget_s=args.cpu_budget / 2, sample_iters=8)
+        if i >= args.warmup:
+            vals.append(cb)
+    value = float(np.mean([v["value"] for v in vals]))
+    out = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * pairs / value,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded smooth SU(3) links, Gaussian sources)",
+        "config": {"workload": WORKLOAD["name"], "parallelism": "host cores (numpy oracle)"},
+        "cpu_baseline": {"kind": "oracle", "cores": vals[-1]["cores"], "sample": vals[-1]["sample"], "value": value},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,222 @@
+/*
+ * ssqcd -- contour-integral (Sakurai-Sugiura) eigensolver with shifted CG for
+ * the Hermitian Wilson fermion matrix A = gamma5 (I - kappa D), on one GPU.
+ *
+ * C ABI.  Plain pointers and sizes only.  Every function returns an int
+ * status (SSQCD_OK = 0 or one of the SSQCD_ERR_* codes below) and never
+ * aborts; ssqcd_last_error() returns a thread-local message for the last
+ * failure on the calling thread.
+ *
+ * Conventions used by every entry point:
+ *  - lattice dims[4] = {X, Y, Z, T}; site s = x + X*(y + Y*(z + Z*t)),
+ *    V = X*Y*Z*T, vector length n = 12 V;
+ *  - complex numbers are interleaved (re, im) doubles ("complex128");
+ *  - a spinor field is [V][4 spin][3 colour] complex128; a block of L fields
+ *    is [L][V][4][3];
+ *  - a gauge field is [4 mu][V][3][3] complex128, U[mu][s] is the link from
+ *    s to s + mu_hat (mu = 0..3 = x, y, z, t), row-major 3x3;
+ *  - the operator (Section 4 of the paper; D written out as the standard
+ *    Wilson hopping matrix with r = 1):
+ *      (D psi)(x) = sum_mu (1 - gamma_mu) U_mu(x) psi(x + mu)
+ *                        + (1 + gamma_mu) U_mu(x - mu)^H psi(x - mu),
+ *    DeGrand-Rossi (chiral) gamma basis, gamma5 = gamma1 gamma2 gamma3 gamma4
+ *    = diag(1, 1, -1, -1); periodic in x, y, z, sign bc_t on hops across
+ *    the t boundary;
+ *  - pointer arguments tagged "host or device" are read/written as device
+ *    memory when the matching on_device flag is nonzero, else as host memory;
+ *    the library copies what it needs and never keeps a caller's pointer.
+ *
+ * Ownership: handles own all device memory they allocate; destroy them with
+ * the matching *_destroy.  All device work is issued on the CUDA stream given
+ * at lattice creation; calls that return host data synchronise that stream.
+ */
+#ifndef SSQCD_H
+#define SSQCD_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes -------------------------------------------------------- */
+#define SSQCD_OK            0
+#define SSQCD_ERR_ARG       1  /* invalid argument (sizes, NULL, state)          */
+#define SSQCD_ERR_OOM       2  /* device allocation failed                       */
+#define SSQCD_ERR_BREAKDOWN 3  /* seed CG breakdown: |(p, K p)| < 1e-30 (r, r)   */
+#define SSQCD_ERR_NOCONV    4  /* shifted CG hit max_iter before every shift met tol */
+#define SSQCD_ERR_CUDA      5  /* a CUDA runtime call failed                     */
+
+/* ---- precision of the solve loop ------------------------------------------ */
+#define SSQCD_FP64  0  /* everything in FP64 ("plain")                          */
+#define SSQCD_MIXED 1  /* FP32 stencil + shift updates, FP16 links, FP64 reliable
+                          updates, FP64 moments and Rayleigh-Ritz              */
+
+/* ---- contour shapes --------------------------------------------------------- */
+#define SSQCD_PATH_LINES  0  /* L+-: z = gamma + rho (x +- i beta), Section 3      */
+#define SSQCD_PATH_CIRCLE 1  /* C:  z = gamma + rho exp(2 pi i (j + 1/2)/N), Sec. 2.1 */
+
+typedef struct ssqcd_lattice_s* ssqcd_lattice;
+typedef struct ssqcd_result_s*  ssqcd_result;
+
+/* Options of ssqcd_ss_solve.  Zero-initialise, then set what you need;
+ * ssqcd_default_opts() fills the defaults named below. */
+typedef struct {
+  int    path;            /* SSQCD_PATH_LINES (default) or SSQCD_PATH_CIRCLE     */
+  double beta;            /* L+- half gap in units of rho (Section 3); 0.3       */
+  int    nprime;          /* N': even, 4 <= N' <= N; 0 selects N/2 (Section 3)   */
+  double tol;             /* per-shift stop ||r_j|| / ||v|| <= tol; 1e-12 (Sec. 4) */
+  double sigma;           /* real seed shift (Section 2.2); 0 as in Section 4    */
+  int    max_iter;        /* cap on seed CG iterations; 100000                   */
+  double rank_tol;        /* keep basis directions with singular value above
+                             rank_tol * largest; 1e-14                           */
+  const double* sources;  /* host or device: [L][V][4][3] complex128, required  */
+  int    sources_on_device;
+  int    reliable_every;  /* SSQCD_MIXED: FP64 seed-residual refresh period; 50   */
+} ssqcd_opts;
+
+/* Counters of one solve.  Times are device milliseconds between CUDA events. */
+typedef struct {
+  int    iterations;      /* seed CG iterations = stencil applications in the loop */
+  int    max_shift_iters; /* largest per-shift iteration count at freeze           */
+  int    matvecs_rr;      /* extra stencil applications in Rayleigh-Ritz           */
+  int    rank;            /* dimension of the orthonormal basis kept               */
+  int    n_ritz;          /* Ritz values computed (= rank)                         */
+  int    n_accepted;      /* Ritz values inside the accepted interval              */
+  int    reliable_updates;/* FP64 seed-residual refreshes (mixed path)             */
+  double ms_cg;           /* shifted-CG loop                                        */
+  double ms_moments;      /* moment accumulation                                    */
+  double ms_rr;           /* Rayleigh-Ritz, acceptance and residuals                */
+  double gamma, rho;      /* the window actually used                               */
+  long long shift_updates;/* sum over (source, shift) of iterations before freezing:
+                             each is one y / p-hat update of n elements            */
+  /* Per-kernel device time of the shifted-CG loop, filled when kernel timing
+   * is on (ssqcd_set_kernel_timing): CUDA events on the lattice stream around
+   * every launch; zero otherwise. */
+  int    timed;
+  int    launches_update;   /* fused multi-shift update launches that did work   */
+  double ms_k_stencil;      /* stencil q = K p with the (p, q) partials           */
+  double ms_k_seed;         /* seed update r -= alpha q                           */
+  double ms_k_scalars;      /* shift scalar recurrences                           */
+  double ms_k_update;       /* fused multi-shift update                           */
+} ssqcd_stats;
+
+/* ---- lattice / operator ---------------------------------------------------- */
+
+/* Create a lattice of extents dims[4] with hopping parameter kappa and time
+ * boundary sign bc_t (+1 periodic, -1 antiperiodic), for the given precision
+ * (SSQCD_FP64 or SSQCD_MIXED); every extent must be >= 1 and V <= 2^27.  cuda_stream is a
+ * cudaStream_t (NULL = legacy default stream) on which all later work runs.
+ * The operator is Section 4's A = gamma5 (I - kappa D).  On success *out owns
+ * the gauge storage (no field until ssqcd_upload_gauge). */
+int ssqcd_create_lattice(const int dims[4], double kappa, int bc_t, int precision,
+                         void* cuda_stream, ssqcd_lattice* out);
+
+/* Copy a gauge field ([4][V][3][3] complex128, host or device) into the
+ * lattice, converting it to the library's device layout (and to FP16
+ * 12-parameter storage as well for SSQCD_MIXED).  The caller keeps ownership
+ * of `links`.  Links are used as given (no unitarity check). */
+int ssqcd_upload_gauge(ssqcd_lattice lat, const double* links, int on_device);
+
+/* out = A in for nrhs spinor fields ([nrhs][V][4][3] complex128; in and out
+ * both host, or both device, per on_device; they must not overlap).  A is
+ * the Hermitian fermion matrix of Section 4, applied in FP64. */
+int ssqcd_apply_H(ssqcd_lattice lat, const double* in, double* out, int nrhs, int on_device);
+
+/* Same as ssqcd_apply_H with the mixed path's operator: links stored FP16
+ * with 12-parameter SU(3) reconstruction, spinors and arithmetic in FP32.
+ * Input and output stay complex128 at the boundary.  Requires a lattice
+ * created with SSQCD_MIXED. */
+int ssqcd_apply_H_mixed(ssqcd_lattice lat, const double* in, double* out, int nrhs, int on_device);
+
+void ssqcd_lattice_destroy(ssqcd_lattice lat);
+
+/* ---- quadrature (host) -------------------------------------------------------- */
+
+/* Quadrature points z[N] and weights w[N] (complex128, host) for a contour:
+ *  - SSQCD_PATH_LINES (Section 3): N/2 equally spaced points per line, ends
+ *    included, x_i = -1 + 2 i/(N/2 - 1); z_{2i} = gamma + rho (x_i + i beta)
+ *    on L+, z_{2i+1} = gamma + rho (x_i - i beta) on L-;
+ *  - SSQCD_PATH_CIRCLE (Section 2.1): z_j = gamma + rho exp(2 pi i (j+1/2)/N).
+ * Weights are the solution of the Section 3 system
+ *    sum_j w_j zeta_j^(k-1) = delta_{k0}, k = 0..N-1, zeta_j = (z_j - gamma)/rho,
+ * in closed form w_j = -P(0)/P'(zeta_j), P(zeta) = prod_k (zeta - zeta_k)
+ * (for C this is zeta_j / N, Section 2.1 normalised by rho).
+ * N must be even and >= 4 (lines) or >= 1 (circle); rho > 0. */
+int ssqcd_contour(int path, double gamma, double rho, double beta, int N, double* z, double* w);
+
+/* ---- shifted CG (Section 2.2) ---------------------------------------------- */
+
+/* Solve (z_j I - A) y_{l,j} = v_l for the N shifts z[N] (complex128, host) and
+ * L sources v ([L][V][4][3] complex128, host or device per on_device) with one
+ * CG recurrence per source on the seed matrix sigma I - A (sigma real) and the
+ * shifted-CG recurrences (residual of shift j = xi_j times the seed residual).
+ * A shift stops when |xi_j| ||r|| / ||v_l|| <= tol.  Outputs (host or device,
+ * per on_device, each may be NULL): y [L][N][V][4][3] complex128;
+ * iters [L][N] int, the iteration at which each shift stopped; xi [L][N]
+ * complex128, its final xi.  *seed_iters (may be NULL) receives the number of
+ * seed iterations.  precision selects SSQCD_FP64 or SSQCD_MIXED (the latter
+ * needs a SSQCD_MIXED lattice; reliable_every as in ssqcd_opts).
+ * Returns SSQCD_ERR_BREAKDOWN or SSQCD_ERR_NOCONV when the loop cannot finish
+ * (outputs then hold the last iterate). */
+int ssqcd_shifted_cg(ssqcd_lattice lat, int N, const double* z, int L, const double* v,
+                     int on_device, double sigma, double tol, int max_iter, int precision,
+                     int reliable_every,
+                     double* y, int* iters, double* xi, int* seed_iters);
+
+/* ---- moments (Eq. 2) ------------------------------------------------------------ */
+
+/* s_hat[l][k] = sum_j w_j zeta_j^k y[l][j] for k < M (Eq. 2), on the device,
+ * FP64.  y: [L][N][V][4][3] complex128 and s_hat: [L][M][V][4][3] complex128,
+ * both host or both device per on_device; w, zeta: [N] complex128 host. */
+int ssqcd_moments(ssqcd_lattice lat, int N, int M, int L, const double* w, const double* zeta,
+                  const double* y, double* s_hat, int on_device);
+
+/* ---- the eigensolver --------------------------------------------------------------- */
+
+void ssqcd_default_opts(ssqcd_opts* opts);
+
+/* Find the eigenpairs of A in the accepted interval [interval[0], interval[1]]
+ * (the paper's Sections 2-3): quadrature points on the line pair L+- placed so
+ * that the N' central points span the interval (gamma = (a + b)/2,
+ * rho = (b - a)/2 (N/2 - 1)/(N'/2 - 1)), or on the circle C of centre
+ * (a + b)/2 and radius (b - a)/2; shifted CG for all N points and L sources;
+ * moments s_hat_k, k < M; Rayleigh-Ritz on span(S_hat) (n x M L); Ritz values
+ * in [a, b] are accepted.  The lattice precision decides the solve loop.
+ * *out receives a result handle (even when the status is an error other than
+ * SSQCD_ERR_ARG/OOM, so its stats can be read). */
+int ssqcd_ss_solve(ssqcd_lattice lat, const double interval[2], int N, int M, int L,
+                   const ssqcd_opts* opts, ssqcd_result* out);
+
+/* Read a result.  *count receives the number of accepted eigenpairs; pass
+ * evals = NULL first to query it.  evals [count] (ascending), residuals
+ * [count] = ||A x - lambda x||_2 with ||x||_2 = 1 (Section 4), evecs
+ * [count][V][4][3] complex128 (host; may be NULL), stats (may be NULL). */
+int ssqcd_ss_eigpairs(ssqcd_result res, int* count, double* evals, double* evecs,
+                      double* residuals, ssqcd_stats* stats);
+
+void ssqcd_result_destroy(ssqcd_result res);
+
+/* ---- small dense helper (host) ----------------------------------------------------- */
+
+/* Eigen-decomposition of an m x m complex Hermitian matrix (row-major
+ * complex128, host; only the lower triangle is read): evals[m] ascending,
+ * evecs[m][m] row-major with eigenvector k in column k (may be NULL).  This
+ * is the small eigenproblem of the Rayleigh-Ritz step (Section 2.1);
+ * Householder reduction to real tridiagonal form, then implicit QL. */
+int ssqcd_small_eigh(int m, const double* a, double* evals, double* evecs);
+
+/* ---- diagnostics ------------------------------------------------------------------------- */
+
+const char* ssqcd_last_error(void);
+
+/* Kernel launches issued by this process so far (all entry points). */
+long long ssqcd_kernel_launches(void);
+
+/* Turn per-kernel CUDA-event timing of the shifted-CG loop on (1) or off (0)
+ * for later solves in this process (see the ms_k_* fields of ssqcd_stats).
+ * Timing adds two event records per timed launch. */
+int ssqcd_set_kernel_timing(int enable);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SSQCD_H */

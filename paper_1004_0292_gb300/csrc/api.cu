@@ -1,0 +1,448 @@
+// C-ABI entry points: lattice handles, gauge upload, operator application,
+// shifted CG, moments and the Sakurai-Sugiura / Rayleigh-Ritz solve.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "internal.h"
+
+using namespace ssqcd;
+
+struct ssqcd_result_s {
+  cudaStream_t stream = nullptr;
+  long long n = 0;
+  int V = 0;
+  std::vector<double> evals;
+  std::vector<double> residuals;
+  DevBuf evecs;  // [count][12][V] device layout
+  ssqcd_stats stats{};
+};
+
+namespace {
+
+int check_lattice(ssqcd_lattice lat, bool need_gauge) {
+  if (lat == nullptr) return fail(SSQCD_ERR_ARG, "NULL lattice");
+  if (need_gauge && !lat->has_gauge) return fail(SSQCD_ERR_ARG, "no gauge field uploaded");
+  return SSQCD_OK;
+}
+
+// Bring a user-layout block of nf spinor fields (host or device) to the device
+// layout in `dst` (resized).
+int to_device_layout(ssqcd_lattice lat, const double* src, int nf, int on_device, DevBuf& dst) {
+  const int V = lat->g.V;
+  const size_t bytes = sizeof(double2) * 12 * (size_t)V * nf;
+  SS_TRY(dst.alloc(bytes));
+  const double2* user = reinterpret_cast<const double2*>(src);
+  if (!on_device) {
+    SS_TRY(lat->stage.alloc(bytes));
+    SS_CUDA(cudaMemcpyAsync(lat->stage.p, src, bytes, cudaMemcpyHostToDevice, lat->stream));
+    user = lat->stage.as<double2>();
+  }
+  return pack_spinors(user, dst.as<double2>(), nf, V, lat->stream);
+}
+
+// Write nf device-layout fields to a user-layout buffer (host or device).
+int from_device_layout(ssqcd_lattice lat, const double2* src, int nf, int on_device, double* dst) {
+  const int V = lat->g.V;
+  const size_t bytes = sizeof(double2) * 12 * (size_t)V * nf;
+  if (on_device) return unpack_spinors(src, reinterpret_cast<double2*>(dst), nf, V, lat->stream);
+  SS_TRY(lat->stage.alloc(bytes));
+  SS_TRY(unpack_spinors(src, lat->stage.as<double2>(), nf, V, lat->stream));
+  SS_CUDA(cudaMemcpyAsync(dst, lat->stage.p, bytes, cudaMemcpyDeviceToHost, lat->stream));
+  SS_CUDA(cudaStreamSynchronize(lat->stream));
+  return SSQCD_OK;
+}
+
+}  // namespace
+
+// --------------------------------------------------------------------------------------------
+extern "C" int ssqcd_create_lattice(const int dims[4], double kappa, int bc_t, int precision, void* cuda_stream,
+                                    ssqcd_lattice* out) {
+  if (out == nullptr || dims == nullptr) return fail(SSQCD_ERR_ARG, "ssqcd_create_lattice: NULL argument");
+  *out = nullptr;
+  long long V = 1;
+  for (int i = 0; i < 4; ++i) {
+    if (dims[i] < 1) return fail(SSQCD_ERR_ARG, "lattice extents must be >= 1");
+    V *= dims[i];
+  }
+  if (V > (1LL << 27)) return fail(SSQCD_ERR_ARG, "lattice volume above 2^27 sites");
+  if (bc_t != 1 && bc_t != -1) return fail(SSQCD_ERR_ARG, "bc_t must be +1 or -1");
+  if (precision != SSQCD_FP64 && precision != SSQCD_MIXED) return fail(SSQCD_ERR_ARG, "unknown precision");
+  if (!std::isfinite(kappa)) return fail(SSQCD_ERR_ARG, "kappa must be finite");
+  int dev = 0;
+  SS_CUDA(cudaGetDevice(&dev));
+  auto* lat = new (std::nothrow) ssqcd_lattice_s();
+  if (!lat) return fail(SSQCD_ERR_OOM, "host allocation failed");
+  lat->g = Geometry{dims[0], dims[1], dims[2], dims[3], (int)V, kappa, (double)bc_t};
+  lat->precision = precision;
+  lat->stream = static_cast<cudaStream_t>(cuda_stream);
+  *out = lat;
+  return SSQCD_OK;
+}
+
+extern "C" void ssqcd_lattice_destroy(ssqcd_lattice lat) {
+  if (!lat) return;
+  cudaStreamSynchronize(lat->stream);
+  delete lat;
+}
+
+extern "C" int ssqcd_upload_gauge(ssqcd_lattice lat, const double* links, int on_device) {
+  SS_TRY(check_lattice(lat, false));
+  if (links == nullptr) return fail(SSQCD_ERR_ARG, "NULL links");
+  const int V = lat->g.V;
+  const size_t bytes = sizeof(double2) * 36 * (size_t)V;
+  SS_TRY(lat->u64.alloc(bytes));
+  const double2* user = reinterpret_cast<const double2*>(links);
+  if (!on_device) {
+    SS_TRY(lat->stage.alloc(bytes));
+    SS_CUDA(cudaMemcpyAsync(lat->stage.p, links, bytes, cudaMemcpyHostToDevice, lat->stream));
+    user = lat->stage.as<double2>();
+  }
+  SS_TRY(pack_gauge64(user, lat->u64.as<double2>(), V, lat->stream));
+  if (lat->precision == SSQCD_MIXED) {
+    SS_TRY(lat->u16.alloc(sizeof(uint2) * 12 * (size_t)V));
+    SS_TRY(pack_gauge16(lat->u64.as<double2>(), lat->u16.p, V, lat->stream));
+  }
+  SS_CUDA(cudaStreamSynchronize(lat->stream));
+  lat->has_gauge = true;
+  return SSQCD_OK;
+}
+
+extern "C" int ssqcd_apply_H(ssqcd_lattice lat, const double* in, double* out, int nrhs, int on_device) {
+  SS_TRY(check_lattice(lat, true));
+  if (nrhs < 0 || (nrhs > 0 && (in == nullptr || out == nullptr))) return fail(SSQCD_ERR_ARG, "bad apply_H arguments");
+  if (nrhs == 0) return SSQCD_OK;
+  DevBuf a, b;
+  SS_TRY(to_device_layout(lat, in, nrhs, on_device, a));
+  SS_TRY(b.alloc(a.bytes));
+  SS_TRY(wilson64(lat->g, lat->u64.as<double2>(), a.as<double2>(), b.as<double2>(), nrhs, 0.0, 1.0, nullptr,
+                  nullptr, lat->stream));
+  SS_TRY(from_device_layout(lat, b.as<double2>(), nrhs, on_device, out));
+  SS_CUDA(cudaStreamSynchronize(lat->stream));
+  return SSQCD_OK;
+}
+
+extern "C" int ssqcd_apply_H_mixed(ssqcd_lattice lat, const double* in, double* out, int nrhs, int on_device) {
+  SS_TRY(check_lattice(lat, true));
+  if (lat->precision != SSQCD_MIXED) return fail(SSQCD_ERR_ARG, "apply_H_mixed needs a SSQCD_MIXED lattice");
+  if (nrhs < 0 || (nrhs > 0 && (in == nullptr || out == nullptr))) return fail(SSQCD_ERR_ARG, "bad apply_H arguments");
+  if (nrhs == 0) return SSQCD_OK;
+  const long long n = 12LL * lat->g.V * nrhs;
+  DevBuf a, a32, b32;
+  SS_TRY(to_device_layout(lat, in, nrhs, on_device, a));
+  SS_TRY(a32.alloc(sizeof(float2) * n));
+  SS_TRY(b32.alloc(sizeof(float2) * n));
+  SS_TRY(convert_f64_to_f32(a.as<double2>(), a32.as<float2>(), n, lat->stream));
+  SS_TRY(wilson32(lat->g, lat->u16.p, a32.as<float2>(), b32.as<float2>(), nrhs, 0.f, 1.f, nullptr, nullptr,
+                  lat->stream));
+  SS_TRY(convert_f32_to_f64(b32.as<float2>(), a.as<double2>(), n, lat->stream));
+  SS_TRY(from_device_layout(lat, a.as<double2>(), nrhs, on_device, out));
+  SS_CUDA(cudaStreamSynchronize(lat->stream));
+  return SSQCD_OK;
+}
+
+extern "C" int ssqcd_shifted_cg(ssqcd_lattice lat, int N, const double* z, int L, const double* v, int on_device,
+                                double sigma, double tol, int max_iter, int precision, int reliable_every,
+                                double* y, int* iters, double* xi, int* seed_iters) {
+  SS_TRY(check_lattice(lat, true));
+  if (z == nullptr || v == nullptr) return fail(SSQCD_ERR_ARG, "NULL z or v");
+  if (N < 1 || L < 1 || !(tol > 0.0) || max_iter < 1 || !std::isfinite(sigma))
+    return fail(SSQCD_ERR_ARG, "bad shifted_cg arguments");
+  if (precision == SSQCD_MIXED && lat->precision != SSQCD_MIXED)
+    return fail(SSQCD_ERR_ARG, "mixed precision needs a SSQCD_MIXED lattice");
+  DevBuf vd, yd;
+  SS_TRY(to_device_layout(lat, v, L, on_device, vd));
+  std::vector<int> it(iters ? (size_t)L * N : 0);
+  std::vector<double2> xx(xi ? (size_t)L * N : 0);
+  ShiftedCGOut o;
+  const int st = shifted_cg_device(lat, N, reinterpret_cast<const double2*>(z), L, vd.as<double2>(), sigma, tol,
+                                   max_iter, precision, reliable_every, yd, iters ? it.data() : nullptr,
+                                   xi ? xx.data() : nullptr, &o);
+  if (st != SSQCD_OK && st != SSQCD_ERR_BREAKDOWN && st != SSQCD_ERR_NOCONV) return st;
+  if (y != nullptr) SS_TRY(from_device_layout(lat, yd.as<double2>(), L * N, on_device, y));
+  if (iters != nullptr) {
+    if (on_device) SS_CUDA(cudaMemcpy(iters, it.data(), sizeof(int) * it.size(), cudaMemcpyHostToDevice));
+    else std::memcpy(iters, it.data(), sizeof(int) * it.size());
+  }
+  if (xi != nullptr) {
+    if (on_device) SS_CUDA(cudaMemcpy(xi, xx.data(), sizeof(double2) * xx.size(), cudaMemcpyHostToDevice));
+    else std::memcpy(xi, xx.data(), sizeof(double2) * xx.size());
+  }
+  if (seed_iters) *seed_iters = o.seed_iters;
+  SS_CUDA(cudaStreamSynchronize(lat->stream));
+  return st;
+}
+
+extern "C" int ssqcd_moments(ssqcd_lattice lat, int N, int M, int L, const double* w, const double* zeta,
+                             const double* y, double* s_hat, int on_device) {
+  SS_TRY(check_lattice(lat, false));
+  if (N < 1 || M < 1 || L < 1 || !w || !zeta || !y || !s_hat) return fail(SSQCD_ERR_ARG, "bad moments arguments");
+  std::vector<double2> coef((size_t)N * M);
+  for (int j = 0; j < N; ++j) {
+    double zr = 1.0, zi = 0.0;  // zeta_j^k
+    for (int k = 0; k < M; ++k) {
+      const double wr = w[2 * j], wi = w[2 * j + 1];
+      coef[(size_t)j * M + k] = make_double2(wr * zr - wi * zi, wr * zi + wi * zr);
+      const double ar = zeta[2 * j], ai = zeta[2 * j + 1];
+      const double nr = zr * ar - zi * ai, ni = zr * ai + zi * ar;
+      zr = nr;
+      zi = ni;
+    }
+  }
+  DevBuf yd, sd, scratch;
+  SS_TRY(to_device_layout(lat, y, L * N, on_device, yd));
+  const long long n = 12LL * lat->g.V;
+  SS_TRY(sd.alloc(sizeof(double2) * n * M * L));
+  SS_TRY(moments_device(yd.as<double2>(), N, M, L, n, coef.data(), sd.as<double2>(), scratch, lat->stream));
+  SS_TRY(from_device_layout(lat, sd.as<double2>(), L * M, on_device, s_hat));
+  SS_CUDA(cudaStreamSynchronize(lat->stream));
+  return SSQCD_OK;
+}
+
+namespace ssqcd {
+
+int moments_device(const double2* y, int N, int M, int L, long long n, const double2* coef_host, double2* s_hat,
+                   DevBuf& scratch, cudaStream_t s) {
+  SS_TRY(scratch.alloc(sizeof(double2) * (size_t)N * M));
+  SS_CUDA(cudaMemcpyAsync(scratch.p, coef_host, sizeof(double2) * (size_t)N * M, cudaMemcpyHostToDevice, s));
+  for (int l = 0; l < L; ++l)
+    SS_TRY(combine(y + (long long)l * N * n, N, n, scratch.as<double2>(), M, s_hat + (long long)l * M * n, s));
+  // the coefficient upload must finish before `scratch` can be reused by the caller
+  SS_CUDA(cudaStreamSynchronize(s));
+  return SSQCD_OK;
+}
+
+}  // namespace ssqcd
+
+// --------------------------------------------------------------------------------------------
+extern "C" void ssqcd_default_opts(ssqcd_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->path = SSQCD_PATH_LINES;
+  o->beta = 0.3;
+  o->nprime = 0;
+  o->tol = 1e-12;
+  o->sigma = 0.0;
+  o->max_iter = 100000;
+  o->rank_tol = 1e-14;
+  o->reliable_every = 50;
+}
+
+namespace {
+
+// Orthonormal basis of span(S) (m vectors of length n, device): CGS2 QR on
+// the device, S = Q0 R, then the SVD of the small R on the host,
+// R = U Sigma W^H, so that S = (Q0 U) Sigma W^H.  The basis is Q0 U_r, the
+// left singular vectors of S whose singular value exceeds rank_tol times the
+// largest (the paper leaves the orthogonalisation open).  Returns r, Q [r][n].
+int orthonormalise(const double2* S, int m, long long n, double rank_tol, DevBuf& Q, int& r, DevBuf& tmp,
+                   DevBuf& scratch, cudaStream_t st) {
+  DevBuf Rd, Cd;
+  SS_TRY(Rd.alloc(sizeof(double2) * m * m));
+  SS_TRY(tmp.alloc(sizeof(double2) * n * m));
+  SS_TRY(cgs2(S, m, n, tmp.as<double2>(), Rd.as<double2>(), scratch, st));
+  std::vector<double2> R((size_t)m * m), U((size_t)m * m);
+  std::vector<double> sig(m);
+  SS_CUDA(cudaMemcpyAsync(R.data(), Rd.p, sizeof(double2) * m * m, cudaMemcpyDeviceToHost, st));
+  SS_CUDA(cudaStreamSynchronize(st));
+  SS_TRY(small_svd_left(m, R.data(), sig.data(), U.data()));
+  if (!(sig[0] > 0.0)) return fail(SSQCD_ERR_ARG, "moment block is zero");
+  int r1 = 0;
+  while (r1 < m && sig[r1] > rank_tol * sig[0]) ++r1;
+  std::vector<double2> C((size_t)m * r1);
+  for (int a = 0; a < m; ++a)
+    for (int c = 0; c < r1; ++c) C[(size_t)a * r1 + c] = U[(size_t)a * m + c];
+  SS_TRY(Cd.alloc(sizeof(double2) * m * r1));
+  SS_CUDA(cudaMemcpyAsync(Cd.p, C.data(), sizeof(double2) * m * r1, cudaMemcpyHostToDevice, st));
+  SS_TRY(Q.alloc(sizeof(double2) * n * r1));
+  SS_TRY(combine(tmp.as<double2>(), m, n, Cd.as<double2>(), r1, Q.as<double2>(), st));
+  SS_CUDA(cudaStreamSynchronize(st));
+  r = r1;
+  return SSQCD_OK;
+}
+
+}  // namespace
+
+extern "C" int ssqcd_ss_solve(ssqcd_lattice lat, const double interval[2], int N, int M, int L,
+                              const ssqcd_opts* opts_in, ssqcd_result* out) {
+  if (out == nullptr) return fail(SSQCD_ERR_ARG, "NULL result pointer");
+  *out = nullptr;
+  SS_TRY(check_lattice(lat, true));
+  if (interval == nullptr || !(interval[1] > interval[0])) return fail(SSQCD_ERR_ARG, "interval must have b > a");
+  if (N < 1 || M < 1 || L < 1) return fail(SSQCD_ERR_ARG, "N, M, L must be >= 1");
+  ssqcd_opts o;
+  ssqcd_default_opts(&o);
+  if (opts_in) o = *opts_in;
+  if (o.sources == nullptr) return fail(SSQCD_ERR_ARG, "opts.sources is required");
+  const double a = interval[0], b = interval[1];
+  double gamma = 0.5 * (a + b), rho = 0.5 * (b - a);
+  if (o.path == SSQCD_PATH_LINES) {
+    const int np = o.nprime == 0 ? N / 2 : o.nprime;
+    if (N < 4 || N % 2 || np < 4 || np % 2 || np > N)
+      return fail(SSQCD_ERR_ARG, "lines need even N >= 4 and even 4 <= N' <= N");
+    rho = 0.5 * (b - a) * (N / 2 - 1) / (double)(np / 2 - 1);
+  } else if (o.path != SSQCD_PATH_CIRCLE) {
+    return fail(SSQCD_ERR_ARG, "unknown path");
+  }
+  std::vector<double2> z, w;
+  SS_TRY(contour_nodes(o.path, gamma, rho, o.beta, N, z, w));
+  // moment coefficients c[j][k] = w_j zeta_j^k
+  std::vector<double2> coef((size_t)N * M);
+  for (int j = 0; j < N; ++j) {
+    const double zr0 = (z[j].x - gamma) / rho, zi0 = z[j].y / rho;
+    double zr = 1.0, zi = 0.0;
+    for (int k = 0; k < M; ++k) {
+      coef[(size_t)j * M + k] = make_double2(w[j].x * zr - w[j].y * zi, w[j].x * zi + w[j].y * zr);
+      const double nr = zr * zr0 - zi * zi0, ni = zr * zi0 + zi * zr0;
+      zr = nr;
+      zi = ni;
+    }
+  }
+  auto* res = new (std::nothrow) ssqcd_result_s();
+  if (!res) return fail(SSQCD_ERR_OOM, "host allocation failed");
+  res->stream = lat->stream;
+  res->V = lat->g.V;
+  res->n = 12LL * lat->g.V;
+  res->stats.gamma = gamma;
+  res->stats.rho = rho;
+  const long long n = res->n;
+  cudaStream_t st = lat->stream;
+  auto bail = [&](int code) {
+    *out = res;
+    return code;
+  };
+
+  // sources -> device layout
+  DevBuf vd, yd, S, Q, tmp, AQ, scratch;
+  int s1 = to_device_layout(lat, o.sources, L, o.sources_on_device, vd);
+  if (s1 != SSQCD_OK) { delete res; return s1; }
+  // shifted CG
+  ShiftedCGOut cg;
+  std::vector<int> iters((size_t)N * L);
+  s1 = shifted_cg_device(lat, N, z.data(), L, vd.as<double2>(), o.sigma, o.tol, o.max_iter, lat->precision,
+                         o.reliable_every, yd, iters.data(), nullptr, &cg);
+  res->stats.iterations = cg.seed_iters;
+  res->stats.reliable_updates = cg.reliable_updates;
+  res->stats.ms_cg = cg.ms;
+  res->stats.max_shift_iters = iters.empty() ? 0 : *std::max_element(iters.begin(), iters.end());
+  res->stats.shift_updates = cg.shift_updates;
+  res->stats.timed = cg.timed ? 1 : 0;
+  res->stats.launches_update = cg.launches_update;
+  res->stats.ms_k_stencil = cg.ms_k[0];
+  res->stats.ms_k_seed = cg.ms_k[1];
+  res->stats.ms_k_scalars = cg.ms_k[2];
+  res->stats.ms_k_update = cg.ms_k[3];
+  if (s1 != SSQCD_OK) return bail(s1);
+  vd.release();
+
+  cudaEvent_t e0, e1, e2;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaEventCreate(&e2);
+  cudaEventRecord(e0, st);
+  // moments
+  const int m = M * L;
+  if ((s1 = S.alloc(sizeof(double2) * n * m)) != SSQCD_OK) return bail(s1);
+  if ((s1 = moments_device(yd.as<double2>(), N, M, L, n, coef.data(), S.as<double2>(), scratch, st)) != SSQCD_OK)
+    return bail(s1);
+  cudaEventRecord(e1, st);
+  yd.release();
+  // Rayleigh-Ritz
+  int r = 0;
+  if ((s1 = orthonormalise(S.as<double2>(), m, n, o.rank_tol, Q, r, tmp, scratch, st)) != SSQCD_OK) return bail(s1);
+  S.release();
+  res->stats.rank = r;
+  res->stats.n_ritz = r;
+  if ((s1 = AQ.alloc(sizeof(double2) * n * r)) != SSQCD_OK) return bail(s1);
+  if ((s1 = wilson64(lat->g, lat->u64.as<double2>(), Q.as<double2>(), AQ.as<double2>(), r, 0.0, 1.0, nullptr,
+                     nullptr, st)) != SSQCD_OK)
+    return bail(s1);
+  DevBuf Gd;
+  if ((s1 = Gd.alloc(sizeof(double2) * r * r)) != SSQCD_OK) return bail(s1);
+  if ((s1 = gram(Q.as<double2>(), r, AQ.as<double2>(), r, n, Gd.as<double2>(), scratch, st)) != SSQCD_OK)
+    return bail(s1);
+  std::vector<double2> At((size_t)r * r), W((size_t)r * r);
+  std::vector<double> theta(r);
+  cudaMemcpyAsync(At.data(), Gd.p, sizeof(double2) * r * r, cudaMemcpyDeviceToHost, st);
+  if (cudaStreamSynchronize(st) != cudaSuccess) return bail(cuda_fail(cudaGetLastError(), "RR sync", __FILE__, __LINE__));
+  // Hermitian part (only the lower triangle is read by small_eigh; symmetrise it)
+  for (int i = 0; i < r; ++i)
+    for (int j = 0; j <= i; ++j) {
+      const double2 x = At[(size_t)i * r + j], y = At[(size_t)j * r + i];
+      At[(size_t)i * r + j] = make_double2(0.5 * (x.x + y.x), 0.5 * (x.y - y.y));
+    }
+  if ((s1 = small_eigh(r, At.data(), theta.data(), W.data())) != SSQCD_OK) return bail(s1);
+  std::vector<int> acc;
+  for (int c = 0; c < r; ++c)
+    if (theta[c] >= a && theta[c] <= b) acc.push_back(c);
+  const int cnt = (int)acc.size();
+  res->stats.n_accepted = cnt;
+  res->stats.matvecs_rr = r + cnt;
+  if (cnt > 0) {
+    std::vector<double2> Wacc((size_t)r * cnt);
+    for (int i = 0; i < r; ++i)
+      for (int c = 0; c < cnt; ++c) Wacc[(size_t)i * cnt + c] = W[(size_t)i * r + acc[c]];
+    DevBuf Wd, AX, th, rn;
+    if ((s1 = Wd.alloc(sizeof(double2) * r * cnt)) != SSQCD_OK) return bail(s1);
+    cudaMemcpyAsync(Wd.p, Wacc.data(), sizeof(double2) * r * cnt, cudaMemcpyHostToDevice, st);
+    if ((s1 = res->evecs.alloc(sizeof(double2) * n * cnt)) != SSQCD_OK) return bail(s1);
+    if ((s1 = combine(Q.as<double2>(), r, n, Wd.as<double2>(), cnt, res->evecs.as<double2>(), st)) != SSQCD_OK)
+      return bail(s1);
+    if ((s1 = AX.alloc(sizeof(double2) * n * cnt)) != SSQCD_OK) return bail(s1);
+    if ((s1 = wilson64(lat->g, lat->u64.as<double2>(), res->evecs.as<double2>(), AX.as<double2>(), cnt, 0.0, 1.0,
+                       nullptr, nullptr, st)) != SSQCD_OK)
+      return bail(s1);
+    res->evals.resize(cnt);
+    for (int c = 0; c < cnt; ++c) res->evals[c] = theta[acc[c]];
+    if ((s1 = th.alloc(sizeof(double) * cnt)) != SSQCD_OK) return bail(s1);
+    if ((s1 = rn.alloc(sizeof(double) * cnt)) != SSQCD_OK) return bail(s1);
+    cudaMemcpyAsync(th.p, res->evals.data(), sizeof(double) * cnt, cudaMemcpyHostToDevice, st);
+    if ((s1 = col_residual_norms(AX.as<double2>(), res->evecs.as<double2>(), th.as<double>(), cnt, n,
+                                 rn.as<double>(), scratch, st)) != SSQCD_OK)
+      return bail(s1);
+    res->residuals.resize(cnt);
+    cudaMemcpyAsync(res->residuals.data(), rn.p, sizeof(double) * cnt, cudaMemcpyDeviceToHost, st);
+    if (cudaStreamSynchronize(st) != cudaSuccess)
+      return bail(cuda_fail(cudaGetLastError(), "RR residuals", __FILE__, __LINE__));
+  }
+  cudaEventRecord(e2, st);
+  cudaEventSynchronize(e2);
+  float ms1 = 0.f, ms2 = 0.f;
+  cudaEventElapsedTime(&ms1, e0, e1);
+  cudaEventElapsedTime(&ms2, e1, e2);
+  res->stats.ms_moments = ms1;
+  res->stats.ms_rr = ms2;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaEventDestroy(e2);
+  *out = res;
+  return SSQCD_OK;
+}
+
+extern "C" int ssqcd_ss_eigpairs(ssqcd_result res, int* count, double* evals, double* evecs, double* residuals,
+                                 ssqcd_stats* stats) {
+  if (res == nullptr || count == nullptr) return fail(SSQCD_ERR_ARG, "NULL result or count");
+  const int cnt = (int)res->evals.size();
+  *count = cnt;
+  if (stats) *stats = res->stats;
+  if (evals == nullptr) return SSQCD_OK;
+  std::memcpy(evals, res->evals.data(), sizeof(double) * cnt);
+  if (residuals) std::memcpy(residuals, res->residuals.data(), sizeof(double) * cnt);
+  if (evecs && cnt > 0) {
+    DevBuf stage;
+    SS_TRY(stage.alloc(sizeof(double2) * res->n * cnt));
+    SS_TRY(unpack_spinors(res->evecs.as<double2>(), stage.as<double2>(), cnt, res->V, res->stream));
+    SS_CUDA(cudaMemcpyAsync(evecs, stage.p, sizeof(double2) * res->n * cnt, cudaMemcpyDeviceToHost, res->stream));
+    SS_CUDA(cudaStreamSynchronize(res->stream));
+  }
+  return SSQCD_OK;
+}
+
+extern "C" void ssqcd_result_destroy(ssqcd_result res) {
+  if (!res) return;
+  cudaStreamSynchronize(res->stream);
+  delete res;
+}

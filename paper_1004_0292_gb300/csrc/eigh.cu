@@ -1,0 +1,235 @@
+// Small dense complex Hermitian eigenproblem (host) for the Rayleigh-Ritz
+// step (Section 2.1): the m x m projected matrix Q^H A Q and the Gram
+// matrices of the basis, m = rank <= M L.
+//
+// Method: Householder reflections reduce A to a Hermitian tridiagonal T
+// (A = Q T Q^H); a diagonal unitary D makes T real (T' = D^H T D with
+// off-diagonals |e_k|); the implicit QL algorithm with Wilkinson shifts
+// diagonalises T' = Z Lambda Z^T with plane rotations; the eigenvectors of A
+// are Q D Z.  O(m^3); m <= 256 here.
+#include <algorithm>
+#include <cfloat>
+#include <cmath>
+#include <complex>
+#include <numeric>
+#include <vector>
+
+#include "internal.h"
+
+namespace ssqcd {
+namespace {
+
+using cd = std::complex<double>;
+
+// Implicit QL on a real symmetric tridiagonal matrix: d[0..n) diagonal,
+// e[i] couples i and i+1 (e[n-1] is workspace).  Z (n x n, row-major) is
+// multiplied on the right by every rotation.
+int tridiagonal_ql(int n, std::vector<double>& d, std::vector<double>& e, std::vector<double>& Z) {
+  for (int l = 0; l < n; ++l) {
+    int sweeps = 0;
+    for (;;) {
+      int m = l;
+      for (; m < n - 1; ++m) {
+        const double scale = std::fabs(d[m]) + std::fabs(d[m + 1]);
+        if (std::fabs(e[m]) <= DBL_EPSILON * scale) break;
+      }
+      if (m == l) break;
+      if (++sweeps > 300) return -1;
+      // Wilkinson shift from the 2x2 block at l; g holds d[m] - shift
+      double g = (d[l + 1] - d[l]) / (2.0 * e[l]);
+      double r = std::hypot(g, 1.0);
+      g = d[m] - d[l] + e[l] / (g + std::copysign(r, g));
+      double s = 1.0, c = 1.0, p = 0.0;
+      int i = m - 1;
+      bool split = false;
+      for (; i >= l; --i) {
+        const double f = s * e[i];
+        const double b = c * e[i];
+        r = std::hypot(f, g);
+        e[i + 1] = r;
+        if (r == 0.0) {  // the sweep splits: restart from the top
+          d[i + 1] -= p;
+          e[m] = 0.0;
+          split = true;
+          break;
+        }
+        s = f / r;
+        c = g / r;
+        g = d[i + 1] - p;
+        r = (d[i] - g) * s + 2.0 * c * b;
+        p = s * r;
+        d[i + 1] = g + p;
+        g = c * r - b;
+        for (int k = 0; k < n; ++k) {
+          const double z1 = Z[(size_t)k * n + i + 1], z0 = Z[(size_t)k * n + i];
+          Z[(size_t)k * n + i + 1] = s * z0 + c * z1;
+          Z[(size_t)k * n + i] = c * z0 - s * z1;
+        }
+      }
+      if (split) continue;
+      d[l] -= p;
+      e[l] = g;
+      e[m] = 0.0;
+    }
+  }
+  return 0;
+}
+
+}  // namespace
+
+int small_eigh(int m, const double2* a_in, double* evals, double2* evecs) {
+  if (m <= 0) return fail(SSQCD_ERR_ARG, "small_eigh: m must be > 0");
+  // full Hermitian copy from the lower triangle
+  std::vector<cd> A((size_t)m * m);
+  for (int i = 0; i < m; ++i)
+    for (int j = 0; j <= i; ++j) {
+      const cd v(a_in[(size_t)i * m + j].x, a_in[(size_t)i * m + j].y);
+      A[(size_t)i * m + j] = (i == j) ? cd(v.real(), 0.0) : v;
+      A[(size_t)j * m + i] = std::conj(A[(size_t)i * m + j]);
+    }
+  std::vector<cd> Q((size_t)m * m, cd(0.0, 0.0));
+  for (int i = 0; i < m; ++i) Q[(size_t)i * m + i] = 1.0;
+  std::vector<double> d(m), e(m, 0.0);
+  std::vector<cd> sub(m, cd(0.0, 0.0));  // complex sub-diagonal T[k+1][k]
+  std::vector<cd> v(m), p(m), w(m), qv(m);
+  for (int k = 0; k + 2 < m; ++k) {
+    const int len = m - k - 1;
+    double xnorm2 = 0.0;
+    for (int i = 0; i < len; ++i) xnorm2 += std::norm(A[(size_t)(k + 1 + i) * m + k]);
+    const double xnorm = std::sqrt(xnorm2);
+    const cd x0 = A[(size_t)(k + 1) * m + k];
+    double tail2 = xnorm2 - std::norm(x0);
+    if (xnorm == 0.0 || tail2 <= 0.0) continue;  // column already reduced
+    const cd phase = std::abs(x0) > 0.0 ? x0 / std::abs(x0) : cd(1.0, 0.0);
+    for (int i = 0; i < len; ++i) v[i] = A[(size_t)(k + 1 + i) * m + k];
+    v[0] += phase * xnorm;
+    double vv = 0.0;
+    for (int i = 0; i < len; ++i) vv += std::norm(v[i]);
+    const double tau = 2.0 / vv;
+    // p = tau A22 v
+    for (int i = 0; i < len; ++i) {
+      cd acc(0.0, 0.0);
+      const cd* row = &A[(size_t)(k + 1 + i) * m + (k + 1)];
+      for (int j = 0; j < len; ++j) acc += row[j] * v[j];
+      p[i] = tau * acc;
+    }
+    cd vp(0.0, 0.0);
+    for (int i = 0; i < len; ++i) vp += std::conj(v[i]) * p[i];
+    const double K = 0.5 * tau * vp.real();
+    for (int i = 0; i < len; ++i) w[i] = p[i] - K * v[i];
+    // A22 -= v w^H + w v^H
+    for (int i = 0; i < len; ++i) {
+      cd* row = &A[(size_t)(k + 1 + i) * m + (k + 1)];
+      for (int j = 0; j < len; ++j) row[j] -= v[i] * std::conj(w[j]) + w[i] * std::conj(v[j]);
+    }
+    // column k below the diagonal becomes (-phase * |x|, 0, ..., 0)
+    A[(size_t)(k + 1) * m + k] = -phase * xnorm;
+    A[(size_t)k * m + (k + 1)] = std::conj(-phase * xnorm);
+    for (int i = 1; i < len; ++i) {
+      A[(size_t)(k + 1 + i) * m + k] = 0.0;
+      A[(size_t)k * m + (k + 1 + i)] = 0.0;
+    }
+    // Q[:, k+1:] -= tau (Q[:, k+1:] v) v^H
+    for (int r = 0; r < m; ++r) {
+      cd acc(0.0, 0.0);
+      const cd* row = &Q[(size_t)r * m + (k + 1)];
+      for (int j = 0; j < len; ++j) acc += row[j] * v[j];
+      acc *= tau;
+      cd* roww = &Q[(size_t)r * m + (k + 1)];
+      for (int j = 0; j < len; ++j) roww[j] -= acc * std::conj(v[j]);
+    }
+  }
+  for (int i = 0; i < m; ++i) d[i] = A[(size_t)i * m + i].real();
+  for (int i = 0; i + 1 < m; ++i) sub[i] = A[(size_t)(i + 1) * m + i];
+  // D: delta_0 = 1, delta_{k+1} = delta_k e_k/|e_k|  -> real off-diagonals |e_k|
+  std::vector<cd> delta(m, cd(1.0, 0.0));
+  for (int i = 0; i + 1 < m; ++i) {
+    const double ae = std::abs(sub[i]);
+    delta[i + 1] = ae > 0.0 ? delta[i] * (sub[i] / ae) : delta[i];
+    e[i] = ae;
+  }
+  std::vector<double> Z((size_t)m * m, 0.0);
+  for (int i = 0; i < m; ++i) Z[(size_t)i * m + i] = 1.0;
+  if (tridiagonal_ql(m, d, e, Z) != 0) return fail(SSQCD_ERR_NOCONV, "small_eigh: QL did not converge");
+  std::vector<int> order(m);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return d[a] < d[b]; });
+  for (int c = 0; c < m; ++c) evals[c] = d[order[c]];
+  if (evecs != nullptr) {
+    // V = Q D Z
+    for (int r = 0; r < m; ++r)
+      for (int c = 0; c < m; ++c) {
+        const int oc = order[c];
+        cd acc(0.0, 0.0);
+        for (int k = 0; k < m; ++k) acc += Q[(size_t)r * m + k] * delta[k] * Z[(size_t)k * m + oc];
+        evecs[(size_t)r * m + c] = make_double2(acc.real(), acc.imag());
+      }
+  }
+  return SSQCD_OK;
+}
+
+// Left singular vectors of a small complex m x m matrix by one-sided
+// (Hestenes) Jacobi: columns b_p, b_q are rotated until pairwise orthogonal,
+// B J = U Sigma; singular values are the final column norms.  Small singular
+// values keep high relative accuracy, which the rank decision of the
+// Rayleigh-Ritz basis relies on.
+int small_svd_left(int m, const double2* a_in, double* sigma, double2* U) {
+  if (m <= 0) return fail(SSQCD_ERR_ARG, "small_svd_left: m must be > 0");
+  std::vector<cd> B((size_t)m * m);  // column-major: B[c * m + r]
+  for (int r = 0; r < m; ++r)
+    for (int c = 0; c < m; ++c) B[(size_t)c * m + r] = cd(a_in[(size_t)r * m + c].x, a_in[(size_t)r * m + c].y);
+  bool rotated = true;
+  for (int sweep = 0; sweep < 60 && rotated; ++sweep) {
+    rotated = false;
+    for (int p = 0; p < m - 1; ++p)
+      for (int q = p + 1; q < m; ++q) {
+        cd* bp = &B[(size_t)p * m];
+        cd* bq = &B[(size_t)q * m];
+        double alpha = 0.0, beta = 0.0;
+        cd g(0.0, 0.0);
+        for (int r = 0; r < m; ++r) {
+          alpha += std::norm(bp[r]);
+          beta += std::norm(bq[r]);
+          g += std::conj(bp[r]) * bq[r];
+        }
+        const double ag = std::abs(g);
+        if (ag == 0.0 || ag <= DBL_EPSILON * std::sqrt(alpha * beta)) continue;
+        rotated = true;
+        const cd ph = g / ag;  // b_q e^{-i phi} makes the coupling real
+        const double zeta = (beta - alpha) / (2.0 * ag);
+        const double t = std::copysign(1.0, zeta) / (std::fabs(zeta) + std::sqrt(1.0 + zeta * zeta));
+        const double c = 1.0 / std::sqrt(1.0 + t * t), s = c * t;
+        for (int r = 0; r < m; ++r) {
+          const cd x = bp[r], y = bq[r] * std::conj(ph);
+          bp[r] = c * x - s * y;
+          bq[r] = s * x + c * y;
+        }
+      }
+  }
+  std::vector<double> nrm(m);
+  for (int c = 0; c < m; ++c) {
+    double s2 = 0.0;
+    for (int r = 0; r < m; ++r) s2 += std::norm(B[(size_t)c * m + r]);
+    nrm[c] = std::sqrt(s2);
+  }
+  std::vector<int> order(m);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return nrm[x] > nrm[y]; });
+  for (int k = 0; k < m; ++k) {
+    const int c = order[k];
+    sigma[k] = nrm[c];
+    const double inv = nrm[c] > 0.0 ? 1.0 / nrm[c] : 0.0;
+    for (int r = 0; r < m; ++r) {
+      const cd u = B[(size_t)c * m + r] * inv;
+      U[(size_t)r * m + k] = make_double2(u.real(), u.imag());
+    }
+  }
+  return SSQCD_OK;
+}
+
+}  // namespace ssqcd
+
+extern "C" int ssqcd_small_eigh(int m, const double* a, double* evals, double* evecs) {
+  if (a == nullptr || evals == nullptr) return ssqcd::fail(SSQCD_ERR_ARG, "ssqcd_small_eigh: NULL argument");
+  return ssqcd::small_eigh(m, reinterpret_cast<const double2*>(a), evals, reinterpret_cast<double2*>(evecs));
+}

@@ -1,0 +1,152 @@
+// Internal declarations of the ssqcd library (not part of the C ABI).
+//
+// Device layout ("component-major, site-fastest"):
+//   spinor field    : [12][V] complex, component c = 3*spin + colour;
+//   block of L      : [L][12][V];
+//   FP64 gauge      : [4][9][V] double2, element (a,b) of U_mu(s) at
+//                     (mu*9 + 3a + b)*V + s;
+//   FP16 gauge      : [4][6][V] __half2 x2 (first two rows, 12 reals) --
+//                     see wilson.cu.
+// A warp of consecutive sites then reads 32 consecutive complex numbers for
+// every component, for the site itself and for each of its 8 neighbours
+// (neighbours of consecutive sites are consecutive except at wraps).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/ssqcd.h"
+
+namespace ssqcd {
+
+// ---- error handling --------------------------------------------------------
+void set_error(const std::string& msg);
+int fail(int code, const std::string& msg);
+int cuda_fail(cudaError_t e, const char* what, const char* file, int line);
+
+#define SS_CUDA(call)                                                          \
+  do {                                                                         \
+    cudaError_t e_ = (call);                                                   \
+    if (e_ != cudaSuccess) return ::ssqcd::cuda_fail(e_, #call, __FILE__, __LINE__); \
+  } while (0)
+
+#define SS_CHECK_LAUNCH()                                                      \
+  do {                                                                         \
+    cudaError_t e_ = cudaGetLastError();                                       \
+    if (e_ != cudaSuccess) return ::ssqcd::cuda_fail(e_, "kernel launch", __FILE__, __LINE__); \
+  } while (0)
+
+#define SS_TRY(expr)                                                           \
+  do {                                                                         \
+    int s_ = (expr);                                                           \
+    if (s_ != SSQCD_OK) return s_;                                             \
+  } while (0)
+
+void count_launches(long long k);
+
+// ---- device buffers --------------------------------------------------------
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  ~DevBuf() { release(); }
+  int alloc(size_t nbytes);          // no-op when already that large
+  void release();
+  template <typename T> T* as() const { return static_cast<T*>(p); }
+};
+
+// ---- lattice -------------------------------------------------------------------
+struct Geometry {
+  int X, Y, Z, T;
+  int V;
+  double kappa;
+  double bc_t;
+};
+
+}  // namespace ssqcd
+
+struct ssqcd_lattice_s {
+  ssqcd::Geometry g;
+  int precision;
+  cudaStream_t stream;
+  bool has_gauge = false;
+  ssqcd::DevBuf u64;     // FP64 links [4][9][V] double2
+  ssqcd::DevBuf u16;     // FP16 links, mixed precision only
+  ssqcd::DevBuf stage;   // staging for host <-> device copies
+};
+
+namespace ssqcd {
+
+// ---- kernels and their host launchers (each .cu file documents its own) ----
+constexpr int kThreads = 256;
+
+int grid_for(long long work, int threads);
+
+// layout conversions (blas.cu)
+int pack_spinors(const double2* user, double2* dev, int nfields, int V, cudaStream_t s);
+int unpack_spinors(const double2* dev, double2* user, int nfields, int V, cudaStream_t s);
+int pack_gauge64(const double2* user, double2* dev, int V, cudaStream_t s);
+
+// stencil (wilson.cu): out = c0 * in + c1 * A in, for nrhs fields of layout
+// [nrhs][12][V]; if dot_partial != nullptr, also per-block partial sums of
+// Re <in, out> into dot_partial[rhs * nblocks + block] (nblocks returned by
+// wilson_blocks).
+int wilson_blocks(const Geometry& g);
+int wilson64(const Geometry& g, const double2* u, const double2* in, double2* out, int nrhs,
+             double c0, double c1, double* dot_partial, const int* skip_if_zero, cudaStream_t s);
+int wilson32(const Geometry& g, const void* u16, const float2* in, float2* out, int nrhs,
+             float c0, float c1, float* dot_partial, const int* skip_if_zero, cudaStream_t s);
+int pack_gauge16(const double2* u64dev, void* u16, int V, cudaStream_t s);
+
+// reductions / dense block ops in FP64 (blas.cu)
+int norm2_partials(const double2* x, int nvec, long long n, double* partial, int nblocks, cudaStream_t s);
+int sum_partials(const double* partial, int nvec, int nblocks, double* out, cudaStream_t s);
+int gram(const double2* X, int mx, const double2* Y, int my, long long n, double2* G, DevBuf& scratch,
+         cudaStream_t s);
+int combine(const double2* S, int ms, long long n, const double2* C, int mc, double2* Q, cudaStream_t s);
+// CGS2 QR of the m vectors S (device): Q [m][n] with orthonormal (or zero)
+// vectors and R (m x m row-major, device, upper triangular), S = Q R.
+int cgs2(const double2* S, int m, long long n, double2* Q, double2* R, DevBuf& scratch, cudaStream_t s);
+int col_residual_norms(const double2* AX, const double2* X, const double* theta, int m, long long n,
+                       double* out, DevBuf& scratch, cudaStream_t s);
+int convert_f64_to_f32(const double2* in, float2* out, long long n, cudaStream_t s);
+int convert_f32_to_f64(const float2* in, double2* out, long long n, cudaStream_t s);
+
+// contour (contour.cu, host)
+int contour_nodes(int path, double gamma, double rho, double beta, int N,
+                  std::vector<double2>& z, std::vector<double2>& w);
+
+// small Hermitian eigenproblem (eigh.cu, host)
+int small_eigh(int m, const double2* a, double* evals, double2* evecs);
+// left singular vectors of a small complex matrix (m x m row-major, host):
+// sigma[m] descending, U[m][m] row-major with singular vector k in column k
+int small_svd_left(int m, const double2* a, double* sigma, double2* U);
+
+// shifted CG (mshift.cu)
+struct ShiftedCGOut {
+  int seed_iters = 0;
+  int reliable_updates = 0;
+  float ms = 0.f;
+  long long shift_updates = 0;
+  bool timed = false;
+  int launches_update = 0;
+  double ms_k[4] = {0, 0, 0, 0};  // stencil, seed update, scalars, shift update
+};
+bool kernel_timing_enabled();
+// Solves for L sources already packed on device (v: [L][12][V]); y out
+// [L][N][12][V] (device, FP64).  iters/xi: host arrays [L*N] (may be null).
+int shifted_cg_device(ssqcd_lattice lat, int N, const double2* z_host, int L, const double2* v,
+                      double sigma, double tol, int max_iter, int precision, int reliable_every,
+                      DevBuf& y, int* iters, double2* xi, ShiftedCGOut* out);
+
+// moments (moments.cu): s_hat [L][M][12][V] from y [L][N][12][V]
+int moments_device(const double2* y, int N, int M, int L, long long n, const double2* coef_host,
+                   double2* s_hat, DevBuf& scratch, cudaStream_t s);
+
+}  // namespace ssqcd

@@ -1,0 +1,81 @@
+"""Host-side checks of the C-ABI library (no GPU needed)."""
+import ctypes
+import subprocess
+
+import numpy as np
+import pytest
+
+from tests._lib import built, header_functions
+
+import synthetic
+from oracle import contour as ocontour
+
+
+@pytest.fixture(scope="module")
+def ss():
+    built()
+    import paper_1004_0292_gb300 as ss
+    return ss
+
+
+def test_every_declared_symbol_is_exported(ss):
+    names = header_functions()
+    assert len(names) >= 15
+    lib = ctypes.CDLL(ss.library_path())
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+    # and they are dynamic symbols with C linkage
+    out = subprocess.run(["nm", "-D", "--defined-only", ss.library_path()], capture_output=True, text=True).stdout
+    exported = set(line.split()[-1] for line in out.splitlines() if line.strip())
+    assert set(names) <= exported
+
+
+def test_small_eigh_matches_lapack(ss):
+    g = synthetic.rng(4)
+    for m in (1, 2, 5, 16, 33, 64):
+        x = g.standard_normal((m, m)) + 1j * g.standard_normal((m, m))
+        a = x + x.conj().T
+        ev, vec = ss.small_eigh(a)
+        ref = np.linalg.eigvalsh(a)
+        assert np.max(np.abs(ev - ref)) <= 1e-13 * max(1.0, np.max(np.abs(ref)))
+        assert np.allclose(vec.conj().T @ vec, np.eye(m), atol=1e-13)
+        assert np.allclose(a @ vec, vec * ev[None, :], atol=1e-12 * max(1.0, np.max(np.abs(ref))))
+
+
+def test_small_eigh_degenerate_and_diagonal(ss):
+    # repeated eigenvalues and an already tridiagonal / diagonal input
+    d = np.array([1.0, 1.0, 1.0, -2.0, 3.0, 3.0])
+    q, _ = np.linalg.qr(synthetic.rng(1).standard_normal((6, 6)) + 1j * synthetic.rng(2).standard_normal((6, 6)))
+    a = q @ np.diag(d) @ q.conj().T
+    ev, vec = ss.small_eigh(a)
+    assert np.allclose(ev, np.sort(d), atol=1e-13)
+    assert np.allclose(a @ vec, vec * ev[None, :], atol=1e-12)
+    ev2, _ = ss.small_eigh(np.diag(d).astype(complex))
+    assert np.allclose(ev2, np.sort(d))
+
+
+@pytest.mark.parametrize("N,beta", [(8, 0.2), (16, 0.5), (32, 0.2), (64, 0.3)])
+def test_contour_matches_oracle(ss, N, beta):
+    z, w = ss.contour(ss.PATH_LINES, 0.1, 0.02, beta, N)
+    zo = ocontour.line_nodes(0.1, 0.02, beta, N)
+    wo = ocontour.weights_closed_form(ocontour.normalise(zo, 0.1, 0.02))
+    assert np.allclose(z, zo, rtol=0, atol=1e-15)
+    assert np.max(np.abs(w - wo)) <= 1e-12 * np.max(np.abs(wo))
+
+
+def test_contour_circle_weights(ss):
+    z, w = ss.contour(ss.PATH_CIRCLE, -0.3, 0.5, 0.0, 32)
+    zeta = (z + 0.3) / 0.5
+    assert np.allclose(w, zeta / 32, atol=1e-15)
+
+
+def test_argument_errors(ss):
+    with pytest.raises(ss.SsqcdError) as e:
+        ss.contour(ss.PATH_LINES, 0.0, 1.0, 0.3, 7)
+    assert e.value.code == ss.ERR_ARG
+    with pytest.raises(ss.SsqcdError):
+        ss.contour(ss.PATH_LINES, 0.0, -1.0, 0.3, 8)
+    with pytest.raises(ss.SsqcdError):
+        ss.create_lattice((4, 4, 0, 4), 0.1)
+    with pytest.raises(ss.SsqcdError):
+        ss.create_lattice((4, 4, 4, 4), 0.1, bc_t=0)
