@@ -19,62 +19,67 @@
 // A shift stops ("freezes") once |xi_{k+1}| ||r_{k+1}|| <= tol ||v|| (the
 // paper's stopping rule ||r_j|| / ||v|| <= tol, Section 3 and Section 4).
 //
-// One iteration = four kernels, all issued asynchronously; the host only
-// polls a counter every few iterations:
-//   1. stencil q = K p with per-block partials of (p, q)            (wilson.cu)
-//   2. seed update: alpha, r -= alpha q, partials of ||r||^2
-//   3. shift scalars: one thread per (source, shift) -> xi, a_j, b_j, freeze
-//   4. fused multi-shift update: y_j, p-hat_j for every live shift, seed p
-// Iteration control without host round trips: counters of live shifts are
-// double-buffered by iteration parity P.  Kernels of iteration k skip their
-// work when cnt[1-P] (the count left by iteration k-1) is zero; kernel 3
-// accumulates cnt[P]; kernel 4 clears cnt[1-P] for iteration k+1 (every reader
-// of cnt[1-P] in iteration k ran before it).  Seed scalars (rr, alpha,
-// beta) are double-buffered the same way; per-shift state is owned by a
-// single thread of kernel 3 and needs no buffering.
-//
-// The reductions are fixed-order, so every run gives bit-identical results.
+// One iteration = three kernels, each finishing its reduction in its last
+// block (fixed summation order, no host round trip):
+//   A. stencil q = K p for every source with block partials of (p, q); the
+//      last block forms alpha_k = (r, r) / (p, q) (breakdown check);
+//   B. seed update r -= alpha q with partials of ||r||^2; the last block
+//      forms (r_{k+1}, r_{k+1}) and beta_k;
+//   C. fused update: every block recomputes the xi recurrence of its
+//      source's shifts (a few dozen FP64 operations per shift, spread over all
+//      SMs instead of serialised in one), then for every live shift
+//      y_j += a_j p-hat_j, p-hat_j = r + b_j p-hat_j, and p = r + beta p.
+// (A two-kernel form that obtains ||r_{k+1}||^2 from (r, r) - 2 alpha (r, q)
+// + alpha^2 (q, q) was tried and rejected: on the indefinite seed the
+// residual can drop by many orders in one step, the three terms cancel, and
+// shifts froze on a wrong residual estimate.)
+// Block 0 of each source also stores xi_{k+1}, the freeze flags and the
+// per-shift iteration counts.  xi lives in a ring of three slots indexed by
+// k mod 3, the other state in two slots indexed by the parity P = k mod 2, so
+// readers and the single writer of an iteration never touch the same slot.
+// Kernel A of iteration k skips when no shift was live after iteration k-1;
+// the host polls the live count every 16 iterations.  All reductions have a
+// fixed order, so runs are bit-reproducible.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <vector>
 
-#include "internal.h"
+#include "wilson_core.cuh"
 
 namespace ssqcd {
 namespace {
 
-struct SeedScalars {
-  double rr;          // (r_k, r_k)
-  double alpha_prev;  // alpha_{k-1}
-  double beta_prev;   // beta_{k-1}
+using namespace wcore;
+
+struct SeedIter {
+  double alpha;  // alpha_k
+  double beta;   // beta_k
+  double rr;     // (r_{k+1}, r_{k+1})
   double pad;
 };
 
-struct ShiftCoef {
-  double2 a;  // y += a * p-hat
-  double2 b;  // p-hat = r + b * p-hat
-};
-
-// Device-side control block of one solve (all sized for L sources, N shifts).
+// Device-side control block of one solve (L sources, N shifts).
 struct Control {
-  SeedScalars* seed;   // [2][L]
-  double* alpha_cur;   // [L]
+  SeedIter* seed;      // [2][L]   slot k&1 written by kernel A of iteration k
   double* vnorm2;      // [L]
-  int* cnt;            // [2]
-  int* cnt_src;        // [2][L]
+  int* src_live;       // [2][L]   live shifts at the start of iteration k: slot k&1
+  int* live_total;     // [2]
+  int* ran;            // [2]      kernel A of iteration k did its work
   int* err;            // [1]
   int* seed_iters;     // [1]
-  double2* shift_s;    // [L*N]  s_j = z_j - sigma
-  double2* xi_cur;     // [L*N]
-  double2* xi_prev;    // [L*N]
-  int* active;         // [L*N]
-  int* upd;            // [L*N]
+  unsigned* done;      // [2]      last-block tickets of kernels A and B
+  double2* shift_s;    // [L*N]    s_j = z_j - sigma
+  double2* xi;         // [3][L*N] ring: slot k%3 = xi_k
+  int* act;            // [2][L*N] active at the start of iteration k: slot k&1
   int* iters;          // [L*N]
-  ShiftCoef* coef;     // [L*N]
+  double* partial;     // [L][nbw]  (p, q) partials of kernel A
+  double* partial_rr;  // [L][nbu]  ||r||^2 partials of kernel B
 };
 
-constexpr int kBlock = 256;
+constexpr int kUpdBlock = 256;
+constexpr int kMaxShifts = 256;
+constexpr int kMaxSources = 64;
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -82,34 +87,7 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// Sum of partial[0..nb) with a fixed order; result valid in every thread.
-__device__ double block_sum_fixed(const double* __restrict__ partial, int nb, double* sh) {
-  double acc = 0.0;
-  for (int i = threadIdx.x; i < nb; i += blockDim.x) acc += partial[i];
-  acc = warp_sum(acc);
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  __syncthreads();
-  if (lane == 0) sh[wid] = acc;
-  __syncthreads();
-  double r = 0.0;
-  const int nw = blockDim.x >> 5;
-  for (int i = 0; i < nw; ++i) r += sh[i];
-  return r;
-}
-
-__device__ double block_reduce(double v, double* sh) {
-  v = warp_sum(v);
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  __syncthreads();
-  if (lane == 0) sh[wid] = v;
-  __syncthreads();
-  double r = 0.0;
-  const int nw = blockDim.x >> 5;
-  for (int i = 0; i < nw; ++i) r += sh[i];
-  return r;
-}
-
-// ---- initialisation: r = p = v, p-hat_j = v, y_j = 0 ------------------------
+// ---- initialisation ---------------------------------------------------------------
 __global__ void init_vectors_kernel(const double2* __restrict__ v, double2* __restrict__ r, double2* __restrict__ p,
                                     double2* __restrict__ y, double2* __restrict__ ph, int N, long long n) {
   const int l = blockIdx.y;
@@ -124,185 +102,259 @@ __global__ void init_vectors_kernel(const double2* __restrict__ v, double2* __re
   }
 }
 
-// One block: seed scalars, per-shift state and the live counts.  A source with
-// ||v|| = 0 has the exact solution y = 0 and starts frozen.
+// A source with ||v|| = 0 has the exact solution y = 0 and starts frozen.
 __global__ void init_control_kernel(Control c, const double* __restrict__ vn2, int L, int N) {
   for (int t = threadIdx.x; t < L; t += blockDim.x) {
-    c.seed[t] = SeedScalars{vn2[t], 1.0, 0.0, 0.0};
-    c.seed[L + t] = SeedScalars{0.0, 0.0, 0.0, 0.0};
+    c.seed[L + t] = SeedIter{1.0, 0.0, vn2[t], 0.0};  // "iteration -1": alpha_{-1} = 1, beta_{-1} = 0, rr_0
+    c.seed[t] = SeedIter{0.0, 0.0, 0.0, 0.0};
     c.vnorm2[t] = vn2[t];
-    c.alpha_cur[t] = 0.0;
-    c.cnt_src[t] = 0;                          // parity 0
-    c.cnt_src[L + t] = vn2[t] > 0.0 ? N : 0;   // parity 1 = "previous iteration"
+    c.src_live[t] = vn2[t] > 0.0 ? N : 0;
+    c.src_live[L + t] = 0;
   }
   for (int t = threadIdx.x; t < L * N; t += blockDim.x) {
-    c.xi_cur[t] = make_double2(1.0, 0.0);
-    c.xi_prev[t] = make_double2(1.0, 0.0);
-    c.active[t] = vn2[t / N] > 0.0 ? 1 : 0;
-    c.upd[t] = 0;
+    c.xi[t] = make_double2(1.0, 0.0);              // xi_0
+    c.xi[2 * L * N + t] = make_double2(1.0, 0.0);  // xi_{-1} (slot 2 = -1 mod 3)
+    c.act[t] = vn2[t / N] > 0.0 ? 1 : 0;
+    c.act[L * N + t] = 0;
     c.iters[t] = 0;
   }
   if (threadIdx.x == 0) {
     int live = 0;
     for (int l = 0; l < L; ++l) live += vn2[l] > 0.0 ? N : 0;
-    c.cnt[0] = 0;
-    c.cnt[1] = live;
+    c.live_total[0] = live;
+    c.live_total[1] = 0;
+    c.ran[0] = c.ran[1] = 0;
     *c.err = 0;
     *c.seed_iters = 0;
+    c.done[0] = c.done[1] = 0u;
   }
 }
 
-// ---- 2. seed update -----------------------------------------------------------
-// grid (nb, L).  alpha_l = rr_l / pq_l (pq from the stencil partials), r -= alpha q,
-// partials of ||r||^2 into rr_part[l * nb + block].
-__global__ void __launch_bounds__(kBlock)
-seed_update_kernel(Control c, int P, double2* __restrict__ r, const double2* __restrict__ q,
-                   const double* __restrict__ pq_part, int nbw, double* __restrict__ rr_part, long long n) {
-  const int l = blockIdx.y;
-  const int L = gridDim.y;
-  if (c.cnt[1 - P] == 0 || c.cnt_src[(1 - P) * L + l] == 0) return;
-  __shared__ double sh[kBlock / 32];
-  const double pq = block_sum_fixed(pq_part + (long long)l * nbw, nbw, sh);
-  const double rr = c.seed[P * L + l].rr;
-  double alpha = rr / pq;
-  if (!(fabs(pq) >= 1e-30 * rr)) {  // breakdown (also catches NaN)
-    if (blockIdx.x == 0 && threadIdx.x == 0) atomicExch(c.err, 1);
-    alpha = 0.0;
-  }
-  if (blockIdx.x == 0 && threadIdx.x == 0) c.alpha_cur[l] = alpha;
-  double acc = 0.0;
-  double2* rl = r + (long long)l * n;
-  const double2* ql = q + (long long)l * n;
-  for (long long e = blockIdx.x * (long long)kBlock + threadIdx.x; e < n; e += (long long)gridDim.x * kBlock) {
-    double2 x = rl[e];
-    const double2 y = ql[e];
-    x.x = fma(-alpha, y.x, x.x);
-    x.y = fma(-alpha, y.y, x.y);
-    rl[e] = x;
-    acc = fma(x.x, x.x, fma(x.y, x.y, acc));
-  }
-  const double b = block_reduce(acc, sh);
-  if (threadIdx.x == 0) rr_part[(long long)l * gridDim.x + blockIdx.x] = b;
-}
-
-// ---- 3. shift scalars -----------------------------------------------------------
-// one thread per (l, j), 32 per block.
-__global__ void __launch_bounds__(32)
-shift_scalars_kernel(Control c, int P, int L, int N, const double* __restrict__ rr_part, int nbr, double tol2) {
-  const int q = blockIdx.x * 32 + threadIdx.x;
-  const bool valid = q < L * N;
-  const int l = valid ? q / N : L - 1;
-  const bool run = c.cnt[1 - P] != 0 && *c.err == 0;
-  // rr_{k+1} for every source present in this warp (warp-cooperative, fixed order)
-  double rr_new = 0.0;
-  const int l_first = (blockIdx.x * 32) / N;
-  const int l_last = min(L - 1, (blockIdx.x * 32 + 31) / N);
-  if (run) {
-    for (int ls = l_first; ls <= l_last; ++ls) {
-      double acc = 0.0;
-      for (int i = threadIdx.x; i < nbr; i += 32) acc += rr_part[(long long)ls * nbr + i];
-      acc = warp_sum(acc);
-      if (ls == l) rr_new = acc;
+// ---- A. stencil q = K p + (p, q) partials; last block: alpha_k ---------------------
+__global__ void __launch_bounds__(kStencilThreads)
+cg_stencil_kernel(Control c, int P, int L, Geometry g, const double2* __restrict__ u, double sigma,
+                  const double2* __restrict__ p_all, double2* __restrict__ q_all) {
+  if (*c.err != 0 || c.live_total[P] == 0) {
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
+      c.ran[P] = 0;
+      c.live_total[1 - P] = 0;
+      for (int l = 0; l < L; ++l) c.src_live[(1 - P) * L + l] = 0;
     }
-  }
-  if (!valid) return;
-  if (!run || c.cnt_src[(1 - P) * L + l] == 0) {
-    c.upd[q] = 0;
     return;
   }
-  const SeedScalars sd = c.seed[P * L + l];
-  const double alpha = c.alpha_cur[l];
-  const double beta = rr_new / sd.rr;
-  const int j = q - l * N;
-  if (j == 0) c.seed[(1 - P) * L + l] = SeedScalars{rr_new, alpha, beta, 0.0};
-  if (q == 0) atomicAdd(c.seed_iters, 1);  // an iteration in which some source was live
-  int live = 0;
-  if (c.active[q]) {
-    const double2 xc = c.xi_cur[q], xp = c.xi_prev[q], s = c.shift_s[q];
-    const double ap = sd.alpha_prev, bp = sd.beta_prev;
-    // numerator xi_k xi_{k-1} alpha_{k-1}
-    double2 num;
-    num.x = (xc.x * xp.x - xc.y * xp.y) * ap;
-    num.y = (xc.x * xp.y + xc.y * xp.x) * ap;
-    // alpha_k beta_{k-1} (xi_{k-1} - xi_k) + xi_{k-1} alpha_{k-1} (1 + s alpha_k)
-    const double ab = alpha * bp;
-    const double2 t1 = make_double2(ab * (xp.x - xc.x), ab * (xp.y - xc.y));
-    const double2 u = make_double2(1.0 + s.x * alpha, s.y * alpha);
-    double2 t2;
-    t2.x = (xp.x * u.x - xp.y * u.y) * ap;
-    t2.y = (xp.x * u.y + xp.y * u.x) * ap;
-    const double2 den = make_double2(t1.x + t2.x, t1.y + t2.y);
-    const double dd = den.x * den.x + den.y * den.y;
-    double2 xn;
-    xn.x = (num.x * den.x + num.y * den.y) / dd;
-    xn.y = (num.y * den.x - num.x * den.y) / dd;
-    // b = beta xi_{k+1} / xi_k
-    const double cc = xc.x * xc.x + xc.y * xc.y;
-    double2 ratio;
-    ratio.x = (xn.x * xc.x + xn.y * xc.y) / cc;
-    ratio.y = (xn.y * xc.x - xn.x * xc.y) / cc;
-    ShiftCoef cf;
-    cf.a = make_double2(alpha * xn.x, alpha * xn.y);
-    cf.b = make_double2(beta * ratio.x, beta * ratio.y);
-    c.coef[q] = cf;
-    c.upd[q] = 1;
-    c.xi_prev[q] = xc;
-    c.xi_cur[q] = xn;
-    c.iters[q] += 1;
-    const double xn2 = xn.x * xn.x + xn.y * xn.y;
-    if (xn2 * rr_new <= tol2 * c.vnorm2[l]) {
-      c.active[q] = 0;
-    } else {
-      live = 1;
+  __shared__ double2 sh[12 * 4 * 32];
+  __shared__ double sred[kStencilThreads / 32];
+  __shared__ double sums[kMaxSources];
+  __shared__ bool s_last;
+  const int l = blockIdx.y;
+  const int V = g.V;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  double d_pq = 0.0;
+  if (c.src_live[P * L + l] != 0) {
+    const double2* p = p_all + (size_t)l * 12 * V;
+    double2* q = q_all + (size_t)l * 12 * V;
+    const int s = blockIdx.x * kSitesPerBlock + lane;
+    double2 acc[3];
+    block_hops64(Links64{u, V}, p, s, g, sh, acc);
+    if (s < V) {
+      // q = sigma p - gamma5 (p - kappa D p); components 3w..3w+2 are spin w
+      const double sg = w < 2 ? -1.0 : 1.0;
+      const double mk = -g.kappa;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const int i = 3 * w + k;
+        const double2 pv = p[i * V + s];
+        double2 o;
+        o.x = fma(sg, fma(mk, acc[k].x, pv.x), sigma * pv.x);
+        o.y = fma(sg, fma(mk, acc[k].y, pv.y), sigma * pv.y);
+        q[i * V + s] = o;
+        d_pq = fma(pv.x, o.x, fma(pv.y, o.y, d_pq));
+      }
     }
-  } else {
-    c.upd[q] = 0;
   }
-  // count live shifts, per source and in total
-  if (live) {
-    atomicAdd(&c.cnt[P], 1);
-    atomicAdd(&c.cnt_src[P * L + l], 1);
+  d_pq = warp_sum(d_pq);
+  if (lane == 0) sred[w] = d_pq;
+  __syncthreads();
+  const int nbw = gridDim.x;
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < kStencilThreads / 32; ++i) t += sred[i];
+    c.partial[(size_t)l * nbw + blockIdx.x] = t;
+    __threadfence();
+    const unsigned ticket = atomicAdd(&c.done[0], 1u);
+    s_last = ticket == gridDim.x * gridDim.y - 1;
   }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  // warp w sums the partials of sources w, w+4, ... in a fixed order
+  for (int ls = w; ls < L; ls += kStencilThreads / 32) {
+    double a = 0.0;
+    for (int b = lane; b < nbw; b += 32) a += __ldcg(c.partial + (size_t)ls * nbw + b);
+    a = warp_sum(a);
+    if (lane == 0) sums[ls] = a;
+  }
+  __syncthreads();
+  for (int ls = threadIdx.x; ls < L; ls += blockDim.x) {
+    if (c.src_live[P * L + ls] == 0) {
+      c.seed[P * L + ls] = SeedIter{0.0, 0.0, 0.0, 0.0};
+      continue;
+    }
+    const double pq = sums[ls];
+    const double rr = c.seed[(1 - P) * L + ls].rr;
+    if (!(fabs(pq) >= 1e-30 * rr)) {  // breakdown (also catches NaN)
+      atomicExch(c.err, 1);
+      continue;
+    }
+    c.seed[P * L + ls] = SeedIter{rr / pq, 0.0, 0.0, 0.0};
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const bool ok = *((volatile int*)c.err) == 0;
+    c.ran[P] = ok ? 1 : 0;
+    c.live_total[1 - P] = 0;
+    if (ok) atomicAdd(c.seed_iters, 1);
+    c.done[0] = 0u;
+  }
+  for (int ls = threadIdx.x; ls < L; ls += blockDim.x) c.src_live[(1 - P) * L + ls] = 0;
 }
 
-// ---- 4. fused multi-shift update --------------------------------------------------
-// grid (nb, L).  Per element: r once; for every shift of source l marked in upd:
-// y += a p-hat; p-hat = r + b p-hat; then p = r + beta p while the source lives.
-constexpr int kMaxShifts = 128;
-
-__global__ void __launch_bounds__(kBlock)
-shift_update_kernel(Control c, int P, int L, int N, const double2* __restrict__ r, double2* __restrict__ p,
-                    double2* __restrict__ y, double2* __restrict__ ph, long long n) {
+// ---- B. seed update r -= alpha q, ||r||^2 partials; last block: rr_{k+1}, beta_k -----
+__global__ void __launch_bounds__(kUpdBlock)
+cg_seed_kernel(Control c, int P, int L, double2* __restrict__ r, const double2* __restrict__ q, long long n) {
+  if (c.ran[P] == 0) return;
+  __shared__ double sred[kUpdBlock / 32];
+  __shared__ double sums[kMaxSources];
+  __shared__ bool s_last;
   const int l = blockIdx.y;
-  if (blockIdx.x == 0 && l == 0 && threadIdx.x == 0) {
-    c.cnt[1 - P] = 0;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  double acc = 0.0;
+  if (c.src_live[P * L + l] != 0) {
+    const double alpha = c.seed[P * L + l].alpha;
+    double2* rl = r + (long long)l * n;
+    const double2* ql = q + (long long)l * n;
+    for (long long e = blockIdx.x * (long long)kUpdBlock + threadIdx.x; e < n;
+         e += (long long)gridDim.x * kUpdBlock) {
+      double2 x = rl[e];
+      const double2 y = ql[e];
+      x.x = fma(-alpha, y.x, x.x);
+      x.y = fma(-alpha, y.y, x.y);
+      rl[e] = x;
+      acc = fma(x.x, x.x, fma(x.y, x.y, acc));
+    }
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) c.cnt_src[(1 - P) * L + l] = 0;
+  acc = warp_sum(acc);
+  if (lane == 0) sred[w] = acc;
+  __syncthreads();
+  const int nb = gridDim.x;
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < kUpdBlock / 32; ++i) t += sred[i];
+    c.partial_rr[(size_t)l * nb + blockIdx.x] = t;
+    __threadfence();
+    const unsigned ticket = atomicAdd(&c.done[1], 1u);
+    s_last = ticket == gridDim.x * gridDim.y - 1;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  for (int ls = w; ls < L; ls += kUpdBlock / 32) {
+    double a = 0.0;
+    for (int b = lane; b < nb; b += 32) a += __ldcg(c.partial_rr + (size_t)ls * nb + b);
+    a = warp_sum(a);
+    if (lane == 0) sums[ls] = a;
+  }
+  __syncthreads();
+  for (int ls = threadIdx.x; ls < L; ls += blockDim.x) {
+    if (c.src_live[P * L + ls] == 0) continue;
+    SeedIter sd = c.seed[P * L + ls];
+    const double rr = c.seed[(1 - P) * L + ls].rr;
+    sd.rr = sums[ls];
+    sd.beta = sums[ls] / rr;
+    c.seed[P * L + ls] = sd;
+  }
+  if (threadIdx.x == 0) c.done[1] = 0u;
+}
+
+// ---- C. fused update ------------------------------------------------------------------
+__global__ void __launch_bounds__(kUpdBlock)
+cg_update_kernel(Control c, int k, int L, int N, double tol2, const double2* __restrict__ r,
+                 double2* __restrict__ p, double2* __restrict__ y, double2* __restrict__ ph, long long n) {
+  const int P = k & 1;
+  const int l = blockIdx.y;
+  if (c.ran[P] == 0 || c.src_live[P * L + l] == 0) return;
   __shared__ int s_j[kMaxShifts];
   __shared__ double2 s_a[kMaxShifts];
   __shared__ double2 s_b[kMaxShifts];
-  __shared__ int s_n;
+  __shared__ int s_flag[kMaxShifts];  // 1: update this iteration; 2: and stays live
+  __shared__ int s_n, s_live;
+  const SeedIter cur = c.seed[P * L + l];
+  const SeedIter prev = c.seed[(1 - P) * L + l];
+  const int slot_k = k % 3, slot_km1 = (k + 2) % 3, slot_kp1 = (k + 1) % 3;
+  const int NL = N * L;
+  for (int j = threadIdx.x; j < N; j += blockDim.x) {
+    const int qi = l * N + j;
+    int flag = 0;
+    if (c.act[P * NL + qi]) {
+      const double2 xc = c.xi[slot_k * NL + qi], xp = c.xi[slot_km1 * NL + qi], s = c.shift_s[qi];
+      const double alpha = cur.alpha, ap = prev.alpha, bp = prev.beta;
+      // xi_{k+1} = xi_k xi_{k-1} alpha_{k-1} /
+      //            [alpha_k beta_{k-1} (xi_{k-1} - xi_k) + xi_{k-1} alpha_{k-1} (1 + s alpha_k)]
+      double2 num;
+      num.x = (xc.x * xp.x - xc.y * xp.y) * ap;
+      num.y = (xc.x * xp.y + xc.y * xp.x) * ap;
+      const double ab = alpha * bp;
+      const double ux = 1.0 + s.x * alpha, uy = s.y * alpha;
+      double2 den;
+      den.x = ab * (xp.x - xc.x) + (xp.x * ux - xp.y * uy) * ap;
+      den.y = ab * (xp.y - xc.y) + (xp.x * uy + xp.y * ux) * ap;
+      const double inv_d = 1.0 / (den.x * den.x + den.y * den.y);
+      double2 xn;
+      xn.x = (num.x * den.x + num.y * den.y) * inv_d;
+      xn.y = (num.y * den.x - num.x * den.y) * inv_d;
+      // b = beta xi_{k+1} / xi_k = beta xi_{k+1} conj(xi_k) / |xi_k|^2
+      const double bc = cur.beta / (xc.x * xc.x + xc.y * xc.y);
+      s_a[j] = make_double2(alpha * xn.x, alpha * xn.y);
+      s_b[j] = make_double2(bc * (xn.x * xc.x + xn.y * xc.y), bc * (xn.y * xc.x - xn.x * xc.y));
+      const bool live = (xn.x * xn.x + xn.y * xn.y) * cur.rr > tol2 * c.vnorm2[l];
+      flag = live ? 2 : 1;
+      if (blockIdx.x == 0) {
+        c.xi[slot_kp1 * NL + qi] = xn;
+        c.act[(1 - P) * NL + qi] = live ? 1 : 0;
+        c.iters[qi] += 1;
+      }
+    } else if (blockIdx.x == 0) {
+      c.act[(1 - P) * NL + qi] = 0;
+    }
+    s_flag[j] = flag;
+  }
+  __syncthreads();
   if (threadIdx.x == 0) {
-    int m = 0;
+    int m = 0, live = 0;
     for (int j = 0; j < N; ++j) {
-      const int q = l * N + j;
-      if (c.upd[q]) {
+      if (s_flag[j]) {
         s_j[m] = j;
-        s_a[m] = c.coef[q].a;
-        s_b[m] = c.coef[q].b;
+        s_a[m] = s_a[j];  // m <= j: in-place compaction keeps the order
+        s_b[m] = s_b[j];
         ++m;
       }
+      live += s_flag[j] == 2;
     }
     s_n = m;
+    s_live = live;
+    if (blockIdx.x == 0) {
+      c.src_live[(1 - P) * L + l] = live;
+      atomicAdd(&c.live_total[1 - P], live);
+    }
   }
   __syncthreads();
   const int m = s_n;
-  const bool seed_live = c.cnt_src[P * L + l] != 0;
-  if (m == 0 && !seed_live) return;
-  const double beta = c.seed[(1 - P) * L + l].beta_prev;
+  const bool seed_continues = s_live > 0;
+  const double alpha = cur.alpha, beta = cur.beta;
+  (void)alpha;
   const double2* rl = r + (long long)l * n;
   double2* pl = p + (long long)l * n;
-  for (long long e = blockIdx.x * (long long)kBlock + threadIdx.x; e < n; e += (long long)gridDim.x * kBlock) {
+  for (long long e = blockIdx.x * (long long)kUpdBlock + threadIdx.x; e < n; e += (long long)gridDim.x * kUpdBlock) {
     const double2 re = rl[e];
     int t = 0;
     for (; t + 2 <= m; t += 2) {
@@ -339,7 +391,7 @@ shift_update_kernel(Control c, int P, int L, int N, const double2* __restrict__ 
       *y0 = yv0;
       *p0 = n0;
     }
-    if (seed_live) {
+    if (seed_continues) {
       double2 pv = pl[e];
       pv.x = fma(beta, pv.x, re.x);
       pv.y = fma(beta, pv.y, re.y);
@@ -348,9 +400,10 @@ shift_update_kernel(Control c, int P, int L, int N, const double2* __restrict__ 
   }
 }
 
-int update_blocks(long long n) {
-  long long b = (n + kBlock - 1) / kBlock;
-  if (b > 152 * 8) b = 152 * 8;
+int update_blocks(long long n, int L) {
+  long long b = (n + kUpdBlock - 1) / kUpdBlock;
+  const long long cap = (152LL * 8 + L - 1) / L;
+  if (b > cap) b = cap;
   return (int)(b < 1 ? 1 : b);
 }
 
@@ -361,60 +414,56 @@ int shifted_cg_device(ssqcd_lattice lat, int N, const double2* z_host, int L, co
                       double2* xi_host, ShiftedCGOut* out) {
   (void)reliable_every;
   if (precision != SSQCD_FP64) return fail(SSQCD_ERR_ARG, "shifted_cg_device: only SSQCD_FP64 here");
-  if (N < 1 || N > kMaxShifts) return fail(SSQCD_ERR_ARG, "N must be in [1, 128]");
-  if (L < 1) return fail(SSQCD_ERR_ARG, "L must be >= 1");
+  if (N < 1 || N > kMaxShifts) return fail(SSQCD_ERR_ARG, "N must be in [1, 256]");
+  if (L < 1 || L > kMaxSources) return fail(SSQCD_ERR_ARG, "L must be in [1, 64]");
   cudaStream_t st = lat->stream;
   const Geometry& g = lat->g;
   const long long n = 12LL * g.V;
   const int NL = N * L;
   const int nbw = wilson_blocks(g);
-  const int nbu = update_blocks(n);
+  const int nbu = update_blocks(n, L);
 
-  // vectors
   DevBuf r, p, q, ph;
   SS_TRY(r.alloc(sizeof(double2) * n * L));
   SS_TRY(p.alloc(sizeof(double2) * n * L));
   SS_TRY(q.alloc(sizeof(double2) * n * L));
   SS_TRY(y.alloc(sizeof(double2) * n * NL));
   SS_TRY(ph.alloc(sizeof(double2) * n * NL));
-  // control block + partials in one allocation
   DevBuf ctl;
   size_t off = 0;
   auto take = [&](size_t bytes) {
-    size_t o = off;
+    const size_t o = off;
     off += (bytes + 255) / 256 * 256;
     return o;
   };
-  const size_t o_seed = take(sizeof(SeedScalars) * 2 * L), o_alpha = take(sizeof(double) * L),
-               o_vn = take(sizeof(double) * L), o_cnt = take(sizeof(int) * 2), o_cnts = take(sizeof(int) * 2 * L),
-               o_err = take(sizeof(int)), o_si = take(sizeof(int)), o_s = take(sizeof(double2) * NL),
-               o_xc = take(sizeof(double2) * NL), o_xp = take(sizeof(double2) * NL), o_act = take(sizeof(int) * NL),
-               o_upd = take(sizeof(int) * NL), o_it = take(sizeof(int) * NL), o_coef = take(sizeof(ShiftCoef) * NL),
-               o_pq = take(sizeof(double) * (size_t)nbw * L), o_rr = take(sizeof(double) * (size_t)nbu * L),
-               o_vp = take(sizeof(double) * (size_t)nbu * L), o_vn2 = take(sizeof(double) * L);
+  const size_t o_seed = take(sizeof(SeedIter) * 2 * L), o_vn = take(sizeof(double) * L),
+               o_live = take(sizeof(int) * 2 * L), o_tot = take(sizeof(int) * 2), o_ran = take(sizeof(int) * 2),
+               o_err = take(sizeof(int)), o_si = take(sizeof(int)), o_done = take(sizeof(unsigned) * 2),
+               o_s = take(sizeof(double2) * NL), o_xi = take(sizeof(double2) * 3 * NL),
+               o_act = take(sizeof(int) * 2 * NL), o_it = take(sizeof(int) * NL),
+               o_part = take(sizeof(double) * (size_t)nbw * L), o_prr = take(sizeof(double) * (size_t)nbu * L),
+               o_vp = take(sizeof(double) * (size_t)nbu * L),
+               o_vn2 = take(sizeof(double) * L);
   SS_TRY(ctl.alloc(off));
   char* base = ctl.as<char>();
   Control c;
-  c.seed = reinterpret_cast<SeedScalars*>(base + o_seed);
-  c.alpha_cur = reinterpret_cast<double*>(base + o_alpha);
+  c.seed = reinterpret_cast<SeedIter*>(base + o_seed);
   c.vnorm2 = reinterpret_cast<double*>(base + o_vn);
-  c.cnt = reinterpret_cast<int*>(base + o_cnt);
-  c.cnt_src = reinterpret_cast<int*>(base + o_cnts);
+  c.src_live = reinterpret_cast<int*>(base + o_live);
+  c.live_total = reinterpret_cast<int*>(base + o_tot);
+  c.ran = reinterpret_cast<int*>(base + o_ran);
   c.err = reinterpret_cast<int*>(base + o_err);
   c.seed_iters = reinterpret_cast<int*>(base + o_si);
+  c.done = reinterpret_cast<unsigned*>(base + o_done);
   c.shift_s = reinterpret_cast<double2*>(base + o_s);
-  c.xi_cur = reinterpret_cast<double2*>(base + o_xc);
-  c.xi_prev = reinterpret_cast<double2*>(base + o_xp);
-  c.active = reinterpret_cast<int*>(base + o_act);
-  c.upd = reinterpret_cast<int*>(base + o_upd);
+  c.xi = reinterpret_cast<double2*>(base + o_xi);
+  c.act = reinterpret_cast<int*>(base + o_act);
   c.iters = reinterpret_cast<int*>(base + o_it);
-  c.coef = reinterpret_cast<ShiftCoef*>(base + o_coef);
-  double* pq_part = reinterpret_cast<double*>(base + o_pq);
-  double* rr_part = reinterpret_cast<double*>(base + o_rr);
+  c.partial = reinterpret_cast<double*>(base + o_part);
+  c.partial_rr = reinterpret_cast<double*>(base + o_prr);
   double* vn_part = reinterpret_cast<double*>(base + o_vp);
   double* vn2 = reinterpret_cast<double*>(base + o_vn2);
 
-  // shifts s_j = z_j - sigma, repeated per source
   std::vector<double2> sh(NL);
   for (int l = 0; l < L; ++l)
     for (int j = 0; j < N; ++j) sh[l * N + j] = make_double2(z_host[j].x - sigma, z_host[j].y);
@@ -422,8 +471,8 @@ int shifted_cg_device(ssqcd_lattice lat, int N, const double2* z_host, int L, co
 
   SS_TRY(norm2_partials(v, L, n, vn_part, nbu, st));
   SS_TRY(sum_partials(vn_part, L, nbu, vn2, st));
-  init_vectors_kernel<<<dim3(nbu, L), kBlock, 0, st>>>(v, r.as<double2>(), p.as<double2>(), y.as<double2>(),
-                                                         ph.as<double2>(), N, n);
+  init_vectors_kernel<<<dim3(nbu, L), kUpdBlock, 0, st>>>(v, r.as<double2>(), p.as<double2>(), y.as<double2>(),
+                                                            ph.as<double2>(), N, n);
   SS_CHECK_LAUNCH();
   init_control_kernel<<<1, 256, 0, st>>>(c, vn2, L, N);
   SS_CHECK_LAUNCH();
@@ -439,57 +488,50 @@ int shifted_cg_device(ssqcd_lattice lat, int N, const double2* z_host, int L, co
   const double tol2 = tol * tol;
   int status = SSQCD_OK;
   int k = 0;
-  const int nbs = (NL + 31) / 32;
-  // optional per-kernel timing: events around the four kernels of every
-  // iteration of a chunk, read back at the chunk's poll
   constexpr int kChunk = 16;
   const bool timing = kernel_timing_enabled();
   std::vector<cudaEvent_t> tev;
-  std::vector<double> t_iter[4];
+  std::vector<double> t_iter[3];
   if (timing) {
-    tev.resize(kChunk * 8);
+    tev.resize(kChunk * 6);
     for (auto& e : tev) SS_CUDA(cudaEventCreate(&e));
   }
   auto mark = [&](int it, int slot) {
-    if (timing) cudaEventRecord(tev[it * 8 + slot], st);
+    if (timing) cudaEventRecord(tev[it * 6 + slot], st);
   };
+  const dim3 grid_a(nbw, L), grid_b(nbu, L);
   while (true) {
-    const int chunk = std::min(kChunk, max_iter - k);  // iterations between polls
-    int done_in_chunk = 0;
+    const int chunk = std::min(kChunk, max_iter - k);
+    int launched = 0;
     for (int it = 0; it < chunk; ++it, ++k) {
       const int P = k & 1;
       mark(it, 0);
-      int s1 = wilson64(g, lat->u64.as<double2>(), p.as<double2>(), q.as<double2>(), L, sigma, -1.0, pq_part,
-                        c.cnt + (1 - P), st);
-      if (s1 != SSQCD_OK) { status = s1; break; }
+      cg_stencil_kernel<<<grid_a, kStencilThreads, 0, st>>>(c, P, L, g, lat->u64.as<double2>(), sigma,
+                                                             p.as<double2>(), q.as<double2>());
       mark(it, 1);
       mark(it, 2);
-      seed_update_kernel<<<dim3(nbu, L), kBlock, 0, st>>>(c, P, r.as<double2>(), q.as<double2>(), pq_part, nbw,
-                                                          rr_part, n);
+      cg_seed_kernel<<<grid_b, kUpdBlock, 0, st>>>(c, P, L, r.as<double2>(), q.as<double2>(), n);
       mark(it, 3);
       mark(it, 4);
-      shift_scalars_kernel<<<nbs, 32, 0, st>>>(c, P, L, N, rr_part, nbu, tol2);
+      cg_update_kernel<<<grid_b, kUpdBlock, 0, st>>>(c, k, L, N, tol2, r.as<double2>(), p.as<double2>(),
+                                                     y.as<double2>(), ph.as<double2>(), n);
       mark(it, 5);
-      mark(it, 6);
-      shift_update_kernel<<<dim3(nbu, L), kBlock, 0, st>>>(c, P, L, N, r.as<double2>(), p.as<double2>(),
-                                                           y.as<double2>(), ph.as<double2>(), n);
-      mark(it, 7);
       count_launches(3);
-      ++done_in_chunk;
+      ++launched;
       cudaError_t le = cudaGetLastError();
       if (le != cudaSuccess) { status = cuda_fail(le, "shifted CG launch", __FILE__, __LINE__); break; }
     }
     if (status != SSQCD_OK) break;
-    // live-shift count left by the last iteration (parity (k-1) & 1)
-    cudaError_t ce = cudaMemcpyAsync(h_poll, c.cnt + ((k - 1) & 1), sizeof(int), cudaMemcpyDeviceToHost, st);
+    // live-shift count at the start of the next iteration, and the error flag
+    cudaError_t ce = cudaMemcpyAsync(h_poll, c.live_total + (k & 1), sizeof(int), cudaMemcpyDeviceToHost, st);
     if (ce == cudaSuccess) ce = cudaMemcpyAsync(h_poll + 1, c.err, sizeof(int), cudaMemcpyDeviceToHost, st);
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
     if (ce != cudaSuccess) { status = cuda_fail(ce, "shifted CG poll", __FILE__, __LINE__); break; }
     if (timing) {
-      for (int it = 0; it < done_in_chunk; ++it)
-        for (int cls = 0; cls < 4; ++cls) {
+      for (int it = 0; it < launched; ++it)
+        for (int cls = 0; cls < 3; ++cls) {
           float ms = 0.f;
-          cudaEventElapsedTime(&ms, tev[it * 8 + 2 * cls], tev[it * 8 + 2 * cls + 1]);
+          cudaEventElapsedTime(&ms, tev[it * 6 + 2 * cls], tev[it * 6 + 2 * cls + 1]);
           t_iter[cls].push_back(ms);
         }
     }
@@ -506,11 +548,14 @@ int shifted_cg_device(ssqcd_lattice lat, int N, const double2* z_host, int L, co
     SS_CUDA(cudaEventRecord(e1, st));
     int seed_iters = 0;
     std::vector<int> it_all(NL);
+    std::vector<double2> xi_all(3 * (size_t)NL);
     SS_CUDA(cudaMemcpyAsync(&seed_iters, c.seed_iters, sizeof(int), cudaMemcpyDeviceToHost, st));
     SS_CUDA(cudaMemcpyAsync(it_all.data(), c.iters, sizeof(int) * NL, cudaMemcpyDeviceToHost, st));
-    if (xi_host) SS_CUDA(cudaMemcpyAsync(xi_host, c.xi_cur, sizeof(double2) * NL, cudaMemcpyDeviceToHost, st));
+    if (xi_host) SS_CUDA(cudaMemcpyAsync(xi_all.data(), c.xi, sizeof(double2) * 3 * NL, cudaMemcpyDeviceToHost, st));
     SS_CUDA(cudaStreamSynchronize(st));
     if (iters_host) std::copy(it_all.begin(), it_all.end(), iters_host);
+    if (xi_host)  // a shift's last xi sits in slot (its iteration count) mod 3
+      for (int qi = 0; qi < NL; ++qi) xi_host[qi] = xi_all[(size_t)(it_all[qi] % 3) * NL + qi];
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
     if (out) {
@@ -519,12 +564,14 @@ int shifted_cg_device(ssqcd_lattice lat, int N, const double2* z_host, int L, co
       out->shift_updates = 0;
       for (int v2 : it_all) out->shift_updates += v2;
       out->timed = timing;
-      out->launches_update = timing ? std::min<int>(seed_iters, (int)t_iter[3].size()) : 0;
-      for (int cls = 0; cls < 4; ++cls) {
+      out->launches_update = timing ? std::min<int>(seed_iters, (int)t_iter[2].size()) : 0;
+      for (int cls = 0; cls < 4; ++cls) out->ms_k[cls] = 0.0;
+      const int slot_of[3] = {0, 1, 3};  // stencil, seed update, shift update
+      for (int cls = 0; cls < 3; ++cls) {
         double acc = 0.0;
-        // iterations after the last live one only skip their work: not counted
+        // iterations after the last live one skip their work: not counted
         for (int i = 0; i < (int)t_iter[cls].size() && i < seed_iters; ++i) acc += t_iter[cls][i];
-        out->ms_k[cls] = acc;
+        out->ms_k[slot_of[cls]] = acc;
       }
     }
   }

@@ -1,0 +1,411 @@
+// Device building blocks of the Wilson-Dirac stencil (A = gamma5 (I - kappa D),
+// Section 4 of the paper), shared by the stand-alone operator kernels
+// (wilson.cu) and the fused shifted-CG kernels (mshift.cu).
+//
+//   (D psi)(x) = sum_mu (1 - gamma_mu) U_mu(x) psi(x + mu)
+//                     + (1 + gamma_mu) U_mu(x - mu)^H psi(x - mu)
+//
+// DeGrand-Rossi basis: gamma_mu = [[0, B_mu], [B_mu^H, 0]] in 2x2 spin blocks,
+// gamma5 = diag(1, 1, -1, -1).  (1 -+ gamma_mu)/2 are rank-2 projectors, so a
+// hop multiplies only a two-spin half spinor by the link:
+//   forward : h = psi_u - B psi_l, lower part of (1 - gamma) psi = -B^H h,
+//   backward: h = psi_u + B psi_l, lower part of (1 + gamma) psi = +B^H h.
+// B_mu, B_mu^H are signed permutations with entries in {+-1, +-i}: the
+// projection and reconstruction are additions only.
+//
+// Work split: a block covers 32 consecutive sites of one right-hand side;
+// warp w (0..3) applies the forward and backward hop in direction mu = w for
+// those 32 sites, so every warp is branch-uniform and every component load
+// of a warp is one coalesced segment (neighbours of consecutive sites are
+// consecutive except at wraps).  The four partial sums meet in shared
+// memory; warp w then finishes spinor components 3w..3w+2 of the 32 sites.
+// Spinor layout [rhs][12][V] (component-major, site fastest).
+#pragma once
+
+#include "internal.h"
+
+namespace ssqcd {
+namespace wcore {
+
+enum : int { P1 = 0, M1 = 1, PI = 2, MI = 3 };
+
+template <typename C>
+__device__ __forceinline__ C unit_mul(int code, C z) {
+  switch (code) {
+    case P1: return z;
+    case M1: return C{-z.x, -z.y};
+    case PI: return C{-z.y, z.x};
+    default: return C{z.y, -z.x};
+  }
+}
+
+// Row r of B_mu has its single nonzero in column bcol_r with value bcode_r;
+// likewise for B_mu^H (hcol_r / hcode_r).
+template <int MU>
+struct Spin {
+  static constexpr int bcol0 = (MU == 0 || MU == 1) ? 1 : 0;
+  static constexpr int bcol1 = (MU == 0 || MU == 1) ? 0 : 1;
+  static constexpr int bcode0 = MU == 0 ? PI : MU == 1 ? M1 : MU == 2 ? PI : P1;
+  static constexpr int bcode1 = MU == 0 ? PI : MU == 1 ? P1 : MU == 2 ? MI : P1;
+  static constexpr int hcol0 = bcol0;
+  static constexpr int hcol1 = bcol1;
+  static constexpr int hcode0 = MU == 0 ? MI : MU == 1 ? P1 : MU == 2 ? MI : P1;
+  static constexpr int hcode1 = MU == 0 ? MI : MU == 1 ? M1 : MU == 2 ? PI : P1;
+};
+
+template <typename C>
+__device__ __forceinline__ C cadd(C a, C b) { return C{a.x + b.x, a.y + b.y}; }
+template <typename C>
+__device__ __forceinline__ C csub(C a, C b) { return C{a.x - b.x, a.y - b.y}; }
+template <typename C>
+__device__ __forceinline__ C cneg(C a) { return C{-a.x, -a.y}; }
+
+// acc += u h,  acc += conj(u) h
+template <typename C>
+__device__ __forceinline__ void cmac(C& acc, C u, C h) {
+  acc.x = fma(u.x, h.x, acc.x);
+  acc.x = fma(-u.y, h.y, acc.x);
+  acc.y = fma(u.x, h.y, acc.y);
+  acc.y = fma(u.y, h.x, acc.y);
+}
+template <typename C>
+__device__ __forceinline__ void cmac_conj(C& acc, C u, C h) {
+  acc.x = fma(u.x, h.x, acc.x);
+  acc.x = fma(u.y, h.y, acc.x);
+  acc.y = fma(u.x, h.y, acc.y);
+  acc.y = fma(-u.y, h.x, acc.y);
+}
+__device__ __forceinline__ double2 cmul(double2 u, double2 h) {
+  return make_double2(fma(u.x, h.x, -u.y * h.y), fma(u.x, h.y, u.y * h.x));
+}
+__device__ __forceinline__ double2 cmul_conj(double2 u, double2 h) {
+  return make_double2(fma(u.x, h.x, u.y * h.y), fma(u.x, h.y, -u.y * h.x));
+}
+__device__ __forceinline__ float2 cmul(float2 u, float2 h) {
+  return make_float2(fmaf(u.x, h.x, -u.y * h.y), fmaf(u.x, h.y, u.y * h.x));
+}
+__device__ __forceinline__ float2 cmul_conj(float2 u, float2 h) {
+  return make_float2(fmaf(u.x, h.x, u.y * h.y), fmaf(u.x, h.y, -u.y * h.x));
+}
+
+struct Coords {
+  int x, y, z, t;
+};
+
+__device__ __forceinline__ Coords site_coords(int s, const Geometry& g) {
+  Coords c;
+  c.x = s % g.X;
+  int r = s / g.X;
+  c.y = r % g.Y;
+  r /= g.Y;
+  c.z = r % g.Z;
+  c.t = r / g.Z;
+  return c;
+}
+
+// neighbour in direction MU, forward (DIR > 0) or backward; wraps
+// periodically, twrap tells whether the hop crossed the t boundary
+template <int MU, int DIR>
+__device__ __forceinline__ int neighbour(int s, const Coords& c, const Geometry& g, bool& twrap) {
+  twrap = false;
+  if (MU == 0) {
+    if (DIR > 0) return c.x == g.X - 1 ? s - (g.X - 1) : s + 1;
+    return c.x == 0 ? s + (g.X - 1) : s - 1;
+  } else if (MU == 1) {
+    const int st = g.X;
+    if (DIR > 0) return c.y == g.Y - 1 ? s - (g.Y - 1) * st : s + st;
+    return c.y == 0 ? s + (g.Y - 1) * st : s - st;
+  } else if (MU == 2) {
+    const int st = g.X * g.Y;
+    if (DIR > 0) return c.z == g.Z - 1 ? s - (g.Z - 1) * st : s + st;
+    return c.z == 0 ? s + (g.Z - 1) * st : s - st;
+  } else {
+    const int st = g.X * g.Y * g.Z;
+    if (DIR > 0) {
+      twrap = c.t == g.T - 1;
+      return twrap ? s - (g.T - 1) * st : s + st;
+    }
+    twrap = c.t == 0;
+    return twrap ? s + (g.T - 1) * st : s - st;
+  }
+}
+
+// ---- link access ----------------------------------------------------------------
+// FP64: [4][9][V] double2, row-major 3x3.
+struct Links64 {
+  const double2* __restrict__ u;
+  int V;
+  __device__ __forceinline__ double2 get(int mu, int a, int b, int s) const {
+    return __ldg(u + (size_t)(mu * 9 + 3 * a + b) * V + s);
+  }
+};
+
+// FP16 12-parameter: rows 0 and 1 as six __half2 (re, im) in [4][3][V] uint2;
+// row 2 = conj(row0 x row1) (exact for SU(3)).
+__device__ __forceinline__ float2 h2f(unsigned int v) {
+  __half2 h = *reinterpret_cast<__half2*>(&v);
+  return __half22float2(h);
+}
+
+struct Link32 {
+  float2 e[3][3];
+};
+
+__device__ __forceinline__ void load_link16(const uint2* __restrict__ u16, int mu, int s, int V, Link32& L) {
+  const uint2 q0 = __ldg(u16 + (size_t)(mu * 3 + 0) * V + s);
+  const uint2 q1 = __ldg(u16 + (size_t)(mu * 3 + 1) * V + s);
+  const uint2 q2 = __ldg(u16 + (size_t)(mu * 3 + 2) * V + s);
+  L.e[0][0] = h2f(q0.x);
+  L.e[0][1] = h2f(q0.y);
+  L.e[0][2] = h2f(q1.x);
+  L.e[1][0] = h2f(q1.y);
+  L.e[1][1] = h2f(q2.x);
+  L.e[1][2] = h2f(q2.y);
+#pragma unroll
+  for (int b = 0; b < 3; ++b) {
+    const int b1 = (b + 1) % 3, b2 = (b + 2) % 3;
+    const float2 a1 = L.e[0][b1], a2 = L.e[0][b2], c1 = L.e[1][b1], c2 = L.e[1][b2];
+    const float re = a1.x * c2.x - a1.y * c2.y - (a2.x * c1.x - a2.y * c1.y);
+    const float im = a1.x * c2.y + a1.y * c2.x - (a2.x * c1.y + a2.y * c1.x);
+    L.e[2][b] = make_float2(re, -im);
+  }
+}
+
+// ---- one direction: forward + backward hop, accumulated into acc[12] --------------
+template <int MU>
+__device__ __forceinline__ void hop_dir64(const Links64& lk, const double2* __restrict__ in, int s, const Coords& c,
+                                          const Geometry& g, double2 (&acc)[12]) {
+  using S = Spin<MU>;
+  const int V = g.V;
+  {  // forward: (1 - gamma_mu) U_mu(x) psi(x + mu)
+    bool w;
+    const int nb = neighbour<MU, +1>(s, c, g, w);
+    double2 h[2][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const double2 u0 = __ldg(in + (0 * 3 + a) * V + nb);
+      const double2 u1 = __ldg(in + (1 * 3 + a) * V + nb);
+      const double2 l0 = __ldg(in + ((2 + S::bcol0) * 3 + a) * V + nb);
+      const double2 l1 = __ldg(in + ((2 + S::bcol1) * 3 + a) * V + nb);
+      h[0][a] = csub(u0, unit_mul(S::bcode0, l0));
+      h[1][a] = csub(u1, unit_mul(S::bcode1, l1));
+    }
+    if (MU == 3 && w && g.bc_t < 0) {
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        h[0][a] = cneg(h[0][a]);
+        h[1][a] = cneg(h[1][a]);
+      }
+    }
+    double2 wv[2][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const double2 ua0 = lk.get(MU, a, 0, s), ua1 = lk.get(MU, a, 1, s), ua2 = lk.get(MU, a, 2, s);
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        double2 t = cmul(ua0, h[r][0]);
+        cmac(t, ua1, h[r][1]);
+        cmac(t, ua2, h[r][2]);
+        wv[r][a] = t;
+      }
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      acc[0 * 3 + a] = cadd(acc[0 * 3 + a], wv[0][a]);
+      acc[1 * 3 + a] = cadd(acc[1 * 3 + a], wv[1][a]);
+      acc[2 * 3 + a] = csub(acc[2 * 3 + a], unit_mul(S::hcode0, wv[S::hcol0][a]));
+      acc[3 * 3 + a] = csub(acc[3 * 3 + a], unit_mul(S::hcode1, wv[S::hcol1][a]));
+    }
+  }
+  {  // backward: (1 + gamma_mu) U_mu(x - mu)^H psi(x - mu)
+    bool w;
+    const int nb = neighbour<MU, -1>(s, c, g, w);
+    double2 h[2][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const double2 u0 = __ldg(in + (0 * 3 + a) * V + nb);
+      const double2 u1 = __ldg(in + (1 * 3 + a) * V + nb);
+      const double2 l0 = __ldg(in + ((2 + S::bcol0) * 3 + a) * V + nb);
+      const double2 l1 = __ldg(in + ((2 + S::bcol1) * 3 + a) * V + nb);
+      h[0][a] = cadd(u0, unit_mul(S::bcode0, l0));
+      h[1][a] = cadd(u1, unit_mul(S::bcode1, l1));
+    }
+    if (MU == 3 && w && g.bc_t < 0) {
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        h[0][a] = cneg(h[0][a]);
+        h[1][a] = cneg(h[1][a]);
+      }
+    }
+    double2 wv[2][3];
+    // (U^H h)_a = sum_b conj(U_ba) h_b
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const double2 u0a = lk.get(MU, 0, a, nb), u1a = lk.get(MU, 1, a, nb), u2a = lk.get(MU, 2, a, nb);
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        double2 t = cmul_conj(u0a, h[r][0]);
+        cmac_conj(t, u1a, h[r][1]);
+        cmac_conj(t, u2a, h[r][2]);
+        wv[r][a] = t;
+      }
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      acc[0 * 3 + a] = cadd(acc[0 * 3 + a], wv[0][a]);
+      acc[1 * 3 + a] = cadd(acc[1 * 3 + a], wv[1][a]);
+      acc[2 * 3 + a] = cadd(acc[2 * 3 + a], unit_mul(S::hcode0, wv[S::hcol0][a]));
+      acc[3 * 3 + a] = cadd(acc[3 * 3 + a], unit_mul(S::hcode1, wv[S::hcol1][a]));
+    }
+  }
+}
+
+template <int MU>
+__device__ __forceinline__ void hop_dir32(const uint2* __restrict__ u16, const float2* __restrict__ in, int s,
+                                          const Coords& c, const Geometry& g, float2 (&acc)[12]) {
+  using S = Spin<MU>;
+  const int V = g.V;
+  {
+    bool w;
+    const int nb = neighbour<MU, +1>(s, c, g, w);
+    float2 h[2][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const float2 u0 = __ldg(in + (0 * 3 + a) * V + nb);
+      const float2 u1 = __ldg(in + (1 * 3 + a) * V + nb);
+      const float2 l0 = __ldg(in + ((2 + S::bcol0) * 3 + a) * V + nb);
+      const float2 l1 = __ldg(in + ((2 + S::bcol1) * 3 + a) * V + nb);
+      h[0][a] = csub(u0, unit_mul(S::bcode0, l0));
+      h[1][a] = csub(u1, unit_mul(S::bcode1, l1));
+    }
+    if (MU == 3 && w && g.bc_t < 0) {
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        h[0][a] = cneg(h[0][a]);
+        h[1][a] = cneg(h[1][a]);
+      }
+    }
+    Link32 L;
+    load_link16(u16, MU, s, V, L);
+    float2 wv[2][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        float2 t = cmul(L.e[a][0], h[r][0]);
+        cmac(t, L.e[a][1], h[r][1]);
+        cmac(t, L.e[a][2], h[r][2]);
+        wv[r][a] = t;
+      }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      acc[0 * 3 + a] = cadd(acc[0 * 3 + a], wv[0][a]);
+      acc[1 * 3 + a] = cadd(acc[1 * 3 + a], wv[1][a]);
+      acc[2 * 3 + a] = csub(acc[2 * 3 + a], unit_mul(S::hcode0, wv[S::hcol0][a]));
+      acc[3 * 3 + a] = csub(acc[3 * 3 + a], unit_mul(S::hcode1, wv[S::hcol1][a]));
+    }
+  }
+  {
+    bool w;
+    const int nb = neighbour<MU, -1>(s, c, g, w);
+    float2 h[2][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const float2 u0 = __ldg(in + (0 * 3 + a) * V + nb);
+      const float2 u1 = __ldg(in + (1 * 3 + a) * V + nb);
+      const float2 l0 = __ldg(in + ((2 + S::bcol0) * 3 + a) * V + nb);
+      const float2 l1 = __ldg(in + ((2 + S::bcol1) * 3 + a) * V + nb);
+      h[0][a] = cadd(u0, unit_mul(S::bcode0, l0));
+      h[1][a] = cadd(u1, unit_mul(S::bcode1, l1));
+    }
+    if (MU == 3 && w && g.bc_t < 0) {
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        h[0][a] = cneg(h[0][a]);
+        h[1][a] = cneg(h[1][a]);
+      }
+    }
+    Link32 L;
+    load_link16(u16, MU, nb, V, L);
+    float2 wv[2][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        float2 t = cmul_conj(L.e[0][a], h[r][0]);
+        cmac_conj(t, L.e[1][a], h[r][1]);
+        cmac_conj(t, L.e[2][a], h[r][2]);
+        wv[r][a] = t;
+      }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      acc[0 * 3 + a] = cadd(acc[0 * 3 + a], wv[0][a]);
+      acc[1 * 3 + a] = cadd(acc[1 * 3 + a], wv[1][a]);
+      acc[2 * 3 + a] = cadd(acc[2 * 3 + a], unit_mul(S::hcode0, wv[S::hcol0][a]));
+      acc[3 * 3 + a] = cadd(acc[3 * 3 + a], unit_mul(S::hcode1, wv[S::hcol1][a]));
+    }
+  }
+}
+
+// ---- block-level stencil ------------------------------------------------------------
+// A block of 128 threads = 4 warps covers sites s0 .. s0+31 of one rhs.  On
+// return, thread (w, lane) holds hop sums acc_out[0..2] = (D psi) components
+// 3w..3w+2 of site s0 + lane (zero beyond V).  sh: 32 x 12 x 4 complex
+// shared-memory scratch.
+constexpr int kSitesPerBlock = 32;
+constexpr int kStencilThreads = 128;
+
+template <typename C>
+__device__ __forceinline__ void reduce_dirs(C (&acc)[12], C* sh, C (&acc_out)[3]) {
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // sh layout [comp 12][dir 4][site 32]
+#pragma unroll
+  for (int i = 0; i < 12; ++i) sh[(i * 4 + w) * 32 + lane] = acc[i];
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const int comp = 3 * w + k;
+    C v = sh[(comp * 4 + 0) * 32 + lane];
+    v = cadd(v, sh[(comp * 4 + 1) * 32 + lane]);
+    v = cadd(v, sh[(comp * 4 + 2) * 32 + lane]);
+    v = cadd(v, sh[(comp * 4 + 3) * 32 + lane]);
+    acc_out[k] = v;
+  }
+}
+
+__device__ __forceinline__ void block_hops64(const Links64& lk, const double2* __restrict__ in, int s,
+                                             const Geometry& g, double2* sh, double2 (&acc_out)[3]) {
+  double2 acc[12];
+#pragma unroll
+  for (int i = 0; i < 12; ++i) acc[i] = make_double2(0.0, 0.0);
+  if (s < g.V) {
+    const Coords c = site_coords(s, g);
+    switch (threadIdx.x >> 5) {
+      case 0: hop_dir64<0>(lk, in, s, c, g, acc); break;
+      case 1: hop_dir64<1>(lk, in, s, c, g, acc); break;
+      case 2: hop_dir64<2>(lk, in, s, c, g, acc); break;
+      default: hop_dir64<3>(lk, in, s, c, g, acc); break;
+    }
+  }
+  reduce_dirs(acc, sh, acc_out);
+}
+
+__device__ __forceinline__ void block_hops32(const uint2* __restrict__ u16, const float2* __restrict__ in, int s,
+                                             const Geometry& g, float2* sh, float2 (&acc_out)[3]) {
+  float2 acc[12];
+#pragma unroll
+  for (int i = 0; i < 12; ++i) acc[i] = make_float2(0.f, 0.f);
+  if (s < g.V) {
+    const Coords c = site_coords(s, g);
+    switch (threadIdx.x >> 5) {
+      case 0: hop_dir32<0>(u16, in, s, c, g, acc); break;
+      case 1: hop_dir32<1>(u16, in, s, c, g, acc); break;
+      case 2: hop_dir32<2>(u16, in, s, c, g, acc); break;
+      default: hop_dir32<3>(u16, in, s, c, g, acc); break;
+    }
+  }
+  reduce_dirs(acc, sh, acc_out);
+}
+
+}  // namespace wcore
+}  // namespace ssqcd
