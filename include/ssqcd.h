@@ -170,6 +170,25 @@ int ssqcd_shifted_cg(ssqcd_lattice lat, int N, const double* z, int L, const dou
 int ssqcd_moments(ssqcd_lattice lat, int N, int M, int L, const double* w, const double* zeta,
                   const double* y, double* s_hat, int on_device);
 
+/* Allocation-free variant of ssqcd_moments for callers that cannot allocate
+ * device memory when they need the moments -- for example code running while
+ * a CUDA graph is being captured, programs that hand all device memory to
+ * their own pool up front, or allocation-free real-time loops.  The paper has
+ * no counterpart; it computes the same s_hat[l][k] = sum_j w_j zeta_j^k
+ * y[l][j] as ssqcd_moments.
+ * y: device, [L][N][n] complex128; s_hat: device, [L][M][n] complex128
+ * (any element order, the same for both; n = 12 V for spinor fields);
+ * w, zeta: host, [N] complex128; work is issued on cuda_stream and the call
+ * does not wait for it.  No cudaMalloc/cudaFree or allocating library call:
+ * the only scratch, the N x M coefficient table, lives in a fixed 64 KiB
+ * device array held by every GPU that loads the library until exit, so
+ * N * M <= 4096 and N <= 256 (else SSQCD_ERR_ARG).  The first call on a
+ * device looks up that array's device address (cudaGetSymbolAddress); make
+ * that first call before any stream capture.  All calls share the array:
+ * calls that overlap on the GPU (different streams, no ordering) race. */
+int ssqcd_moments_noalloc(int N, int M, int L, long long n, const double* w, const double* zeta,
+                          const double* y, double* s_hat, void* cuda_stream);
+
 /* ---- the eigensolver --------------------------------------------------------------- */
 
 void ssqcd_default_opts(ssqcd_opts* opts);

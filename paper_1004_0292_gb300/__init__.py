@@ -24,7 +24,7 @@ __all__ = [
     "OK", "ERR_ARG", "ERR_OOM", "ERR_BREAKDOWN", "ERR_NOCONV", "ERR_CUDA",
     "FP64", "MIXED", "PATH_LINES", "PATH_CIRCLE", "SsqcdError",
     "library_path", "lib", "create_lattice", "upload_gauge", "apply_H", "apply_H_mixed",
-    "contour", "shifted_cg", "moments", "ss_solve", "ss_eigpairs", "small_eigh",
+    "contour", "shifted_cg", "moments", "moments_noalloc", "ss_solve", "ss_eigpairs", "small_eigh",
     "kernel_launches", "set_kernel_timing", "Lattice", "Result", "Opts", "Stats",
 ]
 
@@ -98,6 +98,7 @@ def lib():
         "ssqcd_last_error": (C.c_char_p, []),
         "ssqcd_kernel_launches": (C.c_longlong, []),
         "ssqcd_set_kernel_timing": (i, [i]),
+        "ssqcd_moments_noalloc": (i, [i, i, i, C.c_longlong, vp, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -254,6 +255,26 @@ def moments(lat: Lattice, w, zeta, y, M):
         s = np.empty((L, M, lat.V, 4, 3), dtype=np.complex128)
         ps = s.ctypes.data
     _check(lib().ssqcd_moments(lat.handle, N, int(M), L, w.ctypes.data, zeta.ctypes.data, py, ps, dev))
+    return s
+
+
+def moments_noalloc(w, zeta, y, M, stream=None):
+    """Allocation-free moments: y (L, N, ...) complex128 CUDA tensor ->
+    s_hat (L, M, ...) (Eq. 2).  Uses the library's fixed device scratch
+    (N * M <= 4096); returns a new tensor allocated here by torch, the
+    library itself allocates nothing."""
+    import torch
+    w = np.ascontiguousarray(w, dtype=np.complex128)
+    zeta = np.ascontiguousarray(zeta, dtype=np.complex128)
+    N = len(w)
+    if not (_is_torch(y) and y.is_cuda and y.is_contiguous() and y.dtype == torch.complex128):
+        raise ValueError("y must be a contiguous complex128 CUDA tensor")
+    L = y.shape[0]
+    n = y.numel() // (L * N)
+    s = torch.empty((L, M) + tuple(y.shape[2:]), dtype=torch.complex128, device=y.device)
+    st = _stream_handle(stream if stream is not None else torch.cuda.current_stream())
+    _check(lib().ssqcd_moments_noalloc(N, int(M), L, n, w.ctypes.data, zeta.ctypes.data, y.data_ptr(),
+                                       s.data_ptr(), st))
     return s
 
 
