@@ -158,10 +158,11 @@ class Lattice:
 class Result:
     """Owning handle of a ``ssqcd_result`` plus the status of the solve."""
 
-    def __init__(self, handle, status, lattice):
+    def __init__(self, handle, status, lattice, error=""):
         self.handle = handle
         self.status = status
         self.lattice = lattice
+        self.error = error
 
     def __del__(self):
         if getattr(self, "handle", None):
@@ -293,7 +294,8 @@ def ss_solve(lat: Lattice, interval, N, M, sources, beta=0.3, nprime=0, tol=1e-1
     code = lib().ssqcd_ss_solve(lat.handle, iv, int(N), int(M), L, C.byref(o), C.byref(h))
     if not h.value:
         _check(code)
-    return Result(h, code, lat)
+    err = lib().ssqcd_last_error().decode() if code != OK else ""
+    return Result(h, code, lat, err)
 
 
 def ss_eigpairs(res: Result, want_vectors=True):

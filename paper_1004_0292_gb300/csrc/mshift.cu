@@ -23,26 +23,26 @@
 // block (fixed summation order, no host round trip):
 //   A. stencil q = K p for every source with block partials of (p, q); the
 //      last block forms alpha_k = (r, r) / (p, q) (breakdown check);
-//   B. seed update r -= alpha q with partials of ||r||^2; the last block
-//      forms (r_{k+1}, r_{k+1}) and beta_k;
-//   C. fused update: every block recomputes the xi recurrence of its
-//      source's shifts (a few dozen FP64 operations per shift, spread over all
-//      SMs instead of serialised in one), then for every live shift
-//      y_j += a_j p-hat_j, p-hat_j = r + b_j p-hat_j, and p = r + beta p.
+//   B. seed update r -= alpha q with partials of ||r||^2; meanwhile the
+//      blocks also form xi_{k+1} (it needs only alpha_k and older scalars),
+//      one shift per block, so the FP64 divisions run on many SMs; the last
+//      block forms (r_{k+1}, r_{k+1}), beta_k, the coefficients a_j, b_j and
+//      the freeze test, and writes per source the ordered list of shifts to
+//      update;
+//   C. fused update: for every listed shift y_j += a_j p-hat_j,
+//      p-hat_j = r + b_j p-hat_j, then p = r + beta p.
 // (A two-kernel form that obtains ||r_{k+1}||^2 from (r, r) - 2 alpha (r, q)
 // + alpha^2 (q, q) was tried and rejected: on the indefinite seed the
 // residual can drop by many orders in one step, the three terms cancel, and
 // shifts froze on a wrong residual estimate.)
-// Block 0 of each source also stores xi_{k+1}, the freeze flags and the
-// per-shift iteration counts.  xi lives in a ring of three slots indexed by
-// k mod 3, the other state in two slots indexed by the parity P = k mod 2, so
-// readers and the single writer of an iteration never touch the same slot.
-// Kernel A of iteration k skips when no shift was live after iteration k-1;
-// the host polls the live count every 16 iterations.  All reductions have a
-// fixed order, so runs are bit-reproducible.
+// Every piece of state has a single writer per iteration (a last block), so
+// nothing needs double buffering.  Kernel A skips when no shift is live; the
+// host replays a CUDA graph of 16 iterations and polls the live count between
+// replays.  All reductions have a fixed order: runs are bit-reproducible.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <vector>
 
 #include "wilson_core.cuh"
@@ -52,32 +52,47 @@ namespace {
 
 using namespace wcore;
 
-struct SeedIter {
-  double alpha;  // alpha_k
-  double beta;   // beta_k
-  double rr;     // (r_{k+1}, r_{k+1})
-  double pad;
+// Per-source seed state; single writer: the last block of kernel B.
+struct SeedState {
+  double rr;          // (r_k, r_k)
+  double alpha_prev;  // alpha_{k-1}
+  double beta_prev;   // beta_{k-1}
+  double beta;        // beta_k (valid after kernel B of iteration k)
+  double scale;       // power of two applied to r and p by kernel C of this iteration
+  double pad[3];      // pad[0] = 1 / rr
 };
 
-// Device-side control block of one solve (L sources, N shifts).
+// Device-side control block of one solve (L sources, N shifts).  Every field
+// has one writer per iteration: the last block of kernel A (alpha, ran, err,
+// seed_iters) or of kernel B (everything per shift, the coefficient lists,
+// the live counts); the other kernels only read.
 struct Control {
-  SeedIter* seed;      // [2][L]   slot k&1 written by kernel A of iteration k
+  SeedState* seed;     // [L]
+  double* alpha;       // [L]     alpha_k
   double* vnorm2;      // [L]
-  int* src_live;       // [2][L]   live shifts at the start of iteration k: slot k&1
-  int* live_total;     // [2]
-  int* ran;            // [2]      kernel A of iteration k did its work
+  int* live;           // [L]     shifts still iterating
+  int* live_total;     // [1]
+  int* ran;            // [1]     kernel A of this iteration did its work
   int* err;            // [1]
   int* seed_iters;     // [1]
-  unsigned* done;      // [2]      last-block tickets of kernels A and B
-  double2* shift_s;    // [L*N]    s_j = z_j - sigma
-  double2* xi;         // [3][L*N] ring: slot k%3 = xi_k
-  int* act;            // [2][L*N] active at the start of iteration k: slot k&1
+  unsigned* done;      // [2]     last-block tickets of kernels A and B
+  double2* shift_s;    // [L*N]   s_j = z_j - sigma
+  double2* xi_cur;     // [L*N]   xi_k
+  double2* xi_prev;    // [L*N]   xi_{k-1}
+  double2* xi_next;    // [L*N]   xi_{k+1}, from the blocks of kernel B
+  double2* ratio;      // [L*N]   xi_{k+1} / xi_k
+  int* act;            // [L*N]
   int* iters;          // [L*N]
+  int* list_n;         // [L]     shifts updated in this iteration
+  int* list_j;         // [L*N]   their indices, ascending
+  double2* list_a;     // [L*N]   y += a p-hat
+  double2* list_b;     // [L*N]   p-hat = r + b p-hat
   double* partial;     // [L][nbw]  (p, q) partials of kernel A
-  double* partial_rr;  // [L][nbu]  ||r||^2 partials of kernel B
+  double* partial_rr;  // [L][nbs]  ||r||^2 partials of kernel B
 };
 
 constexpr int kUpdBlock = 256;
+constexpr int kSeedBlock = 256;
 constexpr int kMaxShifts = 256;
 constexpr int kMaxSources = 64;
 
@@ -86,6 +101,17 @@ __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
+
+// The seed system usually converges far faster than the shifted ones (its
+// shift sigma lies in a gap of the spectrum while the quadrature points sit
+// close to eigenvalues), so ||r|| keeps shrinking -- 1e-100 and below --
+// while xi grows to compensate.  Before (r, r) leaves the FP64 range, r and
+// p are multiplied by an exact power of two s and every xi is divided by s;
+// y is unchanged and p-hat absorbs s through b (see kernels B and C).  This
+// also keeps |xi|^2 and the other products of the recurrences far inside
+// the FP64 range, so they need no overflow guards.
+constexpr double kRescaleBelow = 0x1p-400;  // of ||v||^2
+constexpr double kRescaleBy = 0x1p+200;
 
 // ---- initialisation ---------------------------------------------------------------
 __global__ void init_vectors_kernel(const double2* __restrict__ v, double2* __restrict__ r, double2* __restrict__ p,
@@ -105,25 +131,24 @@ __global__ void init_vectors_kernel(const double2* __restrict__ v, double2* __re
 // A source with ||v|| = 0 has the exact solution y = 0 and starts frozen.
 __global__ void init_control_kernel(Control c, const double* __restrict__ vn2, int L, int N) {
   for (int t = threadIdx.x; t < L; t += blockDim.x) {
-    c.seed[L + t] = SeedIter{1.0, 0.0, vn2[t], 0.0};  // "iteration -1": alpha_{-1} = 1, beta_{-1} = 0, rr_0
-    c.seed[t] = SeedIter{0.0, 0.0, 0.0, 0.0};
+    // rr_0, alpha_{-1} = 1, beta_{-1} = 0, scale 1, 1 / rr_0
+    c.seed[t] = SeedState{vn2[t], 1.0, 0.0, 0.0, 1.0, {vn2[t] > 0.0 ? 1.0 / vn2[t] : 0.0, 0.0, 0.0}};
+    c.alpha[t] = 0.0;
     c.vnorm2[t] = vn2[t];
-    c.src_live[t] = vn2[t] > 0.0 ? N : 0;
-    c.src_live[L + t] = 0;
+    c.live[t] = vn2[t] > 0.0 ? N : 0;
+    c.list_n[t] = 0;
   }
   for (int t = threadIdx.x; t < L * N; t += blockDim.x) {
-    c.xi[t] = make_double2(1.0, 0.0);              // xi_0
-    c.xi[2 * L * N + t] = make_double2(1.0, 0.0);  // xi_{-1} (slot 2 = -1 mod 3)
+    c.xi_cur[t] = make_double2(1.0, 0.0);
+    c.xi_prev[t] = make_double2(1.0, 0.0);
     c.act[t] = vn2[t / N] > 0.0 ? 1 : 0;
-    c.act[L * N + t] = 0;
     c.iters[t] = 0;
   }
   if (threadIdx.x == 0) {
     int live = 0;
     for (int l = 0; l < L; ++l) live += vn2[l] > 0.0 ? N : 0;
-    c.live_total[0] = live;
-    c.live_total[1] = 0;
-    c.ran[0] = c.ran[1] = 0;
+    *c.live_total = live;
+    *c.ran = 0;
     *c.err = 0;
     *c.seed_iters = 0;
     c.done[0] = c.done[1] = 0u;
@@ -132,14 +157,10 @@ __global__ void init_control_kernel(Control c, const double* __restrict__ vn2, i
 
 // ---- A. stencil q = K p + (p, q) partials; last block: alpha_k ---------------------
 __global__ void __launch_bounds__(kStencilThreads)
-cg_stencil_kernel(Control c, int P, int L, Geometry g, const double2* __restrict__ u, double sigma,
+cg_stencil_kernel(Control c, int L, Geometry g, const double2* __restrict__ u, double sigma,
                   const double2* __restrict__ p_all, double2* __restrict__ q_all) {
-  if (*c.err != 0 || c.live_total[P] == 0) {
-    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
-      c.ran[P] = 0;
-      c.live_total[1 - P] = 0;
-      for (int l = 0; l < L; ++l) c.src_live[(1 - P) * L + l] = 0;
-    }
+  if (*c.err != 0 || *c.live_total == 0) {
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *c.ran = 0;
     return;
   }
   __shared__ double2 sh[12 * 4 * 32];
@@ -150,7 +171,7 @@ cg_stencil_kernel(Control c, int P, int L, Geometry g, const double2* __restrict
   const int V = g.V;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   double d_pq = 0.0;
-  if (c.src_live[P * L + l] != 0) {
+  if (c.live[l] != 0) {
     const double2* p = p_all + (size_t)l * 12 * V;
     double2* q = q_all + (size_t)l * 12 * V;
     const int s = blockIdx.x * kSitesPerBlock + lane;
@@ -196,108 +217,59 @@ cg_stencil_kernel(Control c, int P, int L, Geometry g, const double2* __restrict
   }
   __syncthreads();
   for (int ls = threadIdx.x; ls < L; ls += blockDim.x) {
-    if (c.src_live[P * L + ls] == 0) {
-      c.seed[P * L + ls] = SeedIter{0.0, 0.0, 0.0, 0.0};
-      continue;
-    }
+    if (c.live[ls] == 0) continue;
     const double pq = sums[ls];
-    const double rr = c.seed[(1 - P) * L + ls].rr;
+    const double rr = c.seed[ls].rr;
     if (!(fabs(pq) >= 1e-30 * rr)) {  // breakdown (also catches NaN)
       atomicExch(c.err, 1);
       continue;
     }
-    c.seed[P * L + ls] = SeedIter{rr / pq, 0.0, 0.0, 0.0};
+    c.alpha[ls] = rr / pq;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
     const bool ok = *((volatile int*)c.err) == 0;
-    c.ran[P] = ok ? 1 : 0;
-    c.live_total[1 - P] = 0;
+    *c.ran = ok ? 1 : 0;
     if (ok) atomicAdd(c.seed_iters, 1);
     c.done[0] = 0u;
   }
-  for (int ls = threadIdx.x; ls < L; ls += blockDim.x) c.src_live[(1 - P) * L + ls] = 0;
 }
 
-// ---- B. seed update r -= alpha q, ||r||^2 partials; last block: rr_{k+1}, beta_k -----
-__global__ void __launch_bounds__(kUpdBlock)
-cg_seed_kernel(Control c, int P, int L, double2* __restrict__ r, const double2* __restrict__ q, long long n) {
-  if (c.ran[P] == 0) return;
-  __shared__ double sred[kUpdBlock / 32];
+// ---- B. seed update + all scalar recurrences -----------------------------------------
+// FP64 on GB300 has a dependent-operation latency of ~64 cycles (a division
+// ~630), so this kernel is written to keep FP64 dependency chains short:
+//  * the blocks do r -= alpha q with two independent accumulators of ||r||^2;
+//  * meanwhile lane 0 of the last warp of block b forms xi_{k+1} and
+//    xi_{k+1}/xi_k for shifts b, b + nblocks, ... (they need only alpha_k and
+//    older scalars): the two divisions of a shift run on different SMs;
+//  * the last block sums the partials, forms beta_k = rr_{k+1} / rr_k with the
+//    stored reciprocal of rr_k, the coefficients a_j = alpha_k xi_{k+1} and
+//    b_j = s beta_k xi_{k+1}/xi_k and the freeze test |xi|^2 rr <= tol^2 ||v||^2
+//    (products only), and builds each source's ordered list of shifts with
+//    warp ballots.
+__global__ void __launch_bounds__(kSeedBlock)
+cg_seed_kernel(Control c, int L, int N, double tol2, double2* __restrict__ r, const double2* __restrict__ q,
+               long long n) {
+  if (*c.ran == 0) return;
+  __shared__ double sred[kSeedBlock / 32];
   __shared__ double sums[kMaxSources];
+  __shared__ double s_scale[kMaxSources], s_beta[kMaxSources];
+  __shared__ double2 s_a[kMaxShifts], s_b[kMaxShifts];
+  __shared__ int s_flag[kMaxShifts];
   __shared__ bool s_last;
   const int l = blockIdx.y;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  double acc = 0.0;
-  if (c.src_live[P * L + l] != 0) {
-    const double alpha = c.seed[P * L + l].alpha;
-    double2* rl = r + (long long)l * n;
-    const double2* ql = q + (long long)l * n;
-    for (long long e = blockIdx.x * (long long)kUpdBlock + threadIdx.x; e < n;
-         e += (long long)gridDim.x * kUpdBlock) {
-      double2 x = rl[e];
-      const double2 y = ql[e];
-      x.x = fma(-alpha, y.x, x.x);
-      x.y = fma(-alpha, y.y, x.y);
-      rl[e] = x;
-      acc = fma(x.x, x.x, fma(x.y, x.y, acc));
-    }
-  }
-  acc = warp_sum(acc);
-  if (lane == 0) sred[w] = acc;
-  __syncthreads();
-  const int nb = gridDim.x;
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int i = 0; i < kUpdBlock / 32; ++i) t += sred[i];
-    c.partial_rr[(size_t)l * nb + blockIdx.x] = t;
-    __threadfence();
-    const unsigned ticket = atomicAdd(&c.done[1], 1u);
-    s_last = ticket == gridDim.x * gridDim.y - 1;
-  }
-  __syncthreads();
-  if (!s_last) return;
-  __threadfence();
-  for (int ls = w; ls < L; ls += kUpdBlock / 32) {
-    double a = 0.0;
-    for (int b = lane; b < nb; b += 32) a += __ldcg(c.partial_rr + (size_t)ls * nb + b);
-    a = warp_sum(a);
-    if (lane == 0) sums[ls] = a;
-  }
-  __syncthreads();
-  for (int ls = threadIdx.x; ls < L; ls += blockDim.x) {
-    if (c.src_live[P * L + ls] == 0) continue;
-    SeedIter sd = c.seed[P * L + ls];
-    const double rr = c.seed[(1 - P) * L + ls].rr;
-    sd.rr = sums[ls];
-    sd.beta = sums[ls] / rr;
-    c.seed[P * L + ls] = sd;
-  }
-  if (threadIdx.x == 0) c.done[1] = 0u;
-}
-
-// ---- C. fused update ------------------------------------------------------------------
-__global__ void __launch_bounds__(kUpdBlock)
-cg_update_kernel(Control c, int k, int L, int N, double tol2, const double2* __restrict__ r,
-                 double2* __restrict__ p, double2* __restrict__ y, double2* __restrict__ ph, long long n) {
-  const int P = k & 1;
-  const int l = blockIdx.y;
-  if (c.ran[P] == 0 || c.src_live[P * L + l] == 0) return;
-  __shared__ int s_j[kMaxShifts];
-  __shared__ double2 s_a[kMaxShifts];
-  __shared__ double2 s_b[kMaxShifts];
-  __shared__ int s_flag[kMaxShifts];  // 1: update this iteration; 2: and stays live
-  __shared__ int s_n, s_live;
-  const SeedIter cur = c.seed[P * L + l];
-  const SeedIter prev = c.seed[(1 - P) * L + l];
-  const int slot_k = k % 3, slot_km1 = (k + 2) % 3, slot_kp1 = (k + 1) % 3;
   const int NL = N * L;
-  for (int j = threadIdx.x; j < N; j += blockDim.x) {
-    const int qi = l * N + j;
-    int flag = 0;
-    if (c.act[P * NL + qi]) {
-      const double2 xc = c.xi[slot_k * NL + qi], xp = c.xi[slot_km1 * NL + qi], s = c.shift_s[qi];
-      const double alpha = cur.alpha, ap = prev.alpha, bp = prev.beta;
+  if (w == kSeedBlock / 32 - 1 && lane == 0) {
+    const int nblk = gridDim.x * gridDim.y;
+    for (int qi = blockIdx.y * gridDim.x + blockIdx.x; qi < NL; qi += nblk) {
+      const int ls = qi / N;
+      if (c.live[ls] == 0 || !c.act[qi]) continue;
+      const SeedState sd = c.seed[ls];
+      const double alpha = c.alpha[ls];
+      const double2 xc = c.xi_cur[qi], xp = c.xi_prev[qi], s = c.shift_s[qi];
+      const double ap = sd.alpha_prev, bp = sd.beta_prev;
+      const double inv_c = 1.0 / (xc.x * xc.x + xc.y * xc.y);  // independent of the chain below
       // xi_{k+1} = xi_k xi_{k-1} alpha_{k-1} /
       //            [alpha_k beta_{k-1} (xi_{k-1} - xi_k) + xi_{k-1} alpha_{k-1} (1 + s alpha_k)]
       double2 num;
@@ -312,99 +284,279 @@ cg_update_kernel(Control c, int k, int L, int N, double tol2, const double2* __r
       double2 xn;
       xn.x = (num.x * den.x + num.y * den.y) * inv_d;
       xn.y = (num.y * den.x - num.x * den.y) * inv_d;
-      // b = beta xi_{k+1} / xi_k = beta xi_{k+1} conj(xi_k) / |xi_k|^2
-      const double bc = cur.beta / (xc.x * xc.x + xc.y * xc.y);
-      s_a[j] = make_double2(alpha * xn.x, alpha * xn.y);
-      s_b[j] = make_double2(bc * (xn.x * xc.x + xn.y * xc.y), bc * (xn.y * xc.x - xn.x * xc.y));
-      const bool live = (xn.x * xn.x + xn.y * xn.y) * cur.rr > tol2 * c.vnorm2[l];
-      flag = live ? 2 : 1;
-      if (blockIdx.x == 0) {
-        c.xi[slot_kp1 * NL + qi] = xn;
-        c.act[(1 - P) * NL + qi] = live ? 1 : 0;
-        c.iters[qi] += 1;
-      }
-    } else if (blockIdx.x == 0) {
-      c.act[(1 - P) * NL + qi] = 0;
+      c.xi_next[qi] = xn;
+      c.ratio[qi] = make_double2((xn.x * xc.x + xn.y * xc.y) * inv_c, (xn.y * xc.x - xn.x * xc.y) * inv_c);
     }
-    s_flag[j] = flag;
+  }
+  double acc0 = 0.0, acc1 = 0.0;
+  if (c.live[l] != 0) {
+    const double alpha = c.alpha[l];
+    double2* rl = r + (long long)l * n;
+    const double2* ql = q + (long long)l * n;
+    const long long stride = (long long)gridDim.x * kSeedBlock;
+    long long e = blockIdx.x * (long long)kSeedBlock + threadIdx.x;
+    for (; e + stride < n; e += 2 * stride) {
+      double2 x0 = rl[e], x1 = rl[e + stride];
+      const double2 y0 = ql[e], y1 = ql[e + stride];
+      x0.x = fma(-alpha, y0.x, x0.x);
+      x0.y = fma(-alpha, y0.y, x0.y);
+      x1.x = fma(-alpha, y1.x, x1.x);
+      x1.y = fma(-alpha, y1.y, x1.y);
+      rl[e] = x0;
+      rl[e + stride] = x1;
+      acc0 = fma(x0.x, x0.x, fma(x0.y, x0.y, acc0));
+      acc1 = fma(x1.x, x1.x, fma(x1.y, x1.y, acc1));
+    }
+    if (e < n) {
+      double2 x0 = rl[e];
+      const double2 y0 = ql[e];
+      x0.x = fma(-alpha, y0.x, x0.x);
+      x0.y = fma(-alpha, y0.y, x0.y);
+      rl[e] = x0;
+      acc0 = fma(x0.x, x0.x, fma(x0.y, x0.y, acc0));
+    }
+  }
+  double acc = warp_sum(acc0 + acc1);
+  if (lane == 0) sred[w] = acc;
+  __syncthreads();
+  const int nb = gridDim.x;
+  if (threadIdx.x == 0) {
+    const double t = ((sred[0] + sred[1]) + (sred[2] + sred[3])) + ((sred[4] + sred[5]) + (sred[6] + sred[7]));
+    c.partial_rr[(size_t)l * nb + blockIdx.x] = t;
+    __threadfence();
+    const unsigned ticket = atomicAdd(&c.done[1], 1u);
+    s_last = ticket == gridDim.x * gridDim.y - 1;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  for (int ls = w; ls < L; ls += kSeedBlock / 32) {
+    double a0 = 0.0, a1 = 0.0;
+    int b = lane;
+    for (; b + 32 < nb; b += 64) {
+      a0 += __ldcg(c.partial_rr + (size_t)ls * nb + b);
+      a1 += __ldcg(c.partial_rr + (size_t)ls * nb + b + 32);
+    }
+    if (b < nb) a0 += __ldcg(c.partial_rr + (size_t)ls * nb + b);
+    const double a = warp_sum(a0 + a1);
+    if (lane == 0) {
+      sums[ls] = a;
+      const SeedState sd = c.seed[ls];
+      s_beta[ls] = a * sd.pad[0];  // pad[0] holds 1 / rr_k
+      s_scale[ls] = (c.live[ls] != 0 && a < kRescaleBelow * c.vnorm2[ls] && a > 0.0) ? kRescaleBy : 1.0;
+    }
+  }
+  __syncthreads();
+  // per shift: coefficients and the freeze test from xi_{k+1}
+  for (int qi = threadIdx.x; qi < NL; qi += blockDim.x) {
+    const int ls = qi / N;
+    int flag = 0;
+    if (c.live[ls] != 0 && c.act[qi]) {
+      const double alpha = c.alpha[ls];
+      const double rr1 = sums[ls], beta = s_beta[ls];
+      const double sc = s_scale[ls], inv_sc = sc == 1.0 ? 1.0 : 1.0 / kRescaleBy;
+      const double2 xn = __ldcg(c.xi_next + qi), ratio = __ldcg(c.ratio + qi), xc = c.xi_cur[qi];
+      s_a[qi] = make_double2(alpha * xn.x, alpha * xn.y);
+      s_b[qi] = make_double2(sc * beta * ratio.x, sc * beta * ratio.y);
+      const bool live = (xn.x * xn.x + xn.y * xn.y) * rr1 > tol2 * c.vnorm2[ls];
+      flag = live ? 2 : 1;
+      c.xi_prev[qi] = make_double2(xc.x * inv_sc, xc.y * inv_sc);
+      c.xi_cur[qi] = make_double2(xn.x * inv_sc, xn.y * inv_sc);
+      c.act[qi] = live ? 1 : 0;
+      c.iters[qi] += 1;
+    }
+    s_flag[qi] = flag;
+  }
+  __syncthreads();
+  // per source (one warp each): ordered list by ballots, live count, seed state
+  for (int ls = w; ls < L; ls += kSeedBlock / 32) {
+    int m = 0, live = 0;
+    for (int j0 = 0; j0 < N; j0 += 32) {
+      const int j = j0 + lane;
+      const int f = j < N ? s_flag[ls * N + j] : 0;
+      const unsigned upd = __ballot_sync(0xffffffffu, f != 0);
+      const unsigned stay = __ballot_sync(0xffffffffu, f == 2);
+      if (f) {
+        const int pos = m + __popc(upd & ((1u << lane) - 1u));
+        c.list_j[ls * N + pos] = j;
+        c.list_a[ls * N + pos] = s_a[ls * N + j];
+        c.list_b[ls * N + pos] = s_b[ls * N + j];
+      }
+      m += __popc(upd);
+      live += __popc(stay);
+    }
+    if (lane == 0) {
+      c.list_n[ls] = m;
+      if (c.live[ls] != 0) {
+        const double sc = s_scale[ls];
+        const double rr = sums[ls] * sc * sc;
+        c.seed[ls] = SeedState{rr, c.alpha[ls], s_beta[ls], s_beta[ls], sc, {1.0 / rr, 0.0, 0.0}};
+      }
+      c.live[ls] = live;
+    }
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    int m = 0, live = 0;
-    for (int j = 0; j < N; ++j) {
-      if (s_flag[j]) {
-        s_j[m] = j;
-        s_a[m] = s_a[j];  // m <= j: in-place compaction keeps the order
-        s_b[m] = s_b[j];
-        ++m;
-      }
-      live += s_flag[j] == 2;
-    }
-    s_n = m;
-    s_live = live;
-    if (blockIdx.x == 0) {
-      c.src_live[(1 - P) * L + l] = live;
-      atomicAdd(&c.live_total[1 - P], live);
-    }
+    int tot = 0;
+    for (int ls = 0; ls < L; ++ls) tot += c.live[ls];
+    *c.live_total = tot;
+    c.done[1] = 0u;
+  }
+}
+
+// ---- C. fused multi-shift update -------------------------------------------------------
+// Thread per EPT elements (stride blockDim) of one source; the block stages
+// its source's list of shifts in shared memory and every thread walks it, two
+// shifts at a time, so each lane keeps 4 EPT loads in flight.  r is rescaled
+// in place when kernel B chose a scale; then p = r + beta p.
+// update coefficients with the imaginary parts negated once per block
+struct alignas(32) Coef4 {
+  double x, y, z, w;  // a.x, -a.y, b.x, -b.y
+};
+
+template <int EPT>
+__global__ void __launch_bounds__(kUpdBlock)
+cg_update_kernel(Control c, int N, double2* __restrict__ r, double2* __restrict__ p,
+                 double2* __restrict__ y, double2* __restrict__ ph, long long n) {
+  if (*c.ran == 0) return;
+  const int l = blockIdx.y;
+  const int m = c.list_n[l];
+  const bool cont = c.live[l] != 0;
+  if (m == 0 && !cont) return;
+  __shared__ int s_j[kMaxShifts];
+  __shared__ Coef4 s_ab[kMaxShifts];
+  __shared__ double s_ay[kMaxShifts], s_by[kMaxShifts];
+  for (int t = threadIdx.x; t < m; t += blockDim.x) {
+    const double2 a = c.list_a[l * N + t], b = c.list_b[l * N + t];
+    s_j[t] = c.list_j[l * N + t];
+    s_ab[t] = Coef4{a.x, -a.y, b.x, -b.y};
+    s_ay[t] = a.y;
+    s_by[t] = b.y;
   }
   __syncthreads();
-  const int m = s_n;
-  const bool seed_continues = s_live > 0;
-  const double alpha = cur.alpha, beta = cur.beta;
-  (void)alpha;
-  const double2* rl = r + (long long)l * n;
+  const double sc = c.seed[l].scale;  // exact power of two, usually 1
+  const double beta = sc * c.seed[l].beta;
+  double2* rl = r + (long long)l * n;
   double2* pl = p + (long long)l * n;
-  for (long long e = blockIdx.x * (long long)kUpdBlock + threadIdx.x; e < n; e += (long long)gridDim.x * kUpdBlock) {
-    const double2 re = rl[e];
+  double2* yl = y + (long long)l * N * n;
+  double2* hl = ph + (long long)l * N * n;
+  const long long chunk = (long long)kUpdBlock * EPT;
+  for (long long base = blockIdx.x * chunk + threadIdx.x; base < n; base += (long long)gridDim.x * chunk) {
+    double2 rv[EPT];
+#pragma unroll
+    for (int i = 0; i < EPT; ++i) {
+      const long long e = base + (long long)i * kUpdBlock;
+      double2 x = e < n ? rl[e] : make_double2(0.0, 0.0);
+      if (sc != 1.0) {
+        x = make_double2(sc * x.x, sc * x.y);
+        if (e < n) rl[e] = x;
+      }
+      rv[i] = x;
+    }
     int t = 0;
     for (; t + 2 <= m; t += 2) {
-      double2* y0 = y + ((long long)l * N + s_j[t]) * n + e;
-      double2* p0 = ph + ((long long)l * N + s_j[t]) * n + e;
-      double2* y1 = y + ((long long)l * N + s_j[t + 1]) * n + e;
-      double2* p1 = ph + ((long long)l * N + s_j[t + 1]) * n + e;
-      double2 yv0 = *y0, pv0 = *p0, yv1 = *y1, pv1 = *p1;
-      const double2 a0 = s_a[t], b0 = s_b[t], a1 = s_a[t + 1], b1 = s_b[t + 1];
-      yv0.x = fma(a0.x, pv0.x, fma(-a0.y, pv0.y, yv0.x));
-      yv0.y = fma(a0.x, pv0.y, fma(a0.y, pv0.x, yv0.y));
-      yv1.x = fma(a1.x, pv1.x, fma(-a1.y, pv1.y, yv1.x));
-      yv1.y = fma(a1.x, pv1.y, fma(a1.y, pv1.x, yv1.y));
-      double2 n0, n1;
-      n0.x = fma(b0.x, pv0.x, fma(-b0.y, pv0.y, re.x));
-      n0.y = fma(b0.x, pv0.y, fma(b0.y, pv0.x, re.y));
-      n1.x = fma(b1.x, pv1.x, fma(-b1.y, pv1.y, re.x));
-      n1.y = fma(b1.x, pv1.y, fma(b1.y, pv1.x, re.y));
-      *y0 = yv0;
-      *p0 = n0;
-      *y1 = yv1;
-      *p1 = n1;
+      const Coef4 c0 = s_ab[t], c1 = s_ab[t + 1];
+      const double a0y = s_ay[t], b0y = s_by[t], a1y = s_ay[t + 1], b1y = s_by[t + 1];
+      double2* y0 = yl + (long long)s_j[t] * n;
+      double2* h0 = hl + (long long)s_j[t] * n;
+      double2* y1 = yl + (long long)s_j[t + 1] * n;
+      double2* h1 = hl + (long long)s_j[t + 1] * n;
+      double2 yv0[EPT], hv0[EPT], yv1[EPT], hv1[EPT];
+#pragma unroll
+      for (int i = 0; i < EPT; ++i) {
+        const long long e = base + (long long)i * kUpdBlock;
+        if (e < n) {
+          yv0[i] = y0[e];
+          hv0[i] = h0[e];
+          yv1[i] = y1[e];
+          hv1[i] = h1[e];
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < EPT; ++i) {
+        const long long e = base + (long long)i * kUpdBlock;
+        if (e < n) {
+          double2 a, b;
+          a.x = fma(c0.x, hv0[i].x, fma(c0.y, hv0[i].y, yv0[i].x));
+          a.y = fma(c0.x, hv0[i].y, fma(a0y, hv0[i].x, yv0[i].y));
+          b.x = fma(c0.z, hv0[i].x, fma(c0.w, hv0[i].y, rv[i].x));
+          b.y = fma(c0.z, hv0[i].y, fma(b0y, hv0[i].x, rv[i].y));
+          y0[e] = a;
+          h0[e] = b;
+          a.x = fma(c1.x, hv1[i].x, fma(c1.y, hv1[i].y, yv1[i].x));
+          a.y = fma(c1.x, hv1[i].y, fma(a1y, hv1[i].x, yv1[i].y));
+          b.x = fma(c1.z, hv1[i].x, fma(c1.w, hv1[i].y, rv[i].x));
+          b.y = fma(c1.z, hv1[i].y, fma(b1y, hv1[i].x, rv[i].y));
+          y1[e] = a;
+          h1[e] = b;
+        }
+      }
     }
     if (t < m) {
-      double2* y0 = y + ((long long)l * N + s_j[t]) * n + e;
-      double2* p0 = ph + ((long long)l * N + s_j[t]) * n + e;
-      double2 yv0 = *y0, pv0 = *p0;
-      const double2 a0 = s_a[t], b0 = s_b[t];
-      yv0.x = fma(a0.x, pv0.x, fma(-a0.y, pv0.y, yv0.x));
-      yv0.y = fma(a0.x, pv0.y, fma(a0.y, pv0.x, yv0.y));
-      double2 n0;
-      n0.x = fma(b0.x, pv0.x, fma(-b0.y, pv0.y, re.x));
-      n0.y = fma(b0.x, pv0.y, fma(b0.y, pv0.x, re.y));
-      *y0 = yv0;
-      *p0 = n0;
+      const Coef4 c0 = s_ab[t];
+      const double a0y = s_ay[t], b0y = s_by[t];
+      double2* y0 = yl + (long long)s_j[t] * n;
+      double2* h0 = hl + (long long)s_j[t] * n;
+#pragma unroll
+      for (int i = 0; i < EPT; ++i) {
+        const long long e = base + (long long)i * kUpdBlock;
+        if (e < n) {
+          const double2 yv = y0[e], hv = h0[e];
+          double2 a, b;
+          a.x = fma(c0.x, hv.x, fma(c0.y, hv.y, yv.x));
+          a.y = fma(c0.x, hv.y, fma(a0y, hv.x, yv.y));
+          b.x = fma(c0.z, hv.x, fma(c0.w, hv.y, rv[i].x));
+          b.y = fma(c0.z, hv.y, fma(b0y, hv.x, rv[i].y));
+          y0[e] = a;
+          h0[e] = b;
+        }
+      }
     }
-    if (seed_continues) {
-      double2 pv = pl[e];
-      pv.x = fma(beta, pv.x, re.x);
-      pv.y = fma(beta, pv.y, re.y);
-      pl[e] = pv;
+    if (cont) {
+#pragma unroll
+      for (int i = 0; i < EPT; ++i) {
+        const long long e = base + (long long)i * kUpdBlock;
+        if (e < n) {
+          double2 pe = pl[e];
+          pe.x = fma(beta, pe.x, rv[i].x);
+          pe.y = fma(beta, pe.y, rv[i].y);
+          pl[e] = pe;
+        }
+      }
     }
   }
 }
 
-int update_blocks(long long n, int L) {
-  long long b = (n + kUpdBlock - 1) / kUpdBlock;
-  const long long cap = (152LL * 8 + L - 1) / L;
+int seed_blocks(long long n, int L) {
+  long long b = (n + 4 * kSeedBlock - 1) / (4 * kSeedBlock);  // >= 4 elements per thread
+  const long long cap = (152LL * 2 + L - 1) / L;
   if (b > cap) b = cap;
   return (int)(b < 1 ? 1 : b);
+}
+
+int update_epts() {
+  static int v = [] {
+    const char* e = std::getenv("SSQCD_UPDATE_EPT");
+    const int x = e ? std::atoi(e) : 1;
+    return (x == 1 || x == 2 || x == 4) ? x : 1;
+  }();
+  return v;
+}
+
+int launch_update(int ept, dim3 grid, cudaStream_t st, const Control& c, int N, double2* r, double2* p,
+                  double2* y, double2* ph, long long n) {
+  switch (ept) {
+    case 1: cg_update_kernel<1><<<grid, kUpdBlock, 0, st>>>(c, N, r, p, y, ph, n); break;
+    case 2: cg_update_kernel<2><<<grid, kUpdBlock, 0, st>>>(c, N, r, p, y, ph, n); break;
+    default: cg_update_kernel<4><<<grid, kUpdBlock, 0, st>>>(c, N, r, p, y, ph, n); break;
+  }
+  return SSQCD_OK;
+}
+
+int update_blocks(long long n, int L, int ept) {
+  const long long chunks = (n + (long long)kUpdBlock * ept - 1) / ((long long)kUpdBlock * ept);
+  const long long cap = (152LL * 8 + L - 1) / L;
+  return (int)std::max(1LL, std::min(chunks, cap));
 }
 
 }  // namespace
@@ -415,13 +567,16 @@ int shifted_cg_device(ssqcd_lattice lat, int N, const double2* z_host, int L, co
   (void)reliable_every;
   if (precision != SSQCD_FP64) return fail(SSQCD_ERR_ARG, "shifted_cg_device: only SSQCD_FP64 here");
   if (N < 1 || N > kMaxShifts) return fail(SSQCD_ERR_ARG, "N must be in [1, 256]");
-  if (L < 1 || L > kMaxSources) return fail(SSQCD_ERR_ARG, "L must be in [1, 64]");
+  if (L < 1 || L > kMaxSources || N * L > kMaxShifts)
+    return fail(SSQCD_ERR_ARG, "L must be in [1, 64] and N * L <= 256");
   cudaStream_t st = lat->stream;
   const Geometry& g = lat->g;
   const long long n = 12LL * g.V;
   const int NL = N * L;
   const int nbw = wilson_blocks(g);
-  const int nbu = update_blocks(n, L);
+  const int nbs = seed_blocks(n, L);
+  const int ept = update_epts();
+  const int nbu = update_blocks(n, L, ept);
 
   DevBuf r, p, q, ph;
   SS_TRY(r.alloc(sizeof(double2) * n * L));
@@ -436,29 +591,39 @@ int shifted_cg_device(ssqcd_lattice lat, int N, const double2* z_host, int L, co
     off += (bytes + 255) / 256 * 256;
     return o;
   };
-  const size_t o_seed = take(sizeof(SeedIter) * 2 * L), o_vn = take(sizeof(double) * L),
-               o_live = take(sizeof(int) * 2 * L), o_tot = take(sizeof(int) * 2), o_ran = take(sizeof(int) * 2),
-               o_err = take(sizeof(int)), o_si = take(sizeof(int)), o_done = take(sizeof(unsigned) * 2),
-               o_s = take(sizeof(double2) * NL), o_xi = take(sizeof(double2) * 3 * NL),
-               o_act = take(sizeof(int) * 2 * NL), o_it = take(sizeof(int) * NL),
-               o_part = take(sizeof(double) * (size_t)nbw * L), o_prr = take(sizeof(double) * (size_t)nbu * L),
-               o_vp = take(sizeof(double) * (size_t)nbu * L),
-               o_vn2 = take(sizeof(double) * L);
+  const size_t o_seed = take(sizeof(SeedState) * L), o_alpha = take(sizeof(double) * L),
+               o_vn = take(sizeof(double) * L), o_live = take(sizeof(int) * L), o_tot = take(sizeof(int)),
+               o_ran = take(sizeof(int)), o_err = take(sizeof(int)), o_si = take(sizeof(int)),
+               o_done = take(sizeof(unsigned) * 2), o_s = take(sizeof(double2) * NL),
+               o_xc = take(sizeof(double2) * NL), o_xp = take(sizeof(double2) * NL),
+               o_xn = take(sizeof(double2) * NL), o_rt = take(sizeof(double2) * NL), o_act = take(sizeof(int) * NL),
+               o_it = take(sizeof(int) * NL), o_ln = take(sizeof(int) * L), o_lj = take(sizeof(int) * NL),
+               o_la = take(sizeof(double2) * NL), o_lb = take(sizeof(double2) * NL),
+               o_part = take(sizeof(double) * (size_t)nbw * L), o_prr = take(sizeof(double) * (size_t)nbs * L),
+               o_vp = take(sizeof(double) * (size_t)nbs * L), o_vn2 = take(sizeof(double) * L);
   SS_TRY(ctl.alloc(off));
   char* base = ctl.as<char>();
   Control c;
-  c.seed = reinterpret_cast<SeedIter*>(base + o_seed);
+  c.seed = reinterpret_cast<SeedState*>(base + o_seed);
+  c.alpha = reinterpret_cast<double*>(base + o_alpha);
   c.vnorm2 = reinterpret_cast<double*>(base + o_vn);
-  c.src_live = reinterpret_cast<int*>(base + o_live);
+  c.live = reinterpret_cast<int*>(base + o_live);
   c.live_total = reinterpret_cast<int*>(base + o_tot);
   c.ran = reinterpret_cast<int*>(base + o_ran);
   c.err = reinterpret_cast<int*>(base + o_err);
   c.seed_iters = reinterpret_cast<int*>(base + o_si);
   c.done = reinterpret_cast<unsigned*>(base + o_done);
   c.shift_s = reinterpret_cast<double2*>(base + o_s);
-  c.xi = reinterpret_cast<double2*>(base + o_xi);
+  c.xi_cur = reinterpret_cast<double2*>(base + o_xc);
+  c.xi_prev = reinterpret_cast<double2*>(base + o_xp);
+  c.xi_next = reinterpret_cast<double2*>(base + o_xn);
+  c.ratio = reinterpret_cast<double2*>(base + o_rt);
   c.act = reinterpret_cast<int*>(base + o_act);
   c.iters = reinterpret_cast<int*>(base + o_it);
+  c.list_n = reinterpret_cast<int*>(base + o_ln);
+  c.list_j = reinterpret_cast<int*>(base + o_lj);
+  c.list_a = reinterpret_cast<double2*>(base + o_la);
+  c.list_b = reinterpret_cast<double2*>(base + o_lb);
   c.partial = reinterpret_cast<double*>(base + o_part);
   c.partial_rr = reinterpret_cast<double*>(base + o_prr);
   double* vn_part = reinterpret_cast<double*>(base + o_vp);
@@ -469,8 +634,8 @@ int shifted_cg_device(ssqcd_lattice lat, int N, const double2* z_host, int L, co
     for (int j = 0; j < N; ++j) sh[l * N + j] = make_double2(z_host[j].x - sigma, z_host[j].y);
   SS_CUDA(cudaMemcpyAsync(c.shift_s, sh.data(), sizeof(double2) * NL, cudaMemcpyHostToDevice, st));
 
-  SS_TRY(norm2_partials(v, L, n, vn_part, nbu, st));
-  SS_TRY(sum_partials(vn_part, L, nbu, vn2, st));
+  SS_TRY(norm2_partials(v, L, n, vn_part, nbs, st));
+  SS_TRY(sum_partials(vn_part, L, nbs, vn2, st));
   init_vectors_kernel<<<dim3(nbu, L), kUpdBlock, 0, st>>>(v, r.as<double2>(), p.as<double2>(), y.as<double2>(),
                                                             ph.as<double2>(), N, n);
   SS_CHECK_LAUNCH();
@@ -497,33 +662,60 @@ int shifted_cg_device(ssqcd_lattice lat, int N, const double2* z_host, int L, co
     for (auto& e : tev) SS_CUDA(cudaEventCreate(&e));
   }
   auto mark = [&](int it, int slot) {
-    if (timing) cudaEventRecord(tev[it * 6 + slot], st);
+    // during capture, only the External flag makes a real event-record node
+    if (timing) cudaEventRecordWithFlags(tev[it * 6 + slot], st, cudaEventRecordExternal);
   };
-  const dim3 grid_a(nbw, L), grid_b(nbu, L);
+  const dim3 grid_a(nbw, L), grid_b(nbs, L), grid_c(nbu, L);
+  auto iteration = [&](int it) {
+    mark(it, 0);
+    cg_stencil_kernel<<<grid_a, kStencilThreads, 0, st>>>(c, L, g, lat->u64.as<double2>(), sigma, p.as<double2>(),
+                                                           q.as<double2>());
+    mark(it, 1);
+    mark(it, 2);
+    cg_seed_kernel<<<grid_b, kSeedBlock, 0, st>>>(c, L, N, tol2, r.as<double2>(), q.as<double2>(), n);
+    mark(it, 3);
+    mark(it, 4);
+    launch_update(ept, grid_c, st, c, N, r.as<double2>(), p.as<double2>(), y.as<double2>(), ph.as<double2>(), n);
+    mark(it, 5);
+  };
+  // A chunk of iterations is captured once as a CUDA graph and replayed (the
+  // kernels read all per-iteration state from device memory, so every replay
+  // is the same graph).  With kernel timing on, the graph also records an
+  // event around every kernel; they are read after each replay.  A stream
+  // that cannot be captured (the legacy default stream) falls back to direct
+  // launches.
+  cudaGraphExec_t gexec = nullptr;
+  {
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+      for (int it = 0; it < kChunk; ++it) iteration(it);
+      if (cudaStreamEndCapture(st, &graph) == cudaSuccess && graph != nullptr) {
+        if (cudaGraphInstantiate(&gexec, graph, 0) != cudaSuccess) gexec = nullptr;
+        cudaGraphDestroy(graph);
+      }
+    }
+    (void)cudaGetLastError();  // a failed capture falls back to direct launches
+  }
   while (true) {
     const int chunk = std::min(kChunk, max_iter - k);
     int launched = 0;
-    for (int it = 0; it < chunk; ++it, ++k) {
-      const int P = k & 1;
-      mark(it, 0);
-      cg_stencil_kernel<<<grid_a, kStencilThreads, 0, st>>>(c, P, L, g, lat->u64.as<double2>(), sigma,
-                                                             p.as<double2>(), q.as<double2>());
-      mark(it, 1);
-      mark(it, 2);
-      cg_seed_kernel<<<grid_b, kUpdBlock, 0, st>>>(c, P, L, r.as<double2>(), q.as<double2>(), n);
-      mark(it, 3);
-      mark(it, 4);
-      cg_update_kernel<<<grid_b, kUpdBlock, 0, st>>>(c, k, L, N, tol2, r.as<double2>(), p.as<double2>(),
-                                                     y.as<double2>(), ph.as<double2>(), n);
-      mark(it, 5);
-      count_launches(3);
-      ++launched;
+    if (gexec != nullptr && chunk == kChunk) {
+      cudaError_t ge = cudaGraphLaunch(gexec, st);
+      if (ge != cudaSuccess) { status = cuda_fail(ge, "shifted CG graph launch", __FILE__, __LINE__); break; }
+      k += kChunk;
+      launched = kChunk;
+      count_launches(3LL * kChunk);
+    } else {
+      for (int it = 0; it < chunk; ++it, ++k) {
+        iteration(it);
+        count_launches(3);
+        ++launched;
+      }
       cudaError_t le = cudaGetLastError();
       if (le != cudaSuccess) { status = cuda_fail(le, "shifted CG launch", __FILE__, __LINE__); break; }
     }
-    if (status != SSQCD_OK) break;
-    // live-shift count at the start of the next iteration, and the error flag
-    cudaError_t ce = cudaMemcpyAsync(h_poll, c.live_total + (k & 1), sizeof(int), cudaMemcpyDeviceToHost, st);
+    // live-shift count after the last iteration, and the error flag
+    cudaError_t ce = cudaMemcpyAsync(h_poll, c.live_total, sizeof(int), cudaMemcpyDeviceToHost, st);
     if (ce == cudaSuccess) ce = cudaMemcpyAsync(h_poll + 1, c.err, sizeof(int), cudaMemcpyDeviceToHost, st);
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
     if (ce != cudaSuccess) { status = cuda_fail(ce, "shifted CG poll", __FILE__, __LINE__); break; }
@@ -544,18 +736,16 @@ int shifted_cg_device(ssqcd_lattice lat, int N, const double2* z_host, int L, co
       break;
     }
   }
+  if (gexec != nullptr) cudaGraphExecDestroy(gexec);
   if (status == SSQCD_OK || status == SSQCD_ERR_BREAKDOWN || status == SSQCD_ERR_NOCONV) {
     SS_CUDA(cudaEventRecord(e1, st));
     int seed_iters = 0;
     std::vector<int> it_all(NL);
-    std::vector<double2> xi_all(3 * (size_t)NL);
     SS_CUDA(cudaMemcpyAsync(&seed_iters, c.seed_iters, sizeof(int), cudaMemcpyDeviceToHost, st));
     SS_CUDA(cudaMemcpyAsync(it_all.data(), c.iters, sizeof(int) * NL, cudaMemcpyDeviceToHost, st));
-    if (xi_host) SS_CUDA(cudaMemcpyAsync(xi_all.data(), c.xi, sizeof(double2) * 3 * NL, cudaMemcpyDeviceToHost, st));
+    if (xi_host) SS_CUDA(cudaMemcpyAsync(xi_host, c.xi_cur, sizeof(double2) * NL, cudaMemcpyDeviceToHost, st));
     SS_CUDA(cudaStreamSynchronize(st));
     if (iters_host) std::copy(it_all.begin(), it_all.end(), iters_host);
-    if (xi_host)  // a shift's last xi sits in slot (its iteration count) mod 3
-      for (int qi = 0; qi < NL; ++qi) xi_host[qi] = xi_all[(size_t)(it_all[qi] % 3) * NL + qi];
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
     if (out) {
@@ -566,7 +756,7 @@ int shifted_cg_device(ssqcd_lattice lat, int N, const double2* z_host, int L, co
       out->timed = timing;
       out->launches_update = timing ? std::min<int>(seed_iters, (int)t_iter[2].size()) : 0;
       for (int cls = 0; cls < 4; ++cls) out->ms_k[cls] = 0.0;
-      const int slot_of[3] = {0, 1, 3};  // stencil, seed update, shift update
+      const int slot_of[3] = {0, 1, 3};  // stencil, seed update + scalars, shift update
       for (int cls = 0; cls < 3; ++cls) {
         double acc = 0.0;
         // iterations after the last live one skip their work: not counted

@@ -21,17 +21,18 @@ def _problem(dims, kind, kappa, bc, L, seed):
     return U, v
 
 
-@pytest.mark.parametrize("dims,kind,kappa,N,L,beta", [
-    ((2, 2, 2, 2), "haar", 0.13, 8, 1, 0.3),
-    ((4, 4, 4, 4), "haar", 0.13, 16, 2, 0.3),
-    ((3, 2, 4, 6), "smooth", 0.125, 12, 3, 0.5),
+@pytest.mark.parametrize("dims,kind,kappa,N,L,beta,side_stream", [
+    ((2, 2, 2, 2), "haar", 0.13, 8, 1, 0.3, False),
+    ((4, 4, 4, 4), "haar", 0.13, 16, 2, 0.3, True),     # CUDA-graph replay of the loop
+    ((3, 2, 4, 6), "smooth", 0.125, 12, 3, 0.5, False),  # direct launches (legacy stream)
 ])
-def test_shifted_cg_matches_oracle(ss, dims, kind, kappa, N, L, beta):
+def test_shifted_cg_matches_oracle(ss, dims, kind, kappa, N, L, beta, side_stream):
+    import torch
     bc = -1
     U, v = _problem(dims, kind, kappa, bc, L, seed=7)
     gamma, rho = 0.38, 0.02
     z = contour.line_nodes(gamma, rho, beta, N)
-    lat = ss.create_lattice(dims, kappa, bc)
+    lat = ss.create_lattice(dims, kappa, bc, stream=torch.cuda.Stream() if side_stream else None)
     ss.upload_gauge(lat, U)
     code, y, iters, xi, seed_iters = ss.shifted_cg(lat, z, v, tol=1e-12)
     assert code == ss.OK

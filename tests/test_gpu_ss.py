@@ -37,7 +37,7 @@ def test_config1_against_oracle_and_dense(ss):
     lat = ss.create_lattice(c["dims"], c["kappa"], c["bc"])
     ss.upload_gauge(lat, U)
     res = ss.ss_solve(lat, c["interval"], c["N"], c["M"], src, beta=c["beta"], nprime=c["nprime"])
-    assert res.status == ss.OK
+    assert res.status == ss.OK, res.error
     ev, vec, rs, st = ss.ss_eigpairs(res)
     ref = oss.ss_solve(U, c["dims"], c["kappa"], c["bc"], c["interval"], c["N"], c["M"], src,
                        beta=c["beta"], Nprime=c["nprime"])
