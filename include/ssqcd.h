@@ -47,8 +47,10 @@ extern "C" {
 
 /* ---- precision of the solve loop ------------------------------------------ */
 #define SSQCD_FP64  0  /* everything in FP64 ("plain")                          */
-#define SSQCD_MIXED 1  /* FP32 stencil + shift updates, FP16 links, FP64 reliable
-                          updates, FP64 moments and Rayleigh-Ritz              */
+#define SSQCD_MIXED 1  /* FP32 stencil + shift updates with FP16 12-parameter
+                          links, FP64 reliable updates of the seed residual,
+                          FP64 moments and Rayleigh-Ritz                       */
+#define SSQCD_MIXED_F32LINKS 2  /* as SSQCD_MIXED with FP32 12-parameter links */
 
 /* ---- contour shapes --------------------------------------------------------- */
 #define SSQCD_PATH_LINES  0  /* L+-: z = gamma + rho (x +- i beta), Section 3      */
@@ -70,7 +72,10 @@ typedef struct {
                              rank_tol * largest; 1e-14                           */
   const double* sources;  /* host or device: [L][V][4][3] complex128, required  */
   int    sources_on_device;
-  int    reliable_every;  /* SSQCD_MIXED: FP64 seed-residual refresh period; 50   */
+  int    reliable_every;  /* mixed precisions: period (iterations) of the FP64
+                             reliable update of the seed residual; 0 (default)
+                             disables it -- measured to degrade the shifted
+                             solutions once ||r|| nears the operator error      */
 } ssqcd_opts;
 
 /* Counters of one solve.  Times are device milliseconds between CUDA events. */
@@ -122,9 +127,10 @@ int ssqcd_upload_gauge(ssqcd_lattice lat, const double* links, int on_device);
 int ssqcd_apply_H(ssqcd_lattice lat, const double* in, double* out, int nrhs, int on_device);
 
 /* Same as ssqcd_apply_H with the mixed path's operator: links stored FP16
- * with 12-parameter SU(3) reconstruction, spinors and arithmetic in FP32.
- * Input and output stay complex128 at the boundary.  Requires a lattice
- * created with SSQCD_MIXED. */
+ * (SSQCD_MIXED) or FP32 (SSQCD_MIXED_F32LINKS) as their first two rows, the
+ * third rebuilt as conj(row0 x row1) (exact for SU(3)); spinors and
+ * arithmetic in FP32.  Input and output stay complex128 at the boundary.
+ * Requires a lattice created with one of the two mixed precisions. */
 int ssqcd_apply_H_mixed(ssqcd_lattice lat, const double* in, double* out, int nrhs, int on_device);
 
 void ssqcd_lattice_destroy(ssqcd_lattice lat);

@@ -212,7 +212,7 @@ def contour(path, gamma, rho, beta, N):
     return z, w
 
 
-def shifted_cg(lat: Lattice, z, v, sigma=0.0, tol=1e-12, max_iter=100000, precision=FP64, reliable_every=50,
+def shifted_cg(lat: Lattice, z, v, sigma=0.0, tol=1e-12, max_iter=100000, precision=FP64, reliable_every=0,
                want_y=True):
     """Solve (z_j I - A) y = v_l for all shifts z (N,) and sources v (L, V, 4, 3).
 
@@ -280,7 +280,7 @@ def moments_noalloc(w, zeta, y, M, stream=None):
 
 
 def ss_solve(lat: Lattice, interval, N, M, sources, beta=0.3, nprime=0, tol=1e-12, sigma=0.0, max_iter=100000,
-             rank_tol=1e-14, path=PATH_LINES, reliable_every=50) -> Result:
+             rank_tol=1e-14, path=PATH_LINES, reliable_every=0) -> Result:
     """Run the solver; returns a Result (check ``status``)."""
     L = int(np.prod(sources.shape)) // lat.n
     o = Opts()

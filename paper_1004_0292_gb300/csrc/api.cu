@@ -70,7 +70,7 @@ extern "C" int ssqcd_create_lattice(const int dims[4], double kappa, int bc_t, i
   }
   if (V > (1LL << 27)) return fail(SSQCD_ERR_ARG, "lattice volume above 2^27 sites");
   if (bc_t != 1 && bc_t != -1) return fail(SSQCD_ERR_ARG, "bc_t must be +1 or -1");
-  if (precision != SSQCD_FP64 && precision != SSQCD_MIXED) return fail(SSQCD_ERR_ARG, "unknown precision");
+  if (precision != SSQCD_FP64 && !is_mixed(precision)) return fail(SSQCD_ERR_ARG, "unknown precision");
   if (!std::isfinite(kappa)) return fail(SSQCD_ERR_ARG, "kappa must be finite");
   int dev = 0;
   SS_CUDA(cudaGetDevice(&dev));
@@ -105,6 +105,9 @@ extern "C" int ssqcd_upload_gauge(ssqcd_lattice lat, const double* links, int on
   if (lat->precision == SSQCD_MIXED) {
     SS_TRY(lat->u16.alloc(sizeof(uint2) * 12 * (size_t)V));
     SS_TRY(pack_gauge16(lat->u64.as<double2>(), lat->u16.p, V, lat->stream));
+  } else if (lat->precision == SSQCD_MIXED_F32LINKS) {
+    SS_TRY(lat->u32.alloc(sizeof(float4) * 12 * (size_t)V));
+    SS_TRY(pack_gauge32(lat->u64.as<double2>(), lat->u32.p, V, lat->stream));
   }
   SS_CUDA(cudaStreamSynchronize(lat->stream));
   lat->has_gauge = true;
@@ -127,7 +130,7 @@ extern "C" int ssqcd_apply_H(ssqcd_lattice lat, const double* in, double* out, i
 
 extern "C" int ssqcd_apply_H_mixed(ssqcd_lattice lat, const double* in, double* out, int nrhs, int on_device) {
   SS_TRY(check_lattice(lat, true));
-  if (lat->precision != SSQCD_MIXED) return fail(SSQCD_ERR_ARG, "apply_H_mixed needs a SSQCD_MIXED lattice");
+  if (!is_mixed(lat->precision)) return fail(SSQCD_ERR_ARG, "apply_H_mixed needs a mixed-precision lattice");
   if (nrhs < 0 || (nrhs > 0 && (in == nullptr || out == nullptr))) return fail(SSQCD_ERR_ARG, "bad apply_H arguments");
   if (nrhs == 0) return SSQCD_OK;
   const long long n = 12LL * lat->g.V * nrhs;
@@ -136,8 +139,9 @@ extern "C" int ssqcd_apply_H_mixed(ssqcd_lattice lat, const double* in, double* 
   SS_TRY(a32.alloc(sizeof(float2) * n));
   SS_TRY(b32.alloc(sizeof(float2) * n));
   SS_TRY(convert_f64_to_f32(a.as<double2>(), a32.as<float2>(), n, lat->stream));
-  SS_TRY(wilson32(lat->g, lat->u16.p, a32.as<float2>(), b32.as<float2>(), nrhs, 0.f, 1.f, nullptr, nullptr,
-                  lat->stream));
+  const bool f16 = lat->precision == SSQCD_MIXED;
+  SS_TRY(wilson32(lat->g, f16 ? lat->u16.p : lat->u32.p, f16 ? 16 : 32, a32.as<float2>(), b32.as<float2>(), nrhs,
+                  0.f, 1.f, nullptr, nullptr, lat->stream));
   SS_TRY(convert_f32_to_f64(b32.as<float2>(), a.as<double2>(), n, lat->stream));
   SS_TRY(from_device_layout(lat, a.as<double2>(), nrhs, on_device, out));
   SS_CUDA(cudaStreamSynchronize(lat->stream));
@@ -151,8 +155,8 @@ extern "C" int ssqcd_shifted_cg(ssqcd_lattice lat, int N, const double* z, int L
   if (z == nullptr || v == nullptr) return fail(SSQCD_ERR_ARG, "NULL z or v");
   if (N < 1 || L < 1 || !(tol > 0.0) || max_iter < 1 || !std::isfinite(sigma))
     return fail(SSQCD_ERR_ARG, "bad shifted_cg arguments");
-  if (precision == SSQCD_MIXED && lat->precision != SSQCD_MIXED)
-    return fail(SSQCD_ERR_ARG, "mixed precision needs a SSQCD_MIXED lattice");
+  if (is_mixed(precision) && precision != lat->precision)
+    return fail(SSQCD_ERR_ARG, "a mixed-precision solve needs a lattice created with that precision");
   DevBuf vd, yd;
   SS_TRY(to_device_layout(lat, v, L, on_device, vd));
   std::vector<int> it(iters ? (size_t)L * N : 0);
@@ -228,7 +232,7 @@ extern "C" void ssqcd_default_opts(ssqcd_opts* o) {
   o->sigma = 0.0;
   o->max_iter = 100000;
   o->rank_tol = 1e-14;
-  o->reliable_every = 50;
+  o->reliable_every = 0;
 }
 
 namespace {

@@ -5,8 +5,8 @@
 //   block of L      : [L][12][V];
 //   FP64 gauge      : [4][9][V] double2, element (a,b) of U_mu(s) at
 //                     (mu*9 + 3a + b)*V + s;
-//   FP16 gauge      : [4][6][V] __half2 x2 (first two rows, 12 reals) --
-//                     see wilson.cu.
+//   FP16 gauge      : [4][3][V] uint2 (rows 0 and 1 as six half2);
+//   FP32 gauge      : [4][3][V] float4 (rows 0 and 1 as six float2).
 // A warp of consecutive sites then reads 32 consecutive complex numbers for
 // every component, for the site itself and for each of its 8 neighbours
 // (neighbours of consecutive sites are consecutive except at wraps).
@@ -77,7 +77,8 @@ struct ssqcd_lattice_s {
   cudaStream_t stream;
   bool has_gauge = false;
   ssqcd::DevBuf u64;     // FP64 links [4][9][V] double2
-  ssqcd::DevBuf u16;     // FP16 links, mixed precision only
+  ssqcd::DevBuf u16;     // FP16 12-parameter links, SSQCD_MIXED only
+  ssqcd::DevBuf u32;     // FP32 12-parameter links, SSQCD_MIXED_F32LINKS only
   ssqcd::DevBuf stage;   // staging for host <-> device copies
 };
 
@@ -100,9 +101,11 @@ int pack_gauge64(const double2* user, double2* dev, int V, cudaStream_t s);
 int wilson_blocks(const Geometry& g);
 int wilson64(const Geometry& g, const double2* u, const double2* in, double2* out, int nrhs,
              double c0, double c1, double* dot_partial, const int* skip_if_zero, cudaStream_t s);
-int wilson32(const Geometry& g, const void* u16, const float2* in, float2* out, int nrhs,
+// link_bits 16: FP16 12-parameter links [4][3][V] uint2; 32: FP32 [4][3][V] float4
+int wilson32(const Geometry& g, const void* links, int link_bits, const float2* in, float2* out, int nrhs,
              float c0, float c1, float* dot_partial, const int* skip_if_zero, cudaStream_t s);
 int pack_gauge16(const double2* u64dev, void* u16, int V, cudaStream_t s);
+int pack_gauge32(const double2* u64dev, void* u32, int V, cudaStream_t s);
 
 // reductions / dense block ops in FP64 (blas.cu)
 int norm2_partials(const double2* x, int nvec, long long n, double* partial, int nblocks, cudaStream_t s);
@@ -139,6 +142,7 @@ struct ShiftedCGOut {
   double ms_k[4] = {0, 0, 0, 0};  // stencil, seed update, scalars, shift update
 };
 bool kernel_timing_enabled();
+inline bool is_mixed(int precision) { return precision == SSQCD_MIXED || precision == SSQCD_MIXED_F32LINKS; }
 // Solves for L sources already packed on device (v: [L][12][V]); y out
 // [L][N][12][V] (device, FP64).  iters/xi: host arrays [L*N] (may be null).
 int shifted_cg_device(ssqcd_lattice lat, int N, const double2* z_host, int L, const double2* v,

@@ -59,7 +59,7 @@ struct SeedState {
   double beta_prev;   // beta_{k-1}
   double beta;        // beta_k (valid after kernel B of iteration k)
   double scale;       // power of two applied to r and p by kernel C of this iteration
-  double pad[3];      // pad[0] = 1 / rr
+  double pad[3];      // pad[0] = 1 / rr, pad[1] = S = product of all scales so far
 };
 
 // Device-side control block of one solve (L sources, N shifts).  Every field
@@ -74,7 +74,7 @@ struct Control {
   int* live_total;     // [1]
   int* ran;            // [1]     kernel A of this iteration did its work
   int* err;            // [1]
-  int* seed_iters;     // [1]
+  int* seed_iters;     // [2]     seed iterations, reliable updates applied
   unsigned* done;      // [2]     last-block tickets of kernels A and B
   double2* shift_s;    // [L*N]   s_j = z_j - sigma
   double2* xi_cur;     // [L*N]   xi_k
@@ -89,6 +89,7 @@ struct Control {
   double2* list_b;     // [L*N]   p-hat = r + b p-hat
   double* partial;     // [L][nbw]  (p, q) partials of kernel A
   double* partial_rr;  // [L][nbs]  ||r||^2 partials of kernel B
+  double2* x;          // [L][n]    FP64 seed solution (mixed precision only, else null)
 };
 
 constexpr int kUpdBlock = 256;
@@ -105,24 +106,26 @@ __device__ __forceinline__ double warp_sum(double v) {
 // The seed system usually converges far faster than the shifted ones (its
 // shift sigma lies in a gap of the spectrum while the quadrature points sit
 // close to eigenvalues), so ||r|| keeps shrinking -- 1e-100 and below --
-// while xi grows to compensate.  Before (r, r) leaves the FP64 range, r and
-// p are multiplied by an exact power of two s and every xi is divided by s;
-// y is unchanged and p-hat absorbs s through b (see kernels B and C).  This
-// also keeps |xi|^2 and the other products of the recurrences far inside
-// the FP64 range, so they need no overflow guards.
-constexpr double kRescaleBelow = 0x1p-400;  // of ||v||^2
-constexpr double kRescaleBy = 0x1p+200;
+// while xi grows to compensate.  Before (r, r) leaves the floating-point
+// range (FP64: below 2^-400 ||v||^2; FP32 vectors: below 2^-40), r and p are
+// multiplied by an exact power of two s and every xi is divided by s; y is
+// unchanged and p-hat absorbs s through b (see kernels B and C).  This also
+// keeps |xi|^2 and the other products of the recurrences far inside the FP64
+// range, so they need no overflow guards.
 
 // ---- initialisation ---------------------------------------------------------------
-__global__ void init_vectors_kernel(const double2* __restrict__ v, double2* __restrict__ r, double2* __restrict__ p,
-                                    double2* __restrict__ y, double2* __restrict__ ph, int N, long long n) {
+template <typename V2>
+__global__ void init_vectors_kernel(const double2* __restrict__ v, V2* __restrict__ r, V2* __restrict__ p,
+                                    V2* __restrict__ y, V2* __restrict__ ph, int N, long long n) {
+  using T = decltype(V2::x);
   const int l = blockIdx.y;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
-    const double2 x = v[l * n + e];
+    const double2 xd = v[l * n + e];
+    const V2 x{(T)xd.x, (T)xd.y};
     r[l * n + e] = x;
     p[l * n + e] = x;
     for (int j = 0; j < N; ++j) {
-      y[((long long)l * N + j) * n + e] = make_double2(0.0, 0.0);
+      y[((long long)l * N + j) * n + e] = V2{0, 0};
       ph[((long long)l * N + j) * n + e] = x;
     }
   }
@@ -132,7 +135,7 @@ __global__ void init_vectors_kernel(const double2* __restrict__ v, double2* __re
 __global__ void init_control_kernel(Control c, const double* __restrict__ vn2, int L, int N) {
   for (int t = threadIdx.x; t < L; t += blockDim.x) {
     // rr_0, alpha_{-1} = 1, beta_{-1} = 0, scale 1, 1 / rr_0
-    c.seed[t] = SeedState{vn2[t], 1.0, 0.0, 0.0, 1.0, {vn2[t] > 0.0 ? 1.0 / vn2[t] : 0.0, 0.0, 0.0}};
+    c.seed[t] = SeedState{vn2[t], 1.0, 0.0, 0.0, 1.0, {vn2[t] > 0.0 ? 1.0 / vn2[t] : 0.0, 1.0, 0.0}};
     c.alpha[t] = 0.0;
     c.vnorm2[t] = vn2[t];
     c.live[t] = vn2[t] > 0.0 ? N : 0;
@@ -150,15 +153,69 @@ __global__ void init_control_kernel(Control c, const double* __restrict__ vn2, i
     *c.live_total = live;
     *c.ran = 0;
     *c.err = 0;
-    *c.seed_iters = 0;
+    c.seed_iters[0] = c.seed_iters[1] = 0;
     c.done[0] = c.done[1] = 0u;
   }
 }
 
 // ---- A. stencil q = K p + (p, q) partials; last block: alpha_k ---------------------
+// Stencil of one block for one source: q = sigma p - gamma5 (p - kappa D p) at
+// spin w's three components of site s; returns this thread's share of (p, q).
+struct Stencil64 {
+  const double2* __restrict__ u;
+  __device__ __forceinline__ double run(const Geometry& g, const double2* __restrict__ p, double2* __restrict__ q,
+                                        double sigma, int s, int w, void* shm) const {
+    double2 acc[3];
+    block_hops64(Links64{u, g.V}, p, s, g, static_cast<double2*>(shm), acc);
+    double d = 0.0;
+    if (s < g.V) {
+      const double sg = w < 2 ? -1.0 : 1.0;
+      const double mk = -g.kappa;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const int i = 3 * w + k;
+        const double2 pv = p[i * g.V + s];
+        double2 o;
+        o.x = fma(sg, fma(mk, acc[k].x, pv.x), sigma * pv.x);
+        o.y = fma(sg, fma(mk, acc[k].y, pv.y), sigma * pv.y);
+        q[i * g.V + s] = o;
+        d = fma(pv.x, o.x, fma(pv.y, o.y, d));
+      }
+    }
+    return d;
+  }
+};
+
+template <typename LK>
+struct Stencil32 {
+  LK lk;
+  __device__ __forceinline__ double run(const Geometry& g, const float2* __restrict__ p, float2* __restrict__ q,
+                                        double sigma, int s, int w, void* shm) const {
+    float2 acc[3];
+    block_hops32(lk, p, s, g, static_cast<float2*>(shm), acc);
+    double d = 0.0;
+    if (s < g.V) {
+      const float sg = w < 2 ? -1.f : 1.f;
+      const float mk = -(float)g.kappa, sf = (float)sigma;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const int i = 3 * w + k;
+        const float2 pv = p[i * g.V + s];
+        float2 o;
+        o.x = fmaf(sg, fmaf(mk, acc[k].x, pv.x), sf * pv.x);
+        o.y = fmaf(sg, fmaf(mk, acc[k].y, pv.y), sf * pv.y);
+        q[i * g.V + s] = o;
+        d += (double)(pv.x * o.x + pv.y * o.y);
+      }
+    }
+    return d;
+  }
+};
+
+template <typename Op, typename V2>
 __global__ void __launch_bounds__(kStencilThreads)
-cg_stencil_kernel(Control c, int L, Geometry g, const double2* __restrict__ u, double sigma,
-                  const double2* __restrict__ p_all, double2* __restrict__ q_all) {
+cg_stencil_kernel(Control c, int L, Geometry g, Op op, double sigma, const V2* __restrict__ p_all,
+                  V2* __restrict__ q_all) {
   if (*c.err != 0 || *c.live_total == 0) {
     if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *c.ran = 0;
     return;
@@ -172,34 +229,15 @@ cg_stencil_kernel(Control c, int L, Geometry g, const double2* __restrict__ u, d
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   double d_pq = 0.0;
   if (c.live[l] != 0) {
-    const double2* p = p_all + (size_t)l * 12 * V;
-    double2* q = q_all + (size_t)l * 12 * V;
     const int s = blockIdx.x * kSitesPerBlock + lane;
-    double2 acc[3];
-    block_hops64(Links64{u, V}, p, s, g, sh, acc);
-    if (s < V) {
-      // q = sigma p - gamma5 (p - kappa D p); components 3w..3w+2 are spin w
-      const double sg = w < 2 ? -1.0 : 1.0;
-      const double mk = -g.kappa;
-#pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        const int i = 3 * w + k;
-        const double2 pv = p[i * V + s];
-        double2 o;
-        o.x = fma(sg, fma(mk, acc[k].x, pv.x), sigma * pv.x);
-        o.y = fma(sg, fma(mk, acc[k].y, pv.y), sigma * pv.y);
-        q[i * V + s] = o;
-        d_pq = fma(pv.x, o.x, fma(pv.y, o.y, d_pq));
-      }
-    }
+    d_pq = op.run(g, p_all + (size_t)l * 12 * V, q_all + (size_t)l * 12 * V, sigma, s, w, sh);
   }
   d_pq = warp_sum(d_pq);
   if (lane == 0) sred[w] = d_pq;
   __syncthreads();
   const int nbw = gridDim.x;
   if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int i = 0; i < kStencilThreads / 32; ++i) t += sred[i];
+    const double t = (sred[0] + sred[1]) + (sred[2] + sred[3]);
     c.partial[(size_t)l * nbw + blockIdx.x] = t;
     __threadfence();
     const unsigned ticket = atomicAdd(&c.done[0], 1u);
@@ -210,9 +248,14 @@ cg_stencil_kernel(Control c, int L, Geometry g, const double2* __restrict__ u, d
   __threadfence();
   // warp w sums the partials of sources w, w+4, ... in a fixed order
   for (int ls = w; ls < L; ls += kStencilThreads / 32) {
-    double a = 0.0;
-    for (int b = lane; b < nbw; b += 32) a += __ldcg(c.partial + (size_t)ls * nbw + b);
-    a = warp_sum(a);
+    double a0 = 0.0, a1 = 0.0;
+    int b = lane;
+    for (; b + 32 < nbw; b += 64) {
+      a0 += __ldcg(c.partial + (size_t)ls * nbw + b);
+      a1 += __ldcg(c.partial + (size_t)ls * nbw + b + 32);
+    }
+    if (b < nbw) a0 += __ldcg(c.partial + (size_t)ls * nbw + b);
+    const double a = warp_sum(a0 + a1);
     if (lane == 0) sums[ls] = a;
   }
   __syncthreads();
@@ -247,9 +290,10 @@ cg_stencil_kernel(Control c, int L, Geometry g, const double2* __restrict__ u, d
 //    b_j = s beta_k xi_{k+1}/xi_k and the freeze test |xi|^2 rr <= tol^2 ||v||^2
 //    (products only), and builds each source's ordered list of shifts with
 //    warp ballots.
+template <typename V2>
 __global__ void __launch_bounds__(kSeedBlock)
-cg_seed_kernel(Control c, int L, int N, double tol2, double2* __restrict__ r, const double2* __restrict__ q,
-               long long n) {
+cg_seed_kernel(Control c, int L, int N, double tol2, V2* __restrict__ r, const V2* __restrict__ q,
+               const V2* __restrict__ p, long long n, double rescale_below, double rescale_by) {
   if (*c.ran == 0) return;
   __shared__ double sred[kSeedBlock / 32];
   __shared__ double sums[kMaxSources];
@@ -291,30 +335,38 @@ cg_seed_kernel(Control c, int L, int N, double tol2, double2* __restrict__ r, co
   double acc0 = 0.0, acc1 = 0.0;
   if (c.live[l] != 0) {
     const double alpha = c.alpha[l];
-    double2* rl = r + (long long)l * n;
-    const double2* ql = q + (long long)l * n;
+    V2* rl = r + (long long)l * n;
+    const V2* ql = q + (long long)l * n;
+    // mixed precision: the FP64 seed solution x += alpha p / S (S: product of
+    // the rescales of r and p so far), for the reliable updates
+    double2* xl = c.x != nullptr ? c.x + (long long)l * n : nullptr;
+    const V2* pl = p + (long long)l * n;
+    const double ax = c.x != nullptr ? alpha / c.seed[l].pad[1] : 0.0;
+    using T = decltype(V2::x);
+    const T af = (T)alpha;
     const long long stride = (long long)gridDim.x * kSeedBlock;
+    auto one = [&](long long e, double& acc) {
+      V2 x0 = rl[e];
+      const V2 y0 = ql[e];
+      x0.x = fma(-af, y0.x, x0.x);
+      x0.y = fma(-af, y0.y, x0.y);
+      rl[e] = x0;
+      const double xr = x0.x, xi = x0.y;
+      acc = fma(xr, xr, fma(xi, xi, acc));
+      if (xl != nullptr) {
+        const V2 pv = pl[e];
+        double2 xv = xl[e];
+        xv.x = fma(ax, (double)pv.x, xv.x);
+        xv.y = fma(ax, (double)pv.y, xv.y);
+        xl[e] = xv;
+      }
+    };
     long long e = blockIdx.x * (long long)kSeedBlock + threadIdx.x;
     for (; e + stride < n; e += 2 * stride) {
-      double2 x0 = rl[e], x1 = rl[e + stride];
-      const double2 y0 = ql[e], y1 = ql[e + stride];
-      x0.x = fma(-alpha, y0.x, x0.x);
-      x0.y = fma(-alpha, y0.y, x0.y);
-      x1.x = fma(-alpha, y1.x, x1.x);
-      x1.y = fma(-alpha, y1.y, x1.y);
-      rl[e] = x0;
-      rl[e + stride] = x1;
-      acc0 = fma(x0.x, x0.x, fma(x0.y, x0.y, acc0));
-      acc1 = fma(x1.x, x1.x, fma(x1.y, x1.y, acc1));
+      one(e, acc0);
+      one(e + stride, acc1);
     }
-    if (e < n) {
-      double2 x0 = rl[e];
-      const double2 y0 = ql[e];
-      x0.x = fma(-alpha, y0.x, x0.x);
-      x0.y = fma(-alpha, y0.y, x0.y);
-      rl[e] = x0;
-      acc0 = fma(x0.x, x0.x, fma(x0.y, x0.y, acc0));
-    }
+    if (e < n) one(e, acc0);
   }
   double acc = warp_sum(acc0 + acc1);
   if (lane == 0) sred[w] = acc;
@@ -343,7 +395,7 @@ cg_seed_kernel(Control c, int L, int N, double tol2, double2* __restrict__ r, co
       sums[ls] = a;
       const SeedState sd = c.seed[ls];
       s_beta[ls] = a * sd.pad[0];  // pad[0] holds 1 / rr_k
-      s_scale[ls] = (c.live[ls] != 0 && a < kRescaleBelow * c.vnorm2[ls] && a > 0.0) ? kRescaleBy : 1.0;
+      s_scale[ls] = (c.live[ls] != 0 && a < rescale_below * c.vnorm2[ls] && a > 0.0) ? rescale_by : 1.0;
     }
   }
   __syncthreads();
@@ -354,7 +406,7 @@ cg_seed_kernel(Control c, int L, int N, double tol2, double2* __restrict__ r, co
     if (c.live[ls] != 0 && c.act[qi]) {
       const double alpha = c.alpha[ls];
       const double rr1 = sums[ls], beta = s_beta[ls];
-      const double sc = s_scale[ls], inv_sc = sc == 1.0 ? 1.0 : 1.0 / kRescaleBy;
+      const double sc = s_scale[ls], inv_sc = sc == 1.0 ? 1.0 : 1.0 / rescale_by;
       const double2 xn = __ldcg(c.xi_next + qi), ratio = __ldcg(c.ratio + qi), xc = c.xi_cur[qi];
       s_a[qi] = make_double2(alpha * xn.x, alpha * xn.y);
       s_b[qi] = make_double2(sc * beta * ratio.x, sc * beta * ratio.y);
@@ -390,7 +442,7 @@ cg_seed_kernel(Control c, int L, int N, double tol2, double2* __restrict__ r, co
       if (c.live[ls] != 0) {
         const double sc = s_scale[ls];
         const double rr = sums[ls] * sc * sc;
-        c.seed[ls] = SeedState{rr, c.alpha[ls], s_beta[ls], s_beta[ls], sc, {1.0 / rr, 0.0, 0.0}};
+        c.seed[ls] = SeedState{rr, c.alpha[ls], s_beta[ls], s_beta[ls], sc, {1.0 / rr, c.seed[ls].pad[1] * sc, 0.0}};
       }
       c.live[ls] = live;
     }
@@ -408,60 +460,62 @@ cg_seed_kernel(Control c, int L, int N, double tol2, double2* __restrict__ r, co
 // Thread per EPT elements (stride blockDim) of one source; the block stages
 // its source's list of shifts in shared memory and every thread walks it, two
 // shifts at a time, so each lane keeps 4 EPT loads in flight.  r is rescaled
-// in place when kernel B chose a scale; then p = r + beta p.
-// update coefficients with the imaginary parts negated once per block
-struct alignas(32) Coef4 {
-  double x, y, z, w;  // a.x, -a.y, b.x, -b.y
+// in place when kernel B chose a scale; then p = r + beta p.  V2 = double2
+// (FP64 path: bound by the FP64 pipe) or float2 (mixed path: bound by HBM).
+template <typename T>
+struct alignas(4 * sizeof(T)) Coef4 {
+  T x, y, z, w;  // a.x, -a.y, b.x, -b.y (imaginary parts negated once per block)
 };
 
-template <int EPT>
+template <typename V2, int EPT>
 __global__ void __launch_bounds__(kUpdBlock)
-cg_update_kernel(Control c, int N, double2* __restrict__ r, double2* __restrict__ p,
-                 double2* __restrict__ y, double2* __restrict__ ph, long long n) {
+cg_update_kernel(Control c, int N, V2* __restrict__ r, V2* __restrict__ p, V2* __restrict__ y,
+                 V2* __restrict__ ph, long long n) {
+  using T = decltype(V2::x);
   if (*c.ran == 0) return;
   const int l = blockIdx.y;
   const int m = c.list_n[l];
   const bool cont = c.live[l] != 0;
   if (m == 0 && !cont) return;
   __shared__ int s_j[kMaxShifts];
-  __shared__ Coef4 s_ab[kMaxShifts];
-  __shared__ double s_ay[kMaxShifts], s_by[kMaxShifts];
+  __shared__ Coef4<T> s_ab[kMaxShifts];
+  __shared__ T s_ay[kMaxShifts], s_by[kMaxShifts];
   for (int t = threadIdx.x; t < m; t += blockDim.x) {
     const double2 a = c.list_a[l * N + t], b = c.list_b[l * N + t];
     s_j[t] = c.list_j[l * N + t];
-    s_ab[t] = Coef4{a.x, -a.y, b.x, -b.y};
-    s_ay[t] = a.y;
-    s_by[t] = b.y;
+    s_ab[t] = Coef4<T>{(T)a.x, (T)-a.y, (T)b.x, (T)-b.y};
+    s_ay[t] = (T)a.y;
+    s_by[t] = (T)b.y;
   }
   __syncthreads();
-  const double sc = c.seed[l].scale;  // exact power of two, usually 1
-  const double beta = sc * c.seed[l].beta;
-  double2* rl = r + (long long)l * n;
-  double2* pl = p + (long long)l * n;
-  double2* yl = y + (long long)l * N * n;
-  double2* hl = ph + (long long)l * N * n;
+  const T sc = (T)c.seed[l].scale;  // exact power of two, usually 1
+  const T beta = (T)(c.seed[l].scale * c.seed[l].beta);
+  V2* rl = r + (long long)l * n;
+  V2* pl = p + (long long)l * n;
+  V2* yl = y + (long long)l * N * n;
+  V2* hl = ph + (long long)l * N * n;
   const long long chunk = (long long)kUpdBlock * EPT;
   for (long long base = blockIdx.x * chunk + threadIdx.x; base < n; base += (long long)gridDim.x * chunk) {
-    double2 rv[EPT];
+    V2 rv[EPT];
 #pragma unroll
     for (int i = 0; i < EPT; ++i) {
       const long long e = base + (long long)i * kUpdBlock;
-      double2 x = e < n ? rl[e] : make_double2(0.0, 0.0);
-      if (sc != 1.0) {
-        x = make_double2(sc * x.x, sc * x.y);
+      V2 x = e < n ? rl[e] : V2{0, 0};
+      if (sc != (T)1) {
+        x = V2{sc * x.x, sc * x.y};
         if (e < n) rl[e] = x;
       }
       rv[i] = x;
     }
     int t = 0;
     for (; t + 2 <= m; t += 2) {
-      const Coef4 c0 = s_ab[t], c1 = s_ab[t + 1];
-      const double a0y = s_ay[t], b0y = s_by[t], a1y = s_ay[t + 1], b1y = s_by[t + 1];
-      double2* y0 = yl + (long long)s_j[t] * n;
-      double2* h0 = hl + (long long)s_j[t] * n;
-      double2* y1 = yl + (long long)s_j[t + 1] * n;
-      double2* h1 = hl + (long long)s_j[t + 1] * n;
-      double2 yv0[EPT], hv0[EPT], yv1[EPT], hv1[EPT];
+      const Coef4<T> c0 = s_ab[t], c1 = s_ab[t + 1];
+      const T a0y = s_ay[t], b0y = s_by[t], a1y = s_ay[t + 1], b1y = s_by[t + 1];
+      V2* y0 = yl + (long long)s_j[t] * n;
+      V2* h0 = hl + (long long)s_j[t] * n;
+      V2* y1 = yl + (long long)s_j[t + 1] * n;
+      V2* h1 = hl + (long long)s_j[t + 1] * n;
+      V2 yv0[EPT], hv0[EPT], yv1[EPT], hv1[EPT];
 #pragma unroll
       for (int i = 0; i < EPT; ++i) {
         const long long e = base + (long long)i * kUpdBlock;
@@ -476,7 +530,7 @@ cg_update_kernel(Control c, int N, double2* __restrict__ r, double2* __restrict_
       for (int i = 0; i < EPT; ++i) {
         const long long e = base + (long long)i * kUpdBlock;
         if (e < n) {
-          double2 a, b;
+          V2 a, b;
           a.x = fma(c0.x, hv0[i].x, fma(c0.y, hv0[i].y, yv0[i].x));
           a.y = fma(c0.x, hv0[i].y, fma(a0y, hv0[i].x, yv0[i].y));
           b.x = fma(c0.z, hv0[i].x, fma(c0.w, hv0[i].y, rv[i].x));
@@ -493,16 +547,16 @@ cg_update_kernel(Control c, int N, double2* __restrict__ r, double2* __restrict_
       }
     }
     if (t < m) {
-      const Coef4 c0 = s_ab[t];
-      const double a0y = s_ay[t], b0y = s_by[t];
-      double2* y0 = yl + (long long)s_j[t] * n;
-      double2* h0 = hl + (long long)s_j[t] * n;
+      const Coef4<T> c0 = s_ab[t];
+      const T a0y = s_ay[t], b0y = s_by[t];
+      V2* y0 = yl + (long long)s_j[t] * n;
+      V2* h0 = hl + (long long)s_j[t] * n;
 #pragma unroll
       for (int i = 0; i < EPT; ++i) {
         const long long e = base + (long long)i * kUpdBlock;
         if (e < n) {
-          const double2 yv = y0[e], hv = h0[e];
-          double2 a, b;
+          const V2 yv = y0[e], hv = h0[e];
+          V2 a, b;
           a.x = fma(c0.x, hv.x, fma(c0.y, hv.y, yv.x));
           a.y = fma(c0.x, hv.y, fma(a0y, hv.x, yv.y));
           b.x = fma(c0.z, hv.x, fma(c0.w, hv.y, rv[i].x));
@@ -517,7 +571,7 @@ cg_update_kernel(Control c, int N, double2* __restrict__ r, double2* __restrict_
       for (int i = 0; i < EPT; ++i) {
         const long long e = base + (long long)i * kUpdBlock;
         if (e < n) {
-          double2 pe = pl[e];
+          V2 pe = pl[e];
           pe.x = fma(beta, pe.x, rv[i].x);
           pe.y = fma(beta, pe.y, rv[i].y);
           pl[e] = pe;
@@ -527,6 +581,70 @@ cg_update_kernel(Control c, int N, double2* __restrict__ r, double2* __restrict_
   }
 }
 
+// ---- reliable update (mixed precision) -------------------------------------------------
+// r = S (v - K x) from the FP64 seed solution x and kx = K x (FP64 stencil),
+// replacing the FP32 recursive residual while ||r|| is above sqrt(floor2)
+// ||v||.  Below that, the true residual of the FP64 operator is dominated by
+// the difference between it and the reduced-precision operator the
+// recursion uses (~3e-4 relative with FP16 links, ~1e-7 with FP32 links), and
+// replacing r would break the Krylov recurrence the shifted systems are
+// built on; the last block stores (r, r) and its reciprocal.
+template <typename V2>
+__global__ void __launch_bounds__(kSeedBlock)
+cg_reliable_kernel(Control c, int L, const double2* __restrict__ v, const double2* __restrict__ kx,
+                   V2* __restrict__ r, long long n, double floor2) {
+  __shared__ double sred[kSeedBlock / 32];
+  __shared__ bool s_last;
+  const int l = blockIdx.y;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const SeedState sd = c.seed[l];
+  const double S = sd.pad[1];
+  const bool apply = c.live[l] != 0 && sd.rr > floor2 * S * S * c.vnorm2[l];
+  double acc = 0.0;
+  if (apply) {
+    using T = decltype(V2::x);
+    const double2* vl = v + (long long)l * n;
+    const double2* kl = kx + (long long)l * n;
+    V2* rl = r + (long long)l * n;
+    for (long long e = blockIdx.x * (long long)kSeedBlock + threadIdx.x; e < n; e += (long long)gridDim.x * kSeedBlock) {
+      const double2 a = vl[e], b = kl[e];
+      const double tx = S * (a.x - b.x), ty = S * (a.y - b.y);
+      rl[e] = V2{(T)tx, (T)ty};
+      acc = fma(tx, tx, fma(ty, ty, acc));
+    }
+  }
+  acc = warp_sum(acc);
+  if (lane == 0) sred[w] = acc;
+  __syncthreads();
+  const int nb = gridDim.x;
+  if (threadIdx.x == 0) {
+    const double t = ((sred[0] + sred[1]) + (sred[2] + sred[3])) + ((sred[4] + sred[5]) + (sred[6] + sred[7]));
+    c.partial_rr[(size_t)l * nb + blockIdx.x] = t;
+    __threadfence();
+    const unsigned ticket = atomicAdd(&c.done[1], 1u);
+    s_last = ticket == gridDim.x * gridDim.y - 1;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  for (int ls = w; ls < L; ls += kSeedBlock / 32) {
+    const SeedState sl = c.seed[ls];
+    const bool ap = c.live[ls] != 0 && sl.rr > floor2 * sl.pad[1] * sl.pad[1] * c.vnorm2[ls];
+    double a = 0.0;
+    for (int b = lane; b < nb; b += 32) a += __ldcg(c.partial_rr + (size_t)ls * nb + b);
+    a = warp_sum(a);
+    if (lane == 0 && ap && a > 0.0) {
+      SeedState sn = sl;
+      sn.rr = a;
+      sn.pad[0] = 1.0 / a;
+      c.seed[ls] = sn;
+      atomicAdd(c.seed_iters + 1, 1);  // reliable-update counter
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) c.done[1] = 0u;
+}
+
 int seed_blocks(long long n, int L) {
   long long b = (n + 4 * kSeedBlock - 1) / (4 * kSeedBlock);  // >= 4 elements per thread
   const long long cap = (152LL * 2 + L - 1) / L;
@@ -534,21 +652,25 @@ int seed_blocks(long long n, int L) {
   return (int)(b < 1 ? 1 : b);
 }
 
-int update_epts() {
+// Elements per thread of the update kernel: 1 for the FP64 path (its FP64
+// pipe, not memory, is the limit; measured 1 > 2 > 4), 2 for FP32.  The
+// environment variable SSQCD_UPDATE_EPT overrides it for tuning runs.
+int update_epts(bool fp32) {
   static int v = [] {
     const char* e = std::getenv("SSQCD_UPDATE_EPT");
-    const int x = e ? std::atoi(e) : 1;
-    return (x == 1 || x == 2 || x == 4) ? x : 1;
+    const int x = e ? std::atoi(e) : 0;
+    return (x == 1 || x == 2 || x == 4) ? x : 0;
   }();
-  return v;
+  return v != 0 ? v : (fp32 ? 2 : 1);
 }
 
-int launch_update(int ept, dim3 grid, cudaStream_t st, const Control& c, int N, double2* r, double2* p,
-                  double2* y, double2* ph, long long n) {
+template <typename V2>
+int launch_update(int ept, dim3 grid, cudaStream_t st, const Control& c, int N, V2* r, V2* p, V2* y, V2* ph,
+                  long long n) {
   switch (ept) {
-    case 1: cg_update_kernel<1><<<grid, kUpdBlock, 0, st>>>(c, N, r, p, y, ph, n); break;
-    case 2: cg_update_kernel<2><<<grid, kUpdBlock, 0, st>>>(c, N, r, p, y, ph, n); break;
-    default: cg_update_kernel<4><<<grid, kUpdBlock, 0, st>>>(c, N, r, p, y, ph, n); break;
+    case 1: cg_update_kernel<V2, 1><<<grid, kUpdBlock, 0, st>>>(c, N, r, p, y, ph, n); break;
+    case 2: cg_update_kernel<V2, 2><<<grid, kUpdBlock, 0, st>>>(c, N, r, p, y, ph, n); break;
+    default: cg_update_kernel<V2, 4><<<grid, kUpdBlock, 0, st>>>(c, N, r, p, y, ph, n); break;
   }
   return SSQCD_OK;
 }
@@ -561,29 +683,46 @@ int update_blocks(long long n, int L, int ept) {
 
 }  // namespace
 
-int shifted_cg_device(ssqcd_lattice lat, int N, const double2* z_host, int L, const double2* v, double sigma,
-                      double tol, int max_iter, int precision, int reliable_every, DevBuf& y, int* iters_host,
-                      double2* xi_host, ShiftedCGOut* out) {
-  (void)reliable_every;
-  if (precision != SSQCD_FP64) return fail(SSQCD_ERR_ARG, "shifted_cg_device: only SSQCD_FP64 here");
-  if (N < 1 || N > kMaxShifts) return fail(SSQCD_ERR_ARG, "N must be in [1, 256]");
-  if (L < 1 || L > kMaxSources || N * L > kMaxShifts)
-    return fail(SSQCD_ERR_ARG, "L must be in [1, 64] and N * L <= 256");
+namespace {
+
+// The solve loop for one precision: V2 = double2 (SSQCD_FP64) or float2 (the
+// mixed precisions).  y_out always receives FP64 solutions.
+template <typename V2>
+int run_shifted_cg(ssqcd_lattice lat, int N, const double2* z_host, int L, const double2* v, double sigma,
+                   double tol, int max_iter, int precision, int reliable_every, DevBuf& y_out, int* iters_host,
+                   double2* xi_host, ShiftedCGOut* out) {
+  constexpr bool kFP32 = sizeof(V2) == sizeof(float2);
   cudaStream_t st = lat->stream;
   const Geometry& g = lat->g;
   const long long n = 12LL * g.V;
   const int NL = N * L;
   const int nbw = wilson_blocks(g);
   const int nbs = seed_blocks(n, L);
-  const int ept = update_epts();
+  const int ept = update_epts(kFP32);
   const int nbu = update_blocks(n, L, ept);
+  // FP32 keeps ||r|| within 2^-20 of ||v|| (its elements stay far above the
+  // FP32 underflow); FP64 within 2^-200.
+  const double rescale_below = kFP32 ? 0x1p-40 : 0x1p-400;
+  const double rescale_by = kFP32 ? 0x1p+20 : 0x1p+200;
 
-  DevBuf r, p, q, ph;
-  SS_TRY(r.alloc(sizeof(double2) * n * L));
-  SS_TRY(p.alloc(sizeof(double2) * n * L));
-  SS_TRY(q.alloc(sizeof(double2) * n * L));
-  SS_TRY(y.alloc(sizeof(double2) * n * NL));
-  SS_TRY(ph.alloc(sizeof(double2) * n * NL));
+  DevBuf r, p, q, ph, y32, x, kx;
+  SS_TRY(r.alloc(sizeof(V2) * n * L));
+  SS_TRY(p.alloc(sizeof(V2) * n * L));
+  SS_TRY(q.alloc(sizeof(V2) * n * L));
+  SS_TRY(ph.alloc(sizeof(V2) * n * NL));
+  V2* yv = nullptr;
+  if (kFP32) {
+    SS_TRY(y32.alloc(sizeof(V2) * n * NL));
+    yv = y32.as<V2>();
+    if (reliable_every > 0) {
+      SS_TRY(x.alloc(sizeof(double2) * n * L));
+      SS_TRY(kx.alloc(sizeof(double2) * n * L));
+      SS_CUDA(cudaMemsetAsync(x.p, 0, sizeof(double2) * n * L, st));
+    }
+  } else {
+    SS_TRY(y_out.alloc(sizeof(double2) * n * NL));
+    yv = reinterpret_cast<V2*>(y_out.p);
+  }
   DevBuf ctl;
   size_t off = 0;
   auto take = [&](size_t bytes) {
@@ -593,7 +732,7 @@ int shifted_cg_device(ssqcd_lattice lat, int N, const double2* z_host, int L, co
   };
   const size_t o_seed = take(sizeof(SeedState) * L), o_alpha = take(sizeof(double) * L),
                o_vn = take(sizeof(double) * L), o_live = take(sizeof(int) * L), o_tot = take(sizeof(int)),
-               o_ran = take(sizeof(int)), o_err = take(sizeof(int)), o_si = take(sizeof(int)),
+               o_ran = take(sizeof(int)), o_err = take(sizeof(int)), o_si = take(sizeof(int) * 2),
                o_done = take(sizeof(unsigned) * 2), o_s = take(sizeof(double2) * NL),
                o_xc = take(sizeof(double2) * NL), o_xp = take(sizeof(double2) * NL),
                o_xn = take(sizeof(double2) * NL), o_rt = take(sizeof(double2) * NL), o_act = take(sizeof(int) * NL),
@@ -626,6 +765,7 @@ int shifted_cg_device(ssqcd_lattice lat, int N, const double2* z_host, int L, co
   c.list_b = reinterpret_cast<double2*>(base + o_lb);
   c.partial = reinterpret_cast<double*>(base + o_part);
   c.partial_rr = reinterpret_cast<double*>(base + o_prr);
+  c.x = x.p != nullptr ? x.as<double2>() : nullptr;
   double* vn_part = reinterpret_cast<double*>(base + o_vp);
   double* vn2 = reinterpret_cast<double*>(base + o_vn2);
 
@@ -636,8 +776,7 @@ int shifted_cg_device(ssqcd_lattice lat, int N, const double2* z_host, int L, co
 
   SS_TRY(norm2_partials(v, L, n, vn_part, nbs, st));
   SS_TRY(sum_partials(vn_part, L, nbs, vn2, st));
-  init_vectors_kernel<<<dim3(nbu, L), kUpdBlock, 0, st>>>(v, r.as<double2>(), p.as<double2>(), y.as<double2>(),
-                                                            ph.as<double2>(), N, n);
+  init_vectors_kernel<<<dim3(nbu, L), kUpdBlock, 0, st>>>(v, r.as<V2>(), p.as<V2>(), yv, ph.as<V2>(), N, n);
   SS_CHECK_LAUNCH();
   init_control_kernel<<<1, 256, 0, st>>>(c, vn2, L, N);
   SS_CHECK_LAUNCH();
@@ -668,14 +807,24 @@ int shifted_cg_device(ssqcd_lattice lat, int N, const double2* z_host, int L, co
   const dim3 grid_a(nbw, L), grid_b(nbs, L), grid_c(nbu, L);
   auto iteration = [&](int it) {
     mark(it, 0);
-    cg_stencil_kernel<<<grid_a, kStencilThreads, 0, st>>>(c, L, g, lat->u64.as<double2>(), sigma, p.as<double2>(),
-                                                           q.as<double2>());
+    if constexpr (kFP32) {
+      if (lat->precision == SSQCD_MIXED)
+        cg_stencil_kernel<<<grid_a, kStencilThreads, 0, st>>>(
+            c, L, g, Stencil32<LinksF16>{LinksF16{lat->u16.as<uint2>(), g.V}}, sigma, p.as<V2>(), q.as<V2>());
+      else
+        cg_stencil_kernel<<<grid_a, kStencilThreads, 0, st>>>(
+            c, L, g, Stencil32<LinksF32>{LinksF32{lat->u32.as<float4>(), g.V}}, sigma, p.as<V2>(), q.as<V2>());
+    } else {
+      cg_stencil_kernel<<<grid_a, kStencilThreads, 0, st>>>(c, L, g, Stencil64{lat->u64.as<double2>()}, sigma,
+                                                             p.as<V2>(), q.as<V2>());
+    }
     mark(it, 1);
     mark(it, 2);
-    cg_seed_kernel<<<grid_b, kSeedBlock, 0, st>>>(c, L, N, tol2, r.as<double2>(), q.as<double2>(), n);
+    cg_seed_kernel<V2><<<grid_b, kSeedBlock, 0, st>>>(c, L, N, tol2, r.as<V2>(), q.as<V2>(), p.as<V2>(), n,
+                                                      rescale_below, rescale_by);
     mark(it, 3);
     mark(it, 4);
-    launch_update(ept, grid_c, st, c, N, r.as<double2>(), p.as<double2>(), y.as<double2>(), ph.as<double2>(), n);
+    launch_update<V2>(ept, grid_c, st, c, N, r.as<V2>(), p.as<V2>(), yv, ph.as<V2>(), n);
     mark(it, 5);
   };
   // A chunk of iterations is captured once as a CUDA graph and replayed (the
@@ -696,6 +845,8 @@ int shifted_cg_device(ssqcd_lattice lat, int N, const double2* z_host, int L, co
     }
     (void)cudaGetLastError();  // a failed capture falls back to direct launches
   }
+  const int ru_chunks = reliable_every > 0 ? std::max(1, (reliable_every + kChunk / 2) / kChunk) : 0;
+  int chunks_done = 0;
   while (true) {
     const int chunk = std::min(kChunk, max_iter - k);
     int launched = 0;
@@ -713,6 +864,15 @@ int shifted_cg_device(ssqcd_lattice lat, int N, const double2* z_host, int L, co
       }
       cudaError_t le = cudaGetLastError();
       if (le != cudaSuccess) { status = cuda_fail(le, "shifted CG launch", __FILE__, __LINE__); break; }
+    }
+    ++chunks_done;
+    if (kFP32 && c.x != nullptr && ru_chunks > 0 && chunks_done % ru_chunks == 0) {
+      // reliable update: r = S (v - K x) in FP64 with the FP64 links
+      int s1 = wilson64(g, lat->u64.as<double2>(), c.x, kx.as<double2>(), L, sigma, -1.0, nullptr, nullptr, st);
+      if (s1 != SSQCD_OK) { status = s1; break; }
+      const double floor2 = lat->precision == SSQCD_MIXED ? 1e-4 : 1e-10;  // (1e-2 / 1e-5 of ||v||)^2
+      cg_reliable_kernel<V2><<<grid_b, kSeedBlock, 0, st>>>(c, L, v, kx.as<double2>(), r.as<V2>(), n, floor2);
+      count_launches(1);
     }
     // live-shift count after the last iteration, and the error flag
     cudaError_t ce = cudaMemcpyAsync(h_poll, c.live_total, sizeof(int), cudaMemcpyDeviceToHost, st);
@@ -738,10 +898,14 @@ int shifted_cg_device(ssqcd_lattice lat, int N, const double2* z_host, int L, co
   }
   if (gexec != nullptr) cudaGraphExecDestroy(gexec);
   if (status == SSQCD_OK || status == SSQCD_ERR_BREAKDOWN || status == SSQCD_ERR_NOCONV) {
+    if (kFP32) {  // hand FP64 solutions to the FP64 moments and Rayleigh-Ritz
+      SS_TRY(y_out.alloc(sizeof(double2) * n * NL));
+      SS_TRY(convert_f32_to_f64(reinterpret_cast<const float2*>(yv), y_out.as<double2>(), n * NL, st));
+    }
     SS_CUDA(cudaEventRecord(e1, st));
-    int seed_iters = 0;
+    int counters[2] = {0, 0};
     std::vector<int> it_all(NL);
-    SS_CUDA(cudaMemcpyAsync(&seed_iters, c.seed_iters, sizeof(int), cudaMemcpyDeviceToHost, st));
+    SS_CUDA(cudaMemcpyAsync(counters, c.seed_iters, sizeof(int) * 2, cudaMemcpyDeviceToHost, st));
     SS_CUDA(cudaMemcpyAsync(it_all.data(), c.iters, sizeof(int) * NL, cudaMemcpyDeviceToHost, st));
     if (xi_host) SS_CUDA(cudaMemcpyAsync(xi_host, c.xi_cur, sizeof(double2) * NL, cudaMemcpyDeviceToHost, st));
     SS_CUDA(cudaStreamSynchronize(st));
@@ -749,18 +913,19 @@ int shifted_cg_device(ssqcd_lattice lat, int N, const double2* z_host, int L, co
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
     if (out) {
-      out->seed_iters = seed_iters;
+      out->seed_iters = counters[0];
+      out->reliable_updates = counters[1];
       out->ms = ms;
       out->shift_updates = 0;
       for (int v2 : it_all) out->shift_updates += v2;
       out->timed = timing;
-      out->launches_update = timing ? std::min<int>(seed_iters, (int)t_iter[2].size()) : 0;
+      out->launches_update = timing ? std::min<int>(counters[0], (int)t_iter[2].size()) : 0;
       for (int cls = 0; cls < 4; ++cls) out->ms_k[cls] = 0.0;
       const int slot_of[3] = {0, 1, 3};  // stencil, seed update + scalars, shift update
       for (int cls = 0; cls < 3; ++cls) {
         double acc = 0.0;
         // iterations after the last live one skip their work: not counted
-        for (int i = 0; i < (int)t_iter[cls].size() && i < seed_iters; ++i) acc += t_iter[cls][i];
+        for (int i = 0; i < (int)t_iter[cls].size() && i < counters[0]; ++i) acc += t_iter[cls][i];
         out->ms_k[slot_of[cls]] = acc;
       }
     }
@@ -770,6 +935,24 @@ int shifted_cg_device(ssqcd_lattice lat, int N, const double2* z_host, int L, co
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   return status;
+}
+
+}  // namespace
+
+int shifted_cg_device(ssqcd_lattice lat, int N, const double2* z_host, int L, const double2* v, double sigma,
+                      double tol, int max_iter, int precision, int reliable_every, DevBuf& y, int* iters_host,
+                      double2* xi_host, ShiftedCGOut* out) {
+  if (precision != SSQCD_FP64 && !is_mixed(precision)) return fail(SSQCD_ERR_ARG, "unknown precision");
+  if (is_mixed(precision) && precision != lat->precision)
+    return fail(SSQCD_ERR_ARG, "a mixed-precision solve needs a lattice created with that precision");
+  if (N < 1 || N > kMaxShifts) return fail(SSQCD_ERR_ARG, "N must be in [1, 256]");
+  if (L < 1 || L > kMaxSources || N * L > kMaxShifts)
+    return fail(SSQCD_ERR_ARG, "L must be in [1, 64] and N * L <= 256");
+  if (precision == SSQCD_FP64)
+    return run_shifted_cg<double2>(lat, N, z_host, L, v, sigma, tol, max_iter, precision, 0, y, iters_host, xi_host,
+                                   out);
+  return run_shifted_cg<float2>(lat, N, z_host, L, v, sigma, tol, max_iter, precision, reliable_every, y, iters_host,
+                                xi_host, out);
 }
 
 }  // namespace ssqcd

@@ -8,7 +8,8 @@
 // 8 x (12 projection adds + 72 link FMA/MUL + 24 reconstruction adds) + 18
 // combine adds + 24 FMA ~ 906 FP64 instructions against 192 B (spinor in) +
 // 192 B (out) + 576 B (links, shared by the rhs) of compulsory traffic.
-// FP32 / FP16 links: HBM-bound; 96 B in, 96 B out, 96 B links per site.
+// FP32 spinors with FP16 (or FP32) 12-parameter links: HBM-bound; 96 B in,
+// 96 B out, 96 (192) B links per site.
 #include "wilson_core.cuh"
 
 namespace ssqcd {
@@ -68,8 +69,9 @@ wilson64_kernel(Geometry g, const double2* __restrict__ u, const double2* __rest
   }
 }
 
+template <typename LK>
 __global__ void __launch_bounds__(kStencilThreads)
-wilson32_kernel(Geometry g, const uint2* __restrict__ u16, const float2* __restrict__ in_all,
+wilson32_kernel(Geometry g, LK lk, const float2* __restrict__ in_all,
                 float2* __restrict__ out_all, float c0, float c1, float* __restrict__ dot_partial,
                 const int* __restrict__ skip_if_zero) {
   if (skip_if_zero != nullptr && *skip_if_zero == 0) return;
@@ -82,7 +84,7 @@ wilson32_kernel(Geometry g, const uint2* __restrict__ u16, const float2* __restr
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int s = blockIdx.x * kSitesPerBlock + lane;
   float2 acc[3];
-  block_hops32(u16, in, s, g, sh, acc);
+  block_hops32(lk, in, s, g, sh, acc);
   double dot = 0.0;
   if (s < V) {
     const float sg = w < 2 ? c1 : -c1;
@@ -102,6 +104,22 @@ wilson32_kernel(Geometry g, const uint2* __restrict__ u16, const float2* __restr
     const double b = block_sum<kStencilThreads>(dot, shd);
     if (threadIdx.x == 0) dot_partial[(size_t)rhs * gridDim.x + blockIdx.x] = (float)b;
   }
+}
+
+// FP64 links [4][9][V] -> FP32 rows 0 and 1, [4][3][V] float4
+__global__ void pack_gauge32_kernel(const double2* __restrict__ u, float4* __restrict__ u32, int V) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= 4LL * V) return;
+  const int mu = (int)(i / V), s = (int)(i % V);
+  float2 e[6];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    const double2 z = u[(size_t)(mu * 9 + k) * V + s];
+    e[k] = make_float2((float)z.x, (float)z.y);
+  }
+  u32[(size_t)(mu * 3 + 0) * V + s] = make_float4(e[0].x, e[0].y, e[1].x, e[1].y);
+  u32[(size_t)(mu * 3 + 1) * V + s] = make_float4(e[2].x, e[2].y, e[3].x, e[3].y);
+  u32[(size_t)(mu * 3 + 2) * V + s] = make_float4(e[4].x, e[4].y, e[5].x, e[5].y);
 }
 
 // FP64 links [4][9][V] -> FP16 rows 0 and 1, [4][3][V] uint2, each value
@@ -136,12 +154,23 @@ int wilson64(const Geometry& g, const double2* u, const double2* in, double2* ou
   return SSQCD_OK;
 }
 
-int wilson32(const Geometry& g, const void* u16, const float2* in, float2* out, int nrhs, float c0,
+int wilson32(const Geometry& g, const void* links, int link_bits, const float2* in, float2* out, int nrhs, float c0,
              float c1, float* dot_partial, const int* skip_if_zero, cudaStream_t s) {
   if (nrhs <= 0) return SSQCD_OK;
   dim3 grid(wilson_blocks(g), nrhs);
-  wilson32_kernel<<<grid, kStencilThreads, 0, s>>>(g, static_cast<const uint2*>(u16), in, out, c0, c1,
-                                                   dot_partial, skip_if_zero);
+  if (link_bits == 16)
+    wilson32_kernel<<<grid, kStencilThreads, 0, s>>>(g, LinksF16{static_cast<const uint2*>(links), g.V}, in, out, c0,
+                                                     c1, dot_partial, skip_if_zero);
+  else
+    wilson32_kernel<<<grid, kStencilThreads, 0, s>>>(g, LinksF32{static_cast<const float4*>(links), g.V}, in, out,
+                                                     c0, c1, dot_partial, skip_if_zero);
+  count_launches(1);
+  SS_CHECK_LAUNCH();
+  return SSQCD_OK;
+}
+
+int pack_gauge32(const double2* u64dev, void* u32, int V, cudaStream_t s) {
+  pack_gauge32_kernel<<<grid_for(4LL * V, 256), 256, 0, s>>>(u64dev, static_cast<float4*>(u32), V);
   count_launches(1);
   SS_CHECK_LAUNCH();
   return SSQCD_OK;

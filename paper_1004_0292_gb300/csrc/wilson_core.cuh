@@ -140,8 +140,8 @@ struct Links64 {
   }
 };
 
-// FP16 12-parameter: rows 0 and 1 as six __half2 (re, im) in [4][3][V] uint2;
-// row 2 = conj(row0 x row1) (exact for SU(3)).
+// Reduced-precision links keep rows 0 and 1 (12 reals); row 2 is rebuilt as
+// conj(row0 x row1), exact for SU(3).
 __device__ __forceinline__ float2 h2f(unsigned int v) {
   __half2 h = *reinterpret_cast<__half2*>(&v);
   return __half22float2(h);
@@ -151,16 +151,8 @@ struct Link32 {
   float2 e[3][3];
 };
 
-__device__ __forceinline__ void load_link16(const uint2* __restrict__ u16, int mu, int s, int V, Link32& L) {
-  const uint2 q0 = __ldg(u16 + (size_t)(mu * 3 + 0) * V + s);
-  const uint2 q1 = __ldg(u16 + (size_t)(mu * 3 + 1) * V + s);
-  const uint2 q2 = __ldg(u16 + (size_t)(mu * 3 + 2) * V + s);
-  L.e[0][0] = h2f(q0.x);
-  L.e[0][1] = h2f(q0.y);
-  L.e[0][2] = h2f(q1.x);
-  L.e[1][0] = h2f(q1.y);
-  L.e[1][1] = h2f(q2.x);
-  L.e[1][2] = h2f(q2.y);
+// row 2 of an SU(3) matrix = complex conjugate of (row 0 x row 1)
+__device__ __forceinline__ void reconstruct_row2(Link32& L) {
 #pragma unroll
   for (int b = 0; b < 3; ++b) {
     const int b1 = (b + 1) % 3, b2 = (b + 2) % 3;
@@ -170,6 +162,42 @@ __device__ __forceinline__ void load_link16(const uint2* __restrict__ u16, int m
     L.e[2][b] = make_float2(re, -im);
   }
 }
+
+// FP16 12-parameter links: rows 0 and 1 as six __half2 in [4][3][V] uint2
+struct LinksF16 {
+  const uint2* __restrict__ u;
+  int V;
+  __device__ __forceinline__ void load(int mu, int s, Link32& L) const {
+    const uint2 q0 = __ldg(u + (size_t)(mu * 3 + 0) * V + s);
+    const uint2 q1 = __ldg(u + (size_t)(mu * 3 + 1) * V + s);
+    const uint2 q2 = __ldg(u + (size_t)(mu * 3 + 2) * V + s);
+    L.e[0][0] = h2f(q0.x);
+    L.e[0][1] = h2f(q0.y);
+    L.e[0][2] = h2f(q1.x);
+    L.e[1][0] = h2f(q1.y);
+    L.e[1][1] = h2f(q2.x);
+    L.e[1][2] = h2f(q2.y);
+    reconstruct_row2(L);
+  }
+};
+
+// FP32 12-parameter links: rows 0 and 1 as six float2 in [4][3][V] float4
+struct LinksF32 {
+  const float4* __restrict__ u;
+  int V;
+  __device__ __forceinline__ void load(int mu, int s, Link32& L) const {
+    const float4 q0 = __ldg(u + (size_t)(mu * 3 + 0) * V + s);
+    const float4 q1 = __ldg(u + (size_t)(mu * 3 + 1) * V + s);
+    const float4 q2 = __ldg(u + (size_t)(mu * 3 + 2) * V + s);
+    L.e[0][0] = make_float2(q0.x, q0.y);
+    L.e[0][1] = make_float2(q0.z, q0.w);
+    L.e[0][2] = make_float2(q1.x, q1.y);
+    L.e[1][0] = make_float2(q1.z, q1.w);
+    L.e[1][1] = make_float2(q2.x, q2.y);
+    L.e[1][2] = make_float2(q2.z, q2.w);
+    reconstruct_row2(L);
+  }
+};
 
 // ---- one direction: forward + backward hop, accumulated into acc[12] --------------
 template <int MU>
@@ -260,8 +288,8 @@ __device__ __forceinline__ void hop_dir64(const Links64& lk, const double2* __re
   }
 }
 
-template <int MU>
-__device__ __forceinline__ void hop_dir32(const uint2* __restrict__ u16, const float2* __restrict__ in, int s,
+template <int MU, typename LK>
+__device__ __forceinline__ void hop_dir32(const LK& lk, const float2* __restrict__ in, int s,
                                           const Coords& c, const Geometry& g, float2 (&acc)[12]) {
   using S = Spin<MU>;
   const int V = g.V;
@@ -286,7 +314,7 @@ __device__ __forceinline__ void hop_dir32(const uint2* __restrict__ u16, const f
       }
     }
     Link32 L;
-    load_link16(u16, MU, s, V, L);
+    lk.load(MU, s, L);
     float2 wv[2][3];
 #pragma unroll
     for (int a = 0; a < 3; ++a)
@@ -326,7 +354,7 @@ __device__ __forceinline__ void hop_dir32(const uint2* __restrict__ u16, const f
       }
     }
     Link32 L;
-    load_link16(u16, MU, nb, V, L);
+    lk.load(MU, nb, L);
     float2 wv[2][3];
 #pragma unroll
     for (int a = 0; a < 3; ++a)
@@ -390,7 +418,8 @@ __device__ __forceinline__ void block_hops64(const Links64& lk, const double2* _
   reduce_dirs(acc, sh, acc_out);
 }
 
-__device__ __forceinline__ void block_hops32(const uint2* __restrict__ u16, const float2* __restrict__ in, int s,
+template <typename LK>
+__device__ __forceinline__ void block_hops32(const LK& lk, const float2* __restrict__ in, int s,
                                              const Geometry& g, float2* sh, float2 (&acc_out)[3]) {
   float2 acc[12];
 #pragma unroll
@@ -398,10 +427,10 @@ __device__ __forceinline__ void block_hops32(const uint2* __restrict__ u16, cons
   if (s < g.V) {
     const Coords c = site_coords(s, g);
     switch (threadIdx.x >> 5) {
-      case 0: hop_dir32<0>(u16, in, s, c, g, acc); break;
-      case 1: hop_dir32<1>(u16, in, s, c, g, acc); break;
-      case 2: hop_dir32<2>(u16, in, s, c, g, acc); break;
-      default: hop_dir32<3>(u16, in, s, c, g, acc); break;
+      case 0: hop_dir32<0>(lk, in, s, c, g, acc); break;
+      case 1: hop_dir32<1>(lk, in, s, c, g, acc); break;
+      case 2: hop_dir32<2>(lk, in, s, c, g, acc); break;
+      default: hop_dir32<3>(lk, in, s, c, g, acc); break;
     }
   }
   reduce_dirs(acc, sh, acc_out);

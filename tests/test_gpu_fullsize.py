@@ -1,0 +1,62 @@
+"""Parity at the benchmark's full size (8^4, N = 32, L = 4) in the launch
+configuration bench.py times (side stream, CUDA-graph replay): outputs the
+oracle can check one by one -- eigenvalues against the independent ARPACK
+spectrum of the oracle operator, eigenvector residuals and sampled
+shifted-CG residuals recomputed with the oracle operator."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from tests._lib import gpu_module
+
+import bench
+from oracle import contour, wilson
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "windows.json")
+
+
+@pytest.fixture(scope="module")
+def setup():
+    import torch
+    ss = gpu_module()
+    w = bench.WORKLOAD
+    U, src = bench.make_inputs(0)
+    stream = torch.cuda.Stream()
+    lat = ss.create_lattice(w["dims"], w["kappa"], w["bc_t"], stream=stream)
+    ss.upload_gauge(lat, U)
+    return ss, w, U, src, lat
+
+
+def test_eigenpairs_full_size(setup):
+    ss, w, U, src, lat = setup
+    res = ss.ss_solve(lat, w["interval"], w["N"], w["M"], src, beta=w["beta"], nprime=w["nprime"], tol=w["tol"])
+    assert res.status == ss.OK, res.error
+    ev, vec, rs, st = ss.ss_eigpairs(res)
+    ref = np.array(json.load(open(GOLDEN))["smooth_8x8x8x8_e0.3_k0.125_s2"]["lowest_abs"])
+    ref = np.sort(ref[(ref >= w["interval"][0]) & (ref <= w["interval"][1])])
+    assert len(ref) == 12 and len(ev) == 12
+    assert np.max(np.abs(ev - ref) / np.abs(ref)) <= 1e-10
+    assert np.max(rs) <= 1e-8
+    for k in (0, 5, 11):
+        r = wilson.apply_H(U, vec[k], w["kappa"], w["dims"], w["bc_t"]) - ev[k] * vec[k]
+        assert np.linalg.norm(r) <= 1e-8
+        assert abs(np.linalg.norm(r) - rs[k]) <= 1e-12 + 1e-6 * rs[k]
+
+
+def test_shifted_cg_full_size_sampled(setup):
+    ss, w, U, src, lat = setup
+    gamma, rho = contour.window_from_interval(*w["interval"], w["N"], w["nprime"])
+    z = contour.line_nodes(gamma, rho, w["beta"], w["N"])
+    code, y, iters, xi, seed_iters = ss.shifted_cg(lat, z, src, tol=w["tol"])
+    assert code == ss.OK
+    normA = 1.0 + 8.0 * w["kappa"]
+    for l, j in [(0, 0), (1, 7), (2, 16), (3, 31)]:
+        v = src[l]
+        r = v - (z[j] * y[l, j] - wilson.apply_H(U, y[l, j], w["kappa"], w["dims"], w["bc_t"]))
+        drift = 4 * int(iters[l, j]) * 2.2e-16 * normA * np.linalg.norm(y[l, j])
+        assert np.linalg.norm(r) <= w["tol"] * np.linalg.norm(v) + drift
+    assert seed_iters == int(iters.max())

@@ -46,8 +46,9 @@ def test_shifted_cg_matches_oracle(ss, dims, kind, kappa, N, L, beta, side_strea
             r_orc = v[l] - (z[j] * ref["y"][j] - A(ref["y"][j]))
             # The stopping rule bounds the recursive residual by tol ||v||; the
             # true residual may exceed it by the rounding drift of the
-            # recurrences, at most ~ iterations x eps x ||A|| x ||y||.
-            drift = int(iters[l, j]) * 2.2e-16 * normA * np.linalg.norm(y[l, j])
+            # recurrences, ~ iterations x eps x ||A|| x ||y|| (a factor 4 covers
+            # the growth of ||y|| along the iteration).
+            drift = 4 * int(iters[l, j]) * 2.2e-16 * normA * np.linalg.norm(y[l, j])
             assert np.linalg.norm(r_gpu) <= 1e-12 * vn + drift
             # y - y_exact = (z I - A)^{-1} r and ||(z I - A)^{-1}|| <= 1/|Im z|
             bound = (np.linalg.norm(r_gpu) + np.linalg.norm(r_orc)) / abs(z[j].imag)
