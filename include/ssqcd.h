@@ -76,6 +76,11 @@ typedef struct {
                              reliable update of the seed residual; 0 (default)
                              disables it -- measured to degrade the shifted
                              solutions once ||r|| nears the operator error      */
+  int    windows;         /* lines only: split [a, b] into this many adjacent
+                             windows with the same N, rho, beta whose cores tile
+                             [a, b]; neighbouring windows reuse all but N' - 2 of
+                             their points (Section 3), so one shifted-CG run
+                             solves N + (windows - 1)(N' - 2) points; 1 default */
 } ssqcd_opts;
 
 /* Counters of one solve.  Times are device milliseconds between CUDA events. */
@@ -90,7 +95,8 @@ typedef struct {
   double ms_cg;           /* shifted-CG loop                                        */
   double ms_moments;      /* moment accumulation                                    */
   double ms_rr;           /* Rayleigh-Ritz, acceptance and residuals                */
-  double gamma, rho;      /* the window actually used                               */
+  double gamma, rho;      /* the (first) window actually used                       */
+  int    points;          /* distinct quadrature points solved                      */
   long long shift_updates;/* sum over (source, shift) of iterations before freezing:
                              each is one y / p-hat update of n elements            */
   /* Per-kernel device time of the shifted-CG loop, filled when kernel timing
@@ -205,7 +211,11 @@ void ssqcd_default_opts(ssqcd_opts* opts);
  * rho = (b - a)/2 (N/2 - 1)/(N'/2 - 1)), or on the circle C of centre
  * (a + b)/2 and radius (b - a)/2; shifted CG for all N points and L sources;
  * moments s_hat_k, k < M; Rayleigh-Ritz on span(S_hat) (n x M L); Ritz values
- * in [a, b] are accepted.  The lattice precision decides the solve loop.
+ * in [a, b] are accepted.  With opts.windows = K > 1 (lines only) the
+ * interval is tiled by K windows whose points are solved together in one
+ * shifted-CG run; each window has its own moments and Rayleigh-Ritz and
+ * accepts the Ritz values in its share [a_k, a_{k+1}) of [a, b].  The
+ * lattice precision decides the solve loop.
  * *out receives a result handle (even when the status is an error other than
  * SSQCD_ERR_ARG/OOM, so its stats can be read). */
 int ssqcd_ss_solve(ssqcd_lattice lat, const double interval[2], int N, int M, int L,

@@ -21,6 +21,10 @@ Test infrastructure (see ``oracle/__init__``).
   m <= N - 2, and those of 1/(zeta P(zeta)) give the k = 0 row.)
 * Filter function (Eq. 3): f_k(x) = sum_j w_j zeta_j^k / (zeta_j - x).
 
+Several windows (Section 3): adjacent line pairs with the same N, rho and
+beta, shifted along the real axis so that their cores tile an interval;
+their nodes are then shared except for N' - 2 per new window.
+
 Pins (tests/test_oracle_contour.py): on circle nodes the closed form returns
 zeta_j / N, and the filter equals x^k / (1 + x^N), both printed in
 Section 2.1; closed form against the linear solve on line nodes for N <= 16;
@@ -106,3 +110,23 @@ def window_from_interval(a: float, b: float, N: int, Nprime: int):
     gamma = 0.5 * (a + b)
     rho = 0.5 * (b - a) / core_half_width(N, Nprime)
     return gamma, rho
+
+
+def tiled_windows(a: float, b: float, K: int, N: int, Nprime: int):
+    """K adjacent line-pair windows with the same N, rho (Section 3): the
+    window cores (N' central points) tile [a, b]; window k is returned as
+    (gamma_k, rho, lo_k, hi_k).  Neighbouring windows are N' - 2 points
+    apart, so their nodes coincide except for N' - 2 new points."""
+    core = (b - a) / K
+    out = []
+    for k in range(K):
+        lo, hi = a + k * core, a + (k + 1) * core
+        gamma, rho = window_from_interval(lo, hi, N, Nprime)
+        out.append((gamma, rho, lo, hi))
+    return out
+
+
+def distinct_points(zs, decimals=12):
+    """Number of distinct quadrature points among several node sets."""
+    allz = np.concatenate([np.asarray(z) for z in zs])
+    return len(np.unique(np.round(allz.real, decimals) + 1j * np.round(allz.imag, decimals)))

@@ -23,11 +23,14 @@ from . import contour, moments as mom, rayleigh_ritz as rr, shifted_cg as scg, w
 
 
 def ss_solve(U, dims, kappa, bc_t, interval, N, M, sources, beta=0.3, Nprime=None,
-             tol=1e-12, sigma=0.0, rank_tol=1e-14, path="line", max_iter=100000):
+             tol=1e-12, sigma=0.0, rank_tol=1e-14, path="line", max_iter=100000, windows=1):
     dims = tuple(int(d) for d in dims)
     a, b = float(interval[0]), float(interval[1])
     if Nprime is None:
         Nprime = N // 2
+    if windows > 1:
+        return _ss_windows(U, dims, kappa, bc_t, (a, b), N, M, sources, beta, Nprime, tol, sigma,
+                           rank_tol, max_iter, windows)
     if path == "line":
         gamma, rho = contour.window_from_interval(a, b, N, Nprime)
         z = contour.line_nodes(gamma, rho, beta, N)
@@ -66,3 +69,24 @@ def ss_solve(U, dims, kappa, bc_t, interval, N, M, sources, beta=0.3, Nprime=Non
         "gamma": gamma, "rho": rho, "z": z, "zeta": zeta, "w": w,
         "iters": np.array(iters), "matvecs": matvecs, "S": S, "ys": ys,
     }
+
+
+def _ss_windows(U, dims, kappa, bc_t, interval, N, M, sources, beta, Nprime, tol, sigma, rank_tol,
+                max_iter, K):
+    """Several adjacent windows (Section 3): each window is solved as a
+    single window and accepts the Ritz values in its share [lo, hi) of the
+    interval (the last one [lo, hi]).  The shared quadrature points are
+    solved again here; the CUDA path solves each distinct point once."""
+    a, b = interval
+    evals, evecs, res, zs = [], [], [], []
+    for k, (gamma, rho, lo, hi) in enumerate(contour.tiled_windows(a, b, K, N, Nprime)):
+        out = ss_solve(U, dims, kappa, bc_t, (lo, hi), N, M, sources, beta=beta, Nprime=Nprime, tol=tol,
+                       sigma=sigma, rank_tol=rank_tol, max_iter=max_iter)
+        keep = out["evals"] < hi if k < K - 1 else np.ones(len(out["evals"]), dtype=bool)
+        evals.append(out["evals"][keep])
+        evecs.append(out["evecs"][:, keep])
+        res.append(out["residuals"][keep])
+        zs.append(out["z"])
+    order = np.argsort(np.concatenate(evals))
+    return {"evals": np.concatenate(evals)[order], "evecs": np.concatenate(evecs, axis=1)[:, order],
+            "residuals": np.concatenate(res)[order], "points": contour.distinct_points(zs)}

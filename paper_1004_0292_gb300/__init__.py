@@ -50,6 +50,7 @@ class Opts(C.Structure):
         ("path", C.c_int), ("beta", C.c_double), ("nprime", C.c_int), ("tol", C.c_double),
         ("sigma", C.c_double), ("max_iter", C.c_int), ("rank_tol", C.c_double),
         ("sources", C.c_void_p), ("sources_on_device", C.c_int), ("reliable_every", C.c_int),
+        ("windows", C.c_int),
     ]
 
 
@@ -58,7 +59,7 @@ class Stats(C.Structure):
         ("iterations", C.c_int), ("max_shift_iters", C.c_int), ("matvecs_rr", C.c_int),
         ("rank", C.c_int), ("n_ritz", C.c_int), ("n_accepted", C.c_int), ("reliable_updates", C.c_int),
         ("ms_cg", C.c_double), ("ms_moments", C.c_double), ("ms_rr", C.c_double),
-        ("gamma", C.c_double), ("rho", C.c_double), ("shift_updates", C.c_longlong),
+        ("gamma", C.c_double), ("rho", C.c_double), ("points", C.c_int), ("shift_updates", C.c_longlong),
         ("timed", C.c_int), ("launches_update", C.c_int), ("ms_k_stencil", C.c_double),
         ("ms_k_seed", C.c_double), ("ms_k_scalars", C.c_double), ("ms_k_update", C.c_double),
     ]
@@ -280,7 +281,7 @@ def moments_noalloc(w, zeta, y, M, stream=None):
 
 
 def ss_solve(lat: Lattice, interval, N, M, sources, beta=0.3, nprime=0, tol=1e-12, sigma=0.0, max_iter=100000,
-             rank_tol=1e-14, path=PATH_LINES, reliable_every=0) -> Result:
+             rank_tol=1e-14, path=PATH_LINES, reliable_every=0, windows=1) -> Result:
     """Run the solver; returns a Result (check ``status``)."""
     L = int(np.prod(sources.shape)) // lat.n
     o = Opts()
@@ -289,6 +290,7 @@ def ss_solve(lat: Lattice, interval, N, M, sources, beta=0.3, nprime=0, tol=1e-1
     o.path, o.beta, o.nprime, o.tol, o.sigma = int(path), float(beta), int(nprime), float(tol), float(sigma)
     o.max_iter, o.rank_tol, o.sources, o.sources_on_device = int(max_iter), float(rank_tol), ps, dev
     o.reliable_every = int(reliable_every)
+    o.windows = int(windows)
     iv = (C.c_double * 2)(float(interval[0]), float(interval[1]))
     h = C.c_void_p()
     code = lib().ssqcd_ss_solve(lat.handle, iv, int(N), int(M), L, C.byref(o), C.byref(h))

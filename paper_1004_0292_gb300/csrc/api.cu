@@ -233,6 +233,7 @@ extern "C" void ssqcd_default_opts(ssqcd_opts* o) {
   o->max_iter = 100000;
   o->rank_tol = 1e-14;
   o->reliable_every = 0;
+  o->windows = 1;
 }
 
 namespace {
@@ -270,6 +271,70 @@ int orthonormalise(const double2* S, int m, long long n, double rank_tol, DevBuf
 
 }  // namespace
 
+namespace {
+
+// Rayleigh-Ritz for one window: orthonormal basis of S (m vectors), Ritz
+// pairs of A on it, acceptance of the Ritz values in [lo, hi] (hi_open: the
+// upper end belongs to the next window), eigenvectors X (device, [cnt][n]),
+// residuals.  Appends to evals / resid and returns X in `X`.
+int rayleigh_ritz_window(ssqcd_lattice lat, const double2* S, int m, double rank_tol, double lo, double hi,
+                         bool hi_open, std::vector<double>& evals, std::vector<double>& resid, DevBuf& X, int& cnt,
+                         int& rank, DevBuf& scratch) {
+  cudaStream_t st = lat->stream;
+  const long long n = 12LL * lat->g.V;
+  DevBuf Q, tmp, AQ, Gd;
+  int r = 0;
+  SS_TRY(orthonormalise(S, m, n, rank_tol, Q, r, tmp, scratch, st));
+  tmp.release();
+  rank = r;
+  SS_TRY(AQ.alloc(sizeof(double2) * n * r));
+  SS_TRY(wilson64(lat->g, lat->u64.as<double2>(), Q.as<double2>(), AQ.as<double2>(), r, 0.0, 1.0, nullptr, nullptr,
+                  st));
+  SS_TRY(Gd.alloc(sizeof(double2) * r * r));
+  SS_TRY(gram(Q.as<double2>(), r, AQ.as<double2>(), r, n, Gd.as<double2>(), scratch, st));
+  std::vector<double2> At((size_t)r * r), W((size_t)r * r);
+  std::vector<double> theta(r);
+  SS_CUDA(cudaMemcpyAsync(At.data(), Gd.p, sizeof(double2) * r * r, cudaMemcpyDeviceToHost, st));
+  SS_CUDA(cudaStreamSynchronize(st));
+  // Hermitian part (small_eigh reads the lower triangle)
+  for (int i = 0; i < r; ++i)
+    for (int j = 0; j <= i; ++j) {
+      const double2 x = At[(size_t)i * r + j], y = At[(size_t)j * r + i];
+      At[(size_t)i * r + j] = make_double2(0.5 * (x.x + y.x), 0.5 * (x.y - y.y));
+    }
+  SS_TRY(small_eigh(r, At.data(), theta.data(), W.data()));
+  std::vector<int> acc;
+  for (int c = 0; c < r; ++c)
+    if (theta[c] >= lo && (hi_open ? theta[c] < hi : theta[c] <= hi)) acc.push_back(c);
+  cnt = (int)acc.size();
+  if (cnt == 0) return SSQCD_OK;
+  std::vector<double2> Wacc((size_t)r * cnt);
+  for (int i = 0; i < r; ++i)
+    for (int c = 0; c < cnt; ++c) Wacc[(size_t)i * cnt + c] = W[(size_t)i * r + acc[c]];
+  DevBuf Wd, AX, th, rn;
+  SS_TRY(Wd.alloc(sizeof(double2) * r * cnt));
+  SS_CUDA(cudaMemcpyAsync(Wd.p, Wacc.data(), sizeof(double2) * r * cnt, cudaMemcpyHostToDevice, st));
+  SS_TRY(X.alloc(sizeof(double2) * n * cnt));
+  SS_TRY(combine(Q.as<double2>(), r, n, Wd.as<double2>(), cnt, X.as<double2>(), st));
+  SS_TRY(AX.alloc(sizeof(double2) * n * cnt));
+  SS_TRY(wilson64(lat->g, lat->u64.as<double2>(), X.as<double2>(), AX.as<double2>(), cnt, 0.0, 1.0, nullptr,
+                  nullptr, st));
+  std::vector<double> ev(cnt), rs(cnt);
+  for (int c = 0; c < cnt; ++c) ev[c] = theta[acc[c]];
+  SS_TRY(th.alloc(sizeof(double) * cnt));
+  SS_TRY(rn.alloc(sizeof(double) * cnt));
+  SS_CUDA(cudaMemcpyAsync(th.p, ev.data(), sizeof(double) * cnt, cudaMemcpyHostToDevice, st));
+  SS_TRY(col_residual_norms(AX.as<double2>(), X.as<double2>(), th.as<double>(), cnt, n, rn.as<double>(), scratch,
+                            st));
+  SS_CUDA(cudaMemcpyAsync(rs.data(), rn.p, sizeof(double) * cnt, cudaMemcpyDeviceToHost, st));
+  SS_CUDA(cudaStreamSynchronize(st));
+  evals.insert(evals.end(), ev.begin(), ev.end());
+  resid.insert(resid.end(), rs.begin(), rs.end());
+  return SSQCD_OK;
+}
+
+}  // namespace
+
 extern "C" int ssqcd_ss_solve(ssqcd_lattice lat, const double interval[2], int N, int M, int L,
                               const ssqcd_opts* opts_in, ssqcd_result* out) {
   if (out == nullptr) return fail(SSQCD_ERR_ARG, "NULL result pointer");
@@ -281,25 +346,49 @@ extern "C" int ssqcd_ss_solve(ssqcd_lattice lat, const double interval[2], int N
   ssqcd_default_opts(&o);
   if (opts_in) o = *opts_in;
   if (o.sources == nullptr) return fail(SSQCD_ERR_ARG, "opts.sources is required");
+  const int K = o.windows < 1 ? 1 : o.windows;
+  if (K > 1 && o.path != SSQCD_PATH_LINES) return fail(SSQCD_ERR_ARG, "several windows need the line contour");
   const double a = interval[0], b = interval[1];
-  double gamma = 0.5 * (a + b), rho = 0.5 * (b - a);
+  const double core = (b - a) / K;  // accepted width of each window
+  double gamma0 = a + 0.5 * core, rho = 0.5 * core;
+  int np = 0, step = 0, half = N / 2;
   if (o.path == SSQCD_PATH_LINES) {
-    const int np = o.nprime == 0 ? N / 2 : o.nprime;
+    np = o.nprime == 0 ? N / 2 : o.nprime;
     if (N < 4 || N % 2 || np < 4 || np % 2 || np > N)
       return fail(SSQCD_ERR_ARG, "lines need even N >= 4 and even 4 <= N' <= N");
-    rho = 0.5 * (b - a) * (N / 2 - 1) / (double)(np / 2 - 1);
+    rho = 0.5 * core * (half - 1) / (double)(np / 2 - 1);
+    step = np / 2 - 1;  // grid points per line between neighbouring windows (Section 3)
   } else if (o.path != SSQCD_PATH_CIRCLE) {
     return fail(SSQCD_ERR_ARG, "unknown path");
   }
+  // nodes and weights of one window (the same in every window's own zeta)
   std::vector<double2> z, w;
-  SS_TRY(contour_nodes(o.path, gamma, rho, o.beta, N, z, w));
-  // moment coefficients c[j][k] = w_j zeta_j^k
-  std::vector<double2> coef((size_t)N * M);
+  SS_TRY(contour_nodes(o.path, gamma0, rho, o.beta, N, z, w));
+  // the union of the windows' nodes: windows k and k+1 share N - (N' - 2)
+  // points; point j of window k is union point 2 (k step + j/2) + j%2
+  const int NU = (K == 1) ? N : 2 * (half + (K - 1) * step);
+  std::vector<double2> zu(NU);
+  if (K == 1) {
+    zu = z;
+  } else {
+    for (int gi = 0; gi < NU / 2; ++gi) {
+      const double x = -1.0 + 2.0 * gi / (half - 1);
+      zu[2 * gi] = make_double2(gamma0 + rho * x, rho * o.beta);
+      zu[2 * gi + 1] = make_double2(gamma0 + rho * x, -rho * o.beta);
+    }
+  }
+  // moment coefficients over the union for each window: c_k[u][m] = w_j zeta_j^m
+  // for the window's points u = u(k, j), zero elsewhere
+  std::vector<std::vector<double2>> coefk(K, std::vector<double2>((size_t)NU * M, make_double2(0.0, 0.0)));
   for (int j = 0; j < N; ++j) {
-    const double zr0 = (z[j].x - gamma) / rho, zi0 = z[j].y / rho;
+    const double zr0 = (z[j].x - gamma0) / rho, zi0 = z[j].y / rho;
     double zr = 1.0, zi = 0.0;
-    for (int k = 0; k < M; ++k) {
-      coef[(size_t)j * M + k] = make_double2(w[j].x * zr - w[j].y * zi, w[j].x * zi + w[j].y * zr);
+    for (int m = 0; m < M; ++m) {
+      const double2 cv = make_double2(w[j].x * zr - w[j].y * zi, w[j].x * zi + w[j].y * zr);
+      for (int k = 0; k < K; ++k) {
+        const int u = (K == 1) ? j : 2 * (k * step + j / 2) + j % 2;
+        coefk[k][(size_t)u * M + m] = cv;
+      }
       const double nr = zr * zr0 - zi * zi0, ni = zr * zi0 + zi * zr0;
       zr = nr;
       zi = ni;
@@ -310,8 +399,9 @@ extern "C" int ssqcd_ss_solve(ssqcd_lattice lat, const double interval[2], int N
   res->stream = lat->stream;
   res->V = lat->g.V;
   res->n = 12LL * lat->g.V;
-  res->stats.gamma = gamma;
+  res->stats.gamma = gamma0;
   res->stats.rho = rho;
+  res->stats.points = NU;
   const long long n = res->n;
   cudaStream_t st = lat->stream;
   auto bail = [&](int code) {
@@ -320,13 +410,13 @@ extern "C" int ssqcd_ss_solve(ssqcd_lattice lat, const double interval[2], int N
   };
 
   // sources -> device layout
-  DevBuf vd, yd, S, Q, tmp, AQ, scratch;
+  DevBuf vd, yd, S, scratch;
   int s1 = to_device_layout(lat, o.sources, L, o.sources_on_device, vd);
   if (s1 != SSQCD_OK) { delete res; return s1; }
-  // shifted CG
+  // shifted CG over the union of the quadrature points (one seed recurrence)
   ShiftedCGOut cg;
-  std::vector<int> iters((size_t)N * L);
-  s1 = shifted_cg_device(lat, N, z.data(), L, vd.as<double2>(), o.sigma, o.tol, o.max_iter, lat->precision,
+  std::vector<int> iters((size_t)NU * L);
+  s1 = shifted_cg_device(lat, NU, zu.data(), L, vd.as<double2>(), o.sigma, o.tol, o.max_iter, lat->precision,
                          o.reliable_every, yd, iters.data(), nullptr, &cg);
   res->stats.iterations = cg.seed_iters;
   res->stats.reliable_updates = cg.reliable_updates;
@@ -347,70 +437,62 @@ extern "C" int ssqcd_ss_solve(ssqcd_lattice lat, const double interval[2], int N
   cudaEventCreate(&e1);
   cudaEventCreate(&e2);
   cudaEventRecord(e0, st);
-  // moments
   const int m = M * L;
-  if ((s1 = S.alloc(sizeof(double2) * n * m)) != SSQCD_OK) return bail(s1);
-  if ((s1 = moments_device(yd.as<double2>(), N, M, L, n, coef.data(), S.as<double2>(), scratch, st)) != SSQCD_OK)
-    return bail(s1);
-  cudaEventRecord(e1, st);
-  yd.release();
-  // Rayleigh-Ritz
-  int r = 0;
-  if ((s1 = orthonormalise(S.as<double2>(), m, n, o.rank_tol, Q, r, tmp, scratch, st)) != SSQCD_OK) return bail(s1);
-  S.release();
-  res->stats.rank = r;
-  res->stats.n_ritz = r;
-  if ((s1 = AQ.alloc(sizeof(double2) * n * r)) != SSQCD_OK) return bail(s1);
-  if ((s1 = wilson64(lat->g, lat->u64.as<double2>(), Q.as<double2>(), AQ.as<double2>(), r, 0.0, 1.0, nullptr,
-                     nullptr, st)) != SSQCD_OK)
-    return bail(s1);
-  DevBuf Gd;
-  if ((s1 = Gd.alloc(sizeof(double2) * r * r)) != SSQCD_OK) return bail(s1);
-  if ((s1 = gram(Q.as<double2>(), r, AQ.as<double2>(), r, n, Gd.as<double2>(), scratch, st)) != SSQCD_OK)
-    return bail(s1);
-  std::vector<double2> At((size_t)r * r), W((size_t)r * r);
-  std::vector<double> theta(r);
-  cudaMemcpyAsync(At.data(), Gd.p, sizeof(double2) * r * r, cudaMemcpyDeviceToHost, st);
-  if (cudaStreamSynchronize(st) != cudaSuccess) return bail(cuda_fail(cudaGetLastError(), "RR sync", __FILE__, __LINE__));
-  // Hermitian part (only the lower triangle is read by small_eigh; symmetrise it)
-  for (int i = 0; i < r; ++i)
-    for (int j = 0; j <= i; ++j) {
-      const double2 x = At[(size_t)i * r + j], y = At[(size_t)j * r + i];
-      At[(size_t)i * r + j] = make_double2(0.5 * (x.x + y.x), 0.5 * (x.y - y.y));
+  std::vector<DevBuf> Xk(K);
+  std::vector<int> cntk(K, 0);
+  float ms_mom = 0.f;
+  for (int k = 0; k < K; ++k) {
+    // moments of window k (Eq. 2), S = [L][M][n]
+    if ((s1 = S.alloc(sizeof(double2) * n * m)) != SSQCD_OK) return bail(s1);
+    if ((s1 = moments_device(yd.as<double2>(), NU, M, L, n, coefk[k].data(), S.as<double2>(), scratch, st)) !=
+        SSQCD_OK)
+      return bail(s1);
+    if (k == K - 1) {
+      cudaEventRecord(e1, st);
+      yd.release();
     }
-  if ((s1 = small_eigh(r, At.data(), theta.data(), W.data())) != SSQCD_OK) return bail(s1);
-  std::vector<int> acc;
-  for (int c = 0; c < r; ++c)
-    if (theta[c] >= a && theta[c] <= b) acc.push_back(c);
-  const int cnt = (int)acc.size();
+    // Rayleigh-Ritz and acceptance in the window's core
+    const double lo = (K == 1) ? a : a + k * core;
+    const double hi = (K == 1) ? b : (k == K - 1 ? b : a + (k + 1) * core);
+    int rank = 0;
+    if ((s1 = rayleigh_ritz_window(lat, S.as<double2>(), m, o.rank_tol, lo, hi, k < K - 1, res->evals,
+                                   res->residuals, Xk[k], cntk[k], rank, scratch)) != SSQCD_OK)
+      return bail(s1);
+    res->stats.rank += rank;
+    res->stats.n_ritz += rank;
+    res->stats.matvecs_rr += rank + cntk[k];
+  }
+  (void)ms_mom;
+  // gather the windows' eigenvectors, then sort everything by eigenvalue
+  int cnt = 0;
+  for (int k = 0; k < K; ++k) cnt += cntk[k];
   res->stats.n_accepted = cnt;
-  res->stats.matvecs_rr = r + cnt;
   if (cnt > 0) {
-    std::vector<double2> Wacc((size_t)r * cnt);
-    for (int i = 0; i < r; ++i)
-      for (int c = 0; c < cnt; ++c) Wacc[(size_t)i * cnt + c] = W[(size_t)i * r + acc[c]];
-    DevBuf Wd, AX, th, rn;
-    if ((s1 = Wd.alloc(sizeof(double2) * r * cnt)) != SSQCD_OK) return bail(s1);
-    cudaMemcpyAsync(Wd.p, Wacc.data(), sizeof(double2) * r * cnt, cudaMemcpyHostToDevice, st);
+    DevBuf all;
+    if ((s1 = all.alloc(sizeof(double2) * n * cnt)) != SSQCD_OK) return bail(s1);
+    int off = 0;
+    for (int k = 0; k < K; ++k) {
+      if (cntk[k] == 0) continue;
+      cudaMemcpyAsync(all.as<double2>() + (size_t)off * n, Xk[k].p, sizeof(double2) * n * cntk[k],
+                      cudaMemcpyDeviceToDevice, st);
+      off += cntk[k];
+      Xk[k].release();
+    }
+    std::vector<int> order(cnt);
+    for (int i = 0; i < cnt; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return res->evals[x] < res->evals[y]; });
     if ((s1 = res->evecs.alloc(sizeof(double2) * n * cnt)) != SSQCD_OK) return bail(s1);
-    if ((s1 = combine(Q.as<double2>(), r, n, Wd.as<double2>(), cnt, res->evecs.as<double2>(), st)) != SSQCD_OK)
-      return bail(s1);
-    if ((s1 = AX.alloc(sizeof(double2) * n * cnt)) != SSQCD_OK) return bail(s1);
-    if ((s1 = wilson64(lat->g, lat->u64.as<double2>(), res->evecs.as<double2>(), AX.as<double2>(), cnt, 0.0, 1.0,
-                       nullptr, nullptr, st)) != SSQCD_OK)
-      return bail(s1);
-    res->evals.resize(cnt);
-    for (int c = 0; c < cnt; ++c) res->evals[c] = theta[acc[c]];
-    if ((s1 = th.alloc(sizeof(double) * cnt)) != SSQCD_OK) return bail(s1);
-    if ((s1 = rn.alloc(sizeof(double) * cnt)) != SSQCD_OK) return bail(s1);
-    cudaMemcpyAsync(th.p, res->evals.data(), sizeof(double) * cnt, cudaMemcpyHostToDevice, st);
-    if ((s1 = col_residual_norms(AX.as<double2>(), res->evecs.as<double2>(), th.as<double>(), cnt, n,
-                                 rn.as<double>(), scratch, st)) != SSQCD_OK)
-      return bail(s1);
-    res->residuals.resize(cnt);
-    cudaMemcpyAsync(res->residuals.data(), rn.p, sizeof(double) * cnt, cudaMemcpyDeviceToHost, st);
+    std::vector<double> ev(cnt), rs(cnt);
+    for (int i = 0; i < cnt; ++i) {
+      ev[i] = res->evals[order[i]];
+      rs[i] = res->residuals[order[i]];
+      cudaMemcpyAsync(res->evecs.as<double2>() + (size_t)i * n, all.as<double2>() + (size_t)order[i] * n,
+                      sizeof(double2) * n, cudaMemcpyDeviceToDevice, st);
+    }
+    res->evals = ev;
+    res->residuals = rs;
     if (cudaStreamSynchronize(st) != cudaSuccess)
-      return bail(cuda_fail(cudaGetLastError(), "RR residuals", __FILE__, __LINE__));
+      return bail(cuda_fail(cudaGetLastError(), "gathering eigenvectors", __FILE__, __LINE__));
   }
   cudaEventRecord(e2, st);
   cudaEventSynchronize(e2);

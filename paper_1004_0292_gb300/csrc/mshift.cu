@@ -94,7 +94,8 @@ struct Control {
 
 constexpr int kUpdBlock = 256;
 constexpr int kSeedBlock = 256;
-constexpr int kMaxShifts = 256;
+constexpr int kMaxShifts = 512;   // quadrature points per source
+constexpr int kMaxTotal = 1024;   // (source, point) pairs in one solve
 constexpr int kMaxSources = 64;
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -298,8 +299,8 @@ cg_seed_kernel(Control c, int L, int N, double tol2, V2* __restrict__ r, const V
   __shared__ double sred[kSeedBlock / 32];
   __shared__ double sums[kMaxSources];
   __shared__ double s_scale[kMaxSources], s_beta[kMaxSources];
-  __shared__ double2 s_a[kMaxShifts], s_b[kMaxShifts];
-  __shared__ int s_flag[kMaxShifts];
+  __shared__ double2 s_a[kMaxTotal], s_b[kMaxTotal];
+  __shared__ int s_flag[kMaxTotal];
   __shared__ bool s_last;
   const int l = blockIdx.y;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -945,9 +946,9 @@ int shifted_cg_device(ssqcd_lattice lat, int N, const double2* z_host, int L, co
   if (precision != SSQCD_FP64 && !is_mixed(precision)) return fail(SSQCD_ERR_ARG, "unknown precision");
   if (is_mixed(precision) && precision != lat->precision)
     return fail(SSQCD_ERR_ARG, "a mixed-precision solve needs a lattice created with that precision");
-  if (N < 1 || N > kMaxShifts) return fail(SSQCD_ERR_ARG, "N must be in [1, 256]");
-  if (L < 1 || L > kMaxSources || N * L > kMaxShifts)
-    return fail(SSQCD_ERR_ARG, "L must be in [1, 64] and N * L <= 256");
+  if (N < 1 || N > kMaxShifts) return fail(SSQCD_ERR_ARG, "N must be in [1, 512]");
+  if (L < 1 || L > kMaxSources || N * L > kMaxTotal)
+    return fail(SSQCD_ERR_ARG, "L must be in [1, 64] and N * L <= 1024");
   if (precision == SSQCD_FP64)
     return run_shifted_cg<double2>(lat, N, z_host, L, v, sigma, tol, max_iter, precision, 0, y, iters_host, xi_host,
                                    out);

@@ -1,0 +1,61 @@
+"""Multi-window tiling with point reuse and the circle contour, against the
+oracle (same readings) and the dense spectrum."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from tests._lib import gpu_module
+
+import synthetic
+from oracle import ss as oss
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "windows.json")
+
+
+@pytest.fixture(scope="module")
+def setup():
+    import torch
+    ss = gpu_module()
+    dims = (4, 4, 4, 4)
+    U = synthetic.gauge_field(dims, "haar", seed=1)
+    src = synthetic.gaussian_sources(dims, 3, seed=100)
+    lat = ss.create_lattice(dims, 0.13, -1, stream=torch.cuda.Stream())
+    ss.upload_gauge(lat, U)
+    lam = np.array(json.load(open(GOLDEN))["haar_4x4x4x4_k0.13_s1"]["lowest_abs"])
+    return ss, dims, U, src, lat, lam
+
+
+def test_two_windows_reuse_points_and_match_oracle(setup):
+    ss, dims, U, src, lat, lam = setup
+    a, b, N, M, Np, K = 0.374, 0.3930, 16, 8, 12, 2
+    res = ss.ss_solve(lat, (a, b), N, M, src, beta=0.3, nprime=Np, windows=K)
+    assert res.status == ss.OK, res.error
+    ev, vec, rs, st = ss.ss_eigpairs(res)
+    assert st["points"] == N + (K - 1) * (Np - 2)     # Section 3: shift by N' - 2 points
+    ref = oss.ss_solve(U, dims, 0.13, -1, (a, b), N, M, src, beta=0.3, Nprime=Np, windows=K)
+    assert ref["points"] == st["points"]
+    exact = np.sort(lam[(lam >= a) & (lam <= b)])
+    assert len(ev) == len(ref["evals"]) == len(exact) == 8
+    assert np.max(np.abs(ev - ref["evals"]) / ref["evals"]) <= 1e-10
+    assert np.max(np.abs(ev - exact) / exact) <= 1e-10
+    assert np.max(rs) <= 1e-8
+
+
+def test_circle_contour_matches_oracle(setup):
+    ss, dims, U, src, lat, lam = setup
+    a, b, N, M = 0.374, 0.3930, 32, 8
+    res = ss.ss_solve(lat, (a, b), N, M, src, path=ss.PATH_CIRCLE)
+    assert res.status == ss.OK, res.error
+    ev, vec, rs, st = ss.ss_eigpairs(res)
+    ref = oss.ss_solve(U, dims, 0.13, -1, (a, b), N, M, src, path="circle")
+    assert len(ev) == len(ref["evals"])
+    assert np.max(np.abs(ev - ref["evals"]) / ref["evals"]) <= 1e-10
+    exact = np.sort(lam[(lam >= a) & (lam <= b)])
+    good = rs <= 1e-8
+    # every well-resolved Ritz pair is an eigenpair of the dense spectrum
+    for e in ev[good]:
+        assert np.min(np.abs(exact - e)) / e <= 1e-10

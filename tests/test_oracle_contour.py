@@ -93,3 +93,20 @@ def test_filter_f0_section3_shape():
         assert f[0] > f[2] > f[3]
         vals[beta] = f
     assert vals[0.2][2] < vals[1.4][2]
+
+
+def test_point_reuse_matches_table2():
+    # Section 4, Table 2: six adjacent line pairs (N = 32, N' = 16) need 102
+    # quadrature points, four circles 128 (no reuse).
+    import json, os
+    facts = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_counts.json")))
+    t = facts["table2_line_pairs"]
+    wins = contour.tiled_windows(-0.1, 0.1, t["windows"], t["N"], t["Nprime"])
+    zs = [contour.line_nodes(g, r, 0.2, t["N"]) for g, r, _, _ in wins]
+    assert contour.distinct_points(zs) == t["points"]
+    # the cores tile the interval and all windows share rho
+    assert np.isclose(wins[0][2], -0.1) and np.isclose(wins[-1][3], 0.1)
+    assert all(np.isclose(w_[1], wins[0][1]) for w_ in wins)
+    c = facts["table2_circles"]
+    circ = [contour.circle_nodes(0.03 * k, 0.01, c["N"]) for k in range(c["circles"])]
+    assert contour.distinct_points(circ) == c["points"]
