@@ -115,16 +115,18 @@ __device__ __forceinline__ double warp_sum(double v) {
 // range, so they need no overflow guards.
 
 // ---- initialisation ---------------------------------------------------------------
-template <typename V2>
-__global__ void init_vectors_kernel(const double2* __restrict__ v, V2* __restrict__ r, V2* __restrict__ p,
+template <typename VR, typename V2>
+__global__ void init_vectors_kernel(const double2* __restrict__ v, VR* __restrict__ r, VR* __restrict__ p,
                                     V2* __restrict__ y, V2* __restrict__ ph, int N, long long n) {
   using T = decltype(V2::x);
+  using TR = decltype(VR::x);
   const int l = blockIdx.y;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
     const double2 xd = v[l * n + e];
+    const VR xr{(TR)xd.x, (TR)xd.y};
     const V2 x{(T)xd.x, (T)xd.y};
-    r[l * n + e] = x;
-    p[l * n + e] = x;
+    r[l * n + e] = xr;
+    p[l * n + e] = xr;
     for (int j = 0; j < N; ++j) {
       y[((long long)l * N + j) * n + e] = V2{0, 0};
       ph[((long long)l * N + j) * n + e] = x;
@@ -468,11 +470,12 @@ struct alignas(4 * sizeof(T)) Coef4 {
   T x, y, z, w;  // a.x, -a.y, b.x, -b.y (imaginary parts negated once per block)
 };
 
-template <typename V2, int EPT>
+template <typename VR, typename V2, int EPT>
 __global__ void __launch_bounds__(kUpdBlock)
-cg_update_kernel(Control c, int N, V2* __restrict__ r, V2* __restrict__ p, V2* __restrict__ y,
+cg_update_kernel(Control c, int N, VR* __restrict__ r, VR* __restrict__ p, V2* __restrict__ y,
                  V2* __restrict__ ph, long long n) {
-  using T = decltype(V2::x);
+  using T = decltype(V2::x);    // shift vectors (y, p-hat)
+  using TR = decltype(VR::x);   // seed vectors (r, p)
   if (*c.ran == 0) return;
   const int l = blockIdx.y;
   const int m = c.list_n[l];
@@ -489,24 +492,26 @@ cg_update_kernel(Control c, int N, V2* __restrict__ r, V2* __restrict__ p, V2* _
     s_by[t] = (T)b.y;
   }
   __syncthreads();
-  const T sc = (T)c.seed[l].scale;  // exact power of two, usually 1
-  const T beta = (T)(c.seed[l].scale * c.seed[l].beta);
-  V2* rl = r + (long long)l * n;
-  V2* pl = p + (long long)l * n;
+  const TR sc = (TR)c.seed[l].scale;  // exact power of two, usually 1
+  const TR beta = (TR)(c.seed[l].scale * c.seed[l].beta);
+  VR* rl = r + (long long)l * n;
+  VR* pl = p + (long long)l * n;
   V2* yl = y + (long long)l * N * n;
   V2* hl = ph + (long long)l * N * n;
   const long long chunk = (long long)kUpdBlock * EPT;
   for (long long base = blockIdx.x * chunk + threadIdx.x; base < n; base += (long long)gridDim.x * chunk) {
-    V2 rv[EPT];
+    VR rs[EPT];   // r in the seed precision (for p)
+    V2 rv[EPT];   // r in the shift precision (for p-hat)
 #pragma unroll
     for (int i = 0; i < EPT; ++i) {
       const long long e = base + (long long)i * kUpdBlock;
-      V2 x = e < n ? rl[e] : V2{0, 0};
-      if (sc != (T)1) {
-        x = V2{sc * x.x, sc * x.y};
+      VR x = e < n ? rl[e] : VR{0, 0};
+      if (sc != (TR)1) {
+        x = VR{sc * x.x, sc * x.y};
         if (e < n) rl[e] = x;
       }
-      rv[i] = x;
+      rs[i] = x;
+      rv[i] = V2{(T)x.x, (T)x.y};
     }
     int t = 0;
     for (; t + 2 <= m; t += 2) {
@@ -572,9 +577,9 @@ cg_update_kernel(Control c, int N, V2* __restrict__ r, V2* __restrict__ p, V2* _
       for (int i = 0; i < EPT; ++i) {
         const long long e = base + (long long)i * kUpdBlock;
         if (e < n) {
-          V2 pe = pl[e];
-          pe.x = fma(beta, pe.x, rv[i].x);
-          pe.y = fma(beta, pe.y, rv[i].y);
+          VR pe = pl[e];
+          pe.x = fma(beta, pe.x, rs[i].x);
+          pe.y = fma(beta, pe.y, rs[i].y);
           pl[e] = pe;
         }
       }
@@ -665,13 +670,13 @@ int update_epts(bool fp32) {
   return v != 0 ? v : (fp32 ? 2 : 1);
 }
 
-template <typename V2>
-int launch_update(int ept, dim3 grid, cudaStream_t st, const Control& c, int N, V2* r, V2* p, V2* y, V2* ph,
+template <typename VR, typename V2>
+int launch_update(int ept, dim3 grid, cudaStream_t st, const Control& c, int N, VR* r, VR* p, V2* y, V2* ph,
                   long long n) {
   switch (ept) {
-    case 1: cg_update_kernel<V2, 1><<<grid, kUpdBlock, 0, st>>>(c, N, r, p, y, ph, n); break;
-    case 2: cg_update_kernel<V2, 2><<<grid, kUpdBlock, 0, st>>>(c, N, r, p, y, ph, n); break;
-    default: cg_update_kernel<V2, 4><<<grid, kUpdBlock, 0, st>>>(c, N, r, p, y, ph, n); break;
+    case 1: cg_update_kernel<VR, V2, 1><<<grid, kUpdBlock, 0, st>>>(c, N, r, p, y, ph, n); break;
+    case 2: cg_update_kernel<VR, V2, 2><<<grid, kUpdBlock, 0, st>>>(c, N, r, p, y, ph, n); break;
+    default: cg_update_kernel<VR, V2, 4><<<grid, kUpdBlock, 0, st>>>(c, N, r, p, y, ph, n); break;
   }
   return SSQCD_OK;
 }
@@ -686,41 +691,47 @@ int update_blocks(long long n, int L, int ept) {
 
 namespace {
 
-// The solve loop for one precision: V2 = double2 (SSQCD_FP64) or float2 (the
-// mixed precisions).  y_out always receives FP64 solutions.
-template <typename V2>
+// The solve loop for one precision: VR is the type of the seed vectors (r, p,
+// q and the stencil), V2 that of the shift vectors (y, p-hat): double2 /
+// double2 (SSQCD_FP64), double2 / float2 (SSQCD_FP64_SHIFT32), float2 /
+// float2 (the mixed precisions).  y_out always receives FP64 solutions.
+template <typename VR, typename V2>
 int run_shifted_cg(ssqcd_lattice lat, int N, const double2* z_host, int L, const double2* v, double sigma,
                    double tol, int max_iter, int precision, int reliable_every, DevBuf& y_out, int* iters_host,
                    double2* xi_host, ShiftedCGOut* out) {
-  constexpr bool kFP32 = sizeof(V2) == sizeof(float2);
+  constexpr bool kFP32 = sizeof(VR) == sizeof(float2);      // seed vectors and stencil in FP32
+  constexpr bool kShift32 = sizeof(V2) == sizeof(float2);   // shift vectors in FP32
   cudaStream_t st = lat->stream;
   const Geometry& g = lat->g;
   const long long n = 12LL * g.V;
   const int NL = N * L;
   const int nbw = wilson_blocks(g);
   const int nbs = seed_blocks(n, L);
-  const int ept = update_epts(kFP32);
+  const int ept = update_epts(kShift32);
   const int nbu = update_blocks(n, L, ept);
   // FP32 keeps ||r|| within 2^-20 of ||v|| (its elements stay far above the
   // FP32 underflow); FP64 within 2^-200.
-  const double rescale_below = kFP32 ? 0x1p-40 : 0x1p-400;
-  const double rescale_by = kFP32 ? 0x1p+20 : 0x1p+200;
+  const double rescale_below = kShift32 ? 0x1p-40 : 0x1p-400;
+  const double rescale_by = kShift32 ? 0x1p+20 : 0x1p+200;
 
   DevBuf r, p, q, ph, y32, x, kx;
-  SS_TRY(r.alloc(sizeof(V2) * n * L));
-  SS_TRY(p.alloc(sizeof(V2) * n * L));
-  SS_TRY(q.alloc(sizeof(V2) * n * L));
+  SS_TRY(r.alloc(sizeof(VR) * n * L));
+  SS_TRY(p.alloc(sizeof(VR) * n * L));
+  SS_TRY(q.alloc(sizeof(VR) * n * L));
   SS_TRY(ph.alloc(sizeof(V2) * n * NL));
   V2* yv = nullptr;
-  if (kFP32) {
+  if (kShift32) {
     SS_TRY(y32.alloc(sizeof(V2) * n * NL));
     yv = y32.as<V2>();
+  }
+  if (kFP32) {
     if (reliable_every > 0) {
       SS_TRY(x.alloc(sizeof(double2) * n * L));
       SS_TRY(kx.alloc(sizeof(double2) * n * L));
       SS_CUDA(cudaMemsetAsync(x.p, 0, sizeof(double2) * n * L, st));
     }
-  } else {
+  }
+  if (!kShift32) {
     SS_TRY(y_out.alloc(sizeof(double2) * n * NL));
     yv = reinterpret_cast<V2*>(y_out.p);
   }
@@ -777,7 +788,7 @@ int run_shifted_cg(ssqcd_lattice lat, int N, const double2* z_host, int L, const
 
   SS_TRY(norm2_partials(v, L, n, vn_part, nbs, st));
   SS_TRY(sum_partials(vn_part, L, nbs, vn2, st));
-  init_vectors_kernel<<<dim3(nbu, L), kUpdBlock, 0, st>>>(v, r.as<V2>(), p.as<V2>(), yv, ph.as<V2>(), N, n);
+  init_vectors_kernel<<<dim3(nbu, L), kUpdBlock, 0, st>>>(v, r.as<VR>(), p.as<VR>(), yv, ph.as<V2>(), N, n);
   SS_CHECK_LAUNCH();
   init_control_kernel<<<1, 256, 0, st>>>(c, vn2, L, N);
   SS_CHECK_LAUNCH();
@@ -811,21 +822,21 @@ int run_shifted_cg(ssqcd_lattice lat, int N, const double2* z_host, int L, const
     if constexpr (kFP32) {
       if (lat->precision == SSQCD_MIXED)
         cg_stencil_kernel<<<grid_a, kStencilThreads, 0, st>>>(
-            c, L, g, Stencil32<LinksF16>{LinksF16{lat->u16.as<uint2>(), g.V}}, sigma, p.as<V2>(), q.as<V2>());
+            c, L, g, Stencil32<LinksF16>{LinksF16{lat->u16.as<uint2>(), g.V}}, sigma, p.as<VR>(), q.as<VR>());
       else
         cg_stencil_kernel<<<grid_a, kStencilThreads, 0, st>>>(
-            c, L, g, Stencil32<LinksF32>{LinksF32{lat->u32.as<float4>(), g.V}}, sigma, p.as<V2>(), q.as<V2>());
+            c, L, g, Stencil32<LinksF32>{LinksF32{lat->u32.as<float4>(), g.V}}, sigma, p.as<VR>(), q.as<VR>());
     } else {
       cg_stencil_kernel<<<grid_a, kStencilThreads, 0, st>>>(c, L, g, Stencil64{lat->u64.as<double2>()}, sigma,
-                                                             p.as<V2>(), q.as<V2>());
+                                                             p.as<VR>(), q.as<VR>());
     }
     mark(it, 1);
     mark(it, 2);
-    cg_seed_kernel<V2><<<grid_b, kSeedBlock, 0, st>>>(c, L, N, tol2, r.as<V2>(), q.as<V2>(), p.as<V2>(), n,
+    cg_seed_kernel<VR><<<grid_b, kSeedBlock, 0, st>>>(c, L, N, tol2, r.as<VR>(), q.as<VR>(), p.as<VR>(), n,
                                                       rescale_below, rescale_by);
     mark(it, 3);
     mark(it, 4);
-    launch_update<V2>(ept, grid_c, st, c, N, r.as<V2>(), p.as<V2>(), yv, ph.as<V2>(), n);
+    launch_update<VR, V2>(ept, grid_c, st, c, N, r.as<VR>(), p.as<VR>(), yv, ph.as<V2>(), n);
     mark(it, 5);
   };
   // A chunk of iterations is captured once as a CUDA graph and replayed (the
@@ -872,7 +883,7 @@ int run_shifted_cg(ssqcd_lattice lat, int N, const double2* z_host, int L, const
       int s1 = wilson64(g, lat->u64.as<double2>(), c.x, kx.as<double2>(), L, sigma, -1.0, nullptr, nullptr, st);
       if (s1 != SSQCD_OK) { status = s1; break; }
       const double floor2 = lat->precision == SSQCD_MIXED ? 1e-4 : 1e-10;  // (1e-2 / 1e-5 of ||v||)^2
-      cg_reliable_kernel<V2><<<grid_b, kSeedBlock, 0, st>>>(c, L, v, kx.as<double2>(), r.as<V2>(), n, floor2);
+      cg_reliable_kernel<VR><<<grid_b, kSeedBlock, 0, st>>>(c, L, v, kx.as<double2>(), r.as<VR>(), n, floor2);
       count_launches(1);
     }
     // live-shift count after the last iteration, and the error flag
@@ -899,7 +910,7 @@ int run_shifted_cg(ssqcd_lattice lat, int N, const double2* z_host, int L, const
   }
   if (gexec != nullptr) cudaGraphExecDestroy(gexec);
   if (status == SSQCD_OK || status == SSQCD_ERR_BREAKDOWN || status == SSQCD_ERR_NOCONV) {
-    if (kFP32) {  // hand FP64 solutions to the FP64 moments and Rayleigh-Ritz
+    if (kShift32) {  // hand FP64 solutions to the FP64 moments and Rayleigh-Ritz
       SS_TRY(y_out.alloc(sizeof(double2) * n * NL));
       SS_TRY(convert_f32_to_f64(reinterpret_cast<const float2*>(yv), y_out.as<double2>(), n * NL, st));
     }
@@ -943,17 +954,21 @@ int run_shifted_cg(ssqcd_lattice lat, int N, const double2* z_host, int L, const
 int shifted_cg_device(ssqcd_lattice lat, int N, const double2* z_host, int L, const double2* v, double sigma,
                       double tol, int max_iter, int precision, int reliable_every, DevBuf& y, int* iters_host,
                       double2* xi_host, ShiftedCGOut* out) {
-  if (precision != SSQCD_FP64 && !is_mixed(precision)) return fail(SSQCD_ERR_ARG, "unknown precision");
+  if (precision != SSQCD_FP64 && precision != SSQCD_FP64_SHIFT32 && !is_mixed(precision))
+    return fail(SSQCD_ERR_ARG, "unknown precision");
   if (is_mixed(precision) && precision != lat->precision)
     return fail(SSQCD_ERR_ARG, "a mixed-precision solve needs a lattice created with that precision");
   if (N < 1 || N > kMaxShifts) return fail(SSQCD_ERR_ARG, "N must be in [1, 512]");
   if (L < 1 || L > kMaxSources || N * L > kMaxTotal)
     return fail(SSQCD_ERR_ARG, "L must be in [1, 64] and N * L <= 1024");
   if (precision == SSQCD_FP64)
-    return run_shifted_cg<double2>(lat, N, z_host, L, v, sigma, tol, max_iter, precision, 0, y, iters_host, xi_host,
-                                   out);
-  return run_shifted_cg<float2>(lat, N, z_host, L, v, sigma, tol, max_iter, precision, reliable_every, y, iters_host,
-                                xi_host, out);
+    return run_shifted_cg<double2, double2>(lat, N, z_host, L, v, sigma, tol, max_iter, precision, 0, y, iters_host,
+                                            xi_host, out);
+  if (precision == SSQCD_FP64_SHIFT32)
+    return run_shifted_cg<double2, float2>(lat, N, z_host, L, v, sigma, tol, max_iter, precision, 0, y, iters_host,
+                                           xi_host, out);
+  return run_shifted_cg<float2, float2>(lat, N, z_host, L, v, sigma, tol, max_iter, precision, reliable_every, y,
+                                        iters_host, xi_host, out);
 }
 
 }  // namespace ssqcd

@@ -117,3 +117,35 @@ def test_reliable_updates_keep_the_solve_valid(ss, precision):
     assert len(ev) == len(exact) == 8
     assert np.max(np.abs(ev - exact) / exact) <= 1e-6
     assert st["reliable_updates"] >= 1
+
+
+def test_fp64_seed_fp32_shift_vectors_against_oracle(ss):
+    # SSQCD_FP64_SHIFT32 keeps the operator and the seed recurrence in FP64
+    # and stores y and p-hat in FP32: the true residual then exceeds tol by at
+    # most the FP32 rounding of the updates, ~ iterations x eps32 x ||zI - A|| x ||y||.
+    import torch
+    dims, kappa, bc, N, L = (4, 4, 4, 4), 0.13, -1, 8, 2
+    U = synthetic.gauge_field(dims, "haar", seed=7)
+    v = synthetic.gaussian_sources(dims, L, seed=8)
+    z = contour.line_nodes(0.38, 0.02, 0.5, N)
+    tol = 1e-6
+    lat = ss.create_lattice(dims, kappa, bc, precision=ss.FP64, stream=torch.cuda.Stream())
+    ss.upload_gauge(lat, U)
+    code, y, iters, xi, seed_iters = ss.shifted_cg(lat, z, v, tol=tol, precision=ss.FP64_SHIFT32)
+    assert code == ss.OK
+    code64, y64, iters64, _, seed64 = ss.shifted_cg(lat, z, v, tol=tol, precision=ss.FP64)
+    assert code64 == ss.OK
+    # the seed recurrence is the FP64 one: identical stopping iterations
+    assert seed_iters == seed64
+    assert np.array_equal(iters, iters64)
+    A = lambda x: wilson.apply_H(U, x, kappa, dims, bc)
+    for l in range(L):
+        ref = oscg.shifted_cg(A, v[l], z, tol=tol)
+        vn = np.linalg.norm(v[l])
+        for j in range(N):
+            r_gpu = v[l] - (z[j] * y[l, j] - A(y[l, j]))
+            r_orc = v[l] - (z[j] * ref["y"][j] - A(ref["y"][j]))
+            drift = 4 * int(iters[l, j]) * EPS32 * (abs(z[j]) + 1 + 8 * kappa) * np.linalg.norm(y[l, j])
+            assert np.linalg.norm(r_gpu) <= tol * vn + drift
+            bound = (np.linalg.norm(r_gpu) + np.linalg.norm(r_orc)) / abs(z[j].imag)
+            assert np.linalg.norm(y[l, j] - ref["y"][j]) <= bound * (1 + 1e-6)
