@@ -53,6 +53,9 @@ extern "C" {
 #define SSQCD_MIXED_F32LINKS 2  /* as SSQCD_MIXED with FP32 12-parameter links */
 #define SSQCD_FP64_SHIFT32 3    /* FP64 links, stencil and seed recurrence; the
                                    per-shift vectors y and p-hat in FP32       */
+#define SSQCD_FP64_DFSHIFT 4    /* as SSQCD_FP64_SHIFT32 with y and p-hat in
+                                   float-float (hi + lo FP32 pair, 48-bit
+                                   significand) updated on the FP32 pipes      */
 
 /* ---- contour shapes --------------------------------------------------------- */
 #define SSQCD_PATH_LINES  0  /* L+-: z = gamma + rho (x +- i beta), Section 3      */
@@ -116,8 +119,7 @@ typedef struct {
 
 /* Create a lattice of extents dims[4] with hopping parameter kappa and time
  * boundary sign bc_t (+1 periodic, -1 antiperiodic), for the given precision
- * (one of the SSQCD_FP64 / SSQCD_MIXED / SSQCD_MIXED_F32LINKS / SSQCD_FP64_SHIFT32
- * codes; ssqcd_ss_solve runs its loop in it); every extent must be >= 1 and V <= 2^27.  cuda_stream is a
+ * (one of the precision codes above; ssqcd_ss_solve runs its loop in it); every extent must be >= 1 and V <= 2^27.  cuda_stream is a
  * cudaStream_t (NULL = legacy default stream) on which all later work runs.
  * The operator is Section 4's A = gamma5 (I - kappa D).  On success *out owns
  * the gauge storage (no field until ssqcd_upload_gauge). */
@@ -169,8 +171,8 @@ int ssqcd_contour(int path, double gamma, double rho, double beta, int N, double
  * iters [L][N] int, the iteration at which each shift stopped; xi [L][N]
  * complex128, its final xi.  *seed_iters (may be NULL) receives the number of
  * seed iterations.  precision is one of the precision codes above; the two
- * mixed ones need a lattice created with that code, SSQCD_FP64 and
- * SSQCD_FP64_SHIFT32 run on any lattice (reliable_every as in ssqcd_opts).
+ * mixed ones need a lattice created with that code, the others run on any
+ * lattice (reliable_every as in ssqcd_opts).
  * Returns SSQCD_ERR_BREAKDOWN or SSQCD_ERR_NOCONV when the loop cannot finish
  * (outputs then hold the last iterate). */
 int ssqcd_shifted_cg(ssqcd_lattice lat, int N, const double* z, int L, const double* v,

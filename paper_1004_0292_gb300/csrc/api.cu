@@ -70,8 +70,7 @@ extern "C" int ssqcd_create_lattice(const int dims[4], double kappa, int bc_t, i
   }
   if (V > (1LL << 27)) return fail(SSQCD_ERR_ARG, "lattice volume above 2^27 sites");
   if (bc_t != 1 && bc_t != -1) return fail(SSQCD_ERR_ARG, "bc_t must be +1 or -1");
-  if (precision != SSQCD_FP64 && precision != SSQCD_FP64_SHIFT32 && !is_mixed(precision))
-    return fail(SSQCD_ERR_ARG, "unknown precision");
+  if (!valid_precision(precision)) return fail(SSQCD_ERR_ARG, "unknown precision");
   if (!std::isfinite(kappa)) return fail(SSQCD_ERR_ARG, "kappa must be finite");
   int dev = 0;
   SS_CUDA(cudaGetDevice(&dev));

@@ -143,6 +143,10 @@ struct ShiftedCGOut {
 };
 bool kernel_timing_enabled();
 inline bool is_mixed(int precision) { return precision == SSQCD_MIXED || precision == SSQCD_MIXED_F32LINKS; }
+inline bool valid_precision(int precision) {
+  return precision == SSQCD_FP64 || precision == SSQCD_FP64_SHIFT32 || precision == SSQCD_FP64_DFSHIFT ||
+         is_mixed(precision);
+}
 // Solves for L sources already packed on device (v: [L][12][V]); y out
 // [L][N][12][V] (device, FP64).  iters/xi: host arrays [L*N] (may be null).
 int shifted_cg_device(ssqcd_lattice lat, int N, const double2* z_host, int L, const double2* v,

@@ -43,8 +43,10 @@
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
+#include <type_traits>
 #include <vector>
 
+#include "floatfloat.cuh"
 #include "wilson_core.cuh"
 
 namespace ssqcd {
@@ -58,7 +60,8 @@ struct SeedState {
   double alpha_prev;  // alpha_{k-1}
   double beta_prev;   // beta_{k-1}
   double beta;        // beta_k (valid after kernel B of iteration k)
-  double scale;       // power of two applied to r and p by kernel C of this iteration
+  double scale;       // power of two applied to p by kernel C of this iteration and to r
+                      // by kernel B of the next (C reads r scaled in registers)
   double pad[3];      // pad[0] = 1 / rr, pad[1] = S = product of all scales so far
 };
 
@@ -115,20 +118,28 @@ __device__ __forceinline__ double warp_sum(double v) {
 // range, so they need no overflow guards.
 
 // ---- initialisation ---------------------------------------------------------------
+// A shift vector element from an FP64 complex: FP64, FP32 (rounded) or
+// float-float (hi + lo).
+__device__ __forceinline__ void put_shift(double2& d, double2 x) { d = x; }
+__device__ __forceinline__ void put_shift(float2& d, double2 x) {
+  d = make_float2(__double2float_rn(x.x), __double2float_rn(x.y));
+}
+__device__ __forceinline__ void put_shift(float4& d, double2 x) { d = ff::from_double2(x); }
+
 template <typename VR, typename V2>
 __global__ void init_vectors_kernel(const double2* __restrict__ v, VR* __restrict__ r, VR* __restrict__ p,
                                     V2* __restrict__ y, V2* __restrict__ ph, int N, long long n) {
-  using T = decltype(V2::x);
   using TR = decltype(VR::x);
   const int l = blockIdx.y;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
     const double2 xd = v[l * n + e];
     const VR xr{(TR)xd.x, (TR)xd.y};
-    const V2 x{(T)xd.x, (T)xd.y};
+    V2 x;
+    put_shift(x, xd);
     r[l * n + e] = xr;
     p[l * n + e] = xr;
     for (int j = 0; j < N; ++j) {
-      y[((long long)l * N + j) * n + e] = V2{0, 0};
+      y[((long long)l * N + j) * n + e] = V2{};
       ph[((long long)l * N + j) * n + e] = x;
     }
   }
@@ -347,12 +358,13 @@ cg_seed_kernel(Control c, int L, int N, double tol2, V2* __restrict__ r, const V
     const double ax = c.x != nullptr ? alpha / c.seed[l].pad[1] : 0.0;
     using T = decltype(V2::x);
     const T af = (T)alpha;
+    const T sc = (T)c.seed[l].scale;  // rescale of r decided last iteration (exact power of two)
     const long long stride = (long long)gridDim.x * kSeedBlock;
     auto one = [&](long long e, double& acc) {
       V2 x0 = rl[e];
       const V2 y0 = ql[e];
-      x0.x = fma(-af, y0.x, x0.x);
-      x0.y = fma(-af, y0.y, x0.y);
+      x0.x = fma(-af, y0.x, sc * x0.x);
+      x0.y = fma(-af, y0.y, sc * x0.y);
       rl[e] = x0;
       const double xr = x0.x, xi = x0.y;
       acc = fma(xr, xr, fma(xi, xi, acc));
@@ -416,7 +428,10 @@ cg_seed_kernel(Control c, int L, int N, double tol2, V2* __restrict__ r, const V
       const bool live = (xn.x * xn.x + xn.y * xn.y) * rr1 > tol2 * c.vnorm2[ls];
       flag = live ? 2 : 1;
       c.xi_prev[qi] = make_double2(xc.x * inv_sc, xc.y * inv_sc);
-      c.xi_cur[qi] = make_double2(xn.x * inv_sc, xn.y * inv_sc);
+      // a freezing shift leaves its unscaled xi (xi_{k+1} S, S = product of
+      // the scales so far); a live one keeps it in the scale of r
+      const double S = live ? inv_sc : c.seed[ls].pad[1];
+      c.xi_cur[qi] = make_double2(xn.x * S, xn.y * S);
       c.act[qi] = live ? 1 : 0;
       c.iters[qi] += 1;
     }
@@ -462,9 +477,10 @@ cg_seed_kernel(Control c, int L, int N, double tol2, V2* __restrict__ r, const V
 // ---- C. fused multi-shift update -------------------------------------------------------
 // Thread per EPT elements (stride blockDim) of one source; the block stages
 // its source's list of shifts in shared memory and every thread walks it, two
-// shifts at a time, so each lane keeps 4 EPT loads in flight.  r is rescaled
-// in place when kernel B chose a scale; then p = r + beta p.  V2 = double2
-// (FP64 path: bound by the FP64 pipe) or float2 (mixed path: bound by HBM).
+// shifts at a time, so each lane keeps 4 EPT loads in flight.  r is only read
+// (times the scale kernel B chose, in registers; kernel B of the next
+// iteration applies that scale to the stored r); then p = r + beta p.  V2 =
+// double2 (FP64 path: bound by the FP64 pipe) or float2 (bound by HBM).
 template <typename T>
 struct alignas(4 * sizeof(T)) Coef4 {
   T x, y, z, w;  // a.x, -a.y, b.x, -b.y (imaginary parts negated once per block)
@@ -472,7 +488,7 @@ struct alignas(4 * sizeof(T)) Coef4 {
 
 template <typename VR, typename V2, int EPT>
 __global__ void __launch_bounds__(kUpdBlock)
-cg_update_kernel(Control c, int N, VR* __restrict__ r, VR* __restrict__ p, V2* __restrict__ y,
+cg_update_kernel(Control c, int N, const VR* __restrict__ r, VR* __restrict__ p, V2* __restrict__ y,
                  V2* __restrict__ ph, long long n) {
   using T = decltype(V2::x);    // shift vectors (y, p-hat)
   using TR = decltype(VR::x);   // seed vectors (r, p)
@@ -494,7 +510,7 @@ cg_update_kernel(Control c, int N, VR* __restrict__ r, VR* __restrict__ p, V2* _
   __syncthreads();
   const TR sc = (TR)c.seed[l].scale;  // exact power of two, usually 1
   const TR beta = (TR)(c.seed[l].scale * c.seed[l].beta);
-  VR* rl = r + (long long)l * n;
+  const VR* rl = r + (long long)l * n;
   VR* pl = p + (long long)l * n;
   V2* yl = y + (long long)l * N * n;
   V2* hl = ph + (long long)l * N * n;
@@ -506,10 +522,7 @@ cg_update_kernel(Control c, int N, VR* __restrict__ r, VR* __restrict__ p, V2* _
     for (int i = 0; i < EPT; ++i) {
       const long long e = base + (long long)i * kUpdBlock;
       VR x = e < n ? rl[e] : VR{0, 0};
-      if (sc != (TR)1) {
-        x = VR{sc * x.x, sc * x.y};
-        if (e < n) rl[e] = x;
-      }
+      x = VR{sc * x.x, sc * x.y};
       rs[i] = x;
       rv[i] = V2{(T)x.x, (T)x.y};
     }
@@ -587,6 +600,120 @@ cg_update_kernel(Control c, int N, VR* __restrict__ r, VR* __restrict__ p, V2* _
   }
 }
 
+// ---- fused update, float-float shift vectors ---------------------------------------------
+// Kernel C of SSQCD_FP64_DFSHIFT: the seed vectors r, p stay FP64; y_j and
+// p-hat_j are complex float-float (float4 {re.hi, im.hi, re.lo, im.lo}, 16
+// bytes like an FP64 complex).  Work unit = (chunk of kUpdBlock * EPT
+// elements, source, group of kDfGroup listed shifts): blockIdx = (chunk,
+// source, group).  Blocks are short-lived and many (~5 waves at the 8^4
+// size), so no wave runs nearly empty; r is re-read once per group (1/16 of
+// the shift traffic at 8 shifts a group) and group 0 also does p = r + beta p.
+// The coefficients a_j, b_j (FP64, from kernel B) and r are split to
+// float-float once per block / per element; each shift then costs two
+// complex float-float multiply-adds on the FP32 pipes.
+constexpr int kDfGroup = 8;
+
+template <int EPT>
+__global__ void __launch_bounds__(kUpdBlock)
+cg_update_df_kernel(Control c, int N, const double2* __restrict__ r, double2* __restrict__ p,
+                    float4* __restrict__ y, float4* __restrict__ ph, long long n) {
+  if (*c.ran == 0) return;
+  const int l = blockIdx.y;
+  const int m = c.list_n[l];
+  const int t0 = blockIdx.z * kDfGroup, t1 = min(m, t0 + kDfGroup);
+  const bool do_p = blockIdx.z == 0 && c.live[l] != 0;
+  if (t1 <= t0 && !do_p) return;
+  __shared__ int s_j[kDfGroup];
+  __shared__ float4 s_a[kDfGroup], s_b[kDfGroup];
+  if (threadIdx.x < kDfGroup && t0 + (int)threadIdx.x < t1) {
+    const int t = t0 + threadIdx.x;
+    s_j[threadIdx.x] = c.list_j[l * N + t];
+    s_a[threadIdx.x] = ff::from_double2(c.list_a[l * N + t]);
+    s_b[threadIdx.x] = ff::from_double2(c.list_b[l * N + t]);
+  }
+  __syncthreads();
+  const int mg = max(0, t1 - t0);
+  const double sc = c.seed[l].scale;  // exact power of two, usually 1
+  const double beta = c.seed[l].scale * c.seed[l].beta;
+  const double2* rl = r + (long long)l * n;
+  double2* pl = p + (long long)l * n;
+  float4* yl = y + (long long)l * N * n;
+  float4* hl = ph + (long long)l * N * n;
+  const long long base = blockIdx.x * (long long)kUpdBlock * EPT + threadIdx.x;
+  double2 rs[EPT];
+  float4 rv[EPT];
+#pragma unroll
+  for (int i = 0; i < EPT; ++i) {
+    const long long e = base + (long long)i * kUpdBlock;
+    const double2 x = e < n ? rl[e] : make_double2(0.0, 0.0);
+    rs[i] = make_double2(sc * x.x, sc * x.y);
+    rv[i] = ff::from_double2(rs[i]);
+  }
+  int t = 0;
+  for (; t + 2 <= mg; t += 2) {
+    const float4 a0 = s_a[t], b0 = s_b[t], a1 = s_a[t + 1], b1 = s_b[t + 1];
+    float4* y0 = yl + (long long)s_j[t] * n;
+    float4* h0 = hl + (long long)s_j[t] * n;
+    float4* y1 = yl + (long long)s_j[t + 1] * n;
+    float4* h1 = hl + (long long)s_j[t + 1] * n;
+    float4 yv0[EPT], hv0[EPT], yv1[EPT], hv1[EPT];
+#pragma unroll
+    for (int i = 0; i < EPT; ++i) {
+      const long long e = base + (long long)i * kUpdBlock;
+      if (e < n) {
+        yv0[i] = y0[e];
+        hv0[i] = h0[e];
+        yv1[i] = y1[e];
+        hv1[i] = h1[e];
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < EPT; ++i) {
+      const long long e = base + (long long)i * kUpdBlock;
+      if (e < n) {
+        y0[e] = ff::cfma(yv0[i], a0, hv0[i]);
+        h0[e] = ff::cfma(rv[i], b0, hv0[i]);
+        y1[e] = ff::cfma(yv1[i], a1, hv1[i]);
+        h1[e] = ff::cfma(rv[i], b1, hv1[i]);
+      }
+    }
+  }
+  if (t < mg) {
+    const float4 a0 = s_a[t], b0 = s_b[t];
+    float4* y0 = yl + (long long)s_j[t] * n;
+    float4* h0 = hl + (long long)s_j[t] * n;
+#pragma unroll
+    for (int i = 0; i < EPT; ++i) {
+      const long long e = base + (long long)i * kUpdBlock;
+      if (e < n) {
+        const float4 yv = y0[e], hv = h0[e];
+        y0[e] = ff::cfma(yv, a0, hv);
+        h0[e] = ff::cfma(rv[i], b0, hv);
+      }
+    }
+  }
+  if (do_p) {
+#pragma unroll
+    for (int i = 0; i < EPT; ++i) {
+      const long long e = base + (long long)i * kUpdBlock;
+      if (e < n) {
+        double2 pe = pl[e];
+        pe.x = fma(beta, pe.x, rs[i].x);
+        pe.y = fma(beta, pe.y, rs[i].y);
+        pl[e] = pe;
+      }
+    }
+  }
+}
+
+// In-place conversion of float-float solutions to FP64 (same element size).
+__global__ void df_to_f64_kernel(float4* __restrict__ y, long long count) {
+  double2* out = reinterpret_cast<double2*>(y);
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < count;
+       e += (long long)gridDim.x * blockDim.x)
+    out[e] = ff::to_double2(y[e]);
+}
+
 // ---- reliable update (mixed precision) -------------------------------------------------
 // r = S (v - K x) from the FP64 seed solution x and kx = K x (FP64 stencil),
 // replacing the FP32 recursive residual while ||r|| is above sqrt(floor2)
@@ -594,7 +721,8 @@ cg_update_kernel(Control c, int N, VR* __restrict__ r, VR* __restrict__ p, V2* _
 // the difference between it and the reduced-precision operator the
 // recursion uses (~3e-4 relative with FP16 links, ~1e-7 with FP32 links), and
 // replacing r would break the Krylov recurrence the shifted systems are
-// built on; the last block stores (r, r) and its reciprocal.
+// built on; the last block stores (r, r) and its reciprocal.  The stored r is
+// divided by the scale chosen in the last iteration, which kernel B applies.
 template <typename V2>
 __global__ void __launch_bounds__(kSeedBlock)
 cg_reliable_kernel(Control c, int L, const double2* __restrict__ v, const double2* __restrict__ kx,
@@ -605,6 +733,7 @@ cg_reliable_kernel(Control c, int L, const double2* __restrict__ v, const double
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const SeedState sd = c.seed[l];
   const double S = sd.pad[1];
+  const double inv_pending = 1.0 / sd.scale;  // kernel B applies sd.scale to the stored r
   const bool apply = c.live[l] != 0 && sd.rr > floor2 * S * S * c.vnorm2[l];
   double acc = 0.0;
   if (apply) {
@@ -615,7 +744,7 @@ cg_reliable_kernel(Control c, int L, const double2* __restrict__ v, const double
     for (long long e = blockIdx.x * (long long)kSeedBlock + threadIdx.x; e < n; e += (long long)gridDim.x * kSeedBlock) {
       const double2 a = vl[e], b = kl[e];
       const double tx = S * (a.x - b.x), ty = S * (a.y - b.y);
-      rl[e] = V2{(T)tx, (T)ty};
+      rl[e] = V2{(T)(tx * inv_pending), (T)(ty * inv_pending)};
       acc = fma(tx, tx, fma(ty, ty, acc));
     }
   }
@@ -658,25 +787,38 @@ int seed_blocks(long long n, int L) {
   return (int)(b < 1 ? 1 : b);
 }
 
-// Elements per thread of the update kernel: 1 for the FP64 path (its FP64
-// pipe, not memory, is the limit; measured 1 > 2 > 4), 2 for FP32.  The
-// environment variable SSQCD_UPDATE_EPT overrides it for tuning runs.
-int update_epts(bool fp32) {
+// Elements per thread of the update kernel: 1 for FP64 shift vectors (the
+// FP64 pipe, not memory, is the limit; measured 1 > 2 > 4), 2 for the
+// memory-bound FP32 and float-float ones.  The environment variable
+// SSQCD_UPDATE_EPT overrides it for tuning runs.
+int update_epts(bool memory_bound) {
   static int v = [] {
     const char* e = std::getenv("SSQCD_UPDATE_EPT");
     const int x = e ? std::atoi(e) : 0;
     return (x == 1 || x == 2 || x == 4) ? x : 0;
   }();
-  return v != 0 ? v : (fp32 ? 2 : 1);
+  return v != 0 ? v : (memory_bound ? 2 : 1);
 }
 
 template <typename VR, typename V2>
-int launch_update(int ept, dim3 grid, cudaStream_t st, const Control& c, int N, VR* r, VR* p, V2* y, V2* ph,
+int launch_update(int ept, dim3 grid, cudaStream_t st, const Control& c, int N, const VR* r, VR* p, V2* y, V2* ph,
                   long long n) {
   switch (ept) {
     case 1: cg_update_kernel<VR, V2, 1><<<grid, kUpdBlock, 0, st>>>(c, N, r, p, y, ph, n); break;
     case 2: cg_update_kernel<VR, V2, 2><<<grid, kUpdBlock, 0, st>>>(c, N, r, p, y, ph, n); break;
     default: cg_update_kernel<VR, V2, 4><<<grid, kUpdBlock, 0, st>>>(c, N, r, p, y, ph, n); break;
+  }
+  return SSQCD_OK;
+}
+
+int launch_update_df(int ept, int L, cudaStream_t st, const Control& c, int N, const double2* r, double2* p,
+                     float4* y, float4* ph, long long n) {
+  const long long chunks = (n + (long long)kUpdBlock * ept - 1) / ((long long)kUpdBlock * ept);
+  const dim3 grid((unsigned)chunks, L, (N + kDfGroup - 1) / kDfGroup);
+  switch (ept) {
+    case 1: cg_update_df_kernel<1><<<grid, kUpdBlock, 0, st>>>(c, N, r, p, y, ph, n); break;
+    case 2: cg_update_df_kernel<2><<<grid, kUpdBlock, 0, st>>>(c, N, r, p, y, ph, n); break;
+    default: cg_update_df_kernel<4><<<grid, kUpdBlock, 0, st>>>(c, N, r, p, y, ph, n); break;
   }
   return SSQCD_OK;
 }
@@ -693,26 +835,29 @@ namespace {
 
 // The solve loop for one precision: VR is the type of the seed vectors (r, p,
 // q and the stencil), V2 that of the shift vectors (y, p-hat): double2 /
-// double2 (SSQCD_FP64), double2 / float2 (SSQCD_FP64_SHIFT32), float2 /
-// float2 (the mixed precisions).  y_out always receives FP64 solutions.
+// double2 (SSQCD_FP64), double2 / float2 (SSQCD_FP64_SHIFT32), double2 /
+// float4 = complex float-float (SSQCD_FP64_DFSHIFT), float2 / float2 (the
+// mixed precisions).  y_out always receives FP64 solutions.
 template <typename VR, typename V2>
 int run_shifted_cg(ssqcd_lattice lat, int N, const double2* z_host, int L, const double2* v, double sigma,
                    double tol, int max_iter, int precision, int reliable_every, DevBuf& y_out, int* iters_host,
                    double2* xi_host, ShiftedCGOut* out) {
   constexpr bool kFP32 = sizeof(VR) == sizeof(float2);      // seed vectors and stencil in FP32
   constexpr bool kShift32 = sizeof(V2) == sizeof(float2);   // shift vectors in FP32
+  constexpr bool kShiftDF = std::is_same<V2, float4>::value; // shift vectors in float-float
   cudaStream_t st = lat->stream;
   const Geometry& g = lat->g;
   const long long n = 12LL * g.V;
   const int NL = N * L;
   const int nbw = wilson_blocks(g);
   const int nbs = seed_blocks(n, L);
-  const int ept = update_epts(kShift32);
+  const int ept = update_epts(kShift32 || kShiftDF);
   const int nbu = update_blocks(n, L, ept);
-  // FP32 keeps ||r|| within 2^-20 of ||v|| (its elements stay far above the
+  // r enters p-hat: with FP32 exponents (FP32 or float-float shift vectors)
+  // ||r|| is kept within 2^-20 of ||v|| (its elements stay far above the
   // FP32 underflow); FP64 within 2^-200.
-  const double rescale_below = kShift32 ? 0x1p-40 : 0x1p-400;
-  const double rescale_by = kShift32 ? 0x1p+20 : 0x1p+200;
+  const double rescale_below = (kShift32 || kShiftDF) ? 0x1p-40 : 0x1p-400;
+  const double rescale_by = (kShift32 || kShiftDF) ? 0x1p+20 : 0x1p+200;
 
   DevBuf r, p, q, ph, y32, x, kx;
   SS_TRY(r.alloc(sizeof(VR) * n * L));
@@ -731,7 +876,8 @@ int run_shifted_cg(ssqcd_lattice lat, int N, const double2* z_host, int L, const
       SS_CUDA(cudaMemsetAsync(x.p, 0, sizeof(double2) * n * L, st));
     }
   }
-  if (!kShift32) {
+  if (!kShift32) {  // FP64 solutions, or float-float ones converted in place at the end
+    static_assert(kShift32 || sizeof(V2) == sizeof(double2), "in-place conversion needs equal element sizes");
     SS_TRY(y_out.alloc(sizeof(double2) * n * NL));
     yv = reinterpret_cast<V2*>(y_out.p);
   }
@@ -836,7 +982,10 @@ int run_shifted_cg(ssqcd_lattice lat, int N, const double2* z_host, int L, const
                                                       rescale_below, rescale_by);
     mark(it, 3);
     mark(it, 4);
-    launch_update<VR, V2>(ept, grid_c, st, c, N, r.as<VR>(), p.as<VR>(), yv, ph.as<V2>(), n);
+    if constexpr (kShiftDF)
+      launch_update_df(ept, L, st, c, N, r.as<double2>(), p.as<double2>(), yv, ph.as<float4>(), n);
+    else
+      launch_update<VR, V2>(ept, grid_c, st, c, N, r.as<VR>(), p.as<VR>(), yv, ph.as<V2>(), n);
     mark(it, 5);
   };
   // A chunk of iterations is captured once as a CUDA graph and replayed (the
@@ -913,14 +1062,32 @@ int run_shifted_cg(ssqcd_lattice lat, int N, const double2* z_host, int L, const
     if (kShift32) {  // hand FP64 solutions to the FP64 moments and Rayleigh-Ritz
       SS_TRY(y_out.alloc(sizeof(double2) * n * NL));
       SS_TRY(convert_f32_to_f64(reinterpret_cast<const float2*>(yv), y_out.as<double2>(), n * NL, st));
+    } else if (kShiftDF) {
+      const long long cnt = n * NL;
+      const int nb = (int)std::max(1LL, std::min((cnt + 255) / 256, 152LL * 16));
+      df_to_f64_kernel<<<nb, 256, 0, st>>>(reinterpret_cast<float4*>(yv), cnt);
+      SS_CHECK_LAUNCH();
+      count_launches(1);
     }
     SS_CUDA(cudaEventRecord(e1, st));
     int counters[2] = {0, 0};
     std::vector<int> it_all(NL);
     SS_CUDA(cudaMemcpyAsync(counters, c.seed_iters, sizeof(int) * 2, cudaMemcpyDeviceToHost, st));
     SS_CUDA(cudaMemcpyAsync(it_all.data(), c.iters, sizeof(int) * NL, cudaMemcpyDeviceToHost, st));
-    if (xi_host) SS_CUDA(cudaMemcpyAsync(xi_host, c.xi_cur, sizeof(double2) * NL, cudaMemcpyDeviceToHost, st));
+    std::vector<int> act_all(xi_host ? NL : 0);
+    std::vector<SeedState> seed_all(xi_host ? L : 0);
+    if (xi_host) {
+      SS_CUDA(cudaMemcpyAsync(xi_host, c.xi_cur, sizeof(double2) * NL, cudaMemcpyDeviceToHost, st));
+      SS_CUDA(cudaMemcpyAsync(act_all.data(), c.act, sizeof(int) * NL, cudaMemcpyDeviceToHost, st));
+      SS_CUDA(cudaMemcpyAsync(seed_all.data(), c.seed, sizeof(SeedState) * L, cudaMemcpyDeviceToHost, st));
+    }
     SS_CUDA(cudaStreamSynchronize(st));
+    if (xi_host)  // shifts still live at the end hold xi / S
+      for (int qi = 0; qi < NL; ++qi)
+        if (act_all[qi]) {
+          const double S = seed_all[qi / N].pad[1];
+          xi_host[qi] = make_double2(xi_host[qi].x * S, xi_host[qi].y * S);
+        }
     if (iters_host) std::copy(it_all.begin(), it_all.end(), iters_host);
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
@@ -954,8 +1121,7 @@ int run_shifted_cg(ssqcd_lattice lat, int N, const double2* z_host, int L, const
 int shifted_cg_device(ssqcd_lattice lat, int N, const double2* z_host, int L, const double2* v, double sigma,
                       double tol, int max_iter, int precision, int reliable_every, DevBuf& y, int* iters_host,
                       double2* xi_host, ShiftedCGOut* out) {
-  if (precision != SSQCD_FP64 && precision != SSQCD_FP64_SHIFT32 && !is_mixed(precision))
-    return fail(SSQCD_ERR_ARG, "unknown precision");
+  if (!valid_precision(precision)) return fail(SSQCD_ERR_ARG, "unknown precision");
   if (is_mixed(precision) && precision != lat->precision)
     return fail(SSQCD_ERR_ARG, "a mixed-precision solve needs a lattice created with that precision");
   if (N < 1 || N > kMaxShifts) return fail(SSQCD_ERR_ARG, "N must be in [1, 512]");
@@ -964,6 +1130,9 @@ int shifted_cg_device(ssqcd_lattice lat, int N, const double2* z_host, int L, co
   if (precision == SSQCD_FP64)
     return run_shifted_cg<double2, double2>(lat, N, z_host, L, v, sigma, tol, max_iter, precision, 0, y, iters_host,
                                             xi_host, out);
+  if (precision == SSQCD_FP64_DFSHIFT)
+    return run_shifted_cg<double2, float4>(lat, N, z_host, L, v, sigma, tol, max_iter, precision, 0, y, iters_host,
+                                           xi_host, out);
   if (precision == SSQCD_FP64_SHIFT32)
     return run_shifted_cg<double2, float2>(lat, N, z_host, L, v, sigma, tol, max_iter, precision, 0, y, iters_host,
                                            xi_host, out);
