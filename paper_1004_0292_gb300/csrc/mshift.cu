@@ -44,6 +44,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <type_traits>
+#include <utility>
 #include <vector>
 
 #include "floatfloat.cuh"
@@ -75,7 +76,9 @@ struct Control {
   double* vnorm2;      // [L]
   int* live;           // [L]     shifts still iterating
   int* live_total;     // [1]
-  int* ran;            // [1]     kernel A of this iteration did its work
+  int* ran;            // [1]     kernel A of this iteration did its work (read by B and P)
+  int* rec_ran;        // [2]     the same per iteration parity (read by C, which may run
+                       //         while the next iteration's A rewrites ran)
   int* err;            // [1]
   int* seed_iters;     // [2]     seed iterations, reliable updates applied
   unsigned* done;      // [2]     last-block tickets of kernels A and B
@@ -86,10 +89,13 @@ struct Control {
   double2* ratio;      // [L*N]   xi_{k+1} / xi_k
   int* act;            // [L*N]
   int* iters;          // [L*N]
-  int* list_n;         // [L]     shifts updated in this iteration
-  int* list_j;         // [L*N]   their indices, ascending
-  double2* list_a;     // [L*N]   y += a p-hat
-  double2* list_b;     // [L*N]   p-hat = r + b p-hat
+  // the record kernel C reads, double-buffered by iteration parity: C of
+  // iteration k runs beside A, B, P of iteration k + 1
+  int* list_n;         // [2][L]     shifts updated in this iteration
+  int* list_j;         // [2][L*N]   their indices, ascending
+  double2* list_a;     // [2][L*N]   y += a p-hat
+  double2* list_b;     // [2][L*N]   p-hat = r + b p-hat
+  double* list_sc;     // [2][L]     scale of r (power of two) for C
   double* partial;     // [L][nbw]  (p, q) partials of kernel A
   double* partial_rr;  // [L][nbs]  ||r||^2 partials of kernel B
   double2* x;          // [L][n]    FP64 seed solution (mixed precision only, else null)
@@ -153,7 +159,7 @@ __global__ void init_control_kernel(Control c, const double* __restrict__ vn2, i
     c.alpha[t] = 0.0;
     c.vnorm2[t] = vn2[t];
     c.live[t] = vn2[t] > 0.0 ? N : 0;
-    c.list_n[t] = 0;
+    c.list_n[t] = c.list_n[L + t] = 0;
   }
   for (int t = threadIdx.x; t < L * N; t += blockDim.x) {
     c.xi_cur[t] = make_double2(1.0, 0.0);
@@ -166,6 +172,7 @@ __global__ void init_control_kernel(Control c, const double* __restrict__ vn2, i
     for (int l = 0; l < L; ++l) live += vn2[l] > 0.0 ? N : 0;
     *c.live_total = live;
     *c.ran = 0;
+    c.rec_ran[0] = c.rec_ran[1] = 0;
     *c.err = 0;
     c.seed_iters[0] = c.seed_iters[1] = 0;
     c.done[0] = c.done[1] = 0u;
@@ -228,10 +235,10 @@ struct Stencil32 {
 
 template <typename Op, typename V2>
 __global__ void __launch_bounds__(kStencilThreads)
-cg_stencil_kernel(Control c, int L, Geometry g, Op op, double sigma, const V2* __restrict__ p_all,
+cg_stencil_kernel(Control c, int L, int par, Geometry g, Op op, double sigma, const V2* __restrict__ p_all,
                   V2* __restrict__ q_all) {
   if (*c.err != 0 || *c.live_total == 0) {
-    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *c.ran = 0;
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *c.ran = c.rec_ran[par] = 0;
     return;
   }
   __shared__ double2 sh[12 * 4 * 32];
@@ -286,7 +293,7 @@ cg_stencil_kernel(Control c, int L, Geometry g, Op op, double sigma, const V2* _
   __syncthreads();
   if (threadIdx.x == 0) {
     const bool ok = *((volatile int*)c.err) == 0;
-    *c.ran = ok ? 1 : 0;
+    *c.ran = c.rec_ran[par] = ok ? 1 : 0;
     if (ok) atomicAdd(c.seed_iters, 1);
     c.done[0] = 0u;
   }
@@ -306,8 +313,9 @@ cg_stencil_kernel(Control c, int L, Geometry g, Op op, double sigma, const V2* _
 //    warp ballots.
 template <typename V2>
 __global__ void __launch_bounds__(kSeedBlock)
-cg_seed_kernel(Control c, int L, int N, double tol2, V2* __restrict__ r, const V2* __restrict__ q,
-               const V2* __restrict__ p, long long n, double rescale_below, double rescale_by) {
+cg_seed_kernel(Control c, int L, int N, int par, double tol2, const V2* __restrict__ r_in, V2* __restrict__ r_out,
+               const V2* __restrict__ q, const V2* __restrict__ p, long long n, double rescale_below,
+               double rescale_by) {
   if (*c.ran == 0) return;
   __shared__ double sred[kSeedBlock / 32];
   __shared__ double sums[kMaxSources];
@@ -349,7 +357,8 @@ cg_seed_kernel(Control c, int L, int N, double tol2, V2* __restrict__ r, const V
   double acc0 = 0.0, acc1 = 0.0;
   if (c.live[l] != 0) {
     const double alpha = c.alpha[l];
-    V2* rl = r + (long long)l * n;
+    const V2* rl = r_in + (long long)l * n;
+    V2* ro = r_out + (long long)l * n;
     const V2* ql = q + (long long)l * n;
     // mixed precision: the FP64 seed solution x += alpha p / S (S: product of
     // the rescales of r and p so far), for the reliable updates
@@ -365,7 +374,7 @@ cg_seed_kernel(Control c, int L, int N, double tol2, V2* __restrict__ r, const V
       const V2 y0 = ql[e];
       x0.x = fma(-af, y0.x, sc * x0.x);
       x0.y = fma(-af, y0.y, sc * x0.y);
-      rl[e] = x0;
+      ro[e] = x0;
       const double xr = x0.x, xi = x0.y;
       acc = fma(xr, xr, fma(xi, xi, acc));
       if (xl != nullptr) {
@@ -448,15 +457,17 @@ cg_seed_kernel(Control c, int L, int N, double tol2, V2* __restrict__ r, const V
       const unsigned stay = __ballot_sync(0xffffffffu, f == 2);
       if (f) {
         const int pos = m + __popc(upd & ((1u << lane) - 1u));
-        c.list_j[ls * N + pos] = j;
-        c.list_a[ls * N + pos] = s_a[ls * N + j];
-        c.list_b[ls * N + pos] = s_b[ls * N + j];
+        const int o = (par * L + ls) * N + pos;
+        c.list_j[o] = j;
+        c.list_a[o] = s_a[ls * N + j];
+        c.list_b[o] = s_b[ls * N + j];
       }
       m += __popc(upd);
       live += __popc(stay);
     }
     if (lane == 0) {
-      c.list_n[ls] = m;
+      c.list_n[par * L + ls] = m;
+      c.list_sc[par * L + ls] = s_scale[ls];
       if (c.live[ls] != 0) {
         const double sc = s_scale[ls];
         const double rr = sums[ls] * sc * sc;
@@ -474,13 +485,38 @@ cg_seed_kernel(Control c, int L, int N, double tol2, V2* __restrict__ r, const V
   }
 }
 
+// ---- P. seed direction p = s (r + beta p) ------------------------------------------------
+// s: the power of two kernel B chose for this iteration (applied to the
+// stored r by the next iteration's kernel B).  Runs on the main chain right
+// after B, so the next stencil can start while kernel C still updates the
+// shifts.
+template <typename VR>
+__global__ void __launch_bounds__(kUpdBlock)
+cg_seed_p_kernel(Control c, const VR* __restrict__ r, VR* __restrict__ p, long long n) {
+  if (*c.ran == 0) return;
+  const int l = blockIdx.y;
+  if (c.live[l] == 0) return;
+  using TR = decltype(VR::x);
+  const TR sc = (TR)c.seed[l].scale;
+  const TR beta = (TR)(c.seed[l].scale * c.seed[l].beta);
+  const VR* rl = r + (long long)l * n;
+  VR* pl = p + (long long)l * n;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const VR x = rl[e];
+    VR pe = pl[e];
+    pe.x = fma(beta, pe.x, sc * x.x);
+    pe.y = fma(beta, pe.y, sc * x.y);
+    pl[e] = pe;
+  }
+}
+
 // ---- C. fused multi-shift update -------------------------------------------------------
 // Thread per EPT elements (stride blockDim) of one source; the block stages
-// its source's list of shifts in shared memory and every thread walks it, two
-// shifts at a time, so each lane keeps 4 EPT loads in flight.  r is only read
-// (times the scale kernel B chose, in registers; kernel B of the next
-// iteration applies that scale to the stored r); then p = r + beta p.  V2 =
-// double2 (FP64 path: bound by the FP64 pipe) or float2 (bound by HBM).
+// its source's list of shifts (the record of iteration parity par) in shared
+// memory and every thread walks it, two shifts at a time, so each lane keeps
+// 4 EPT loads in flight.  r (the buffer kernel B of the same iteration wrote)
+// is only read, times the record's scale.  V2 = double2 (FP64 path: bound by
+// the FP64 pipe) or float2 (bound by HBM).
 template <typename T>
 struct alignas(4 * sizeof(T)) Coef4 {
   T x, y, z, w;  // a.x, -a.y, b.x, -b.y (imaginary parts negated once per block)
@@ -488,43 +524,38 @@ struct alignas(4 * sizeof(T)) Coef4 {
 
 template <typename VR, typename V2, int EPT>
 __global__ void __launch_bounds__(kUpdBlock)
-cg_update_kernel(Control c, int N, const VR* __restrict__ r, VR* __restrict__ p, V2* __restrict__ y,
-                 V2* __restrict__ ph, long long n) {
+cg_update_kernel(Control c, int N, int par, const VR* __restrict__ r, V2* __restrict__ y, V2* __restrict__ ph,
+                 long long n) {
   using T = decltype(V2::x);    // shift vectors (y, p-hat)
-  using TR = decltype(VR::x);   // seed vectors (r, p)
-  if (*c.ran == 0) return;
-  const int l = blockIdx.y;
-  const int m = c.list_n[l];
-  const bool cont = c.live[l] != 0;
-  if (m == 0 && !cont) return;
+  using TR = decltype(VR::x);   // seed vectors (r)
+  if (c.rec_ran[par] == 0) return;
+  const int l = blockIdx.y, L = gridDim.y;
+  const int m = c.list_n[par * L + l];
+  if (m == 0) return;
   __shared__ int s_j[kMaxShifts];
   __shared__ Coef4<T> s_ab[kMaxShifts];
   __shared__ T s_ay[kMaxShifts], s_by[kMaxShifts];
+  const int o = (par * L + l) * N;
   for (int t = threadIdx.x; t < m; t += blockDim.x) {
-    const double2 a = c.list_a[l * N + t], b = c.list_b[l * N + t];
-    s_j[t] = c.list_j[l * N + t];
+    const double2 a = c.list_a[o + t], b = c.list_b[o + t];
+    s_j[t] = c.list_j[o + t];
     s_ab[t] = Coef4<T>{(T)a.x, (T)-a.y, (T)b.x, (T)-b.y};
     s_ay[t] = (T)a.y;
     s_by[t] = (T)b.y;
   }
   __syncthreads();
-  const TR sc = (TR)c.seed[l].scale;  // exact power of two, usually 1
-  const TR beta = (TR)(c.seed[l].scale * c.seed[l].beta);
+  const TR sc = (TR)c.list_sc[par * L + l];  // exact power of two, usually 1
   const VR* rl = r + (long long)l * n;
-  VR* pl = p + (long long)l * n;
   V2* yl = y + (long long)l * N * n;
   V2* hl = ph + (long long)l * N * n;
   const long long chunk = (long long)kUpdBlock * EPT;
   for (long long base = blockIdx.x * chunk + threadIdx.x; base < n; base += (long long)gridDim.x * chunk) {
-    VR rs[EPT];   // r in the seed precision (for p)
-    V2 rv[EPT];   // r in the shift precision (for p-hat)
+    V2 rv[EPT];   // s r in the shift precision
 #pragma unroll
     for (int i = 0; i < EPT; ++i) {
       const long long e = base + (long long)i * kUpdBlock;
-      VR x = e < n ? rl[e] : VR{0, 0};
-      x = VR{sc * x.x, sc * x.y};
-      rs[i] = x;
-      rv[i] = V2{(T)x.x, (T)x.y};
+      const VR x = e < n ? rl[e] : VR{0, 0};
+      rv[i] = V2{(T)(sc * x.x), (T)(sc * x.y)};
     }
     int t = 0;
     for (; t + 2 <= m; t += 2) {
@@ -585,18 +616,6 @@ cg_update_kernel(Control c, int N, const VR* __restrict__ r, VR* __restrict__ p,
         }
       }
     }
-    if (cont) {
-#pragma unroll
-      for (int i = 0; i < EPT; ++i) {
-        const long long e = base + (long long)i * kUpdBlock;
-        if (e < n) {
-          VR pe = pl[e];
-          pe.x = fma(beta, pe.x, rs[i].x);
-          pe.y = fma(beta, pe.y, rs[i].y);
-          pl[e] = pe;
-        }
-      }
-    }
   }
 }
 
@@ -607,7 +626,7 @@ cg_update_kernel(Control c, int N, const VR* __restrict__ r, VR* __restrict__ p,
 // elements, source, group of kDfGroup listed shifts): blockIdx = (chunk,
 // source, group).  Blocks are short-lived and many (~5 waves at the 8^4
 // size), so no wave runs nearly empty; r is re-read once per group (1/16 of
-// the shift traffic at 8 shifts a group) and group 0 also does p = r + beta p.
+// the shift traffic at 8 shifts a group).
 // The coefficients a_j, b_j (FP64, from kernel B) and r are split to
 // float-float once per block / per element; each shift then costs two
 // complex float-float multiply-adds on the FP32 pipes.
@@ -615,39 +634,34 @@ constexpr int kDfGroup = 8;
 
 template <int EPT>
 __global__ void __launch_bounds__(kUpdBlock)
-cg_update_df_kernel(Control c, int N, const double2* __restrict__ r, double2* __restrict__ p,
-                    float4* __restrict__ y, float4* __restrict__ ph, long long n) {
-  if (*c.ran == 0) return;
-  const int l = blockIdx.y;
-  const int m = c.list_n[l];
+cg_update_df_kernel(Control c, int N, int par, const double2* __restrict__ r, float4* __restrict__ y,
+                    float4* __restrict__ ph, long long n) {
+  if (c.rec_ran[par] == 0) return;
+  const int l = blockIdx.y, L = gridDim.y;
+  const int m = c.list_n[par * L + l];
   const int t0 = blockIdx.z * kDfGroup, t1 = min(m, t0 + kDfGroup);
-  const bool do_p = blockIdx.z == 0 && c.live[l] != 0;
-  if (t1 <= t0 && !do_p) return;
+  if (t1 <= t0) return;
   __shared__ int s_j[kDfGroup];
   __shared__ float4 s_a[kDfGroup], s_b[kDfGroup];
   if (threadIdx.x < kDfGroup && t0 + (int)threadIdx.x < t1) {
-    const int t = t0 + threadIdx.x;
-    s_j[threadIdx.x] = c.list_j[l * N + t];
-    s_a[threadIdx.x] = ff::from_double2(c.list_a[l * N + t]);
-    s_b[threadIdx.x] = ff::from_double2(c.list_b[l * N + t]);
+    const int o = (par * L + l) * N + t0 + threadIdx.x;
+    s_j[threadIdx.x] = c.list_j[o];
+    s_a[threadIdx.x] = ff::from_double2(c.list_a[o]);
+    s_b[threadIdx.x] = ff::from_double2(c.list_b[o]);
   }
   __syncthreads();
-  const int mg = max(0, t1 - t0);
-  const double sc = c.seed[l].scale;  // exact power of two, usually 1
-  const double beta = c.seed[l].scale * c.seed[l].beta;
+  const int mg = t1 - t0;
+  const double sc = c.list_sc[par * L + l];  // exact power of two, usually 1
   const double2* rl = r + (long long)l * n;
-  double2* pl = p + (long long)l * n;
   float4* yl = y + (long long)l * N * n;
   float4* hl = ph + (long long)l * N * n;
   const long long base = blockIdx.x * (long long)kUpdBlock * EPT + threadIdx.x;
-  double2 rs[EPT];
   float4 rv[EPT];
 #pragma unroll
   for (int i = 0; i < EPT; ++i) {
     const long long e = base + (long long)i * kUpdBlock;
     const double2 x = e < n ? rl[e] : make_double2(0.0, 0.0);
-    rs[i] = make_double2(sc * x.x, sc * x.y);
-    rv[i] = ff::from_double2(rs[i]);
+    rv[i] = ff::from_double2(make_double2(sc * x.x, sc * x.y));
   }
   int t = 0;
   for (; t + 2 <= mg; t += 2) {
@@ -689,18 +703,6 @@ cg_update_df_kernel(Control c, int N, const double2* __restrict__ r, double2* __
         const float4 yv = y0[e], hv = h0[e];
         y0[e] = ff::cfma(yv, a0, hv);
         h0[e] = ff::cfma(rv[i], b0, hv);
-      }
-    }
-  }
-  if (do_p) {
-#pragma unroll
-    for (int i = 0; i < EPT; ++i) {
-      const long long e = base + (long long)i * kUpdBlock;
-      if (e < n) {
-        double2 pe = pl[e];
-        pe.x = fma(beta, pe.x, rs[i].x);
-        pe.y = fma(beta, pe.y, rs[i].y);
-        pl[e] = pe;
       }
     }
   }
@@ -780,6 +782,25 @@ cg_reliable_kernel(Control c, int L, const double2* __restrict__ v, const double
   if (threadIdx.x == 0) c.done[1] = 0u;
 }
 
+// Kernel launch with a scheduling priority (cudaLaunchAttributePriority; kept
+// as a node attribute when captured into a graph).  The main chain A, B, P
+// runs at the device's greatest priority so that its blocks are dispatched
+// ahead of the remaining blocks of the concurrent shift update C.
+template <typename... KArgs, typename... Args>
+void launch_prio(void (*kern)(KArgs...), dim3 grid, dim3 block, cudaStream_t st, int prio, Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributePriority;
+  attr[0].val.priority = prio;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
+
 int seed_blocks(long long n, int L) {
   long long b = (n + 4 * kSeedBlock - 1) / (4 * kSeedBlock);  // >= 4 elements per thread
   const long long cap = (152LL * 2 + L - 1) / L;
@@ -801,26 +822,24 @@ int update_epts(bool memory_bound) {
 }
 
 template <typename VR, typename V2>
-int launch_update(int ept, dim3 grid, cudaStream_t st, const Control& c, int N, const VR* r, VR* p, V2* y, V2* ph,
-                  long long n) {
+void launch_update(int ept, dim3 grid, cudaStream_t st, int prio, const Control& c, int N, int par, const VR* r,
+                   V2* y, V2* ph, long long n) {
   switch (ept) {
-    case 1: cg_update_kernel<VR, V2, 1><<<grid, kUpdBlock, 0, st>>>(c, N, r, p, y, ph, n); break;
-    case 2: cg_update_kernel<VR, V2, 2><<<grid, kUpdBlock, 0, st>>>(c, N, r, p, y, ph, n); break;
-    default: cg_update_kernel<VR, V2, 4><<<grid, kUpdBlock, 0, st>>>(c, N, r, p, y, ph, n); break;
+    case 1: launch_prio(cg_update_kernel<VR, V2, 1>, grid, kUpdBlock, st, prio, c, N, par, r, y, ph, n); break;
+    case 2: launch_prio(cg_update_kernel<VR, V2, 2>, grid, kUpdBlock, st, prio, c, N, par, r, y, ph, n); break;
+    default: launch_prio(cg_update_kernel<VR, V2, 4>, grid, kUpdBlock, st, prio, c, N, par, r, y, ph, n); break;
   }
-  return SSQCD_OK;
 }
 
-int launch_update_df(int ept, int L, cudaStream_t st, const Control& c, int N, const double2* r, double2* p,
-                     float4* y, float4* ph, long long n) {
+void launch_update_df(int ept, int L, cudaStream_t st, int prio, const Control& c, int N, int par,
+                      const double2* r, float4* y, float4* ph, long long n) {
   const long long chunks = (n + (long long)kUpdBlock * ept - 1) / ((long long)kUpdBlock * ept);
   const dim3 grid((unsigned)chunks, L, (N + kDfGroup - 1) / kDfGroup);
   switch (ept) {
-    case 1: cg_update_df_kernel<1><<<grid, kUpdBlock, 0, st>>>(c, N, r, p, y, ph, n); break;
-    case 2: cg_update_df_kernel<2><<<grid, kUpdBlock, 0, st>>>(c, N, r, p, y, ph, n); break;
-    default: cg_update_df_kernel<4><<<grid, kUpdBlock, 0, st>>>(c, N, r, p, y, ph, n); break;
+    case 1: launch_prio(cg_update_df_kernel<1>, grid, kUpdBlock, st, prio, c, N, par, r, y, ph, n); break;
+    case 2: launch_prio(cg_update_df_kernel<2>, grid, kUpdBlock, st, prio, c, N, par, r, y, ph, n); break;
+    default: launch_prio(cg_update_df_kernel<4>, grid, kUpdBlock, st, prio, c, N, par, r, y, ph, n); break;
   }
-  return SSQCD_OK;
 }
 
 int update_blocks(long long n, int L, int ept) {
@@ -860,7 +879,7 @@ int run_shifted_cg(ssqcd_lattice lat, int N, const double2* z_host, int L, const
   const double rescale_by = (kShift32 || kShiftDF) ? 0x1p+20 : 0x1p+200;
 
   DevBuf r, p, q, ph, y32, x, kx;
-  SS_TRY(r.alloc(sizeof(VR) * n * L));
+  SS_TRY(r.alloc(2 * sizeof(VR) * n * L));  // r_k and r_{k+1}: parity buffers
   SS_TRY(p.alloc(sizeof(VR) * n * L));
   SS_TRY(q.alloc(sizeof(VR) * n * L));
   SS_TRY(ph.alloc(sizeof(V2) * n * NL));
@@ -890,12 +909,14 @@ int run_shifted_cg(ssqcd_lattice lat, int N, const double2* z_host, int L, const
   };
   const size_t o_seed = take(sizeof(SeedState) * L), o_alpha = take(sizeof(double) * L),
                o_vn = take(sizeof(double) * L), o_live = take(sizeof(int) * L), o_tot = take(sizeof(int)),
-               o_ran = take(sizeof(int)), o_err = take(sizeof(int)), o_si = take(sizeof(int) * 2),
+               o_ran = take(sizeof(int)), o_rran = take(sizeof(int) * 2), o_err = take(sizeof(int)),
+               o_si = take(sizeof(int) * 2),
                o_done = take(sizeof(unsigned) * 2), o_s = take(sizeof(double2) * NL),
                o_xc = take(sizeof(double2) * NL), o_xp = take(sizeof(double2) * NL),
                o_xn = take(sizeof(double2) * NL), o_rt = take(sizeof(double2) * NL), o_act = take(sizeof(int) * NL),
-               o_it = take(sizeof(int) * NL), o_ln = take(sizeof(int) * L), o_lj = take(sizeof(int) * NL),
-               o_la = take(sizeof(double2) * NL), o_lb = take(sizeof(double2) * NL),
+               o_it = take(sizeof(int) * NL), o_ln = take(sizeof(int) * 2 * L), o_lj = take(sizeof(int) * 2 * NL),
+               o_la = take(sizeof(double2) * 2 * NL), o_lb = take(sizeof(double2) * 2 * NL),
+               o_lsc = take(sizeof(double) * 2 * L),
                o_part = take(sizeof(double) * (size_t)nbw * L), o_prr = take(sizeof(double) * (size_t)nbs * L),
                o_vp = take(sizeof(double) * (size_t)nbs * L), o_vn2 = take(sizeof(double) * L);
   SS_TRY(ctl.alloc(off));
@@ -907,6 +928,7 @@ int run_shifted_cg(ssqcd_lattice lat, int N, const double2* z_host, int L, const
   c.live = reinterpret_cast<int*>(base + o_live);
   c.live_total = reinterpret_cast<int*>(base + o_tot);
   c.ran = reinterpret_cast<int*>(base + o_ran);
+  c.rec_ran = reinterpret_cast<int*>(base + o_rran);
   c.err = reinterpret_cast<int*>(base + o_err);
   c.seed_iters = reinterpret_cast<int*>(base + o_si);
   c.done = reinterpret_cast<unsigned*>(base + o_done);
@@ -921,6 +943,7 @@ int run_shifted_cg(ssqcd_lattice lat, int N, const double2* z_host, int L, const
   c.list_j = reinterpret_cast<int*>(base + o_lj);
   c.list_a = reinterpret_cast<double2*>(base + o_la);
   c.list_b = reinterpret_cast<double2*>(base + o_lb);
+  c.list_sc = reinterpret_cast<double*>(base + o_lsc);
   c.partial = reinterpret_cast<double*>(base + o_part);
   c.partial_rr = reinterpret_cast<double*>(base + o_prr);
   c.x = x.p != nullptr ? x.as<double2>() : nullptr;
@@ -950,57 +973,100 @@ int run_shifted_cg(ssqcd_lattice lat, int N, const double2* z_host, int L, const
   const double tol2 = tol * tol;
   int status = SSQCD_OK;
   int k = 0;
-  constexpr int kChunk = 16;
+  constexpr int kChunk = 16;  // even: every chunk starts at parity 0
   const bool timing = kernel_timing_enabled();
+  // Two streams: the main chain A -> B -> P runs on the caller's stream at
+  // the greatest priority; C (the shift update of iteration k) runs on a side
+  // stream beside A, B, P of iteration k + 1.  Dependencies: C(k) after B(k)
+  // (coefficients, r_{k+1}) and after C(k-1) (stream order); A(k) after
+  // C(k-2) (A and B of iteration k rewrite the parity-(k % 2) record and r
+  // buffer that C(k-2) read).  Each chunk forks the side stream from the
+  // main one and joins it back at the end.
+  int prio_lo = 0, prio_hi = 0;
+  SS_CUDA(cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi));
+  struct SideRes {
+    cudaStream_t side = nullptr;
+    std::vector<cudaEvent_t> ev;
+    ~SideRes() {
+      for (auto e : ev) cudaEventDestroy(e);
+      if (side) cudaStreamDestroy(side);
+    }
+  } sr;
+  SS_CUDA(cudaStreamCreateWithPriority(&sr.side, cudaStreamNonBlocking, prio_lo));
+  sr.ev.resize(2 * kChunk + 1);
+  for (auto& e : sr.ev) SS_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  cudaStream_t side = sr.side;
+  cudaEvent_t ev_fork = sr.ev[2 * kChunk];
+  auto ev_b = [&](int it) { return sr.ev[it]; };
+  auto ev_c = [&](int it) { return sr.ev[kChunk + it]; };
+  constexpr int kSlots = 8;  // per iteration: A, B, C, P start/stop
   std::vector<cudaEvent_t> tev;
-  std::vector<double> t_iter[3];
+  std::vector<double> t_iter[4];
   if (timing) {
-    tev.resize(kChunk * 6);
+    tev.resize(kChunk * kSlots);
     for (auto& e : tev) SS_CUDA(cudaEventCreate(&e));
   }
-  auto mark = [&](int it, int slot) {
+  auto mark = [&](int it, int slot, cudaStream_t s_) {
     // during capture, only the External flag makes a real event-record node
-    if (timing) cudaEventRecordWithFlags(tev[it * 6 + slot], st, cudaEventRecordExternal);
+    if (timing) cudaEventRecordWithFlags(tev[it * kSlots + slot], s_, cudaEventRecordExternal);
   };
   const dim3 grid_a(nbw, L), grid_b(nbs, L), grid_c(nbu, L);
+  VR* const r0 = r.as<VR>();
   auto iteration = [&](int it) {
-    mark(it, 0);
+    const int par = it & 1;
+    const VR* r_in = r0 + (size_t)par * n * L;
+    VR* r_out = r0 + (size_t)(par ^ 1) * n * L;
+    if (it >= 2) cudaStreamWaitEvent(st, ev_c(it - 2), 0);
+    mark(it, 0, st);
     if constexpr (kFP32) {
       if (lat->precision == SSQCD_MIXED)
-        cg_stencil_kernel<<<grid_a, kStencilThreads, 0, st>>>(
-            c, L, g, Stencil32<LinksF16>{LinksF16{lat->u16.as<uint2>(), g.V}}, sigma, p.as<VR>(), q.as<VR>());
+        launch_prio(cg_stencil_kernel<Stencil32<LinksF16>, VR>, grid_a, kStencilThreads, st, prio_hi, c, L, par, g,
+                    Stencil32<LinksF16>{LinksF16{lat->u16.as<uint2>(), g.V}}, sigma, p.as<VR>(), q.as<VR>());
       else
-        cg_stencil_kernel<<<grid_a, kStencilThreads, 0, st>>>(
-            c, L, g, Stencil32<LinksF32>{LinksF32{lat->u32.as<float4>(), g.V}}, sigma, p.as<VR>(), q.as<VR>());
+        launch_prio(cg_stencil_kernel<Stencil32<LinksF32>, VR>, grid_a, kStencilThreads, st, prio_hi, c, L, par, g,
+                    Stencil32<LinksF32>{LinksF32{lat->u32.as<float4>(), g.V}}, sigma, p.as<VR>(), q.as<VR>());
     } else {
-      cg_stencil_kernel<<<grid_a, kStencilThreads, 0, st>>>(c, L, g, Stencil64{lat->u64.as<double2>()}, sigma,
-                                                             p.as<VR>(), q.as<VR>());
+      launch_prio(cg_stencil_kernel<Stencil64, VR>, grid_a, kStencilThreads, st, prio_hi, c, L, par, g,
+                  Stencil64{lat->u64.as<double2>()}, sigma, p.as<VR>(), q.as<VR>());
     }
-    mark(it, 1);
-    mark(it, 2);
-    cg_seed_kernel<VR><<<grid_b, kSeedBlock, 0, st>>>(c, L, N, tol2, r.as<VR>(), q.as<VR>(), p.as<VR>(), n,
-                                                      rescale_below, rescale_by);
-    mark(it, 3);
-    mark(it, 4);
+    mark(it, 1, st);
+    mark(it, 2, st);
+    launch_prio(cg_seed_kernel<VR>, grid_b, kSeedBlock, st, prio_hi, c, L, N, par, tol2, r_in, r_out, q.as<VR>(),
+                p.as<VR>(), n, rescale_below, rescale_by);
+    mark(it, 3, st);
+    cudaEventRecord(ev_b(it), st);
+    mark(it, 6, st);
+    launch_prio(cg_seed_p_kernel<VR>, grid_b, kUpdBlock, st, prio_hi, c, r_out, p.as<VR>(), n);
+    mark(it, 7, st);
+    cudaStreamWaitEvent(side, ev_b(it), 0);
+    mark(it, 4, side);
     if constexpr (kShiftDF)
-      launch_update_df(ept, L, st, c, N, r.as<double2>(), p.as<double2>(), yv, ph.as<float4>(), n);
+      launch_update_df(ept, L, side, prio_lo, c, N, par, r_out, yv, ph.as<float4>(), n);
     else
-      launch_update<VR, V2>(ept, grid_c, st, c, N, r.as<VR>(), p.as<VR>(), yv, ph.as<V2>(), n);
-    mark(it, 5);
+      launch_update<VR, V2>(ept, grid_c, side, prio_lo, c, N, par, r_out, yv, ph.as<V2>(), n);
+    mark(it, 5, side);
+    cudaEventRecord(ev_c(it), side);
+  };
+  auto run_chunk = [&](int count) {
+    cudaEventRecord(ev_fork, st);
+    cudaStreamWaitEvent(side, ev_fork, 0);
+    for (int it = 0; it < count; ++it) iteration(it);
+    cudaStreamWaitEvent(st, ev_c(count - 1), 0);
   };
   // A chunk of iterations is captured once as a CUDA graph and replayed (the
   // kernels read all per-iteration state from device memory, so every replay
-  // is the same graph).  With kernel timing on, the graph also records an
-  // event around every kernel; they are read after each replay.  A stream
-  // that cannot be captured (the legacy default stream) falls back to direct
-  // launches.
+  // is the same graph; node priorities are kept).  With kernel timing on,
+  // the graph also records an event around every kernel; they are read after
+  // each replay.  A stream that cannot be captured (the legacy default
+  // stream) falls back to direct launches.
   cudaGraphExec_t gexec = nullptr;
   {
     cudaGraph_t graph = nullptr;
     if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
-      for (int it = 0; it < kChunk; ++it) iteration(it);
+      run_chunk(kChunk);
       if (cudaStreamEndCapture(st, &graph) == cudaSuccess && graph != nullptr) {
-        if (cudaGraphInstantiate(&gexec, graph, 0) != cudaSuccess) gexec = nullptr;
+        if (cudaGraphInstantiate(&gexec, graph, cudaGraphInstantiateFlagUseNodePriority) != cudaSuccess)
+          gexec = nullptr;
         cudaGraphDestroy(graph);
       }
     }
@@ -1016,13 +1082,12 @@ int run_shifted_cg(ssqcd_lattice lat, int N, const double2* z_host, int L, const
       if (ge != cudaSuccess) { status = cuda_fail(ge, "shifted CG graph launch", __FILE__, __LINE__); break; }
       k += kChunk;
       launched = kChunk;
-      count_launches(3LL * kChunk);
+      count_launches(4LL * kChunk);
     } else {
-      for (int it = 0; it < chunk; ++it, ++k) {
-        iteration(it);
-        count_launches(3);
-        ++launched;
-      }
+      run_chunk(chunk);
+      k += chunk;
+      launched = chunk;
+      count_launches(4LL * chunk);
       cudaError_t le = cudaGetLastError();
       if (le != cudaSuccess) { status = cuda_fail(le, "shifted CG launch", __FILE__, __LINE__); break; }
     }
@@ -1032,7 +1097,9 @@ int run_shifted_cg(ssqcd_lattice lat, int N, const double2* z_host, int L, const
       int s1 = wilson64(g, lat->u64.as<double2>(), c.x, kx.as<double2>(), L, sigma, -1.0, nullptr, nullptr, st);
       if (s1 != SSQCD_OK) { status = s1; break; }
       const double floor2 = lat->precision == SSQCD_MIXED ? 1e-4 : 1e-10;  // (1e-2 / 1e-5 of ||v||)^2
-      cg_reliable_kernel<VR><<<grid_b, kSeedBlock, 0, st>>>(c, L, v, kx.as<double2>(), r.as<VR>(), n, floor2);
+      // the next iteration (parity of the launched count) reads this buffer
+      VR* r_next = r0 + (size_t)(launched & 1) * n * L;
+      cg_reliable_kernel<VR><<<grid_b, kSeedBlock, 0, st>>>(c, L, v, kx.as<double2>(), r_next, n, floor2);
       count_launches(1);
     }
     // live-shift count after the last iteration, and the error flag
@@ -1042,9 +1109,9 @@ int run_shifted_cg(ssqcd_lattice lat, int N, const double2* z_host, int L, const
     if (ce != cudaSuccess) { status = cuda_fail(ce, "shifted CG poll", __FILE__, __LINE__); break; }
     if (timing) {
       for (int it = 0; it < launched; ++it)
-        for (int cls = 0; cls < 3; ++cls) {
+        for (int cls = 0; cls < 4; ++cls) {
           float ms = 0.f;
-          cudaEventElapsedTime(&ms, tev[it * 6 + 2 * cls], tev[it * 6 + 2 * cls + 1]);
+          cudaEventElapsedTime(&ms, tev[it * kSlots + 2 * cls], tev[it * kSlots + 2 * cls + 1]);
           t_iter[cls].push_back(ms);
         }
     }
@@ -1100,8 +1167,8 @@ int run_shifted_cg(ssqcd_lattice lat, int N, const double2* z_host, int L, const
       out->timed = timing;
       out->launches_update = timing ? std::min<int>(counters[0], (int)t_iter[2].size()) : 0;
       for (int cls = 0; cls < 4; ++cls) out->ms_k[cls] = 0.0;
-      const int slot_of[3] = {0, 1, 3};  // stencil, seed update + scalars, shift update
-      for (int cls = 0; cls < 3; ++cls) {
+      const int slot_of[4] = {0, 1, 3, 2};  // stencil, seed update + scalars, shift update, seed p
+      for (int cls = 0; cls < 4; ++cls) {
         double acc = 0.0;
         // iterations after the last live one skip their work: not counted
         for (int i = 0; i < (int)t_iter[cls].size() && i < counters[0]; ++i) acc += t_iter[cls][i];
