@@ -56,6 +56,9 @@ extern "C" {
 #define SSQCD_FP64_DFSHIFT 4    /* as SSQCD_FP64_SHIFT32 with y and p-hat in
                                    float-float (hi + lo FP32 pair, 48-bit
                                    significand) updated on the FP32 pipes      */
+#define SSQCD_DF           5    /* links, stencil, seed and shift vectors all in
+                                   float-float on the FP32 pipes; recurrence
+                                   scalars, moments and Rayleigh-Ritz in FP64  */
 
 /* ---- contour shapes --------------------------------------------------------- */
 #define SSQCD_PATH_LINES  0  /* L+-: z = gamma + rho (x +- i beta), Section 3      */
@@ -141,7 +144,9 @@ int ssqcd_apply_H(ssqcd_lattice lat, const double* in, double* out, int nrhs, in
  * (SSQCD_MIXED) or FP32 (SSQCD_MIXED_F32LINKS) as their first two rows, the
  * third rebuilt as conj(row0 x row1) (exact for SU(3)); spinors and
  * arithmetic in FP32.  Input and output stay complex128 at the boundary.
- * Requires a lattice created with one of the two mixed precisions. */
+ * On a SSQCD_DF lattice: links, spinors and arithmetic in float-float
+ * (relative error ~1e-14).  Requires a lattice created with one of the two
+ * mixed precisions or with SSQCD_DF. */
 int ssqcd_apply_H_mixed(ssqcd_lattice lat, const double* in, double* out, int nrhs, int on_device);
 
 void ssqcd_lattice_destroy(ssqcd_lattice lat);

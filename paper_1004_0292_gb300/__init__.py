@@ -22,14 +22,14 @@ import numpy as np
 
 __all__ = [
     "OK", "ERR_ARG", "ERR_OOM", "ERR_BREAKDOWN", "ERR_NOCONV", "ERR_CUDA",
-    "FP64", "MIXED", "MIXED_F32LINKS", "FP64_SHIFT32", "FP64_DFSHIFT", "PATH_LINES", "PATH_CIRCLE", "SsqcdError",
+    "FP64", "MIXED", "MIXED_F32LINKS", "FP64_SHIFT32", "FP64_DFSHIFT", "DF", "PATH_LINES", "PATH_CIRCLE", "SsqcdError",
     "library_path", "lib", "create_lattice", "upload_gauge", "apply_H", "apply_H_mixed",
     "contour", "shifted_cg", "moments", "moments_noalloc", "ss_solve", "ss_eigpairs", "small_eigh",
     "kernel_launches", "set_kernel_timing", "Lattice", "Result", "Opts", "Stats",
 ]
 
 OK, ERR_ARG, ERR_OOM, ERR_BREAKDOWN, ERR_NOCONV, ERR_CUDA = 0, 1, 2, 3, 4, 5
-FP64, MIXED, MIXED_F32LINKS, FP64_SHIFT32, FP64_DFSHIFT = 0, 1, 2, 3, 4
+FP64, MIXED, MIXED_F32LINKS, FP64_SHIFT32, FP64_DFSHIFT, DF = 0, 1, 2, 3, 4, 5
 PATH_LINES, PATH_CIRCLE = 0, 1
 
 _HERE = os.path.dirname(os.path.abspath(__file__))

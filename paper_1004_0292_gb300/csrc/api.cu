@@ -109,8 +109,18 @@ extern "C" int ssqcd_upload_gauge(ssqcd_lattice lat, const double* links, int on
     SS_TRY(lat->u32.alloc(sizeof(float4) * 12 * (size_t)V));
     SS_TRY(pack_gauge32(lat->u64.as<double2>(), lat->u32.p, V, lat->stream));
   }
+  lat->gauge_version++;
+  if (lat->precision == SSQCD_DF) SS_TRY(ensure_df_links(lat));
   SS_CUDA(cudaStreamSynchronize(lat->stream));
   lat->has_gauge = true;
+  return SSQCD_OK;
+}
+
+int ssqcd::ensure_df_links(ssqcd_lattice lat) {
+  if (lat->udf.p != nullptr && lat->udf_version == lat->gauge_version) return SSQCD_OK;
+  SS_TRY(lat->udf.alloc(sizeof(float4) * 36 * (size_t)lat->g.V));
+  SS_TRY(pack_gauge_df(lat->u64.as<double2>(), lat->udf.as<float4>(), lat->g.V, lat->stream));
+  lat->udf_version = lat->gauge_version;
   return SSQCD_OK;
 }
 
@@ -130,12 +140,25 @@ extern "C" int ssqcd_apply_H(ssqcd_lattice lat, const double* in, double* out, i
 
 extern "C" int ssqcd_apply_H_mixed(ssqcd_lattice lat, const double* in, double* out, int nrhs, int on_device) {
   SS_TRY(check_lattice(lat, true));
-  if (!is_mixed(lat->precision)) return fail(SSQCD_ERR_ARG, "apply_H_mixed needs a mixed-precision lattice");
+  if (!is_mixed(lat->precision) && lat->precision != SSQCD_DF)
+    return fail(SSQCD_ERR_ARG, "apply_H_mixed needs a mixed-precision or SSQCD_DF lattice");
   if (nrhs < 0 || (nrhs > 0 && (in == nullptr || out == nullptr))) return fail(SSQCD_ERR_ARG, "bad apply_H arguments");
   if (nrhs == 0) return SSQCD_OK;
   const long long n = 12LL * lat->g.V * nrhs;
   DevBuf a, a32, b32;
   SS_TRY(to_device_layout(lat, in, nrhs, on_device, a));
+  if (lat->precision == SSQCD_DF) {
+    SS_TRY(ensure_df_links(lat));
+    SS_TRY(a32.alloc(sizeof(float4) * n));
+    SS_TRY(b32.alloc(sizeof(float4) * n));
+    SS_TRY(convert_f64_to_df(a.as<double2>(), a32.as<float4>(), n, lat->stream));
+    SS_TRY(wilson_df(lat->g, lat->udf.as<float4>(), a32.as<float4>(), b32.as<float4>(), nrhs, 0.0, 1.0,
+                     lat->stream));
+    SS_TRY(convert_df_to_f64(b32.as<float4>(), a.as<double2>(), n, lat->stream));
+    SS_TRY(from_device_layout(lat, a.as<double2>(), nrhs, on_device, out));
+    SS_CUDA(cudaStreamSynchronize(lat->stream));
+    return SSQCD_OK;
+  }
   SS_TRY(a32.alloc(sizeof(float2) * n));
   SS_TRY(b32.alloc(sizeof(float2) * n));
   SS_TRY(convert_f64_to_f32(a.as<double2>(), a32.as<float2>(), n, lat->stream));

@@ -60,14 +60,122 @@ __device__ __forceinline__ float2 fma2(float ch, float cl, float u1h, float u1l,
   return make_float2(h, l);
 }
 
+// ---- real float-float values: float2 {hi, lo} --------------------------------
+
+// a + b (two_sum of the leading parts, lo parts added, renormalised); the
+// error is within a few units of 2^-48 (|a| + |b|).
+__device__ __forceinline__ float2 add(float2 a, float2 b) {
+  float s, e;
+  two_sum(a.x, b.x, s, e);
+  e = __fadd_rn(e, __fadd_rn(a.y, b.y));
+  float h, l;
+  fast_two_sum(s, e, h, l);
+  return make_float2(h, l);
+}
+
+// c + u v
+__device__ __forceinline__ float2 fma1(float2 c, float2 u, float2 v) {
+  const float p = __fmul_rn(u.x, v.x);
+  const float e = __fmaf_rn(u.x, v.x, -p);
+  float s, t;
+  two_sum(c.x, p, s, t);
+  float lo = __fadd_rn(c.y, __fadd_rn(e, t));
+  lo = __fmaf_rn(u.x, v.y, lo);
+  lo = __fmaf_rn(u.y, v.x, lo);
+  float h, l;
+  fast_two_sum(s, lo, h, l);
+  return make_float2(h, l);
+}
+
+// sum_i a_i b_i for K float-float pairs: the leading products and their sum
+// exactly (TwoProduct, TwoSum chain), every lower-order term in one FP32
+// sum, one renormalisation.
+template <int K>
+__device__ __forceinline__ float2 dot(const float2 (&a)[K], const float2 (&b)[K]) {
+  float s = __fmul_rn(a[0].x, b[0].x);
+  float lo = __fmaf_rn(a[0].x, b[0].x, -s);
+  lo = __fmaf_rn(a[0].x, b[0].y, lo);
+  lo = __fmaf_rn(a[0].y, b[0].x, lo);
+#pragma unroll
+  for (int i = 1; i < K; ++i) {
+    const float p = __fmul_rn(a[i].x, b[i].x);
+    const float e = __fmaf_rn(a[i].x, b[i].x, -p);
+    float t;
+    two_sum(s, p, s, t);
+    lo = __fadd_rn(lo, __fadd_rn(e, t));
+    lo = __fmaf_rn(a[i].x, b[i].y, lo);
+    lo = __fmaf_rn(a[i].y, b[i].x, lo);
+  }
+  float h, l;
+  fast_two_sum(s, lo, h, l);
+  return make_float2(h, l);
+}
+
+__device__ __forceinline__ float2 neg(float2 a) { return make_float2(-a.x, -a.y); }
+
+// Nearest float-float to a double (x - hi is exact in FP64).
+__device__ __forceinline__ float2 split(double x) {
+  const float h = __double2float_rn(x);
+  return make_float2(h, __double2float_rn(x - (double)h));
+}
+
 // Complex float-float value: {re.hi, im.hi, re.lo, im.lo}.
 using cff = float4;
 
+__device__ __forceinline__ float2 re(cff z) { return make_float2(z.x, z.z); }
+__device__ __forceinline__ float2 im(cff z) { return make_float2(z.y, z.w); }
+__device__ __forceinline__ cff make(float2 re_, float2 im_) { return make_float4(re_.x, im_.x, re_.y, im_.y); }
+__device__ __forceinline__ cff cadd(cff a, cff b) { return make(add(re(a), re(b)), add(im(a), im(b))); }
+__device__ __forceinline__ cff csub(cff a, cff b) { return make(add(re(a), neg(re(b))), add(im(a), neg(im(b)))); }
+__device__ __forceinline__ cff cneg(cff a) { return make_float4(-a.x, -a.y, -a.z, -a.w); }
+// exact scaling by a power of two
+__device__ __forceinline__ cff cscale2(cff a, float s) { return make_float4(s * a.x, s * a.y, s * a.z, s * a.w); }
+// c + u v with u real
+__device__ __forceinline__ cff caxpy(cff c, float2 u, cff v) { return make(fma1(re(c), u, re(v)), fma1(im(c), u, im(v))); }
+// multiplication by +1, -1, +i, -i (codes 0..3): exact
+__device__ __forceinline__ cff unit_mul(int code, cff z) {
+  switch (code) {
+    case 0: return z;
+    case 1: return make_float4(-z.x, -z.y, -z.z, -z.w);
+    case 2: return make_float4(-z.y, z.x, -z.w, z.z);
+    default: return make_float4(z.y, -z.x, z.w, -z.z);
+  }
+}
+// sum_b u_b h_b and sum_b conj(u_b) h_b over three complex float-float pairs
+__device__ __forceinline__ cff cdot3(cff u0, cff u1, cff u2, cff h0, cff h1, cff h2) {
+  const float2 ar[6] = {re(u0), neg(im(u0)), re(u1), neg(im(u1)), re(u2), neg(im(u2))};
+  const float2 br[6] = {re(h0), im(h0), re(h1), im(h1), re(h2), im(h2)};
+  const float2 ai[6] = {re(u0), im(u0), re(u1), im(u1), re(u2), im(u2)};
+  const float2 bi[6] = {im(h0), re(h0), im(h1), re(h1), im(h2), re(h2)};
+  return make(dot<6>(ar, br), dot<6>(ai, bi));
+}
+__device__ __forceinline__ cff cdot3_conj(cff u0, cff u1, cff u2, cff h0, cff h1, cff h2) {
+  const float2 ar[6] = {re(u0), im(u0), re(u1), im(u1), re(u2), im(u2)};
+  const float2 br[6] = {re(h0), im(h0), re(h1), im(h1), re(h2), im(h2)};
+  const float2 ai[6] = {re(u0), neg(im(u0)), re(u1), neg(im(u1)), re(u2), neg(im(u2))};
+  const float2 bi[6] = {im(h0), re(h0), im(h1), re(h1), im(h2), re(h2)};
+  return make(dot<6>(ar, br), dot<6>(ai, bi));
+}
+// |z|^2 accumulated into a float-float sum (s, lo): exact squares of the
+// leading parts, 2 hi lo cross terms in the FP32 low sum
+__device__ __forceinline__ void norm2_acc(cff z, float& s, float& lo) {
+  float p = __fmul_rn(z.x, z.x), t;
+  lo = __fadd_rn(lo, __fmaf_rn(z.x, z.x, -p));
+  two_sum(s, p, s, t);
+  lo = __fadd_rn(lo, t);
+  lo = __fmaf_rn(2.f * z.x, z.z, lo);
+  p = __fmul_rn(z.y, z.y);
+  lo = __fadd_rn(lo, __fmaf_rn(z.y, z.y, -p));
+  two_sum(s, p, s, t);
+  lo = __fadd_rn(lo, t);
+  lo = __fmaf_rn(2.f * z.y, z.w, lo);
+}
+
 // c + u v for complex float-float c, u, v.
 __device__ __forceinline__ cff cfma(cff c, cff u, cff v) {
-  const float2 re = fma2(c.x, c.z, u.x, u.z, v.x, v.z, -u.y, -u.w, v.y, v.w);
-  const float2 im = fma2(c.y, c.w, u.x, u.z, v.y, v.w, u.y, u.w, v.x, v.z);
-  return make_float4(re.x, im.x, re.y, im.y);
+  const float2 r_ = fma2(c.x, c.z, u.x, u.z, v.x, v.z, -u.y, -u.w, v.y, v.w);
+  const float2 i_ = fma2(c.y, c.w, u.x, u.z, v.y, v.w, u.y, u.w, v.x, v.z);
+  return make_float4(r_.x, i_.x, r_.y, i_.y);
 }
 
 // Nearest float-float to an FP64 complex (hi = fl32(x), lo = fl32(x - hi);

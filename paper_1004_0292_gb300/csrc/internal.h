@@ -79,6 +79,9 @@ struct ssqcd_lattice_s {
   ssqcd::DevBuf u64;     // FP64 links [4][9][V] double2
   ssqcd::DevBuf u16;     // FP16 12-parameter links, SSQCD_MIXED only
   ssqcd::DevBuf u32;     // FP32 12-parameter links, SSQCD_MIXED_F32LINKS only
+  ssqcd::DevBuf udf;     // float-float links [4][9][V] float4, built on first SSQCD_DF use
+  int gauge_version = 0; // bumped by every upload
+  int udf_version = -1;  // gauge_version udf was built from
   ssqcd::DevBuf stage;   // staging for host <-> device copies
 };
 
@@ -105,6 +108,13 @@ int wilson64(const Geometry& g, const double2* u, const double2* in, double2* ou
 int wilson32(const Geometry& g, const void* links, int link_bits, const float2* in, float2* out, int nrhs,
              float c0, float c1, float* dot_partial, const int* skip_if_zero, cudaStream_t s);
 int pack_gauge16(const double2* u64dev, void* u16, int V, cudaStream_t s);
+int wilson_df(const Geometry& g, const float4* u, const float4* in, float4* out, int nrhs, double c0, double c1,
+              cudaStream_t s);
+int convert_f64_to_df(const double2* a, float4* b, long long n, cudaStream_t s);
+int convert_df_to_f64(const float4* a, double2* b, long long n, cudaStream_t s);
+int pack_gauge_df(const double2* u64dev, float4* udf, int V, cudaStream_t s);
+// float-float links of the current gauge field (built or rebuilt on demand)
+int ensure_df_links(ssqcd_lattice lat);
 int pack_gauge32(const double2* u64dev, void* u32, int V, cudaStream_t s);
 
 // reductions / dense block ops in FP64 (blas.cu)
@@ -145,7 +155,7 @@ bool kernel_timing_enabled();
 inline bool is_mixed(int precision) { return precision == SSQCD_MIXED || precision == SSQCD_MIXED_F32LINKS; }
 inline bool valid_precision(int precision) {
   return precision == SSQCD_FP64 || precision == SSQCD_FP64_SHIFT32 || precision == SSQCD_FP64_DFSHIFT ||
-         is_mixed(precision);
+         precision == SSQCD_DF || is_mixed(precision);
 }
 // Solves for L sources already packed on device (v: [L][12][V]); y out
 // [L][N][12][V] (device, FP64).  iters/xi: host arrays [L*N] (may be null).

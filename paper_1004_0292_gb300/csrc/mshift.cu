@@ -49,6 +49,7 @@
 
 #include "floatfloat.cuh"
 #include "wilson_core.cuh"
+#include "wilson_df.cuh"
 
 namespace ssqcd {
 namespace {
@@ -135,11 +136,11 @@ __device__ __forceinline__ void put_shift(float4& d, double2 x) { d = ff::from_d
 template <typename VR, typename V2>
 __global__ void init_vectors_kernel(const double2* __restrict__ v, VR* __restrict__ r, VR* __restrict__ p,
                                     V2* __restrict__ y, V2* __restrict__ ph, int N, long long n) {
-  using TR = decltype(VR::x);
   const int l = blockIdx.y;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
     const double2 xd = v[l * n + e];
-    const VR xr{(TR)xd.x, (TR)xd.y};
+    VR xr;
+    put_shift(xr, xd);
     V2 x;
     put_shift(x, xd);
     r[l * n + e] = xr;
@@ -228,6 +229,22 @@ struct Stencil32 {
         q[i * g.V + s] = o;
         d += (double)(pv.x * o.x + pv.y * o.y);
       }
+    }
+    return d;
+  }
+};
+
+// float-float stencil (SSQCD_DF): q = sigma p - A p, float-float share of (p, q)
+struct StencilDF {
+  const float4* __restrict__ u;
+  __device__ __forceinline__ double run(const Geometry& g, const float4* __restrict__ p, float4* __restrict__ q,
+                                        double sigma, int s, int w, void* shm) const {
+    float4 acc[3];
+    block_hops_df(LinksDF{u, g.V}, p, s, g, static_cast<float4*>(shm), acc);
+    double d = 0.0;
+    if (s < g.V) {
+      const float2 t = finish_df(g, p, q, ff::split(sigma), make_float2(-1.f, 0.f), s, w, acc);
+      d = (double)t.x + (double)t.y;
     }
     return d;
   }
@@ -369,28 +386,41 @@ cg_seed_kernel(Control c, int L, int N, int par, double tol2, const V2* __restri
     const T af = (T)alpha;
     const T sc = (T)c.seed[l].scale;  // rescale of r decided last iteration (exact power of two)
     const long long stride = (long long)gridDim.x * kSeedBlock;
-    auto one = [&](long long e, double& acc) {
-      V2 x0 = rl[e];
-      const V2 y0 = ql[e];
-      x0.x = fma(-af, y0.x, sc * x0.x);
-      x0.y = fma(-af, y0.y, sc * x0.y);
-      ro[e] = x0;
-      const double xr = x0.x, xi = x0.y;
-      acc = fma(xr, xr, fma(xi, xi, acc));
-      if (xl != nullptr) {
-        const V2 pv = pl[e];
-        double2 xv = xl[e];
-        xv.x = fma(ax, (double)pv.x, xv.x);
-        xv.y = fma(ax, (double)pv.y, xv.y);
-        xl[e] = xv;
+    if constexpr (std::is_same<V2, float4>::value) {
+      // float-float: r_out = s r_in - alpha q, ||r_out||^2 summed in float-float per thread
+      const float2 naf = ff::split(-alpha);
+      const float scf = (float)c.seed[l].scale;
+      float hs = 0.f, hl = 0.f;
+      for (long long e = blockIdx.x * (long long)kSeedBlock + threadIdx.x; e < n; e += stride) {
+        const float4 x1 = ff::caxpy(ff::cscale2(rl[e], scf), naf, ql[e]);
+        ro[e] = x1;
+        ff::norm2_acc(x1, hs, hl);
       }
-    };
-    long long e = blockIdx.x * (long long)kSeedBlock + threadIdx.x;
-    for (; e + stride < n; e += 2 * stride) {
-      one(e, acc0);
-      one(e + stride, acc1);
+      acc0 = (double)hs + (double)hl;
+    } else {
+      auto one = [&](long long e, double& acc) {
+        V2 x0 = rl[e];
+        const V2 y0 = ql[e];
+        x0.x = fma(-af, y0.x, sc * x0.x);
+        x0.y = fma(-af, y0.y, sc * x0.y);
+        ro[e] = x0;
+        const double xr = x0.x, xi = x0.y;
+        acc = fma(xr, xr, fma(xi, xi, acc));
+        if (xl != nullptr) {
+          const V2 pv = pl[e];
+          double2 xv = xl[e];
+          xv.x = fma(ax, (double)pv.x, xv.x);
+          xv.y = fma(ax, (double)pv.y, xv.y);
+          xl[e] = xv;
+        }
+      };
+      long long e = blockIdx.x * (long long)kSeedBlock + threadIdx.x;
+      for (; e + stride < n; e += 2 * stride) {
+        one(e, acc0);
+        one(e + stride, acc1);
+      }
+      if (e < n) one(e, acc0);
     }
-    if (e < n) one(e, acc0);
   }
   double acc = warp_sum(acc0 + acc1);
   if (lane == 0) sred[w] = acc;
@@ -496,17 +526,26 @@ cg_seed_p_kernel(Control c, const VR* __restrict__ r, VR* __restrict__ p, long l
   if (*c.ran == 0) return;
   const int l = blockIdx.y;
   if (c.live[l] == 0) return;
-  using TR = decltype(VR::x);
-  const TR sc = (TR)c.seed[l].scale;
-  const TR beta = (TR)(c.seed[l].scale * c.seed[l].beta);
   const VR* rl = r + (long long)l * n;
   VR* pl = p + (long long)l * n;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
-    const VR x = rl[e];
-    VR pe = pl[e];
-    pe.x = fma(beta, pe.x, sc * x.x);
-    pe.y = fma(beta, pe.y, sc * x.y);
-    pl[e] = pe;
+  if constexpr (std::is_same<VR, float4>::value) {  // float-float
+    const float scf = (float)c.seed[l].scale;
+    const float2 beta = ff::split(c.seed[l].scale * c.seed[l].beta);
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+         e += (long long)gridDim.x * blockDim.x)
+      pl[e] = ff::caxpy(ff::cscale2(rl[e], scf), beta, pl[e]);
+  } else {
+    using TR = decltype(VR::x);
+    const TR sc = (TR)c.seed[l].scale;
+    const TR beta = (TR)(c.seed[l].scale * c.seed[l].beta);
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+         e += (long long)gridDim.x * blockDim.x) {
+      const VR x = rl[e];
+      VR pe = pl[e];
+      pe.x = fma(beta, pe.x, sc * x.x);
+      pe.y = fma(beta, pe.y, sc * x.y);
+      pl[e] = pe;
+    }
   }
 }
 
@@ -632,9 +671,16 @@ cg_update_kernel(Control c, int N, int par, const VR* __restrict__ r, V2* __rest
 // complex float-float multiply-adds on the FP32 pipes.
 constexpr int kDfGroup = 8;
 
-template <int EPT>
+// s r as complex float-float: from FP64 (SSQCD_FP64_DFSHIFT) or float-float
+// (SSQCD_DF) seed vectors
+__device__ __forceinline__ float4 scaled_r(double2 x, double sc) {
+  return ff::from_double2(make_double2(sc * x.x, sc * x.y));
+}
+__device__ __forceinline__ float4 scaled_r(float4 x, double sc) { return ff::cscale2(x, (float)sc); }
+
+template <typename RT, int EPT>
 __global__ void __launch_bounds__(kUpdBlock)
-cg_update_df_kernel(Control c, int N, int par, const double2* __restrict__ r, float4* __restrict__ y,
+cg_update_df_kernel(Control c, int N, int par, const RT* __restrict__ r, float4* __restrict__ y,
                     float4* __restrict__ ph, long long n) {
   if (c.rec_ran[par] == 0) return;
   const int l = blockIdx.y, L = gridDim.y;
@@ -652,7 +698,7 @@ cg_update_df_kernel(Control c, int N, int par, const double2* __restrict__ r, fl
   __syncthreads();
   const int mg = t1 - t0;
   const double sc = c.list_sc[par * L + l];  // exact power of two, usually 1
-  const double2* rl = r + (long long)l * n;
+  const RT* rl = r + (long long)l * n;
   float4* yl = y + (long long)l * N * n;
   float4* hl = ph + (long long)l * N * n;
   const long long base = blockIdx.x * (long long)kUpdBlock * EPT + threadIdx.x;
@@ -660,8 +706,7 @@ cg_update_df_kernel(Control c, int N, int par, const double2* __restrict__ r, fl
 #pragma unroll
   for (int i = 0; i < EPT; ++i) {
     const long long e = base + (long long)i * kUpdBlock;
-    const double2 x = e < n ? rl[e] : make_double2(0.0, 0.0);
-    rv[i] = ff::from_double2(make_double2(sc * x.x, sc * x.y));
+    rv[i] = e < n ? scaled_r(rl[e], sc) : make_float4(0.f, 0.f, 0.f, 0.f);
   }
   int t = 0;
   for (; t + 2 <= mg; t += 2) {
@@ -831,14 +876,15 @@ void launch_update(int ept, dim3 grid, cudaStream_t st, int prio, const Control&
   }
 }
 
-void launch_update_df(int ept, int L, cudaStream_t st, int prio, const Control& c, int N, int par,
-                      const double2* r, float4* y, float4* ph, long long n) {
+template <typename RT>
+void launch_update_df(int ept, int L, cudaStream_t st, int prio, const Control& c, int N, int par, const RT* r,
+                      float4* y, float4* ph, long long n) {
   const long long chunks = (n + (long long)kUpdBlock * ept - 1) / ((long long)kUpdBlock * ept);
   const dim3 grid((unsigned)chunks, L, (N + kDfGroup - 1) / kDfGroup);
   switch (ept) {
-    case 1: launch_prio(cg_update_df_kernel<1>, grid, kUpdBlock, st, prio, c, N, par, r, y, ph, n); break;
-    case 2: launch_prio(cg_update_df_kernel<2>, grid, kUpdBlock, st, prio, c, N, par, r, y, ph, n); break;
-    default: launch_prio(cg_update_df_kernel<4>, grid, kUpdBlock, st, prio, c, N, par, r, y, ph, n); break;
+    case 1: launch_prio(cg_update_df_kernel<RT, 1>, grid, kUpdBlock, st, prio, c, N, par, r, y, ph, n); break;
+    case 2: launch_prio(cg_update_df_kernel<RT, 2>, grid, kUpdBlock, st, prio, c, N, par, r, y, ph, n); break;
+    default: launch_prio(cg_update_df_kernel<RT, 4>, grid, kUpdBlock, st, prio, c, N, par, r, y, ph, n); break;
   }
 }
 
@@ -864,6 +910,8 @@ int run_shifted_cg(ssqcd_lattice lat, int N, const double2* z_host, int L, const
   constexpr bool kFP32 = sizeof(VR) == sizeof(float2);      // seed vectors and stencil in FP32
   constexpr bool kShift32 = sizeof(V2) == sizeof(float2);   // shift vectors in FP32
   constexpr bool kShiftDF = std::is_same<V2, float4>::value; // shift vectors in float-float
+  constexpr bool kSeedDF = std::is_same<VR, float4>::value;  // seed vectors and stencil in float-float
+  if constexpr (kSeedDF) SS_TRY(ensure_df_links(lat));
   cudaStream_t st = lat->stream;
   const Geometry& g = lat->g;
   const long long n = 12LL * g.V;
@@ -1025,6 +1073,9 @@ int run_shifted_cg(ssqcd_lattice lat, int N, const double2* z_host, int L, const
       else
         launch_prio(cg_stencil_kernel<Stencil32<LinksF32>, VR>, grid_a, kStencilThreads, st, prio_hi, c, L, par, g,
                     Stencil32<LinksF32>{LinksF32{lat->u32.as<float4>(), g.V}}, sigma, p.as<VR>(), q.as<VR>());
+    } else if constexpr (kSeedDF) {
+      launch_prio(cg_stencil_kernel<StencilDF, VR>, grid_a, kStencilThreads, st, prio_hi, c, L, par, g,
+                  StencilDF{lat->udf.as<float4>()}, sigma, p.as<VR>(), q.as<VR>());
     } else {
       launch_prio(cg_stencil_kernel<Stencil64, VR>, grid_a, kStencilThreads, st, prio_hi, c, L, par, g,
                   Stencil64{lat->u64.as<double2>()}, sigma, p.as<VR>(), q.as<VR>());
@@ -1041,7 +1092,7 @@ int run_shifted_cg(ssqcd_lattice lat, int N, const double2* z_host, int L, const
     cudaStreamWaitEvent(side, ev_b(it), 0);
     mark(it, 4, side);
     if constexpr (kShiftDF)
-      launch_update_df(ept, L, side, prio_lo, c, N, par, r_out, yv, ph.as<float4>(), n);
+      launch_update_df<VR>(ept, L, side, prio_lo, c, N, par, r_out, yv, ph.as<float4>(), n);
     else
       launch_update<VR, V2>(ept, grid_c, side, prio_lo, c, N, par, r_out, yv, ph.as<V2>(), n);
     mark(it, 5, side);
@@ -1197,6 +1248,9 @@ int shifted_cg_device(ssqcd_lattice lat, int N, const double2* z_host, int L, co
   if (precision == SSQCD_FP64)
     return run_shifted_cg<double2, double2>(lat, N, z_host, L, v, sigma, tol, max_iter, precision, 0, y, iters_host,
                                             xi_host, out);
+  if (precision == SSQCD_DF)
+    return run_shifted_cg<float4, float4>(lat, N, z_host, L, v, sigma, tol, max_iter, precision, 0, y, iters_host,
+                                          xi_host, out);
   if (precision == SSQCD_FP64_DFSHIFT)
     return run_shifted_cg<double2, float4>(lat, N, z_host, L, v, sigma, tol, max_iter, precision, 0, y, iters_host,
                                            xi_host, out);

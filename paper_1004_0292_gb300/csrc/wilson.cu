@@ -11,6 +11,7 @@
 // FP32 spinors with FP16 (or FP32) 12-parameter links: HBM-bound; 96 B in,
 // 96 B out, 96 (192) B links per site.
 #include "wilson_core.cuh"
+#include "wilson_df.cuh"
 
 namespace ssqcd {
 namespace {
@@ -106,6 +107,33 @@ wilson32_kernel(Geometry g, LK lk, const float2* __restrict__ in_all,
   }
 }
 
+// Float-float stencil (SSQCD_DF): out = c0 in + c1 A in with float-float
+// spinors and links; see wilson_df.cuh.
+__global__ void __launch_bounds__(kStencilThreads)
+wilson_df_kernel(Geometry g, const float4* __restrict__ u, const float4* __restrict__ in_all,
+                 float4* __restrict__ out_all, float2 c0, float2 c1) {
+  __shared__ float4 sh[12 * 4 * 32];
+  const int rhs = blockIdx.y;
+  const int V = g.V;
+  const float4* in = in_all + (size_t)rhs * 12 * V;
+  float4* out = out_all + (size_t)rhs * 12 * V;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int s = blockIdx.x * kSitesPerBlock + lane;
+  float4 acc[3];
+  block_hops_df(LinksDF{u, V}, in, s, g, sh, acc);
+  if (s < V) (void)finish_df(g, in, out, c0, c1, s, w, acc);
+}
+
+// FP64 <-> float-float complex arrays (same element size)
+__global__ void f64_to_df_kernel(const double2* __restrict__ a, float4* __restrict__ b, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    b[i] = ff::from_double2(a[i]);
+}
+__global__ void df_to_f64_kernel(const float4* __restrict__ a, double2* __restrict__ b, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    b[i] = ff::to_double2(a[i]);
+}
+
 // FP64 links [4][9][V] -> FP32 rows 0 and 1, [4][3][V] float4
 __global__ void pack_gauge32_kernel(const double2* __restrict__ u, float4* __restrict__ u32, int V) {
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -167,6 +195,41 @@ int wilson32(const Geometry& g, const void* links, int link_bits, const float2* 
   count_launches(1);
   SS_CHECK_LAUNCH();
   return SSQCD_OK;
+}
+
+int wilson_df(const Geometry& g, const float4* u, const float4* in, float4* out, int nrhs, double c0, double c1,
+              cudaStream_t s) {
+  if (nrhs <= 0) return SSQCD_OK;
+  dim3 grid(wilson_blocks(g), nrhs);
+  auto split = [](double x) {
+    const float h = (float)x;
+    return make_float2(h, (float)(x - (double)h));
+  };
+  wilson_df_kernel<<<grid, kStencilThreads, 0, s>>>(g, u, in, out, split(c0), split(c1));
+  count_launches(1);
+  SS_CHECK_LAUNCH();
+  return SSQCD_OK;
+}
+
+int convert_f64_to_df(const double2* a, float4* b, long long n, cudaStream_t s) {
+  if (n <= 0) return SSQCD_OK;
+  f64_to_df_kernel<<<grid_for(n, 256), 256, 0, s>>>(a, b, n);
+  count_launches(1);
+  SS_CHECK_LAUNCH();
+  return SSQCD_OK;
+}
+
+int convert_df_to_f64(const float4* a, double2* b, long long n, cudaStream_t s) {
+  if (n <= 0) return SSQCD_OK;
+  df_to_f64_kernel<<<grid_for(n, 256), 256, 0, s>>>(a, b, n);
+  count_launches(1);
+  SS_CHECK_LAUNCH();
+  return SSQCD_OK;
+}
+
+// float-float links: the FP64 [4][9][V] array element by element
+int pack_gauge_df(const double2* u64dev, float4* udf, int V, cudaStream_t s) {
+  return convert_f64_to_df(u64dev, udf, 36LL * V, s);
 }
 
 int pack_gauge32(const double2* u64dev, void* u32, int V, cudaStream_t s) {
