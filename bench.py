@@ -18,6 +18,11 @@ host.  Under torchrun every rank solves an independent replica (its own
 sources): the path has no data exchange, so scaling is weak and there is no
 collective on the data path.
 
+``mixed`` reports the same metric for the float-float solve precision
+(SSQCD_DF: links, stencil, seed and shift vectors as pairs of FP32 words on
+the FP32 pipes, FP64 scalars, moments and Rayleigh-Ritz) on the same
+workload at the same residual bar, with its ratio to the plain FP64 value.
+
 ``--impl reference`` times the FP64 numpy oracle on the host cores on a
 bounded sample of the same workload (shifted-CG iterations of one source and
 one Rayleigh-Ritz pass), extrapolated to a full step.
@@ -212,15 +217,17 @@ def run_ours(args):
 
     # ---- roofline of the dominant kernel (fused multi-shift update) ----
     n = 12 * int(np.prod(w["dims"]))
+    # kernel events cover one chunk of 16 iterations in four (the library's
+    # sampled kernel timing); units and times below are those iterations'
     ms_upd = sum(s["ms_k_update"] for s in stats)
-    units = sum(s["shift_updates"] for s in stats) * n
+    units = sum(s["timed_shift_updates"] for s in stats) * n
     launches_upd = sum(s["launches_update"] for s in stats)
     flops = UPDATE_FLOP_PER_UNIT * units
     achieved_tf = flops / (ms_upd / 1e3) / 1e12
     bytes_upd = UPDATE_BYTES_PER_UNIT * units
     peaks = _measured_peaks()
     ms_sten = sum(s["ms_k_stencil"] for s in stats)
-    it_tot = sum(s["iterations"] for s in stats)
+    it_tot = launches_upd  # timed iterations
     V = int(np.prod(w["dims"]))
     sten_bytes = it_tot * V * (w["L"] * 2 * 192 + 576)
     sten_flops = it_tot * V * w["L"] * STENCIL_FLOP_PER_SITE
@@ -246,6 +253,66 @@ def run_ours(args):
             del res, lat2
         e2e = {"value": float(sum(e2e_pairs) / sum(e2e_times)), "unit": UNIT,
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+
+    # ---- mixed-precision arm: float-float solve (SSQCD_DF), same workload and residual bar ----
+    mixed = None
+    if not args.no_mixed:
+        lat_m = ss.create_lattice(w["dims"], w["kappa"], w["bc_t"], precision=ss.DF, stream=stream)
+        ss.upload_gauge(lat_m, U_d)
+
+        def step_m():
+            res = ss.ss_solve(lat_m, w["interval"], w["N"], w["M"], src_d, beta=w["beta"], nprime=w["nprime"],
+                              tol=w["tol"])
+            if res.status != ss.OK:
+                raise RuntimeError(f"float-float solve failed with status {res.status}: {res.error}")
+            ev, _, rs, st = ss.ss_eigpairs(res, want_vectors=False)
+            return ev, rs, st
+
+        for _ in range(args.warmup):
+            step_m()
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        ss.set_kernel_timing(True)
+        t_m, c_m, s_m, r_m = [], [], [], []
+        for _ in range(args.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            ev, rs, st = step_m()
+            e1.record(stream)
+            e1.synchronize()
+            t_m.append(e0.elapsed_time(e1))
+            c_m.append(int(np.sum(rs <= RES_TOL)))
+            s_m.append(st)
+            r_m.append(float(np.max(rs[rs <= RES_TOL])) if np.any(rs <= RES_TOL) else None)
+        torch.cuda.synchronize()
+        ss.set_kernel_timing(False)
+        ms_m, pairs_m = reduce_job(float(sum(t_m)), float(sum(c_m)), world, "cuda")
+        value_m = pairs_m / (ms_m / 1e3)
+        ms_upd_m = sum(x["ms_k_update"] for x in s_m)
+        units_m = sum(x["timed_shift_updates"] for x in s_m) * n
+        it_m = max(1, sum(x["launches_update"] for x in s_m))
+        gbs_m = UPDATE_BYTES_PER_UNIT * units_m / (ms_upd_m / 1e3) / 1e9
+        mixed = {
+            "precision": "float-float (SSQCD_DF): links, stencil, seed and shift vectors as FP32 pairs "
+                         "(48-bit significand); FP64 scalars, moments, Rayleigh-Ritz",
+            "value": value_m, "unit": UNIT, "ms_per_step": ms_m / args.steps,
+            "vs_plain_fp64": value_m / value, "eigenpairs_per_step": c_m[-1],
+            "max_accepted_residual": r_m[-1], "iterations_per_step": s_m[-1]["iterations"],
+            "cg_us_per_iteration": 1e3 * s_m[-1]["ms_cg"] / max(1, s_m[-1]["iterations"]),
+            "kernel_us_per_iteration": {"stencil": 1e3 * sum(x["ms_k_stencil"] for x in s_m) / it_m,
+                                        "seed_update": 1e3 * sum(x["ms_k_seed"] for x in s_m) / it_m,
+                                        "seed_direction": 1e3 * sum(x["ms_k_scalars"] for x in s_m) / it_m,
+                                        "shift_update": 1e3 * ms_upd_m / it_m, "timed_iterations": it_m},
+            "roofline": {"kernel": "cg_update_df_kernel (fused multi-shift update, float-float)", "bound": "hbm",
+                         "achieved": gbs_m, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                         "frac": gbs_m / peaks["hbm_gbs"], "traffic": None,
+                         "avg_launch_us": 1e3 * ms_upd_m / it_m},
+        }
+        del lat_m
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -275,16 +342,21 @@ def run_ours(args):
                 "hbm_achieved_gbs": bytes_upd / (ms_upd / 1e3) / 1e9,
                 "hbm_frac_of_measured": bytes_upd / (ms_upd / 1e3) / 1e9 / peaks["hbm_gbs"],
                 "avg_launch_us": 1e3 * ms_upd / max(1, launches_upd),
-                "share_of_step": ms_upd / total_ms * world,
+                "fraction_of_cg_iteration": (ms_upd / max(1, it_tot)) /
+                                            (stats[-1]["ms_cg"] / max(1, stats[-1]["iterations"])),
             },
             "stencil": {"bound": "alu", "achieved_tflops": sten_flops / (ms_sten / 1e3) / 1e12,
                         "frac_fp64_peak": sten_flops / (ms_sten / 1e3) / 1e12 / FP64_PEAK_TFLOPS,
                         "hbm_gbs": sten_bytes / (ms_sten / 1e3) / 1e9,
                         "avg_launch_us": 1e3 * ms_sten / max(1, it_tot)},
-            "kernel_ms_per_step": {"stencil": ms_sten / args.steps, "seed_update": sum(s["ms_k_seed"] for s in stats) / args.steps,
-                                   "shift_scalars": sum(s["ms_k_scalars"] for s in stats) / args.steps,
-                                   "shift_update": ms_upd / args.steps},
-            "e2e": e2e, "cpu_baseline": cpu, "clocks": clk, "gpu_launches": int(launches),
+            "kernel_us_per_iteration": {"stencil": 1e3 * ms_sten / max(1, it_tot),
+                                        "seed_update": 1e3 * sum(s["ms_k_seed"] for s in stats) / max(1, it_tot),
+                                        "seed_direction": 1e3 * sum(s["ms_k_scalars"] for s in stats) / max(1, it_tot),
+                                        "shift_update": 1e3 * ms_upd / max(1, it_tot),
+                                        "timed_iterations": it_tot,
+                                        "note": "CUDA events on one 16-iteration chunk in four; the shift update "
+                                                "overlaps the next iteration's stencil and seed kernels"},
+            "e2e": e2e, "cpu_baseline": cpu, "clocks": clk, "gpu_launches": int(launches), "mixed": mixed,
         }
         print(json.dumps(out), flush=True)
     if world > 1:
@@ -376,6 +448,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the float-float arm")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     args = ap.parse_args()
     if args.impl == "reference":

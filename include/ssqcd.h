@@ -108,14 +108,18 @@ typedef struct {
   long long shift_updates;/* sum over (source, shift) of iterations before freezing:
                              each is one y / p-hat update of n elements            */
   /* Per-kernel device time of the shifted-CG loop, filled when kernel timing
-   * is on (ssqcd_set_kernel_timing): CUDA events on the lattice stream around
-   * every launch; zero otherwise. */
+   * is on (ssqcd_set_kernel_timing): CUDA events around every launch, on the
+   * stream each kernel runs on, in one chunk of 16 iterations out of every 4
+   * (the sums below cover those timed iterations only); zero otherwise.  The
+   * shift update of one iteration runs on a second stream beside the stencil
+   * and seed work of the next, so these times overlap. */
   int    timed;
-  int    launches_update;   /* fused multi-shift update launches that did work   */
-  double ms_k_stencil;      /* stencil q = K p with the (p, q) partials           */
-  double ms_k_seed;         /* seed update r -= alpha q                           */
-  double ms_k_scalars;      /* shift scalar recurrences                           */
+  int    launches_update;   /* timed iterations that did work                    */
+  double ms_k_stencil;      /* stencil q = K p with the (p, q) partials and alpha */
+  double ms_k_seed;         /* seed update r -= alpha q, shift scalars, freezing  */
+  double ms_k_scalars;      /* seed direction p = r + beta p                      */
   double ms_k_update;       /* fused multi-shift update                           */
+  long long timed_shift_updates; /* (source, shift) updates in the timed iterations */
 } ssqcd_stats;
 
 /* ---- lattice / operator ---------------------------------------------------- */

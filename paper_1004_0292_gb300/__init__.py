@@ -62,6 +62,7 @@ class Stats(C.Structure):
         ("gamma", C.c_double), ("rho", C.c_double), ("points", C.c_int), ("shift_updates", C.c_longlong),
         ("timed", C.c_int), ("launches_update", C.c_int), ("ms_k_stencil", C.c_double),
         ("ms_k_seed", C.c_double), ("ms_k_scalars", C.c_double), ("ms_k_update", C.c_double),
+        ("timed_shift_updates", C.c_longlong),
     ]
 
     def as_dict(self):

@@ -452,6 +452,7 @@ extern "C" int ssqcd_ss_solve(ssqcd_lattice lat, const double interval[2], int N
   res->stats.ms_k_seed = cg.ms_k[1];
   res->stats.ms_k_scalars = cg.ms_k[2];
   res->stats.ms_k_update = cg.ms_k[3];
+  res->stats.timed_shift_updates = cg.timed_units;
   if (s1 != SSQCD_OK) return bail(s1);
   vd.release();
 

@@ -148,8 +148,9 @@ struct ShiftedCGOut {
   float ms = 0.f;
   long long shift_updates = 0;
   bool timed = false;
-  int launches_update = 0;
-  double ms_k[4] = {0, 0, 0, 0};  // stencil, seed update, scalars, shift update
+  int launches_update = 0;        // timed iterations (with work)
+  long long timed_units = 0;      // (source, shift) updates in the timed iterations
+  double ms_k[4] = {0, 0, 0, 0};  // stencil, seed update, seed direction, shift update (timed iterations)
 };
 bool kernel_timing_enabled();
 inline bool is_mixed(int precision) { return precision == SSQCD_MIXED || precision == SSQCD_MIXED_F32LINKS; }

@@ -1054,9 +1054,10 @@ int run_shifted_cg(ssqcd_lattice lat, int N, const double2* z_host, int L, const
     tev.resize(kChunk * kSlots);
     for (auto& e : tev) SS_CUDA(cudaEventCreate(&e));
   }
+  bool mark_on = false;  // events recorded in the chunk being built / launched
   auto mark = [&](int it, int slot, cudaStream_t s_) {
     // during capture, only the External flag makes a real event-record node
-    if (timing) cudaEventRecordWithFlags(tev[it * kSlots + slot], s_, cudaEventRecordExternal);
+    if (mark_on) cudaEventRecordWithFlags(tev[it * kSlots + slot], s_, cudaEventRecordExternal);
   };
   const dim3 grid_a(nbw, L), grid_b(nbs, L), grid_c(nbu, L);
   VR* const r0 = r.as<VR>();
@@ -1106,36 +1107,50 @@ int run_shifted_cg(ssqcd_lattice lat, int N, const double2* z_host, int L, const
   };
   // A chunk of iterations is captured once as a CUDA graph and replayed (the
   // kernels read all per-iteration state from device memory, so every replay
-  // is the same graph; node priorities are kept).  With kernel timing on,
-  // the graph also records an event around every kernel; they are read after
-  // each replay.  A stream that cannot be captured (the legacy default
-  // stream) falls back to direct launches.
-  cudaGraphExec_t gexec = nullptr;
-  {
+  // is the same graph; node priorities are kept).  With kernel timing on, a
+  // second graph also records an event around every kernel; it replaces the
+  // plain one for one chunk in kTimedEvery (the event nodes cost ~7% of the
+  // loop), and its events are read after that replay.  A stream that cannot
+  // be captured (the legacy default stream) falls back to direct launches.
+  constexpr int kTimedEvery = 4;
+  auto capture = [&](bool with_events) {
+    cudaGraphExec_t ge = nullptr;
     cudaGraph_t graph = nullptr;
+    mark_on = with_events;
     if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
       run_chunk(kChunk);
       if (cudaStreamEndCapture(st, &graph) == cudaSuccess && graph != nullptr) {
-        if (cudaGraphInstantiate(&gexec, graph, cudaGraphInstantiateFlagUseNodePriority) != cudaSuccess)
-          gexec = nullptr;
+        if (cudaGraphInstantiate(&ge, graph, cudaGraphInstantiateFlagUseNodePriority) != cudaSuccess) ge = nullptr;
         cudaGraphDestroy(graph);
       }
     }
     (void)cudaGetLastError();  // a failed capture falls back to direct launches
-  }
+    mark_on = false;
+    return ge;
+  };
+  cudaGraphExec_t gexec = capture(false);
+  cudaGraphExec_t gexec_t = (timing && gexec != nullptr) ? capture(true) : nullptr;
+  int* h_iters = nullptr;  // per-shift iteration counts, read after each chunk when timing
+  if (timing) SS_CUDA(cudaMallocHost(&h_iters, sizeof(int) * NL));
+  long long units_prev = 0, timed_units = 0;
+  std::vector<int> t_k;  // global iteration index of each timed iteration
   const int ru_chunks = reliable_every > 0 ? std::max(1, (reliable_every + kChunk / 2) / kChunk) : 0;
   int chunks_done = 0;
   while (true) {
     const int chunk = std::min(kChunk, max_iter - k);
+    const int k_start = k;
+    const bool tchunk = timing && chunks_done % kTimedEvery == 0 && (gexec == nullptr || gexec_t != nullptr);
     int launched = 0;
     if (gexec != nullptr && chunk == kChunk) {
-      cudaError_t ge = cudaGraphLaunch(gexec, st);
+      cudaError_t ge = cudaGraphLaunch(tchunk ? gexec_t : gexec, st);
       if (ge != cudaSuccess) { status = cuda_fail(ge, "shifted CG graph launch", __FILE__, __LINE__); break; }
       k += kChunk;
       launched = kChunk;
       count_launches(4LL * kChunk);
     } else {
+      mark_on = tchunk;
       run_chunk(chunk);
+      mark_on = false;
       k += chunk;
       launched = chunk;
       count_launches(4LL * chunk);
@@ -1156,15 +1171,24 @@ int run_shifted_cg(ssqcd_lattice lat, int N, const double2* z_host, int L, const
     // live-shift count after the last iteration, and the error flag
     cudaError_t ce = cudaMemcpyAsync(h_poll, c.live_total, sizeof(int), cudaMemcpyDeviceToHost, st);
     if (ce == cudaSuccess) ce = cudaMemcpyAsync(h_poll + 1, c.err, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (ce == cudaSuccess && timing) ce = cudaMemcpyAsync(h_iters, c.iters, sizeof(int) * NL, cudaMemcpyDeviceToHost, st);
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
     if (ce != cudaSuccess) { status = cuda_fail(ce, "shifted CG poll", __FILE__, __LINE__); break; }
     if (timing) {
-      for (int it = 0; it < launched; ++it)
-        for (int cls = 0; cls < 4; ++cls) {
-          float ms = 0.f;
-          cudaEventElapsedTime(&ms, tev[it * kSlots + 2 * cls], tev[it * kSlots + 2 * cls + 1]);
-          t_iter[cls].push_back(ms);
+      long long units = 0;
+      for (int qi = 0; qi < NL; ++qi) units += h_iters[qi];
+      if (tchunk) {
+        timed_units += units - units_prev;
+        for (int it = 0; it < launched; ++it) {
+          t_k.push_back(k_start + it);
+          for (int cls = 0; cls < 4; ++cls) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, tev[it * kSlots + 2 * cls], tev[it * kSlots + 2 * cls + 1]);
+            t_iter[cls].push_back(ms);
+          }
         }
+      }
+      units_prev = units;
     }
     if (h_poll[1] != 0) { status = fail(SSQCD_ERR_BREAKDOWN, "seed CG breakdown: |(p, K p)| < 1e-30 (r, r)"); break; }
     if (h_poll[0] == 0) break;
@@ -1176,6 +1200,8 @@ int run_shifted_cg(ssqcd_lattice lat, int N, const double2* z_host, int L, const
     }
   }
   if (gexec != nullptr) cudaGraphExecDestroy(gexec);
+  if (gexec_t != nullptr) cudaGraphExecDestroy(gexec_t);
+  if (h_iters != nullptr) cudaFreeHost(h_iters);
   if (status == SSQCD_OK || status == SSQCD_ERR_BREAKDOWN || status == SSQCD_ERR_NOCONV) {
     if (kShift32) {  // hand FP64 solutions to the FP64 moments and Rayleigh-Ritz
       SS_TRY(y_out.alloc(sizeof(double2) * n * NL));
@@ -1216,13 +1242,17 @@ int run_shifted_cg(ssqcd_lattice lat, int N, const double2* z_host, int L, const
       out->shift_updates = 0;
       for (int v2 : it_all) out->shift_updates += v2;
       out->timed = timing;
-      out->launches_update = timing ? std::min<int>(counters[0], (int)t_iter[2].size()) : 0;
+      out->timed_units = timed_units;
+      int n_timed = 0;
+      for (int kk : t_k) n_timed += kk < counters[0] ? 1 : 0;
+      out->launches_update = n_timed;
       for (int cls = 0; cls < 4; ++cls) out->ms_k[cls] = 0.0;
       const int slot_of[4] = {0, 1, 3, 2};  // stencil, seed update + scalars, shift update, seed p
       for (int cls = 0; cls < 4; ++cls) {
         double acc = 0.0;
         // iterations after the last live one skip their work: not counted
-        for (int i = 0; i < (int)t_iter[cls].size() && i < counters[0]; ++i) acc += t_iter[cls][i];
+        for (size_t i = 0; i < t_iter[cls].size(); ++i)
+          if (t_k[i] < counters[0]) acc += t_iter[cls][i];
         out->ms_k[slot_of[cls]] = acc;
       }
     }
