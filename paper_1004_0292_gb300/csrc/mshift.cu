@@ -83,6 +83,7 @@ struct Control {
   int* err;            // [1]
   int* seed_iters;     // [2]     seed iterations, reliable updates applied
   unsigned* done;      // [2]     last-block tickets of kernels A and B
+  unsigned* task_ctr;  // [2]     per parity: next task of the TMA-fed update (reset by B)
   double2* shift_s;    // [L*N]   s_j = z_j - sigma
   double2* xi_cur;     // [L*N]   xi_k
   double2* xi_prev;    // [L*N]   xi_{k-1}
@@ -177,6 +178,7 @@ __global__ void init_control_kernel(Control c, const double* __restrict__ vn2, i
     *c.err = 0;
     c.seed_iters[0] = c.seed_iters[1] = 0;
     c.done[0] = c.done[1] = 0u;
+    c.task_ctr[0] = c.task_ctr[1] = 0u;
   }
 }
 
@@ -184,6 +186,8 @@ __global__ void init_control_kernel(Control c, const double* __restrict__ vn2, i
 // Stencil of one block for one source: q = sigma p - gamma5 (p - kappa D p) at
 // spin w's three components of site s; returns this thread's share of (p, q).
 struct Stencil64 {
+  static constexpr int kThreads = kStencilThreads;
+  static constexpr int kMinBlocks = 1;
   const double2* __restrict__ u;
   __device__ __forceinline__ double run(const Geometry& g, const double2* __restrict__ p, double2* __restrict__ q,
                                         double sigma, int s, int w, void* shm) const {
@@ -210,6 +214,8 @@ struct Stencil64 {
 
 template <typename LK>
 struct Stencil32 {
+  static constexpr int kThreads = kStencilThreads;
+  static constexpr int kMinBlocks = 1;
   LK lk;
   __device__ __forceinline__ double run(const Geometry& g, const float2* __restrict__ p, float2* __restrict__ q,
                                         double sigma, int s, int w, void* shm) const {
@@ -234,32 +240,42 @@ struct Stencil32 {
   }
 };
 
-// float-float stencil (SSQCD_DF): q = sigma p - A p, float-float share of (p, q)
+// float-float stencil (SSQCD_DF): q = sigma p - A p, float-float share of
+// (p, q); one hop per warp, 8 warps per block (wilson_df.cuh)
 struct StencilDF {
+  static constexpr int kThreads = kStencilThreadsDF;
+  static constexpr int kMinBlocks = 1;  // a 64-register cap (4 blocks / SM) spilled and measured slower
   const float4* __restrict__ u;
   __device__ __forceinline__ double run(const Geometry& g, const float4* __restrict__ p, float4* __restrict__ q,
                                         double sigma, int s, int w, void* shm) const {
-    float4 acc[3];
-    block_hops_df(LinksDF{u, g.V}, p, s, g, static_cast<float4*>(shm), acc);
+    float4* sh = static_cast<float4*>(shm);
+    const int lane = threadIdx.x & 31;
+    block_hops_df8(LinksDF{u, g.V}, p, s, g, sh);
     double d = 0.0;
     if (s < g.V) {
-      const float2 t = finish_df(g, p, q, ff::split(sigma), make_float2(-1.f, 0.f), s, w, acc);
+      const float2 c0 = ff::split(sigma), c1 = make_float2(-1.f, 0.f);
+      float2 t = finish_df1(g, p, q, c0, c1, s, w, hop_sum_df(sh, w, lane));
       d = (double)t.x + (double)t.y;
+      if (w < 4) {
+        t = finish_df1(g, p, q, c0, c1, s, w + 8, hop_sum_df(sh, w + 8, lane));
+        d += (double)t.x + (double)t.y;
+      }
     }
     return d;
   }
 };
 
 template <typename Op, typename V2>
-__global__ void __launch_bounds__(kStencilThreads)
+__global__ void __launch_bounds__(Op::kThreads, Op::kMinBlocks)
 cg_stencil_kernel(Control c, int L, int par, Geometry g, Op op, double sigma, const V2* __restrict__ p_all,
                   V2* __restrict__ q_all) {
   if (*c.err != 0 || *c.live_total == 0) {
     if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *c.ran = c.rec_ran[par] = 0;
     return;
   }
-  __shared__ double2 sh[12 * 4 * 32];
-  __shared__ double sred[kStencilThreads / 32];
+  constexpr int kWarps = Op::kThreads / 32;
+  __shared__ double2 sh[12 * 4 * 32];  // 24 KB: 12 x 4 x 32 double2 or 8 x 6 x 32 float4
+  __shared__ double sred[kWarps];
   __shared__ double sums[kMaxSources];
   __shared__ bool s_last;
   const int l = blockIdx.y;
@@ -275,7 +291,10 @@ cg_stencil_kernel(Control c, int L, int par, Geometry g, Op op, double sigma, co
   __syncthreads();
   const int nbw = gridDim.x;
   if (threadIdx.x == 0) {
-    const double t = (sred[0] + sred[1]) + (sred[2] + sred[3]);
+    // pairwise sum of the warp partials (fixed order)
+    double t = (sred[0] + sred[1]) + (sred[2] + sred[3]);
+    if constexpr (kWarps == 8) t += (sred[4] + sred[5]) + (sred[6] + sred[7]);
+    static_assert(kWarps == 4 || kWarps == 8, "four or eight warps");
     c.partial[(size_t)l * nbw + blockIdx.x] = t;
     __threadfence();
     const unsigned ticket = atomicAdd(&c.done[0], 1u);
@@ -284,8 +303,8 @@ cg_stencil_kernel(Control c, int L, int par, Geometry g, Op op, double sigma, co
   __syncthreads();
   if (!s_last) return;
   __threadfence();
-  // warp w sums the partials of sources w, w+4, ... in a fixed order
-  for (int ls = w; ls < L; ls += kStencilThreads / 32) {
+  // warp w sums the partials of sources w, w + kWarps, ... in a fixed order
+  for (int ls = w; ls < L; ls += kWarps) {
     double a0 = 0.0, a1 = 0.0;
     int b = lane;
     for (; b + 32 < nbw; b += 64) {
@@ -512,6 +531,7 @@ cg_seed_kernel(Control c, int L, int N, int par, double tol2, const V2* __restri
     for (int ls = 0; ls < L; ++ls) tot += c.live[ls];
     *c.live_total = tot;
     c.done[1] = 0u;
+    c.task_ctr[par] = 0u;
   }
 }
 
@@ -753,6 +773,191 @@ cg_update_df_kernel(Control c, int N, int par, const RT* __restrict__ r, float4*
   }
 }
 
+// ---- fused update, float-float shift vectors, fed by bulk copies -----------------------
+// Persistent form of the float-float kernel C: one CTA per SM with 8
+// consumer warps and 1 producer warp and a ring of kTmaStages shared-memory
+// stages.  A task is (source l, chunk of kTmaCh elements); the producer takes
+// tasks from a per-parity counter, and for each listed shift of the task
+// fills the next free stage with the y and p-hat segments of that shift
+// (plus the r segment for the task's first shift) by bulk copies
+// (cp.async.bulk, completion counted on the stage's mbarrier); consumer
+// thread i updates elements i, i + 256, ... and writes y and p-hat back to
+// global memory, then the warps release the stage.  A CTA this small leaves
+// room on every SM for the blocks of the stencil and seed kernels that run
+// beside it, while the stage ring keeps kTmaStages x 16 KB of loads in flight
+// per SM.
+// Every wait is bounded: past kSpinLimit polls the kernel sets c.err = 2,
+// drains its outstanding copies (bounded again) and returns.
+constexpr int kTmaConsumerWarps = 8;
+constexpr int kTmaEpt = 2;  // elements per consumer thread and stage
+constexpr int kTmaCh = kTmaConsumerWarps * 32 * kTmaEpt;
+constexpr int kTmaStages = 4;
+constexpr int kTmaThreads = (kTmaConsumerWarps + 1) * 32;
+constexpr long long kSpinLimit = 1LL << 22;
+
+struct __align__(16) TmaStage {
+  float4 y[kTmaCh];
+  float4 h[kTmaCh];
+  float4 r[kTmaCh];
+};
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_test(unsigned long long* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// true once the phase of the given parity has completed; false after kSpinLimit polls
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
+  for (long long i = 0; i < kSpinLimit; ++i)
+    if (mbar_test(bar, parity)) return true;
+  return false;
+}
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+size_t tma_smem_bytes(int NL, int L) {
+  return sizeof(TmaStage) * kTmaStages + 2 * kTmaStages * sizeof(unsigned long long) + kTmaStages * sizeof(int4) +
+         (size_t)NL * (2 * sizeof(float4) + sizeof(int)) + (size_t)L * sizeof(int);
+}
+
+template <typename RT>
+__global__ void __launch_bounds__(kTmaThreads, 1)
+cg_update_tma_kernel(Control c, int N, int L, int par, const RT* __restrict__ r, float4* __restrict__ y,
+                     float4* __restrict__ ph, long long n, int nchunks) {
+  if (c.rec_ran[par] == 0) return;
+  extern __shared__ __align__(128) unsigned char smem[];
+  TmaStage* stage = reinterpret_cast<TmaStage*>(smem);
+  unsigned long long* full = reinterpret_cast<unsigned long long*>(stage + kTmaStages);
+  unsigned long long* empty = full + kTmaStages;
+  int4* meta = reinterpret_cast<int4*>(empty + kTmaStages);
+  const int NL = N * L;
+  float4* la = reinterpret_cast<float4*>(meta + kTmaStages);
+  float4* lb = la + NL;
+  int* lj = reinterpret_cast<int*>(lb + NL);
+  int* ln = lj + NL;
+  // this iteration's record, coefficients split to float-float once
+  for (int i = threadIdx.x; i < NL; i += blockDim.x) {
+    const int l = i / N, t = i - l * N;
+    if (t < c.list_n[par * L + l]) {
+      const int o = par * NL + i;
+      la[i] = ff::from_double2(c.list_a[o]);
+      lb[i] = ff::from_double2(c.list_b[o]);
+      lj[i] = c.list_j[o];
+    }
+  }
+  for (int l = threadIdx.x; l < L; l += blockDim.x) ln[l] = c.list_n[par * L + l];
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kTmaStages; ++s) {
+      mbar_init(full + s, 1);
+      mbar_init(empty + s, kTmaConsumerWarps);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (warp == kTmaConsumerWarps) {
+    // ---- producer (one lane) ----
+    if (lane != 0) return;
+    const unsigned total = (unsigned)L * (unsigned)nchunks;
+    long long s = 0;  // stages issued
+    bool ok = true;
+    for (;;) {
+      const unsigned task = atomicAdd(c.task_ctr + par, 1u);
+      if (task >= total) break;
+      const int l = (int)(task / (unsigned)nchunks), ch = (int)(task % (unsigned)nchunks);
+      const int m = ln[l];
+      const long long e0 = (long long)ch * kTmaCh;
+      const unsigned cnt = (unsigned)min((long long)kTmaCh, n - e0);
+      for (int t = 0; t < m && ok; ++t, ++s) {
+        const int slot = (int)(s % kTmaStages);
+        if (s >= kTmaStages) ok = mbar_wait(empty + slot, (unsigned)((s / kTmaStages + 1) & 1));
+        if (!ok) break;
+        meta[slot] = make_int4(l, ch, t, (int)cnt);
+        const long long off = ((long long)l * N + lj[l * N + t]) * n + e0;
+        mbar_arrive_tx(full + slot, (t == 0 ? 3u : 2u) * cnt * 16u);
+        bulk_load(stage[slot].y, y + off, cnt * 16u, full + slot);
+        bulk_load(stage[slot].h, ph + off, cnt * 16u, full + slot);
+        if (t == 0) bulk_load(stage[slot].r, r + (long long)l * n + e0, cnt * 16u, full + slot);
+      }
+      if (!ok) break;
+    }
+    if (ok) {  // end marker for the consumers
+      const int slot = (int)(s % kTmaStages);
+      if (s >= kTmaStages) ok = mbar_wait(empty + slot, (unsigned)((s / kTmaStages + 1) & 1));
+      if (ok) {
+        meta[slot] = make_int4(-1, 0, 0, 0);
+        mbar_arrive(full + slot);
+      }
+    }
+    if (!ok) {
+      atomicExch(c.err, 2);
+      // let the copies already issued land before the CTA can exit
+      for (long long q = s - 1; q >= 0 && q >= s - kTmaStages; --q)
+        (void)mbar_wait(full + (int)(q % kTmaStages), (unsigned)((q / kTmaStages) & 1));
+    }
+    return;
+  }
+  // ---- consumers: thread i <-> elements i + 256 e of the chunk ----
+  constexpr int kConsumers = kTmaConsumerWarps * 32;
+  const int i = threadIdx.x;
+  float4 rv[kTmaEpt];
+#pragma unroll
+  for (int e = 0; e < kTmaEpt; ++e) rv[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (long long s = 0;; ++s) {
+    const int slot = (int)(s % kTmaStages);
+    if (!mbar_wait(full + slot, (unsigned)((s / kTmaStages) & 1))) {
+      atomicExch(c.err, 2);
+      return;
+    }
+    const int4 mt = meta[slot];
+    if (mt.x < 0) return;
+    const int l = mt.x, t = mt.z;
+    const int q = l * N + t;
+    const float4 a = la[q], b = lb[q];
+    if (t == 0) {
+      const double sc = c.list_sc[par * L + l];
+#pragma unroll
+      for (int e = 0; e < kTmaEpt; ++e)
+        if (i + e * kConsumers < mt.w)
+          rv[e] = scaled_r(reinterpret_cast<const RT*>(stage[slot].r)[i + e * kConsumers], sc);
+    }
+    const long long base = ((long long)l * N + lj[q]) * n + (long long)mt.y * kTmaCh + i;
+    float4 yv[kTmaEpt], hv[kTmaEpt];
+#pragma unroll
+    for (int e = 0; e < kTmaEpt; ++e)
+      if (i + e * kConsumers < mt.w) {
+        yv[e] = stage[slot].y[i + e * kConsumers];
+        hv[e] = stage[slot].h[i + e * kConsumers];
+      }
+#pragma unroll
+    for (int e = 0; e < kTmaEpt; ++e)
+      if (i + e * kConsumers < mt.w) {
+        y[base + e * kConsumers] = ff::cfma(yv[e], a, hv[e]);
+        ph[base + e * kConsumers] = ff::cfma(rv[e], b, hv[e]);
+      }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(empty + slot);
+  }
+}
+
 // In-place conversion of float-float solutions to FP64 (same element size).
 __global__ void df_to_f64_kernel(float4* __restrict__ y, long long count) {
   double2* out = reinterpret_cast<double2*>(y);
@@ -832,11 +1037,12 @@ cg_reliable_kernel(Control c, int L, const double2* __restrict__ v, const double
 // runs at the device's greatest priority so that its blocks are dispatched
 // ahead of the remaining blocks of the concurrent shift update C.
 template <typename... KArgs, typename... Args>
-void launch_prio(void (*kern)(KArgs...), dim3 grid, dim3 block, cudaStream_t st, int prio, Args&&... args) {
+void launch_prio_smem(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, int prio,
+                      Args&&... args) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = grid;
   cfg.blockDim = block;
-  cfg.dynamicSmemBytes = 0;
+  cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributePriority;
@@ -844,6 +1050,10 @@ void launch_prio(void (*kern)(KArgs...), dim3 grid, dim3 block, cudaStream_t st,
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
+template <typename... KArgs, typename... Args>
+void launch_prio(void (*kern)(KArgs...), dim3 grid, dim3 block, cudaStream_t st, int prio, Args&&... args) {
+  launch_prio_smem(kern, grid, block, 0, st, prio, std::forward<Args>(args)...);
 }
 
 int seed_blocks(long long n, int L) {
@@ -888,6 +1098,31 @@ void launch_update_df(int ept, int L, cudaStream_t st, int prio, const Control& 
   }
 }
 
+// The TMA-fed float-float update (default; SSQCD_UPDATE_TMA=0 selects the
+// grouped register kernel instead, for comparison runs).
+bool use_tma_update() {
+  static const bool v = [] {
+    const char* e = std::getenv("SSQCD_UPDATE_TMA");
+    return !(e && e[0] == '0');
+  }();
+  return v;
+}
+
+template <typename RT>
+int prepare_update_tma(int NL, int L) {
+  const size_t smem = tma_smem_bytes(NL, L);
+  SS_CUDA(cudaFuncSetAttribute(cg_update_tma_kernel<RT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  return SSQCD_OK;
+}
+
+template <typename RT>
+void launch_update_tma(int nblocks, int L, cudaStream_t st, int prio, const Control& c, int N, int par, const RT* r,
+                       float4* y, float4* ph, long long n) {
+  const int nchunks = (int)((n + kTmaCh - 1) / kTmaCh);
+  launch_prio_smem(cg_update_tma_kernel<RT>, dim3(nblocks), dim3(kTmaThreads), tma_smem_bytes(N * L, L), st, prio, c,
+                   N, L, par, r, y, ph, n, nchunks);
+}
+
 int update_blocks(long long n, int L, int ept) {
   const long long chunks = (n + (long long)kUpdBlock * ept - 1) / ((long long)kUpdBlock * ept);
   const long long cap = (152LL * 8 + L - 1) / L;
@@ -912,6 +1147,16 @@ int run_shifted_cg(ssqcd_lattice lat, int N, const double2* z_host, int L, const
   constexpr bool kShiftDF = std::is_same<V2, float4>::value; // shift vectors in float-float
   constexpr bool kSeedDF = std::is_same<VR, float4>::value;  // seed vectors and stencil in float-float
   if constexpr (kSeedDF) SS_TRY(ensure_df_links(lat));
+  const bool tma = kShiftDF && use_tma_update();
+  int n_sm = 0;
+  {
+    int dev = 0;
+    SS_CUDA(cudaGetDevice(&dev));
+    SS_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
+  }
+  if constexpr (kShiftDF) {
+    if (tma) SS_TRY(prepare_update_tma<VR>(N * L, L));
+  }
   cudaStream_t st = lat->stream;
   const Geometry& g = lat->g;
   const long long n = 12LL * g.V;
@@ -959,7 +1204,7 @@ int run_shifted_cg(ssqcd_lattice lat, int N, const double2* z_host, int L, const
                o_vn = take(sizeof(double) * L), o_live = take(sizeof(int) * L), o_tot = take(sizeof(int)),
                o_ran = take(sizeof(int)), o_rran = take(sizeof(int) * 2), o_err = take(sizeof(int)),
                o_si = take(sizeof(int) * 2),
-               o_done = take(sizeof(unsigned) * 2), o_s = take(sizeof(double2) * NL),
+               o_done = take(sizeof(unsigned) * 4), o_s = take(sizeof(double2) * NL),
                o_xc = take(sizeof(double2) * NL), o_xp = take(sizeof(double2) * NL),
                o_xn = take(sizeof(double2) * NL), o_rt = take(sizeof(double2) * NL), o_act = take(sizeof(int) * NL),
                o_it = take(sizeof(int) * NL), o_ln = take(sizeof(int) * 2 * L), o_lj = take(sizeof(int) * 2 * NL),
@@ -980,6 +1225,7 @@ int run_shifted_cg(ssqcd_lattice lat, int N, const double2* z_host, int L, const
   c.err = reinterpret_cast<int*>(base + o_err);
   c.seed_iters = reinterpret_cast<int*>(base + o_si);
   c.done = reinterpret_cast<unsigned*>(base + o_done);
+  c.task_ctr = c.done + 2;
   c.shift_s = reinterpret_cast<double2*>(base + o_s);
   c.xi_cur = reinterpret_cast<double2*>(base + o_xc);
   c.xi_prev = reinterpret_cast<double2*>(base + o_xp);
@@ -1060,6 +1306,7 @@ int run_shifted_cg(ssqcd_lattice lat, int N, const double2* z_host, int L, const
     if (mark_on) cudaEventRecordWithFlags(tev[it * kSlots + slot], s_, cudaEventRecordExternal);
   };
   const dim3 grid_a(nbw, L), grid_b(nbs, L), grid_c(nbu, L);
+  const dim3 grid_p((unsigned)((n + kUpdBlock - 1) / kUpdBlock), L);  // one element per thread
   VR* const r0 = r.as<VR>();
   auto iteration = [&](int it) {
     const int par = it & 1;
@@ -1075,7 +1322,7 @@ int run_shifted_cg(ssqcd_lattice lat, int N, const double2* z_host, int L, const
         launch_prio(cg_stencil_kernel<Stencil32<LinksF32>, VR>, grid_a, kStencilThreads, st, prio_hi, c, L, par, g,
                     Stencil32<LinksF32>{LinksF32{lat->u32.as<float4>(), g.V}}, sigma, p.as<VR>(), q.as<VR>());
     } else if constexpr (kSeedDF) {
-      launch_prio(cg_stencil_kernel<StencilDF, VR>, grid_a, kStencilThreads, st, prio_hi, c, L, par, g,
+      launch_prio(cg_stencil_kernel<StencilDF, VR>, grid_a, StencilDF::kThreads, st, prio_hi, c, L, par, g,
                   StencilDF{lat->udf.as<float4>()}, sigma, p.as<VR>(), q.as<VR>());
     } else {
       launch_prio(cg_stencil_kernel<Stencil64, VR>, grid_a, kStencilThreads, st, prio_hi, c, L, par, g,
@@ -1088,12 +1335,16 @@ int run_shifted_cg(ssqcd_lattice lat, int N, const double2* z_host, int L, const
     mark(it, 3, st);
     cudaEventRecord(ev_b(it), st);
     mark(it, 6, st);
-    launch_prio(cg_seed_p_kernel<VR>, grid_b, kUpdBlock, st, prio_hi, c, r_out, p.as<VR>(), n);
+    launch_prio(cg_seed_p_kernel<VR>, grid_p, kUpdBlock, st, prio_hi, c, r_out, p.as<VR>(), n);
     mark(it, 7, st);
     cudaStreamWaitEvent(side, ev_b(it), 0);
     mark(it, 4, side);
-    if constexpr (kShiftDF)
-      launch_update_df<VR>(ept, L, side, prio_lo, c, N, par, r_out, yv, ph.as<float4>(), n);
+    if constexpr (kShiftDF) {
+      if (tma)
+        launch_update_tma<VR>(n_sm, L, side, prio_lo, c, N, par, r_out, yv, ph.as<float4>(), n);
+      else
+        launch_update_df<VR>(ept, L, side, prio_lo, c, N, par, r_out, yv, ph.as<float4>(), n);
+    }
     else
       launch_update<VR, V2>(ept, grid_c, side, prio_lo, c, N, par, r_out, yv, ph.as<V2>(), n);
     mark(it, 5, side);
@@ -1190,6 +1441,7 @@ int run_shifted_cg(ssqcd_lattice lat, int N, const double2* z_host, int L, const
       }
       units_prev = units;
     }
+    if (h_poll[1] == 2) { status = fail(SSQCD_ERR_NOCONV, "shift update: a device-side wait hit its limit"); break; }
     if (h_poll[1] != 0) { status = fail(SSQCD_ERR_BREAKDOWN, "seed CG breakdown: |(p, K p)| < 1e-30 (r, r)"); break; }
     if (h_poll[0] == 0) break;
     if (k >= max_iter) {

@@ -109,19 +109,21 @@ wilson32_kernel(Geometry g, LK lk, const float2* __restrict__ in_all,
 
 // Float-float stencil (SSQCD_DF): out = c0 in + c1 A in with float-float
 // spinors and links; see wilson_df.cuh.
-__global__ void __launch_bounds__(kStencilThreads)
+__global__ void __launch_bounds__(kStencilThreadsDF)
 wilson_df_kernel(Geometry g, const float4* __restrict__ u, const float4* __restrict__ in_all,
                  float4* __restrict__ out_all, float2 c0, float2 c1) {
-  __shared__ float4 sh[12 * 4 * 32];
+  __shared__ float4 sh[8 * 6 * 32];
   const int rhs = blockIdx.y;
   const int V = g.V;
   const float4* in = in_all + (size_t)rhs * 12 * V;
   float4* out = out_all + (size_t)rhs * 12 * V;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int s = blockIdx.x * kSitesPerBlock + lane;
-  float4 acc[3];
-  block_hops_df(LinksDF{u, V}, in, s, g, sh, acc);
-  if (s < V) (void)finish_df(g, in, out, c0, c1, s, w, acc);
+  block_hops_df8(LinksDF{u, V}, in, s, g, sh);
+  if (s < V) {
+    (void)finish_df1(g, in, out, c0, c1, s, w, hop_sum_df(sh, w, lane));
+    if (w < 4) (void)finish_df1(g, in, out, c0, c1, s, w + 8, hop_sum_df(sh, w + 8, lane));
+  }
 }
 
 // FP64 <-> float-float complex arrays (same element size)
@@ -205,7 +207,7 @@ int wilson_df(const Geometry& g, const float4* u, const float4* in, float4* out,
     const float h = (float)x;
     return make_float2(h, (float)(x - (double)h));
   };
-  wilson_df_kernel<<<grid, kStencilThreads, 0, s>>>(g, u, in, out, split(c0), split(c1));
+  wilson_df_kernel<<<grid, kStencilThreadsDF, 0, s>>>(g, u, in, out, split(c0), split(c1));
   count_launches(1);
   SS_CHECK_LAUNCH();
   return SSQCD_OK;

