@@ -22,7 +22,7 @@ import numpy as np
 
 __all__ = [
     "OK", "ERR_ARG", "ERR_OOM", "ERR_BREAKDOWN", "ERR_NOCONV", "ERR_CUDA",
-    "FP64", "MIXED", "MIXED_F32LINKS", "FP64_SHIFT32", "FP64_DFSHIFT", "DF", "PATH_LINES", "PATH_CIRCLE", "SsqcdError",
+    "FP64", "MIXED", "MIXED_F32LINKS", "FP64_SHIFT32", "FP64_DFSHIFT", "DF", "EXTRACT_RR", "EXTRACT_HANKEL", "PATH_LINES", "PATH_CIRCLE", "SsqcdError",
     "library_path", "lib", "create_lattice", "upload_gauge", "apply_H", "apply_H_mixed",
     "contour", "shifted_cg", "moments", "moments_noalloc", "ss_solve", "ss_eigpairs", "small_eigh",
     "kernel_launches", "set_kernel_timing", "Lattice", "Result", "Opts", "Stats",
@@ -30,6 +30,7 @@ __all__ = [
 
 OK, ERR_ARG, ERR_OOM, ERR_BREAKDOWN, ERR_NOCONV, ERR_CUDA = 0, 1, 2, 3, 4, 5
 FP64, MIXED, MIXED_F32LINKS, FP64_SHIFT32, FP64_DFSHIFT, DF = 0, 1, 2, 3, 4, 5
+EXTRACT_RR, EXTRACT_HANKEL = 0, 1
 PATH_LINES, PATH_CIRCLE = 0, 1
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -50,7 +51,7 @@ class Opts(C.Structure):
         ("path", C.c_int), ("beta", C.c_double), ("nprime", C.c_int), ("tol", C.c_double),
         ("sigma", C.c_double), ("max_iter", C.c_int), ("rank_tol", C.c_double),
         ("sources", C.c_void_p), ("sources_on_device", C.c_int), ("reliable_every", C.c_int),
-        ("windows", C.c_int),
+        ("windows", C.c_int), ("extract", C.c_int), ("hankel_tol", C.c_double),
     ]
 
 
@@ -282,7 +283,8 @@ def moments_noalloc(w, zeta, y, M, stream=None):
 
 
 def ss_solve(lat: Lattice, interval, N, M, sources, beta=0.3, nprime=0, tol=1e-12, sigma=0.0, max_iter=100000,
-             rank_tol=1e-14, path=PATH_LINES, reliable_every=0, windows=1) -> Result:
+             rank_tol=1e-14, path=PATH_LINES, reliable_every=0, windows=1, extract=0,
+             hankel_tol=1e-12) -> Result:
     """Run the solver; returns a Result (check ``status``)."""
     L = int(np.prod(sources.shape)) // lat.n
     o = Opts()
@@ -292,6 +294,7 @@ def ss_solve(lat: Lattice, interval, N, M, sources, beta=0.3, nprime=0, tol=1e-1
     o.max_iter, o.rank_tol, o.sources, o.sources_on_device = int(max_iter), float(rank_tol), ps, dev
     o.reliable_every = int(reliable_every)
     o.windows = int(windows)
+    o.extract, o.hankel_tol = int(extract), float(hankel_tol)
     iv = (C.c_double * 2)(float(interval[0]), float(interval[1]))
     h = C.c_void_p()
     code = lib().ssqcd_ss_solve(lat.handle, iv, int(N), int(M), L, C.byref(o), C.byref(h))

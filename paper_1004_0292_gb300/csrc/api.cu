@@ -257,6 +257,8 @@ extern "C" void ssqcd_default_opts(ssqcd_opts* o) {
   o->rank_tol = 1e-14;
   o->reliable_every = 0;
   o->windows = 1;
+  o->extract = SSQCD_EXTRACT_RR;
+  o->hankel_tol = 1e-12;
 }
 
 namespace {
@@ -356,6 +358,87 @@ int rayleigh_ritz_window(ssqcd_lattice lat, const double2* S, int m, double rank
   return SSQCD_OK;
 }
 
+// Block Hankel extraction for one window (Section 2.1): mu_k = V^H s_hat_k
+// (L x L, k < 2M), H = [mu_{i+j}], H< = [mu_{i+j+1}] (ML x ML); the
+// eigenvalues of the pencil (H<, H) are eta = (lambda - gamma) / rho.  With a
+// contour symmetric under conjugation (both line pairs and the circle are)
+// and Hermitian A, every mu_k is Hermitian and H = W^H f_0(Lambda) W with
+// the filter f_0 > 0 on the real axis, so H is Hermitian positive
+// semidefinite: H = Q diag(h) Q^H truncated to h_i > tol h_max reduces the
+// pencil to the Hermitian matrix h^-1/2 Q^H H< Q h^-1/2, whose eigenvalues
+// are those of the pencil (the same reduction as through the SVD of H,
+// which equals this eigendecomposition).  Both small problems use the host
+// Hermitian eigensolver.  S = [L][2M][n], V = [L][n] (device).
+int hankel_window(const double2* V, int L, const double2* S, int M, long long n, double tol, double gamma,
+                  double rho, double lo, double hi, bool hi_open, std::vector<double>& evals,
+                  std::vector<double>& resid, int& rank, DevBuf& scratch, cudaStream_t st) {
+  const int M2 = 2 * M, m = M * L;
+  DevBuf Gd;
+  SS_TRY(Gd.alloc(sizeof(double2) * L * L * M2));
+  SS_TRY(gram(V, L, S, L * M2, n, Gd.as<double2>(), scratch, st));
+  std::vector<double2> G((size_t)L * L * M2);
+  SS_CUDA(cudaMemcpyAsync(G.data(), Gd.p, sizeof(double2) * G.size(), cudaMemcpyDeviceToHost, st));
+  SS_CUDA(cudaStreamSynchronize(st));
+  // mu_k[l][l'] = v_l^H s_hat_{k, l'} = G[l][l' 2M + k]
+  auto mu = [&](int k, int l, int lp) { return G[(size_t)l * L * M2 + (size_t)lp * M2 + k]; };
+  // Hermitian parts of H and H< (lower triangles suffice for small_eigh)
+  std::vector<double2> H((size_t)m * m), Hs((size_t)m * m);
+  for (int i = 0; i < M; ++i)
+    for (int j = 0; j < M; ++j)
+      for (int l = 0; l < L; ++l)
+        for (int lp = 0; lp < L; ++lp) {
+          const size_t r = (size_t)i * L + l, c = (size_t)j * L + lp;
+          const double2 a0 = mu(i + j, l, lp), b0 = mu(i + j, lp, l);
+          const double2 a1 = mu(i + j + 1, l, lp), b1 = mu(i + j + 1, lp, l);
+          H[r * m + c] = make_double2(0.5 * (a0.x + b0.x), 0.5 * (a0.y - b0.y));
+          Hs[r * m + c] = make_double2(0.5 * (a1.x + b1.x), 0.5 * (a1.y - b1.y));
+        }
+  std::vector<double> h(m);
+  std::vector<double2> Q((size_t)m * m);
+  SS_TRY(small_eigh(m, H.data(), h.data(), Q.data()));
+  const double hmax = h[m - 1];
+  if (!(hmax > 0.0)) return fail(SSQCD_ERR_ARG, "Hankel matrix of the moments is zero");
+  std::vector<int> keep;
+  for (int c = m - 1; c >= 0; --c)
+    if (h[c] > tol * hmax) keep.push_back(c);
+  const int r = (int)keep.size();
+  rank = r;
+  // C = h^-1/2 Q_r^H H< Q_r h^-1/2
+  std::vector<double2> T((size_t)m * r), C((size_t)r * r);
+  for (int a = 0; a < m; ++a)
+    for (int q = 0; q < r; ++q) {  // T = H< Q_r (full H< from its Hermitian lower part)
+      double sr = 0.0, si = 0.0;
+      for (int b = 0; b < m; ++b) {
+        const double2 x = a >= b ? Hs[(size_t)a * m + b] : make_double2(Hs[(size_t)b * m + a].x, -Hs[(size_t)b * m + a].y);
+        const double2 y = Q[(size_t)b * m + keep[q]];
+        sr += x.x * y.x - x.y * y.y;
+        si += x.x * y.y + x.y * y.x;
+      }
+      T[(size_t)a * r + q] = make_double2(sr, si);
+    }
+  for (int p = 0; p < r; ++p)
+    for (int q = 0; q < r; ++q) {
+      double sr = 0.0, si = 0.0;
+      for (int a = 0; a < m; ++a) {
+        const double2 x = Q[(size_t)a * m + keep[p]], y = T[(size_t)a * r + q];
+        sr += x.x * y.x + x.y * y.y;  // conj(x) y
+        si += x.x * y.y - x.y * y.x;
+      }
+      const double sc = 1.0 / std::sqrt(h[keep[p]] * h[keep[q]]);
+      C[(size_t)p * r + q] = make_double2(sr * sc, si * sc);
+    }
+  std::vector<double> eta(r);
+  SS_TRY(small_eigh(r, C.data(), eta.data(), nullptr));
+  for (int c = 0; c < r; ++c) {
+    const double lam = gamma + rho * eta[c];
+    if (lam >= lo && (hi_open ? lam < hi : lam <= hi)) {
+      evals.push_back(lam);
+      resid.push_back(std::nan(""));
+    }
+  }
+  return SSQCD_OK;
+}
+
 }  // namespace
 
 extern "C" int ssqcd_ss_solve(ssqcd_lattice lat, const double interval[2], int N, int M, int L,
@@ -369,6 +452,13 @@ extern "C" int ssqcd_ss_solve(ssqcd_lattice lat, const double interval[2], int N
   ssqcd_default_opts(&o);
   if (opts_in) o = *opts_in;
   if (o.sources == nullptr) return fail(SSQCD_ERR_ARG, "opts.sources is required");
+  if (o.extract != SSQCD_EXTRACT_RR && o.extract != SSQCD_EXTRACT_HANKEL)
+    return fail(SSQCD_ERR_ARG, "unknown extraction");
+  const bool hankel = o.extract == SSQCD_EXTRACT_HANKEL;
+  if (hankel && !(o.hankel_tol > 0.0 && o.hankel_tol < 1.0)) return fail(SSQCD_ERR_ARG, "hankel_tol must be in (0, 1)");
+  // Hankel needs the moments up to k = 2M - 1 (filter identity: 2M <= N)
+  const int MM = hankel ? 2 * M : M;
+  if (hankel && MM > N) return fail(SSQCD_ERR_ARG, "Hankel extraction needs 2M <= N");
   const int K = o.windows < 1 ? 1 : o.windows;
   if (K > 1 && o.path != SSQCD_PATH_LINES) return fail(SSQCD_ERR_ARG, "several windows need the line contour");
   const double a = interval[0], b = interval[1];
@@ -402,15 +492,15 @@ extern "C" int ssqcd_ss_solve(ssqcd_lattice lat, const double interval[2], int N
   }
   // moment coefficients over the union for each window: c_k[u][m] = w_j zeta_j^m
   // for the window's points u = u(k, j), zero elsewhere
-  std::vector<std::vector<double2>> coefk(K, std::vector<double2>((size_t)NU * M, make_double2(0.0, 0.0)));
+  std::vector<std::vector<double2>> coefk(K, std::vector<double2>((size_t)NU * MM, make_double2(0.0, 0.0)));
   for (int j = 0; j < N; ++j) {
     const double zr0 = (z[j].x - gamma0) / rho, zi0 = z[j].y / rho;
     double zr = 1.0, zi = 0.0;
-    for (int m = 0; m < M; ++m) {
+    for (int m = 0; m < MM; ++m) {
       const double2 cv = make_double2(w[j].x * zr - w[j].y * zi, w[j].x * zi + w[j].y * zr);
       for (int k = 0; k < K; ++k) {
         const int u = (K == 1) ? j : 2 * (k * step + j / 2) + j % 2;
-        coefk[k][(size_t)u * M + m] = cv;
+        coefk[k][(size_t)u * MM + m] = cv;
       }
       const double nr = zr * zr0 - zi * zi0, ni = zr * zi0 + zi * zr0;
       zr = nr;
@@ -454,21 +544,21 @@ extern "C" int ssqcd_ss_solve(ssqcd_lattice lat, const double interval[2], int N
   res->stats.ms_k_update = cg.ms_k[3];
   res->stats.timed_shift_updates = cg.timed_units;
   if (s1 != SSQCD_OK) return bail(s1);
-  vd.release();
+  if (!hankel) vd.release();
 
   cudaEvent_t e0, e1, e2;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   cudaEventCreate(&e2);
   cudaEventRecord(e0, st);
-  const int m = M * L;
+  const int m = MM * L;
   std::vector<DevBuf> Xk(K);
   std::vector<int> cntk(K, 0);
   float ms_mom = 0.f;
   for (int k = 0; k < K; ++k) {
     // moments of window k (Eq. 2), S = [L][M][n]
     if ((s1 = S.alloc(sizeof(double2) * n * m)) != SSQCD_OK) return bail(s1);
-    if ((s1 = moments_device(yd.as<double2>(), NU, M, L, n, coefk[k].data(), S.as<double2>(), scratch, st)) !=
+    if ((s1 = moments_device(yd.as<double2>(), NU, MM, L, n, coefk[k].data(), S.as<double2>(), scratch, st)) !=
         SSQCD_OK)
       return bail(s1);
     if (k == K - 1) {
@@ -479,6 +569,16 @@ extern "C" int ssqcd_ss_solve(ssqcd_lattice lat, const double interval[2], int N
     const double lo = (K == 1) ? a : a + k * core;
     const double hi = (K == 1) ? b : (k == K - 1 ? b : a + (k + 1) * core);
     int rank = 0;
+    if (hankel) {
+      const size_t before = res->evals.size();
+      if ((s1 = hankel_window(vd.as<double2>(), L, S.as<double2>(), M, n, o.hankel_tol, gamma0 + k * core, rho, lo,
+                              hi, k < K - 1, res->evals, res->residuals, rank, scratch, st)) != SSQCD_OK)
+        return bail(s1);
+      cntk[k] = (int)(res->evals.size() - before);
+      res->stats.rank += rank;
+      res->stats.n_ritz += rank;
+      continue;
+    }
     if ((s1 = rayleigh_ritz_window(lat, S.as<double2>(), m, o.rank_tol, lo, hi, k < K - 1, res->evals,
                                    res->residuals, Xk[k], cntk[k], rank, scratch)) != SSQCD_OK)
       return bail(s1);
@@ -491,7 +591,9 @@ extern "C" int ssqcd_ss_solve(ssqcd_lattice lat, const double interval[2], int N
   int cnt = 0;
   for (int k = 0; k < K; ++k) cnt += cntk[k];
   res->stats.n_accepted = cnt;
-  if (cnt > 0) {
+  if (hankel) {  // eigenvalues only: sort them
+    std::sort(res->evals.begin(), res->evals.end());
+  } else if (cnt > 0) {
     DevBuf all;
     if ((s1 = all.alloc(sizeof(double2) * n * cnt)) != SSQCD_OK) return bail(s1);
     int off = 0;
@@ -541,6 +643,8 @@ extern "C" int ssqcd_ss_eigpairs(ssqcd_result res, int* count, double* evals, do
   if (evals == nullptr) return SSQCD_OK;
   std::memcpy(evals, res->evals.data(), sizeof(double) * cnt);
   if (residuals) std::memcpy(residuals, res->residuals.data(), sizeof(double) * cnt);
+  if (evecs && cnt > 0 && res->evecs.p == nullptr)
+    return fail(SSQCD_ERR_ARG, "no eigenvectors: the solve used the Hankel extraction");
   if (evecs && cnt > 0) {
     DevBuf stage;
     SS_TRY(stage.alloc(sizeof(double2) * res->n * cnt));

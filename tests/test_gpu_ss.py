@@ -58,3 +58,44 @@ def test_config1_against_oracle_and_dense(ss):
         assert abs(np.linalg.norm(r) - rs[k]) <= 1e-12 + 1e-6 * rs[k]
     # iteration counts are not unique in floating point (see the shifted-CG test)
     assert st["iterations"] <= 1.2 * int(ref["iters"].max()) + 2
+
+
+def test_hankel_extraction_config1(ss):
+    # Block Hankel pencil of the GPU moments (2M = 16 <= N): eigenvalues only,
+    # accuracy bounded by the conditioning of the Hankel matrix.  Against the
+    # exact spectrum and against the oracle's own Hankel extraction (SVD
+    # reduction, numpy eig) of the oracle's moments of the same solve.
+    c = CFG1
+    U = synthetic.gauge_field(c["dims"], c["kind"], seed=c["seed"])
+    src = synthetic.gaussian_sources(c["dims"], c["L"], seed=c["src_seed"])
+    lat = ss.create_lattice(c["dims"], c["kappa"], c["bc"])
+    ss.upload_gauge(lat, U)
+    res = ss.ss_solve(lat, c["interval"], c["N"], c["M"], src, beta=c["beta"], nprime=c["nprime"],
+                      extract=ss.EXTRACT_HANKEL)
+    assert res.status == ss.OK, res.error
+    ev, vec, rs, st = ss.ss_eigpairs(res, want_vectors=False)
+    assert np.all(np.isnan(rs)) and st["matvecs_rr"] == 0
+    exact = _reference_spectrum("haar_4x4x4x4_k0.13_s1")
+    exact = np.sort(exact[(exact >= c["interval"][0]) & (exact <= c["interval"][1])])
+    assert len(ev) == len(exact) == 8
+    # the oracle's Hankel extraction of this case reaches 1.5e-5 (its own
+    # moments, shifted CG at tol 1e-12); the bar leaves a factor ~7
+    assert np.max(np.abs(ev - exact) / exact) <= 1e-4
+    # the oracle's Hankel extraction on its own shifted-CG moments
+    from oracle import contour, hankel, moments, shifted_cg, wilson
+    a, b = c["interval"]
+    g, r = contour.window_from_interval(a, b, c["N"], c["nprime"])
+    z = contour.line_nodes(g, r, c["beta"], c["N"])
+    zeta = contour.normalise(z, g, r)
+    w = contour.weights_closed_form(zeta)
+    A = lambda x: wilson.apply_H(U, x, c["kappa"], c["dims"], c["bc"])
+    M2 = 2 * c["M"]
+    ys = [shifted_cg.shifted_cg(A, v, z, tol=1e-12)["y"] for v in src]
+    S = np.stack([np.stack([moments.moments(ys[l], w, zeta, M2)[k].reshape(-1) for l in range(c["L"])], axis=1)
+                  for k in range(M2)])
+    lam_o = g + r * hankel.block_hankel_eigs(src.reshape(c["L"], -1).T, S, rank_tol=1e-12)
+    lam_o = np.sort(lam_o[(np.abs(lam_o.imag) < 1e-6) & (lam_o.real >= a) & (lam_o.real <= b)].real)
+    assert len(lam_o) == 8
+    assert np.max(np.abs(ev - lam_o) / lam_o) <= 1e-4
+    with pytest.raises(Exception):
+        ss.ss_eigpairs(res, want_vectors=True)

@@ -95,3 +95,35 @@ def test_pipeline_4x4_config_against_dense():
     assert len(out["evals"]) == len(exact) == 8
     assert np.max(np.abs(out["evals"] - exact) / exact) < 1e-10
     assert np.max(out["residuals"]) < 1e-8
+
+
+def test_hankel_blocks_hermitian_psd_on_conjugate_symmetric_contours():
+    # With Hermitian A and nodes closed under conjugation (weights conjugate
+    # too, since P has real coefficients), mu_k = V^H s_k is Hermitian and
+    # the block Hankel matrix H = [mu_{i+j}] is positive semidefinite (the
+    # filter P(0)/P(x) is positive on the real axis): the reading the GPU
+    # extraction reduces through two Hermitian eigenproblems.
+    U, Hd = _dense(seed=5)
+    lam = np.linalg.eigvalsh(Hd)
+    pos = np.sort(lam[lam > 0])
+    a, b = pos[0] - 0.005, 0.5 * (pos[2] + pos[3])
+    N, L, M = 16, 2, 4
+    for path in ("lines", "circle"):
+        gamma, rho = contour.window_from_interval(a, b, N, N // 2)
+        if path == "lines":
+            z = contour.line_nodes(gamma, rho, 0.3, N)
+        else:
+            z = contour.circle_nodes(gamma, rho, N)
+        zeta = contour.normalise(z, gamma, rho)
+        w = contour.weights_closed_form(zeta)
+        V = synthetic.gaussian_sources((2, 2, 2, 2), L, seed=8).reshape(L, -1).T
+        n = Hd.shape[0]
+        ys = [np.stack([np.linalg.solve(zj * np.eye(n) - Hd, V[:, l]) for zj in z]) for l in range(L)]
+        s = np.stack([np.stack([moments.moments(ys[l], w, zeta, 2 * M)[k] for l in range(L)], axis=1)
+                      for k in range(2 * M)])
+        mu = np.stack([V.conj().T @ s[k] for k in range(2 * M)])
+        scale = np.max(np.abs(mu))
+        assert np.max(np.abs(mu - mu.conj().transpose(0, 2, 1))) <= 1e-12 * scale
+        H = np.block([[mu[i + j] for j in range(M)] for i in range(M)])
+        h = np.linalg.eigvalsh(0.5 * (H + H.conj().T))
+        assert h.min() >= -1e-12 * h.max()
