@@ -187,7 +187,7 @@ __global__ void init_control_kernel(Control c, const double* __restrict__ vn2, i
 // spin w's three components of site s; returns this thread's share of (p, q).
 struct Stencil64 {
   static constexpr int kThreads = kStencilThreads;
-  static constexpr int kMinBlocks = 1;
+  static constexpr int kMinBlocks = 4;  // <= 128 registers (four 128-thread blocks per SM)
   const double2* __restrict__ u;
   __device__ __forceinline__ double run(const Geometry& g, const double2* __restrict__ p, double2* __restrict__ q,
                                         double sigma, int s, int w, void* shm) const {
@@ -244,7 +244,7 @@ struct Stencil32 {
 // (p, q); one hop per warp, 8 warps per block (wilson_df.cuh)
 struct StencilDF {
   static constexpr int kThreads = kStencilThreadsDF;
-  static constexpr int kMinBlocks = 1;  // a 64-register cap (4 blocks / SM) spilled and measured slower
+  static constexpr int kMinBlocks = 3;  // <= 85 registers; a 64-register cap (4 blocks) spilled and measured slower
   const float4* __restrict__ u;
   __device__ __forceinline__ double run(const Geometry& g, const float4* __restrict__ p, float4* __restrict__ q,
                                         double sigma, int s, int w, void* shm) const {
