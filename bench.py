@@ -67,6 +67,13 @@ UPDATE_BYTES_PER_UNIT = 64
 # + 24 = 888 FP64 instructions; counted as 1368 flop/site/rhs (FMA = 2); bytes:
 # spinor in 192 B + out 192 B + links 576 B (shared by the rhs) per site.
 STENCIL_FLOP_PER_SITE = 1368
+# DRAM traffic of one launch of each update kernel with all 128 (source,
+# shift) pairs live on this workload (ncu dram__bytes_read.sum +
+# dram__bytes_write.sum, one capture per kernel; the algorithmic bytes of such
+# a launch are 64 x 128 x 49152 = 402.7 MB -- part of y / p-hat stays in L2).
+# Null them when the kernel changes.
+UPDATE_FP64_TRAFFIC_ALL_LIVE = (204.556544 + 140.414464) * 1e6
+UPDATE_TMA_TRAFFIC_ALL_LIVE = (204.506880 + 139.959808) * 1e6
 
 
 def _measured_peaks():
@@ -312,7 +319,7 @@ def run_ours(args):
             "roofline": {"kernel": "cg_update_tma_kernel (fused multi-shift update, float-float, bulk-copy fed)",
                          "bound": "hbm",
                          "achieved": gbs_m, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                         "frac": gbs_m / peaks["hbm_gbs"], "traffic": None,
+                         "frac": gbs_m / peaks["hbm_gbs"], "traffic": UPDATE_TMA_TRAFFIC_ALL_LIVE,
                          "avg_launch_us": 1e3 * ms_upd_m / it_m},
         }
         del lat_m
@@ -340,13 +347,19 @@ def run_ours(args):
             "roofline": {
                 "kernel": "shift_update_kernel (fused multi-shift update, FP64)",
                 "bound": "alu", "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved_tf / FP64_PEAK_TFLOPS, "traffic": None,
+                "frac": achieved_tf / FP64_PEAK_TFLOPS, "traffic": UPDATE_FP64_TRAFFIC_ALL_LIVE,
+                "traffic_note": "one launch with all 128 shift vectors live; algorithmic 402.7 MB",
                 "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz",
                 "hbm_achieved_gbs": bytes_upd / (ms_upd / 1e3) / 1e9,
                 "hbm_frac_of_measured": bytes_upd / (ms_upd / 1e3) / 1e9 / peaks["hbm_gbs"],
                 "avg_launch_us": 1e3 * ms_upd / max(1, launches_upd),
                 "fraction_of_cg_iteration": (ms_upd / max(1, it_tot)) /
                                             (stats[-1]["ms_cg"] / max(1, stats[-1]["iterations"])),
+                # the update shares the FP64 pipe with the stencil of the next
+                # iteration (side stream): FP64 flops of both over the CG loop time
+                "loop_fp64_frac": (UPDATE_FLOP_PER_UNIT * n * stats[-1]["shift_updates"]
+                                   + STENCIL_FLOP_PER_SITE * V * w["L"] * stats[-1]["iterations"])
+                                  / (stats[-1]["ms_cg"] / 1e3) / 1e12 / FP64_PEAK_TFLOPS,
             },
             "stencil": {"bound": "alu", "achieved_tflops": sten_flops / (ms_sten / 1e3) / 1e12,
                         "frac_fp64_peak": sten_flops / (ms_sten / 1e3) / 1e12 / FP64_PEAK_TFLOPS,
