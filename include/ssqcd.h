@@ -42,7 +42,8 @@ extern "C" {
 #define SSQCD_ERR_ARG       1  /* invalid argument (sizes, NULL, state)          */
 #define SSQCD_ERR_OOM       2  /* device allocation failed                       */
 #define SSQCD_ERR_BREAKDOWN 3  /* seed CG breakdown: |(p, K p)| < 1e-30 (r, r)   */
-#define SSQCD_ERR_NOCONV    4  /* shifted CG hit max_iter before every shift met tol */
+#define SSQCD_ERR_NOCONV    4  /* shifted CG hit max_iter before every shift met tol,
+                               or a device-side wait hit its time limit (1 s)   */
 #define SSQCD_ERR_CUDA      5  /* a CUDA runtime call failed                     */
 
 /* ---- precision of the solve loop ------------------------------------------ */

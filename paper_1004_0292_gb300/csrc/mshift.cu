@@ -786,14 +786,18 @@ cg_update_df_kernel(Control c, int N, int par, const RT* __restrict__ r, float4*
 // room on every SM for the blocks of the stencil and seed kernels that run
 // beside it, while the stage ring keeps kTmaStages x 16 KB of loads in flight
 // per SM.
-// Every wait is bounded: past kSpinLimit polls the kernel sets c.err = 2,
-// drains its outstanding copies (bounded again) and returns.
+// Every wait is bounded: after 1 s (device global timer; kSpinLimit polls as
+// a backstop) the kernel sets c.err = 2, drains its outstanding copies
+// (bounded again) and returns.  With
+// producer_off set (a test of that path, SSQCD_TEST_UPDATE_STALL=1) the
+// producer issues nothing, so the consumers' first wait runs out.
 constexpr int kTmaConsumerWarps = 8;
 constexpr int kTmaEpt = 2;  // elements per consumer thread and stage
 constexpr int kTmaCh = kTmaConsumerWarps * 32 * kTmaEpt;
 constexpr int kTmaStages = 4;
 constexpr int kTmaThreads = (kTmaConsumerWarps + 1) * 32;
-constexpr long long kSpinLimit = 1LL << 22;
+constexpr long long kSpinLimit = 1LL << 24;        // polls (backstop)
+constexpr unsigned long long kWaitLimitNs = 1000000000ull;  // 1 s of device time
 
 struct __align__(16) TmaStage {
   float4 y[kTmaCh];
@@ -820,10 +824,20 @@ __device__ __forceinline__ bool mbar_test(unsigned long long* bar, unsigned pari
       : "memory");
   return ok != 0;
 }
-// true once the phase of the given parity has completed; false after kSpinLimit polls
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// true once the phase of the given parity has completed; false after
+// kWaitLimitNs (or kSpinLimit polls)
 __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
-  for (long long i = 0; i < kSpinLimit; ++i)
+  if (mbar_test(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  for (long long i = 1; i < kSpinLimit; ++i) {
     if (mbar_test(bar, parity)) return true;
+    if ((i & 255) == 0 && global_ns() - t0 > kWaitLimitNs) return false;
+  }
   return false;
 }
 __device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
@@ -841,7 +855,7 @@ size_t tma_smem_bytes(int NL, int L) {
 template <typename RT>
 __global__ void __launch_bounds__(kTmaThreads, 1)
 cg_update_tma_kernel(Control c, int N, int L, int par, const RT* __restrict__ r, float4* __restrict__ y,
-                     float4* __restrict__ ph, long long n, int nchunks) {
+                     float4* __restrict__ ph, long long n, int nchunks, int producer_off) {
   if (c.rec_ran[par] == 0) return;
   extern __shared__ __align__(128) unsigned char smem[];
   TmaStage* stage = reinterpret_cast<TmaStage*>(smem);
@@ -875,7 +889,7 @@ cg_update_tma_kernel(Control c, int N, int L, int par, const RT* __restrict__ r,
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (warp == kTmaConsumerWarps) {
     // ---- producer (one lane) ----
-    if (lane != 0) return;
+    if (lane != 0 || producer_off) return;
     const unsigned total = (unsigned)L * (unsigned)nchunks;
     long long s = 0;  // stages issued
     bool ok = true;
@@ -1108,6 +1122,16 @@ bool use_tma_update() {
   return v;
 }
 
+// Test of the bounded waits: SSQCD_TEST_UPDATE_STALL=1 keeps the producer of
+// the TMA-fed update idle (the wait-limit error path, without a fault).
+int update_stall_test() {
+  static const int v = [] {
+    const char* e = std::getenv("SSQCD_TEST_UPDATE_STALL");
+    return (e && e[0] == '1') ? 1 : 0;
+  }();
+  return v;
+}
+
 template <typename RT>
 int prepare_update_tma(int NL, int L) {
   const size_t smem = tma_smem_bytes(NL, L);
@@ -1120,7 +1144,7 @@ void launch_update_tma(int nblocks, int L, cudaStream_t st, int prio, const Cont
                        float4* y, float4* ph, long long n) {
   const int nchunks = (int)((n + kTmaCh - 1) / kTmaCh);
   launch_prio_smem(cg_update_tma_kernel<RT>, dim3(nblocks), dim3(kTmaThreads), tma_smem_bytes(N * L, L), st, prio, c,
-                   N, L, par, r, y, ph, n, nchunks);
+                   N, L, par, r, y, ph, n, nchunks, update_stall_test());
 }
 
 int update_blocks(long long n, int L, int ept) {
