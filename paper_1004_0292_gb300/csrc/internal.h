@@ -16,6 +16,8 @@
 #include <cuda_fp16.h>
 #include <cstddef>
 #include <cstdint>
+#include <memory>
+#include <utility>
 #include <string>
 #include <vector>
 
@@ -49,16 +51,41 @@ int cuda_fail(cudaError_t e, const char* what, const char* file, int line);
 void count_launches(long long k);
 
 // ---- device buffers --------------------------------------------------------
+// Allocation is stream-ordered (cudaMallocAsync / cudaFreeAsync) on the
+// stream of the innermost AllocStream scope of the calling thread, else
+// plain cudaMalloc / cudaFree (which synchronise the device on free).  A
+// buffer remembers the stream it was allocated on and frees on it; the code
+// that uses a buffer on other streams joins them into that stream first.
 struct DevBuf {
   void* p = nullptr;
   size_t bytes = 0;
+  cudaStream_t stream = nullptr;
+  bool async = false;
   DevBuf() = default;
   DevBuf(const DevBuf&) = delete;
   DevBuf& operator=(const DevBuf&) = delete;
   ~DevBuf() { release(); }
   int alloc(size_t nbytes);          // no-op when already that large
   void release();
+  void swap(DevBuf& o) {
+    std::swap(p, o.p);
+    std::swap(bytes, o.bytes);
+    std::swap(stream, o.stream);
+    std::swap(async, o.async);
+  }
   template <typename T> T* as() const { return static_cast<T*>(p); }
+};
+
+// RAII: DevBuf allocations of this thread use stream-ordered allocation on s.
+struct AllocStream {
+  explicit AllocStream(cudaStream_t s);
+  ~AllocStream();
+  AllocStream(const AllocStream&) = delete;
+  AllocStream& operator=(const AllocStream&) = delete;
+
+ private:
+  cudaStream_t prev_;
+  bool prev_on_;
 };
 
 // ---- lattice -------------------------------------------------------------------
@@ -160,6 +187,18 @@ inline bool valid_precision(int precision) {
 }
 // Solves for L sources already packed on device (v: [L][12][V]); y out
 // [L][N][12][V] (device, FP64).  iters/xi: host arrays [L*N] (may be null).
+// A resumable shifted-CG run (mshift.cu): see CgRun there.
+class CgRunBase {
+ public:
+  enum { kPollRunning = 0, kPollDone = 1, kPollBusy = 2 };
+  virtual ~CgRunBase() = default;
+  virtual int launch() = 0;                          // enqueue one chunk and its poll read
+  virtual int poll(bool wait, int* state) = 0;       // the oldest enqueued chunk's outcome
+  virtual int in_flight() const = 0;                 // chunks enqueued, not yet polled
+  virtual int finish(DevBuf& y, int* iters_host, double2* xi_host, ShiftedCGOut* out) = 0;
+};
+int make_cg_run(ssqcd_lattice lat, int N, const double2* z_host, int L, const double2* v, double sigma, double tol,
+                int max_iter, int precision, int reliable_every, cudaStream_t st, std::unique_ptr<CgRunBase>* out);
 int shifted_cg_device(ssqcd_lattice lat, int N, const double2* z_host, int L, const double2* v,
                       double sigma, double tol, int max_iter, int precision, int reliable_every,
                       DevBuf& y, int* iters, double2* xi, ShiftedCGOut* out);

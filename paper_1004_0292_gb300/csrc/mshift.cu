@@ -43,6 +43,8 @@
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
+#include <memory>
+#include <new>
 #include <type_traits>
 #include <utility>
 #include <vector>
@@ -1160,411 +1162,510 @@ namespace {
 // The solve loop for one precision: VR is the type of the seed vectors (r, p,
 // q and the stencil), V2 that of the shift vectors (y, p-hat): double2 /
 // double2 (SSQCD_FP64), double2 / float2 (SSQCD_FP64_SHIFT32), double2 /
-// float4 = complex float-float (SSQCD_FP64_DFSHIFT), float2 / float2 (the
-// mixed precisions).  y_out always receives FP64 solutions.
+// float4 = complex float-float (SSQCD_FP64_DFSHIFT), float4 / float4
+// (SSQCD_DF), float2 / float2 (the mixed precisions).  The final solutions
+// are FP64.
+//
+// A run is resumable: init() allocates and initialises on the run's stream
+// and captures the chunk graph; launch() enqueues one chunk of kChunk
+// iterations followed by the read of the live-shift count and error flag
+// into pinned memory (never blocks); poll() looks at the oldest launched
+// chunk (waiting for it or not) and reports whether shifts are still live;
+// finish() hands over the FP64 solutions and the counters.  ss_solve drives
+// one run to the end; the request scheduler interleaves many.
 template <typename VR, typename V2>
-int run_shifted_cg(ssqcd_lattice lat, int N, const double2* z_host, int L, const double2* v, double sigma,
-                   double tol, int max_iter, int precision, int reliable_every, DevBuf& y_out, int* iters_host,
-                   double2* xi_host, ShiftedCGOut* out) {
-  constexpr bool kFP32 = sizeof(VR) == sizeof(float2);      // seed vectors and stencil in FP32
-  constexpr bool kShift32 = sizeof(V2) == sizeof(float2);   // shift vectors in FP32
-  constexpr bool kShiftDF = std::is_same<V2, float4>::value; // shift vectors in float-float
-  constexpr bool kSeedDF = std::is_same<VR, float4>::value;  // seed vectors and stencil in float-float
-  if constexpr (kSeedDF) SS_TRY(ensure_df_links(lat));
-  const bool tma = kShiftDF && use_tma_update();
-  int n_sm = 0;
-  {
-    int dev = 0;
-    SS_CUDA(cudaGetDevice(&dev));
-    SS_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
-  }
-  if constexpr (kShiftDF) {
-    if (tma) SS_TRY(prepare_update_tma<VR>(N * L, L));
-  }
-  cudaStream_t st = lat->stream;
-  const Geometry& g = lat->g;
-  const long long n = 12LL * g.V;
-  const int NL = N * L;
-  const int nbw = wilson_blocks(g);
-  const int nbs = seed_blocks(n, L);
-  const int ept = update_epts(kShift32 || kShiftDF);
-  const int nbu = update_blocks(n, L, ept);
-  // r enters p-hat: with FP32 exponents (FP32 or float-float shift vectors)
-  // ||r|| is kept within 2^-20 of ||v|| (its elements stay far above the
-  // FP32 underflow); FP64 within 2^-200.
-  const double rescale_below = (kShift32 || kShiftDF) ? 0x1p-40 : 0x1p-400;
-  const double rescale_by = (kShift32 || kShiftDF) ? 0x1p+20 : 0x1p+200;
+class CgRun final : public CgRunBase {
+  static constexpr bool kFP32 = sizeof(VR) == sizeof(float2);       // seed vectors and stencil in FP32
+  static constexpr bool kShift32 = sizeof(V2) == sizeof(float2);    // shift vectors in FP32
+  static constexpr bool kShiftDF = std::is_same<V2, float4>::value;  // shift vectors in float-float
+  static constexpr bool kSeedDF = std::is_same<VR, float4>::value;   // seed vectors and stencil in float-float
+  static constexpr int kChunk = 16;  // even: every chunk starts at parity 0
+  static constexpr int kSlots = 8;   // timing events per iteration: A, B, C, P start/stop
+  static constexpr int kTimedEvery = 4;
+  static constexpr int kInFlight = 2;  // chunks enqueued ahead of the poll
 
-  DevBuf r, p, q, ph, y32, x, kx;
-  SS_TRY(r.alloc(2 * sizeof(VR) * n * L));  // r_k and r_{k+1}: parity buffers
-  SS_TRY(p.alloc(sizeof(VR) * n * L));
-  SS_TRY(q.alloc(sizeof(VR) * n * L));
-  SS_TRY(ph.alloc(sizeof(V2) * n * NL));
-  V2* yv = nullptr;
-  if (kShift32) {
-    SS_TRY(y32.alloc(sizeof(V2) * n * NL));
-    yv = y32.as<V2>();
+ public:
+  ~CgRun() override {
+    if (st_ != nullptr) cudaStreamSynchronize(st_);
+    if (gexec_ != nullptr) cudaGraphExecDestroy(gexec_);
+    if (gexec_t_ != nullptr) cudaGraphExecDestroy(gexec_t_);
+    for (auto e : tev_) cudaEventDestroy(e);
+    for (auto e : ev_) cudaEventDestroy(e);
+    for (auto e : ev_poll_) cudaEventDestroy(e);
+    if (e0_) cudaEventDestroy(e0_);
+    if (e1_) cudaEventDestroy(e1_);
+    if (side_) cudaStreamDestroy(side_);
+    if (h_poll_) cudaFreeHost(h_poll_);
+    if (h_iters_) cudaFreeHost(h_iters_);
   }
-  if (kFP32) {
-    if (reliable_every > 0) {
-      SS_TRY(x.alloc(sizeof(double2) * n * L));
-      SS_TRY(kx.alloc(sizeof(double2) * n * L));
-      SS_CUDA(cudaMemsetAsync(x.p, 0, sizeof(double2) * n * L, st));
+
+  int init(ssqcd_lattice lat, int N, const double2* z_host, int L, const double2* v, double sigma, double tol,
+           int max_iter, int reliable_every, cudaStream_t st) {
+    lat_ = lat;
+    N_ = N;
+    L_ = L;
+    v_ = v;
+    sigma_ = sigma;
+    max_iter_ = max_iter;
+    st_ = st;
+    // lattice-owned data first, outside the run's stream-ordered allocations
+    if constexpr (kSeedDF) SS_TRY(ensure_df_links(lat));
+    AllocStream scope(st_);
+    tma_ = kShiftDF && use_tma_update();
+    {
+      int dev = 0;
+      SS_CUDA(cudaGetDevice(&dev));
+      SS_CUDA(cudaDeviceGetAttribute(&n_sm_, cudaDevAttrMultiProcessorCount, dev));
     }
-  }
-  if (!kShift32) {  // FP64 solutions, or float-float ones converted in place at the end
-    static_assert(kShift32 || sizeof(V2) == sizeof(double2), "in-place conversion needs equal element sizes");
-    SS_TRY(y_out.alloc(sizeof(double2) * n * NL));
-    yv = reinterpret_cast<V2*>(y_out.p);
-  }
-  DevBuf ctl;
-  size_t off = 0;
-  auto take = [&](size_t bytes) {
-    const size_t o = off;
-    off += (bytes + 255) / 256 * 256;
-    return o;
-  };
-  const size_t o_seed = take(sizeof(SeedState) * L), o_alpha = take(sizeof(double) * L),
-               o_vn = take(sizeof(double) * L), o_live = take(sizeof(int) * L), o_tot = take(sizeof(int)),
-               o_ran = take(sizeof(int)), o_rran = take(sizeof(int) * 2), o_err = take(sizeof(int)),
-               o_si = take(sizeof(int) * 2),
-               o_done = take(sizeof(unsigned) * 4), o_s = take(sizeof(double2) * NL),
-               o_xc = take(sizeof(double2) * NL), o_xp = take(sizeof(double2) * NL),
-               o_xn = take(sizeof(double2) * NL), o_rt = take(sizeof(double2) * NL), o_act = take(sizeof(int) * NL),
-               o_it = take(sizeof(int) * NL), o_ln = take(sizeof(int) * 2 * L), o_lj = take(sizeof(int) * 2 * NL),
-               o_la = take(sizeof(double2) * 2 * NL), o_lb = take(sizeof(double2) * 2 * NL),
-               o_lsc = take(sizeof(double) * 2 * L),
-               o_part = take(sizeof(double) * (size_t)nbw * L), o_prr = take(sizeof(double) * (size_t)nbs * L),
-               o_vp = take(sizeof(double) * (size_t)nbs * L), o_vn2 = take(sizeof(double) * L);
-  SS_TRY(ctl.alloc(off));
-  char* base = ctl.as<char>();
-  Control c;
-  c.seed = reinterpret_cast<SeedState*>(base + o_seed);
-  c.alpha = reinterpret_cast<double*>(base + o_alpha);
-  c.vnorm2 = reinterpret_cast<double*>(base + o_vn);
-  c.live = reinterpret_cast<int*>(base + o_live);
-  c.live_total = reinterpret_cast<int*>(base + o_tot);
-  c.ran = reinterpret_cast<int*>(base + o_ran);
-  c.rec_ran = reinterpret_cast<int*>(base + o_rran);
-  c.err = reinterpret_cast<int*>(base + o_err);
-  c.seed_iters = reinterpret_cast<int*>(base + o_si);
-  c.done = reinterpret_cast<unsigned*>(base + o_done);
-  c.task_ctr = c.done + 2;
-  c.shift_s = reinterpret_cast<double2*>(base + o_s);
-  c.xi_cur = reinterpret_cast<double2*>(base + o_xc);
-  c.xi_prev = reinterpret_cast<double2*>(base + o_xp);
-  c.xi_next = reinterpret_cast<double2*>(base + o_xn);
-  c.ratio = reinterpret_cast<double2*>(base + o_rt);
-  c.act = reinterpret_cast<int*>(base + o_act);
-  c.iters = reinterpret_cast<int*>(base + o_it);
-  c.list_n = reinterpret_cast<int*>(base + o_ln);
-  c.list_j = reinterpret_cast<int*>(base + o_lj);
-  c.list_a = reinterpret_cast<double2*>(base + o_la);
-  c.list_b = reinterpret_cast<double2*>(base + o_lb);
-  c.list_sc = reinterpret_cast<double*>(base + o_lsc);
-  c.partial = reinterpret_cast<double*>(base + o_part);
-  c.partial_rr = reinterpret_cast<double*>(base + o_prr);
-  c.x = x.p != nullptr ? x.as<double2>() : nullptr;
-  double* vn_part = reinterpret_cast<double*>(base + o_vp);
-  double* vn2 = reinterpret_cast<double*>(base + o_vn2);
-
-  std::vector<double2> sh(NL);
-  for (int l = 0; l < L; ++l)
-    for (int j = 0; j < N; ++j) sh[l * N + j] = make_double2(z_host[j].x - sigma, z_host[j].y);
-  SS_CUDA(cudaMemcpyAsync(c.shift_s, sh.data(), sizeof(double2) * NL, cudaMemcpyHostToDevice, st));
-
-  SS_TRY(norm2_partials(v, L, n, vn_part, nbs, st));
-  SS_TRY(sum_partials(vn_part, L, nbs, vn2, st));
-  init_vectors_kernel<<<dim3(nbu, L), kUpdBlock, 0, st>>>(v, r.as<VR>(), p.as<VR>(), yv, ph.as<V2>(), N, n);
-  SS_CHECK_LAUNCH();
-  init_control_kernel<<<1, 256, 0, st>>>(c, vn2, L, N);
-  SS_CHECK_LAUNCH();
-  count_launches(2);
-
-  cudaEvent_t e0, e1;
-  SS_CUDA(cudaEventCreate(&e0));
-  SS_CUDA(cudaEventCreate(&e1));
-  SS_CUDA(cudaEventRecord(e0, st));
-
-  int* h_poll = nullptr;
-  SS_CUDA(cudaMallocHost(&h_poll, sizeof(int) * 4));
-  const double tol2 = tol * tol;
-  int status = SSQCD_OK;
-  int k = 0;
-  constexpr int kChunk = 16;  // even: every chunk starts at parity 0
-  const bool timing = kernel_timing_enabled();
-  // Two streams: the main chain A -> B -> P runs on the caller's stream at
-  // the greatest priority; C (the shift update of iteration k) runs on a side
-  // stream beside A, B, P of iteration k + 1.  Dependencies: C(k) after B(k)
-  // (coefficients, r_{k+1}) and after C(k-1) (stream order); A(k) after
-  // C(k-2) (A and B of iteration k rewrite the parity-(k % 2) record and r
-  // buffer that C(k-2) read).  Each chunk forks the side stream from the
-  // main one and joins it back at the end.
-  int prio_lo = 0, prio_hi = 0;
-  SS_CUDA(cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi));
-  struct SideRes {
-    cudaStream_t side = nullptr;
-    std::vector<cudaEvent_t> ev;
-    ~SideRes() {
-      for (auto e : ev) cudaEventDestroy(e);
-      if (side) cudaStreamDestroy(side);
-    }
-  } sr;
-  SS_CUDA(cudaStreamCreateWithPriority(&sr.side, cudaStreamNonBlocking, prio_lo));
-  sr.ev.resize(2 * kChunk + 1);
-  for (auto& e : sr.ev) SS_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-  cudaStream_t side = sr.side;
-  cudaEvent_t ev_fork = sr.ev[2 * kChunk];
-  auto ev_b = [&](int it) { return sr.ev[it]; };
-  auto ev_c = [&](int it) { return sr.ev[kChunk + it]; };
-  constexpr int kSlots = 8;  // per iteration: A, B, C, P start/stop
-  std::vector<cudaEvent_t> tev;
-  std::vector<double> t_iter[4];
-  if (timing) {
-    tev.resize(kChunk * kSlots);
-    for (auto& e : tev) SS_CUDA(cudaEventCreate(&e));
-  }
-  bool mark_on = false;  // events recorded in the chunk being built / launched
-  auto mark = [&](int it, int slot, cudaStream_t s_) {
-    // during capture, only the External flag makes a real event-record node
-    if (mark_on) cudaEventRecordWithFlags(tev[it * kSlots + slot], s_, cudaEventRecordExternal);
-  };
-  const dim3 grid_a(nbw, L), grid_b(nbs, L), grid_c(nbu, L);
-  const dim3 grid_p((unsigned)((n + kUpdBlock - 1) / kUpdBlock), L);  // one element per thread
-  VR* const r0 = r.as<VR>();
-  auto iteration = [&](int it) {
-    const int par = it & 1;
-    const VR* r_in = r0 + (size_t)par * n * L;
-    VR* r_out = r0 + (size_t)(par ^ 1) * n * L;
-    if (it >= 2) cudaStreamWaitEvent(st, ev_c(it - 2), 0);
-    mark(it, 0, st);
-    if constexpr (kFP32) {
-      if (lat->precision == SSQCD_MIXED)
-        launch_prio(cg_stencil_kernel<Stencil32<LinksF16>, VR>, grid_a, kStencilThreads, st, prio_hi, c, L, par, g,
-                    Stencil32<LinksF16>{LinksF16{lat->u16.as<uint2>(), g.V}}, sigma, p.as<VR>(), q.as<VR>());
-      else
-        launch_prio(cg_stencil_kernel<Stencil32<LinksF32>, VR>, grid_a, kStencilThreads, st, prio_hi, c, L, par, g,
-                    Stencil32<LinksF32>{LinksF32{lat->u32.as<float4>(), g.V}}, sigma, p.as<VR>(), q.as<VR>());
-    } else if constexpr (kSeedDF) {
-      launch_prio(cg_stencil_kernel<StencilDF, VR>, grid_a, StencilDF::kThreads, st, prio_hi, c, L, par, g,
-                  StencilDF{lat->udf.as<float4>()}, sigma, p.as<VR>(), q.as<VR>());
-    } else {
-      launch_prio(cg_stencil_kernel<Stencil64, VR>, grid_a, kStencilThreads, st, prio_hi, c, L, par, g,
-                  Stencil64{lat->u64.as<double2>()}, sigma, p.as<VR>(), q.as<VR>());
-    }
-    mark(it, 1, st);
-    mark(it, 2, st);
-    launch_prio(cg_seed_kernel<VR>, grid_b, kSeedBlock, st, prio_hi, c, L, N, par, tol2, r_in, r_out, q.as<VR>(),
-                p.as<VR>(), n, rescale_below, rescale_by);
-    mark(it, 3, st);
-    cudaEventRecord(ev_b(it), st);
-    mark(it, 6, st);
-    launch_prio(cg_seed_p_kernel<VR>, grid_p, kUpdBlock, st, prio_hi, c, r_out, p.as<VR>(), n);
-    mark(it, 7, st);
-    cudaStreamWaitEvent(side, ev_b(it), 0);
-    mark(it, 4, side);
     if constexpr (kShiftDF) {
-      if (tma)
-        launch_update_tma<VR>(n_sm, L, side, prio_lo, c, N, par, r_out, yv, ph.as<float4>(), n);
-      else
-        launch_update_df<VR>(ept, L, side, prio_lo, c, N, par, r_out, yv, ph.as<float4>(), n);
+      if (tma_) SS_TRY(prepare_update_tma<VR>(N * L, L));
     }
-    else
-      launch_update<VR, V2>(ept, grid_c, side, prio_lo, c, N, par, r_out, yv, ph.as<V2>(), n);
-    mark(it, 5, side);
-    cudaEventRecord(ev_c(it), side);
-  };
-  auto run_chunk = [&](int count) {
-    cudaEventRecord(ev_fork, st);
-    cudaStreamWaitEvent(side, ev_fork, 0);
-    for (int it = 0; it < count; ++it) iteration(it);
-    cudaStreamWaitEvent(st, ev_c(count - 1), 0);
-  };
-  // A chunk of iterations is captured once as a CUDA graph and replayed (the
-  // kernels read all per-iteration state from device memory, so every replay
-  // is the same graph; node priorities are kept).  With kernel timing on, a
-  // second graph also records an event around every kernel; it replaces the
-  // plain one for one chunk in kTimedEvery (the event nodes cost ~7% of the
-  // loop), and its events are read after that replay.  A stream that cannot
-  // be captured (the legacy default stream) falls back to direct launches.
-  constexpr int kTimedEvery = 4;
-  auto capture = [&](bool with_events) {
-    cudaGraphExec_t ge = nullptr;
-    cudaGraph_t graph = nullptr;
-    mark_on = with_events;
-    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
-      run_chunk(kChunk);
-      if (cudaStreamEndCapture(st, &graph) == cudaSuccess && graph != nullptr) {
-        if (cudaGraphInstantiate(&ge, graph, cudaGraphInstantiateFlagUseNodePriority) != cudaSuccess) ge = nullptr;
-        cudaGraphDestroy(graph);
-      }
+    const Geometry& g = lat->g;
+    n_ = 12LL * g.V;
+    const long long n = n_;
+    const int NL = N * L;
+    nbw_ = wilson_blocks(g);
+    nbs_ = seed_blocks(n, L);
+    ept_ = update_epts(kShift32 || kShiftDF);
+    nbu_ = update_blocks(n, L, ept_);
+    // r enters p-hat: with FP32 exponents (FP32 or float-float shift vectors)
+    // ||r|| is kept within 2^-20 of ||v|| (its elements stay far above the
+    // FP32 underflow); FP64 within 2^-200.
+    rescale_below_ = (kShift32 || kShiftDF) ? 0x1p-40 : 0x1p-400;
+    rescale_by_ = (kShift32 || kShiftDF) ? 0x1p+20 : 0x1p+200;
+    tol2_ = tol * tol;
+
+    SS_TRY(r_.alloc(2 * sizeof(VR) * n * L));  // r_k and r_{k+1}: parity buffers
+    SS_TRY(p_.alloc(sizeof(VR) * n * L));
+    SS_TRY(q_.alloc(sizeof(VR) * n * L));
+    SS_TRY(ph_.alloc(sizeof(V2) * n * NL));
+    if (kShift32) {
+      SS_TRY(y32_.alloc(sizeof(V2) * n * NL));
+      yv_ = y32_.as<V2>();
     }
-    (void)cudaGetLastError();  // a failed capture falls back to direct launches
-    mark_on = false;
-    return ge;
-  };
-  cudaGraphExec_t gexec = capture(false);
-  cudaGraphExec_t gexec_t = (timing && gexec != nullptr) ? capture(true) : nullptr;
-  int* h_iters = nullptr;  // per-shift iteration counts, read after each chunk when timing
-  if (timing) SS_CUDA(cudaMallocHost(&h_iters, sizeof(int) * NL));
-  long long units_prev = 0, timed_units = 0;
-  std::vector<int> t_k;  // global iteration index of each timed iteration
-  const int ru_chunks = reliable_every > 0 ? std::max(1, (reliable_every + kChunk / 2) / kChunk) : 0;
-  int chunks_done = 0;
-  while (true) {
-    const int chunk = std::min(kChunk, max_iter - k);
-    const int k_start = k;
-    const bool tchunk = timing && chunks_done % kTimedEvery == 0 && (gexec == nullptr || gexec_t != nullptr);
-    int launched = 0;
-    if (gexec != nullptr && chunk == kChunk) {
-      cudaError_t ge = cudaGraphLaunch(tchunk ? gexec_t : gexec, st);
-      if (ge != cudaSuccess) { status = cuda_fail(ge, "shifted CG graph launch", __FILE__, __LINE__); break; }
-      k += kChunk;
-      launched = kChunk;
-      count_launches(4LL * kChunk);
-    } else {
-      mark_on = tchunk;
-      run_chunk(chunk);
-      mark_on = false;
-      k += chunk;
-      launched = chunk;
-      count_launches(4LL * chunk);
-      cudaError_t le = cudaGetLastError();
-      if (le != cudaSuccess) { status = cuda_fail(le, "shifted CG launch", __FILE__, __LINE__); break; }
+    if (kFP32 && reliable_every > 0) {
+      SS_TRY(x_.alloc(sizeof(double2) * n * L));
+      SS_TRY(kx_.alloc(sizeof(double2) * n * L));
+      SS_CUDA(cudaMemsetAsync(x_.p, 0, sizeof(double2) * n * L, st_));
     }
-    ++chunks_done;
-    if (kFP32 && c.x != nullptr && ru_chunks > 0 && chunks_done % ru_chunks == 0) {
-      // reliable update: r = S (v - K x) in FP64 with the FP64 links
-      int s1 = wilson64(g, lat->u64.as<double2>(), c.x, kx.as<double2>(), L, sigma, -1.0, nullptr, nullptr, st);
-      if (s1 != SSQCD_OK) { status = s1; break; }
-      const double floor2 = lat->precision == SSQCD_MIXED ? 1e-4 : 1e-10;  // (1e-2 / 1e-5 of ||v||)^2
-      // the next iteration (parity of the launched count) reads this buffer
-      VR* r_next = r0 + (size_t)(launched & 1) * n * L;
-      cg_reliable_kernel<VR><<<grid_b, kSeedBlock, 0, st>>>(c, L, v, kx.as<double2>(), r_next, n, floor2);
-      count_launches(1);
+    if (!kShift32) {  // FP64 solutions, or float-float ones converted in place at the end
+      static_assert(kShift32 || sizeof(V2) == sizeof(double2), "in-place conversion needs equal element sizes");
+      SS_TRY(y_out_.alloc(sizeof(double2) * n * NL));
+      yv_ = reinterpret_cast<V2*>(y_out_.p);
     }
-    // live-shift count after the last iteration, and the error flag
-    cudaError_t ce = cudaMemcpyAsync(h_poll, c.live_total, sizeof(int), cudaMemcpyDeviceToHost, st);
-    if (ce == cudaSuccess) ce = cudaMemcpyAsync(h_poll + 1, c.err, sizeof(int), cudaMemcpyDeviceToHost, st);
-    if (ce == cudaSuccess && timing) ce = cudaMemcpyAsync(h_iters, c.iters, sizeof(int) * NL, cudaMemcpyDeviceToHost, st);
-    if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
-    if (ce != cudaSuccess) { status = cuda_fail(ce, "shifted CG poll", __FILE__, __LINE__); break; }
-    if (timing) {
-      long long units = 0;
-      for (int qi = 0; qi < NL; ++qi) units += h_iters[qi];
-      if (tchunk) {
-        timed_units += units - units_prev;
-        for (int it = 0; it < launched; ++it) {
-          t_k.push_back(k_start + it);
-          for (int cls = 0; cls < 4; ++cls) {
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, tev[it * kSlots + 2 * cls], tev[it * kSlots + 2 * cls + 1]);
-            t_iter[cls].push_back(ms);
-          }
-        }
-      }
-      units_prev = units;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+      const size_t o = off;
+      off += (bytes + 255) / 256 * 256;
+      return o;
+    };
+    const size_t o_seed = take(sizeof(SeedState) * L), o_alpha = take(sizeof(double) * L),
+                 o_vn = take(sizeof(double) * L), o_live = take(sizeof(int) * L), o_tot = take(sizeof(int)),
+                 o_ran = take(sizeof(int)), o_rran = take(sizeof(int) * 2), o_err = take(sizeof(int)),
+                 o_si = take(sizeof(int) * 2), o_done = take(sizeof(unsigned) * 4),
+                 o_s = take(sizeof(double2) * NL), o_xc = take(sizeof(double2) * NL),
+                 o_xp = take(sizeof(double2) * NL), o_xn = take(sizeof(double2) * NL),
+                 o_rt = take(sizeof(double2) * NL), o_act = take(sizeof(int) * NL), o_it = take(sizeof(int) * NL),
+                 o_ln = take(sizeof(int) * 2 * L), o_lj = take(sizeof(int) * 2 * NL),
+                 o_la = take(sizeof(double2) * 2 * NL), o_lb = take(sizeof(double2) * 2 * NL),
+                 o_lsc = take(sizeof(double) * 2 * L), o_part = take(sizeof(double) * (size_t)nbw_ * L),
+                 o_prr = take(sizeof(double) * (size_t)nbs_ * L), o_vp = take(sizeof(double) * (size_t)nbs_ * L),
+                 o_vn2 = take(sizeof(double) * L);
+    SS_TRY(ctl_.alloc(off));
+    char* base = ctl_.as<char>();
+    Control& c = c_;
+    c.seed = reinterpret_cast<SeedState*>(base + o_seed);
+    c.alpha = reinterpret_cast<double*>(base + o_alpha);
+    c.vnorm2 = reinterpret_cast<double*>(base + o_vn);
+    c.live = reinterpret_cast<int*>(base + o_live);
+    c.live_total = reinterpret_cast<int*>(base + o_tot);
+    c.ran = reinterpret_cast<int*>(base + o_ran);
+    c.rec_ran = reinterpret_cast<int*>(base + o_rran);
+    c.err = reinterpret_cast<int*>(base + o_err);
+    c.seed_iters = reinterpret_cast<int*>(base + o_si);
+    c.done = reinterpret_cast<unsigned*>(base + o_done);
+    c.task_ctr = c.done + 2;
+    c.shift_s = reinterpret_cast<double2*>(base + o_s);
+    c.xi_cur = reinterpret_cast<double2*>(base + o_xc);
+    c.xi_prev = reinterpret_cast<double2*>(base + o_xp);
+    c.xi_next = reinterpret_cast<double2*>(base + o_xn);
+    c.ratio = reinterpret_cast<double2*>(base + o_rt);
+    c.act = reinterpret_cast<int*>(base + o_act);
+    c.iters = reinterpret_cast<int*>(base + o_it);
+    c.list_n = reinterpret_cast<int*>(base + o_ln);
+    c.list_j = reinterpret_cast<int*>(base + o_lj);
+    c.list_a = reinterpret_cast<double2*>(base + o_la);
+    c.list_b = reinterpret_cast<double2*>(base + o_lb);
+    c.list_sc = reinterpret_cast<double*>(base + o_lsc);
+    c.partial = reinterpret_cast<double*>(base + o_part);
+    c.partial_rr = reinterpret_cast<double*>(base + o_prr);
+    c.x = x_.p != nullptr ? x_.as<double2>() : nullptr;
+    double* vn_part = reinterpret_cast<double*>(base + o_vp);
+    double* vn2 = reinterpret_cast<double*>(base + o_vn2);
+
+    shift_host_.resize(NL);
+    for (int l = 0; l < L; ++l)
+      for (int j = 0; j < N; ++j) shift_host_[l * N + j] = make_double2(z_host[j].x - sigma, z_host[j].y);
+    SS_CUDA(cudaMemcpyAsync(c.shift_s, shift_host_.data(), sizeof(double2) * NL, cudaMemcpyHostToDevice, st_));
+
+    SS_TRY(norm2_partials(v, L, n, vn_part, nbs_, st_));
+    SS_TRY(sum_partials(vn_part, L, nbs_, vn2, st_));
+    init_vectors_kernel<<<dim3(nbu_, L), kUpdBlock, 0, st_>>>(v, r_.as<VR>(), p_.as<VR>(), yv_, ph_.as<V2>(), N, n);
+    SS_CHECK_LAUNCH();
+    init_control_kernel<<<1, 256, 0, st_>>>(c, vn2, L, N);
+    SS_CHECK_LAUNCH();
+    count_launches(2);
+
+    SS_CUDA(cudaEventCreate(&e0_));
+    SS_CUDA(cudaEventCreate(&e1_));
+    SS_CUDA(cudaEventRecord(e0_, st_));
+    SS_CUDA(cudaMallocHost(&h_poll_, sizeof(int) * 2 * kInFlight));
+    ev_poll_.resize(kInFlight);
+    for (auto& e : ev_poll_) SS_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    timing_ = kernel_timing_enabled();
+    ru_chunks_ = (kFP32 && reliable_every > 0) ? std::max(1, (reliable_every + kChunk / 2) / kChunk) : 0;
+    // Two streams: the main chain A -> B -> P runs on the run's stream at
+    // the greatest priority; C (the shift update of iteration k) runs on a
+    // side stream beside A, B, P of iteration k + 1.  Dependencies: C(k)
+    // after B(k) (coefficients, r_{k+1}) and after C(k-1) (stream order);
+    // A(k) after C(k-2) (A and B of iteration k rewrite the parity-(k % 2)
+    // record and r buffer that C(k-2) read).  Each chunk forks the side
+    // stream from the main one and joins it back at the end.
+    SS_CUDA(cudaDeviceGetStreamPriorityRange(&prio_lo_, &prio_hi_));
+    SS_CUDA(cudaStreamCreateWithPriority(&side_, cudaStreamNonBlocking, prio_lo_));
+    ev_.resize(2 * kChunk + 1);
+    for (auto& e : ev_) SS_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    if (timing_) {
+      tev_.resize(kChunk * kSlots);
+      for (auto& e : tev_) SS_CUDA(cudaEventCreate(&e));
+      SS_CUDA(cudaMallocHost(&h_iters_, sizeof(int) * NL));
     }
-    if (h_poll[1] == 2) { status = fail(SSQCD_ERR_NOCONV, "shift update: a device-side wait hit its limit"); break; }
-    if (h_poll[1] != 0) { status = fail(SSQCD_ERR_BREAKDOWN, "seed CG breakdown: |(p, K p)| < 1e-30 (r, r)"); break; }
-    if (h_poll[0] == 0) break;
-    if (k >= max_iter) {
-      char buf[128];
-      std::snprintf(buf, sizeof(buf), "shifted CG: %d shifts still above tol after %d iterations", h_poll[0], k);
-      status = fail(SSQCD_ERR_NOCONV, buf);
-      break;
-    }
+    // A chunk of iterations is captured once as a CUDA graph and replayed
+    // (the kernels read all per-iteration state from device memory, so every
+    // replay is the same graph; node priorities are kept).  With kernel
+    // timing on, a second graph also records an event around every kernel;
+    // it replaces the plain one for one chunk in kTimedEvery (the event nodes
+    // cost ~7% of the loop), and its events are read after that replay.  A
+    // stream that cannot be captured (the legacy default stream) falls back
+    // to direct launches.
+    gexec_ = capture(false);
+    gexec_t_ = (timing_ && gexec_ != nullptr) ? capture(true) : nullptr;
+    return SSQCD_OK;
   }
-  if (gexec != nullptr) cudaGraphExecDestroy(gexec);
-  if (gexec_t != nullptr) cudaGraphExecDestroy(gexec_t);
-  if (h_iters != nullptr) cudaFreeHost(h_iters);
-  if (status == SSQCD_OK || status == SSQCD_ERR_BREAKDOWN || status == SSQCD_ERR_NOCONV) {
-    if (kShift32) {  // hand FP64 solutions to the FP64 moments and Rayleigh-Ritz
-      SS_TRY(y_out.alloc(sizeof(double2) * n * NL));
-      SS_TRY(convert_f32_to_f64(reinterpret_cast<const float2*>(yv), y_out.as<double2>(), n * NL, st));
-    } else if (kShiftDF) {
-      const long long cnt = n * NL;
-      const int nb = (int)std::max(1LL, std::min((cnt + 255) / 256, 152LL * 16));
-      df_to_f64_kernel<<<nb, 256, 0, st>>>(reinterpret_cast<float4*>(yv), cnt);
+
+  int launch() override {
+    AllocStream scope(st_);
+    const int chunk = std::min(kChunk, max_iter_ - k_);
+    if (chunk <= 0) return SSQCD_OK;
+    const int slot = (int)(launched_chunks_ % kInFlight);
+    ChunkInfo info;
+    info.k_start = k_;
+    info.timed = timing_ && launched_chunks_ % kTimedEvery == 0 && (gexec_ == nullptr || gexec_t_ != nullptr);
+    if (gexec_ != nullptr && chunk == kChunk) {
+      cudaError_t ge = cudaGraphLaunch(info.timed ? gexec_t_ : gexec_, st_);
+      if (ge != cudaSuccess) return cuda_fail(ge, "shifted CG graph launch", __FILE__, __LINE__);
+    } else {
+      mark_on_ = info.timed;
+      run_chunk(chunk);
+      mark_on_ = false;
+      cudaError_t le = cudaGetLastError();
+      if (le != cudaSuccess) return cuda_fail(le, "shifted CG launch", __FILE__, __LINE__);
+    }
+    count_launches(4LL * chunk);
+    k_ += chunk;
+    info.count = chunk;
+    ++launched_chunks_;
+    if (kFP32 && c_.x != nullptr && ru_chunks_ > 0 && launched_chunks_ % ru_chunks_ == 0) {
+      // reliable update: r = S (v - K x) in FP64 with the FP64 links
+      SS_TRY(wilson64(lat_->g, lat_->u64.as<double2>(), c_.x, kx_.as<double2>(), L_, sigma_, -1.0, nullptr, nullptr,
+                      st_));
+      const double floor2 = lat_->precision == SSQCD_MIXED ? 1e-4 : 1e-10;  // (1e-2 / 1e-5 of ||v||)^2
+      // the next iteration (parity of the chunk length) reads this buffer
+      VR* r_next = r_.as<VR>() + (size_t)(chunk & 1) * n_ * L_;
+      cg_reliable_kernel<VR><<<dim3(nbs_, L_), kSeedBlock, 0, st_>>>(c_, L_, v_, kx_.as<double2>(), r_next, n_,
+                                                                     floor2);
       SS_CHECK_LAUNCH();
       count_launches(1);
     }
-    SS_CUDA(cudaEventRecord(e1, st));
+    // live-shift count after the last iteration and the error flag
+    SS_CUDA(cudaMemcpyAsync(h_poll_ + 2 * slot, c_.live_total, sizeof(int), cudaMemcpyDeviceToHost, st_));
+    SS_CUDA(cudaMemcpyAsync(h_poll_ + 2 * slot + 1, c_.err, sizeof(int), cudaMemcpyDeviceToHost, st_));
+    if (timing_) SS_CUDA(cudaMemcpyAsync(h_iters_, c_.iters, sizeof(int) * N_ * L_, cudaMemcpyDeviceToHost, st_));
+    SS_CUDA(cudaEventRecord(ev_poll_[slot], st_));
+    pending_.push_back(info);
+    return SSQCD_OK;
+  }
+
+  int in_flight() const override { return (int)pending_.size(); }
+
+  int poll(bool wait, int* state) override {
+    *state = kPollRunning;
+    if (pending_.empty()) {
+      if (k_ >= max_iter_) return fail(SSQCD_ERR_NOCONV, "shifted CG: max_iter reached");
+      return SSQCD_OK;
+    }
+    const int slot = (int)(polled_chunks_ % kInFlight);
+    if (wait) {
+      SS_CUDA(cudaEventSynchronize(ev_poll_[slot]));
+    } else {
+      const cudaError_t q = cudaEventQuery(ev_poll_[slot]);
+      if (q == cudaErrorNotReady) {
+        *state = kPollBusy;
+        return SSQCD_OK;
+      }
+      if (q != cudaSuccess) return cuda_fail(q, "shifted CG poll", __FILE__, __LINE__);
+    }
+    const ChunkInfo info = pending_.front();
+    pending_.erase(pending_.begin());
+    ++polled_chunks_;
+    if (timing_ && pending_.empty()) {
+      // h_iters holds the counts after the last launched chunk: read only
+      // when no later chunk is in flight (the timed chunk is then the last)
+      long long units = 0;
+      for (int qi = 0; qi < N_ * L_; ++qi) units += h_iters_[qi];
+      if (info.timed) {
+        timed_units_ += units - units_prev_;
+        for (int it = 0; it < info.count; ++it) {
+          t_k_.push_back(info.k_start + it);
+          for (int cls = 0; cls < 4; ++cls) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, tev_[it * kSlots + 2 * cls], tev_[it * kSlots + 2 * cls + 1]);
+            t_iter_[cls].push_back(ms);
+          }
+        }
+      }
+      units_prev_ = units;
+    }
+    const int live = h_poll_[2 * slot], err = h_poll_[2 * slot + 1];
+    if (err == 2) return fail(SSQCD_ERR_NOCONV, "shift update: a device-side wait hit its limit");
+    if (err != 0) return fail(SSQCD_ERR_BREAKDOWN, "seed CG breakdown: |(p, K p)| < 1e-30 (r, r)");
+    if (live == 0) {
+      *state = kPollDone;
+      return SSQCD_OK;
+    }
+    if (info.k_start + info.count >= max_iter_) {
+      char buf[128];
+      std::snprintf(buf, sizeof(buf), "shifted CG: %d shifts still above tol after %d iterations", live, max_iter_);
+      return fail(SSQCD_ERR_NOCONV, buf);
+    }
+    return SSQCD_OK;
+  }
+
+  int finish(DevBuf& y_out, int* iters_host, double2* xi_host, ShiftedCGOut* out) override {
+    AllocStream scope(st_);
+    const long long n = n_;
+    const int NL = N_ * L_;
+    // chunks enqueued past convergence do no work; wait for them
+    SS_CUDA(cudaStreamSynchronize(st_));
+    pending_.clear();
+    if (kShift32) {  // hand FP64 solutions to the FP64 moments and Rayleigh-Ritz
+      SS_TRY(y_out_.alloc(sizeof(double2) * n * NL));
+      SS_TRY(convert_f32_to_f64(reinterpret_cast<const float2*>(yv_), y_out_.as<double2>(), n * NL, st_));
+    } else if (kShiftDF) {
+      const long long cnt = n * NL;
+      const int nb = (int)std::max(1LL, std::min((cnt + 255) / 256, 152LL * 16));
+      df_to_f64_kernel<<<nb, 256, 0, st_>>>(reinterpret_cast<float4*>(yv_), cnt);
+      SS_CHECK_LAUNCH();
+      count_launches(1);
+    }
+    SS_CUDA(cudaEventRecord(e1_, st_));
     int counters[2] = {0, 0};
     std::vector<int> it_all(NL);
-    SS_CUDA(cudaMemcpyAsync(counters, c.seed_iters, sizeof(int) * 2, cudaMemcpyDeviceToHost, st));
-    SS_CUDA(cudaMemcpyAsync(it_all.data(), c.iters, sizeof(int) * NL, cudaMemcpyDeviceToHost, st));
+    SS_CUDA(cudaMemcpyAsync(counters, c_.seed_iters, sizeof(int) * 2, cudaMemcpyDeviceToHost, st_));
+    SS_CUDA(cudaMemcpyAsync(it_all.data(), c_.iters, sizeof(int) * NL, cudaMemcpyDeviceToHost, st_));
     std::vector<int> act_all(xi_host ? NL : 0);
-    std::vector<SeedState> seed_all(xi_host ? L : 0);
+    std::vector<SeedState> seed_all(xi_host ? L_ : 0);
     if (xi_host) {
-      SS_CUDA(cudaMemcpyAsync(xi_host, c.xi_cur, sizeof(double2) * NL, cudaMemcpyDeviceToHost, st));
-      SS_CUDA(cudaMemcpyAsync(act_all.data(), c.act, sizeof(int) * NL, cudaMemcpyDeviceToHost, st));
-      SS_CUDA(cudaMemcpyAsync(seed_all.data(), c.seed, sizeof(SeedState) * L, cudaMemcpyDeviceToHost, st));
+      SS_CUDA(cudaMemcpyAsync(xi_host, c_.xi_cur, sizeof(double2) * NL, cudaMemcpyDeviceToHost, st_));
+      SS_CUDA(cudaMemcpyAsync(act_all.data(), c_.act, sizeof(int) * NL, cudaMemcpyDeviceToHost, st_));
+      SS_CUDA(cudaMemcpyAsync(seed_all.data(), c_.seed, sizeof(SeedState) * L_, cudaMemcpyDeviceToHost, st_));
     }
-    SS_CUDA(cudaStreamSynchronize(st));
+    SS_CUDA(cudaStreamSynchronize(st_));
     if (xi_host)  // shifts still live at the end hold xi / S
       for (int qi = 0; qi < NL; ++qi)
         if (act_all[qi]) {
-          const double S = seed_all[qi / N].pad[1];
+          const double S = seed_all[qi / N_].pad[1];
           xi_host[qi] = make_double2(xi_host[qi].x * S, xi_host[qi].y * S);
         }
     if (iters_host) std::copy(it_all.begin(), it_all.end(), iters_host);
     float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventElapsedTime(&ms, e0_, e1_);
     if (out) {
       out->seed_iters = counters[0];
       out->reliable_updates = counters[1];
       out->ms = ms;
       out->shift_updates = 0;
       for (int v2 : it_all) out->shift_updates += v2;
-      out->timed = timing;
-      out->timed_units = timed_units;
+      out->timed = timing_;
+      out->timed_units = timed_units_;
       int n_timed = 0;
-      for (int kk : t_k) n_timed += kk < counters[0] ? 1 : 0;
+      for (int kk : t_k_) n_timed += kk < counters[0] ? 1 : 0;
       out->launches_update = n_timed;
       for (int cls = 0; cls < 4; ++cls) out->ms_k[cls] = 0.0;
       const int slot_of[4] = {0, 1, 3, 2};  // stencil, seed update + scalars, shift update, seed p
       for (int cls = 0; cls < 4; ++cls) {
         double acc = 0.0;
         // iterations after the last live one skip their work: not counted
-        for (size_t i = 0; i < t_iter[cls].size(); ++i)
-          if (t_k[i] < counters[0]) acc += t_iter[cls][i];
+        for (size_t i = 0; i < t_iter_[cls].size(); ++i)
+          if (t_k_[i] < counters[0]) acc += t_iter_[cls][i];
         out->ms_k[slot_of[cls]] = acc;
       }
     }
+    y_out.swap(y_out_);
+    return SSQCD_OK;
   }
-  for (auto& e : tev) cudaEventDestroy(e);
-  cudaFreeHost(h_poll);
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  return status;
-}
+
+ private:
+  struct ChunkInfo {
+    int k_start = 0, count = 0;
+    bool timed = false;
+  };
+
+  void mark(int it, int slot, cudaStream_t s) {
+    // during capture, only the External flag makes a real event-record node
+    if (mark_on_) cudaEventRecordWithFlags(tev_[it * kSlots + slot], s, cudaEventRecordExternal);
+  }
+
+  void iteration(int it) {
+    const Geometry& g = lat_->g;
+    const long long n = n_;
+    const int L = L_, N = N_;
+    Control& c = c_;
+    const dim3 grid_a(nbw_, L), grid_b(nbs_, L), grid_c(nbu_, L);
+    const dim3 grid_p((unsigned)((n + kUpdBlock - 1) / kUpdBlock), L);  // one element per thread
+    VR* const r0 = r_.as<VR>();
+    const int par = it & 1;
+    const VR* r_in = r0 + (size_t)par * n * L;
+    VR* r_out = r0 + (size_t)(par ^ 1) * n * L;
+    cudaStream_t st = st_;
+    if (it >= 2) cudaStreamWaitEvent(st, ev_[kChunk + it - 2], 0);
+    mark(it, 0, st);
+    if constexpr (kFP32) {
+      if (lat_->precision == SSQCD_MIXED)
+        launch_prio(cg_stencil_kernel<Stencil32<LinksF16>, VR>, grid_a, kStencilThreads, st, prio_hi_, c, L, par, g,
+                    Stencil32<LinksF16>{LinksF16{lat_->u16.as<uint2>(), g.V}}, sigma_, p_.as<VR>(), q_.as<VR>());
+      else
+        launch_prio(cg_stencil_kernel<Stencil32<LinksF32>, VR>, grid_a, kStencilThreads, st, prio_hi_, c, L, par, g,
+                    Stencil32<LinksF32>{LinksF32{lat_->u32.as<float4>(), g.V}}, sigma_, p_.as<VR>(), q_.as<VR>());
+    } else if constexpr (kSeedDF) {
+      launch_prio(cg_stencil_kernel<StencilDF, VR>, grid_a, StencilDF::kThreads, st, prio_hi_, c, L, par, g,
+                  StencilDF{lat_->udf.as<float4>()}, sigma_, p_.as<VR>(), q_.as<VR>());
+    } else {
+      launch_prio(cg_stencil_kernel<Stencil64, VR>, grid_a, kStencilThreads, st, prio_hi_, c, L, par, g,
+                  Stencil64{lat_->u64.as<double2>()}, sigma_, p_.as<VR>(), q_.as<VR>());
+    }
+    mark(it, 1, st);
+    mark(it, 2, st);
+    launch_prio(cg_seed_kernel<VR>, grid_b, kSeedBlock, st, prio_hi_, c, L, N, par, tol2_, r_in, r_out, q_.as<VR>(),
+                p_.as<VR>(), n, rescale_below_, rescale_by_);
+    mark(it, 3, st);
+    cudaEventRecord(ev_[it], st);
+    mark(it, 6, st);
+    launch_prio(cg_seed_p_kernel<VR>, grid_p, kUpdBlock, st, prio_hi_, c, r_out, p_.as<VR>(), n);
+    mark(it, 7, st);
+    cudaStreamWaitEvent(side_, ev_[it], 0);
+    mark(it, 4, side_);
+    if constexpr (kShiftDF) {
+      if (tma_)
+        launch_update_tma<VR>(n_sm_, L, side_, prio_lo_, c, N, par, r_out, yv_, ph_.as<float4>(), n);
+      else
+        launch_update_df<VR>(ept_, L, side_, prio_lo_, c, N, par, r_out, yv_, ph_.as<float4>(), n);
+    } else {
+      launch_update<VR, V2>(ept_, grid_c, side_, prio_lo_, c, N, par, r_out, yv_, ph_.as<V2>(), n);
+    }
+    mark(it, 5, side_);
+    cudaEventRecord(ev_[kChunk + it], side_);
+  }
+
+  void run_chunk(int count) {
+    cudaEvent_t ev_fork = ev_[2 * kChunk];
+    cudaEventRecord(ev_fork, st_);
+    cudaStreamWaitEvent(side_, ev_fork, 0);
+    for (int it = 0; it < count; ++it) iteration(it);
+    cudaStreamWaitEvent(st_, ev_[kChunk + count - 1], 0);
+  }
+
+  cudaGraphExec_t capture(bool with_events) {
+    cudaGraphExec_t ge = nullptr;
+    cudaGraph_t graph = nullptr;
+    mark_on_ = with_events;
+    if (cudaStreamBeginCapture(st_, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+      run_chunk(kChunk);
+      if (cudaStreamEndCapture(st_, &graph) == cudaSuccess && graph != nullptr) {
+        if (cudaGraphInstantiate(&ge, graph, cudaGraphInstantiateFlagUseNodePriority) != cudaSuccess) ge = nullptr;
+        cudaGraphDestroy(graph);
+      }
+    }
+    (void)cudaGetLastError();  // a failed capture falls back to direct launches
+    mark_on_ = false;
+    return ge;
+  }
+
+  ssqcd_lattice lat_ = nullptr;
+  int N_ = 0, L_ = 0, max_iter_ = 0;
+  const double2* v_ = nullptr;
+  double sigma_ = 0.0, tol2_ = 0.0, rescale_below_ = 0.0, rescale_by_ = 0.0;
+  cudaStream_t st_ = nullptr, side_ = nullptr;
+  long long n_ = 0;
+  int nbw_ = 0, nbs_ = 0, nbu_ = 0, ept_ = 1, n_sm_ = 0, prio_lo_ = 0, prio_hi_ = 0, ru_chunks_ = 0;
+  bool tma_ = false, timing_ = false, mark_on_ = false;
+  DevBuf r_, p_, q_, ph_, y32_, x_, kx_, y_out_, ctl_;
+  V2* yv_ = nullptr;
+  Control c_{};
+  std::vector<double2> shift_host_;
+  std::vector<cudaEvent_t> ev_, tev_, ev_poll_;
+  cudaEvent_t e0_ = nullptr, e1_ = nullptr;
+  cudaGraphExec_t gexec_ = nullptr, gexec_t_ = nullptr;
+  int* h_poll_ = nullptr;
+  int* h_iters_ = nullptr;
+  int k_ = 0;
+  long long launched_chunks_ = 0, polled_chunks_ = 0;
+  std::vector<ChunkInfo> pending_;
+  long long units_prev_ = 0, timed_units_ = 0;
+  std::vector<int> t_k_;
+  std::vector<double> t_iter_[4];
+};
 
 }  // namespace
 
-int shifted_cg_device(ssqcd_lattice lat, int N, const double2* z_host, int L, const double2* v, double sigma,
-                      double tol, int max_iter, int precision, int reliable_every, DevBuf& y, int* iters_host,
-                      double2* xi_host, ShiftedCGOut* out) {
+int make_cg_run(ssqcd_lattice lat, int N, const double2* z_host, int L, const double2* v, double sigma, double tol,
+                int max_iter, int precision, int reliable_every, cudaStream_t st, std::unique_ptr<CgRunBase>* out) {
   if (!valid_precision(precision)) return fail(SSQCD_ERR_ARG, "unknown precision");
   if (is_mixed(precision) && precision != lat->precision)
     return fail(SSQCD_ERR_ARG, "a mixed-precision solve needs a lattice created with that precision");
   if (N < 1 || N > kMaxShifts) return fail(SSQCD_ERR_ARG, "N must be in [1, 512]");
   if (L < 1 || L > kMaxSources || N * L > kMaxTotal)
     return fail(SSQCD_ERR_ARG, "L must be in [1, 64] and N * L <= 1024");
-  if (precision == SSQCD_FP64)
-    return run_shifted_cg<double2, double2>(lat, N, z_host, L, v, sigma, tol, max_iter, precision, 0, y, iters_host,
-                                            xi_host, out);
-  if (precision == SSQCD_DF)
-    return run_shifted_cg<float4, float4>(lat, N, z_host, L, v, sigma, tol, max_iter, precision, 0, y, iters_host,
-                                          xi_host, out);
-  if (precision == SSQCD_FP64_DFSHIFT)
-    return run_shifted_cg<double2, float4>(lat, N, z_host, L, v, sigma, tol, max_iter, precision, 0, y, iters_host,
-                                           xi_host, out);
-  if (precision == SSQCD_FP64_SHIFT32)
-    return run_shifted_cg<double2, float2>(lat, N, z_host, L, v, sigma, tol, max_iter, precision, 0, y, iters_host,
-                                           xi_host, out);
-  return run_shifted_cg<float2, float2>(lat, N, z_host, L, v, sigma, tol, max_iter, precision, reliable_every, y,
-                                        iters_host, xi_host, out);
+  auto make = [&](auto* run) -> int {
+    std::unique_ptr<CgRunBase> holder(run);
+    if (!run) return fail(SSQCD_ERR_OOM, "host allocation failed");
+    SS_TRY(run->init(lat, N, z_host, L, v, sigma, tol, max_iter, reliable_every, st));
+    *out = std::move(holder);
+    return SSQCD_OK;
+  };
+  if (precision == SSQCD_FP64) return make(new (std::nothrow) CgRun<double2, double2>());
+  if (precision == SSQCD_DF) return make(new (std::nothrow) CgRun<float4, float4>());
+  if (precision == SSQCD_FP64_DFSHIFT) return make(new (std::nothrow) CgRun<double2, float4>());
+  if (precision == SSQCD_FP64_SHIFT32) return make(new (std::nothrow) CgRun<double2, float2>());
+  return make(new (std::nothrow) CgRun<float2, float2>());
+}
+
+int shifted_cg_device(ssqcd_lattice lat, int N, const double2* z_host, int L, const double2* v, double sigma,
+                      double tol, int max_iter, int precision, int reliable_every, DevBuf& y, int* iters_host,
+                      double2* xi_host, ShiftedCGOut* out) {
+  std::unique_ptr<CgRunBase> run;
+  SS_TRY(make_cg_run(lat, N, z_host, L, v, sigma, tol, max_iter, precision, reliable_every, lat->stream, &run));
+  // one chunk in flight: launch, wait for its poll, repeat
+  int status = SSQCD_OK;
+  for (;;) {
+    if ((status = run->launch()) != SSQCD_OK) break;
+    int state = 0;
+    if ((status = run->poll(true, &state)) != SSQCD_OK) break;
+    if (state == CgRunBase::kPollDone) break;
+  }
+  if (status != SSQCD_OK && status != SSQCD_ERR_BREAKDOWN && status != SSQCD_ERR_NOCONV) return status;
+  const int s2 = run->finish(y, iters_host, xi_host, out);
+  return s2 != SSQCD_OK ? s2 : status;
 }
 
 }  // namespace ssqcd

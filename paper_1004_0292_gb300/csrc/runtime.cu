@@ -31,11 +31,27 @@ void count_launches(long long k) { g_launches.fetch_add(k, std::memory_order_rel
 
 bool kernel_timing_enabled() { return g_timing.load() != 0; }
 
+namespace {
+thread_local cudaStream_t t_alloc_stream = nullptr;
+thread_local bool t_alloc_on = false;
+}  // namespace
+
+AllocStream::AllocStream(cudaStream_t s) : prev_(t_alloc_stream), prev_on_(t_alloc_on) {
+  t_alloc_stream = s;
+  t_alloc_on = true;
+}
+AllocStream::~AllocStream() {
+  t_alloc_stream = prev_;
+  t_alloc_on = prev_on_;
+}
+
 int DevBuf::alloc(size_t nbytes) {
   if (p && bytes >= nbytes) return SSQCD_OK;
   release();
   if (nbytes == 0) return SSQCD_OK;
-  cudaError_t e = cudaMalloc(&p, nbytes);
+  async = t_alloc_on;
+  stream = t_alloc_stream;
+  cudaError_t e = async ? cudaMallocAsync(&p, nbytes, stream) : cudaMalloc(&p, nbytes);
   if (e != cudaSuccess) {
     p = nullptr;
     bytes = 0;
@@ -50,9 +66,16 @@ int DevBuf::alloc(size_t nbytes) {
 }
 
 void DevBuf::release() {
-  if (p) cudaFree(p);
+  if (p) {
+    if (async)
+      cudaFreeAsync(p, stream);
+    else
+      cudaFree(p);
+  }
   p = nullptr;
   bytes = 0;
+  async = false;
+  stream = nullptr;
 }
 
 int grid_for(long long work, int threads) {
