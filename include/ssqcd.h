@@ -33,6 +33,8 @@
 #ifndef SSQCD_H
 #define SSQCD_H
 
+#include <stddef.h>
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -262,6 +264,63 @@ int ssqcd_ss_eigpairs(ssqcd_result res, int* count, double* evals, double* evecs
                       double* residuals, ssqcd_stats* stats);
 
 void ssqcd_result_destroy(ssqcd_result res);
+
+/* ---- request scheduler: many solves in flight on one GPU --------------------------- */
+
+/* Continuous batching of independent eigen-window requests (each one
+ * ssqcd_ss_solve, on any lattice), driven by one host thread.  A submitted
+ * request waits in a FIFO; ssqcd_server_progress admits requests from its
+ * head while the estimated device memory of the running ones (dominated by
+ * the N x L shift vectors) stays within the budget, runs every admitted
+ * request on its own stream with its shifted-CG chunks enqueued ahead, so
+ * the kernels of all running requests interleave on the device, and
+ * finishes each request whose shifts have all frozen (moments, extraction,
+ * memory freed).  A request's arithmetic does not depend on the others:
+ * its result is the same alone and in the mix.  Not a part of the paper. */
+typedef struct ssqcd_server_s* ssqcd_server;
+
+#define SSQCD_REQ_QUEUED  0
+#define SSQCD_REQ_RUNNING 1
+#define SSQCD_REQ_DONE    2
+#define SSQCD_REQ_FAILED  3
+
+/* memory_budget: device bytes the running requests may hold (0: 80% of the
+ * currently free memory). */
+int ssqcd_server_create(size_t memory_budget, ssqcd_server* out);
+
+/* Queue a request; arguments as ssqcd_ss_solve (the sources are copied now,
+ * host or device).  *id receives its handle.  SSQCD_ERR_OOM if the request
+ * alone needs more than the budget; SSQCD_ERR_ARG as ssqcd_ss_solve.  The
+ * lattice must outlive the request. */
+int ssqcd_server_submit(ssqcd_server srv, ssqcd_lattice lat, const double interval[2], int N, int M,
+                        int L, const ssqcd_opts* opts, long long* id);
+
+/* Admit, advance and finish requests.  wait = 0 never blocks on the device
+ * (returns at once when all running work is still in flight); wait = 1
+ * blocks until at least one running request could move.  *completed (may be
+ * NULL) receives the number of requests finished (done or failed) by this
+ * call. */
+int ssqcd_server_progress(ssqcd_server srv, int wait, int* completed);
+
+/* State (SSQCD_REQ_*) of a request and its latency so far or at completion
+ * (ms from submission; may be NULL). */
+int ssqcd_server_status(ssqcd_server srv, long long id, int* state, double* latency_ms);
+
+/* Hand over a finished request's result (destroy it with
+ * ssqcd_result_destroy) and forget the request; returns the request's own
+ * status (its result handle, if any, is still handed over).  SSQCD_ERR_ARG
+ * if the request is unknown or not finished. */
+int ssqcd_server_take(ssqcd_server srv, long long id, ssqcd_result* out);
+
+/* Device bytes the scheduler reserves for a request while it runs (its
+ * admission estimate). */
+int ssqcd_server_request_bytes(ssqcd_server srv, long long id, size_t* bytes);
+
+/* Number of requests queued, running and finished (not yet taken). */
+int ssqcd_server_counts(ssqcd_server srv, int* queued, int* running, int* finished);
+
+/* Waits for the running requests' device work and frees everything. */
+void ssqcd_server_destroy(ssqcd_server srv);
 
 /* ---- small dense helper (host) ----------------------------------------------------- */
 

@@ -23,7 +23,7 @@ import numpy as np
 __all__ = [
     "OK", "ERR_ARG", "ERR_OOM", "ERR_BREAKDOWN", "ERR_NOCONV", "ERR_CUDA",
     "FP64", "MIXED", "MIXED_F32LINKS", "FP64_SHIFT32", "FP64_DFSHIFT", "DF", "EXTRACT_RR", "EXTRACT_HANKEL", "PATH_LINES", "PATH_CIRCLE", "SsqcdError",
-    "library_path", "lib", "create_lattice", "upload_gauge", "apply_H", "apply_H_mixed",
+    "library_path", "lib", "Server", "create_lattice", "upload_gauge", "apply_H", "apply_H_mixed",
     "contour", "shifted_cg", "moments", "moments_noalloc", "ss_solve", "ss_eigpairs", "small_eigh",
     "kernel_launches", "set_kernel_timing", "Lattice", "Result", "Opts", "Stats",
 ]
@@ -89,6 +89,14 @@ def lib():
         "ssqcd_upload_gauge": (i, [vp, vp, i]),
         "ssqcd_apply_H": (i, [vp, vp, vp, i, i]),
         "ssqcd_apply_H_mixed": (i, [vp, vp, vp, i, i]),
+        "ssqcd_server_create": (i, [C.c_size_t, vp]),
+        "ssqcd_server_submit": (i, [vp, vp, vp, i, i, i, vp, vp]),
+        "ssqcd_server_progress": (i, [vp, i, vp]),
+        "ssqcd_server_status": (i, [vp, C.c_longlong, vp, vp]),
+        "ssqcd_server_take": (i, [vp, C.c_longlong, vp]),
+        "ssqcd_server_counts": (i, [vp, vp, vp, vp]),
+        "ssqcd_server_request_bytes": (i, [vp, C.c_longlong, vp]),
+        "ssqcd_server_destroy": (None, [vp]),
         "ssqcd_lattice_destroy": (None, [vp]),
         "ssqcd_contour": (i, [i, d, d, d, i, vp, vp]),
         "ssqcd_shifted_cg": (i, [vp, i, vp, i, vp, i, d, d, i, i, i, vp, vp, vp, vp]),
@@ -320,6 +328,74 @@ def ss_eigpairs(res: Result, want_vectors=True):
         # still fill stats
         pass
     return ev, vec, rs, st.as_dict()
+
+
+class Server:
+    """Request scheduler (ssqcd_server_*): continuous batching of solves."""
+
+    QUEUED, RUNNING, DONE, FAILED = 0, 1, 2, 3
+
+    def __init__(self, memory_budget=0):
+        h = C.c_void_p()
+        _check(lib().ssqcd_server_create(C.c_size_t(int(memory_budget)), C.byref(h)))
+        self.handle = h
+        self._lats = {}
+
+    def submit(self, lat: Lattice, interval, N, M, sources, beta=0.3, nprime=0, tol=1e-12, sigma=0.0,
+               max_iter=100000, rank_tol=1e-14, path=PATH_LINES, windows=1, extract=0, hankel_tol=1e-12):
+        L = int(np.prod(sources.shape)) // lat.n
+        o = Opts()
+        lib().ssqcd_default_opts(C.byref(o))
+        ps, dev, keep = _ptr(sources)
+        o.path, o.beta, o.nprime, o.tol, o.sigma = int(path), float(beta), int(nprime), float(tol), float(sigma)
+        o.max_iter, o.rank_tol, o.sources, o.sources_on_device = int(max_iter), float(rank_tol), ps, dev
+        o.windows, o.extract, o.hankel_tol = int(windows), int(extract), float(hankel_tol)
+        iv = (C.c_double * 2)(float(interval[0]), float(interval[1]))
+        rid = C.c_longlong(0)
+        _check(lib().ssqcd_server_submit(self.handle, lat.handle, iv, int(N), int(M), L, C.byref(o), C.byref(rid)))
+        self._lats[rid.value] = lat
+        return rid.value
+
+    def progress(self, wait=False) -> int:
+        n = C.c_int(0)
+        _check(lib().ssqcd_server_progress(self.handle, 1 if wait else 0, C.byref(n)))
+        return n.value
+
+    def status(self, rid):
+        st = C.c_int(0)
+        ms = C.c_double(0.0)
+        _check(lib().ssqcd_server_status(self.handle, C.c_longlong(rid), C.byref(st), C.byref(ms)))
+        return st.value, ms.value
+
+    def request_bytes(self, rid) -> int:
+        b = C.c_size_t(0)
+        _check(lib().ssqcd_server_request_bytes(self.handle, C.c_longlong(rid), C.byref(b)))
+        return b.value
+
+    def counts(self):
+        q, r, f = C.c_int(0), C.c_int(0), C.c_int(0)
+        _check(lib().ssqcd_server_counts(self.handle, C.byref(q), C.byref(r), C.byref(f)))
+        return q.value, r.value, f.value
+
+    def take(self, rid) -> "Result":
+        h = C.c_void_p()
+        code = lib().ssqcd_server_take(self.handle, C.c_longlong(rid), C.byref(h))
+        lat = self._lats.pop(rid, None)
+        err = lib().ssqcd_last_error().decode() if code != OK else ""
+        if not h.value:
+            _check(code)
+        return Result(h, code, lat, err)
+
+    def close(self):
+        if self.handle is not None and self.handle.value:
+            lib().ssqcd_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def small_eigh(a):

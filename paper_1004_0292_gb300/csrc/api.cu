@@ -1,9 +1,13 @@
 // C-ABI entry points: lattice handles, gauge upload, operator application,
 // shifted CG, moments and the Sakurai-Sugiura / Rayleigh-Ritz solve.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
 #include <new>
 #include <vector>
 
@@ -20,6 +24,20 @@ struct ssqcd_result_s {
   DevBuf evecs;  // [count][12][V] device layout
   ssqcd_stats stats{};
 };
+
+namespace {
+
+// A solve with its host-side setup done (plan_solve).
+struct SolvePlan {
+  ssqcd_opts o{};
+  int N = 0, M = 0, L = 0, K = 1, MM = 0, NU = 0;
+  bool hankel = false;
+  double a = 0.0, b = 0.0, core = 0.0, gamma0 = 0.0, rho = 0.0;
+  std::vector<double2> zu;                   // union of the windows' points
+  std::vector<std::vector<double2>> coefk;   // per window: [NU][MM] moment coefficients
+};
+
+}  // namespace
 
 namespace {
 
@@ -120,6 +138,8 @@ int ssqcd::ensure_df_links(ssqcd_lattice lat) {
   if (lat->udf.p != nullptr && lat->udf_version == lat->gauge_version) return SSQCD_OK;
   SS_TRY(lat->udf.alloc(sizeof(float4) * 36 * (size_t)lat->g.V));
   SS_TRY(pack_gauge_df(lat->u64.as<double2>(), lat->udf.as<float4>(), lat->g.V, lat->stream));
+  // ready for work on any stream (the request scheduler uses its own)
+  SS_CUDA(cudaStreamSynchronize(lat->stream));
   lat->udf_version = lat->gauge_version;
   return SSQCD_OK;
 }
@@ -304,8 +324,7 @@ namespace {
 // residuals.  Appends to evals / resid and returns X in `X`.
 int rayleigh_ritz_window(ssqcd_lattice lat, const double2* S, int m, double rank_tol, double lo, double hi,
                          bool hi_open, std::vector<double>& evals, std::vector<double>& resid, DevBuf& X, int& cnt,
-                         int& rank, DevBuf& scratch) {
-  cudaStream_t st = lat->stream;
+                         int& rank, DevBuf& scratch, cudaStream_t st) {
   const long long n = 12LL * lat->g.V;
   DevBuf Q, tmp, AQ, Gd;
   int r = 0;
@@ -441,11 +460,11 @@ int hankel_window(const double2* V, int L, const double2* S, int M, long long n,
 
 }  // namespace
 
-extern "C" int ssqcd_ss_solve(ssqcd_lattice lat, const double interval[2], int N, int M, int L,
-                              const ssqcd_opts* opts_in, ssqcd_result* out) {
-  if (out == nullptr) return fail(SSQCD_ERR_ARG, "NULL result pointer");
-  *out = nullptr;
-  SS_TRY(check_lattice(lat, true));
+namespace {
+
+// Everything of a solve that does not touch the device: windows, nodes,
+// the union of the windows' points and the moment coefficients.
+int plan_solve(const double interval[2], int N, int M, int L, const ssqcd_opts* opts_in, SolvePlan* P) {
   if (interval == nullptr || !(interval[1] > interval[0])) return fail(SSQCD_ERR_ARG, "interval must have b > a");
   if (N < 1 || M < 1 || L < 1) return fail(SSQCD_ERR_ARG, "N, M, L must be >= 1");
   ssqcd_opts o;
@@ -507,107 +526,117 @@ extern "C" int ssqcd_ss_solve(ssqcd_lattice lat, const double interval[2], int N
       zi = ni;
     }
   }
-  auto* res = new (std::nothrow) ssqcd_result_s();
-  if (!res) return fail(SSQCD_ERR_OOM, "host allocation failed");
-  res->stream = lat->stream;
-  res->V = lat->g.V;
-  res->n = 12LL * lat->g.V;
-  res->stats.gamma = gamma0;
-  res->stats.rho = rho;
+  P->o = o;
+  P->N = N;
+  P->M = M;
+  P->L = L;
+  P->K = K;
+  P->MM = MM;
+  P->NU = NU;
+  P->hankel = hankel;
+  P->a = a;
+  P->b = b;
+  P->core = core;
+  P->gamma0 = gamma0;
+  P->rho = rho;
+  P->zu.swap(zu);
+  P->coefk.swap(coefk);
+  return SSQCD_OK;
+}
+
+void fill_cg_stats(const ShiftedCGOut& cg, const std::vector<int>& iters, ssqcd_stats* st) {
+  st->iterations = cg.seed_iters;
+  st->reliable_updates = cg.reliable_updates;
+  st->ms_cg = cg.ms;
+  st->max_shift_iters = iters.empty() ? 0 : *std::max_element(iters.begin(), iters.end());
+  st->shift_updates = cg.shift_updates;
+  st->timed = cg.timed ? 1 : 0;
+  st->launches_update = cg.launches_update;
+  st->ms_k_stencil = cg.ms_k[0];
+  st->ms_k_seed = cg.ms_k[1];
+  st->ms_k_scalars = cg.ms_k[2];
+  st->ms_k_update = cg.ms_k[3];
+  st->timed_shift_updates = cg.timed_units;
+}
+
+// After the shifted CG: per window the moments (Eq. 2) and Rayleigh-Ritz (or
+// the Hankel pencil) with acceptance in the window's core; then the
+// eigenpairs of all windows sorted by eigenvalue.  yd: [L][NU][n] FP64
+// solutions (released once the last window's moments exist); vd: the
+// sources [L][n].  All device work on st.
+int extract_eigenpairs(ssqcd_lattice lat, const SolvePlan& P, DevBuf& yd, DevBuf& vd, ssqcd_result_s* res,
+                       cudaStream_t st) {
+  const long long n = 12LL * lat->g.V;
+  const int K = P.K, L = P.L, MM = P.MM, M = P.M, NU = P.NU;
+  const double a = P.a, b = P.b, core = P.core, rho = P.rho;
+  res->stats.gamma = P.gamma0;
+  res->stats.rho = P.rho;
   res->stats.points = NU;
-  const long long n = res->n;
-  cudaStream_t st = lat->stream;
-  auto bail = [&](int code) {
-    *out = res;
-    return code;
-  };
-
-  // sources -> device layout
-  DevBuf vd, yd, S, scratch;
-  int s1 = to_device_layout(lat, o.sources, L, o.sources_on_device, vd);
-  if (s1 != SSQCD_OK) { delete res; return s1; }
-  // shifted CG over the union of the quadrature points (one seed recurrence)
-  ShiftedCGOut cg;
-  std::vector<int> iters((size_t)NU * L);
-  s1 = shifted_cg_device(lat, NU, zu.data(), L, vd.as<double2>(), o.sigma, o.tol, o.max_iter, lat->precision,
-                         o.reliable_every, yd, iters.data(), nullptr, &cg);
-  res->stats.iterations = cg.seed_iters;
-  res->stats.reliable_updates = cg.reliable_updates;
-  res->stats.ms_cg = cg.ms;
-  res->stats.max_shift_iters = iters.empty() ? 0 : *std::max_element(iters.begin(), iters.end());
-  res->stats.shift_updates = cg.shift_updates;
-  res->stats.timed = cg.timed ? 1 : 0;
-  res->stats.launches_update = cg.launches_update;
-  res->stats.ms_k_stencil = cg.ms_k[0];
-  res->stats.ms_k_seed = cg.ms_k[1];
-  res->stats.ms_k_scalars = cg.ms_k[2];
-  res->stats.ms_k_update = cg.ms_k[3];
-  res->stats.timed_shift_updates = cg.timed_units;
-  if (s1 != SSQCD_OK) return bail(s1);
-  if (!hankel) vd.release();
-
+  DevBuf S, scratch;
   cudaEvent_t e0, e1, e2;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   cudaEventCreate(&e2);
+  struct Ev {
+    cudaEvent_t* e[3];
+    ~Ev() {
+      for (auto x : e) cudaEventDestroy(*x);
+    }
+  } evs{{&e0, &e1, &e2}};
   cudaEventRecord(e0, st);
   const int m = MM * L;
   std::vector<DevBuf> Xk(K);
   std::vector<int> cntk(K, 0);
-  float ms_mom = 0.f;
   for (int k = 0; k < K; ++k) {
-    // moments of window k (Eq. 2), S = [L][M][n]
-    if ((s1 = S.alloc(sizeof(double2) * n * m)) != SSQCD_OK) return bail(s1);
-    if ((s1 = moments_device(yd.as<double2>(), NU, MM, L, n, coefk[k].data(), S.as<double2>(), scratch, st)) !=
-        SSQCD_OK)
-      return bail(s1);
+    // moments of window k (Eq. 2), S = [L][MM][n]
+    SS_TRY(S.alloc(sizeof(double2) * n * m));
+    SS_TRY(moments_device(yd.as<double2>(), NU, MM, L, n, P.coefk[k].data(), S.as<double2>(), scratch, st));
     if (k == K - 1) {
       cudaEventRecord(e1, st);
       yd.release();
     }
-    // Rayleigh-Ritz and acceptance in the window's core
+    // Rayleigh-Ritz (or the Hankel pencil) and acceptance in the window's core
     const double lo = (K == 1) ? a : a + k * core;
     const double hi = (K == 1) ? b : (k == K - 1 ? b : a + (k + 1) * core);
     int rank = 0;
-    if (hankel) {
+    if (P.hankel) {
       const size_t before = res->evals.size();
-      if ((s1 = hankel_window(vd.as<double2>(), L, S.as<double2>(), M, n, o.hankel_tol, gamma0 + k * core, rho, lo,
-                              hi, k < K - 1, res->evals, res->residuals, rank, scratch, st)) != SSQCD_OK)
-        return bail(s1);
+      SS_TRY(hankel_window(vd.as<double2>(), L, S.as<double2>(), M, n, P.o.hankel_tol, P.gamma0 + k * core, rho, lo,
+                           hi, k < K - 1, res->evals, res->residuals, rank, scratch, st));
       cntk[k] = (int)(res->evals.size() - before);
       res->stats.rank += rank;
       res->stats.n_ritz += rank;
       continue;
     }
-    if ((s1 = rayleigh_ritz_window(lat, S.as<double2>(), m, o.rank_tol, lo, hi, k < K - 1, res->evals,
-                                   res->residuals, Xk[k], cntk[k], rank, scratch)) != SSQCD_OK)
-      return bail(s1);
+    SS_TRY(rayleigh_ritz_window(lat, S.as<double2>(), m, P.o.rank_tol, lo, hi, k < K - 1, res->evals,
+                                res->residuals, Xk[k], cntk[k], rank, scratch, st));
     res->stats.rank += rank;
     res->stats.n_ritz += rank;
     res->stats.matvecs_rr += rank + cntk[k];
   }
-  (void)ms_mom;
   // gather the windows' eigenvectors, then sort everything by eigenvalue
   int cnt = 0;
   for (int k = 0; k < K; ++k) cnt += cntk[k];
   res->stats.n_accepted = cnt;
-  if (hankel) {  // eigenvalues only: sort them
+  if (P.hankel) {  // eigenvalues only: sort them
     std::sort(res->evals.begin(), res->evals.end());
   } else if (cnt > 0) {
     DevBuf all;
-    if ((s1 = all.alloc(sizeof(double2) * n * cnt)) != SSQCD_OK) return bail(s1);
+    SS_TRY(all.alloc(sizeof(double2) * n * cnt));
     int off = 0;
     for (int k = 0; k < K; ++k) {
       if (cntk[k] == 0) continue;
       cudaMemcpyAsync(all.as<double2>() + (size_t)off * n, Xk[k].p, sizeof(double2) * n * cntk[k],
                       cudaMemcpyDeviceToDevice, st);
       off += cntk[k];
-      Xk[k].release();
     }
     std::vector<int> order(cnt);
     for (int i = 0; i < cnt; ++i) order[i] = i;
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return res->evals[x] < res->evals[y]; });
-    if ((s1 = res->evecs.alloc(sizeof(double2) * n * cnt)) != SSQCD_OK) return bail(s1);
+    {
+      AllocStream plain(nullptr, false);  // the result outlives the caller's streams
+      SS_TRY(res->evecs.alloc(sizeof(double2) * n * cnt));
+    }
     std::vector<double> ev(cnt), rs(cnt);
     for (int i = 0; i < cnt; ++i) {
       ev[i] = res->evals[order[i]];
@@ -618,7 +647,7 @@ extern "C" int ssqcd_ss_solve(ssqcd_lattice lat, const double interval[2], int N
     res->evals = ev;
     res->residuals = rs;
     if (cudaStreamSynchronize(st) != cudaSuccess)
-      return bail(cuda_fail(cudaGetLastError(), "gathering eigenvectors", __FILE__, __LINE__));
+      return cuda_fail(cudaGetLastError(), "gathering eigenvectors", __FILE__, __LINE__);
   }
   cudaEventRecord(e2, st);
   cudaEventSynchronize(e2);
@@ -627,11 +656,360 @@ extern "C" int ssqcd_ss_solve(ssqcd_lattice lat, const double interval[2], int N
   cudaEventElapsedTime(&ms2, e1, e2);
   res->stats.ms_moments = ms1;
   res->stats.ms_rr = ms2;
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  cudaEventDestroy(e2);
-  *out = res;
   return SSQCD_OK;
+}
+
+}  // namespace
+
+extern "C" int ssqcd_ss_solve(ssqcd_lattice lat, const double interval[2], int N, int M, int L,
+                              const ssqcd_opts* opts_in, ssqcd_result* out) {
+  if (out == nullptr) return fail(SSQCD_ERR_ARG, "NULL result pointer");
+  *out = nullptr;
+  SS_TRY(check_lattice(lat, true));
+  SolvePlan P;
+  SS_TRY(plan_solve(interval, N, M, L, opts_in, &P));
+  auto* res = new (std::nothrow) ssqcd_result_s();
+  if (!res) return fail(SSQCD_ERR_OOM, "host allocation failed");
+  res->stream = lat->stream;
+  res->V = lat->g.V;
+  res->n = 12LL * lat->g.V;
+  res->stats.gamma = P.gamma0;
+  res->stats.rho = P.rho;
+  res->stats.points = P.NU;
+  cudaStream_t st = lat->stream;
+  // sources -> device layout
+  DevBuf vd, yd;
+  int s1 = to_device_layout(lat, P.o.sources, L, P.o.sources_on_device, vd);
+  if (s1 != SSQCD_OK) {
+    delete res;
+    return s1;
+  }
+  // shifted CG over the union of the quadrature points (one seed recurrence)
+  ShiftedCGOut cg;
+  std::vector<int> iters((size_t)P.NU * L);
+  s1 = shifted_cg_device(lat, P.NU, P.zu.data(), L, vd.as<double2>(), P.o.sigma, P.o.tol, P.o.max_iter,
+                         lat->precision, P.o.reliable_every, yd, iters.data(), nullptr, &cg);
+  fill_cg_stats(cg, iters, &res->stats);
+  *out = res;  // a result handle even on failure, so its stats can be read
+  if (s1 != SSQCD_OK) return s1;
+  if (!P.hankel) vd.release();
+  return extract_eigenpairs(lat, P, yd, vd, res, st);
+}
+
+// --------------------------------------------------------------------------------------------
+// Request scheduler: continuous batching of independent solves on one GPU.
+//
+// A request is one ss_solve.  Submitted requests wait in a FIFO; each call
+// of ssqcd_server_progress admits from its head while the estimated device
+// memory of the running requests (shift vectors y and p-hat of every
+// quadrature point and source dominate) stays within the budget, gives every
+// admitted request its own stream, and keeps up to two 16-iteration chunks of
+// its shifted CG enqueued there, so the kernels of all running requests
+// interleave on the device.  A request whose shifts have all frozen gets its
+// moments and Rayleigh-Ritz on its stream and frees its memory; its latency
+// runs from submission to that point.  Arithmetic and reduction order of a
+// request do not depend on the others: results are the same alone and in
+// the mix.  One host thread drives a server.
+
+struct ServerRequest {
+  long long id = 0;
+  ssqcd_lattice lat = nullptr;
+  SolvePlan P;
+  std::vector<double> src;  // user layout, copied at submission
+  size_t est_bytes = 0;
+  int state = SSQCD_REQ_QUEUED;
+  int status = SSQCD_OK;
+  std::string error;
+  std::chrono::steady_clock::time_point t_submit, t_done;
+  cudaStream_t stream = nullptr;
+  DevBuf vd;
+  std::unique_ptr<CgRunBase> run;
+  ssqcd_result_s* res = nullptr;
+
+  ~ServerRequest() {
+    run.reset();
+    vd.release();
+    if (stream) {
+      cudaStreamSynchronize(stream);
+      cudaStreamDestroy(stream);
+    }
+    delete res;
+  }
+};
+
+struct ssqcd_server_s {
+  size_t budget = 0;
+  size_t running_bytes = 0;
+  int running = 0;
+  long long next_id = 1;
+  std::deque<long long> queue;
+  std::map<long long, std::unique_ptr<ServerRequest>> reqs;
+};
+
+namespace {
+
+constexpr int kServerChunksAhead = 2;
+
+// Device memory of one request at its peak: shift vectors, seed vectors and
+// sources during the CG; moments and the Rayleigh-Ritz basis afterwards.
+size_t estimate_request_bytes(ssqcd_lattice lat, const SolvePlan& P) {
+  const size_t n = 12ull * lat->g.V;
+  const int prec = lat->precision;
+  const size_t sh = (prec == SSQCD_FP64_SHIFT32 || is_mixed(prec)) ? 8 : 16;
+  const size_t sd = is_mixed(prec) ? 8 : 16;
+  const size_t NL = (size_t)P.NU * P.L;
+  size_t cg = 2 * sh * n * NL + 4 * sd * n * P.L + 16 * n * P.L;
+  if (sh == 8) cg += 16 * n * NL;  // FP64 copy of the solutions at the end
+  const size_t ex = 16 * n * NL + 4 * 16 * n * (size_t)P.MM * P.L;
+  return std::max(cg, ex) + (64u << 20);
+}
+
+void request_fail(ssqcd_server_s* srv, ServerRequest& r, int status) {
+  r.status = status;
+  r.error = ssqcd_last_error();
+  r.state = SSQCD_REQ_FAILED;
+  r.t_done = std::chrono::steady_clock::now();
+  if (r.run) {
+    r.run.reset();
+    srv->running_bytes -= r.est_bytes;
+    srv->running -= 1;
+  }
+  r.vd.release();
+}
+
+int request_start(ssqcd_server_s* srv, ServerRequest& r) {
+  ssqcd_lattice lat = r.lat;
+  SS_CUDA(cudaStreamCreateWithFlags(&r.stream, cudaStreamNonBlocking));
+  {
+    AllocStream scope(r.stream);
+    const int V = lat->g.V, L = r.P.L;
+    const size_t bytes = sizeof(double2) * 12 * (size_t)V * L;
+    DevBuf stage;
+    SS_TRY(stage.alloc(bytes));
+    SS_TRY(r.vd.alloc(bytes));
+    SS_CUDA(cudaMemcpyAsync(stage.p, r.src.data(), bytes, cudaMemcpyHostToDevice, r.stream));
+    SS_TRY(pack_spinors(stage.as<double2>(), r.vd.as<double2>(), L, V, r.stream));
+  }
+  std::unique_ptr<CgRunBase> run;
+  SS_TRY(make_cg_run(lat, r.P.NU, r.P.zu.data(), r.P.L, r.vd.as<double2>(), r.P.o.sigma, r.P.o.tol, r.P.o.max_iter,
+                     lat->precision, r.P.o.reliable_every, r.stream, &run));
+  r.run = std::move(run);
+  srv->running_bytes += r.est_bytes;
+  srv->running += 1;
+  r.state = SSQCD_REQ_RUNNING;
+  for (int i = 0; i < kServerChunksAhead; ++i) SS_TRY(r.run->launch());
+  return SSQCD_OK;
+}
+
+int request_complete(ssqcd_server_s* srv, ServerRequest& r) {
+  ssqcd_lattice lat = r.lat;
+  auto* res = new (std::nothrow) ssqcd_result_s();
+  if (!res) return fail(SSQCD_ERR_OOM, "host allocation failed");
+  r.res = res;
+  res->V = lat->g.V;
+  res->n = 12LL * lat->g.V;
+  DevBuf yd;
+  ShiftedCGOut cg;
+  std::vector<int> iters((size_t)r.P.NU * r.P.L);
+  SS_TRY(r.run->finish(yd, iters.data(), nullptr, &cg));
+  fill_cg_stats(cg, iters, &res->stats);
+  r.run.reset();
+  if (!r.P.hankel) r.vd.release();
+  {
+    AllocStream scope(r.stream);  // no device-wide synchronisation on frees
+    SS_TRY(extract_eigenpairs(lat, r.P, yd, r.vd, res, r.stream));
+  }
+  yd.release();
+  r.vd.release();
+  SS_CUDA(cudaStreamSynchronize(r.stream));
+  res->stream = lat->stream;  // later reads of the result run on the lattice stream
+  srv->running_bytes -= r.est_bytes;
+  srv->running -= 1;
+  r.state = SSQCD_REQ_DONE;
+  r.t_done = std::chrono::steady_clock::now();
+  return SSQCD_OK;
+}
+
+}  // namespace
+
+extern "C" int ssqcd_server_create(size_t memory_budget, ssqcd_server* out) {
+  if (out == nullptr) return fail(SSQCD_ERR_ARG, "NULL server pointer");
+  *out = nullptr;
+  if (memory_budget == 0) {
+    size_t fr = 0, tot = 0;
+    SS_CUDA(cudaMemGetInfo(&fr, &tot));
+    memory_budget = fr / 10 * 8;  // 80% of the free device memory
+  }
+  auto* srv = new (std::nothrow) ssqcd_server_s();
+  if (!srv) return fail(SSQCD_ERR_OOM, "host allocation failed");
+  srv->budget = memory_budget;
+  *out = srv;
+  return SSQCD_OK;
+}
+
+extern "C" int ssqcd_server_submit(ssqcd_server srv, ssqcd_lattice lat, const double interval[2], int N, int M,
+                                   int L, const ssqcd_opts* opts, long long* id) {
+  if (srv == nullptr || id == nullptr) return fail(SSQCD_ERR_ARG, "NULL server or id");
+  SS_TRY(check_lattice(lat, true));
+  auto r = std::make_unique<ServerRequest>();
+  SS_TRY(plan_solve(interval, N, M, L, opts, &r->P));
+  r->lat = lat;
+  r->est_bytes = estimate_request_bytes(lat, r->P);
+  if (r->est_bytes > srv->budget)
+    return fail(SSQCD_ERR_OOM, "request needs more device memory than the server budget");
+  const size_t nd = 2ull * 12 * lat->g.V * L;  // doubles
+  r->src.resize(nd);
+  if (r->P.o.sources_on_device)
+    SS_CUDA(cudaMemcpy(r->src.data(), r->P.o.sources, sizeof(double) * nd, cudaMemcpyDeviceToHost));
+  else
+    std::memcpy(r->src.data(), r->P.o.sources, sizeof(double) * nd);
+  r->P.o.sources = nullptr;
+  r->id = srv->next_id++;
+  r->t_submit = std::chrono::steady_clock::now();
+  *id = r->id;
+  srv->queue.push_back(r->id);
+  srv->reqs[r->id] = std::move(r);
+  return SSQCD_OK;
+}
+
+extern "C" int ssqcd_server_progress(ssqcd_server srv, int wait, int* completed) {
+  if (srv == nullptr) return fail(SSQCD_ERR_ARG, "NULL server");
+  int done = 0;
+  // admission from the head of the queue
+  while (!srv->queue.empty()) {
+    auto it = srv->reqs.find(srv->queue.front());
+    if (it == srv->reqs.end()) {
+      srv->queue.pop_front();
+      continue;
+    }
+    ServerRequest& r = *it->second;
+    if (srv->running > 0 && srv->running_bytes + r.est_bytes > srv->budget) break;
+    srv->queue.pop_front();
+    const int s1 = request_start(srv, r);
+    if (s1 != SSQCD_OK) {
+      request_fail(srv, r, s1);
+      ++done;
+    }
+  }
+  // advance every running request; with wait, block on the first one whose
+  // oldest chunk is still on the device if no request moved
+  bool moved = false;
+  ServerRequest* first_busy = nullptr;
+  for (auto& kv : srv->reqs) {
+    ServerRequest& r = *kv.second;
+    if (r.state != SSQCD_REQ_RUNNING) continue;
+    for (;;) {
+      int state = 0;
+      int s1 = r.run->poll(false, &state);
+      if (s1 != SSQCD_OK) {
+        request_fail(srv, r, s1);
+        ++done;
+        moved = true;
+        break;
+      }
+      if (state == CgRunBase::kPollBusy) {
+        if (!first_busy) first_busy = &r;
+        break;
+      }
+      moved = true;
+      if (state == CgRunBase::kPollDone) {
+        s1 = request_complete(srv, r);
+        if (s1 != SSQCD_OK) request_fail(srv, r, s1);
+        ++done;
+        break;
+      }
+      while (r.run->in_flight() < kServerChunksAhead) {
+        s1 = r.run->launch();
+        if (s1 != SSQCD_OK) break;
+      }
+      if (s1 != SSQCD_OK) {
+        request_fail(srv, r, s1);
+        ++done;
+        break;
+      }
+    }
+  }
+  if (wait && !moved && done == 0 && first_busy != nullptr) {
+    int state = 0;
+    ServerRequest& r = *first_busy;
+    int s1 = r.run->poll(true, &state);
+    if (s1 != SSQCD_OK) {
+      request_fail(srv, r, s1);
+      ++done;
+    } else if (state == CgRunBase::kPollDone) {
+      s1 = request_complete(srv, r);
+      if (s1 != SSQCD_OK) request_fail(srv, r, s1);
+      ++done;
+    } else {
+      while (r.run->in_flight() < kServerChunksAhead)
+        if ((s1 = r.run->launch()) != SSQCD_OK) {
+          request_fail(srv, r, s1);
+          ++done;
+          break;
+        }
+    }
+  }
+  if (completed) *completed = done;
+  return SSQCD_OK;
+}
+
+extern "C" int ssqcd_server_status(ssqcd_server srv, long long id, int* state, double* latency_ms) {
+  if (srv == nullptr || state == nullptr) return fail(SSQCD_ERR_ARG, "NULL server or state");
+  auto it = srv->reqs.find(id);
+  if (it == srv->reqs.end()) return fail(SSQCD_ERR_ARG, "unknown request id");
+  const ServerRequest& r = *it->second;
+  *state = r.state;
+  if (latency_ms) {
+    const bool fin = r.state == SSQCD_REQ_DONE || r.state == SSQCD_REQ_FAILED;
+    const auto t1 = fin ? r.t_done : std::chrono::steady_clock::now();
+    *latency_ms = std::chrono::duration<double, std::milli>(t1 - r.t_submit).count();
+  }
+  return SSQCD_OK;
+}
+
+extern "C" int ssqcd_server_take(ssqcd_server srv, long long id, ssqcd_result* out) {
+  if (srv == nullptr || out == nullptr) return fail(SSQCD_ERR_ARG, "NULL server or result pointer");
+  *out = nullptr;
+  auto it = srv->reqs.find(id);
+  if (it == srv->reqs.end()) return fail(SSQCD_ERR_ARG, "unknown request id");
+  ServerRequest& r = *it->second;
+  if (r.state == SSQCD_REQ_QUEUED || r.state == SSQCD_REQ_RUNNING)
+    return fail(SSQCD_ERR_ARG, "request not finished");
+  const int status = r.status;
+  const std::string err = r.error;
+  *out = r.res;
+  r.res = nullptr;
+  srv->reqs.erase(it);
+  if (status != SSQCD_OK) return fail(status, err);
+  return SSQCD_OK;
+}
+
+extern "C" int ssqcd_server_request_bytes(ssqcd_server srv, long long id, size_t* bytes) {
+  if (srv == nullptr || bytes == nullptr) return fail(SSQCD_ERR_ARG, "NULL server or bytes");
+  auto it = srv->reqs.find(id);
+  if (it == srv->reqs.end()) return fail(SSQCD_ERR_ARG, "unknown request id");
+  *bytes = it->second->est_bytes;
+  return SSQCD_OK;
+}
+
+extern "C" int ssqcd_server_counts(ssqcd_server srv, int* queued, int* running, int* finished) {
+  if (srv == nullptr) return fail(SSQCD_ERR_ARG, "NULL server");
+  int q = 0, ru = 0, f = 0;
+  for (auto& kv : srv->reqs) {
+    const int st = kv.second->state;
+    q += st == SSQCD_REQ_QUEUED;
+    ru += st == SSQCD_REQ_RUNNING;
+    f += st == SSQCD_REQ_DONE || st == SSQCD_REQ_FAILED;
+  }
+  if (queued) *queued = q;
+  if (running) *running = ru;
+  if (finished) *finished = f;
+  return SSQCD_OK;
+}
+
+extern "C" void ssqcd_server_destroy(ssqcd_server srv) {
+  if (!srv) return;
+  delete srv;  // requests finish their device work and free their memory
 }
 
 extern "C" int ssqcd_ss_eigpairs(ssqcd_result res, int* count, double* evals, double* evecs, double* residuals,

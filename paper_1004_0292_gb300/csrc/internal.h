@@ -76,9 +76,10 @@ struct DevBuf {
   template <typename T> T* as() const { return static_cast<T*>(p); }
 };
 
-// RAII: DevBuf allocations of this thread use stream-ordered allocation on s.
+// RAII: DevBuf allocations of this thread use stream-ordered allocation on s
+// (on = false: plain allocation inside an enclosing scope).
 struct AllocStream {
-  explicit AllocStream(cudaStream_t s);
+  explicit AllocStream(cudaStream_t s, bool on = true);
   ~AllocStream();
   AllocStream(const AllocStream&) = delete;
   AllocStream& operator=(const AllocStream&) = delete;

@@ -36,9 +36,9 @@ thread_local cudaStream_t t_alloc_stream = nullptr;
 thread_local bool t_alloc_on = false;
 }  // namespace
 
-AllocStream::AllocStream(cudaStream_t s) : prev_(t_alloc_stream), prev_on_(t_alloc_on) {
+AllocStream::AllocStream(cudaStream_t s, bool on) : prev_(t_alloc_stream), prev_on_(t_alloc_on) {
   t_alloc_stream = s;
-  t_alloc_on = true;
+  t_alloc_on = on;
 }
 AllocStream::~AllocStream() {
   t_alloc_stream = prev_;
