@@ -324,6 +324,10 @@ def run_ours(args):
         }
         del lat_m
 
+    serving = None
+    if not args.no_serving:
+        serving = run_serving(ss, stream, U, seed=17 + rank)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(stats[-1], counts[-1], budget_s=args.cpu_budget)
@@ -373,11 +377,94 @@ def run_ours(args):
                                         "note": "CUDA events on one 16-iteration chunk in four; the shift update "
                                                 "overlaps the next iteration's stencil and seed kernels"},
             "e2e": e2e, "cpu_baseline": cpu, "clocks": clk, "gpu_launches": int(launches), "mixed": mixed,
+            "serving": serving,
         }
         print(json.dumps(out), flush=True)
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
+
+
+SERVING = dict(n_requests=24, rate_per_s=20.0, lattices=("8^4 bench field", "4^4 Haar kappa 0.13"),
+               sources=(1, 2, 3, 4), points=(16, 32))
+
+
+def run_serving(ss, stream, U8, seed=17):
+    """Poisson-arrival eigen-window requests on two resident lattices (the
+    8^4 bench field and a 4^4 Haar field, kappa 0.13), driven through the
+    library's request scheduler; once with plain FP64 lattices and once with
+    the mixed precision (float-float shift vectors).  Each request: its
+    lattice's known interval, L in {1..4} Gaussian sources, N in {16, 32}
+    points.  Two arrival patterns of the same requests: exponential gaps
+    with mean 1/20 s (seeded; latency under load) and all at once (the GPU
+    saturated; throughput).  Reports p50/p99 latency (submission to result)
+    and eigenpairs/s at residual <= 1e-8 over the span from the first arrival
+    to the last completion."""
+    import synthetic
+    w = WORKLOAD
+    dims4 = (4, 4, 4, 4)
+    U4 = synthetic.gauge_field(dims4, "haar", seed=1)
+    rng = np.random.default_rng(seed)
+    cfg = SERVING
+    arrivals = np.cumsum(rng.exponential(1.0 / cfg["rate_per_s"], cfg["n_requests"]))
+    plan = []
+    for i in range(cfg["n_requests"]):
+        big = bool(rng.random() < 0.5)
+        L = int(rng.choice(cfg["sources"]))
+        N = int(rng.choice(cfg["points"]))
+        if big:
+            src = synthetic.gaussian_sources(w["dims"], L, seed=5000 + i)
+            plan.append(("8", w["interval"], N, w["M"], src, dict(beta=w["beta"], nprime=min(w["nprime"], N))))
+        else:
+            src = synthetic.gaussian_sources(dims4, L, seed=6000 + i)
+            plan.append(("4", (0.374, 0.3930), N, 8, src, dict(beta=0.3, nprime=min(14, N))))
+    out = {"requests": cfg["n_requests"], "arrivals": f"Poisson, mean {cfg['rate_per_s']}/s, seed {seed}",
+           "mix": "half 8^4 (bench field, its 12-eigenpair window), half 4^4 Haar (8-eigenpair window); "
+                  "L in 1..4, N in {16, 32}"}
+    def serve(lats, arrive):
+        srv = ss.Server()
+        ids = []
+        t0 = time.perf_counter()
+        nxt = 0
+        while True:
+            now = time.perf_counter() - t0
+            while nxt < len(plan) and arrive[nxt] <= now:
+                key, iv, N, M, src, kw = plan[nxt]
+                ids.append(srv.submit(lats[key], iv, N, M, src, **kw))
+                nxt += 1
+            q, r, f = srv.counts()
+            if nxt == len(plan) and q == 0 and r == 0:
+                break
+            if r > 0 or q > 0:
+                srv.progress(wait=(nxt == len(plan) or arrive[nxt] - now > 0.002))
+            else:
+                time.sleep(max(0.0, arrive[nxt] - now))
+        t_end = time.perf_counter() - t0
+        lat_ms, pairs, failed = [], 0, 0
+        for i in ids:
+            state, ms = srv.status(i)
+            lat_ms.append(ms)
+            res = srv.take(i)
+            if res.status != ss.OK:
+                failed += 1
+                continue
+            _, _, rs, _ = ss.ss_eigpairs(res, want_vectors=False)
+            pairs += int(np.sum(rs <= RES_TOL))
+        srv.close()
+        return {"eigenpairs_per_s": pairs / (t_end - arrive[0]), "eigenpairs": pairs, "failed": failed,
+                "latency_ms": {"p50": float(np.percentile(lat_ms, 50)), "p99": float(np.percentile(lat_ms, 99))},
+                "span_s": t_end - arrive[0]}
+
+    for name, prec in (("plain_fp64", ss.FP64), ("mixed", ss.FP64_DFSHIFT)):
+        lats = {"8": ss.create_lattice(w["dims"], w["kappa"], w["bc_t"], precision=prec, stream=stream),
+                "4": ss.create_lattice(dims4, 0.13, -1, precision=prec, stream=stream)}
+        ss.upload_gauge(lats["8"], U8)
+        ss.upload_gauge(lats["4"], U4)
+        out[name] = {"poisson": serve(lats, arrivals),
+                     "burst": serve(lats, np.zeros(len(plan)))}
+    out["burst_mixed_vs_plain"] = (out["mixed"]["burst"]["eigenpairs_per_s"]
+                                   / out["plain_fp64"]["burst"]["eigenpairs_per_s"])
+    return out
 
 
 def cpu_baseline(gpu_stats, pairs, budget_s=20.0, sample_iters=None):
@@ -465,6 +552,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true", help="skip the float-float arm")
+    ap.add_argument("--no-serving", action="store_true", help="skip the request-scheduler run")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     args = ap.parse_args()
     if args.impl == "reference":
