@@ -105,6 +105,15 @@ typedef struct {
   double hankel_tol;      /* Hankel: keep eigen-directions of the (Hermitian
                              positive semidefinite) block Hankel matrix above
                              hankel_tol * its largest eigenvalue; 1e-12          */
+  int    refine;          /* Rayleigh-Ritz: 0 (default) Ritz vectors; 1 refined
+                             Ritz vectors -- for each accepted Ritz value theta
+                             the unit vector x of span(S_hat) minimising
+                             ||(A - theta) x|| (Jia's refined projection, not in
+                             the paper), reported with its Rayleigh quotient;
+                             of two refined vectors that overlap by more than
+                             1/sqrt(2) (a spurious Ritz value lands on its
+                             neighbour's eigenvector) the one with the larger
+                             ||(A - theta) x|| is dropped                      */
 } ssqcd_opts;
 
 /* Counters of one solve.  Times are device milliseconds between CUDA events. */

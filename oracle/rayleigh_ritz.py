@@ -50,3 +50,26 @@ def accept(theta, lo, hi):
     """Mask of Ritz values inside the core interval [lo, hi]."""
     theta = np.asarray(theta)
     return (theta >= lo) & (theta <= hi)
+
+
+def refined_ritz(apply_A_cols, S, thetas, rank_tol=1e-14):
+    """Refined Ritz vectors (Jia's refined projection; an extension, not in
+    the paper): for each given Ritz value theta, the unit vector x of span(S)
+    that minimises ||(A - theta) x||_2, i.e. x = Q v with v the right
+    singular vector of the smallest singular value of A Q - theta Q.
+    Returns (Rayleigh quotients x^H A x, X with unit columns, residuals
+    ||A x - (x^H A x) x||_2)."""
+    Q, _ = orthonormal_basis(S, rank_tol)
+    AQ = apply_A_cols(Q)
+    X = np.empty((Q.shape[0], len(thetas)), dtype=np.complex128)
+    rq = np.empty(len(thetas))
+    res = np.empty(len(thetas))
+    for k, th in enumerate(thetas):
+        _, _, Vh = np.linalg.svd(AQ - th * Q, full_matrices=False)
+        x = Q @ Vh[-1].conj()
+        x = x / np.linalg.norm(x)
+        Ax = apply_A_cols(x[:, None])[:, 0]
+        rq[k] = np.real(np.vdot(x, Ax))
+        res[k] = np.linalg.norm(Ax - rq[k] * x)
+        X[:, k] = x
+    return rq, X, res

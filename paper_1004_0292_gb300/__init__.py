@@ -51,7 +51,7 @@ class Opts(C.Structure):
         ("path", C.c_int), ("beta", C.c_double), ("nprime", C.c_int), ("tol", C.c_double),
         ("sigma", C.c_double), ("max_iter", C.c_int), ("rank_tol", C.c_double),
         ("sources", C.c_void_p), ("sources_on_device", C.c_int), ("reliable_every", C.c_int),
-        ("windows", C.c_int), ("extract", C.c_int), ("hankel_tol", C.c_double),
+        ("windows", C.c_int), ("extract", C.c_int), ("hankel_tol", C.c_double), ("refine", C.c_int),
     ]
 
 
@@ -292,7 +292,7 @@ def moments_noalloc(w, zeta, y, M, stream=None):
 
 def ss_solve(lat: Lattice, interval, N, M, sources, beta=0.3, nprime=0, tol=1e-12, sigma=0.0, max_iter=100000,
              rank_tol=1e-14, path=PATH_LINES, reliable_every=0, windows=1, extract=0,
-             hankel_tol=1e-12) -> Result:
+             hankel_tol=1e-12, refine=0) -> Result:
     """Run the solver; returns a Result (check ``status``)."""
     L = int(np.prod(sources.shape)) // lat.n
     o = Opts()
@@ -302,7 +302,7 @@ def ss_solve(lat: Lattice, interval, N, M, sources, beta=0.3, nprime=0, tol=1e-1
     o.max_iter, o.rank_tol, o.sources, o.sources_on_device = int(max_iter), float(rank_tol), ps, dev
     o.reliable_every = int(reliable_every)
     o.windows = int(windows)
-    o.extract, o.hankel_tol = int(extract), float(hankel_tol)
+    o.extract, o.hankel_tol, o.refine = int(extract), float(hankel_tol), int(refine)
     iv = (C.c_double * 2)(float(interval[0]), float(interval[1]))
     h = C.c_void_p()
     code = lib().ssqcd_ss_solve(lat.handle, iv, int(N), int(M), L, C.byref(o), C.byref(h))
@@ -342,14 +342,14 @@ class Server:
         self._lats = {}
 
     def submit(self, lat: Lattice, interval, N, M, sources, beta=0.3, nprime=0, tol=1e-12, sigma=0.0,
-               max_iter=100000, rank_tol=1e-14, path=PATH_LINES, windows=1, extract=0, hankel_tol=1e-12):
+               max_iter=100000, rank_tol=1e-14, path=PATH_LINES, windows=1, extract=0, hankel_tol=1e-12, refine=0):
         L = int(np.prod(sources.shape)) // lat.n
         o = Opts()
         lib().ssqcd_default_opts(C.byref(o))
         ps, dev, keep = _ptr(sources)
         o.path, o.beta, o.nprime, o.tol, o.sigma = int(path), float(beta), int(nprime), float(tol), float(sigma)
         o.max_iter, o.rank_tol, o.sources, o.sources_on_device = int(max_iter), float(rank_tol), ps, dev
-        o.windows, o.extract, o.hankel_tol = int(windows), int(extract), float(hankel_tol)
+        o.windows, o.extract, o.hankel_tol, o.refine = int(windows), int(extract), float(hankel_tol), int(refine)
         iv = (C.c_double * 2)(float(interval[0]), float(interval[1]))
         rid = C.c_longlong(0)
         _check(lib().ssqcd_server_submit(self.handle, lat.handle, iv, int(N), int(M), L, C.byref(o), C.byref(rid)))

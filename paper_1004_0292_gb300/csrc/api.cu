@@ -279,6 +279,7 @@ extern "C" void ssqcd_default_opts(ssqcd_opts* o) {
   o->windows = 1;
   o->extract = SSQCD_EXTRACT_RR;
   o->hankel_tol = 1e-12;
+  o->refine = 0;
 }
 
 namespace {
@@ -322,9 +323,9 @@ namespace {
 // pairs of A on it, acceptance of the Ritz values in [lo, hi] (hi_open: the
 // upper end belongs to the next window), eigenvectors X (device, [cnt][n]),
 // residuals.  Appends to evals / resid and returns X in `X`.
-int rayleigh_ritz_window(ssqcd_lattice lat, const double2* S, int m, double rank_tol, double lo, double hi,
-                         bool hi_open, std::vector<double>& evals, std::vector<double>& resid, DevBuf& X, int& cnt,
-                         int& rank, DevBuf& scratch, cudaStream_t st) {
+int rayleigh_ritz_window(ssqcd_lattice lat, const double2* S, int m, double rank_tol, bool refine, double lo,
+                         double hi, bool hi_open, std::vector<double>& evals, std::vector<double>& resid, DevBuf& X,
+                         int& cnt, int& rank, DevBuf& scratch, cudaStream_t st) {
   const long long n = 12LL * lat->g.V;
   DevBuf Q, tmp, AQ, Gd;
   int r = 0;
@@ -355,6 +356,83 @@ int rayleigh_ritz_window(ssqcd_lattice lat, const double2* S, int m, double rank
   std::vector<double2> Wacc((size_t)r * cnt);
   for (int i = 0; i < r; ++i)
     for (int c = 0; c < cnt; ++c) Wacc[(size_t)i * cnt + c] = W[(size_t)i * r + acc[c]];
+  std::vector<double> ev(cnt), rs(cnt);
+  for (int c = 0; c < cnt; ++c) ev[c] = theta[acc[c]];
+  if (refine) {
+    // Refined Ritz vectors: [Q, AQ] = W2 R2 (CGS2 on the device), so that
+    // (A - theta) Q w = W2 R2 [-theta w; w]; w minimises the norm of the
+    // small 2r x r matrix R2 [-theta I; I] times w (one-sided Jacobi, host)
+    DevBuf QA, W2, R2d;
+    SS_TRY(QA.alloc(sizeof(double2) * n * 2 * r));
+    SS_CUDA(cudaMemcpyAsync(QA.p, Q.p, sizeof(double2) * n * r, cudaMemcpyDeviceToDevice, st));
+    SS_CUDA(cudaMemcpyAsync(QA.as<double2>() + (size_t)n * r, AQ.p, sizeof(double2) * n * r,
+                            cudaMemcpyDeviceToDevice, st));
+    SS_TRY(W2.alloc(sizeof(double2) * n * 2 * r));
+    SS_TRY(R2d.alloc(sizeof(double2) * 4 * r * r));
+    SS_TRY(cgs2(QA.as<double2>(), 2 * r, n, W2.as<double2>(), R2d.as<double2>(), scratch, st));
+    const int r2 = 2 * r;
+    std::vector<double2> R2((size_t)r2 * r2), Mt((size_t)r2 * r), w(r);
+    SS_CUDA(cudaMemcpyAsync(R2.data(), R2d.p, sizeof(double2) * R2.size(), cudaMemcpyDeviceToHost, st));
+    SS_CUDA(cudaStreamSynchronize(st));
+    auto a_full = [&](int i, int j) {  // Hermitian part of Q^H A Q from its lower triangle
+      return i >= j ? At[(size_t)i * r + j] : make_double2(At[(size_t)j * r + i].x, -At[(size_t)j * r + i].y);
+    };
+    std::vector<double> sminv(cnt);
+    for (int c = 0; c < cnt; ++c) {
+      const double th = ev[c];
+      for (int i = 0; i < r2; ++i)
+        for (int j = 0; j < r; ++j) {
+          const double2 a0 = R2[(size_t)i * r2 + j], a1 = R2[(size_t)i * r2 + r + j];
+          Mt[(size_t)i * r + j] = make_double2(a1.x - th * a0.x, a1.y - th * a0.y);
+        }
+      double smin = 0.0;
+      SS_TRY(small_svd_min_right(r2, r, Mt.data(), &smin, w.data()));
+      sminv[c] = smin;
+      double rq = 0.0;  // Rayleigh quotient w^H (Q^H A Q) w (|w| = 1)
+      for (int i = 0; i < r; ++i)
+        for (int j = 0; j < r; ++j) {
+          const double2 a = a_full(i, j), wi = w[i], wj = w[j];
+          // Re(conj(wi) a wj)
+          const double tr = a.x * wj.x - a.y * wj.y, ti = a.x * wj.y + a.y * wj.x;
+          rq += wi.x * tr + wi.y * ti;
+        }
+      ev[c] = rq;
+      for (int i = 0; i < r; ++i) Wacc[(size_t)i * cnt + c] = w[i];
+    }
+    // A Ritz value with no eigenvalue next to it (spurious) gets the refined
+    // vector of the nearest eigenvalue, a duplicate of that pair: of two
+    // refined vectors with overlap |x_i^H x_j| > 1/sqrt(2) (X = Q W, Q
+    // orthonormal: the overlap is w_i^H w_j) keep the one with the smaller
+    // ||(A - theta) x||.
+    std::vector<char> keep(cnt, 1);
+    for (int i = 0; i < cnt; ++i)
+      for (int j = i + 1; j < cnt; ++j) {
+        if (!keep[i] || !keep[j]) continue;
+        double or_ = 0.0, oi = 0.0;
+        for (int a = 0; a < r; ++a) {
+          const double2 x = Wacc[(size_t)a * cnt + i], y = Wacc[(size_t)a * cnt + j];
+          or_ += x.x * y.x + x.y * y.y;
+          oi += x.x * y.y - x.y * y.x;
+        }
+        if (or_ * or_ + oi * oi > 0.5) keep[sminv[i] <= sminv[j] ? j : i] = 0;
+      }
+    int kept = 0;
+    for (int c = 0; c < cnt; ++c) kept += keep[c];
+    if (kept < cnt) {
+      std::vector<double2> W2acc((size_t)r * kept);
+      std::vector<double> ev2;
+      for (int c = 0, o = 0; c < cnt; ++c) {
+        if (!keep[c]) continue;
+        for (int i = 0; i < r; ++i) W2acc[(size_t)i * kept + o] = Wacc[(size_t)i * cnt + c];
+        ev2.push_back(ev[c]);
+        ++o;
+      }
+      Wacc.swap(W2acc);
+      ev.swap(ev2);
+      cnt = kept;
+      rs.resize(cnt);
+    }
+  }
   DevBuf Wd, AX, th, rn;
   SS_TRY(Wd.alloc(sizeof(double2) * r * cnt));
   SS_CUDA(cudaMemcpyAsync(Wd.p, Wacc.data(), sizeof(double2) * r * cnt, cudaMemcpyHostToDevice, st));
@@ -363,8 +441,6 @@ int rayleigh_ritz_window(ssqcd_lattice lat, const double2* S, int m, double rank
   SS_TRY(AX.alloc(sizeof(double2) * n * cnt));
   SS_TRY(wilson64(lat->g, lat->u64.as<double2>(), X.as<double2>(), AX.as<double2>(), cnt, 0.0, 1.0, nullptr,
                   nullptr, st));
-  std::vector<double> ev(cnt), rs(cnt);
-  for (int c = 0; c < cnt; ++c) ev[c] = theta[acc[c]];
   SS_TRY(th.alloc(sizeof(double) * cnt));
   SS_TRY(rn.alloc(sizeof(double) * cnt));
   SS_CUDA(cudaMemcpyAsync(th.p, ev.data(), sizeof(double) * cnt, cudaMemcpyHostToDevice, st));
@@ -608,8 +684,8 @@ int extract_eigenpairs(ssqcd_lattice lat, const SolvePlan& P, DevBuf& yd, DevBuf
       res->stats.n_ritz += rank;
       continue;
     }
-    SS_TRY(rayleigh_ritz_window(lat, S.as<double2>(), m, P.o.rank_tol, lo, hi, k < K - 1, res->evals,
-                                res->residuals, Xk[k], cntk[k], rank, scratch, st));
+    SS_TRY(rayleigh_ritz_window(lat, S.as<double2>(), m, P.o.rank_tol, P.o.refine != 0, lo, hi, k < K - 1,
+                                res->evals, res->residuals, Xk[k], cntk[k], rank, scratch, st));
     res->stats.rank += rank;
     res->stats.n_ritz += rank;
     res->stats.matvecs_rr += rank + cntk[k];

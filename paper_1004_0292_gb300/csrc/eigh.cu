@@ -227,6 +227,71 @@ int small_svd_left(int m, const double2* a_in, double* sigma, double2* U) {
   return SSQCD_OK;
 }
 
+// Right singular vector of the smallest singular value of a small complex
+// rows x cols matrix (rows >= cols, row-major) by one-sided Jacobi on its
+// columns, accumulating the rotations: M J = U Sigma, so the columns of J
+// are the right singular vectors.  Returns sigma_min in *smin and the vector
+// in v[cols].
+int small_svd_min_right(int rows, int cols, const double2* a_in, double* smin, double2* v) {
+  if (rows < cols || cols <= 0) return fail(SSQCD_ERR_ARG, "small_svd_min_right: need rows >= cols > 0");
+  std::vector<cd> B((size_t)cols * rows);  // column-major
+  for (int r = 0; r < rows; ++r)
+    for (int c = 0; c < cols; ++c) B[(size_t)c * rows + r] = cd(a_in[(size_t)r * cols + c].x, a_in[(size_t)r * cols + c].y);
+  std::vector<cd> J((size_t)cols * cols, cd(0.0, 0.0));  // column-major
+  for (int c = 0; c < cols; ++c) J[(size_t)c * cols + c] = 1.0;
+  bool rotated = true;
+  for (int sweep = 0; sweep < 60 && rotated; ++sweep) {
+    rotated = false;
+    for (int p = 0; p < cols - 1; ++p)
+      for (int q = p + 1; q < cols; ++q) {
+        cd* bp = &B[(size_t)p * rows];
+        cd* bq = &B[(size_t)q * rows];
+        double alpha = 0.0, beta = 0.0;
+        cd g(0.0, 0.0);
+        for (int r = 0; r < rows; ++r) {
+          alpha += std::norm(bp[r]);
+          beta += std::norm(bq[r]);
+          g += std::conj(bp[r]) * bq[r];
+        }
+        const double ag = std::abs(g);
+        if (ag == 0.0 || ag <= DBL_EPSILON * std::sqrt(alpha * beta)) continue;
+        rotated = true;
+        const cd ph = g / ag;
+        const double zeta = (beta - alpha) / (2.0 * ag);
+        const double t = std::copysign(1.0, zeta) / (std::fabs(zeta) + std::sqrt(1.0 + zeta * zeta));
+        const double c = 1.0 / std::sqrt(1.0 + t * t), s = c * t;
+        for (int r = 0; r < rows; ++r) {
+          const cd x = bp[r], y = bq[r] * std::conj(ph);
+          bp[r] = c * x - s * y;
+          bq[r] = s * x + c * y;
+        }
+        cd* jp = &J[(size_t)p * cols];
+        cd* jq = &J[(size_t)q * cols];
+        for (int r = 0; r < cols; ++r) {
+          const cd x = jp[r], y = jq[r] * std::conj(ph);
+          jp[r] = c * x - s * y;
+          jq[r] = s * x + c * y;
+        }
+      }
+  }
+  int cmin = 0;
+  double nmin = 0.0;
+  for (int c = 0; c < cols; ++c) {
+    double s2 = 0.0;
+    for (int r = 0; r < rows; ++r) s2 += std::norm(B[(size_t)c * rows + r]);
+    if (c == 0 || s2 < nmin) {
+      nmin = s2;
+      cmin = c;
+    }
+  }
+  *smin = std::sqrt(nmin);
+  for (int r = 0; r < cols; ++r) {
+    const cd x = J[(size_t)cmin * cols + r];
+    v[r] = make_double2(x.real(), x.imag());
+  }
+  return SSQCD_OK;
+}
+
 }  // namespace ssqcd
 
 extern "C" int ssqcd_small_eigh(int m, const double* a, double* evals, double* evecs) {

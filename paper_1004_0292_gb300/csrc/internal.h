@@ -165,6 +165,7 @@ int contour_nodes(int path, double gamma, double rho, double beta, int N,
 
 // small Hermitian eigenproblem (eigh.cu, host)
 int small_eigh(int m, const double2* a, double* evals, double2* evecs);
+int small_svd_min_right(int rows, int cols, const double2* a, double* smin, double2* v);
 // left singular vectors of a small complex matrix (m x m row-major, host):
 // sigma[m] descending, U[m][m] row-major with singular vector k in column k
 int small_svd_left(int m, const double2* a, double* sigma, double2* U);

@@ -214,3 +214,38 @@ def test_df_eigenpairs_full_size(ss):
     for k in np.flatnonzero(good)[[0, -1]]:
         r = wilson.apply_H(U, vec[k], w["kappa"], w["dims"], w["bc_t"]) - ev[k] * vec[k]
         assert np.linalg.norm(r) <= 1e-8
+
+
+@pytest.mark.parametrize("precision", ["FP64", "FP64_DFSHIFT", "DF"])
+def test_refined_ritz_vectors_full_size(ss, precision):
+    # Refined Ritz vectors (opts.refine): the same eigenvalues, and for every
+    # converged pair a residual no larger than its Ritz residual; the pairs
+    # that a spurious Ritz value nearby contaminates recover FP64-level
+    # residuals, and the spurious value itself (whose refined vector would
+    # duplicate its neighbour) is dropped.
+    import torch
+    w = bench.WORKLOAD
+    U, src = bench.make_inputs(0)
+    lat = ss.create_lattice(w["dims"], w["kappa"], w["bc_t"], precision=getattr(ss, precision),
+                            stream=torch.cuda.Stream())
+    ss.upload_gauge(lat, U)
+    kw = dict(beta=w["beta"], nprime=w["nprime"], tol=w["tol"])
+    r0 = ss.ss_solve(lat, w["interval"], w["N"], w["M"], src, **kw)
+    r1 = ss.ss_solve(lat, w["interval"], w["N"], w["M"], src, refine=1, **kw)
+    assert r0.status == ss.OK and r1.status == ss.OK, (r0.error, r1.error)
+    ev0, _, rs0, _ = ss.ss_eigpairs(r0, want_vectors=False)
+    ev1, vec1, rs1, _ = ss.ss_eigpairs(r1)
+    ref = np.array(json.load(open(GOLDEN))["smooth_8x8x8x8_e0.3_k0.125_s2"]["lowest_abs"])
+    ref = np.sort(ref[(ref >= w["interval"][0]) & (ref <= w["interval"][1])])
+    good0, good1 = rs0 <= 1e-8, rs1 <= 1e-8
+    assert good0.sum() == good1.sum() == 12
+    assert np.max(np.abs(ev1[good1] - ref) / ref) <= 1e-10
+    assert len(ev1) == 12 and np.all(good1)
+    # each refined residual <= the Ritz residual of the same eigenvalue
+    for e, r in zip(ev1, rs1):
+        k0 = int(np.argmin(np.abs(ev0 - e)))
+        assert abs(ev0[k0] - e) <= 1e-10 * e and r <= rs0[k0] * (1 + 1e-6) + 1e-13
+    assert np.max(rs1) <= 1e-9
+    k = int(np.argmax(np.where(good1, rs1, 0)))
+    r = wilson.apply_H(U, vec1[k], w["kappa"], w["dims"], w["bc_t"]) - ev1[k] * vec1[k]
+    assert abs(np.linalg.norm(r) - rs1[k]) <= 1e-12 + 1e-6 * rs1[k]

@@ -127,3 +127,28 @@ def test_hankel_blocks_hermitian_psd_on_conjugate_symmetric_contours():
         H = np.block([[mu[i + j] for j in range(M)] for i in range(M)])
         h = np.linalg.eigvalsh(0.5 * (H + H.conj().T))
         assert h.min() >= -1e-12 * h.max()
+
+
+def test_refined_ritz_properties():
+    # (1) an exact invariant subspace gives eigenvectors; (2) on a perturbed
+    # subspace the refined residual never exceeds the Ritz residual and
+    # equals the smallest singular value of A Q - theta Q (brute force).
+    U, Hd = _dense(seed=6)
+    lam, Vecs = np.linalg.eigh(Hd)
+    n = Hd.shape[0]
+    A = lambda X: Hd @ X
+    S = Vecs[:, 10:14] @ np.diag([1.0, 0.5, 2.0, 1.5])
+    th, X, res = rayleigh_ritz.refined_ritz(A, S, lam[10:14])
+    assert np.max(np.abs(th - lam[10:14])) <= 1e-12
+    assert np.max(res) <= 1e-12
+    g = np.random.default_rng(3)
+    E = g.standard_normal((n, 6)) + 1j * g.standard_normal((n, 6))
+    S2 = Vecs[:, 10:16] + 1e-6 * E
+    th_r, X_r, res_r, _ = rayleigh_ritz.rayleigh_ritz(A, S2)
+    th_f, X_f, res_f = rayleigh_ritz.refined_ritz(A, S2, th_r)
+    assert np.all(res_f <= res_r * (1 + 1e-10) + 1e-15)
+    Q, _ = rayleigh_ritz.orthonormal_basis(S2)
+    for k in range(len(th_r)):
+        smin = np.linalg.svd(Hd @ Q - th_r[k] * Q, compute_uv=False)[-1]
+        x = X_f[:, k]
+        assert np.linalg.norm(Hd @ x - th_r[k] * x) <= smin * (1 + 1e-8) + 1e-15
