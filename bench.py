@@ -324,6 +324,10 @@ def run_ours(args):
         }
         del lat_m
 
+    stencil_large = None
+    if not args.no_serving:
+        stencil_large = run_stencil_large(ss, stream, peaks)
+
     serving = None
     if not args.no_serving:
         serving = run_serving(ss, stream, U, seed=17 + rank)
@@ -377,12 +381,40 @@ def run_ours(args):
                                         "note": "CUDA events on one 16-iteration chunk in four; the shift update "
                                                 "overlaps the next iteration's stencil and seed kernels"},
             "e2e": e2e, "cpu_baseline": cpu, "clocks": clk, "gpu_launches": int(launches), "mixed": mixed,
-            "serving": serving,
+            "serving": serving, "stencil_large": stencil_large,
         }
         print(json.dumps(out), flush=True)
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
+
+
+STENCIL_LARGE = dict(dims=(16, 16, 16, 32), kappa=0.135, eps=0.5, gauge_seed=4, rhs=8, reps=20)
+
+
+def run_stencil_large(ss, stream, peaks):
+    """The stencil alone on the mixed-path lattice shape (16^3 x 32, 8
+    right-hand sides, smooth links eps 0.5, kappa 0.135) where its data no
+    longer fits in L2: FP64, float-float and FP32 spinors with FP16 / FP32
+    12-parameter links.  Algorithmic bytes per application: spinors in and
+    out for every rhs plus the links once (shared by the rhs)."""
+    import synthetic
+    c = STENCIL_LARGE
+    U = synthetic.gauge_field(c["dims"], "smooth", seed=c["gauge_seed"], eps=c["eps"])
+    V = int(np.prod(c["dims"]))
+    out = {"lattice": "x".join(map(str, c["dims"])), "rhs": c["rhs"],
+           "note": "device time of the stencil kernel alone, CUDA events, mean of 20 applications"}
+    for name, prec, cplx, link_b in (("fp64", ss.FP64, 16, 576), ("float_float", ss.DF, 16, 576),
+                                     ("fp32_fp16links", ss.MIXED, 8, 96), ("fp32_fp32links", ss.MIXED_F32LINKS, 8, 192)):
+        lat = ss.create_lattice(c["dims"], c["kappa"], -1, precision=prec, stream=stream)
+        ss.upload_gauge(lat, U)
+        ms = ss.time_stencil(lat, c["rhs"], c["reps"])
+        byts = c["rhs"] * V * 2 * 12 * cplx + V * link_b
+        gbs = byts / (ms / 1e3) / 1e9
+        out[name] = {"us_per_call": 1e3 * ms, "hbm_gbs": gbs, "hbm_frac": gbs / peaks["hbm_gbs"],
+                     "tflops": STENCIL_FLOP_PER_SITE * V * c["rhs"] / (ms / 1e3) / 1e12}
+        del lat
+    return out
 
 
 SERVING = dict(n_requests=24, rate_per_s=20.0, lattices=("8^4 bench field", "4^4 Haar kappa 0.13"),

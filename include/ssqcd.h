@@ -344,6 +344,14 @@ int ssqcd_small_eigh(int m, const double* a, double* evals, double* evecs);
 
 const char* ssqcd_last_error(void);
 
+/* Device time of the stencil alone: `reps` applications of A (after two
+ * warm-up applications) to nrhs device-resident fields, in the lattice's
+ * precision (SSQCD_FP64 / _FP64_SHIFT32 / _FP64_DFSHIFT: FP64; SSQCD_DF:
+ * float-float; the mixed ones: FP32 spinors with their 12-parameter links),
+ * CUDA events on the lattice stream.  *ms_per_call receives the mean time of
+ * one application (all nrhs fields). */
+int ssqcd_time_stencil(ssqcd_lattice lat, int nrhs, int reps, double* ms_per_call);
+
 /* Kernel launches issued by this process so far (all entry points). */
 long long ssqcd_kernel_launches(void);
 

@@ -23,7 +23,7 @@ import numpy as np
 __all__ = [
     "OK", "ERR_ARG", "ERR_OOM", "ERR_BREAKDOWN", "ERR_NOCONV", "ERR_CUDA",
     "FP64", "MIXED", "MIXED_F32LINKS", "FP64_SHIFT32", "FP64_DFSHIFT", "DF", "EXTRACT_RR", "EXTRACT_HANKEL", "PATH_LINES", "PATH_CIRCLE", "SsqcdError",
-    "library_path", "lib", "Server", "create_lattice", "upload_gauge", "apply_H", "apply_H_mixed",
+    "library_path", "lib", "Server", "time_stencil", "create_lattice", "upload_gauge", "apply_H", "apply_H_mixed",
     "contour", "shifted_cg", "moments", "moments_noalloc", "ss_solve", "ss_eigpairs", "small_eigh",
     "kernel_launches", "set_kernel_timing", "Lattice", "Result", "Opts", "Stats",
 ]
@@ -108,6 +108,7 @@ def lib():
         "ssqcd_small_eigh": (i, [i, vp, vp, vp]),
         "ssqcd_last_error": (C.c_char_p, []),
         "ssqcd_kernel_launches": (C.c_longlong, []),
+        "ssqcd_time_stencil": (i, [vp, i, i, vp]),
         "ssqcd_set_kernel_timing": (i, [i]),
         "ssqcd_moments_noalloc": (i, [i, i, i, C.c_longlong, vp, vp, vp, vp, vp]),
     }
@@ -406,6 +407,13 @@ def small_eigh(a):
     vec = np.empty((m, m), dtype=np.complex128)
     _check(lib().ssqcd_small_eigh(m, a.ctypes.data, ev.ctypes.data, vec.ctypes.data))
     return ev, vec
+
+
+def time_stencil(lat: Lattice, nrhs: int, reps: int = 20) -> float:
+    """Mean device ms of one stencil application to nrhs fields (the lattice's precision)."""
+    ms = C.c_double(0.0)
+    _check(lib().ssqcd_time_stencil(lat.handle, int(nrhs), int(reps), C.byref(ms)))
+    return ms.value
 
 
 def kernel_launches() -> int:

@@ -1088,6 +1088,46 @@ extern "C" void ssqcd_server_destroy(ssqcd_server srv) {
   delete srv;  // requests finish their device work and free their memory
 }
 
+extern "C" int ssqcd_time_stencil(ssqcd_lattice lat, int nrhs, int reps, double* ms_per_call) {
+  SS_TRY(check_lattice(lat, true));
+  if (nrhs < 1 || reps < 1 || ms_per_call == nullptr) return fail(SSQCD_ERR_ARG, "bad ssqcd_time_stencil arguments");
+  cudaStream_t st = lat->stream;
+  const long long n = 12LL * lat->g.V * nrhs;
+  const bool mixed = is_mixed(lat->precision), df = lat->precision == SSQCD_DF;
+  if (df) SS_TRY(ensure_df_links(lat));
+  const size_t elem = mixed ? sizeof(float2) : sizeof(double2);
+  DevBuf a, b;
+  SS_TRY(a.alloc(elem * n));
+  SS_TRY(b.alloc(elem * n));
+  SS_CUDA(cudaMemsetAsync(a.p, 0, elem * n, st));
+  auto once = [&]() -> int {
+    if (mixed) {
+      const bool f16 = lat->precision == SSQCD_MIXED;
+      return wilson32(lat->g, f16 ? lat->u16.p : lat->u32.p, f16 ? 16 : 32, a.as<float2>(), b.as<float2>(), nrhs,
+                      0.f, 1.f, nullptr, nullptr, st);
+    }
+    if (df) return wilson_df(lat->g, lat->udf.as<float4>(), a.as<float4>(), b.as<float4>(), nrhs, 0.0, 1.0, st);
+    return wilson64(lat->g, lat->u64.as<double2>(), a.as<double2>(), b.as<double2>(), nrhs, 0.0, 1.0, nullptr,
+                    nullptr, st);
+  };
+  for (int i = 0; i < 2; ++i) SS_TRY(once());
+  cudaEvent_t e0, e1;
+  SS_CUDA(cudaEventCreate(&e0));
+  SS_CUDA(cudaEventCreate(&e1));
+  cudaEventRecord(e0, st);
+  int s1 = SSQCD_OK;
+  for (int i = 0; i < reps && s1 == SSQCD_OK; ++i) s1 = once();
+  cudaEventRecord(e1, st);
+  cudaEventSynchronize(e1);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  SS_TRY(s1);
+  *ms_per_call = ms / reps;
+  return SSQCD_OK;
+}
+
 extern "C" int ssqcd_ss_eigpairs(ssqcd_result res, int* count, double* evals, double* evecs, double* residuals,
                                  ssqcd_stats* stats) {
   if (res == nullptr || count == nullptr) return fail(SSQCD_ERR_ARG, "NULL result or count");
