@@ -188,6 +188,7 @@ __global__ void init_control_kernel(Control c, const double* __restrict__ vn2, i
 // Stencil of one block for one source: q = sigma p - gamma5 (p - kappa D p) at
 // spin w's three components of site s; returns this thread's share of (p, q).
 struct Stencil64 {
+  static constexpr bool kThreadPerSite = false;
   static constexpr int kThreads = kStencilThreads;
   static constexpr int kMinBlocks = 4;  // <= 128 registers (four 128-thread blocks per SM)
   const double2* __restrict__ u;
@@ -214,29 +215,32 @@ struct Stencil64 {
   }
 };
 
+// FP32 spinors (mixed precisions): one thread per site (memory-bound form)
 template <typename LK>
 struct Stencil32 {
-  static constexpr int kThreads = kStencilThreads;
+  static constexpr int kThreads = kSiteThreads;
   static constexpr int kMinBlocks = 1;
+  static constexpr bool kThreadPerSite = true;
   LK lk;
   __device__ __forceinline__ double run(const Geometry& g, const float2* __restrict__ p, float2* __restrict__ q,
-                                        double sigma, int s, int w, void* shm) const {
-    float2 acc[3];
-    block_hops32(lk, p, s, g, static_cast<float2*>(shm), acc);
+                                        double sigma, int s, int, void*) const {
     double d = 0.0;
     if (s < g.V) {
-      const float sg = w < 2 ? -1.f : 1.f;
+      float2 acc[12];
+      site_hops32(lk, p, s, g, acc);
       const float mk = -(float)g.kappa, sf = (float)sigma;
+      float dp = 0.f;
 #pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        const int i = 3 * w + k;
+      for (int i = 0; i < 12; ++i) {
+        const float sg = i < 6 ? -1.f : 1.f;
         const float2 pv = p[i * g.V + s];
         float2 o;
-        o.x = fmaf(sg, fmaf(mk, acc[k].x, pv.x), sf * pv.x);
-        o.y = fmaf(sg, fmaf(mk, acc[k].y, pv.y), sf * pv.y);
+        o.x = fmaf(sg, fmaf(mk, acc[i].x, pv.x), sf * pv.x);
+        o.y = fmaf(sg, fmaf(mk, acc[i].y, pv.y), sf * pv.y);
         q[i * g.V + s] = o;
-        d += (double)(pv.x * o.x + pv.y * o.y);
+        dp = fmaf(pv.x, o.x, fmaf(pv.y, o.y, dp));
       }
+      d = (double)dp;
     }
     return d;
   }
@@ -245,6 +249,7 @@ struct Stencil32 {
 // float-float stencil (SSQCD_DF): q = sigma p - A p, float-float share of
 // (p, q); one hop per warp, 8 warps per block (wilson_df.cuh)
 struct StencilDF {
+  static constexpr bool kThreadPerSite = false;
   static constexpr int kThreads = kStencilThreadsDF;
   static constexpr int kMinBlocks = 3;  // <= 85 registers; a 64-register cap (4 blocks) spilled and measured slower
   const float4* __restrict__ u;
@@ -285,7 +290,8 @@ cg_stencil_kernel(Control c, int L, int par, Geometry g, Op op, double sigma, co
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   double d_pq = 0.0;
   if (c.live[l] != 0) {
-    const int s = blockIdx.x * kSitesPerBlock + lane;
+    const int s = Op::kThreadPerSite ? blockIdx.x * Op::kThreads + (int)threadIdx.x
+                                     : blockIdx.x * kSitesPerBlock + lane;
     d_pq = op.run(g, p_all + (size_t)l * 12 * V, q_all + (size_t)l * 12 * V, sigma, s, w, sh);
   }
   d_pq = warp_sum(d_pq);
@@ -1311,6 +1317,11 @@ class CgRun final : public CgRunBase {
       SS_CUDA(cudaGetDevice(&dev));
       SS_CUDA(cudaDeviceGetAttribute(&n_sm_, cudaDevAttrMultiProcessorCount, dev));
     }
+    tma_ctas_ = n_sm_;
+    if (const char* e = std::getenv("SSQCD_UPDATE_CTAS")) {  // tuning runs: persistent CTAs of the update
+      const int v = std::atoi(e);
+      if (v >= 1 && v <= 4 * n_sm_) tma_ctas_ = v;
+    }
     if constexpr (kShiftDF) {
       if (tma_) SS_TRY(prepare_update_tma<VR>(N * L, L));
     }
@@ -1318,7 +1329,7 @@ class CgRun final : public CgRunBase {
     n_ = 12LL * g.V;
     const long long n = n_;
     const int NL = N * L;
-    nbw_ = wilson_blocks(g);
+    nbw_ = kFP32 ? (g.V + kSiteThreads - 1) / kSiteThreads : wilson_blocks(g);
     nbs_ = seed_blocks(n, L);
     ept_ = update_epts(kShift32 || kShiftDF);
     nbu_ = update_blocks(n, L, ept_);
@@ -1636,10 +1647,10 @@ class CgRun final : public CgRunBase {
     mark(it, 0, st);
     if constexpr (kFP32) {
       if (lat_->precision == SSQCD_MIXED)
-        launch_prio(cg_stencil_kernel<Stencil32<LinksF16>, VR>, grid_a, kStencilThreads, st, prio_hi_, c, L, par, g,
+        launch_prio(cg_stencil_kernel<Stencil32<LinksF16>, VR>, grid_a, kSiteThreads, st, prio_hi_, c, L, par, g,
                     Stencil32<LinksF16>{LinksF16{lat_->u16.as<uint2>(), g.V}}, sigma_, p_.as<VR>(), q_.as<VR>());
       else
-        launch_prio(cg_stencil_kernel<Stencil32<LinksF32>, VR>, grid_a, kStencilThreads, st, prio_hi_, c, L, par, g,
+        launch_prio(cg_stencil_kernel<Stencil32<LinksF32>, VR>, grid_a, kSiteThreads, st, prio_hi_, c, L, par, g,
                     Stencil32<LinksF32>{LinksF32{lat_->u32.as<float4>(), g.V}}, sigma_, p_.as<VR>(), q_.as<VR>());
     } else if constexpr (kSeedDF) {
       launch_prio(cg_stencil_kernel<StencilDF, VR>, grid_a, StencilDF::kThreads, st, prio_hi_, c, L, par, g,
@@ -1661,7 +1672,7 @@ class CgRun final : public CgRunBase {
     mark(it, 4, side_);
     if constexpr (kShiftDF) {
       if (tma_)
-        launch_update_tma<VR>(n_sm_, L, side_, prio_lo_, c, N, par, r_out, yv_, ph_.as<float4>(), n);
+        launch_update_tma<VR>(tma_ctas_, L, side_, prio_lo_, c, N, par, r_out, yv_, ph_.as<float4>(), n);
       else
         launch_update_df<VR>(ept_, L, side_, prio_lo_, c, N, par, r_out, yv_, ph_.as<float4>(), n);
     } else {
@@ -1701,7 +1712,7 @@ class CgRun final : public CgRunBase {
   double sigma_ = 0.0, tol2_ = 0.0, rescale_below_ = 0.0, rescale_by_ = 0.0;
   cudaStream_t st_ = nullptr, side_ = nullptr;
   long long n_ = 0;
-  int nbw_ = 0, nbs_ = 0, nbu_ = 0, ept_ = 1, n_sm_ = 0, prio_lo_ = 0, prio_hi_ = 0, ru_chunks_ = 0;
+  int nbw_ = 0, nbs_ = 0, nbu_ = 0, ept_ = 1, n_sm_ = 0, tma_ctas_ = 0, prio_lo_ = 0, prio_hi_ = 0, ru_chunks_ = 0;
   bool tma_ = false, timing_ = false, mark_on_ = false;
   DevBuf r_, p_, q_, ph_, y32_, x_, kx_, y_out_, ctl_;
   V2* yv_ = nullptr;

@@ -70,39 +70,37 @@ wilson64_kernel(Geometry g, const double2* __restrict__ u, const double2* __rest
   }
 }
 
+// FP32 spinors, one thread per site (see site_hops32).
 template <typename LK>
-__global__ void __launch_bounds__(kStencilThreads)
+__global__ void __launch_bounds__(kSiteThreads)
 wilson32_kernel(Geometry g, LK lk, const float2* __restrict__ in_all,
                 float2* __restrict__ out_all, float c0, float c1, float* __restrict__ dot_partial,
                 const int* __restrict__ skip_if_zero) {
   if (skip_if_zero != nullptr && *skip_if_zero == 0) return;
-  __shared__ float2 sh[12 * 4 * 32];
-  __shared__ double shd[kStencilThreads / 32];
+  __shared__ double shd[kSiteThreads / 32];
   const int rhs = blockIdx.y;
   const int V = g.V;
   const float2* in = in_all + (size_t)rhs * 12 * V;
   float2* out = out_all + (size_t)rhs * 12 * V;
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int s = blockIdx.x * kSitesPerBlock + lane;
-  float2 acc[3];
-  block_hops32(lk, in, s, g, sh, acc);
+  const int s = blockIdx.x * kSiteThreads + threadIdx.x;
   double dot = 0.0;
   if (s < V) {
-    const float sg = w < 2 ? c1 : -c1;
+    float2 acc[12];
+    site_hops32(lk, in, s, g, acc);
     const float mk = -(float)g.kappa;
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      const int i = 3 * w + k;
+    for (int i = 0; i < 12; ++i) {
+      const float sg = i < 6 ? c1 : -c1;
       const float2 p = in[i * V + s];
       float2 o;
-      o.x = fmaf(sg, fmaf(mk, acc[k].x, p.x), c0 * p.x);
-      o.y = fmaf(sg, fmaf(mk, acc[k].y, p.y), c0 * p.y);
+      o.x = fmaf(sg, fmaf(mk, acc[i].x, p.x), c0 * p.x);
+      o.y = fmaf(sg, fmaf(mk, acc[i].y, p.y), c0 * p.y);
       out[i * V + s] = o;
       dot += (double)p.x * o.x + (double)p.y * o.y;
     }
   }
   if (dot_partial != nullptr) {
-    const double b = block_sum<kStencilThreads>(dot, shd);
+    const double b = block_sum<kSiteThreads>(dot, shd);
     if (threadIdx.x == 0) dot_partial[(size_t)rhs * gridDim.x + blockIdx.x] = (float)b;
   }
 }
@@ -187,13 +185,13 @@ int wilson64(const Geometry& g, const double2* u, const double2* in, double2* ou
 int wilson32(const Geometry& g, const void* links, int link_bits, const float2* in, float2* out, int nrhs, float c0,
              float c1, float* dot_partial, const int* skip_if_zero, cudaStream_t s) {
   if (nrhs <= 0) return SSQCD_OK;
-  dim3 grid(wilson_blocks(g), nrhs);
+  dim3 grid((g.V + kSiteThreads - 1) / kSiteThreads, nrhs);
   if (link_bits == 16)
-    wilson32_kernel<<<grid, kStencilThreads, 0, s>>>(g, LinksF16{static_cast<const uint2*>(links), g.V}, in, out, c0,
-                                                     c1, dot_partial, skip_if_zero);
+    wilson32_kernel<<<grid, kSiteThreads, 0, s>>>(g, LinksF16{static_cast<const uint2*>(links), g.V}, in, out, c0, c1,
+                                                  dot_partial, skip_if_zero);
   else
-    wilson32_kernel<<<grid, kStencilThreads, 0, s>>>(g, LinksF32{static_cast<const float4*>(links), g.V}, in, out,
-                                                     c0, c1, dot_partial, skip_if_zero);
+    wilson32_kernel<<<grid, kSiteThreads, 0, s>>>(g, LinksF32{static_cast<const float4*>(links), g.V}, in, out, c0,
+                                                  c1, dot_partial, skip_if_zero);
   count_launches(1);
   SS_CHECK_LAUNCH();
   return SSQCD_OK;

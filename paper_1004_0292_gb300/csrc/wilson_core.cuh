@@ -418,6 +418,25 @@ __device__ __forceinline__ void block_hops64(const Links64& lk, const double2* _
   reduce_dirs(acc, sh, acc_out);
 }
 
+// ---- FP32: one thread per site ------------------------------------------------------
+// For the memory-bound FP32 stencil a thread applies all eight hops of its
+// site and keeps the twelve output components in registers: no cross-warp
+// reduction, no barrier, and the coordinates are computed once per site.  A
+// block of kSiteThreads threads covers kSiteThreads consecutive sites.
+constexpr int kSiteThreads = 128;
+
+template <typename LK>
+__device__ __forceinline__ void site_hops32(const LK& lk, const float2* __restrict__ in, int s, const Geometry& g,
+                                            float2 (&acc)[12]) {
+#pragma unroll
+  for (int i = 0; i < 12; ++i) acc[i] = make_float2(0.f, 0.f);
+  const Coords c = site_coords(s, g);
+  hop_dir32<0>(lk, in, s, c, g, acc);
+  hop_dir32<1>(lk, in, s, c, g, acc);
+  hop_dir32<2>(lk, in, s, c, g, acc);
+  hop_dir32<3>(lk, in, s, c, g, acc);
+}
+
 template <typename LK>
 __device__ __forceinline__ void block_hops32(const LK& lk, const float2* __restrict__ in, int s,
                                              const Geometry& g, float2* sh, float2 (&acc_out)[3]) {
