@@ -72,8 +72,8 @@ STENCIL_FLOP_PER_SITE = 1368
 # dram__bytes_write.sum, one capture per kernel; the algorithmic bytes of such
 # a launch are 64 x 128 x 49152 = 402.7 MB -- part of y / p-hat stays in L2).
 # Null them when the kernel changes.
-UPDATE_FP64_TRAFFIC_ALL_LIVE = (204.486400 + 139.281664) * 1e6
-UPDATE_TMA_TRAFFIC_ALL_LIVE = (204.506880 + 139.959808) * 1e6
+UPDATE_FP64_TRAFFIC_ALL_LIVE = (204.503552 + 139.793408) * 1e6
+UPDATE_TMA_TRAFFIC_ALL_LIVE = (204.504320 + 139.588352) * 1e6
 
 
 def _measured_peaks():
