@@ -347,9 +347,10 @@ cg_stencil_kernel(Control c, int L, int par, Geometry g, Op op, double sigma, co
 // FP64 on GB300 has a dependent-operation latency of ~64 cycles (a division
 // ~630), so this kernel is written to keep FP64 dependency chains short:
 //  * the blocks do r -= alpha q with two independent accumulators of ||r||^2;
-//  * meanwhile lane 0 of the last warp of block b forms xi_{k+1} and
-//    xi_{k+1}/xi_k for shifts b, b + nblocks, ... (they need only alpha_k and
-//    older scalars): the two divisions of a shift run on different SMs;
+//  * meanwhile lane i of the last warp of block b forms xi_{k+1} and
+//    xi_{k+1}/xi_k for shifts b + i nblocks, b + (i + 32) nblocks, ... (they
+//    need only alpha_k and older scalars): the divisions of different
+//    shifts run in parallel lanes and SMs;
 //  * the last block sums the partials, forms beta_k = rr_{k+1} / rr_k with the
 //    stored reciprocal of rr_k, the coefficients a_j = alpha_k xi_{k+1} and
 //    b_j = s beta_k xi_{k+1}/xi_k and the freeze test |xi|^2 rr <= tol^2 ||v||^2
@@ -370,9 +371,9 @@ cg_seed_kernel(Control c, int L, int N, int par, double tol2, const V2* __restri
   const int l = blockIdx.y;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int NL = N * L;
-  if (w == kSeedBlock / 32 - 1 && lane == 0) {
+  if (w == kSeedBlock / 32 - 1) {
     const int nblk = gridDim.x * gridDim.y;
-    for (int qi = blockIdx.y * gridDim.x + blockIdx.x; qi < NL; qi += nblk) {
+    for (int qi = blockIdx.y * gridDim.x + blockIdx.x + lane * nblk; qi < NL; qi += 32 * nblk) {
       const int ls = qi / N;
       if (c.live[ls] == 0 || !c.act[qi]) continue;
       const SeedState sd = c.seed[ls];
@@ -1158,7 +1159,12 @@ void launch_prio(void (*kern)(KArgs...), dim3 grid, dim3 block, cudaStream_t st,
 }
 
 int seed_blocks(long long n, int L) {
-  long long b = (n + 4 * kSeedBlock - 1) / (4 * kSeedBlock);  // >= 4 elements per thread
+  static const int ept = [] {  // SSQCD_SEED_EPT: elements per thread (tuning runs)
+    const char* e = std::getenv("SSQCD_SEED_EPT");
+    const int v = e ? std::atoi(e) : 0;
+    return (v >= 1 && v <= 64) ? v : 4;
+  }();
+  long long b = (n + (long long)ept * kSeedBlock - 1) / ((long long)ept * kSeedBlock);
   const long long cap = (152LL * 2 + L - 1) / L;
   if (b > cap) b = cap;
   return (int)(b < 1 ? 1 : b);
