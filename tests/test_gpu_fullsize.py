@@ -12,6 +12,7 @@ import pytest
 from tests._lib import gpu_module
 
 import bench
+import synthetic
 from oracle import contour, wilson
 
 pytestmark = pytest.mark.gpu
@@ -67,3 +68,40 @@ def test_shifted_cg_full_size_sampled(setup):
         drift = 4 * int(iters[l, j]) * 2.2e-16 * normA * np.linalg.norm(y[l, j])
         assert np.linalg.norm(r) <= w["tol"] * np.linalg.norm(v) + drift
     assert seed_iters == int(iters.max())
+
+
+GOLDEN12 = os.path.join(os.path.dirname(__file__), "golden", "window_12.json")
+
+
+@pytest.mark.parametrize("precision", ["FP64", "FP64_DFSHIFT"])
+def test_eigenpairs_12x12x12x12(precision):
+    # A larger lattice (n = 248832, the 12^4 size of the batched configuration):
+    # the lowest positive cluster of the seeded eps = 0.4 field (12
+    # eigenvalues in [0.0864, 0.0898], next one 0.1495), against the ARPACK
+    # spectrum of the oracle operator; residuals recomputed by the oracle.
+    import torch
+    ss = gpu_module()
+    g = json.load(open(GOLDEN12))["smooth_12x12x12x12_e0.4_k0.13_s3"]
+    dims, kappa, bc = tuple(g["dims"]), g["kappa"], g["bc_t"]
+    U = synthetic.gauge_field(dims, g["kind"], seed=g["seed"], eps=g["eps"])
+    src = synthetic.gaussian_sources(dims, 4, seed=400)
+    lat = ss.create_lattice(dims, kappa, bc, precision=getattr(ss, precision), stream=torch.cuda.Stream())
+    ss.upload_gauge(lat, U)
+    # the core interval brackets the cluster with both ends in spectral gaps;
+    # the contour (rho = 0.0075, beta 0.3) stays far from the next clusters
+    interval = (0.085, 0.091)
+    res = ss.ss_solve(lat, interval, 32, 8, src, beta=0.3, nprime=16)
+    assert res.status == ss.OK, res.error
+    ev, vec, rs, st = ss.ss_eigpairs(res)
+    lam = np.array(g["lowest_abs"])
+    ref = np.sort(lam[(lam >= interval[0]) & (lam <= interval[1])])
+    assert len(ref) == 12
+    good = rs <= 1e-8
+    assert good.sum() == 12
+    assert np.all(rs[~good] > 1e-3)
+    ev, vec, rs = ev[good], vec[good], rs[good]
+    assert np.max(np.abs(ev - ref) / ref) <= 1e-10
+    for k in (0, 11):
+        r = wilson.apply_H(U, vec[k], kappa, dims, bc) - ev[k] * vec[k]
+        assert np.linalg.norm(r) <= 1e-8
+        assert abs(np.linalg.norm(r) - rs[k]) <= 1e-12 + 1e-6 * rs[k]
