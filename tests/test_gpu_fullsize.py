@@ -105,3 +105,30 @@ def test_eigenpairs_12x12x12x12(precision):
         r = wilson.apply_H(U, vec[k], kappa, dims, bc) - ev[k] * vec[k]
         assert np.linalg.norm(r) <= 1e-8
         assert abs(np.linalg.norm(r) - rs[k]) <= 1e-12 + 1e-6 * rs[k]
+
+
+def test_shifted_cg_16x16x16x32_true_residuals():
+    # The lattice shape of the mixed configuration (n = 1572864; 16^3 x 32,
+    # kappa 0.135, eps 0.5): the operator against the oracle's, and the true
+    # residual of every shifted solution recomputed by the oracle operator
+    # (float-float shift vectors; the stopping rule is 1e-10 relative).
+    import torch
+    ss = gpu_module()
+    dims, kappa = (16, 16, 16, 32), 0.135
+    U = synthetic.gauge_field(dims, "smooth", seed=4, eps=0.5)
+    v = synthetic.gaussian_sources(dims, 2, seed=301)
+    z = np.array([0.1 + 0.01j, 0.1 - 0.01j, 0.005j, 0.05 + 0.002j])
+    lat = ss.create_lattice(dims, kappa, -1, precision=ss.FP64_DFSHIFT, stream=torch.cuda.Stream())
+    ss.upload_gauge(lat, U)
+    A = lambda x: wilson.apply_H(U, x, kappa, dims, -1)
+    got = ss.apply_H(lat, v[:1])[0]
+    ref = A(v[0])
+    assert np.linalg.norm(got - ref) <= 1e-13 * np.linalg.norm(ref)
+    code, y, iters, xi, seed_iters = ss.shifted_cg(lat, z, v, tol=1e-10, precision=ss.FP64_DFSHIFT)
+    assert code == ss.OK
+    for l in range(2):
+        vn = np.linalg.norm(v[l])
+        for j in range(len(z)):
+            r = v[l] - (z[j] * y[l, j] - A(y[l, j]))
+            drift = 8 * int(iters[l, j]) * 2.0 ** -48 * (abs(z[j]) + 1 + 8 * kappa) * np.linalg.norm(y[l, j])
+            assert np.linalg.norm(r) <= 1e-10 * vn + drift
