@@ -18,11 +18,16 @@ host.  Under torchrun every rank solves an independent replica (its own
 sources): the path has no data exchange, so scaling is weak and there is no
 collective on the data path.
 
-``mixed`` reports the same metric for the mixed solve precision
-SSQCD_FP64_DFSHIFT (FP64 links, stencil and seed recurrence; the per-shift
-vectors y and p-hat as float-float pairs of FP32 words updated on the FP32
-pipes; FP64 moments and Rayleigh-Ritz) on the same workload at the same
-residual bar, with its ratio to the plain FP64 value.
+The solve runs in the library's default Krylov-basis form: the CG loop is
+the seed recurrence alone (stencil, seed update with the shift scalars,
+seed direction) and stores every seed residual; the moments are formed
+once from the stored residuals.  ``update_form`` times the same solve with
+the per-iteration shift-vector updates (opts.basis = 0) for comparison.
+
+``mixed`` reports the same metric for the solve precision SSQCD_DF
+(float-float links, stencil and seed vectors on the FP32 pipes; FP64
+recurrence scalars, moments and Rayleigh-Ritz) on the same workload at the
+same residual bar, with its ratio to the plain FP64 value.
 
 ``--impl reference`` times the FP64 numpy oracle on the host cores on a
 bounded sample of the same workload (shifted-CG iterations of one source and
@@ -67,6 +72,9 @@ UPDATE_BYTES_PER_UNIT = 64
 # + 24 = 888 FP64 instructions; counted as 1368 flop/site/rhs (FMA = 2); bytes:
 # spinor in 192 B + out 192 B + links 576 B (shared by the rhs) per site.
 STENCIL_FLOP_PER_SITE = 1368
+# DRAM traffic of one launch of the FP64 stencil kernel (cg_stencil_kernel<Stencil64>,
+# 4 rhs, 8^4) from an ncu capture; None until captured for the current kernel.
+STENCIL_FP64_TRAFFIC = None
 # DRAM traffic of one launch of each update kernel with all 128 (source,
 # shift) pairs live on this workload (ncu dram__bytes_read.sum +
 # dram__bytes_write.sum, one capture per kernel; the algorithmic bytes of such
@@ -186,9 +194,9 @@ def run_ours(args):
     ss.upload_gauge(lat, U_d)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
 
-    def step(timing=False):
+    def step(basis=1):
         res = ss.ss_solve(lat, w["interval"], w["N"], w["M"], src_d, beta=w["beta"], nprime=w["nprime"],
-                          tol=w["tol"])
+                          tol=w["tol"], basis=basis)
         if res.status != ss.OK:
             raise RuntimeError(f"solve failed with status {res.status}: {res.error}")
         ev, _, rs, st = ss.ss_eigpairs(res, want_vectors=False)
@@ -223,22 +231,21 @@ def run_ours(args):
     total_ms, total_pairs = reduce_job(float(sum(times)), float(sum(counts)), world, "cuda")
     value = total_pairs / (total_ms / 1e3)
 
-    # ---- roofline of the dominant kernel (fused multi-shift update) ----
+    # ---- roofline of the dominant kernel: the FP64 stencil of the CG loop ----
     n = 12 * int(np.prod(w["dims"]))
-    # kernel events cover one chunk of 16 iterations in four (the library's
-    # sampled kernel timing); units and times below are those iterations'
-    ms_upd = sum(s["ms_k_update"] for s in stats)
-    units = sum(s["timed_shift_updates"] for s in stats) * n
-    launches_upd = sum(s["launches_update"] for s in stats)
-    flops = UPDATE_FLOP_PER_UNIT * units
-    achieved_tf = flops / (ms_upd / 1e3) / 1e12
-    bytes_upd = UPDATE_BYTES_PER_UNIT * units
-    peaks = _measured_peaks()
-    ms_sten = sum(s["ms_k_stencil"] for s in stats)
-    it_tot = launches_upd  # timed iterations
     V = int(np.prod(w["dims"]))
+    peaks = _measured_peaks()
+    # kernel events cover one chunk of 16 iterations in four (the library's
+    # sampled kernel timing); the sums below are those iterations'
+    it_tot = sum(s["launches_update"] for s in stats)  # timed iterations with work
+    ms_sten = sum(s["ms_k_stencil"] for s in stats)
     sten_bytes = it_tot * V * (w["L"] * 2 * 192 + 576)
     sten_flops = it_tot * V * w["L"] * STENCIL_FLOP_PER_SITE
+    sten_tf = sten_flops / (ms_sten / 1e3) / 1e12
+    # moments from the stored residuals: 8 flop per complex FMA, M moments x
+    # (iterations + 1) residuals x n elements x L sources
+    comb_flops = 8 * w["M"] * (stats[-1]["iterations"] + 1) * n * w["L"]
+    update_form = None if args.no_update_form else run_update_form(step, stream, flush, args, n, world)
 
     # ---- end to end through the C ABI with host buffers ----
     e2e = None
@@ -262,10 +269,10 @@ def run_ours(args):
         e2e = {"value": float(sum(e2e_pairs) / sum(e2e_times)), "unit": UNIT,
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
 
-    # ---- mixed-precision arm: float-float shift vectors (SSQCD_FP64_DFSHIFT), same workload and bar ----
+    # ---- mixed-precision arm: float-float links, stencil and seed vectors (SSQCD_DF), same workload and bar ----
     mixed = None
     if not args.no_mixed:
-        lat_m = ss.create_lattice(w["dims"], w["kappa"], w["bc_t"], precision=ss.FP64_DFSHIFT, stream=stream)
+        lat_m = ss.create_lattice(w["dims"], w["kappa"], w["bc_t"], precision=ss.DF, stream=stream)
         ss.upload_gauge(lat_m, U_d)
 
         def step_m():
@@ -300,27 +307,20 @@ def run_ours(args):
         ss.set_kernel_timing(False)
         ms_m, pairs_m = reduce_job(float(sum(t_m)), float(sum(c_m)), world, "cuda")
         value_m = pairs_m / (ms_m / 1e3)
-        ms_upd_m = sum(x["ms_k_update"] for x in s_m)
-        units_m = sum(x["timed_shift_updates"] for x in s_m) * n
         it_m = max(1, sum(x["launches_update"] for x in s_m))
-        gbs_m = UPDATE_BYTES_PER_UNIT * units_m / (ms_upd_m / 1e3) / 1e9
         mixed = {
-            "precision": "SSQCD_FP64_DFSHIFT: FP64 links, stencil and seed recurrence; shift vectors y, p-hat "
-                         "as float-float FP32 pairs (48-bit significand) on the FP32 pipes; FP64 moments, "
-                         "Rayleigh-Ritz",
+            "precision": "SSQCD_DF: float-float (FP32 pair, 48-bit significand) links, stencil and seed vectors "
+                         "on the FP32 pipes; FP64 recurrence scalars, moments, Rayleigh-Ritz",
             "value": value_m, "unit": UNIT, "ms_per_step": ms_m / args.steps,
             "vs_plain_fp64": value_m / value, "eigenpairs_per_step": c_m[-1],
             "max_accepted_residual": r_m[-1], "iterations_per_step": s_m[-1]["iterations"],
+            "basis": s_m[-1]["basis"],
+            "phase_ms": {"cg": s_m[-1]["ms_cg"], "moments": s_m[-1]["ms_moments"], "rr": s_m[-1]["ms_rr"]},
             "cg_us_per_iteration": 1e3 * s_m[-1]["ms_cg"] / max(1, s_m[-1]["iterations"]),
             "kernel_us_per_iteration": {"stencil": 1e3 * sum(x["ms_k_stencil"] for x in s_m) / it_m,
                                         "seed_update": 1e3 * sum(x["ms_k_seed"] for x in s_m) / it_m,
                                         "seed_direction": 1e3 * sum(x["ms_k_scalars"] for x in s_m) / it_m,
-                                        "shift_update": 1e3 * ms_upd_m / it_m, "timed_iterations": it_m},
-            "roofline": {"kernel": "cg_update_tma_kernel (fused multi-shift update, float-float, bulk-copy fed)",
-                         "bound": "hbm",
-                         "achieved": gbs_m, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                         "frac": gbs_m / peaks["hbm_gbs"], "traffic": UPDATE_TMA_TRAFFIC_ALL_LIVE,
-                         "avg_launch_us": 1e3 * ms_upd_m / it_m},
+                                        "timed_iterations": it_m},
         }
         del lat_m
 
@@ -351,35 +351,28 @@ def run_ours(args):
             "eigenpairs_per_step": counts[-1], "iterations_per_step": stats[-1]["iterations"],
             "latency_ms": {"p50": float(np.percentile(lat_sorted, 50)), "p99": float(np.percentile(lat_sorted, 99))},
             "phase_ms": {"cg": stats[-1]["ms_cg"], "moments": stats[-1]["ms_moments"], "rr": stats[-1]["ms_rr"]},
+            "basis": {"form": stats[-1]["basis"], "stored_bytes": stats[-1]["basis_bytes"],
+                      "moments_tflops": comb_flops / (stats[-1]["ms_moments"] / 1e3) / 1e12,
+                      "moments_frac_fp64_peak": comb_flops / (stats[-1]["ms_moments"] / 1e3) / 1e12
+                                                / FP64_PEAK_TFLOPS},
             "cg_us_per_iteration": 1e3 * stats[-1]["ms_cg"] / max(1, stats[-1]["iterations"]),
             "roofline": {
-                "kernel": "cg_update_pf_kernel (fused multi-shift update, FP64, software-pipelined)",
-                "bound": "alu", "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved_tf / FP64_PEAK_TFLOPS, "traffic": UPDATE_FP64_TRAFFIC_ALL_LIVE,
-                "traffic_note": "one launch with all 128 shift vectors live; algorithmic 402.7 MB",
+                "kernel": "cg_stencil_kernel<Stencil64> (Wilson stencil q = K p with the (p, q) partials, FP64)",
+                "bound": "alu", "achieved": sten_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": sten_tf / FP64_PEAK_TFLOPS, "traffic": STENCIL_FP64_TRAFFIC,
+                "flop_per_site_rhs": STENCIL_FLOP_PER_SITE,
                 "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz",
-                "hbm_achieved_gbs": bytes_upd / (ms_upd / 1e3) / 1e9,
-                "hbm_frac_of_measured": bytes_upd / (ms_upd / 1e3) / 1e9 / peaks["hbm_gbs"],
-                "avg_launch_us": 1e3 * ms_upd / max(1, launches_upd),
-                "fraction_of_cg_iteration": (ms_upd / max(1, it_tot)) /
+                "hbm_achieved_gbs": sten_bytes / (ms_sten / 1e3) / 1e9,
+                "avg_launch_us": 1e3 * ms_sten / max(1, it_tot),
+                "fraction_of_cg_iteration": (ms_sten / max(1, it_tot)) /
                                             (stats[-1]["ms_cg"] / max(1, stats[-1]["iterations"])),
-                # the update shares the FP64 pipe with the stencil of the next
-                # iteration (side stream): FP64 flops of both over the CG loop time
-                "loop_fp64_frac": (UPDATE_FLOP_PER_UNIT * n * stats[-1]["shift_updates"]
-                                   + STENCIL_FLOP_PER_SITE * V * w["L"] * stats[-1]["iterations"])
-                                  / (stats[-1]["ms_cg"] / 1e3) / 1e12 / FP64_PEAK_TFLOPS,
             },
-            "stencil": {"bound": "alu", "achieved_tflops": sten_flops / (ms_sten / 1e3) / 1e12,
-                        "frac_fp64_peak": sten_flops / (ms_sten / 1e3) / 1e12 / FP64_PEAK_TFLOPS,
-                        "hbm_gbs": sten_bytes / (ms_sten / 1e3) / 1e9,
-                        "avg_launch_us": 1e3 * ms_sten / max(1, it_tot)},
             "kernel_us_per_iteration": {"stencil": 1e3 * ms_sten / max(1, it_tot),
                                         "seed_update": 1e3 * sum(s["ms_k_seed"] for s in stats) / max(1, it_tot),
                                         "seed_direction": 1e3 * sum(s["ms_k_scalars"] for s in stats) / max(1, it_tot),
-                                        "shift_update": 1e3 * ms_upd / max(1, it_tot),
                                         "timed_iterations": it_tot,
-                                        "note": "CUDA events on one 16-iteration chunk in four; the shift update "
-                                                "overlaps the next iteration's stencil and seed kernels"},
+                                        "note": "CUDA events on one 16-iteration chunk in four"},
+            "update_form": update_form,
             "e2e": e2e, "cpu_baseline": cpu, "clocks": clk, "gpu_launches": int(launches), "mixed": mixed,
             "serving": serving, "stencil_large": stencil_large,
         }
@@ -387,6 +380,43 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def run_update_form(step, stream, flush, args, n, world):
+    """The same FP64 solve with the per-iteration shift-vector updates
+    (opts.basis = 0): value, loop time and the update kernel's FP64 roofline."""
+    import torch
+
+    import paper_1004_0292_gb300 as ss
+    for _ in range(args.warmup):
+        step(basis=0)
+    ss.set_kernel_timing(True)
+    times, counts, stats = [], [], []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        ev, rs, st = step(basis=0)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+        counts.append(int(np.sum(rs <= RES_TOL)))
+        stats.append(st)
+    ss.set_kernel_timing(False)
+    ms, pairs = reduce_job(float(sum(times)), float(sum(counts)), world, "cuda")
+    ms_upd = sum(s["ms_k_update"] for s in stats)
+    units = sum(s["timed_shift_updates"] for s in stats) * n
+    it = max(1, sum(s["launches_update"] for s in stats))
+    tf = UPDATE_FLOP_PER_UNIT * units / (ms_upd / 1e3) / 1e12 if ms_upd > 0 else None
+    return {"value": pairs / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / args.steps, "basis": stats[-1]["basis"],
+            "phase_ms": {"cg": stats[-1]["ms_cg"], "moments": stats[-1]["ms_moments"], "rr": stats[-1]["ms_rr"]},
+            "cg_us_per_iteration": 1e3 * stats[-1]["ms_cg"] / max(1, stats[-1]["iterations"]),
+            "update_kernel": {"kernel": "cg_update_pf_kernel (fused multi-shift update, FP64)",
+                              "achieved_tflops": tf, "frac_fp64_peak": tf / FP64_PEAK_TFLOPS if tf else None,
+                              "avg_launch_us": 1e3 * ms_upd / it, "traffic": UPDATE_FP64_TRAFFIC_ALL_LIVE,
+                              "traffic_note": "one launch with all 128 shift vectors live; algorithmic 402.7 MB"}}
 
 
 STENCIL_LARGE = dict(dims=(16, 16, 16, 32), kappa=0.135, eps=0.5, gauge_seed=4, rhs=8, reps=20)
@@ -425,7 +455,7 @@ def run_serving(ss, stream, U8, seed=17):
     """Poisson-arrival eigen-window requests on two resident lattices (the
     8^4 bench field and a 4^4 Haar field, kappa 0.13), driven through the
     library's request scheduler; once with plain FP64 lattices and once with
-    the mixed precision (float-float shift vectors).  Each request: its
+    float-float ones (SSQCD_DF).  Each request: its
     lattice's known interval, L in {1..4} Gaussian sources, N in {16, 32}
     points.  Two arrival patterns of the same requests: exponential gaps
     with mean 1/20 s (seeded; latency under load) and all at once (the GPU
@@ -487,7 +517,7 @@ def run_serving(ss, stream, U8, seed=17):
                 "latency_ms": {"p50": float(np.percentile(lat_ms, 50)), "p99": float(np.percentile(lat_ms, 99))},
                 "span_s": t_end - arrive[0]}
 
-    for name, prec in (("plain_fp64", ss.FP64), ("mixed", ss.FP64_DFSHIFT)):
+    for name, prec in (("plain_fp64", ss.FP64), ("mixed", ss.DF)):
         lats = {"8": ss.create_lattice(w["dims"], w["kappa"], w["bc_t"], precision=prec, stream=stream),
                 "4": ss.create_lattice(dims4, 0.13, -1, precision=prec, stream=stream)}
         ss.upload_gauge(lats["8"], U8)
@@ -585,6 +615,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true", help="skip the float-float arm")
     ap.add_argument("--no-serving", action="store_true", help="skip the request-scheduler run")
+    ap.add_argument("--no-update-form", action="store_true", help="skip the shift-vector update form")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     args = ap.parse_args()
     if args.impl == "reference":

@@ -114,6 +114,19 @@ typedef struct {
                              1/sqrt(2) (a spurious Ritz value lands on its
                              neighbour's eigenvector) the one with the larger
                              ||(A - theta) x|| is dropped                      */
+  int    basis;           /* SSQCD_FP64 and SSQCD_DF solves: 1 (default) stores
+                             every seed residual r_k and the shift coefficients
+                             of every iteration instead of updating the shift
+                             vectors; the moments are then formed once, from
+                             the stored residuals (y_j = sum_k g_jk r_k, the
+                             g_jk from a backward recurrence over the shift
+                             coefficients).  0: y_j and p-hat_j are updated
+                             every iteration.  Other precisions always update */
+  double basis_max_bytes; /* device memory the stored residuals may take; 0 =
+                             half of the free device memory when the solve
+                             starts.  A solve that reaches it forms y_j and
+                             p-hat_j from the stored residuals and continues
+                             with the per-iteration updates                    */
 } ssqcd_opts;
 
 /* Counters of one solve.  Times are device milliseconds between CUDA events. */
@@ -145,6 +158,10 @@ typedef struct {
   double ms_k_scalars;      /* seed direction p = r + beta p                      */
   double ms_k_update;       /* fused multi-shift update                           */
   long long timed_shift_updates; /* (source, shift) updates in the timed iterations */
+  int    basis;           /* 1: moments from the stored seed residuals; 2: began
+                             so and switched to shift-vector updates at the
+                             memory cap; 0: shift-vector updates throughout    */
+  double basis_bytes;     /* device memory the stored residuals took at most  */
 } ssqcd_stats;
 
 /* ---- lattice / operator ---------------------------------------------------- */
@@ -263,6 +280,16 @@ void ssqcd_default_opts(ssqcd_opts* opts);
  * SSQCD_ERR_ARG/OOM, so its stats can be read). */
 int ssqcd_ss_solve(ssqcd_lattice lat, const double interval[2], int N, int M, int L,
                    const ssqcd_opts* opts, ssqcd_result* out);
+
+/* The filtered block of one window without the extraction: the shifted CG
+ * of ssqcd_ss_solve (same options, same quadrature points, the same choice
+ * between per-iteration shift-vector updates and the stored seed residuals,
+ * opts.basis) and its moments s_hat_k = sum_j w_j zeta_j^k y_j, k < M (Eq. 2),
+ * of the first window.  s_hat: [L][M][V][4][3] complex128, host or device
+ * (s_hat_on_device), written by the library; stats (may be NULL) receives
+ * the shifted-CG counters.  Errors as ssqcd_ss_solve. */
+int ssqcd_ss_moments(ssqcd_lattice lat, const double interval[2], int N, int M, int L, const ssqcd_opts* opts,
+                     double* s_hat, int s_hat_on_device, ssqcd_stats* stats);
 
 /* Read a result.  *count receives the number of accepted eigenpairs; pass
  * evals = NULL first to query it.  evals [count] (ascending), residuals

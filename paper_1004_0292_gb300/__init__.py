@@ -52,6 +52,7 @@ class Opts(C.Structure):
         ("sigma", C.c_double), ("max_iter", C.c_int), ("rank_tol", C.c_double),
         ("sources", C.c_void_p), ("sources_on_device", C.c_int), ("reliable_every", C.c_int),
         ("windows", C.c_int), ("extract", C.c_int), ("hankel_tol", C.c_double), ("refine", C.c_int),
+        ("basis", C.c_int), ("basis_max_bytes", C.c_double),
     ]
 
 
@@ -63,7 +64,7 @@ class Stats(C.Structure):
         ("gamma", C.c_double), ("rho", C.c_double), ("points", C.c_int), ("shift_updates", C.c_longlong),
         ("timed", C.c_int), ("launches_update", C.c_int), ("ms_k_stencil", C.c_double),
         ("ms_k_seed", C.c_double), ("ms_k_scalars", C.c_double), ("ms_k_update", C.c_double),
-        ("timed_shift_updates", C.c_longlong),
+        ("timed_shift_updates", C.c_longlong), ("basis", C.c_int), ("basis_bytes", C.c_double),
     ]
 
     def as_dict(self):
@@ -103,6 +104,7 @@ def lib():
         "ssqcd_moments": (i, [vp, i, i, i, vp, vp, vp, vp, i]),
         "ssqcd_default_opts": (None, [vp]),
         "ssqcd_ss_solve": (i, [vp, vp, i, i, i, vp, vp]),
+        "ssqcd_ss_moments": (i, [vp, vp, i, i, i, vp, vp, i, vp]),
         "ssqcd_ss_eigpairs": (i, [vp, vp, vp, vp, vp, vp]),
         "ssqcd_result_destroy": (None, [vp]),
         "ssqcd_small_eigh": (i, [i, vp, vp, vp]),
@@ -293,8 +295,9 @@ def moments_noalloc(w, zeta, y, M, stream=None):
 
 def ss_solve(lat: Lattice, interval, N, M, sources, beta=0.3, nprime=0, tol=1e-12, sigma=0.0, max_iter=100000,
              rank_tol=1e-14, path=PATH_LINES, reliable_every=0, windows=1, extract=0,
-             hankel_tol=1e-12, refine=0) -> Result:
-    """Run the solver; returns a Result (check ``status``)."""
+             hankel_tol=1e-12, refine=0, basis=1, basis_max_bytes=0.0) -> Result:
+    """Run the solver; returns a Result (check ``status``).  ``basis`` / ``basis_max_bytes``: moments
+    from the stored seed residuals (FP64 and DF lattices; see ssqcd_opts)."""
     L = int(np.prod(sources.shape)) // lat.n
     o = Opts()
     lib().ssqcd_default_opts(C.byref(o))
@@ -304,6 +307,7 @@ def ss_solve(lat: Lattice, interval, N, M, sources, beta=0.3, nprime=0, tol=1e-1
     o.reliable_every = int(reliable_every)
     o.windows = int(windows)
     o.extract, o.hankel_tol, o.refine = int(extract), float(hankel_tol), int(refine)
+    o.basis, o.basis_max_bytes = int(basis), float(basis_max_bytes)
     iv = (C.c_double * 2)(float(interval[0]), float(interval[1]))
     h = C.c_void_p()
     code = lib().ssqcd_ss_solve(lat.handle, iv, int(N), int(M), L, C.byref(o), C.byref(h))
@@ -311,6 +315,24 @@ def ss_solve(lat: Lattice, interval, N, M, sources, beta=0.3, nprime=0, tol=1e-1
         _check(code)
     err = lib().ssqcd_last_error().decode() if code != OK else ""
     return Result(h, code, lat, err)
+
+
+def ss_moments(lat: Lattice, interval, N, M, sources, beta=0.3, nprime=0, tol=1e-12, sigma=0.0, max_iter=100000,
+               path=PATH_LINES, basis=1, basis_max_bytes=0.0):
+    """The moments s_hat (L, M, V, 4, 3) of the first window of ss_solve with these options (Eq. 2) and the
+    shifted-CG stats dict."""
+    L = int(np.prod(sources.shape)) // lat.n
+    o = Opts()
+    lib().ssqcd_default_opts(C.byref(o))
+    ps, dev, keep = _ptr(sources)
+    o.path, o.beta, o.nprime, o.tol, o.sigma = int(path), float(beta), int(nprime), float(tol), float(sigma)
+    o.max_iter, o.sources, o.sources_on_device = int(max_iter), ps, dev
+    o.basis, o.basis_max_bytes = int(basis), float(basis_max_bytes)
+    iv = (C.c_double * 2)(float(interval[0]), float(interval[1]))
+    s = np.empty((L, int(M), lat.V, 4, 3), dtype=np.complex128)
+    st = Stats()
+    _check(lib().ssqcd_ss_moments(lat.handle, iv, int(N), int(M), L, C.byref(o), s.ctypes.data, 0, C.byref(st)))
+    return s, st.as_dict()
 
 
 def ss_eigpairs(res: Result, want_vectors=True):
@@ -343,7 +365,8 @@ class Server:
         self._lats = {}
 
     def submit(self, lat: Lattice, interval, N, M, sources, beta=0.3, nprime=0, tol=1e-12, sigma=0.0,
-               max_iter=100000, rank_tol=1e-14, path=PATH_LINES, windows=1, extract=0, hankel_tol=1e-12, refine=0):
+               max_iter=100000, rank_tol=1e-14, path=PATH_LINES, windows=1, extract=0, hankel_tol=1e-12, refine=0,
+               basis=1, basis_max_bytes=0.0):
         L = int(np.prod(sources.shape)) // lat.n
         o = Opts()
         lib().ssqcd_default_opts(C.byref(o))
@@ -351,6 +374,7 @@ class Server:
         o.path, o.beta, o.nprime, o.tol, o.sigma = int(path), float(beta), int(nprime), float(tol), float(sigma)
         o.max_iter, o.rank_tol, o.sources, o.sources_on_device = int(max_iter), float(rank_tol), ps, dev
         o.windows, o.extract, o.hankel_tol, o.refine = int(windows), int(extract), float(hankel_tol), int(refine)
+        o.basis, o.basis_max_bytes = int(basis), float(basis_max_bytes)
         iv = (C.c_double * 2)(float(interval[0]), float(interval[1]))
         rid = C.c_longlong(0)
         _check(lib().ssqcd_server_submit(self.handle, lat.handle, iv, int(N), int(M), L, C.byref(o), C.byref(rid)))

@@ -280,6 +280,8 @@ extern "C" void ssqcd_default_opts(ssqcd_opts* o) {
   o->extract = SSQCD_EXTRACT_RR;
   o->hankel_tol = 1e-12;
   o->refine = 0;
+  o->basis = 1;
+  o->basis_max_bytes = 0.0;
 }
 
 namespace {
@@ -633,15 +635,18 @@ void fill_cg_stats(const ShiftedCGOut& cg, const std::vector<int>& iters, ssqcd_
   st->ms_k_scalars = cg.ms_k[2];
   st->ms_k_update = cg.ms_k[3];
   st->timed_shift_updates = cg.timed_units;
+  st->basis = cg.basis;
+  st->basis_bytes = cg.basis_bytes;
 }
 
 // After the shifted CG: per window the moments (Eq. 2) and Rayleigh-Ritz (or
 // the Hankel pencil) with acceptance in the window's core; then the
 // eigenpairs of all windows sorted by eigenvalue.  yd: [L][NU][n] FP64
-// solutions (released once the last window's moments exist); vd: the
+// solutions, or kb: the stored residuals of a Krylov-basis run (whichever
+// is filled; released once the last window's moments exist); vd: the
 // sources [L][n].  All device work on st.
-int extract_eigenpairs(ssqcd_lattice lat, const SolvePlan& P, DevBuf& yd, DevBuf& vd, ssqcd_result_s* res,
-                       cudaStream_t st) {
+int extract_eigenpairs(ssqcd_lattice lat, const SolvePlan& P, DevBuf& yd, KrylovBasis& kb, DevBuf& vd,
+                       ssqcd_result_s* res, cudaStream_t st) {
   const long long n = 12LL * lat->g.V;
   const int K = P.K, L = P.L, MM = P.MM, M = P.M, NU = P.NU;
   const double a = P.a, b = P.b, core = P.core, rho = P.rho;
@@ -666,10 +671,14 @@ int extract_eigenpairs(ssqcd_lattice lat, const SolvePlan& P, DevBuf& yd, DevBuf
   for (int k = 0; k < K; ++k) {
     // moments of window k (Eq. 2), S = [L][MM][n]
     SS_TRY(S.alloc(sizeof(double2) * n * m));
-    SS_TRY(moments_device(yd.as<double2>(), NU, MM, L, n, P.coefk[k].data(), S.as<double2>(), scratch, st));
+    if (kb.S > 0)
+      SS_TRY(basis_moments(kb, P.coefk[k].data(), MM, S.as<double2>(), scratch, st));
+    else
+      SS_TRY(moments_device(yd.as<double2>(), NU, MM, L, n, P.coefk[k].data(), S.as<double2>(), scratch, st));
     if (k == K - 1) {
       cudaEventRecord(e1, st);
       yd.release();
+      kb.release();
     }
     // Rayleigh-Ritz (or the Hankel pencil) and acceptance in the window's core
     const double lo = (K == 1) ? a : a + k * core;
@@ -755,6 +764,7 @@ extern "C" int ssqcd_ss_solve(ssqcd_lattice lat, const double interval[2], int N
   cudaStream_t st = lat->stream;
   // sources -> device layout
   DevBuf vd, yd;
+  KrylovBasis kb;
   int s1 = to_device_layout(lat, P.o.sources, L, P.o.sources_on_device, vd);
   if (s1 != SSQCD_OK) {
     delete res;
@@ -763,13 +773,49 @@ extern "C" int ssqcd_ss_solve(ssqcd_lattice lat, const double interval[2], int N
   // shifted CG over the union of the quadrature points (one seed recurrence)
   ShiftedCGOut cg;
   std::vector<int> iters((size_t)P.NU * L);
-  s1 = shifted_cg_device(lat, P.NU, P.zu.data(), L, vd.as<double2>(), P.o.sigma, P.o.tol, P.o.max_iter,
-                         lat->precision, P.o.reliable_every, yd, iters.data(), nullptr, &cg);
+  s1 = shifted_cg_solve(lat, P.NU, P.zu.data(), L, vd.as<double2>(), P.o.sigma, P.o.tol, P.o.max_iter,
+                        lat->precision, P.o.reliable_every,
+                        basis_cap_for(lat->precision, P.o.basis, P.o.basis_max_bytes), yd, &kb, iters.data(), &cg);
   fill_cg_stats(cg, iters, &res->stats);
   *out = res;  // a result handle even on failure, so its stats can be read
   if (s1 != SSQCD_OK) return s1;
   if (!P.hankel) vd.release();
-  return extract_eigenpairs(lat, P, yd, vd, res, st);
+  return extract_eigenpairs(lat, P, yd, kb, vd, res, st);
+}
+
+extern "C" int ssqcd_ss_moments(ssqcd_lattice lat, const double interval[2], int N, int M, int L,
+                                const ssqcd_opts* opts_in, double* s_hat, int s_hat_on_device, ssqcd_stats* stats) {
+  SS_TRY(check_lattice(lat, true));
+  if (s_hat == nullptr) return fail(SSQCD_ERR_ARG, "NULL s_hat");
+  SolvePlan P;
+  SS_TRY(plan_solve(interval, N, M, L, opts_in, &P));
+  const long long n = 12LL * lat->g.V;
+  cudaStream_t st = lat->stream;
+  DevBuf vd, yd, S, scratch;
+  KrylovBasis kb;
+  SS_TRY(to_device_layout(lat, P.o.sources, L, P.o.sources_on_device, vd));
+  ShiftedCGOut cg;
+  std::vector<int> iters((size_t)P.NU * L);
+  SS_TRY(shifted_cg_solve(lat, P.NU, P.zu.data(), L, vd.as<double2>(), P.o.sigma, P.o.tol, P.o.max_iter,
+                          lat->precision, P.o.reliable_every,
+                          basis_cap_for(lat->precision, P.o.basis, P.o.basis_max_bytes), yd, &kb, iters.data(), &cg));
+  SS_TRY(S.alloc(sizeof(double2) * n * P.MM * L));
+  if (kb.S > 0)
+    SS_TRY(basis_moments(kb, P.coefk[0].data(), P.MM, S.as<double2>(), scratch, st));
+  else
+    SS_TRY(moments_device(yd.as<double2>(), P.NU, P.MM, L, n, P.coefk[0].data(), S.as<double2>(), scratch, st));
+  // the first M of the MM moments of each source
+  SS_TRY(vd.alloc(sizeof(double2) * n * M * L));
+  for (int l = 0; l < L; ++l)
+    SS_CUDA(cudaMemcpyAsync(vd.as<double2>() + (size_t)l * M * n, S.as<double2>() + (size_t)l * P.MM * n,
+                            sizeof(double2) * n * M, cudaMemcpyDeviceToDevice, st));
+  SS_TRY(from_device_layout(lat, vd.as<double2>(), M * L, s_hat_on_device, s_hat));
+  SS_CUDA(cudaStreamSynchronize(st));
+  if (stats) {
+    *stats = ssqcd_stats{};
+    fill_cg_stats(cg, iters, stats);
+  }
+  return SSQCD_OK;
 }
 
 // --------------------------------------------------------------------------------------------
@@ -799,11 +845,14 @@ struct ServerRequest {
   std::chrono::steady_clock::time_point t_submit, t_done;
   cudaStream_t stream = nullptr;
   DevBuf vd;
+  double basis_cap = 0.0;  // bytes its stored residuals may take (in est_bytes)
   std::unique_ptr<CgRunBase> run;
+  KrylovBasis basis;
   ssqcd_result_s* res = nullptr;
 
   ~ServerRequest() {
     run.reset();
+    basis.release();
     vd.release();
     if (stream) {
       cudaStreamSynchronize(stream);
@@ -826,9 +875,10 @@ namespace {
 
 constexpr int kServerChunksAhead = 2;
 
-// Device memory of one request at its peak: shift vectors, seed vectors and
-// sources during the CG; moments and the Rayleigh-Ritz basis afterwards.
-size_t estimate_request_bytes(ssqcd_lattice lat, const SolvePlan& P) {
+// Device memory of one request at its peak: shift vectors (or the stored
+// residuals up to their cap), seed vectors and sources during the CG;
+// moments and the Rayleigh-Ritz basis afterwards.
+size_t estimate_request_bytes(ssqcd_lattice lat, const SolvePlan& P, double basis_cap) {
   const size_t n = 12ull * lat->g.V;
   const int prec = lat->precision;
   const size_t sh = (prec == SSQCD_FP64_SHIFT32 || is_mixed(prec)) ? 8 : 16;
@@ -836,8 +886,20 @@ size_t estimate_request_bytes(ssqcd_lattice lat, const SolvePlan& P) {
   const size_t NL = (size_t)P.NU * P.L;
   size_t cg = 2 * sh * n * NL + 4 * sd * n * P.L + 16 * n * P.L;
   if (sh == 8) cg += 16 * n * NL;  // FP64 copy of the solutions at the end
+  // at the cap the run forms y and p-hat while the residuals are still held
+  if (basis_cap > 0.0) cg = std::max(cg, (size_t)basis_cap + 2 * sh * n * NL + 4 * sd * n * P.L + 16 * n * P.L);
   const size_t ex = 16 * n * NL + 4 * 16 * n * (size_t)P.MM * P.L;
   return std::max(cg, ex) + (64u << 20);
+}
+
+// Stored-residual cap of a request: opts.basis_max_bytes, else sixteen times
+// the memory of its shift vectors (2 x 16 B x n per quadrature point and
+// source: up to 32 N iterations), at most half the budget.
+double request_basis_cap(ssqcd_lattice lat, const SolvePlan& P, size_t budget) {
+  if (basis_cap_for(lat->precision, P.o.basis, 1.0) == 0.0) return 0.0;
+  if (P.o.basis_max_bytes > 0.0) return P.o.basis_max_bytes;
+  const double shift = 32.0 * 12.0 * lat->g.V * (double)P.NU * P.L;
+  return std::min(16.0 * shift, 0.5 * (double)budget);
 }
 
 void request_fail(ssqcd_server_s* srv, ServerRequest& r, int status) {
@@ -850,6 +912,7 @@ void request_fail(ssqcd_server_s* srv, ServerRequest& r, int status) {
     srv->running_bytes -= r.est_bytes;
     srv->running -= 1;
   }
+  r.basis.release();
   r.vd.release();
 }
 
@@ -868,7 +931,7 @@ int request_start(ssqcd_server_s* srv, ServerRequest& r) {
   }
   std::unique_ptr<CgRunBase> run;
   SS_TRY(make_cg_run(lat, r.P.NU, r.P.zu.data(), r.P.L, r.vd.as<double2>(), r.P.o.sigma, r.P.o.tol, r.P.o.max_iter,
-                     lat->precision, r.P.o.reliable_every, r.stream, &run));
+                     lat->precision, r.P.o.reliable_every, r.basis_cap, r.stream, &run));
   r.run = std::move(run);
   srv->running_bytes += r.est_bytes;
   srv->running += 1;
@@ -888,14 +951,16 @@ int request_complete(ssqcd_server_s* srv, ServerRequest& r) {
   ShiftedCGOut cg;
   std::vector<int> iters((size_t)r.P.NU * r.P.L);
   SS_TRY(r.run->finish(yd, iters.data(), nullptr, &cg));
+  r.run->take_basis(&r.basis);
   fill_cg_stats(cg, iters, &res->stats);
   r.run.reset();
   if (!r.P.hankel) r.vd.release();
   {
     AllocStream scope(r.stream);  // no device-wide synchronisation on frees
-    SS_TRY(extract_eigenpairs(lat, r.P, yd, r.vd, res, r.stream));
+    SS_TRY(extract_eigenpairs(lat, r.P, yd, r.basis, r.vd, res, r.stream));
   }
   yd.release();
+  r.basis.release();
   r.vd.release();
   SS_CUDA(cudaStreamSynchronize(r.stream));
   res->stream = lat->stream;  // later reads of the result run on the lattice stream
@@ -930,7 +995,8 @@ extern "C" int ssqcd_server_submit(ssqcd_server srv, ssqcd_lattice lat, const do
   auto r = std::make_unique<ServerRequest>();
   SS_TRY(plan_solve(interval, N, M, L, opts, &r->P));
   r->lat = lat;
-  r->est_bytes = estimate_request_bytes(lat, r->P);
+  r->basis_cap = request_basis_cap(lat, r->P, srv->budget);
+  r->est_bytes = estimate_request_bytes(lat, r->P, r->basis_cap);
   if (r->est_bytes > srv->budget)
     return fail(SSQCD_ERR_OOM, "request needs more device memory than the server budget");
   const size_t nd = 2ull * 12 * lat->g.V * L;  // doubles

@@ -180,6 +180,8 @@ struct ShiftedCGOut {
   int launches_update = 0;        // timed iterations (with work)
   long long timed_units = 0;      // (source, shift) updates in the timed iterations
   double ms_k[4] = {0, 0, 0, 0};  // stencil, seed update, seed direction, shift update (timed iterations)
+  int basis = 0;                  // 1 Krylov-basis form, 2 switched to updates at the cap, 0 updates
+  double basis_bytes = 0.0;       // peak bytes of the stored residuals
 };
 bool kernel_timing_enabled();
 inline bool is_mixed(int precision) { return precision == SSQCD_MIXED || precision == SSQCD_MIXED_F32LINKS; }
@@ -187,6 +189,26 @@ inline bool valid_precision(int precision) {
   return precision == SSQCD_FP64 || precision == SSQCD_FP64_SHIFT32 || precision == SSQCD_FP64_DFSHIFT ||
          precision == SSQCD_DF || is_mixed(precision);
 }
+// The stored seed residuals of a shifted-CG run in the Krylov-basis form
+// (mshift.cu): slot s holds r_s (slot 0: the source), kBasisBlock slots and
+// as many iterations' shift coefficients per device block; gam[l][j][s] is
+// the coefficient of slot s in the solution y_j of source l, so
+//   y_j = sum_s gam[l][j][s] r_s   and   s_hat_m = sum_j w_j zeta_j^m y_j
+//       = sum_s (sum_j w_j zeta_j^m gam[l][j][s]) r_s.
+struct KrylovBasis {
+  int L = 0, N = 0, S = 0;     // sources, shifts, slot stride of gam
+  bool df = false;             // float-float residuals (else FP64)
+  long long n = 0;
+  std::vector<std::unique_ptr<DevBuf>> blocks;  // the stored residuals and coefficient records
+  DevBuf tab;                  // device table of the block pointers
+  DevBuf gam;                  // [L][N][S] complex FP64
+  DevBuf count;                // [L] int: slots of source l that enter (the rest are unused)
+  void release();
+};
+// s_hat [L][M][n] = sum_s (sum_j coef[j][m] gam[l][j][s]) r_s; coef_host [N][M]
+int basis_moments(const KrylovBasis& b, const double2* coef_host, int M, double2* s_hat, DevBuf& scratch,
+                  cudaStream_t st);
+
 // Solves for L sources already packed on device (v: [L][12][V]); y out
 // [L][N][12][V] (device, FP64).  iters/xi: host arrays [L*N] (may be null).
 // A resumable shifted-CG run (mshift.cu): see CgRun there.
@@ -197,13 +219,26 @@ class CgRunBase {
   virtual int launch() = 0;                          // enqueue one chunk and its poll read
   virtual int poll(bool wait, int* state) = 0;       // the oldest enqueued chunk's outcome
   virtual int in_flight() const = 0;                 // chunks enqueued, not yet polled
+  // y: FP64 solutions, or left empty when the run ended in the Krylov-basis
+  // form (then take_basis hands over the stored residuals)
   virtual int finish(DevBuf& y, int* iters_host, double2* xi_host, ShiftedCGOut* out) = 0;
+  virtual bool take_basis(KrylovBasis* out) = 0;
 };
+// basis_cap: bytes the stored residuals may take (Krylov-basis form, FP64 and
+// DF precisions); 0 selects the per-iteration shift-vector updates
 int make_cg_run(ssqcd_lattice lat, int N, const double2* z_host, int L, const double2* v, double sigma, double tol,
-                int max_iter, int precision, int reliable_every, cudaStream_t st, std::unique_ptr<CgRunBase>* out);
+                int max_iter, int precision, int reliable_every, double basis_cap, cudaStream_t st,
+                std::unique_ptr<CgRunBase>* out);
+// the basis_cap of a solve from its options: 0 when the form does not apply
+double basis_cap_for(int precision, int basis, double basis_max_bytes);
 int shifted_cg_device(ssqcd_lattice lat, int N, const double2* z_host, int L, const double2* v,
                       double sigma, double tol, int max_iter, int precision, int reliable_every,
                       DevBuf& y, int* iters, double2* xi, ShiftedCGOut* out);
+// The same driven to the end with basis_cap (see make_cg_run): y, or y left
+// empty and *basis filled
+int shifted_cg_solve(ssqcd_lattice lat, int N, const double2* z_host, int L, const double2* v, double sigma,
+                     double tol, int max_iter, int precision, int reliable_every, double basis_cap, DevBuf& y,
+                     KrylovBasis* basis, int* iters, ShiftedCGOut* out);
 
 // moments (moments.cu): s_hat [L][M][12][V] from y [L][N][12][V]
 int moments_device(const double2* y, int N, int M, int L, long long n, const double2* coef_host,

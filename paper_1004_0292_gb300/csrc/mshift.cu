@@ -103,10 +103,54 @@ struct Control {
   double* partial;     // [L][nbw]  (p, q) partials of kernel A
   double* partial_rr;  // [L][nbs]  ||r||^2 partials of kernel B
   double2* x;          // [L][n]    FP64 seed solution (mixed precision only, else null)
+  // Krylov-basis form (null otherwise): table of the blocks that hold the
+  // stored residuals and coefficient records, and the bytes of a block's
+  // residual slots
+  char* const* tab;
+  size_t blk_vec;
 };
 
 constexpr int kUpdBlock = 256;
 constexpr int kSeedBlock = 256;
+
+// ---- Krylov-basis form ------------------------------------------------------------------
+// Instead of updating y_j and p-hat_j for every live shift in every iteration
+// (kernel C), the run keeps every seed residual and the coefficients a_j, b_j
+// and scale of every iteration; since
+//   p-hat_j(k+1) = u_k + b_j(k) p-hat_j(k),  y_j += a_j(k) p-hat_j(k),
+//   p-hat_j(0) = v,  u_k = sc_k r_{k+1}  (r_{k+1} as kernel B stores it),
+// the solution is a fixed combination of the stored vectors r_0 = v, r_1, ...:
+//   y_j = sum_s g_j(s) scs(s) r_s,  g_j(s) = a_j(s) + b_j(s) g_j(s+1)
+// for s = K_j .. 0 with g_j(K_j + 1) = 0 (K_j: the last iteration that
+// updated shift j), scs(0) = 1 and scs(s) = sc_{s-1}.  The moments (Eq. 2)
+// are then one combination of the stored residuals per source, formed once
+// after the loop, and the loop itself is the seed recurrence alone.  The
+// residuals live in blocks of kBasisBlock slots (one chunk of iterations):
+//   [kBasisBlock][L][n] residuals | a [kBasisBlock][L N] | b [kBasisBlock][L N]
+//   | scale [kBasisBlock][L],
+// slot s in block s / kBasisBlock; the coefficient records of iteration k in
+// block k / kBasisBlock.  Kernel B of iteration k reads slot k and writes slot
+// k + 1, with k from the device iteration counter, so the captured chunk
+// graph stays valid as the blocks grow.
+constexpr int kBasisLog = 4;
+constexpr int kBasisBlock = 1 << kBasisLog;
+
+template <typename VR>
+__device__ __forceinline__ VR* basis_slot(const Control& c, int s, long long Ln) {
+  return reinterpret_cast<VR*>(c.tab[s >> kBasisLog]) + (long long)(s & (kBasisBlock - 1)) * Ln;
+}
+// which 0: a_j, 1: b_j of iteration k
+__device__ __forceinline__ double2* basis_coef(const Control& c, int k, int NL, int which) {
+  return reinterpret_cast<double2*>(c.tab[k >> kBasisLog] + c.blk_vec) +
+         ((size_t)which * kBasisBlock + (k & (kBasisBlock - 1))) * NL;
+}
+__device__ __forceinline__ double* basis_scale(const Control& c, int k, int NL, int L) {
+  return reinterpret_cast<double*>(c.tab[k >> kBasisLog] + c.blk_vec + (size_t)2 * kBasisBlock * NL * sizeof(double2)) +
+         (size_t)(k & (kBasisBlock - 1)) * L;
+}
+size_t basis_block_bytes(size_t vec_bytes, int NL, int L) {
+  return vec_bytes + (size_t)2 * kBasisBlock * NL * sizeof(double2) + (size_t)kBasisBlock * L * sizeof(double);
+}
 constexpr int kMaxShifts = 512;   // quadrature points per source
 constexpr int kMaxTotal = 1024;   // (source, point) pairs in one solve
 constexpr int kMaxSources = 64;
@@ -362,6 +406,11 @@ cg_seed_kernel(Control c, int L, int N, int par, double tol2, const V2* __restri
                const V2* __restrict__ q, const V2* __restrict__ p, long long n, double rescale_below,
                double rescale_by) {
   if (*c.ran == 0) return;
+  const int kb = c.tab != nullptr ? *c.seed_iters - 1 : 0;  // this iteration (Krylov-basis form)
+  if (c.tab != nullptr) {
+    r_in = basis_slot<V2>(c, kb, (long long)L * n);
+    r_out = basis_slot<V2>(c, kb + 1, (long long)L * n);
+  }
   __shared__ double sred[kSeedBlock / 32];
   __shared__ double sums[kMaxSources];
   __shared__ double s_scale[kMaxSources], s_beta[kMaxSources];
@@ -492,6 +541,10 @@ cg_seed_kernel(Control c, int L, int N, int par, double tol2, const V2* __restri
       const double2 xn = __ldcg(c.xi_next + qi), ratio = __ldcg(c.ratio + qi), xc = c.xi_cur[qi];
       s_a[qi] = make_double2(alpha * xn.x, alpha * xn.y);
       s_b[qi] = make_double2(sc * beta * ratio.x, sc * beta * ratio.y);
+      if (c.tab != nullptr) {
+        basis_coef(c, kb, NL, 0)[qi] = s_a[qi];
+        basis_coef(c, kb, NL, 1)[qi] = s_b[qi];
+      }
       const bool live = (xn.x * xn.x + xn.y * xn.y) * rr1 > tol2 * c.vnorm2[ls];
       flag = live ? 2 : 1;
       c.xi_prev[qi] = make_double2(xc.x * inv_sc, xc.y * inv_sc);
@@ -526,6 +579,7 @@ cg_seed_kernel(Control c, int L, int N, int par, double tol2, const V2* __restri
     if (lane == 0) {
       c.list_n[par * L + ls] = m;
       c.list_sc[par * L + ls] = s_scale[ls];
+      if (c.tab != nullptr) basis_scale(c, kb, NL, L)[ls] = s_scale[ls];
       if (c.live[ls] != 0) {
         const double sc = s_scale[ls];
         const double rr = sums[ls] * sc * sc;
@@ -555,6 +609,7 @@ cg_seed_p_kernel(Control c, const VR* __restrict__ r, VR* __restrict__ p, long l
   if (*c.ran == 0) return;
   const int l = blockIdx.y;
   if (c.live[l] == 0) return;
+  if (c.tab != nullptr) r = basis_slot<VR>(c, *c.seed_iters, (long long)gridDim.y * n);  // slot k + 1
   const VR* rl = r + (long long)l * n;
   VR* pl = p + (long long)l * n;
   if constexpr (std::is_same<VR, float4>::value) {  // float-float
@@ -1134,6 +1189,150 @@ cg_reliable_kernel(Control c, int L, const double2* __restrict__ v, const double
   if (threadIdx.x == 0) c.done[1] = 0u;
 }
 
+// ---- Krylov-basis form: coefficients and the combination of stored residuals ----------
+// g_j(s) scs(s) for every (source, shift) pair, one thread each: the backward
+// recurrence g_j(s) = a_j(s) + b_j(s) g_j(s+1) from s = K_j = iters_j - 1
+// (zero above); gam [L N][S].
+__global__ void basis_gamma_kernel(Control c, int L, int N, int S, double2* __restrict__ gam) {
+  const int qi = blockIdx.x * blockDim.x + threadIdx.x;
+  const int NL = N * L;
+  if (qi >= NL) return;
+  const int l = qi / N;
+  const int K = c.iters[qi] - 1;
+  double2* gq = gam + (size_t)qi * S;
+  double gx = 0.0, gy = 0.0;
+  for (int s = S - 1; s >= 0; --s) {
+    if (s > K) {
+      gq[s] = make_double2(0.0, 0.0);
+      continue;
+    }
+    const double2 a = basis_coef(c, s, NL, 0)[qi], b = basis_coef(c, s, NL, 1)[qi];
+    const double nx = fma(b.x, gx, fma(-b.y, gy, a.x));
+    const double ny = fma(b.x, gy, fma(b.y, gx, a.y));
+    gx = nx;
+    gy = ny;
+    const double sc = s == 0 ? 1.0 : basis_scale(c, s - 1, NL, L)[l];
+    gq[s] = make_double2(gx * sc, gy * sc);
+  }
+}
+
+// Coefficients of p-hat_j after k iterations for the shifts still live:
+// p-hat_j(k) = sum_{s <= k} (prod_{m=s}^{k-1} b_j(m)) scs(s) r_s; zero for
+// frozen shifts (their p-hat is never used again); P [L N][S].
+__global__ void basis_phat_kernel(Control c, int L, int N, int k, int S, double2* __restrict__ P) {
+  const int qi = blockIdx.x * blockDim.x + threadIdx.x;
+  const int NL = N * L;
+  if (qi >= NL) return;
+  const int l = qi / N;
+  const bool live = c.act[qi] != 0;
+  double2* pq = P + (size_t)qi * S;
+  double px = 1.0, py = 0.0;
+  for (int s = S - 1; s >= 0; --s) {
+    if (!live || s > k) {
+      pq[s] = make_double2(0.0, 0.0);
+      continue;
+    }
+    const double sc = s == 0 ? 1.0 : basis_scale(c, s - 1, NL, L)[l];
+    pq[s] = make_double2(px * sc, py * sc);
+    if (s > 0) {
+      const double2 b = basis_coef(c, s - 1, NL, 1)[qi];
+      const double nx = b.x * px - b.y * py, ny = b.x * py + b.y * px;
+      px = nx;
+      py = ny;
+    }
+  }
+}
+
+// Moment coefficients of one window: G[l][m][s] = sum_j W[j][m] gam[l][j][s]
+// (j ascending: a fixed order).
+__global__ void basis_window_kernel(const double2* __restrict__ gam, const double2* __restrict__ W, int N, int M,
+                                    int L, int S, double2* __restrict__ G) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= (long long)L * M * S) return;
+  const int s = (int)(t % S);
+  const int m = (int)((t / S) % M);
+  const int l = (int)(t / ((long long)S * M));
+  double re = 0.0, im = 0.0;
+  for (int j = 0; j < N; ++j) {
+    const double2 w = W[j * M + m], g = gam[((size_t)l * N + j) * S + s];
+    re = fma(w.x, g.x, fma(-w.y, g.y, re));
+    im = fma(w.x, g.y, fma(w.y, g.x, im));
+  }
+  G[t] = make_double2(re, im);
+}
+
+__device__ __forceinline__ double2 to_d2(double2 x) { return x; }
+__device__ __forceinline__ double2 to_d2(float4 x) { return ff::to_double2(x); }
+__device__ __forceinline__ void put_out(double2& d, double2 x) { d = x; }
+__device__ __forceinline__ void put_out(float4& d, double2 x) { d = ff::from_double2(x); }
+__device__ __forceinline__ void put_out(float2& d, double2 x) {
+  d = make_float2(__double2float_rn(x.x), __double2float_rn(x.y));
+}
+
+// out[l][o][e] = sum_{s < count[l]} C[l][o][s] r_s[l][e] for O outputs per
+// source, kCombOut of them per block (grid.z): every thread keeps kCombOut
+// complex FP64 accumulators of one element and streams the stored residuals
+// of its source once; the coefficients of kCombTile slots at a time sit in
+// shared memory.  FP64 FMA bound (4 kCombOut FMA per 16-byte load).
+constexpr int kCombOut = 8;
+constexpr int kCombTile = 32;
+constexpr int kCombThreads = 256;
+
+template <typename VR, typename VO>
+__global__ void __launch_bounds__(kCombThreads, 2)
+basis_combine_kernel(char* const* __restrict__ tab, long long n, int L, const double2* __restrict__ C, int O, int S,
+                     const int* __restrict__ count, VO* __restrict__ out) {
+  __shared__ double2 s_c[kCombTile][kCombOut];
+  __shared__ const VR* s_p[kCombTile];
+  const int l = blockIdx.y, o0 = blockIdx.z * kCombOut;
+  const int no = min(kCombOut, O - o0);
+  const int Sl = count[l];
+  const long long e = blockIdx.x * (long long)kCombThreads + threadIdx.x;
+  const long long Ln = (long long)L * n;
+  double ax[kCombOut], ay[kCombOut];
+#pragma unroll
+  for (int o = 0; o < kCombOut; ++o) ax[o] = ay[o] = 0.0;
+  for (int s0 = 0; s0 < Sl; s0 += kCombTile) {
+    const int ns = min(kCombTile, Sl - s0);
+    __syncthreads();
+    for (int t = threadIdx.x; t < kCombTile * kCombOut; t += kCombThreads) {
+      const int ss = t / kCombOut, oo = t % kCombOut;
+      s_c[ss][oo] = (ss < ns && oo < no) ? C[((size_t)l * O + o0 + oo) * S + s0 + ss] : make_double2(0.0, 0.0);
+    }
+    if (threadIdx.x < kCombTile) {
+      const int s = s0 + threadIdx.x;
+      s_p[threadIdx.x] = threadIdx.x < ns ? reinterpret_cast<const VR*>(tab[s >> kBasisLog]) +
+                                                (long long)(s & (kBasisBlock - 1)) * Ln + (long long)l * n
+                                          : nullptr;
+    }
+    __syncthreads();
+    if (e < n) {
+#pragma unroll 4
+      for (int ss = 0; ss < ns; ++ss) {
+        const double2 x = to_d2(s_p[ss][e]);
+#pragma unroll
+        for (int o = 0; o < kCombOut; ++o) {
+          const double2 w = s_c[ss][o];
+          ax[o] = fma(w.x, x.x, fma(-w.y, x.y, ax[o]));
+          ay[o] = fma(w.x, x.y, fma(w.y, x.x, ay[o]));
+        }
+      }
+    }
+  }
+  if (e < n)
+    for (int o = 0; o < no; ++o) put_out(out[((size_t)l * O + o0 + o) * n + e], make_double2(ax[o], ay[o]));
+}
+
+template <typename VR, typename VO>
+int launch_combine(char* const* tab, long long n, int L, const double2* C, int O, int S, const int* count, VO* out,
+                   cudaStream_t st) {
+  const dim3 grid((unsigned)((n + kCombThreads - 1) / kCombThreads), L, (O + kCombOut - 1) / kCombOut);
+  basis_combine_kernel<VR, VO><<<grid, kCombThreads, 0, st>>>(tab, n, L, C, O, S, count, out);
+  SS_CHECK_LAUNCH();
+  count_launches(1);
+  return SSQCD_OK;
+}
+
 // Kernel launch with a scheduling priority (cudaLaunchAttributePriority; kept
 // as a node attribute when captured into a graph).  The main chain A, B, P
 // runs at the device's greatest priority so that its blocks are dispatched
@@ -1303,11 +1502,17 @@ class CgRun final : public CgRunBase {
     if (side_) cudaStreamDestroy(side_);
     if (h_poll_) cudaFreeHost(h_poll_);
     if (h_iters_) cudaFreeHost(h_iters_);
+    if (h_tab_) cudaFreeHost(h_tab_);
   }
 
   int init(ssqcd_lattice lat, int N, const double2* z_host, int L, const double2* v, double sigma, double tol,
-           int max_iter, int reliable_every, cudaStream_t st) {
+           int max_iter, int reliable_every, double basis_cap, cudaStream_t st) {
     lat_ = lat;
+    // the Krylov-basis form: 16-byte seed vectors (FP64 or float-float) and
+    // shift vectors of the same type, no reliable updates
+    basis_ = basis_cap > 0.0 && kBasisCapable && reliable_every <= 0;
+    basis_cap_ = basis_cap;
+    basis_state_ = basis_ ? 1 : 0;
     N_ = N;
     L_ = L;
     v_ = v;
@@ -1346,23 +1551,25 @@ class CgRun final : public CgRunBase {
     rescale_by_ = (kShift32 || kShiftDF) ? 0x1p+20 : 0x1p+200;
     tol2_ = tol * tol;
 
-    SS_TRY(r_.alloc(2 * sizeof(VR) * n * L));  // r_k and r_{k+1}: parity buffers
     SS_TRY(p_.alloc(sizeof(VR) * n * L));
     SS_TRY(q_.alloc(sizeof(VR) * n * L));
-    SS_TRY(ph_.alloc(sizeof(V2) * n * NL));
-    if (kShift32) {
-      SS_TRY(y32_.alloc(sizeof(V2) * n * NL));
-      yv_ = y32_.as<V2>();
+    if (basis_) {
+      // block table (pinned host mirror, written once per entry) and the
+      // first two blocks: slot 0 and the first chunk's residuals
+      blk_vec_ = (sizeof(VR) * kBasisBlock * (size_t)L * n + 255) / 256 * 256;
+      blk_bytes_ = basis_block_bytes(blk_vec_, NL, L);
+      tab_cap_ = (max_iter + kChunk) / kBasisBlock + 2;
+      SS_TRY(tab_.alloc(sizeof(char*) * tab_cap_));
+      SS_CUDA(cudaMallocHost(&h_tab_, sizeof(char*) * tab_cap_));
+      SS_TRY(ensure_blocks(kChunk));
+      if (!basis_) return fail(SSQCD_ERR_OOM, "stored residuals: the memory cap is below two blocks");
+    } else {
+      SS_TRY(alloc_update_vectors());
     }
     if (kFP32 && reliable_every > 0) {
       SS_TRY(x_.alloc(sizeof(double2) * n * L));
       SS_TRY(kx_.alloc(sizeof(double2) * n * L));
       SS_CUDA(cudaMemsetAsync(x_.p, 0, sizeof(double2) * n * L, st_));
-    }
-    if (!kShift32) {  // FP64 solutions, or float-float ones converted in place at the end
-      static_assert(kShift32 || sizeof(V2) == sizeof(double2), "in-place conversion needs equal element sizes");
-      SS_TRY(y_out_.alloc(sizeof(double2) * n * NL));
-      yv_ = reinterpret_cast<V2*>(y_out_.p);
     }
     size_t off = 0;
     auto take = [&](size_t bytes) {
@@ -1411,6 +1618,8 @@ class CgRun final : public CgRunBase {
     c.partial = reinterpret_cast<double*>(base + o_part);
     c.partial_rr = reinterpret_cast<double*>(base + o_prr);
     c.x = x_.p != nullptr ? x_.as<double2>() : nullptr;
+    c.tab = basis_ ? tab_.as<char*>() : nullptr;
+    c.blk_vec = blk_vec_;
     double* vn_part = reinterpret_cast<double*>(base + o_vp);
     double* vn2 = reinterpret_cast<double*>(base + o_vn2);
 
@@ -1421,7 +1630,11 @@ class CgRun final : public CgRunBase {
 
     SS_TRY(norm2_partials(v, L, n, vn_part, nbs_, st_));
     SS_TRY(sum_partials(vn_part, L, nbs_, vn2, st_));
-    init_vectors_kernel<<<dim3(nbu_, L), kUpdBlock, 0, st_>>>(v, r_.as<VR>(), p_.as<VR>(), yv_, ph_.as<V2>(), N, n);
+    if (basis_)  // r_0 = v into slot 0; no shift vectors
+      init_vectors_kernel<<<dim3(nbu_, L), kUpdBlock, 0, st_>>>(v, blocks_[0]->as<VR>(), p_.as<VR>(), (V2*)nullptr,
+                                                                (V2*)nullptr, 0, n);
+    else
+      init_vectors_kernel<<<dim3(nbu_, L), kUpdBlock, 0, st_>>>(v, r_.as<VR>(), p_.as<VR>(), yv_, ph_.as<V2>(), N, n);
     SS_CHECK_LAUNCH();
     init_control_kernel<<<1, 256, 0, st_>>>(c, vn2, L, N);
     SS_CHECK_LAUNCH();
@@ -1449,7 +1662,7 @@ class CgRun final : public CgRunBase {
     if (timing_) {
       tev_.resize(kChunk * kSlots);
       for (auto& e : tev_) SS_CUDA(cudaEventCreate(&e));
-      SS_CUDA(cudaMallocHost(&h_iters_, sizeof(int) * NL));
+      SS_CUDA(cudaMallocHost(&h_iters_, sizeof(int) * NL * kInFlight));
     }
     // A chunk of iterations is captured once as a CUDA graph and replayed
     // (the kernels read all per-iteration state from device memory, so every
@@ -1468,6 +1681,7 @@ class CgRun final : public CgRunBase {
     AllocStream scope(st_);
     const int chunk = std::min(kChunk, max_iter_ - k_);
     if (chunk <= 0) return SSQCD_OK;
+    if (basis_) SS_TRY(ensure_blocks(k_ + chunk));  // may switch to the update form
     const int slot = (int)(launched_chunks_ % kInFlight);
     ChunkInfo info;
     info.k_start = k_;
@@ -1482,7 +1696,7 @@ class CgRun final : public CgRunBase {
       cudaError_t le = cudaGetLastError();
       if (le != cudaSuccess) return cuda_fail(le, "shifted CG launch", __FILE__, __LINE__);
     }
-    count_launches(4LL * chunk);
+    count_launches((basis_ ? 3LL : 4LL) * chunk);
     k_ += chunk;
     info.count = chunk;
     ++launched_chunks_;
@@ -1501,7 +1715,9 @@ class CgRun final : public CgRunBase {
     // live-shift count after the last iteration and the error flag
     SS_CUDA(cudaMemcpyAsync(h_poll_ + 2 * slot, c_.live_total, sizeof(int), cudaMemcpyDeviceToHost, st_));
     SS_CUDA(cudaMemcpyAsync(h_poll_ + 2 * slot + 1, c_.err, sizeof(int), cudaMemcpyDeviceToHost, st_));
-    if (timing_) SS_CUDA(cudaMemcpyAsync(h_iters_, c_.iters, sizeof(int) * N_ * L_, cudaMemcpyDeviceToHost, st_));
+    if (timing_)
+      SS_CUDA(cudaMemcpyAsync(h_iters_ + (size_t)slot * N_ * L_, c_.iters, sizeof(int) * N_ * L_,
+                              cudaMemcpyDeviceToHost, st_));
     SS_CUDA(cudaEventRecord(ev_poll_[slot], st_));
     pending_.push_back(info);
     return SSQCD_OK;
@@ -1529,11 +1745,11 @@ class CgRun final : public CgRunBase {
     const ChunkInfo info = pending_.front();
     pending_.erase(pending_.begin());
     ++polled_chunks_;
-    if (timing_ && pending_.empty()) {
-      // h_iters holds the counts after the last launched chunk: read only
-      // when no later chunk is in flight (the timed chunk is then the last)
+    if (timing_) {
+      // the counts after this chunk (each in-flight chunk has its own copy)
       long long units = 0;
-      for (int qi = 0; qi < N_ * L_; ++qi) units += h_iters_[qi];
+      const int* hi = h_iters_ + (size_t)slot * N_ * L_;
+      for (int qi = 0; qi < N_ * L_; ++qi) units += hi[qi];
       if (info.timed) {
         timed_units_ += units - units_prev_;
         for (int it = 0; it < info.count; ++it) {
@@ -1569,7 +1785,9 @@ class CgRun final : public CgRunBase {
     // chunks enqueued past convergence do no work; wait for them
     SS_CUDA(cudaStreamSynchronize(st_));
     pending_.clear();
-    if (kShift32) {  // hand FP64 solutions to the FP64 moments and Rayleigh-Ritz
+    if (basis_) {
+      SS_TRY(finish_basis());
+    } else if (kShift32) {  // hand FP64 solutions to the FP64 moments and Rayleigh-Ritz
       SS_TRY(y_out_.alloc(sizeof(double2) * n * NL));
       SS_TRY(convert_f32_to_f64(reinterpret_cast<const float2*>(yv_), y_out_.as<double2>(), n * NL, st_));
     } else if (kShiftDF) {
@@ -1609,6 +1827,8 @@ class CgRun final : public CgRunBase {
       for (int v2 : it_all) out->shift_updates += v2;
       out->timed = timing_;
       out->timed_units = timed_units_;
+      out->basis = basis_state_;
+      out->basis_bytes = (double)basis_peak_;
       int n_timed = 0;
       for (int kk : t_k_) n_timed += kk < counters[0] ? 1 : 0;
       out->launches_update = n_timed;
@@ -1626,7 +1846,141 @@ class CgRun final : public CgRunBase {
     return SSQCD_OK;
   }
 
+  bool take_basis(KrylovBasis* out) override {
+    if (!basis_ || out == nullptr) return false;
+    out->release();
+    out->L = L_;
+    out->N = N_;
+    out->S = basis_S_;
+    out->df = kSeedDF;
+    out->n = n_;
+    out->blocks.swap(blocks_);
+    out->tab.swap(tab_);
+    out->gam.swap(gam_);
+    out->count.swap(count_);
+    basis_ = false;
+    return true;
+  }
+
  private:
+  static constexpr bool kBasisCapable = sizeof(VR) == 16 && std::is_same<VR, V2>::value;
+
+  // y and p-hat of every shift (and r's parity buffers) for the update form
+  int alloc_update_vectors() {
+    const long long n = n_;
+    const int NL = N_ * L_;
+    SS_TRY(r_.alloc(2 * sizeof(VR) * n * L_));  // r_k and r_{k+1}: parity buffers
+    SS_TRY(ph_.alloc(sizeof(V2) * n * NL));
+    if (kShift32) {
+      SS_TRY(y32_.alloc(sizeof(V2) * n * NL));
+      yv_ = y32_.as<V2>();
+    } else {  // FP64 solutions, or float-float ones converted in place at the end
+      static_assert(kShift32 || sizeof(V2) == sizeof(double2), "in-place conversion needs equal element sizes");
+      SS_TRY(y_out_.alloc(sizeof(double2) * n * NL));
+      yv_ = reinterpret_cast<V2*>(y_out_.p);
+    }
+    return SSQCD_OK;
+  }
+
+  // Blocks for every slot up to kend (and the coefficient records of the
+  // iterations before it); at the memory cap, switch to the update form.
+  int ensure_blocks(int kend) {
+    const size_t need = (size_t)(kend >> kBasisLog) + 1;
+    while (blocks_.size() < need) {
+      if (blocks_.size() >= tab_cap_) return fail(SSQCD_ERR_ARG, "stored residuals: block table full");
+      if ((double)(basis_bytes_ + blk_bytes_) > basis_cap_ && blocks_.size() >= 2) return switch_to_updates();
+      auto b = std::make_unique<DevBuf>();
+      SS_TRY(b->alloc(blk_bytes_));
+      const size_t i = blocks_.size();
+      h_tab_[i] = b->as<char>();
+      SS_CUDA(cudaMemcpyAsync(tab_.as<char*>() + i, h_tab_ + i, sizeof(char*), cudaMemcpyHostToDevice, st_));
+      blocks_.push_back(std::move(b));
+      basis_bytes_ += blk_bytes_;
+      basis_peak_ = std::max(basis_peak_, basis_bytes_);
+    }
+    return SSQCD_OK;
+  }
+
+  // Slot counts from the per-shift iteration counts: S (the stride) and, per
+  // source, the slots its solutions combine (k + 1 while a shift is live).
+  int slot_counts(int k, bool with_live, std::vector<int>& it_all, std::vector<int>& act_all, int* S_out) {
+    const int NL = N_ * L_;
+    it_all.resize(NL);
+    act_all.resize(NL);
+    SS_CUDA(cudaMemcpyAsync(it_all.data(), c_.iters, sizeof(int) * NL, cudaMemcpyDeviceToHost, st_));
+    SS_CUDA(cudaMemcpyAsync(act_all.data(), c_.act, sizeof(int) * NL, cudaMemcpyDeviceToHost, st_));
+    SS_CUDA(cudaStreamSynchronize(st_));
+    std::vector<int> cnt(L_, 0);
+    for (int qi = 0; qi < NL; ++qi) {
+      int c = it_all[qi];
+      if (with_live && act_all[qi]) c = k + 1;
+      cnt[qi / N_] = std::max(cnt[qi / N_], c);
+    }
+    int S = 1;
+    for (int v : cnt) S = std::max(S, v);
+    SS_TRY(count_.alloc(sizeof(int) * L_));
+    SS_CUDA(cudaMemcpyAsync(count_.p, cnt.data(), sizeof(int) * L_, cudaMemcpyHostToDevice, st_));
+    SS_CUDA(cudaStreamSynchronize(st_));  // cnt is a local array
+    *S_out = S;
+    return SSQCD_OK;
+  }
+
+  // End of a run in the Krylov-basis form: the coefficient of every slot in
+  // every solution (the moments are formed from them later).
+  int finish_basis() {
+    int k = 0;
+    SS_CUDA(cudaMemcpy(&k, c_.seed_iters, sizeof(int), cudaMemcpyDeviceToHost));
+    std::vector<int> it_all, act_all;
+    SS_TRY(slot_counts(k, false, it_all, act_all, &basis_S_));
+    const int NL = N_ * L_;
+    SS_TRY(gam_.alloc(sizeof(double2) * (size_t)NL * basis_S_));
+    basis_gamma_kernel<<<(NL + 127) / 128, 128, 0, st_>>>(c_, L_, N_, basis_S_, gam_.as<double2>());
+    SS_CHECK_LAUNCH();
+    count_launches(1);
+    return SSQCD_OK;
+  }
+
+  // At the memory cap: form y_j and p-hat_j from the stored residuals, put
+  // r_k into the parity buffer the next iteration reads, free the blocks and
+  // continue with the per-iteration updates (new chunk graphs).
+  int switch_to_updates() {
+    SS_CUDA(cudaStreamSynchronize(st_));
+    int k = 0;
+    SS_CUDA(cudaMemcpy(&k, c_.seed_iters, sizeof(int), cudaMemcpyDeviceToHost));
+    std::vector<int> it_all, act_all;
+    int S = 0;
+    SS_TRY(slot_counts(k, true, it_all, act_all, &S));
+    SS_TRY(alloc_update_vectors());
+    const int NL = N_ * L_;
+    DevBuf gy, gp;
+    SS_TRY(gy.alloc(sizeof(double2) * (size_t)NL * S));
+    SS_TRY(gp.alloc(sizeof(double2) * (size_t)NL * S));
+    basis_gamma_kernel<<<(NL + 127) / 128, 128, 0, st_>>>(c_, L_, N_, S, gy.as<double2>());
+    SS_CHECK_LAUNCH();
+    basis_phat_kernel<<<(NL + 127) / 128, 128, 0, st_>>>(c_, L_, N_, k, S, gp.as<double2>());
+    SS_CHECK_LAUNCH();
+    count_launches(2);
+    if constexpr (kBasisCapable) {
+      SS_TRY((launch_combine<VR, V2>(tab_.as<char*>(), n_, L_, gy.as<double2>(), N_, S, count_.as<int>(), yv_, st_)));
+      SS_TRY((launch_combine<VR, V2>(tab_.as<char*>(), n_, L_, gp.as<double2>(), N_, S, count_.as<int>(),
+                                     ph_.as<V2>(), st_)));
+    }
+    const char* rk = h_tab_[k >> kBasisLog] + (size_t)(k & (kBasisBlock - 1)) * L_ * n_ * sizeof(VR);
+    SS_CUDA(cudaMemcpyAsync(r_.p, rk, sizeof(VR) * L_ * n_, cudaMemcpyDeviceToDevice, st_));
+    SS_CUDA(cudaStreamSynchronize(st_));
+    gy.release();
+    gp.release();
+    blocks_.clear();
+    basis_bytes_ = 0;
+    basis_ = false;
+    basis_state_ = 2;
+    c_.tab = nullptr;
+    if (gexec_ != nullptr) cudaGraphExecDestroy(gexec_);
+    if (gexec_t_ != nullptr) cudaGraphExecDestroy(gexec_t_);
+    gexec_ = capture(false);
+    gexec_t_ = (timing_ && gexec_ != nullptr) ? capture(true) : nullptr;
+    return SSQCD_OK;
+  }
   struct ChunkInfo {
     int k_start = 0, count = 0;
     bool timed = false;
@@ -1644,12 +1998,12 @@ class CgRun final : public CgRunBase {
     Control& c = c_;
     const dim3 grid_a(nbw_, L), grid_b(nbs_, L), grid_c(nbu_, L);
     const dim3 grid_p((unsigned)((n + kUpdBlock - 1) / kUpdBlock), L);  // one element per thread
-    VR* const r0 = r_.as<VR>();
+    VR* const r0 = r_.as<VR>();  // null in the Krylov-basis form (kernels B, P address the slots)
     const int par = it & 1;
-    const VR* r_in = r0 + (size_t)par * n * L;
-    VR* r_out = r0 + (size_t)(par ^ 1) * n * L;
+    const VR* r_in = basis_ ? nullptr : r0 + (size_t)par * n * L;
+    VR* r_out = basis_ ? nullptr : r0 + (size_t)(par ^ 1) * n * L;
     cudaStream_t st = st_;
-    if (it >= 2) cudaStreamWaitEvent(st, ev_[kChunk + it - 2], 0);
+    if (it >= 2 && !basis_) cudaStreamWaitEvent(st, ev_[kChunk + it - 2], 0);
     mark(it, 0, st);
     if constexpr (kFP32) {
       if (lat_->precision == SSQCD_MIXED)
@@ -1674,6 +2028,11 @@ class CgRun final : public CgRunBase {
     mark(it, 6, st);
     launch_prio(cg_seed_p_kernel<VR>, grid_p, kUpdBlock, st, prio_hi_, c, r_out, p_.as<VR>(), n);
     mark(it, 7, st);
+    if (basis_) {  // no shift-vector update
+      mark(it, 4, st);
+      mark(it, 5, st);
+      return;
+    }
     cudaStreamWaitEvent(side_, ev_[it], 0);
     mark(it, 4, side_);
     if constexpr (kShiftDF) {
@@ -1689,6 +2048,10 @@ class CgRun final : public CgRunBase {
   }
 
   void run_chunk(int count) {
+    if (basis_) {
+      for (int it = 0; it < count; ++it) iteration(it);
+      return;
+    }
     cudaEvent_t ev_fork = ev_[2 * kChunk];
     cudaEventRecord(ev_fork, st_);
     cudaStreamWaitEvent(side_, ev_fork, 0);
@@ -1720,6 +2083,14 @@ class CgRun final : public CgRunBase {
   long long n_ = 0;
   int nbw_ = 0, nbs_ = 0, nbu_ = 0, ept_ = 1, n_sm_ = 0, tma_ctas_ = 0, prio_lo_ = 0, prio_hi_ = 0, ru_chunks_ = 0;
   bool tma_ = false, timing_ = false, mark_on_ = false;
+  // Krylov-basis form
+  bool basis_ = false;
+  int basis_state_ = 0, basis_S_ = 0;
+  double basis_cap_ = 0.0;
+  size_t blk_vec_ = 0, blk_bytes_ = 0, tab_cap_ = 0, basis_bytes_ = 0, basis_peak_ = 0;
+  std::vector<std::unique_ptr<DevBuf>> blocks_;
+  DevBuf tab_, gam_, count_;
+  char** h_tab_ = nullptr;
   DevBuf r_, p_, q_, ph_, y32_, x_, kx_, y_out_, ctl_;
   V2* yv_ = nullptr;
   Control c_{};
@@ -1740,7 +2111,8 @@ class CgRun final : public CgRunBase {
 }  // namespace
 
 int make_cg_run(ssqcd_lattice lat, int N, const double2* z_host, int L, const double2* v, double sigma, double tol,
-                int max_iter, int precision, int reliable_every, cudaStream_t st, std::unique_ptr<CgRunBase>* out) {
+                int max_iter, int precision, int reliable_every, double basis_cap, cudaStream_t st,
+                std::unique_ptr<CgRunBase>* out) {
   if (!valid_precision(precision)) return fail(SSQCD_ERR_ARG, "unknown precision");
   if (is_mixed(precision) && precision != lat->precision)
     return fail(SSQCD_ERR_ARG, "a mixed-precision solve needs a lattice created with that precision");
@@ -1750,7 +2122,7 @@ int make_cg_run(ssqcd_lattice lat, int N, const double2* z_host, int L, const do
   auto make = [&](auto* run) -> int {
     std::unique_ptr<CgRunBase> holder(run);
     if (!run) return fail(SSQCD_ERR_OOM, "host allocation failed");
-    SS_TRY(run->init(lat, N, z_host, L, v, sigma, tol, max_iter, reliable_every, st));
+    SS_TRY(run->init(lat, N, z_host, L, v, sigma, tol, max_iter, reliable_every, basis_cap, st));
     *out = std::move(holder);
     return SSQCD_OK;
   };
@@ -1761,22 +2133,81 @@ int make_cg_run(ssqcd_lattice lat, int N, const double2* z_host, int L, const do
   return make(new (std::nothrow) CgRun<float2, float2>());
 }
 
+namespace {
+
+// Drive a run to the end with two chunks in flight (the host polls one
+// while the device works on the next; a chunk enqueued past convergence
+// does no work).
+int drive(CgRunBase* run) {
+  int status = run->launch();
+  if (status == SSQCD_OK) status = run->launch();
+  while (status == SSQCD_OK) {
+    int state = 0;
+    if ((status = run->poll(true, &state)) != SSQCD_OK) break;
+    if (state == CgRunBase::kPollDone) break;
+    status = run->launch();
+  }
+  return status;
+}
+
+}  // namespace
+
 int shifted_cg_device(ssqcd_lattice lat, int N, const double2* z_host, int L, const double2* v, double sigma,
                       double tol, int max_iter, int precision, int reliable_every, DevBuf& y, int* iters_host,
                       double2* xi_host, ShiftedCGOut* out) {
   std::unique_ptr<CgRunBase> run;
-  SS_TRY(make_cg_run(lat, N, z_host, L, v, sigma, tol, max_iter, precision, reliable_every, lat->stream, &run));
-  // one chunk in flight: launch, wait for its poll, repeat
-  int status = SSQCD_OK;
-  for (;;) {
-    if ((status = run->launch()) != SSQCD_OK) break;
-    int state = 0;
-    if ((status = run->poll(true, &state)) != SSQCD_OK) break;
-    if (state == CgRunBase::kPollDone) break;
-  }
+  SS_TRY(make_cg_run(lat, N, z_host, L, v, sigma, tol, max_iter, precision, reliable_every, 0.0, lat->stream,
+                     &run));
+  const int status = drive(run.get());
   if (status != SSQCD_OK && status != SSQCD_ERR_BREAKDOWN && status != SSQCD_ERR_NOCONV) return status;
   const int s2 = run->finish(y, iters_host, xi_host, out);
   return s2 != SSQCD_OK ? s2 : status;
+}
+
+int shifted_cg_solve(ssqcd_lattice lat, int N, const double2* z_host, int L, const double2* v, double sigma,
+                     double tol, int max_iter, int precision, int reliable_every, double basis_cap, DevBuf& y,
+                     KrylovBasis* basis, int* iters_host, ShiftedCGOut* out) {
+  std::unique_ptr<CgRunBase> run;
+  SS_TRY(make_cg_run(lat, N, z_host, L, v, sigma, tol, max_iter, precision, reliable_every, basis_cap, lat->stream,
+                     &run));
+  const int status = drive(run.get());
+  if (status != SSQCD_OK && status != SSQCD_ERR_BREAKDOWN && status != SSQCD_ERR_NOCONV) return status;
+  const int s2 = run->finish(y, iters_host, nullptr, out);
+  if (s2 != SSQCD_OK) return s2;
+  run->take_basis(basis);
+  return status;
+}
+
+double basis_cap_for(int precision, int basis, double basis_max_bytes) {
+  if (basis == 0 || !(precision == SSQCD_FP64 || precision == SSQCD_DF)) return 0.0;
+  if (basis_max_bytes > 0.0) return basis_max_bytes;
+  size_t free_b = 0, total_b = 0;
+  if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) return 0.0;
+  return 0.5 * (double)free_b;
+}
+
+void KrylovBasis::release() {
+  blocks.clear();
+  tab.release();
+  gam.release();
+  count.release();
+  S = 0;
+}
+
+int basis_moments(const KrylovBasis& b, const double2* coef_host, int M, double2* s_hat, DevBuf& scratch,
+                  cudaStream_t st) {
+  const int N = b.N, L = b.L, S = b.S;
+  const size_t w_bytes = (sizeof(double2) * (size_t)N * M + 255) / 256 * 256;
+  SS_TRY(scratch.alloc(w_bytes + sizeof(double2) * (size_t)L * M * S));
+  double2* W = scratch.as<double2>();
+  double2* G = reinterpret_cast<double2*>(scratch.as<char>() + w_bytes);
+  SS_CUDA(cudaMemcpyAsync(W, coef_host, sizeof(double2) * (size_t)N * M, cudaMemcpyHostToDevice, st));
+  const long long cnt = (long long)L * M * S;
+  basis_window_kernel<<<(unsigned)((cnt + 255) / 256), 256, 0, st>>>(b.gam.as<double2>(), W, N, M, L, S, G);
+  SS_CHECK_LAUNCH();
+  count_launches(1);
+  if (b.df) return launch_combine<float4, double2>(b.tab.as<char*>(), b.n, L, G, M, S, b.count.as<int>(), s_hat, st);
+  return launch_combine<double2, double2>(b.tab.as<char*>(), b.n, L, G, M, S, b.count.as<int>(), s_hat, st);
 }
 
 }  // namespace ssqcd
