@@ -207,29 +207,21 @@ def run_ours(args):
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
-    ss.set_kernel_timing(True)
     clocks = ClockSampler(local)
     clocks.start()
     launches0 = ss.kernel_launches()
-    times, counts, stats = [], [], []
-    for _ in range(args.steps):
-        flush.zero_()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        e0.record(stream)
-        ev, rs, st = step()
-        e1.record(stream)
-        e1.synchronize()
-        times.append(e0.elapsed_time(e1))
-        counts.append(int(np.sum(rs <= RES_TOL)))
-        stats.append(st)
+    times, counts, plain, _ = timed_steps(step, flush, stream, args.steps)
     torch.cuda.synchronize()
     launches = ss.kernel_launches() - launches0
     clk = clocks.stop()
-    ss.set_kernel_timing(False)
     total_ms, total_pairs = reduce_job(float(sum(times)), float(sum(counts)), world, "cuda")
     value = total_pairs / (total_ms / 1e3)
+    # per-kernel device times: separate steps with the library's sampled
+    # kernel timing on (its event nodes slow the loop by a few per cent, so
+    # they stay out of the timed steps above)
+    ss.set_kernel_timing(True)
+    _, _, stats, _ = timed_steps(step, flush, stream, KERNEL_TIMING_STEPS)
+    ss.set_kernel_timing(False)
 
     # ---- roofline of the dominant kernel: the FP64 stencil of the CG loop ----
     n = 12 * int(np.prod(w["dims"]))
@@ -244,7 +236,7 @@ def run_ours(args):
     sten_tf = sten_flops / (ms_sten / 1e3) / 1e12
     # moments from the stored residuals: 8 flop per complex FMA, M moments x
     # (iterations + 1) residuals x n elements x L sources
-    comb_flops = 8 * w["M"] * (stats[-1]["iterations"] + 1) * n * w["L"]
+    comb_flops = 8 * w["M"] * (plain[-1]["iterations"] + 1) * n * w["L"]
     update_form = None if args.no_update_form else run_update_form(step, stream, flush, args, n, world)
 
     # ---- end to end through the C ABI with host buffers ----
@@ -288,22 +280,10 @@ def run_ours(args):
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
+        t_m, c_m, p_m, res_m = timed_steps(step_m, flush, stream, args.steps)
+        r_m = [float(np.max(rs[rs <= RES_TOL])) if np.any(rs <= RES_TOL) else None for rs in res_m]
         ss.set_kernel_timing(True)
-        t_m, c_m, s_m, r_m = [], [], [], []
-        for _ in range(args.steps):
-            flush.zero_()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            torch.cuda.synchronize()
-            e0.record(stream)
-            ev, rs, st = step_m()
-            e1.record(stream)
-            e1.synchronize()
-            t_m.append(e0.elapsed_time(e1))
-            c_m.append(int(np.sum(rs <= RES_TOL)))
-            s_m.append(st)
-            r_m.append(float(np.max(rs[rs <= RES_TOL])) if np.any(rs <= RES_TOL) else None)
-        torch.cuda.synchronize()
+        _, _, s_m, _ = timed_steps(step_m, flush, stream, KERNEL_TIMING_STEPS)
         ss.set_kernel_timing(False)
         ms_m, pairs_m = reduce_job(float(sum(t_m)), float(sum(c_m)), world, "cuda")
         value_m = pairs_m / (ms_m / 1e3)
@@ -313,10 +293,10 @@ def run_ours(args):
                          "on the FP32 pipes; FP64 recurrence scalars, moments, Rayleigh-Ritz",
             "value": value_m, "unit": UNIT, "ms_per_step": ms_m / args.steps,
             "vs_plain_fp64": value_m / value, "eigenpairs_per_step": c_m[-1],
-            "max_accepted_residual": r_m[-1], "iterations_per_step": s_m[-1]["iterations"],
-            "basis": s_m[-1]["basis"],
-            "phase_ms": {"cg": s_m[-1]["ms_cg"], "moments": s_m[-1]["ms_moments"], "rr": s_m[-1]["ms_rr"]},
-            "cg_us_per_iteration": 1e3 * s_m[-1]["ms_cg"] / max(1, s_m[-1]["iterations"]),
+            "max_accepted_residual": r_m[-1], "iterations_per_step": p_m[-1]["iterations"],
+            "basis": p_m[-1]["basis"],
+            "phase_ms": {"cg": p_m[-1]["ms_cg"], "moments": p_m[-1]["ms_moments"], "rr": p_m[-1]["ms_rr"]},
+            "cg_us_per_iteration": 1e3 * p_m[-1]["ms_cg"] / max(1, p_m[-1]["iterations"]),
             "kernel_us_per_iteration": {"stencil": 1e3 * sum(x["ms_k_stencil"] for x in s_m) / it_m,
                                         "seed_update": 1e3 * sum(x["ms_k_seed"] for x in s_m) / it_m,
                                         "seed_direction": 1e3 * sum(x["ms_k_scalars"] for x in s_m) / it_m,
@@ -334,7 +314,7 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(stats[-1], counts[-1], budget_s=args.cpu_budget)
+        cpu = cpu_baseline(plain[-1], counts[-1], budget_s=args.cpu_budget)
 
     if rank == 0:
         lat_sorted = sorted(times)
@@ -348,16 +328,16 @@ def run_ours(args):
                        "interval": list(w["interval"]), "beta": w["beta"], "nprime": w["nprime"],
                        "tol": w["tol"], "parallelism": f"replicas x{world}",
                        "l2": "flushed between steps (256 MB write)"},
-            "eigenpairs_per_step": counts[-1], "iterations_per_step": stats[-1]["iterations"],
+            "eigenpairs_per_step": counts[-1], "iterations_per_step": plain[-1]["iterations"],
             "latency_ms": {"p50": float(np.percentile(lat_sorted, 50)), "p99": float(np.percentile(lat_sorted, 99))},
-            "phase_ms": {"cg": stats[-1]["ms_cg"], "moments": stats[-1]["ms_moments"], "rr": stats[-1]["ms_rr"]},
-            "basis": {"form": stats[-1]["basis"], "stored_bytes": stats[-1]["basis_bytes"],
-                      "moments_tflops": comb_flops / (stats[-1]["ms_moments"] / 1e3) / 1e12,
-                      "moments_frac_fp64_peak": comb_flops / (stats[-1]["ms_moments"] / 1e3) / 1e12
+            "phase_ms": {"cg": plain[-1]["ms_cg"], "moments": plain[-1]["ms_moments"], "rr": plain[-1]["ms_rr"]},
+            "basis": {"form": plain[-1]["basis"], "stored_bytes": plain[-1]["basis_bytes"],
+                      "moments_tflops": comb_flops / (plain[-1]["ms_moments"] / 1e3) / 1e12,
+                      "moments_frac_fp64_peak": comb_flops / (plain[-1]["ms_moments"] / 1e3) / 1e12
                                                 / FP64_PEAK_TFLOPS},
-            "cg_us_per_iteration": 1e3 * stats[-1]["ms_cg"] / max(1, stats[-1]["iterations"]),
+            "cg_us_per_iteration": 1e3 * plain[-1]["ms_cg"] / max(1, plain[-1]["iterations"]),
             "roofline": {
-                "kernel": "cg_stencil_kernel<Stencil64> (Wilson stencil q = K p with the (p, q) partials, FP64)",
+                "kernel": "cg_stencil_kernel<Stencil64h> (Wilson stencil q = K p with the (p, q) partials, FP64, 16 sites a block)",
                 "bound": "alu", "achieved": sten_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": sten_tf / FP64_PEAK_TFLOPS, "traffic": STENCIL_FP64_TRAFFIC,
                 "flop_per_site_rhs": STENCIL_FLOP_PER_SITE,
@@ -365,13 +345,13 @@ def run_ours(args):
                 "hbm_achieved_gbs": sten_bytes / (ms_sten / 1e3) / 1e9,
                 "avg_launch_us": 1e3 * ms_sten / max(1, it_tot),
                 "fraction_of_cg_iteration": (ms_sten / max(1, it_tot)) /
-                                            (stats[-1]["ms_cg"] / max(1, stats[-1]["iterations"])),
+                                            (plain[-1]["ms_cg"] / max(1, plain[-1]["iterations"])),
             },
             "kernel_us_per_iteration": {"stencil": 1e3 * ms_sten / max(1, it_tot),
                                         "seed_update": 1e3 * sum(s["ms_k_seed"] for s in stats) / max(1, it_tot),
                                         "seed_direction": 1e3 * sum(s["ms_k_scalars"] for s in stats) / max(1, it_tot),
                                         "timed_iterations": it_tot,
-                                        "note": "CUDA events on one 16-iteration chunk in four"},
+                                        "note": "separate steps with the library kernel timing on: CUDA events on one 16-iteration chunk in four"},
             "update_form": update_form,
             "e2e": e2e, "cpu_baseline": cpu, "clocks": clk, "gpu_launches": int(launches), "mixed": mixed,
             "serving": serving, "stencil_large": stencil_large,
@@ -382,37 +362,49 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def run_update_form(step, stream, flush, args, n, world):
-    """The same FP64 solve with the per-iteration shift-vector updates
-    (opts.basis = 0): value, loop time and the update kernel's FP64 roofline."""
-    import torch
+KERNEL_TIMING_STEPS = 2
 
-    import paper_1004_0292_gb300 as ss
-    for _ in range(args.warmup):
-        step(basis=0)
-    ss.set_kernel_timing(True)
-    times, counts, stats = [], [], []
-    for _ in range(args.steps):
+
+def timed_steps(step, flush, stream, k, **kw):
+    """k solves, each timed with CUDA events on the library's stream after an
+    L2 flush: (ms list, accepted-pair counts, stats list, residual arrays)."""
+    import torch
+    times, counts, stats, res = [], [], [], []
+    for _ in range(k):
         flush.zero_()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         e0.record(stream)
-        ev, rs, st = step(basis=0)
+        ev, rs, st = step(**kw)
         e1.record(stream)
         e1.synchronize()
         times.append(e0.elapsed_time(e1))
         counts.append(int(np.sum(rs <= RES_TOL)))
         stats.append(st)
-    ss.set_kernel_timing(False)
+        res.append(rs)
+    torch.cuda.synchronize()
+    return times, counts, stats, res
+
+
+def run_update_form(step, stream, flush, args, n, world):
+    """The same FP64 solve with the per-iteration shift-vector updates
+    (opts.basis = 0): value, loop time and the update kernel's FP64 roofline."""
+    import paper_1004_0292_gb300 as ss
+    for _ in range(args.warmup):
+        step(basis=0)
+    times, counts, plain, _ = timed_steps(step, flush, stream, args.steps, basis=0)
     ms, pairs = reduce_job(float(sum(times)), float(sum(counts)), world, "cuda")
+    ss.set_kernel_timing(True)
+    _, _, stats, _ = timed_steps(step, flush, stream, KERNEL_TIMING_STEPS, basis=0)
+    ss.set_kernel_timing(False)
     ms_upd = sum(s["ms_k_update"] for s in stats)
     units = sum(s["timed_shift_updates"] for s in stats) * n
     it = max(1, sum(s["launches_update"] for s in stats))
     tf = UPDATE_FLOP_PER_UNIT * units / (ms_upd / 1e3) / 1e12 if ms_upd > 0 else None
-    return {"value": pairs / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / args.steps, "basis": stats[-1]["basis"],
-            "phase_ms": {"cg": stats[-1]["ms_cg"], "moments": stats[-1]["ms_moments"], "rr": stats[-1]["ms_rr"]},
-            "cg_us_per_iteration": 1e3 * stats[-1]["ms_cg"] / max(1, stats[-1]["iterations"]),
+    return {"value": pairs / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / args.steps, "basis": plain[-1]["basis"],
+            "phase_ms": {"cg": plain[-1]["ms_cg"], "moments": plain[-1]["ms_moments"], "rr": plain[-1]["ms_rr"]},
+            "cg_us_per_iteration": 1e3 * plain[-1]["ms_cg"] / max(1, plain[-1]["iterations"]),
             "update_kernel": {"kernel": "cg_update_pf_kernel (fused multi-shift update, FP64)",
                               "achieved_tflops": tf, "frac_fp64_peak": tf / FP64_PEAK_TFLOPS if tf else None,
                               "avg_launch_us": 1e3 * ms_upd / it, "traffic": UPDATE_FP64_TRAFFIC_ALL_LIVE,

@@ -123,10 +123,12 @@ typedef struct {
                              coefficients).  0: y_j and p-hat_j are updated
                              every iteration.  Other precisions always update */
   double basis_max_bytes; /* device memory the stored residuals may take; 0 =
-                             half of the free device memory when the solve
-                             starts.  A solve that reaches it forms y_j and
-                             p-hat_j from the stored residuals and continues
-                             with the per-iteration updates                    */
+                             sixteen times what the shift vectors would take
+                             (32 N L n bytes: up to 32 N iterations) or 4 GiB
+                             if more, at most half the free device memory.  A solve that
+                             reaches it forms y_j and p-hat_j from the stored
+                             residuals and continues with the per-iteration
+                             updates (the same eigenpairs, other rounding)     */
 } ssqcd_opts;
 
 /* Counters of one solve.  Times are device milliseconds between CUDA events. */

@@ -775,7 +775,8 @@ extern "C" int ssqcd_ss_solve(ssqcd_lattice lat, const double interval[2], int N
   std::vector<int> iters((size_t)P.NU * L);
   s1 = shifted_cg_solve(lat, P.NU, P.zu.data(), L, vd.as<double2>(), P.o.sigma, P.o.tol, P.o.max_iter,
                         lat->precision, P.o.reliable_every,
-                        basis_cap_for(lat->precision, P.o.basis, P.o.basis_max_bytes), yd, &kb, iters.data(), &cg);
+                        basis_cap_for(lat->precision, P.o.basis, P.o.basis_max_bytes, 12LL * lat->g.V, P.NU, L), yd, &kb,
+                        iters.data(), &cg);
   fill_cg_stats(cg, iters, &res->stats);
   *out = res;  // a result handle even on failure, so its stats can be read
   if (s1 != SSQCD_OK) return s1;
@@ -798,7 +799,8 @@ extern "C" int ssqcd_ss_moments(ssqcd_lattice lat, const double interval[2], int
   std::vector<int> iters((size_t)P.NU * L);
   SS_TRY(shifted_cg_solve(lat, P.NU, P.zu.data(), L, vd.as<double2>(), P.o.sigma, P.o.tol, P.o.max_iter,
                           lat->precision, P.o.reliable_every,
-                          basis_cap_for(lat->precision, P.o.basis, P.o.basis_max_bytes), yd, &kb, iters.data(), &cg));
+                          basis_cap_for(lat->precision, P.o.basis, P.o.basis_max_bytes, 12LL * lat->g.V, P.NU, L), yd, &kb,
+                        iters.data(), &cg));
   SS_TRY(S.alloc(sizeof(double2) * n * P.MM * L));
   if (kb.S > 0)
     SS_TRY(basis_moments(kb, P.coefk[0].data(), P.MM, S.as<double2>(), scratch, st));
@@ -892,14 +894,13 @@ size_t estimate_request_bytes(ssqcd_lattice lat, const SolvePlan& P, double basi
   return std::max(cg, ex) + (64u << 20);
 }
 
-// Stored-residual cap of a request: opts.basis_max_bytes, else sixteen times
-// the memory of its shift vectors (2 x 16 B x n per quadrature point and
-// source: up to 32 N iterations), at most half the budget.
+// Stored-residual cap of a request: the one ss_solve would use (so that the
+// result is the same as solved alone); if the request does not fit the
+// budget with it, the update form (cap 0) when that fits.
 double request_basis_cap(ssqcd_lattice lat, const SolvePlan& P, size_t budget) {
-  if (basis_cap_for(lat->precision, P.o.basis, 1.0) == 0.0) return 0.0;
-  if (P.o.basis_max_bytes > 0.0) return P.o.basis_max_bytes;
-  const double shift = 32.0 * 12.0 * lat->g.V * (double)P.NU * P.L;
-  return std::min(16.0 * shift, 0.5 * (double)budget);
+  const double cap = basis_cap_for(lat->precision, P.o.basis, P.o.basis_max_bytes, 12LL * lat->g.V, P.NU, P.L);
+  if (cap > 0.0 && estimate_request_bytes(lat, P, cap) > budget) return 0.0;
+  return cap;
 }
 
 void request_fail(ssqcd_server_s* srv, ServerRequest& r, int status) {

@@ -229,8 +229,9 @@ class CgRunBase {
 int make_cg_run(ssqcd_lattice lat, int N, const double2* z_host, int L, const double2* v, double sigma, double tol,
                 int max_iter, int precision, int reliable_every, double basis_cap, cudaStream_t st,
                 std::unique_ptr<CgRunBase>* out);
-// the basis_cap of a solve from its options: 0 when the form does not apply
-double basis_cap_for(int precision, int basis, double basis_max_bytes);
+// the basis_cap of a solve from its options and size (n, N points, L
+// sources): 0 when the form does not apply
+double basis_cap_for(int precision, int basis, double basis_max_bytes, long long n, int N, int L);
 int shifted_cg_device(ssqcd_lattice lat, int N, const double2* z_host, int L, const double2* v,
                       double sigma, double tol, int max_iter, int precision, int reliable_every,
                       DevBuf& y, int* iters, double2* xi, ShiftedCGOut* out);

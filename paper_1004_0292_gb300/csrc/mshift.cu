@@ -108,6 +108,7 @@ struct Control {
   // residual slots
   char* const* tab;
   size_t blk_vec;
+  char** rptr;         // [2] slots r_k, r_{k+1} of the coming iteration (written by the last block of B)
 };
 
 constexpr int kUpdBlock = 256;
@@ -154,6 +155,18 @@ size_t basis_block_bytes(size_t vec_bytes, int NL, int L) {
 constexpr int kMaxShifts = 512;   // quadrature points per source
 constexpr int kMaxTotal = 1024;   // (source, point) pairs in one solve
 constexpr int kMaxSources = 64;
+
+// Programmatic dependent launch (Blackwell/Hopper griddepcontrol): the chain
+// kernels of the Krylov-basis loop are launched with programmatic stream
+// serialisation, so a kernel's launch and block scheduling overlap the tail
+// of its predecessor.  Every kernel waits for its predecessor grid to
+// complete (and its writes to be visible) before it reads anything the
+// predecessor wrote; a kernel launched without the attribute returns from
+// the wait at once.  A block signals its dependents once its main work is
+// done (a dependent grid starts only when every block has signalled or
+// exited, so it never takes the place of an unscheduled block).
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -234,6 +247,8 @@ __global__ void init_control_kernel(Control c, const double* __restrict__ vn2, i
 struct Stencil64 {
   static constexpr bool kThreadPerSite = false;
   static constexpr int kThreads = kStencilThreads;
+  static constexpr int kSites = kSitesPerBlock;
+  static constexpr int kShElems = 12 * 4 * kSitesPerBlock;
   static constexpr int kMinBlocks = 4;  // <= 128 registers (four 128-thread blocks per SM)
   const double2* __restrict__ u;
   __device__ __forceinline__ double run(const Geometry& g, const double2* __restrict__ p, double2* __restrict__ q,
@@ -259,12 +274,50 @@ struct Stencil64 {
   }
 };
 
+// FP64, balanced form (16 sites per block, spin halves in half-warps); used
+// by the solve loop
+struct Stencil64h {
+  static constexpr bool kThreadPerSite = false;
+  static constexpr int kThreads = kStencilThreads;
+  static constexpr int kSites = kSitesPerBlockH;
+  static constexpr int kShElems = 12 * 4 * kSitesPerBlockH;
+  static constexpr int kMinBlocks = 7;  // <= 72 registers: 7 blocks an SM (1064 >= the 1024 blocks of 8^4 x 4)
+  const double2* __restrict__ u;
+  __device__ __forceinline__ double run(const Geometry& g, const double2* __restrict__ p, double2* __restrict__ q,
+                                        double sigma, int, int, void* shm) const {
+    double2* sh = static_cast<double2*>(shm);
+    const int s0 = blockIdx.x * kSitesPerBlockH;
+    block_hops64h(Links64{u, g.V}, p, s0, g, sh);
+    // finish: 16 sites x 12 components, component-major so that a warp's
+    // stores are two 256-byte segments
+    double d = 0.0;
+    const double mk = -g.kappa;
+    for (int idx = threadIdx.x; idx < 12 * kSitesPerBlockH; idx += kThreads) {
+      const int comp = idx / kSitesPerBlockH, i = idx % kSitesPerBlockH;
+      const int s = s0 + i;
+      if (s >= g.V) continue;
+      const double2* e = sh + comp * 4 * kSitesPerBlockH + i;
+      double2 acc = cadd(cadd(e[0], e[kSitesPerBlockH]), cadd(e[2 * kSitesPerBlockH], e[3 * kSitesPerBlockH]));
+      const double sg = comp < 6 ? -1.0 : 1.0;
+      const double2 pv = p[comp * g.V + s];
+      double2 o;
+      o.x = fma(sg, fma(mk, acc.x, pv.x), sigma * pv.x);
+      o.y = fma(sg, fma(mk, acc.y, pv.y), sigma * pv.y);
+      q[comp * g.V + s] = o;
+      d = fma(pv.x, o.x, fma(pv.y, o.y, d));
+    }
+    return d;
+  }
+};
+
 // FP32 spinors (mixed precisions): one thread per site (memory-bound form)
 template <typename LK>
 struct Stencil32 {
   static constexpr int kThreads = kSiteThreads;
   static constexpr int kMinBlocks = 1;
   static constexpr bool kThreadPerSite = true;
+  static constexpr int kSites = kSiteThreads;
+  static constexpr int kShElems = 1;
   LK lk;
   __device__ __forceinline__ double run(const Geometry& g, const float2* __restrict__ p, float2* __restrict__ q,
                                         double sigma, int s, int, void*) const {
@@ -295,6 +348,8 @@ struct Stencil32 {
 struct StencilDF {
   static constexpr bool kThreadPerSite = false;
   static constexpr int kThreads = kStencilThreadsDF;
+  static constexpr int kSites = kSitesPerBlock;
+  static constexpr int kShElems = 12 * 4 * kSitesPerBlock;  // 8 x 6 x 32 float4
   static constexpr int kMinBlocks = 3;  // <= 85 registers; a 64-register cap (4 blocks) spilled and measured slower
   const float4* __restrict__ u;
   __device__ __forceinline__ double run(const Geometry& g, const float4* __restrict__ p, float4* __restrict__ q,
@@ -320,12 +375,13 @@ template <typename Op, typename V2>
 __global__ void __launch_bounds__(Op::kThreads, Op::kMinBlocks)
 cg_stencil_kernel(Control c, int L, int par, Geometry g, Op op, double sigma, const V2* __restrict__ p_all,
                   V2* __restrict__ q_all) {
+  pdl_wait();
   if (*c.err != 0 || *c.live_total == 0) {
     if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *c.ran = c.rec_ran[par] = 0;
     return;
   }
   constexpr int kWarps = Op::kThreads / 32;
-  __shared__ double2 sh[12 * 4 * 32];  // 24 KB: 12 x 4 x 32 double2 or 8 x 6 x 32 float4
+  __shared__ double2 sh[Op::kShElems];  // the op's reduction scratch
   __shared__ double sred[kWarps];
   __shared__ double sums[kMaxSources];
   __shared__ bool s_last;
@@ -335,7 +391,7 @@ cg_stencil_kernel(Control c, int L, int par, Geometry g, Op op, double sigma, co
   double d_pq = 0.0;
   if (c.live[l] != 0) {
     const int s = Op::kThreadPerSite ? blockIdx.x * Op::kThreads + (int)threadIdx.x
-                                     : blockIdx.x * kSitesPerBlock + lane;
+                                     : blockIdx.x * Op::kSites + lane;
     d_pq = op.run(g, p_all + (size_t)l * 12 * V, q_all + (size_t)l * 12 * V, sigma, s, w, sh);
   }
   d_pq = warp_sum(d_pq);
@@ -348,6 +404,7 @@ cg_stencil_kernel(Control c, int L, int par, Geometry g, Op op, double sigma, co
     if constexpr (kWarps == 8) t += (sred[4] + sred[5]) + (sred[6] + sred[7]);
     static_assert(kWarps == 4 || kWarps == 8, "four or eight warps");
     c.partial[(size_t)l * nbw + blockIdx.x] = t;
+    pdl_trigger();
     __threadfence();
     const unsigned ticket = atomicAdd(&c.done[0], 1u);
     s_last = ticket == gridDim.x * gridDim.y - 1;
@@ -405,29 +462,34 @@ __global__ void __launch_bounds__(kSeedBlock)
 cg_seed_kernel(Control c, int L, int N, int par, double tol2, const V2* __restrict__ r_in, V2* __restrict__ r_out,
                const V2* __restrict__ q, const V2* __restrict__ p, long long n, double rescale_below,
                double rescale_by) {
-  if (*c.ran == 0) return;
-  const int kb = c.tab != nullptr ? *c.seed_iters - 1 : 0;  // this iteration (Krylov-basis form)
-  if (c.tab != nullptr) {
-    r_in = basis_slot<V2>(c, kb, (long long)L * n);
-    r_out = basis_slot<V2>(c, kb + 1, (long long)L * n);
+  pdl_wait();
+  // the control words this block needs, loaded together (one round trip)
+  const int l = blockIdx.y;
+  const int ran = *c.ran, live_l = c.live[l];
+  const double alpha_l = c.alpha[l], scale_l = c.seed[l].scale, spad1_l = c.seed[l].pad[1];
+  if (c.tab != nullptr) {  // Krylov-basis form: this iteration's slots
+    r_in = reinterpret_cast<const V2*>(c.rptr[0]);
+    r_out = reinterpret_cast<V2*>(c.rptr[1]);
   }
+  if (ran == 0) return;
   __shared__ double sred[kSeedBlock / 32];
   __shared__ double sums[kMaxSources];
   __shared__ double s_scale[kMaxSources], s_beta[kMaxSources];
   __shared__ double2 s_a[kMaxTotal], s_b[kMaxTotal];
   __shared__ int s_flag[kMaxTotal];
   __shared__ bool s_last;
-  const int l = blockIdx.y;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int NL = N * L;
   if (w == kSeedBlock / 32 - 1) {
     const int nblk = gridDim.x * gridDim.y;
     for (int qi = blockIdx.y * gridDim.x + blockIdx.x + lane * nblk; qi < NL; qi += 32 * nblk) {
       const int ls = qi / N;
-      if (c.live[ls] == 0 || !c.act[qi]) continue;
+      // all loads first (independent addresses), then the test
+      const int lv = c.live[ls], ac = c.act[qi];
       const SeedState sd = c.seed[ls];
       const double alpha = c.alpha[ls];
       const double2 xc = c.xi_cur[qi], xp = c.xi_prev[qi], s = c.shift_s[qi];
+      if (lv == 0 || !ac) continue;
       const double ap = sd.alpha_prev, bp = sd.beta_prev;
       const double inv_c = 1.0 / (xc.x * xc.x + xc.y * xc.y);  // independent of the chain below
       // xi_{k+1} = xi_k xi_{k-1} alpha_{k-1} /
@@ -449,8 +511,8 @@ cg_seed_kernel(Control c, int L, int N, int par, double tol2, const V2* __restri
     }
   }
   double acc0 = 0.0, acc1 = 0.0;
-  if (c.live[l] != 0) {
-    const double alpha = c.alpha[l];
+  if (live_l != 0) {
+    const double alpha = alpha_l;
     const V2* rl = r_in + (long long)l * n;
     V2* ro = r_out + (long long)l * n;
     const V2* ql = q + (long long)l * n;
@@ -458,15 +520,15 @@ cg_seed_kernel(Control c, int L, int N, int par, double tol2, const V2* __restri
     // the rescales of r and p so far), for the reliable updates
     double2* xl = c.x != nullptr ? c.x + (long long)l * n : nullptr;
     const V2* pl = p + (long long)l * n;
-    const double ax = c.x != nullptr ? alpha / c.seed[l].pad[1] : 0.0;
+    const double ax = c.x != nullptr ? alpha / spad1_l : 0.0;
     using T = decltype(V2::x);
     const T af = (T)alpha;
-    const T sc = (T)c.seed[l].scale;  // rescale of r decided last iteration (exact power of two)
+    const T sc = (T)scale_l;  // rescale of r decided last iteration (exact power of two)
     const long long stride = (long long)gridDim.x * kSeedBlock;
     if constexpr (std::is_same<V2, float4>::value) {
       // float-float: r_out = s r_in - alpha q, ||r_out||^2 summed in float-float per thread
       const float2 naf = ff::split(-alpha);
-      const float scf = (float)c.seed[l].scale;
+      const float scf = (float)scale_l;
       float hs = 0.f, hl = 0.f;
       for (long long e = blockIdx.x * (long long)kSeedBlock + threadIdx.x; e < n; e += stride) {
         const float4 x1 = ff::caxpy(ff::cscale2(rl[e], scf), naf, ql[e]);
@@ -506,6 +568,7 @@ cg_seed_kernel(Control c, int L, int N, int par, double tol2, const V2* __restri
   if (threadIdx.x == 0) {
     const double t = ((sred[0] + sred[1]) + (sred[2] + sred[3])) + ((sred[4] + sred[5]) + (sred[6] + sred[7]));
     c.partial_rr[(size_t)l * nb + blockIdx.x] = t;
+    pdl_trigger();
     __threadfence();
     const unsigned ticket = atomicAdd(&c.done[1], 1u);
     s_last = ticket == gridDim.x * gridDim.y - 1;
@@ -513,7 +576,11 @@ cg_seed_kernel(Control c, int L, int N, int par, double tol2, const V2* __restri
   __syncthreads();
   if (!s_last) return;
   __threadfence();
+  const int kb = c.tab != nullptr ? *c.seed_iters - 1 : 0;  // this iteration (Krylov-basis form)
   for (int ls = w; ls < L; ls += kSeedBlock / 32) {
+    // the source's control words together with its partials
+    const double pad0 = c.seed[ls].pad[0], vn2 = c.vnorm2[ls];  // pad[0] holds 1 / rr_k
+    const int lv = c.live[ls];
     double a0 = 0.0, a1 = 0.0;
     int b = lane;
     for (; b + 32 < nb; b += 64) {
@@ -524,33 +591,39 @@ cg_seed_kernel(Control c, int L, int N, int par, double tol2, const V2* __restri
     const double a = warp_sum(a0 + a1);
     if (lane == 0) {
       sums[ls] = a;
-      const SeedState sd = c.seed[ls];
-      s_beta[ls] = a * sd.pad[0];  // pad[0] holds 1 / rr_k
-      s_scale[ls] = (c.live[ls] != 0 && a < rescale_below * c.vnorm2[ls] && a > 0.0) ? rescale_by : 1.0;
+      s_beta[ls] = a * pad0;
+      s_scale[ls] = (lv != 0 && a < rescale_below * vn2 && a > 0.0) ? rescale_by : 1.0;
     }
+  }
+  if (c.tab != nullptr && threadIdx.x == 0) {  // slots of the next iteration
+    const long long Ln = (long long)L * n;
+    c.rptr[0] = reinterpret_cast<char*>(basis_slot<V2>(c, kb + 1, Ln));
+    c.rptr[1] = reinterpret_cast<char*>(basis_slot<V2>(c, kb + 2, Ln));
   }
   __syncthreads();
   // per shift: coefficients and the freeze test from xi_{k+1}
   for (int qi = threadIdx.x; qi < NL; qi += blockDim.x) {
     const int ls = qi / N;
     int flag = 0;
-    if (c.live[ls] != 0 && c.act[qi]) {
-      const double alpha = c.alpha[ls];
+    // all loads first (independent addresses), then the test
+    const int lv = c.live[ls], ac = c.act[qi];
+    const double alpha = c.alpha[ls], vn2 = c.vnorm2[ls], spad1 = c.seed[ls].pad[1];
+    const double2 xn = __ldcg(c.xi_next + qi), ratio = __ldcg(c.ratio + qi), xc = c.xi_cur[qi];
+    if (lv != 0 && ac) {
       const double rr1 = sums[ls], beta = s_beta[ls];
       const double sc = s_scale[ls], inv_sc = sc == 1.0 ? 1.0 : 1.0 / rescale_by;
-      const double2 xn = __ldcg(c.xi_next + qi), ratio = __ldcg(c.ratio + qi), xc = c.xi_cur[qi];
       s_a[qi] = make_double2(alpha * xn.x, alpha * xn.y);
       s_b[qi] = make_double2(sc * beta * ratio.x, sc * beta * ratio.y);
       if (c.tab != nullptr) {
         basis_coef(c, kb, NL, 0)[qi] = s_a[qi];
         basis_coef(c, kb, NL, 1)[qi] = s_b[qi];
       }
-      const bool live = (xn.x * xn.x + xn.y * xn.y) * rr1 > tol2 * c.vnorm2[ls];
+      const bool live = (xn.x * xn.x + xn.y * xn.y) * rr1 > tol2 * vn2;
       flag = live ? 2 : 1;
       c.xi_prev[qi] = make_double2(xc.x * inv_sc, xc.y * inv_sc);
       // a freezing shift leaves its unscaled xi (xi_{k+1} S, S = product of
       // the scales so far); a live one keeps it in the scale of r
-      const double S = live ? inv_sc : c.seed[ls].pad[1];
+      const double S = live ? inv_sc : spad1;
       c.xi_cur[qi] = make_double2(xn.x * S, xn.y * S);
       c.act[qi] = live ? 1 : 0;
       c.iters[qi] += 1;
@@ -606,22 +679,24 @@ cg_seed_kernel(Control c, int L, int N, int par, double tol2, const V2* __restri
 template <typename VR>
 __global__ void __launch_bounds__(kUpdBlock)
 cg_seed_p_kernel(Control c, const VR* __restrict__ r, VR* __restrict__ p, long long n) {
-  if (*c.ran == 0) return;
+  pdl_wait();
   const int l = blockIdx.y;
-  if (c.live[l] == 0) return;
-  if (c.tab != nullptr) r = basis_slot<VR>(c, *c.seed_iters, (long long)gridDim.y * n);  // slot k + 1
+  const int ran = *c.ran, live_l = c.live[l];
+  const double scale_l = c.seed[l].scale, beta_l = c.seed[l].beta;
+  if (c.tab != nullptr) r = reinterpret_cast<const VR*>(c.rptr[0]);  // r_{k+1}: kernel B advanced the slots
+  if (ran == 0 || live_l == 0) return;
   const VR* rl = r + (long long)l * n;
   VR* pl = p + (long long)l * n;
   if constexpr (std::is_same<VR, float4>::value) {  // float-float
-    const float scf = (float)c.seed[l].scale;
-    const float2 beta = ff::split(c.seed[l].scale * c.seed[l].beta);
+    const float scf = (float)scale_l;
+    const float2 beta = ff::split(scale_l * beta_l);
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
          e += (long long)gridDim.x * blockDim.x)
       pl[e] = ff::caxpy(ff::cscale2(rl[e], scf), beta, pl[e]);
   } else {
     using TR = decltype(VR::x);
-    const TR sc = (TR)c.seed[l].scale;
-    const TR beta = (TR)(c.seed[l].scale * c.seed[l].beta);
+    const TR sc = (TR)scale_l;
+    const TR beta = (TR)(scale_l * beta_l);
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
          e += (long long)gridDim.x * blockDim.x) {
       const VR x = rl[e];
@@ -631,6 +706,7 @@ cg_seed_p_kernel(Control c, const VR* __restrict__ r, VR* __restrict__ p, long l
       pl[e] = pe;
     }
   }
+  pdl_trigger();
 }
 
 // ---- C. fused multi-shift update -------------------------------------------------------
@@ -1337,24 +1413,53 @@ int launch_combine(char* const* tab, long long n, int L, const double2* C, int O
 // as a node attribute when captured into a graph).  The main chain A, B, P
 // runs at the device's greatest priority so that its blocks are dispatched
 // ahead of the remaining blocks of the concurrent shift update C.
+// pdl: programmatic dependent launch on the previous kernel of the stream.
 template <typename... KArgs, typename... Args>
 void launch_prio_smem(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, int prio,
-                      Args&&... args) {
+                      bool pdl, Args&&... args) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = grid;
   cfg.blockDim = block;
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
-  cudaLaunchAttribute attr[1];
+  cudaLaunchAttribute attr[2];
   attr[0].id = cudaLaunchAttributePriority;
   attr[0].val.priority = prio;
+  attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[1].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = pdl ? 2 : 1;
   cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
 }
 template <typename... KArgs, typename... Args>
 void launch_prio(void (*kern)(KArgs...), dim3 grid, dim3 block, cudaStream_t st, int prio, Args&&... args) {
-  launch_prio_smem(kern, grid, block, 0, st, prio, std::forward<Args>(args)...);
+  launch_prio_smem(kern, grid, block, 0, st, prio, false, std::forward<Args>(args)...);
+}
+template <typename... KArgs, typename... Args>
+void launch_chain(void (*kern)(KArgs...), dim3 grid, dim3 block, cudaStream_t st, int prio, bool pdl,
+                  Args&&... args) {
+  launch_prio_smem(kern, grid, block, 0, st, prio, pdl, std::forward<Args>(args)...);
+}
+
+// Programmatic dependent launch of the chain kernels in the Krylov-basis
+// loop: off by default (measured 59.7 us per iteration without, 65.6 with,
+// on the 8^4 x 4 workload); SSQCD_PDL=1 turns it on for comparison runs.
+bool use_pdl() {
+  static const bool v = [] {
+    const char* e = std::getenv("SSQCD_PDL");
+    return e && e[0] == '1';
+  }();
+  return v;
+}
+
+// The FP64 stencil of the solve loop: the balanced 16-site form (default) or
+// the 32-site form (SSQCD_STENCIL_SITES=32, for comparison runs).
+bool balanced_stencil() {
+  static const bool v = [] {
+    const char* e = std::getenv("SSQCD_STENCIL_SITES");
+    return !(e && std::atoi(e) == 32);
+  }();
+  return v;
 }
 
 int seed_blocks(long long n, int L) {
@@ -1450,8 +1555,8 @@ template <typename RT>
 void launch_update_tma(int nblocks, int L, cudaStream_t st, int prio, const Control& c, int N, int par, const RT* r,
                        float4* y, float4* ph, long long n) {
   const int nchunks = (int)((n + kTmaCh - 1) / kTmaCh);
-  launch_prio_smem(cg_update_tma_kernel<RT>, dim3(nblocks), dim3(kTmaThreads), tma_smem_bytes(N * L, L), st, prio, c,
-                   N, L, par, r, y, ph, n, nchunks, update_stall_test());
+  launch_prio_smem(cg_update_tma_kernel<RT>, dim3(nblocks), dim3(kTmaThreads), tma_smem_bytes(N * L, L), st, prio,
+                   false, c, N, L, par, r, y, ph, n, nchunks, update_stall_test());
 }
 
 int update_blocks(long long n, int L, int ept) {
@@ -1540,7 +1645,9 @@ class CgRun final : public CgRunBase {
     n_ = 12LL * g.V;
     const long long n = n_;
     const int NL = N * L;
-    nbw_ = kFP32 ? (g.V + kSiteThreads - 1) / kSiteThreads : wilson_blocks(g);
+    nbw_ = kFP32 ? (g.V + kSiteThreads - 1) / kSiteThreads
+           : (kSeedDF || !balanced_stencil()) ? wilson_blocks(g)
+                                              : (g.V + kSitesPerBlockH - 1) / kSitesPerBlockH;
     nbs_ = seed_blocks(n, L);
     ept_ = update_epts(kShift32 || kShiftDF);
     nbu_ = update_blocks(n, L, ept_);
@@ -1560,8 +1667,8 @@ class CgRun final : public CgRunBase {
       blk_bytes_ = basis_block_bytes(blk_vec_, NL, L);
       tab_cap_ = (max_iter + kChunk) / kBasisBlock + 2;
       SS_TRY(tab_.alloc(sizeof(char*) * tab_cap_));
-      SS_CUDA(cudaMallocHost(&h_tab_, sizeof(char*) * tab_cap_));
-      SS_TRY(ensure_blocks(kChunk));
+      SS_CUDA(cudaMallocHost(&h_tab_, sizeof(char*) * (tab_cap_ + 2)));  // + the first two slot pointers
+      SS_TRY(ensure_blocks(kChunk + 1));
       if (!basis_) return fail(SSQCD_ERR_OOM, "stored residuals: the memory cap is below two blocks");
     } else {
       SS_TRY(alloc_update_vectors());
@@ -1588,7 +1695,7 @@ class CgRun final : public CgRunBase {
                  o_la = take(sizeof(double2) * 2 * NL), o_lb = take(sizeof(double2) * 2 * NL),
                  o_lsc = take(sizeof(double) * 2 * L), o_part = take(sizeof(double) * (size_t)nbw_ * L),
                  o_prr = take(sizeof(double) * (size_t)nbs_ * L), o_vp = take(sizeof(double) * (size_t)nbs_ * L),
-                 o_vn2 = take(sizeof(double) * L);
+                 o_vn2 = take(sizeof(double) * L), o_rptr = take(sizeof(char*) * 2);
     SS_TRY(ctl_.alloc(off));
     char* base = ctl_.as<char>();
     Control& c = c_;
@@ -1620,6 +1727,12 @@ class CgRun final : public CgRunBase {
     c.x = x_.p != nullptr ? x_.as<double2>() : nullptr;
     c.tab = basis_ ? tab_.as<char*>() : nullptr;
     c.blk_vec = blk_vec_;
+    c.rptr = reinterpret_cast<char**>(base + o_rptr);
+    if (basis_) {  // slots 0 and 1 for the first iteration
+      h_tab_[tab_cap_] = h_tab_[0];
+      h_tab_[tab_cap_ + 1] = h_tab_[0] + sizeof(VR) * (size_t)L * n;
+      SS_CUDA(cudaMemcpyAsync(c.rptr, h_tab_ + tab_cap_, sizeof(char*) * 2, cudaMemcpyHostToDevice, st_));
+    }
     double* vn_part = reinterpret_cast<double*>(base + o_vp);
     double* vn2 = reinterpret_cast<double*>(base + o_vn2);
 
@@ -1681,7 +1794,7 @@ class CgRun final : public CgRunBase {
     AllocStream scope(st_);
     const int chunk = std::min(kChunk, max_iter_ - k_);
     if (chunk <= 0) return SSQCD_OK;
-    if (basis_) SS_TRY(ensure_blocks(k_ + chunk));  // may switch to the update form
+    if (basis_) SS_TRY(ensure_blocks(k_ + chunk + 1));  // kernel B of the last iteration looks one slot ahead
     const int slot = (int)(launched_chunks_ % kInFlight);
     ChunkInfo info;
     info.k_start = k_;
@@ -2007,26 +2120,29 @@ class CgRun final : public CgRunBase {
     mark(it, 0, st);
     if constexpr (kFP32) {
       if (lat_->precision == SSQCD_MIXED)
-        launch_prio(cg_stencil_kernel<Stencil32<LinksF16>, VR>, grid_a, kSiteThreads, st, prio_hi_, c, L, par, g,
+        launch_chain(cg_stencil_kernel<Stencil32<LinksF16>, VR>, grid_a, kSiteThreads, st, prio_hi_, basis_ && use_pdl(), c, L, par, g,
                     Stencil32<LinksF16>{LinksF16{lat_->u16.as<uint2>(), g.V}}, sigma_, p_.as<VR>(), q_.as<VR>());
       else
-        launch_prio(cg_stencil_kernel<Stencil32<LinksF32>, VR>, grid_a, kSiteThreads, st, prio_hi_, c, L, par, g,
+        launch_chain(cg_stencil_kernel<Stencil32<LinksF32>, VR>, grid_a, kSiteThreads, st, prio_hi_, basis_ && use_pdl(), c, L, par, g,
                     Stencil32<LinksF32>{LinksF32{lat_->u32.as<float4>(), g.V}}, sigma_, p_.as<VR>(), q_.as<VR>());
     } else if constexpr (kSeedDF) {
-      launch_prio(cg_stencil_kernel<StencilDF, VR>, grid_a, StencilDF::kThreads, st, prio_hi_, c, L, par, g,
+      launch_chain(cg_stencil_kernel<StencilDF, VR>, grid_a, StencilDF::kThreads, st, prio_hi_, basis_ && use_pdl(), c, L, par, g,
                   StencilDF{lat_->udf.as<float4>()}, sigma_, p_.as<VR>(), q_.as<VR>());
+    } else if (balanced_stencil()) {
+      launch_chain(cg_stencil_kernel<Stencil64h, VR>, grid_a, kStencilThreads, st, prio_hi_, basis_ && use_pdl(), c, L, par, g,
+                  Stencil64h{lat_->u64.as<double2>()}, sigma_, p_.as<VR>(), q_.as<VR>());
     } else {
-      launch_prio(cg_stencil_kernel<Stencil64, VR>, grid_a, kStencilThreads, st, prio_hi_, c, L, par, g,
+      launch_chain(cg_stencil_kernel<Stencil64, VR>, grid_a, kStencilThreads, st, prio_hi_, basis_ && use_pdl(), c, L, par, g,
                   Stencil64{lat_->u64.as<double2>()}, sigma_, p_.as<VR>(), q_.as<VR>());
     }
     mark(it, 1, st);
     mark(it, 2, st);
-    launch_prio(cg_seed_kernel<VR>, grid_b, kSeedBlock, st, prio_hi_, c, L, N, par, tol2_, r_in, r_out, q_.as<VR>(),
+    launch_chain(cg_seed_kernel<VR>, grid_b, kSeedBlock, st, prio_hi_, basis_ && use_pdl(), c, L, N, par, tol2_, r_in, r_out, q_.as<VR>(),
                 p_.as<VR>(), n, rescale_below_, rescale_by_);
     mark(it, 3, st);
     cudaEventRecord(ev_[it], st);
     mark(it, 6, st);
-    launch_prio(cg_seed_p_kernel<VR>, grid_p, kUpdBlock, st, prio_hi_, c, r_out, p_.as<VR>(), n);
+    launch_chain(cg_seed_p_kernel<VR>, grid_p, kUpdBlock, st, prio_hi_, basis_ && use_pdl(), c, r_out, p_.as<VR>(), n);
     mark(it, 7, st);
     if (basis_) {  // no shift-vector update
       mark(it, 4, st);
@@ -2178,12 +2294,18 @@ int shifted_cg_solve(ssqcd_lattice lat, int N, const double2* z_host, int L, con
   return status;
 }
 
-double basis_cap_for(int precision, int basis, double basis_max_bytes) {
+double basis_cap_for(int precision, int basis, double basis_max_bytes, long long n, int N, int L) {
   if (basis == 0 || !(precision == SSQCD_FP64 || precision == SSQCD_DF)) return 0.0;
   if (basis_max_bytes > 0.0) return basis_max_bytes;
+  // sixteen times the memory of the shift vectors the update form would
+  // hold (y and p-hat, 16 B a complex element: 32 N L n bytes), i.e. up to
+  // 32 N iterations, and at least 4 GiB; a function of the problem only, so
+  // that a solve makes the same choice (and the same arithmetic) wherever it
+  // runs, unless the device has less than twice that free
+  const double cap = std::max(16.0 * 32.0 * (double)n * N * L, 4.0 * (1ull << 30));
   size_t free_b = 0, total_b = 0;
   if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) return 0.0;
-  return 0.5 * (double)free_b;
+  return std::min(cap, 0.5 * (double)free_b);
 }
 
 void KrylovBasis::release() {

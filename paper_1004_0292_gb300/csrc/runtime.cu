@@ -45,12 +45,35 @@ AllocStream::~AllocStream() {
   t_alloc_on = prev_on_;
 }
 
+namespace {
+// The stream-ordered allocations come from the device's default memory pool.
+// By default the pool hands its unused memory back to the driver at every
+// synchronisation, so each solve would map its gigabytes of stored
+// residuals afresh; keeping the freed memory in the pool (release threshold
+// at the maximum, once per device) makes the next solve's allocations reuse
+// it.  The setting lives in this process's context only.
+void keep_pool_memory() {
+  static std::atomic<unsigned long long> done_mask{0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev >= 64) return;
+  const unsigned long long bit = 1ull << dev;
+  if (done_mask.fetch_or(bit) & bit) return;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    unsigned long long thr = ~0ull;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+  (void)cudaGetLastError();
+}
+}  // namespace
+
 int DevBuf::alloc(size_t nbytes) {
   if (p && bytes >= nbytes) return SSQCD_OK;
   release();
   if (nbytes == 0) return SSQCD_OK;
   async = t_alloc_on;
   stream = t_alloc_stream;
+  if (async) keep_pool_memory();
   cudaError_t e = async ? cudaMallocAsync(&p, nbytes, stream) : cudaMalloc(&p, nbytes);
   if (e != cudaSuccess) {
     p = nullptr;

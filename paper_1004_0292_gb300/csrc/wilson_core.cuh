@@ -418,6 +418,121 @@ __device__ __forceinline__ void block_hops64(const Links64& lk, const double2* _
   reduce_dirs(acc, sh, acc_out);
 }
 
+// ---- FP64, balanced form: 16 sites per block, spin halves split ---------------------
+// The FP64 stencil is bound by the FP64 pipe.  With 32 sites per block
+// (above) an 8^4 lattice with four right-hand sides is 512 blocks, 3.4 per
+// SM: the SMs holding four blocks set the time and the others idle ~25% of
+// it.  Here a block covers 16 sites with 4 warps (warp w: direction w, both
+// hops); the half-warp h = lane / 16 computes spin row h of the projected
+// half spinor (h_r = psi_r -+ (B psi_l)_r) and its link product wv_r, which
+// feeds upper output spin r and one lower output spin 2 + t(r) (B^H is a
+// signed permutation).  No FP64 work is duplicated: the two halves share
+// only the link loads (same addresses in one warp instruction), and each
+// thread keeps 6 complex accumulators instead of 12, so the block fits 64
+// registers a thread and 8 blocks an SM: 1024 blocks in one wave, 6.7 per SM.
+// The per-lane differences (which spin components, which unit +-1, +-i of
+// B and B^H) are applied with selects and sign-bit flips on the integer
+// pipes, so the warp never diverges and the FP64 instruction count per
+// site is the same as above.
+constexpr int kSitesPerBlockH = 16;
+constexpr unsigned long long kSignBit = 0x8000000000000000ull;
+
+// multiplication by the unit `code` (+1, -1, +i, -i) with an extra sign flip
+// of both parts (neg): selects and integer xors only
+__device__ __forceinline__ double2 unit_apply(double2 z, int code, unsigned long long neg) {
+  const bool swap = code >= PI;
+  const unsigned long long mx = ((code == M1 || code == PI) ? kSignBit : 0ull) ^ neg;
+  const unsigned long long my = ((code == M1 || code == MI) ? kSignBit : 0ull) ^ neg;
+  const double a = swap ? z.y : z.x, b = swap ? z.x : z.y;
+  return make_double2(__longlong_as_double(__double_as_longlong(a) ^ mx),
+                      __longlong_as_double(__double_as_longlong(b) ^ my));
+}
+__device__ __forceinline__ double2 flip(double2 z, unsigned long long neg) {
+  return make_double2(__longlong_as_double(__double_as_longlong(z.x) ^ neg),
+                      __longlong_as_double(__double_as_longlong(z.y) ^ neg));
+}
+
+// One hop (forward: DIR = +1, U_mu(x) psi(x + mu), h = psi_u - B psi_l;
+// backward: U_mu(x - mu)^H psi(x - mu), h = psi_u + B psi_l) for spin row r
+// of site s; adds wv_r to up[] and -+ hcode B^H-row t to lo[].
+template <int MU, int DIR>
+__device__ __forceinline__ void hop_half64(const Links64& lk, const double2* __restrict__ in, int s, const Coords& c,
+                                           const Geometry& g, int r, double2 (&up)[3], double2 (&lo)[3]) {
+  using S = Spin<MU>;
+  const int V = g.V;
+  bool w;
+  const int nb = neighbour<MU, DIR>(s, c, g, w);
+  const int bcol = r ? S::bcol1 : S::bcol0;
+  const int bcode = r ? S::bcode1 : S::bcode0;
+  const int t = (r == S::hcol0) ? 0 : 1;
+  const int hcode = t ? S::hcode1 : S::hcode0;
+  // forward subtracts B psi_l and B^H wv; antiperiodic wrap negates h
+  const unsigned long long nproj = DIR > 0 ? kSignBit : 0ull;
+  const unsigned long long nwrap = (MU == 3 && w && g.bc_t < 0) ? kSignBit : 0ull;
+  const unsigned long long nrec = DIR > 0 ? kSignBit : 0ull;
+  double2 h[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const double2 u = __ldg(in + (r * 3 + a) * V + nb);
+    const double2 l = unit_apply(__ldg(in + ((2 + bcol) * 3 + a) * V + nb), bcode, nproj);
+    h[a] = flip(make_double2(u.x + l.x, u.y + l.y), nwrap);
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    double2 tv;
+    if (DIR > 0) {
+      const double2 u0 = lk.get(MU, a, 0, s), u1 = lk.get(MU, a, 1, s), u2 = lk.get(MU, a, 2, s);
+      tv = cmul(u0, h[0]);
+      cmac(tv, u1, h[1]);
+      cmac(tv, u2, h[2]);
+    } else {
+      const double2 u0 = lk.get(MU, 0, a, nb), u1 = lk.get(MU, 1, a, nb), u2 = lk.get(MU, 2, a, nb);
+      tv = cmul_conj(u0, h[0]);
+      cmac_conj(tv, u1, h[1]);
+      cmac_conj(tv, u2, h[2]);
+    }
+    up[a] = cadd(up[a], tv);
+    lo[a] = cadd(lo[a], unit_apply(tv, hcode, nrec));
+  }
+}
+
+template <int MU>
+__device__ __forceinline__ void hop_dir_half64(const Links64& lk, const double2* __restrict__ in, int s,
+                                               const Geometry& g, int r, double2* sh, int i) {
+  double2 up[3], lo[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) up[a] = lo[a] = make_double2(0.0, 0.0);
+  if (s < g.V) {
+    const Coords c = site_coords(s, g);
+    hop_half64<MU, +1>(lk, in, s, c, g, r, up, lo);
+    hop_half64<MU, -1>(lk, in, s, c, g, r, up, lo);
+  }
+  using S = Spin<MU>;
+  const int t = (r == S::hcol0) ? 0 : 1;
+  // sh layout [comp 12][dir 4][site 16]
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    sh[((r * 3 + a) * 4 + MU) * kSitesPerBlockH + i] = up[a];
+    sh[(((2 + t) * 3 + a) * 4 + MU) * kSitesPerBlockH + i] = lo[a];
+  }
+}
+
+// Block of 128 threads: sites s0 .. s0 + 15 of one rhs; on return (after the
+// barrier) sh holds the four directions' sums of every component.
+__device__ __forceinline__ void block_hops64h(const Links64& lk, const double2* __restrict__ in, int s0,
+                                              const Geometry& g, double2* sh) {
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i = lane & (kSitesPerBlockH - 1), r = lane >> 4;
+  const int s = s0 + i;
+  switch (w) {
+    case 0: hop_dir_half64<0>(lk, in, s, g, r, sh, i); break;
+    case 1: hop_dir_half64<1>(lk, in, s, g, r, sh, i); break;
+    case 2: hop_dir_half64<2>(lk, in, s, g, r, sh, i); break;
+    default: hop_dir_half64<3>(lk, in, s, g, r, sh, i); break;
+  }
+  __syncthreads();
+}
+
 // ---- FP32: one thread per site ------------------------------------------------------
 // For the memory-bound FP32 stencil a thread applies all eight hops of its
 // site and keeps the twelve output components in registers: no cross-warp
