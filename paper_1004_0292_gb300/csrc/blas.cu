@@ -249,93 +249,188 @@ __global__ void f32_to_f64_kernel(const float2* __restrict__ in, double2* __rest
 }
 
 
-// ---- classical Gram-Schmidt with one re-orthogonalisation pass (CGS2) ----
-// Column j of the basis: h = Q[0:j]^H v; v -= Q[0:j] h (twice); R[0:j, j]
-// accumulates both h; R[j, j] = ||v||; Q_j = v / ||v||.
-constexpr int kPC = 8;  // basis vectors per thread in the projection kernel
+// ---- classical Gram-Schmidt with one re-orthogonalisation pass (CGS2), three
+// fused launches per column ------------------------------------------------------
+// The steps of column j (j >= 1), each one launch over all elements whose
+// last block (ticket) reduces the block partials in block order:
+//   kSubProj : v -= Q[0:j] h          then partials of h = Q[0:j]^H v  (pass 2)
+//   kSubNorm : v -= Q[0:j] h          then partials of ||v||^2
+//   kScale   : v *= 1 / ||v||         then, for column j + 1 (w): partials of
+//              h = Q[0:j+1]^H w and of ||w||^2 (the start of its pass 1; the
+//              new Q_j enters from registers)
+// (column 0 starts with a kStart launch: ||Q_0||^2 only).  R[a][j] gathers
+// both passes' h; R[j][j] = ||v||; a column whose norm fell below 1e-15 of
+// the original is dependent and becomes zero (R[j][j] = 0).  Per thread:
+// one element (the grid covers n), the projections in tiles of kPT columns
+// reduced by warp shuffles and one pass over the warps.
+enum CgsMode : int { kStart = 0, kSubProj = 1, kSubNorm = 2, kScale = 3 };
 
-// partial[(a) * nb + blk] = sum over block blk's elements of conj(Q_a) v
+// Warp sums of 16 values at once by halving exchanges: at the step with
+// offset O a lane keeps one half of its values and adds the partner's copy of
+// that half, so the four steps take 8 + 4 + 2 + 1 additions and one more
+// pairs the lanes: 16 FP64 additions a lane instead of 16 x 5 for separate
+// shuffle trees (FP64 issues at 1/64 of the FP32 rate here).  On return lane
+// L holds the warp total of value (L >> 1) & 15.
+template <int O, int HALF>
+__device__ __forceinline__ void halve_step(double (&v)[16], int lane) {
+  const bool up = (lane & O) != 0;
+#pragma unroll
+  for (int i = 0; i < HALF; ++i) {
+    const double send = up ? v[i] : v[i + HALF];
+    const double keep = up ? v[i + HALF] : v[i];
+    v[i] = keep + __shfl_xor_sync(0xffffffffu, send, O);
+  }
+}
+__device__ __forceinline__ double warp_reduce16(double (&v)[16]) {
+  const int lane = threadIdx.x & 31;
+  halve_step<16, 8>(v, lane);
+  halve_step<8, 4>(v, lane);
+  halve_step<4, 2>(v, lane);
+  halve_step<2, 1>(v, lane);
+  return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+}
+constexpr int kPT = 8;
+constexpr int kCgsMaxCols = 128;
+
+struct CgsState {
+  double2* partial;   // [kCgsMaxCols][nb]
+  double* npart;      // [nb]
+  double2* h;         // [kCgsMaxCols]
+  double* scal;       // [0] ||v_orig||^2 of the current column, [1] ||v||^2, [2] 1 / ||v||
+  unsigned* ticket;
+};
+
 __global__ void __launch_bounds__(kRedBlock)
-proj_partial_kernel(const double2* __restrict__ Q, int j, const double2* __restrict__ v, long long n,
-                    double2* __restrict__ partial) {
-  const int a0 = blockIdx.y * kPC;
-  double2 acc[kPC];
+cgs2_step_kernel(CgsState st, double2* __restrict__ Q, long long n, int chunk, int m, int j, int mode,
+                 double2* __restrict__ R) {
+  __shared__ double2 s_h[kCgsMaxCols];
+  __shared__ double s_red[kRedBlock / 32][2 * kPT];
+  __shared__ double s_nred[kRedBlock / 32];
+  __shared__ bool s_last;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int nb = gridDim.x;
+  const long long e = blockIdx.x * (long long)chunk + threadIdx.x;
+  const bool in = (int)threadIdx.x < chunk && e < n;
+  // 1. the update of column j
+  double2 x = make_double2(0.0, 0.0);
+  if (mode == kSubProj || mode == kSubNorm) {
+    for (int a = threadIdx.x; a < j; a += kRedBlock) s_h[a] = st.h[a];
+    __syncthreads();
+    if (in) {
+      x = Q[(long long)j * n + e];
+      // kPT loads in flight at a time; the subtractions in column order
+      for (int a0 = 0; a0 < j; a0 += kPT) {
+        double2 q[kPT];
 #pragma unroll
-  for (int c = 0; c < kPC; ++c) acc[c] = make_double2(0.0, 0.0);
-  for (long long e = blockIdx.x * (long long)kRedBlock + threadIdx.x; e < n; e += (long long)gridDim.x * kRedBlock) {
-    const double2 x = v[e];
+        for (int c = 0; c < kPT; ++c) q[c] = a0 + c < j ? Q[(long long)(a0 + c) * n + e] : make_double2(0.0, 0.0);
 #pragma unroll
-    for (int c = 0; c < kPC; ++c) {
-      if (a0 + c < j) {
-        const double2 q = Q[(long long)(a0 + c) * n + e];
-        acc[c].x = fma(q.x, x.x, fma(q.y, x.y, acc[c].x));
-        acc[c].y = fma(q.x, x.y, fma(-q.y, x.x, acc[c].y));
+        for (int c = 0; c < kPT; ++c) {
+          if (a0 + c < j) {
+            const double2 h = s_h[a0 + c];
+            x.x -= q[c].x * h.x - q[c].y * h.y;
+            x.y -= q[c].x * h.y + q[c].y * h.x;
+          }
+        }
+      }
+      Q[(long long)j * n + e] = x;
+    }
+  } else if (mode == kScale) {
+    const double inv = st.scal[2];
+    if (in) {
+      x = Q[(long long)j * n + e];
+      x.x *= inv;
+      x.y *= inv;
+      Q[(long long)j * n + e] = x;
+    }
+  }
+  // 2. partials: of h for column jp against its first np columns, of a norm
+  const int jp = mode == kScale ? j + 1 : j;  // the column being projected
+  const int np = mode == kSubNorm ? 0 : (mode == kStart ? 0 : jp);
+  const bool want_norm = mode != kSubProj;
+  if (mode == kScale && jp >= m) return;  // last column: scaling only
+  double2 y = x;                           // the vector the partials are of
+  if (mode == kScale) y = in ? Q[(long long)jp * n + e] : make_double2(0.0, 0.0);
+  else if (mode == kStart) y = in ? Q[(long long)j * n + e] : make_double2(0.0, 0.0);
+  for (int a0 = 0; a0 < np; a0 += kPT) {
+    double acc[2 * kPT];  // re, im of conj(Q_a) y for kPT columns
+#pragma unroll
+    for (int c = 0; c < kPT; ++c) {
+      acc[2 * c] = acc[2 * c + 1] = 0.0;
+      const int a = a0 + c;
+      if (in && a < np) {
+        const double2 q = (mode == kScale && a == j) ? x : Q[(long long)a * n + e];
+        acc[2 * c] = fma(q.x, y.x, q.y * y.y);
+        acc[2 * c + 1] = fma(q.x, y.y, -q.y * y.x);
+      }
+    }
+    const double t = warp_reduce16(acc);
+    if ((lane & 1) == 0) s_red[w][lane >> 1] = t;
+    __syncthreads();
+    if (threadIdx.x < 2 * kPT && a0 + (int)threadIdx.x / 2 < np) {
+      double u = s_red[0][threadIdx.x];
+      for (int ww = 1; ww < kRedBlock / 32; ++ww) u += s_red[ww][threadIdx.x];
+      reinterpret_cast<double*>(st.partial)[2 * ((long long)(a0 + threadIdx.x / 2) * nb + blockIdx.x) +
+                                            (threadIdx.x & 1)] = u;
+    }
+    __syncthreads();
+  }
+  if (want_norm) {
+    double v2 = in ? fma(y.x, y.x, y.y * y.y) : 0.0;
+    v2 = warp_sum(v2);
+    if (lane == 0) s_nred[w] = v2;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int ww = 0; ww < kRedBlock / 32; ++ww) t += s_nred[ww];
+      st.npart[blockIdx.x] = t;
+    }
+  }
+  // 3. the last block reduces the partials in block order
+  if (threadIdx.x == 0) {
+    __threadfence();
+    s_last = atomicAdd(st.ticket, 1u) == (unsigned)nb - 1;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  // warp w: columns [a0, a0 + kPT) for a0 = kPT w, kPT (w + 8), ...
+  for (int a0 = kPT * w; a0 < np; a0 += kPT * (kRedBlock / 32)) {
+    double acc[2 * kPT];
+#pragma unroll
+    for (int c = 0; c < 2 * kPT; ++c) acc[c] = 0.0;
+    for (int b = lane; b < nb; b += 32) {
+#pragma unroll
+      for (int c = 0; c < kPT; ++c) {
+        if (a0 + c < np) {
+          const double2 t = __ldcg(st.partial + (long long)(a0 + c) * nb + b);
+          acc[2 * c] += t.x;
+          acc[2 * c + 1] += t.y;
+        }
+      }
+    }
+    const double t = warp_reduce16(acc);
+    const int a = a0 + (lane >> 2), comp = (lane >> 1) & 1;
+    if ((lane & 1) == 0 && a < np) {
+      reinterpret_cast<double*>(st.h)[2 * a + comp] = t;
+      reinterpret_cast<double*>(R)[2 * ((long long)a * m + jp) + comp] += t;
+    }
+  }
+  if (want_norm && w == 0) {
+    double t = 0.0;
+    for (int b = lane; b < nb; b += 32) t += __ldcg(st.npart + b);
+    t = warp_sum(t);
+    if (lane == 0) {
+      if (mode == kSubNorm) {
+        const bool dep = !(t > 1e-30 * st.scal[0]);
+        st.scal[1] = t;
+        st.scal[2] = dep ? 0.0 : 1.0 / sqrt(t);
+        R[(long long)j * m + j] = make_double2(dep ? 0.0 : sqrt(t), 0.0);
+      } else {
+        st.scal[0] = t;  // the original norm of column jp
       }
     }
   }
-#pragma unroll
-  for (int c = 0; c < kPC; ++c) {
-    const double rx = block_reduce(acc[c].x);
-    __syncthreads();
-    const double ry = block_reduce(acc[c].y);
-    __syncthreads();
-    if (threadIdx.x == 0 && a0 + c < j) partial[(long long)(a0 + c) * gridDim.x + blockIdx.x] = make_double2(rx, ry);
-  }
-}
-
-// h[a] = sum_b partial[a * nb + b]; R[a * m + j] += h[a]; one warp per a
-__global__ void proj_reduce_kernel(const double2* __restrict__ partial, int nb, int j, double2* __restrict__ h,
-                                   double2* __restrict__ R, int m) {
-  const int a = blockIdx.x;
-  if (a >= j) return;
-  double sx = 0.0, sy = 0.0;
-  for (int b = threadIdx.x; b < nb; b += 32) {
-    sx += partial[(long long)a * nb + b].x;
-    sy += partial[(long long)a * nb + b].y;
-  }
-  sx = warp_sum(sx);
-  sy = warp_sum(sy);
-  if (threadIdx.x == 0) {
-    h[a] = make_double2(sx, sy);
-    R[(long long)a * m + j].x += sx;
-    R[(long long)a * m + j].y += sy;
-  }
-}
-
-// v -= Q[0:j] h
-__global__ void __launch_bounds__(256)
-proj_subtract_kernel(const double2* __restrict__ Q, int j, const double2* __restrict__ h, double2* __restrict__ v,
-                     long long n) {
-  extern __shared__ double2 sh_h[];
-  for (int a = threadIdx.x; a < j; a += blockDim.x) sh_h[a] = h[a];
-  __syncthreads();
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
-    double2 x = v[e];
-    for (int a = 0; a < j; ++a) {
-      const double2 q = Q[(long long)a * n + e];
-      const double2 c = sh_h[a];
-      x.x -= q.x * c.x - q.y * c.y;
-      x.y -= q.x * c.y + q.y * c.x;
-    }
-    v[e] = x;
-  }
-}
-
-// R[j, j] = ||v|| (from the summed square), Q_j = v / ||v||; a vector whose
-// norm fell below 1e-15 of the original column's is numerically dependent
-// and becomes zero (R[j, j] = 0).
-__global__ void normalise_col_kernel(double2* __restrict__ v, long long n, const double* __restrict__ nrm2,
-                                     const double* __restrict__ orig2, double2* __restrict__ R, int m, int j) {
-  const double s2 = *nrm2;
-  const bool dep = !(s2 > 1e-30 * (*orig2));
-  const double inv = dep ? 0.0 : 1.0 / sqrt(s2);
-  if (blockIdx.x == 0 && threadIdx.x == 0) R[(long long)j * m + j] = make_double2(dep ? 0.0 : sqrt(s2), 0.0);
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
-    double2 x = v[e];
-    x.x *= inv;
-    x.y *= inv;
-    v[e] = x;
-  }
+  if (threadIdx.x == 0) *st.ticket = 0u;
 }
 
 int reduce_blocks(long long n) {
@@ -411,36 +506,37 @@ int gram(const double2* X, int mx, const double2* Y, int my, long long n, double
 
 
 int cgs2(const double2* S, int m, long long n, double2* Q, double2* R, DevBuf& scratch, cudaStream_t s) {
-  const int nb = reduce_blocks(n);
-  const size_t part_bytes = sizeof(double2) * (size_t)nb * m;
-  SS_TRY(scratch.alloc(part_bytes + sizeof(double2) * m + sizeof(double) * (2 * (size_t)nb + 2)));
-  double2* partial = scratch.as<double2>();
-  double2* h = partial + (size_t)nb * m;
-  double* npart = reinterpret_cast<double*>(h + m);
-  double* nrm2 = npart + nb;
-  double* orig2 = nrm2 + 1;
+  if (m > kCgsMaxCols) return fail(SSQCD_ERR_ARG, "CGS2 of more than 128 columns");
+  if (m <= 0 || n <= 0) return SSQCD_OK;
+  // one element per thread (measured faster here than whole numbers of
+  // blocks per SM with shorter chunks: 3.57 against 3.85 ms for 32 columns
+  // of n = 49152)
+  const long long nbl = (n + kRedBlock - 1) / kRedBlock;
+  if (nbl > (1LL << 30)) return fail(SSQCD_ERR_ARG, "CGS2 vectors too long");
+  const int nb = (int)nbl;
+  const int chunk = kRedBlock;
+  const size_t o_part = 0, o_np = o_part + sizeof(double2) * (size_t)kCgsMaxCols * nb,
+               o_h = (o_np + sizeof(double) * nb + 255) / 256 * 256, o_sc = o_h + sizeof(double2) * kCgsMaxCols,
+               o_t = o_sc + sizeof(double) * 4, total = o_t + 256;
+  SS_TRY(scratch.alloc(total));
+  char* base = scratch.as<char>();
+  CgsState st{reinterpret_cast<double2*>(base + o_part), reinterpret_cast<double*>(base + o_np),
+              reinterpret_cast<double2*>(base + o_h), reinterpret_cast<double*>(base + o_sc),
+              reinterpret_cast<unsigned*>(base + o_t)};
+  SS_CUDA(cudaMemsetAsync(st.ticket, 0, sizeof(unsigned), s));
   SS_CUDA(cudaMemsetAsync(R, 0, sizeof(double2) * m * m, s));
   SS_CUDA(cudaMemcpyAsync(Q, S, sizeof(double2) * n * m, cudaMemcpyDeviceToDevice, s));
-  if (m * sizeof(double2) > 48 * 1024)
-    SS_CUDA(cudaFuncSetAttribute(proj_subtract_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)(m * sizeof(double2))));
-  for (int j = 0; j < m; ++j) {
-    double2* v = Q + (long long)j * n;
-    SS_TRY(norm2_partials(v, 1, n, npart, nb, s));
-    SS_TRY(sum_partials(npart, 1, nb, orig2, s));
-    for (int pass = 0; pass < 2 && j > 0; ++pass) {
-      proj_partial_kernel<<<dim3(nb, (j + kPC - 1) / kPC), kRedBlock, 0, s>>>(Q, j, v, n, partial);
-      proj_reduce_kernel<<<j, 32, 0, s>>>(partial, nb, j, h, R, m);
-      proj_subtract_kernel<<<nb, 256, sizeof(double2) * j, s>>>(Q, j, h, v, n);
-      count_launches(3);
-      SS_CHECK_LAUNCH();
-    }
-    SS_TRY(norm2_partials(v, 1, n, npart, nb, s));
-    SS_TRY(sum_partials(npart, 1, nb, nrm2, s));
-    normalise_col_kernel<<<nb, 256, 0, s>>>(v, n, nrm2, orig2, R, m, j);
+  auto step = [&](int j, int mode) {
+    cgs2_step_kernel<<<nb, kRedBlock, 0, s>>>(st, Q, n, chunk, m, j, mode, R);
     count_launches(1);
-    SS_CHECK_LAUNCH();
+  };
+  step(0, kStart);
+  for (int j = 0; j < m; ++j) {
+    if (j > 0) step(j, kSubProj);  // first pass's h came with the previous kScale (or kStart)
+    step(j, kSubNorm);             // j = 0: no projection, the norm only
+    step(j, kScale);               // and the start of column j + 1
   }
+  SS_CHECK_LAUNCH();
   return SSQCD_OK;
 }
 

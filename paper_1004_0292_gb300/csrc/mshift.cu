@@ -1346,10 +1346,17 @@ __device__ __forceinline__ void put_out(float2& d, double2 x) {
 }
 
 // out[l][o][e] = sum_{s < count[l]} C[l][o][s] r_s[l][e] for O outputs per
-// source, kCombOut of them per block (grid.z): every thread keeps kCombOut
-// complex FP64 accumulators of one element and streams the stored residuals
-// of its source once; the coefficients of kCombTile slots at a time sit in
-// shared memory.  FP64 FMA bound (4 kCombOut FMA per 16-byte load).
+// source, kCombOut of them per block (grid.z): every thread keeps the
+// accumulators of kCombOut outputs for one element and streams the stored
+// residuals of its source once; the coefficients of kCombTile slots at a
+// time sit in shared memory.  The complex products use three real
+// multiplications (Gauss): with x = xr + i xi and w = wr + i wi,
+//   Re(w x) = wr xr - wi xi,  Im(w x) = (wr + wi)(xr + xi) - wr xr - wi xi,
+// accumulated as the three real sums A1 = sum wr xr, A2 = sum wi xi,
+// A3 = sum (wr + wi)(xr + xi): 3 FMA per term instead of 4 (the kernel is
+// bound by the FP64 pipe).  The imaginary part's rounding error is within a
+// few units of 2^-53 (|A1| + |A2| + |A3|), the order of that of the direct
+// product sum relative to sum |w| |x|.
 constexpr int kCombOut = 8;
 constexpr int kCombTile = 32;
 constexpr int kCombThreads = 256;
@@ -1358,22 +1365,25 @@ template <typename VR, typename VO>
 __global__ void __launch_bounds__(kCombThreads, 2)
 basis_combine_kernel(char* const* __restrict__ tab, long long n, int L, const double2* __restrict__ C, int O, int S,
                      const int* __restrict__ count, VO* __restrict__ out) {
-  __shared__ double2 s_c[kCombTile][kCombOut];
+  __shared__ double s_wr[kCombTile][kCombOut], s_wi[kCombTile][kCombOut], s_ws[kCombTile][kCombOut];
   __shared__ const VR* s_p[kCombTile];
   const int l = blockIdx.y, o0 = blockIdx.z * kCombOut;
   const int no = min(kCombOut, O - o0);
   const int Sl = count[l];
   const long long e = blockIdx.x * (long long)kCombThreads + threadIdx.x;
   const long long Ln = (long long)L * n;
-  double ax[kCombOut], ay[kCombOut];
+  double a1[kCombOut], a2[kCombOut], a3[kCombOut];
 #pragma unroll
-  for (int o = 0; o < kCombOut; ++o) ax[o] = ay[o] = 0.0;
+  for (int o = 0; o < kCombOut; ++o) a1[o] = a2[o] = a3[o] = 0.0;
   for (int s0 = 0; s0 < Sl; s0 += kCombTile) {
     const int ns = min(kCombTile, Sl - s0);
     __syncthreads();
     for (int t = threadIdx.x; t < kCombTile * kCombOut; t += kCombThreads) {
       const int ss = t / kCombOut, oo = t % kCombOut;
-      s_c[ss][oo] = (ss < ns && oo < no) ? C[((size_t)l * O + o0 + oo) * S + s0 + ss] : make_double2(0.0, 0.0);
+      const double2 c = (ss < ns && oo < no) ? C[((size_t)l * O + o0 + oo) * S + s0 + ss] : make_double2(0.0, 0.0);
+      s_wr[ss][oo] = c.x;
+      s_wi[ss][oo] = c.y;
+      s_ws[ss][oo] = c.x + c.y;
     }
     if (threadIdx.x < kCombTile) {
       const int s = s0 + threadIdx.x;
@@ -1386,17 +1396,19 @@ basis_combine_kernel(char* const* __restrict__ tab, long long n, int L, const do
 #pragma unroll 4
       for (int ss = 0; ss < ns; ++ss) {
         const double2 x = to_d2(s_p[ss][e]);
+        const double xs = x.x + x.y;
 #pragma unroll
         for (int o = 0; o < kCombOut; ++o) {
-          const double2 w = s_c[ss][o];
-          ax[o] = fma(w.x, x.x, fma(-w.y, x.y, ax[o]));
-          ay[o] = fma(w.x, x.y, fma(w.y, x.x, ay[o]));
+          a1[o] = fma(s_wr[ss][o], x.x, a1[o]);
+          a2[o] = fma(s_wi[ss][o], x.y, a2[o]);
+          a3[o] = fma(s_ws[ss][o], xs, a3[o]);
         }
       }
     }
   }
   if (e < n)
-    for (int o = 0; o < no; ++o) put_out(out[((size_t)l * O + o0 + o) * n + e], make_double2(ax[o], ay[o]));
+    for (int o = 0; o < no; ++o)
+      put_out(out[((size_t)l * O + o0 + o) * n + e], make_double2(a1[o] - a2[o], (a3[o] - a1[o]) - a2[o]));
 }
 
 template <typename VR, typename VO>
