@@ -65,8 +65,9 @@ def shifted_cg(apply_A, v, z, sigma=0.0, tol=1e-12, max_iter=100000, history=Fal
     with ``y`` (N, *v.shape), ``iters`` (per-shift iteration count at which it
     stopped), ``xi`` (final xi per shift), ``matvecs``, and, when
     ``history`` is set, per-iteration lists of ``r`` and ``xi``
-    (``hist_r[k]`` = r_k, ``hist_xi[k][j]`` = xi^j_k) and ``hist_y``
-    (y_j after k updates)."""
+    (``hist_r[k]`` = r_k, ``hist_xi[k][j]`` = xi^j_k), ``hist_y``
+    (y_j after k updates) and the seed scalars ``hist_alpha[k]`` = alpha_k,
+    ``hist_beta[k]`` = beta_k."""
     z = np.asarray(z, dtype=np.complex128)
     N = len(z)
     s = z - sigma
@@ -85,7 +86,7 @@ def shifted_cg(apply_A, v, z, sigma=0.0, tol=1e-12, max_iter=100000, history=Fal
     alpha_prev, beta_prev = 1.0, 0.0
     active = np.ones(N, dtype=bool)
     iters = np.zeros(N, dtype=np.int64)
-    out = {"hist_r": [], "hist_xi": [], "hist_y": []} if history else {}
+    out = {"hist_r": [], "hist_xi": [], "hist_y": [], "hist_alpha": [], "hist_beta": []} if history else {}
     if history:
         out["hist_r"].append(r.copy())
         out["hist_xi"].append(xi_cur.copy())
@@ -124,5 +125,7 @@ def shifted_cg(apply_A, v, z, sigma=0.0, tol=1e-12, max_iter=100000, history=Fal
             out["hist_r"].append(r.copy())
             out["hist_xi"].append(xi_cur.copy())
             out["hist_y"].append(y.copy())
+            out["hist_alpha"].append(alpha)
+            out["hist_beta"].append(beta)
     out.update(y=y, iters=iters, xi=xi_cur, matvecs=k)
     return out
