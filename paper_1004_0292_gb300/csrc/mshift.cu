@@ -276,12 +276,15 @@ struct Stencil64 {
 
 // FP64, balanced form (16 sites per block, spin halves in half-warps); used
 // by the solve loop
+// MinB blocks an SM: 7 (<= 72 registers; 1064 resident blocks >= the 1024 of
+// 8^4 x 4 rhs) by default, 8 (64 registers, a few spilled) for comparison
+template <int MinB>
 struct Stencil64h {
   static constexpr bool kThreadPerSite = false;
   static constexpr int kThreads = kStencilThreads;
   static constexpr int kSites = kSitesPerBlockH;
   static constexpr int kShElems = 12 * 4 * kSitesPerBlockH;
-  static constexpr int kMinBlocks = 7;  // <= 72 registers: 7 blocks an SM (1064 >= the 1024 blocks of 8^4 x 4)
+  static constexpr int kMinBlocks = MinB;
   const double2* __restrict__ u;
   __device__ __forceinline__ double run(const Geometry& g, const double2* __restrict__ p, double2* __restrict__ q,
                                         double sigma, int, int, void* shm) const {
@@ -345,12 +348,16 @@ struct Stencil32 {
 
 // float-float stencil (SSQCD_DF): q = sigma p - A p, float-float share of
 // (p, q); one hop per warp, 8 warps per block (wilson_df.cuh)
+// MinB blocks an SM: 4 (64 registers, a few spilled) by default, which puts
+// the 512 blocks of 8^4 x 4 rhs in one wave (CG iteration 45.0 us against
+// 57.2 us at 3 blocks an SM, <= 85 registers, 1.12 waves); 3 for comparison
+template <int MinB>
 struct StencilDF {
   static constexpr bool kThreadPerSite = false;
   static constexpr int kThreads = kStencilThreadsDF;
   static constexpr int kSites = kSitesPerBlock;
   static constexpr int kShElems = 12 * 4 * kSitesPerBlock;  // 8 x 6 x 32 float4
-  static constexpr int kMinBlocks = 3;  // <= 85 registers; a 64-register cap (4 blocks) spilled and measured slower
+  static constexpr int kMinBlocks = MinB;
   const float4* __restrict__ u;
   __device__ __forceinline__ double run(const Geometry& g, const float4* __restrict__ p, float4* __restrict__ q,
                                         double sigma, int s, int w, void* shm) const {
@@ -1411,6 +1418,63 @@ basis_combine_kernel(char* const* __restrict__ tab, long long n, int L, const do
       put_out(out[((size_t)l * O + o0 + o) * n + e], make_double2(a1[o] - a2[o], (a3[o] - a1[o]) - a2[o]));
 }
 
+// The same combination for float-float residuals (SSQCD_DF runs), on the
+// FP32 pipes: within a tile of kCombTile slots each output accumulates
+// c += w r in float-float (the FP64 coefficients split into float-float
+// pairs once per tile), then the tile's sums enter FP64 accumulators, so at
+// most kCombTile terms share a float-float sum (rounding ~kCombTile 2^-48 of
+// their magnitudes, against the residuals' own 2^-48).  The FP64 pipe only
+// sees the per-tile conversions.
+__global__ void __launch_bounds__(kCombThreads, 2)
+basis_combine_df_kernel(char* const* __restrict__ tab, long long n, int L, const double2* __restrict__ C, int O, int S,
+                        const int* __restrict__ count, double2* __restrict__ out) {
+  __shared__ float4 s_w[kCombTile][kCombOut];
+  __shared__ const float4* s_p[kCombTile];
+  const int l = blockIdx.y, o0 = blockIdx.z * kCombOut;
+  const int no = min(kCombOut, O - o0);
+  const int Sl = count[l];
+  const long long e = blockIdx.x * (long long)kCombThreads + threadIdx.x;
+  const long long Ln = (long long)L * n;
+  double2 accd[kCombOut];
+#pragma unroll
+  for (int o = 0; o < kCombOut; ++o) accd[o] = make_double2(0.0, 0.0);
+  for (int s0 = 0; s0 < Sl; s0 += kCombTile) {
+    const int ns = min(kCombTile, Sl - s0);
+    __syncthreads();
+    for (int t = threadIdx.x; t < kCombTile * kCombOut; t += kCombThreads) {
+      const int ss = t / kCombOut, oo = t % kCombOut;
+      const double2 c = (ss < ns && oo < no) ? C[((size_t)l * O + o0 + oo) * S + s0 + ss] : make_double2(0.0, 0.0);
+      s_w[ss][oo] = ff::from_double2(c);
+    }
+    if (threadIdx.x < kCombTile) {
+      const int s = s0 + threadIdx.x;
+      s_p[threadIdx.x] = threadIdx.x < ns ? reinterpret_cast<const float4*>(tab[s >> kBasisLog]) +
+                                                (long long)(s & (kBasisBlock - 1)) * Ln + (long long)l * n
+                                          : nullptr;
+    }
+    __syncthreads();
+    if (e < n) {
+      ff::cff acc[kCombOut];
+#pragma unroll
+      for (int o = 0; o < kCombOut; ++o) acc[o] = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 2
+      for (int ss = 0; ss < ns; ++ss) {
+        const float4 x = s_p[ss][e];
+#pragma unroll
+        for (int o = 0; o < kCombOut; ++o) acc[o] = ff::cfma(acc[o], s_w[ss][o], x);
+      }
+#pragma unroll
+      for (int o = 0; o < kCombOut; ++o) {
+        const double2 t = ff::to_double2(acc[o]);
+        accd[o].x += t.x;
+        accd[o].y += t.y;
+      }
+    }
+  }
+  if (e < n)
+    for (int o = 0; o < no; ++o) out[((size_t)l * O + o0 + o) * n + e] = accd[o];
+}
+
 template <typename VR, typename VO>
 int launch_combine(char* const* tab, long long n, int L, const double2* C, int O, int S, const int* count, VO* out,
                    cudaStream_t st) {
@@ -1460,6 +1524,16 @@ bool use_pdl() {
   static const bool v = [] {
     const char* e = std::getenv("SSQCD_PDL");
     return e && e[0] == '1';
+  }();
+  return v;
+}
+
+// Blocks per SM of the loop's stencil (register cap), SSQCD_STENCIL_MINB for
+// comparison runs: 0 = the default of each form.
+int stencil_minb() {
+  static const int v = [] {
+    const char* e = std::getenv("SSQCD_STENCIL_MINB");
+    return e ? std::atoi(e) : 0;
   }();
   return v;
 }
@@ -2138,11 +2212,23 @@ class CgRun final : public CgRunBase {
         launch_chain(cg_stencil_kernel<Stencil32<LinksF32>, VR>, grid_a, kSiteThreads, st, prio_hi_, basis_ && use_pdl(), c, L, par, g,
                     Stencil32<LinksF32>{LinksF32{lat_->u32.as<float4>(), g.V}}, sigma_, p_.as<VR>(), q_.as<VR>());
     } else if constexpr (kSeedDF) {
-      launch_chain(cg_stencil_kernel<StencilDF, VR>, grid_a, StencilDF::kThreads, st, prio_hi_, basis_ && use_pdl(), c, L, par, g,
-                  StencilDF{lat_->udf.as<float4>()}, sigma_, p_.as<VR>(), q_.as<VR>());
+      if (stencil_minb() == 3)
+        launch_chain(cg_stencil_kernel<StencilDF<3>, VR>, grid_a, kStencilThreadsDF, st, prio_hi_,
+                     basis_ && use_pdl(), c, L, par, g, StencilDF<3>{lat_->udf.as<float4>()}, sigma_, p_.as<VR>(),
+                     q_.as<VR>());
+      else
+        launch_chain(cg_stencil_kernel<StencilDF<4>, VR>, grid_a, kStencilThreadsDF, st, prio_hi_,
+                     basis_ && use_pdl(), c, L, par, g, StencilDF<4>{lat_->udf.as<float4>()}, sigma_, p_.as<VR>(),
+                     q_.as<VR>());
     } else if (balanced_stencil()) {
-      launch_chain(cg_stencil_kernel<Stencil64h, VR>, grid_a, kStencilThreads, st, prio_hi_, basis_ && use_pdl(), c, L, par, g,
-                  Stencil64h{lat_->u64.as<double2>()}, sigma_, p_.as<VR>(), q_.as<VR>());
+      if (stencil_minb() == 8)
+        launch_chain(cg_stencil_kernel<Stencil64h<8>, VR>, grid_a, kStencilThreads, st, prio_hi_,
+                     basis_ && use_pdl(), c, L, par, g, Stencil64h<8>{lat_->u64.as<double2>()}, sigma_,
+                     p_.as<VR>(), q_.as<VR>());
+      else
+        launch_chain(cg_stencil_kernel<Stencil64h<7>, VR>, grid_a, kStencilThreads, st, prio_hi_,
+                     basis_ && use_pdl(), c, L, par, g, Stencil64h<7>{lat_->u64.as<double2>()}, sigma_,
+                     p_.as<VR>(), q_.as<VR>());
     } else {
       launch_chain(cg_stencil_kernel<Stencil64, VR>, grid_a, kStencilThreads, st, prio_hi_, basis_ && use_pdl(), c, L, par, g,
                   Stencil64{lat_->u64.as<double2>()}, sigma_, p_.as<VR>(), q_.as<VR>());
@@ -2340,7 +2426,14 @@ int basis_moments(const KrylovBasis& b, const double2* coef_host, int M, double2
   basis_window_kernel<<<(unsigned)((cnt + 255) / 256), 256, 0, st>>>(b.gam.as<double2>(), W, N, M, L, S, G);
   SS_CHECK_LAUNCH();
   count_launches(1);
-  if (b.df) return launch_combine<float4, double2>(b.tab.as<char*>(), b.n, L, G, M, S, b.count.as<int>(), s_hat, st);
+  if (b.df) {
+    const dim3 grid((unsigned)((b.n + kCombThreads - 1) / kCombThreads), L, (M + kCombOut - 1) / kCombOut);
+    basis_combine_df_kernel<<<grid, kCombThreads, 0, st>>>(b.tab.as<char*>(), b.n, L, G, M, S, b.count.as<int>(),
+                                                           s_hat);
+    SS_CHECK_LAUNCH();
+    count_launches(1);
+    return SSQCD_OK;
+  }
   return launch_combine<double2, double2>(b.tab.as<char*>(), b.n, L, G, M, S, b.count.as<int>(), s_hat, st);
 }
 
