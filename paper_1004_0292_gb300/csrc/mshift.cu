@@ -304,8 +304,14 @@ struct Stencil64h {
       const double sg = comp < 6 ? -1.0 : 1.0;
       const double2 pv = p[comp * g.V + s];
       double2 o;
-      o.x = fma(sg, fma(mk, acc.x, pv.x), sigma * pv.x);
-      o.y = fma(sg, fma(mk, acc.y, pv.y), sigma * pv.y);
+      if (sigma == 0.0) {  // the paper's seed shift: no sigma p term; the gamma5 sign as a negation
+        const double tx = fma(mk, acc.x, pv.x), ty = fma(mk, acc.y, pv.y);
+        o.x = comp < 6 ? -tx : tx;
+        o.y = comp < 6 ? -ty : ty;
+      } else {
+        o.x = fma(sg, fma(mk, acc.x, pv.x), sigma * pv.x);
+        o.y = fma(sg, fma(mk, acc.y, pv.y), sigma * pv.y);
+      }
       q[comp * g.V + s] = o;
       d = fma(pv.x, o.x, fma(pv.y, o.y, d));
     }

@@ -454,8 +454,10 @@ __device__ __forceinline__ double2 flip(double2 z, unsigned long long neg) {
 
 // One hop (forward: DIR = +1, U_mu(x) psi(x + mu), h = psi_u - B psi_l;
 // backward: U_mu(x - mu)^H psi(x - mu), h = psi_u + B psi_l) for spin row r
-// of site s; adds wv_r to up[] and -+ hcode B^H-row t to lo[].
-template <int MU, int DIR>
+// of site s; adds wv_r to up[] and -+ hcode B^H-row t to lo[] (INIT: sets
+// them -- the first hop of a thread, sparing the additions to zero, which
+// IEEE arithmetic cannot drop by itself because of -0).
+template <int MU, int DIR, bool INIT>
 __device__ __forceinline__ void hop_half64(const Links64& lk, const double2* __restrict__ in, int s, const Coords& c,
                                            const Geometry& g, int r, double2 (&up)[3], double2 (&lo)[3]) {
   using S = Spin<MU>;
@@ -491,8 +493,13 @@ __device__ __forceinline__ void hop_half64(const Links64& lk, const double2* __r
       cmac_conj(tv, u1, h[1]);
       cmac_conj(tv, u2, h[2]);
     }
-    up[a] = cadd(up[a], tv);
-    lo[a] = cadd(lo[a], unit_apply(tv, hcode, nrec));
+    if (INIT) {
+      up[a] = tv;
+      lo[a] = unit_apply(tv, hcode, nrec);
+    } else {
+      up[a] = cadd(up[a], tv);
+      lo[a] = cadd(lo[a], unit_apply(tv, hcode, nrec));
+    }
   }
 }
 
@@ -500,12 +507,13 @@ template <int MU>
 __device__ __forceinline__ void hop_dir_half64(const Links64& lk, const double2* __restrict__ in, int s,
                                                const Geometry& g, int r, double2* sh, int i) {
   double2 up[3], lo[3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) up[a] = lo[a] = make_double2(0.0, 0.0);
   if (s < g.V) {
     const Coords c = site_coords(s, g);
-    hop_half64<MU, +1>(lk, in, s, c, g, r, up, lo);
-    hop_half64<MU, -1>(lk, in, s, c, g, r, up, lo);
+    hop_half64<MU, +1, true>(lk, in, s, c, g, r, up, lo);
+    hop_half64<MU, -1, false>(lk, in, s, c, g, r, up, lo);
+  } else {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) up[a] = lo[a] = make_double2(0.0, 0.0);
   }
   using S = Spin<MU>;
   const int t = (r == S::hcol0) ? 0 : 1;
