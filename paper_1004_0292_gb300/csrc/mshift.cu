@@ -1289,19 +1289,35 @@ __global__ void basis_gamma_kernel(Control c, int L, int N, int S, double2* __re
   const int l = qi / N;
   const int K = c.iters[qi] - 1;
   double2* gq = gam + (size_t)qi * S;
+  for (int s = S - 1; s > K; --s) gq[s] = make_double2(0.0, 0.0);
+  // the recurrence is a chain of dependent FMAs (64 cycles each); the loads
+  // of the coefficients it needs are independent of it, so they are issued
+  // kG steps ahead
+  constexpr int kG = 8;
   double gx = 0.0, gy = 0.0;
-  for (int s = S - 1; s >= 0; --s) {
-    if (s > K) {
-      gq[s] = make_double2(0.0, 0.0);
-      continue;
+  for (int s1 = K; s1 >= 0; s1 -= kG) {
+    double2 a[kG], b[kG];
+    double sc[kG];
+#pragma unroll
+    for (int i = 0; i < kG; ++i) {
+      const int s = s1 - i;
+      if (s >= 0) {
+        a[i] = basis_coef(c, s, NL, 0)[qi];
+        b[i] = basis_coef(c, s, NL, 1)[qi];
+        sc[i] = s == 0 ? 1.0 : basis_scale(c, s - 1, NL, L)[l];
+      }
     }
-    const double2 a = basis_coef(c, s, NL, 0)[qi], b = basis_coef(c, s, NL, 1)[qi];
-    const double nx = fma(b.x, gx, fma(-b.y, gy, a.x));
-    const double ny = fma(b.x, gy, fma(b.y, gx, a.y));
-    gx = nx;
-    gy = ny;
-    const double sc = s == 0 ? 1.0 : basis_scale(c, s - 1, NL, L)[l];
-    gq[s] = make_double2(gx * sc, gy * sc);
+#pragma unroll
+    for (int i = 0; i < kG; ++i) {
+      const int s = s1 - i;
+      if (s >= 0) {
+        const double nx = fma(b[i].x, gx, fma(-b[i].y, gy, a[i].x));
+        const double ny = fma(b[i].x, gy, fma(b[i].y, gx, a[i].y));
+        gx = nx;
+        gy = ny;
+        gq[s] = make_double2(gx * sc[i], gy * sc[i]);
+      }
+    }
   }
 }
 
@@ -1372,7 +1388,10 @@ __device__ __forceinline__ void put_out(float2& d, double2 x) {
 // product sum relative to sum |w| |x|.
 constexpr int kCombOut = 8;
 constexpr int kCombTile = 32;
-constexpr int kCombThreads = 256;
+// small blocks: the work per element is uniform, so the per-SM load is even
+// only when blocks are small against it (8^4 x 4 sources: 3072 blocks of 64
+// threads, ~20 an SM, against 768 of 256 filling 2.5 waves of 2 an SM)
+constexpr int kCombThreads = 64;
 
 template <typename VR, typename VO>
 __global__ void __launch_bounds__(kCombThreads, 2)
