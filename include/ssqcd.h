@@ -133,7 +133,10 @@ typedef struct {
 
 /* Counters of one solve.  Times are device milliseconds between CUDA events. */
 typedef struct {
-  int    iterations;      /* seed CG iterations = stencil applications in the loop */
+  int    iterations;      /* seed CG iterations that updated a shift (= the largest
+                             per-shift count; the Krylov-basis loop may apply the
+                             stencil once more after the last freeze, because it
+                             reads the live count one iteration late)            */
   int    max_shift_iters; /* largest per-shift iteration count at freeze           */
   int    matvecs_rr;      /* extra stencil applications in Rayleigh-Ritz           */
   int    rank;            /* dimension of the orthonormal basis kept               */

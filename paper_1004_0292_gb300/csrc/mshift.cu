@@ -109,6 +109,13 @@ struct Control {
   char* const* tab;
   size_t blk_vec;
   char** rptr;         // [2] slots r_k, r_{k+1} of the coming iteration (written by the last block of B)
+  // Krylov-basis loop: the per-shift scalar work runs in kernel S on a side
+  // stream (split = 1) from these per-parity records
+  int split;
+  double* alpha_rec;   // [2][L]    alpha_k (last block of A)
+  double* srec;        // [2][L][4] rr_{k+1}, beta_k, scale s_k, product of the earlier scales (last block of B)
+  int* srec_k;         // [2]       iteration index k
+  double* sprev;       // [L][2]    alpha_{k-1}, beta_{k-1} (kernel S's own state)
 };
 
 constexpr int kUpdBlock = 256;
@@ -221,6 +228,10 @@ __global__ void init_control_kernel(Control c, const double* __restrict__ vn2, i
     c.vnorm2[t] = vn2[t];
     c.live[t] = vn2[t] > 0.0 ? N : 0;
     c.list_n[t] = c.list_n[L + t] = 0;
+    if (c.sprev != nullptr) {
+      c.sprev[2 * t] = 1.0;  // alpha_{-1}
+      c.sprev[2 * t + 1] = 0.0;  // beta_{-1}
+    }
   }
   for (int t = threadIdx.x; t < L * N; t += blockDim.x) {
     c.xi_cur[t] = make_double2(1.0, 0.0);
@@ -447,6 +458,7 @@ cg_stencil_kernel(Control c, int L, int par, Geometry g, Op op, double sigma, co
       continue;
     }
     c.alpha[ls] = rr / pq;
+    if (c.split) c.alpha_rec[par * L + ls] = rr / pq;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -493,7 +505,7 @@ cg_seed_kernel(Control c, int L, int N, int par, double tol2, const V2* __restri
   __shared__ bool s_last;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int NL = N * L;
-  if (w == kSeedBlock / 32 - 1) {
+  if (w == kSeedBlock / 32 - 1 && !c.split) {
     const int nblk = gridDim.x * gridDim.y;
     for (int qi = blockIdx.y * gridDim.x + blockIdx.x + lane * nblk; qi < NL; qi += 32 * nblk) {
       const int ls = qi / N;
@@ -614,6 +626,28 @@ cg_seed_kernel(Control c, int L, int N, int par, double tol2, const V2* __restri
     c.rptr[1] = reinterpret_cast<char*>(basis_slot<V2>(c, kb + 2, Ln));
   }
   __syncthreads();
+  if (c.split) {
+    // the seed state only; kernel S takes the shifts from this record
+    for (int ls = threadIdx.x; ls < L; ls += blockDim.x) {
+      const double sc = s_scale[ls];
+      const SeedState sd = c.seed[ls];
+      double* rec = c.srec + ((size_t)par * L + ls) * 4;
+      rec[0] = sums[ls];
+      rec[1] = s_beta[ls];
+      rec[2] = sc;
+      rec[3] = sd.pad[1];
+      if (c.live[ls] != 0) {
+        const double rr = sums[ls] * sc * sc;
+        c.seed[ls] = SeedState{rr, c.alpha[ls], s_beta[ls], s_beta[ls], sc, {1.0 / rr, sd.pad[1] * sc, 0.0}};
+      }
+    }
+    if (threadIdx.x == 0) {
+      c.srec_k[par] = kb;
+      c.done[1] = 0u;
+      c.task_ctr[par] = 0u;
+    }
+    return;
+  }
   // per shift: coefficients and the freeze test from xi_{k+1}
   for (int qi = threadIdx.x; qi < NL; qi += blockDim.x) {
     const int ls = qi / N;
@@ -720,6 +754,79 @@ cg_seed_p_kernel(Control c, const VR* __restrict__ r, VR* __restrict__ p, long l
     }
   }
   pdl_trigger();
+}
+
+// ---- S. shift scalars of the Krylov-basis loop (side stream) ---------------------------
+// For every live shift of iteration k (record of parity par): xi_{k+1} from
+// alpha_k and the older scalars, the coefficients a_j = alpha_k xi_{k+1} and
+// b_j = s beta_k xi_{k+1} / xi_k into the coefficient records, the freeze
+// test |xi_{k+1}|^2 rr_{k+1} <= tol^2 ||v||^2, and the live counts.  It runs
+// beside P(k), A(k+1), B(k+1) of the main stream: they read the live counts
+// only to skip finished work, and a count one iteration old only makes them
+// do some of it once more (counts only fall).  A(k+2) waits for S(k), whose
+// records (alpha_rec, srec of this parity) it and B(k+2) rewrite.  One block.
+__global__ void __launch_bounds__(kSeedBlock)
+cg_shift_kernel(Control c, int L, int N, int par, double tol2, double rescale_by) {
+  if (c.rec_ran[par] == 0) return;
+  __shared__ int s_live[kMaxSources];
+  const int NL = N * L;
+  const int kb = c.srec_k[par];
+  for (int t = threadIdx.x; t < L; t += blockDim.x) s_live[t] = 0;
+  __syncthreads();
+  for (int qi = threadIdx.x; qi < NL; qi += blockDim.x) {
+    const int ls = qi / N;
+    const int lv = c.live[ls], ac = c.act[qi];
+    const double* rec = c.srec + ((size_t)par * L + ls) * 4;
+    const double rr1 = rec[0], beta = rec[1], sc = rec[2], spad1 = rec[3];
+    const double alpha = c.alpha_rec[par * L + ls], ap = c.sprev[2 * ls], bp = c.sprev[2 * ls + 1];
+    const double vn2 = c.vnorm2[ls];
+    const double2 xc = c.xi_cur[qi], xp = c.xi_prev[qi], s = c.shift_s[qi];
+    if (lv == 0 || !ac) continue;
+    const double inv_c = 1.0 / (xc.x * xc.x + xc.y * xc.y);  // independent of the chain below
+    // xi_{k+1} = xi_k xi_{k-1} alpha_{k-1} /
+    //            [alpha_k beta_{k-1} (xi_{k-1} - xi_k) + xi_{k-1} alpha_{k-1} (1 + s alpha_k)]
+    double2 num;
+    num.x = (xc.x * xp.x - xc.y * xp.y) * ap;
+    num.y = (xc.x * xp.y + xc.y * xp.x) * ap;
+    const double ab = alpha * bp;
+    const double ux = 1.0 + s.x * alpha, uy = s.y * alpha;
+    double2 den;
+    den.x = ab * (xp.x - xc.x) + (xp.x * ux - xp.y * uy) * ap;
+    den.y = ab * (xp.y - xc.y) + (xp.x * uy + xp.y * ux) * ap;
+    const double inv_d = 1.0 / (den.x * den.x + den.y * den.y);
+    double2 xn;
+    xn.x = (num.x * den.x + num.y * den.y) * inv_d;
+    xn.y = (num.y * den.x - num.x * den.y) * inv_d;
+    const double2 ratio = make_double2((xn.x * xc.x + xn.y * xc.y) * inv_c, (xn.y * xc.x - xn.x * xc.y) * inv_c);
+    const double inv_sc = sc == 1.0 ? 1.0 : 1.0 / rescale_by;
+    basis_coef(c, kb, NL, 0)[qi] = make_double2(alpha * xn.x, alpha * xn.y);
+    basis_coef(c, kb, NL, 1)[qi] = make_double2(sc * beta * ratio.x, sc * beta * ratio.y);
+    const bool live = (xn.x * xn.x + xn.y * xn.y) * rr1 > tol2 * vn2;
+    c.xi_prev[qi] = make_double2(xc.x * inv_sc, xc.y * inv_sc);
+    // a freezing shift leaves its unscaled xi (xi_{k+1} S, S = product of
+    // the scales so far); a live one keeps it in the scale of r
+    const double S = live ? inv_sc : spad1;
+    c.xi_cur[qi] = make_double2(xn.x * S, xn.y * S);
+    c.act[qi] = live ? 1 : 0;
+    c.iters[qi] += 1;
+    if (live) atomicAdd(&s_live[ls], 1);
+  }
+  __syncthreads();
+  for (int ls = threadIdx.x; ls < L; ls += blockDim.x) {
+    const double* rec = c.srec + ((size_t)par * L + ls) * 4;
+    basis_scale(c, kb, NL, L)[ls] = rec[2];
+    if (c.live[ls] != 0) {
+      c.sprev[2 * ls] = c.alpha_rec[par * L + ls];
+      c.sprev[2 * ls + 1] = rec[1];
+    }
+    c.live[ls] = s_live[ls];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int tot = 0;
+    for (int ls = 0; ls < L; ++ls) tot += s_live[ls];
+    *c.live_total = tot;
+  }
 }
 
 // ---- C. fused multi-shift update -------------------------------------------------------
@@ -1806,7 +1913,9 @@ class CgRun final : public CgRunBase {
                  o_la = take(sizeof(double2) * 2 * NL), o_lb = take(sizeof(double2) * 2 * NL),
                  o_lsc = take(sizeof(double) * 2 * L), o_part = take(sizeof(double) * (size_t)nbw_ * L),
                  o_prr = take(sizeof(double) * (size_t)nbs_ * L), o_vp = take(sizeof(double) * (size_t)nbs_ * L),
-                 o_vn2 = take(sizeof(double) * L), o_rptr = take(sizeof(char*) * 2);
+                 o_vn2 = take(sizeof(double) * L), o_rptr = take(sizeof(char*) * 2),
+                 o_arec = take(sizeof(double) * 2 * L), o_srec = take(sizeof(double) * 8 * L),
+                 o_srk = take(sizeof(int) * 2), o_sprev = take(sizeof(double) * 2 * L);
     SS_TRY(ctl_.alloc(off));
     char* base = ctl_.as<char>();
     Control& c = c_;
@@ -1839,6 +1948,11 @@ class CgRun final : public CgRunBase {
     c.tab = basis_ ? tab_.as<char*>() : nullptr;
     c.blk_vec = blk_vec_;
     c.rptr = reinterpret_cast<char**>(base + o_rptr);
+    c.split = basis_ ? 1 : 0;
+    c.alpha_rec = reinterpret_cast<double*>(base + o_arec);
+    c.srec = reinterpret_cast<double*>(base + o_srec);
+    c.srec_k = reinterpret_cast<int*>(base + o_srk);
+    c.sprev = reinterpret_cast<double*>(base + o_sprev);
     if (basis_) {  // slots 0 and 1 for the first iteration
       h_tab_[tab_cap_] = h_tab_[0];
       h_tab_[tab_cap_ + 1] = h_tab_[0] + sizeof(VR) * (size_t)L * n;
@@ -1920,7 +2034,7 @@ class CgRun final : public CgRunBase {
       cudaError_t le = cudaGetLastError();
       if (le != cudaSuccess) return cuda_fail(le, "shifted CG launch", __FILE__, __LINE__);
     }
-    count_launches((basis_ ? 3LL : 4LL) * chunk);
+    count_launches(4LL * chunk);
     k_ += chunk;
     info.count = chunk;
     ++launched_chunks_;
@@ -1989,11 +2103,14 @@ class CgRun final : public CgRunBase {
     }
     const int live = h_poll_[2 * slot], err = h_poll_[2 * slot + 1];
     if (err == 2) return fail(SSQCD_ERR_NOCONV, "shift update: a device-side wait hit its limit");
-    if (err != 0) return fail(SSQCD_ERR_BREAKDOWN, "seed CG breakdown: |(p, K p)| < 1e-30 (r, r)");
+    // every shift frozen: done, even if an iteration that ran after the last
+    // freeze (the Krylov-basis loop reads the live count one iteration late)
+    // met a breakdown of the then useless seed recurrence
     if (live == 0) {
       *state = kPollDone;
       return SSQCD_OK;
     }
+    if (err != 0) return fail(SSQCD_ERR_BREAKDOWN, "seed CG breakdown: |(p, K p)| < 1e-30 (r, r)");
     if (info.k_start + info.count >= max_iter_) {
       char buf[128];
       std::snprintf(buf, sizeof(buf), "shifted CG: %d shifts still above tol after %d iterations", live, max_iter_);
@@ -2044,7 +2161,9 @@ class CgRun final : public CgRunBase {
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0_, e1_);
     if (out) {
-      out->seed_iters = counters[0];
+      // iterations that updated a shift: the stencil applications but for
+      // at most one after the last freeze (Krylov-basis loop, see poll)
+      out->seed_iters = it_all.empty() ? 0 : *std::max_element(it_all.begin(), it_all.end());
       out->reliable_updates = counters[1];
       out->ms = ms;
       out->shift_updates = 0;
@@ -2199,6 +2318,7 @@ class CgRun final : public CgRunBase {
     basis_ = false;
     basis_state_ = 2;
     c_.tab = nullptr;
+    c_.split = 0;  // kernel B takes the shift scalars again
     if (gexec_ != nullptr) cudaGraphExecDestroy(gexec_);
     if (gexec_t_ != nullptr) cudaGraphExecDestroy(gexec_t_);
     gexec_ = capture(false);
@@ -2227,7 +2347,9 @@ class CgRun final : public CgRunBase {
     const VR* r_in = basis_ ? nullptr : r0 + (size_t)par * n * L;
     VR* r_out = basis_ ? nullptr : r0 + (size_t)(par ^ 1) * n * L;
     cudaStream_t st = st_;
-    if (it >= 2 && !basis_) cudaStreamWaitEvent(st, ev_[kChunk + it - 2], 0);
+    // A(k) after the side-stream kernel of k - 2 (C or S), which reads the
+    // parity-(k % 2) records that A(k) and B(k) rewrite
+    if (it >= 2) cudaStreamWaitEvent(st, ev_[kChunk + it - 2], 0);
     mark(it, 0, st);
     if constexpr (kFP32) {
       if (lat_->precision == SSQCD_MIXED)
@@ -2267,9 +2389,12 @@ class CgRun final : public CgRunBase {
     mark(it, 6, st);
     launch_chain(cg_seed_p_kernel<VR>, grid_p, kUpdBlock, st, prio_hi_, basis_ && use_pdl(), c, r_out, p_.as<VR>(), n);
     mark(it, 7, st);
-    if (basis_) {  // no shift-vector update
-      mark(it, 4, st);
-      mark(it, 5, st);
+    if (basis_) {  // no shift-vector update: the shift scalars on the side stream
+      cudaStreamWaitEvent(side_, ev_[it], 0);
+      mark(it, 4, side_);
+      launch_prio(cg_shift_kernel, dim3(1), kSeedBlock, side_, prio_lo_, c, L, N, par, tol2_, rescale_by_);
+      mark(it, 5, side_);
+      cudaEventRecord(ev_[kChunk + it], side_);
       return;
     }
     cudaStreamWaitEvent(side_, ev_[it], 0);
@@ -2287,10 +2412,6 @@ class CgRun final : public CgRunBase {
   }
 
   void run_chunk(int count) {
-    if (basis_) {
-      for (int it = 0; it < count; ++it) iteration(it);
-      return;
-    }
     cudaEvent_t ev_fork = ev_[2 * kChunk];
     cudaEventRecord(ev_fork, st_);
     cudaStreamWaitEvent(side_, ev_fork, 0);
