@@ -1680,6 +1680,21 @@ bool balanced_stencil() {
   return v;
 }
 
+// Blocks per source of kernel P (it strides): two blocks an SM over all
+// sources by default (8^4 x 4: 50.3 against 50.6 us an iteration with one
+// element per thread); SSQCD_P_BLOCKS sets the cap for tuning runs.
+unsigned p_blocks(long long n, int L) {
+  static const long long env = [] {
+    const char* e = std::getenv("SSQCD_P_BLOCKS");
+    const long long v = e ? std::atoll(e) : 0;
+    return v > 0 ? v : 0LL;
+  }();
+  const long long cap = env > 0 ? env : (152LL * 2 + L - 1) / L;
+  long long b = (n + kUpdBlock - 1) / kUpdBlock;
+  if (b > cap) b = cap;
+  return (unsigned)(b < 1 ? 1 : b);
+}
+
 int seed_blocks(long long n, int L) {
   static const int ept = [] {  // SSQCD_SEED_EPT: elements per thread (tuning runs)
     const char* e = std::getenv("SSQCD_SEED_EPT");
@@ -2341,7 +2356,7 @@ class CgRun final : public CgRunBase {
     const int L = L_, N = N_;
     Control& c = c_;
     const dim3 grid_a(nbw_, L), grid_b(nbs_, L), grid_c(nbu_, L);
-    const dim3 grid_p((unsigned)((n + kUpdBlock - 1) / kUpdBlock), L);  // one element per thread
+    const dim3 grid_p(p_blocks(n, L), L);
     VR* const r0 = r_.as<VR>();  // null in the Krylov-basis form (kernels B, P address the slots)
     const int par = it & 1;
     const VR* r_in = basis_ ? nullptr : r0 + (size_t)par * n * L;

@@ -454,10 +454,13 @@ __device__ __forceinline__ double2 flip(double2 z, unsigned long long neg) {
 
 // One hop (forward: DIR = +1, U_mu(x) psi(x + mu), h = psi_u - B psi_l;
 // backward: U_mu(x - mu)^H psi(x - mu), h = psi_u + B psi_l) for spin row r
-// of site s; adds wv_r to up[] and -+ hcode B^H-row t to lo[] (INIT: sets
-// them -- the first hop of a thread, sparing the additions to zero, which
-// IEEE arithmetic cannot drop by itself because of -0).
-template <int MU, int DIR, bool INIT>
+// of site s.  The forward hop (first) sets up[] = lo[] = its product wf (no
+// additions to zero, which IEEE arithmetic cannot drop by itself because of
+// -0); the backward hop accumulates its product wb into up[] by FMA chains
+// (up = wf + wb) and forms the lower row from the same sum: the lower spin
+// t gets hcode (wb - wf) = hcode (up - 2 wf), one FMA a real part instead of
+// a product and two additions.
+template <int MU, int DIR>
 __device__ __forceinline__ void hop_half64(const Links64& lk, const double2* __restrict__ in, int s, const Coords& c,
                                            const Geometry& g, int r, double2 (&up)[3], double2 (&lo)[3]) {
   using S = Spin<MU>;
@@ -479,26 +482,24 @@ __device__ __forceinline__ void hop_half64(const Links64& lk, const double2* __r
     const double2 l = unit_apply(__ldg(in + ((2 + bcol) * 3 + a) * V + nb), bcode, nproj);
     h[a] = flip(make_double2(u.x + l.x, u.y + l.y), nwrap);
   }
+  (void)nrec;
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    double2 tv;
     if (DIR > 0) {
       const double2 u0 = lk.get(MU, a, 0, s), u1 = lk.get(MU, a, 1, s), u2 = lk.get(MU, a, 2, s);
-      tv = cmul(u0, h[0]);
+      double2 tv = cmul(u0, h[0]);
       cmac(tv, u1, h[1]);
       cmac(tv, u2, h[2]);
+      up[a] = tv;
+      lo[a] = tv;
     } else {
       const double2 u0 = lk.get(MU, 0, a, nb), u1 = lk.get(MU, 1, a, nb), u2 = lk.get(MU, 2, a, nb);
-      tv = cmul_conj(u0, h[0]);
+      double2 tv = up[a];
+      cmac_conj(tv, u0, h[0]);
       cmac_conj(tv, u1, h[1]);
       cmac_conj(tv, u2, h[2]);
-    }
-    if (INIT) {
       up[a] = tv;
-      lo[a] = unit_apply(tv, hcode, nrec);
-    } else {
-      up[a] = cadd(up[a], tv);
-      lo[a] = cadd(lo[a], unit_apply(tv, hcode, nrec));
+      lo[a] = unit_apply(make_double2(fma(-2.0, lo[a].x, tv.x), fma(-2.0, lo[a].y, tv.y)), hcode, 0ull);
     }
   }
 }
@@ -509,8 +510,8 @@ __device__ __forceinline__ void hop_dir_half64(const Links64& lk, const double2*
   double2 up[3], lo[3];
   if (s < g.V) {
     const Coords c = site_coords(s, g);
-    hop_half64<MU, +1, true>(lk, in, s, c, g, r, up, lo);
-    hop_half64<MU, -1, false>(lk, in, s, c, g, r, up, lo);
+    hop_half64<MU, +1>(lk, in, s, c, g, r, up, lo);
+    hop_half64<MU, -1>(lk, in, s, c, g, r, up, lo);
   } else {
 #pragma unroll
     for (int a = 0; a < 3; ++a) up[a] = lo[a] = make_double2(0.0, 0.0);
