@@ -74,7 +74,7 @@ UPDATE_BYTES_PER_UNIT = 64
 STENCIL_FLOP_PER_SITE = 1368
 # DRAM traffic of one launch of the FP64 stencil kernel (cg_stencil_kernel<Stencil64>,
 # 4 rhs, 8^4) from an ncu capture; None until captured for the current kernel.
-STENCIL_FP64_TRAFFIC = None
+STENCIL_FP64_TRAFFIC = 5.565952e6  # ncu: dram read 5.565952 MB, write 0 per launch
 # DRAM traffic of one launch of each update kernel with all 128 (source,
 # shift) pairs live on this workload (ncu dram__bytes_read.sum +
 # dram__bytes_write.sum, one capture per kernel; the algorithmic bytes of such
