@@ -249,21 +249,22 @@ __global__ void f32_to_f64_kernel(const float2* __restrict__ in, double2* __rest
 }
 
 
-// ---- classical Gram-Schmidt with one re-orthogonalisation pass (CGS2), three
+// ---- classical Gram-Schmidt with one re-orthogonalisation pass (CGS2), two
 // fused launches per column ------------------------------------------------------
-// The steps of column j (j >= 1), each one launch over all elements whose
-// last block (ticket) reduces the block partials in block order:
-//   kSubProj : v -= Q[0:j] h          then partials of h = Q[0:j]^H v  (pass 2)
-//   kSubNorm : v -= Q[0:j] h          then partials of ||v||^2
-//   kScale   : v *= 1 / ||v||         then, for column j + 1 (w): partials of
-//              h = Q[0:j+1]^H w and of ||w||^2 (the start of its pass 1; the
-//              new Q_j enters from registers)
-// (column 0 starts with a kStart launch: ||Q_0||^2 only).  R[a][j] gathers
-// both passes' h; R[j][j] = ||v||; a column whose norm fell below 1e-15 of
-// the original is dependent and becomes zero (R[j][j] = 0).  Per thread:
-// one element (the grid covers n), the projections in tiles of kPT columns
-// reduced by warp shuffles and one pass over the warps.
-enum CgsMode : int { kStart = 0, kSubProj = 1, kSubNorm = 2, kScale = 3 };
+// The columns are kept unnormalised (v_a, with nu_a^2 = ||v_a||^2 after both
+// passes) until one final scaling launch; the projection on Q_a = v_a / nu_a
+// is w -= v_a c_a with c_a = (v_a^H w) / nu_a^2 and R[a][j] += (v_a^H w) / nu_a.
+// Column j (w = v_j) takes two launches, each over all elements, whose last
+// block (ticket) reduces the block partials in block order:
+//   kSubProj : w -= sum_a v_a c_a (pass 1)   then partials of v_a^H w (pass 2)
+//   kSubNext : w -= sum_a v_a c'_a (pass 2)  then partials of ||w||^2, and for
+//              column j + 1 (u): partials of v_a^H u (a <= j, v_j from
+//              registers) and ||u||^2; the last block forms nu_j^2 first
+// and kStart gives column 0's norm; a column whose norm fell below 1e-15 of
+// its original is dependent: Q_j = 0, R[j][j] = 0 and c_j = 0 from then on.
+// Per thread: one element (the grid covers n); the projections in tiles of
+// kPT columns, reduced by halving warp exchanges and one pass over the warps.
+enum CgsMode : int { kStart = 0, kSubProj = 1, kSubNext = 2, kFinal = 3 };
 
 // Warp sums of 16 values at once by halving exchanges: at the step with
 // offset O a lane keeps one half of its values and adds the partner's copy of
@@ -294,31 +295,41 @@ constexpr int kCgsMaxCols = 128;
 
 struct CgsState {
   double2* partial;   // [kCgsMaxCols][nb]
-  double* npart;      // [nb]
-  double2* h;         // [kCgsMaxCols]
-  double* scal;       // [0] ||v_orig||^2 of the current column, [1] ||v||^2, [2] 1 / ||v||
+  double* npart;      // [2][nb]: ||w||^2, ||u||^2
+  double2* c;         // [kCgsMaxCols] subtraction coefficients of the next launch
+  double* inv_nu2;    // [kCgsMaxCols] 1 / nu_a^2 (0: dependent)
+  double* inv_nu;     // [kCgsMaxCols] 1 / nu_a   (0: dependent)
+  double* orig2;      // [kCgsMaxCols] ||v_a||^2 before the projections
   unsigned* ticket;
 };
 
 __global__ void __launch_bounds__(kRedBlock)
-cgs2_step_kernel(CgsState st, double2* __restrict__ Q, long long n, int chunk, int m, int j, int mode,
+cgs2_step_kernel(CgsState st, double2* __restrict__ Q, long long n, int m, int j, int mode,
                  double2* __restrict__ R) {
-  __shared__ double2 s_h[kCgsMaxCols];
+  __shared__ double2 s_c[kCgsMaxCols];
   __shared__ double s_red[kRedBlock / 32][2 * kPT];
-  __shared__ double s_nred[kRedBlock / 32];
+  __shared__ double s_nred[2][kRedBlock / 32];
   __shared__ bool s_last;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int nb = gridDim.x;
-  const long long e = blockIdx.x * (long long)chunk + threadIdx.x;
-  const bool in = (int)threadIdx.x < chunk && e < n;
-  // 1. the update of column j
+  const long long e = blockIdx.x * (long long)kRedBlock + threadIdx.x;
+  const bool in = e < n;
+  if (mode == kFinal) {  // Q_a = v_a / nu_a for every column
+    for (int a = 0; a < m; ++a)
+      if (in) {
+        const double s = st.inv_nu[a];
+        double2 x = Q[(long long)a * n + e];
+        Q[(long long)a * n + e] = make_double2(x.x * s, x.y * s);
+      }
+    return;
+  }
+  // 1. the subtraction w -= sum_a v_a c_a on column j (kPT loads in flight)
   double2 x = make_double2(0.0, 0.0);
-  if (mode == kSubProj || mode == kSubNorm) {
-    for (int a = threadIdx.x; a < j; a += kRedBlock) s_h[a] = st.h[a];
+  if (in) x = Q[(long long)j * n + e];
+  if (mode == kSubProj || mode == kSubNext) {
+    for (int a = threadIdx.x; a < j; a += kRedBlock) s_c[a] = st.c[a];
     __syncthreads();
     if (in) {
-      x = Q[(long long)j * n + e];
-      // kPT loads in flight at a time; the subtractions in column order
       for (int a0 = 0; a0 < j; a0 += kPT) {
         double2 q[kPT];
 #pragma unroll
@@ -326,7 +337,7 @@ cgs2_step_kernel(CgsState st, double2* __restrict__ Q, long long n, int chunk, i
 #pragma unroll
         for (int c = 0; c < kPT; ++c) {
           if (a0 + c < j) {
-            const double2 h = s_h[a0 + c];
+            const double2 h = s_c[a0 + c];
             x.x -= q[c].x * h.x - q[c].y * h.y;
             x.y -= q[c].x * h.y + q[c].y * h.x;
           }
@@ -334,31 +345,21 @@ cgs2_step_kernel(CgsState st, double2* __restrict__ Q, long long n, int chunk, i
       }
       Q[(long long)j * n + e] = x;
     }
-  } else if (mode == kScale) {
-    const double inv = st.scal[2];
-    if (in) {
-      x = Q[(long long)j * n + e];
-      x.x *= inv;
-      x.y *= inv;
-      Q[(long long)j * n + e] = x;
-    }
   }
-  // 2. partials: of h for column jp against its first np columns, of a norm
-  const int jp = mode == kScale ? j + 1 : j;  // the column being projected
-  const int np = mode == kSubNorm ? 0 : (mode == kStart ? 0 : jp);
-  const bool want_norm = mode != kSubProj;
-  if (mode == kScale && jp >= m) return;  // last column: scaling only
-  double2 y = x;                           // the vector the partials are of
-  if (mode == kScale) y = in ? Q[(long long)jp * n + e] : make_double2(0.0, 0.0);
-  else if (mode == kStart) y = in ? Q[(long long)j * n + e] : make_double2(0.0, 0.0);
+  // 2. partials: projections of column jp on its first np columns, norms
+  const int jp = mode == kSubNext ? j + 1 : j;
+  const bool next = mode == kSubNext && jp < m;
+  const int np = mode == kSubProj ? j : (next ? jp : 0);
+  double2 y = x;  // the vector being projected
+  if (next) y = in ? Q[(long long)jp * n + e] : make_double2(0.0, 0.0);
   for (int a0 = 0; a0 < np; a0 += kPT) {
-    double acc[2 * kPT];  // re, im of conj(Q_a) y for kPT columns
+    double acc[2 * kPT];  // re, im of conj(v_a) y for kPT columns
 #pragma unroll
     for (int c = 0; c < kPT; ++c) {
       acc[2 * c] = acc[2 * c + 1] = 0.0;
       const int a = a0 + c;
       if (in && a < np) {
-        const double2 q = (mode == kScale && a == j) ? x : Q[(long long)a * n + e];
+        const double2 q = (next && a == j) ? x : Q[(long long)a * n + e];
         acc[2 * c] = fma(q.x, y.x, q.y * y.y);
         acc[2 * c + 1] = fma(q.x, y.y, -q.y * y.x);
       }
@@ -374,15 +375,23 @@ cgs2_step_kernel(CgsState st, double2* __restrict__ Q, long long n, int chunk, i
     }
     __syncthreads();
   }
-  if (want_norm) {
-    double v2 = in ? fma(y.x, y.x, y.y * y.y) : 0.0;
-    v2 = warp_sum(v2);
-    if (lane == 0) s_nred[w] = v2;
+  // norms: kStart / kSubNext: ||w||^2 of column j; kSubNext with a next
+  // column: also ||u||^2
+  const bool norm_w = mode == kStart || mode == kSubNext;
+  if (norm_w || next) {
+    double v0 = in ? fma(x.x, x.x, x.y * x.y) : 0.0;
+    double v1 = (next && in) ? fma(y.x, y.x, y.y * y.y) : 0.0;
+    v0 = warp_sum(v0);
+    v1 = warp_sum(v1);
+    if (lane == 0) {
+      s_nred[0][w] = v0;
+      s_nred[1][w] = v1;
+    }
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 2) {
       double t = 0.0;
-      for (int ww = 0; ww < kRedBlock / 32; ++ww) t += s_nred[ww];
-      st.npart[blockIdx.x] = t;
+      for (int ww = 0; ww < kRedBlock / 32; ++ww) t += s_nred[threadIdx.x][ww];
+      st.npart[threadIdx.x * nb + blockIdx.x] = t;
     }
   }
   // 3. the last block reduces the partials in block order
@@ -393,6 +402,25 @@ cgs2_step_kernel(CgsState st, double2* __restrict__ Q, long long n, int chunk, i
   __syncthreads();
   if (!s_last) return;
   __threadfence();
+  if (norm_w || next) {  // norms first: nu_j^2 enters the coefficients below
+    if (w < 2 && (w == 0 ? norm_w : next)) {
+      double t = 0.0;
+      for (int b = lane; b < nb; b += 32) t += __ldcg(st.npart + w * nb + b);
+      t = warp_sum(t);
+      if (lane == 0) {
+        if (w == 0) {
+          if (mode == kStart) st.orig2[j] = t;
+          const bool dep = !(t > 1e-30 * (mode == kStart ? t : st.orig2[j]));
+          st.inv_nu2[j] = dep ? 0.0 : 1.0 / t;
+          st.inv_nu[j] = dep ? 0.0 : 1.0 / sqrt(t);
+          R[(long long)j * m + j] = make_double2(dep ? 0.0 : sqrt(t), 0.0);
+        } else {
+          st.orig2[jp] = t;
+        }
+      }
+    }
+    __syncthreads();
+  }
   // warp w: columns [a0, a0 + kPT) for a0 = kPT w, kPT (w + 8), ...
   for (int a0 = kPT * w; a0 < np; a0 += kPT * (kRedBlock / 32)) {
     double acc[2 * kPT];
@@ -411,23 +439,10 @@ cgs2_step_kernel(CgsState st, double2* __restrict__ Q, long long n, int chunk, i
     const double t = warp_reduce16(acc);
     const int a = a0 + (lane >> 2), comp = (lane >> 1) & 1;
     if ((lane & 1) == 0 && a < np) {
-      reinterpret_cast<double*>(st.h)[2 * a + comp] = t;
-      reinterpret_cast<double*>(R)[2 * ((long long)a * m + jp) + comp] += t;
-    }
-  }
-  if (want_norm && w == 0) {
-    double t = 0.0;
-    for (int b = lane; b < nb; b += 32) t += __ldcg(st.npart + b);
-    t = warp_sum(t);
-    if (lane == 0) {
-      if (mode == kSubNorm) {
-        const bool dep = !(t > 1e-30 * st.scal[0]);
-        st.scal[1] = t;
-        st.scal[2] = dep ? 0.0 : 1.0 / sqrt(t);
-        R[(long long)j * m + j] = make_double2(dep ? 0.0 : sqrt(t), 0.0);
-      } else {
-        st.scal[0] = t;  // the original norm of column jp
-      }
+      // v_a^H y: subtraction coefficient / nu_a^2, R entry / nu_a
+      const double i2 = __ldcg(st.inv_nu2 + a), i1 = __ldcg(st.inv_nu + a);
+      reinterpret_cast<double*>(st.c)[2 * a + comp] = t * i2;
+      reinterpret_cast<double*>(R)[2 * ((long long)a * m + jp) + comp] += t * i1;
     }
   }
   if (threadIdx.x == 0) *st.ticket = 0u;
@@ -508,34 +523,37 @@ int gram(const double2* X, int mx, const double2* Y, int my, long long n, double
 int cgs2(const double2* S, int m, long long n, double2* Q, double2* R, DevBuf& scratch, cudaStream_t s) {
   if (m > kCgsMaxCols) return fail(SSQCD_ERR_ARG, "CGS2 of more than 128 columns");
   if (m <= 0 || n <= 0) return SSQCD_OK;
-  // one element per thread (measured faster here than whole numbers of
-  // blocks per SM with shorter chunks: 3.57 against 3.85 ms for 32 columns
-  // of n = 49152)
-  const long long nbl = (n + kRedBlock - 1) / kRedBlock;
+  const long long nbl = (n + kRedBlock - 1) / kRedBlock;  // one element per thread
   if (nbl > (1LL << 30)) return fail(SSQCD_ERR_ARG, "CGS2 vectors too long");
   const int nb = (int)nbl;
-  const int chunk = kRedBlock;
   const size_t o_part = 0, o_np = o_part + sizeof(double2) * (size_t)kCgsMaxCols * nb,
-               o_h = (o_np + sizeof(double) * nb + 255) / 256 * 256, o_sc = o_h + sizeof(double2) * kCgsMaxCols,
-               o_t = o_sc + sizeof(double) * 4, total = o_t + 256;
+               o_c = (o_np + sizeof(double) * 2 * nb + 255) / 256 * 256, o_i2 = o_c + sizeof(double2) * kCgsMaxCols,
+               o_i1 = o_i2 + sizeof(double) * kCgsMaxCols, o_or = o_i1 + sizeof(double) * kCgsMaxCols,
+               o_t = o_or + sizeof(double) * kCgsMaxCols, total = o_t + 256;
   SS_TRY(scratch.alloc(total));
   char* base = scratch.as<char>();
   CgsState st{reinterpret_cast<double2*>(base + o_part), reinterpret_cast<double*>(base + o_np),
-              reinterpret_cast<double2*>(base + o_h), reinterpret_cast<double*>(base + o_sc),
+              reinterpret_cast<double2*>(base + o_c), reinterpret_cast<double*>(base + o_i2),
+              reinterpret_cast<double*>(base + o_i1), reinterpret_cast<double*>(base + o_or),
               reinterpret_cast<unsigned*>(base + o_t)};
   SS_CUDA(cudaMemsetAsync(st.ticket, 0, sizeof(unsigned), s));
   SS_CUDA(cudaMemsetAsync(R, 0, sizeof(double2) * m * m, s));
   SS_CUDA(cudaMemcpyAsync(Q, S, sizeof(double2) * n * m, cudaMemcpyDeviceToDevice, s));
   auto step = [&](int j, int mode) {
-    cgs2_step_kernel<<<nb, kRedBlock, 0, s>>>(st, Q, n, chunk, m, j, mode, R);
+    cgs2_step_kernel<<<nb, kRedBlock, 0, s>>>(st, Q, n, m, j, mode, R);
     count_launches(1);
   };
-  step(0, kStart);
-  for (int j = 0; j < m; ++j) {
-    if (j > 0) step(j, kSubProj);  // first pass's h came with the previous kScale (or kStart)
-    step(j, kSubNorm);             // j = 0: no projection, the norm only
-    step(j, kScale);               // and the start of column j + 1
+  step(0, kStart);    // nu_0 (column 0 has nothing to project on)
+  if (m > 1) {
+    // column 0's partials for column 1 (pass 1) come from a kSubNext on
+    // column 0 with nothing to subtract
+    step(0, kSubNext);
   }
+  for (int j = 1; j < m; ++j) {
+    step(j, kSubProj);  // pass 1 subtraction, pass 2 partials
+    step(j, kSubNext);  // pass 2 subtraction, nu_j, pass 1 partials of column j + 1
+  }
+  step(0, kFinal);
   SS_CHECK_LAUNCH();
   return SSQCD_OK;
 }
