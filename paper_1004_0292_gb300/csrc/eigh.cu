@@ -175,41 +175,52 @@ int small_eigh(int m, const double2* a_in, double* evals, double2* evecs) {
 // Rayleigh-Ritz basis relies on.
 int small_svd_left(int m, const double2* a_in, double* sigma, double2* U) {
   if (m <= 0) return fail(SSQCD_ERR_ARG, "small_svd_left: m must be > 0");
-  std::vector<cd> B((size_t)m * m);  // column-major: B[c * m + r]
+  // columns as separate real and imaginary arrays, column-major (Bre[c m + r]);
+  // the complex products are written out in real arithmetic (no library
+  // complex multiplication with its special-value handling in the inner loops)
+  std::vector<double> Bre((size_t)m * m), Bim((size_t)m * m);
   for (int r = 0; r < m; ++r)
-    for (int c = 0; c < m; ++c) B[(size_t)c * m + r] = cd(a_in[(size_t)r * m + c].x, a_in[(size_t)r * m + c].y);
+    for (int c = 0; c < m; ++c) {
+      Bre[(size_t)c * m + r] = a_in[(size_t)r * m + c].x;
+      Bim[(size_t)c * m + r] = a_in[(size_t)r * m + c].y;
+    }
   bool rotated = true;
   for (int sweep = 0; sweep < 60 && rotated; ++sweep) {
     rotated = false;
     for (int p = 0; p < m - 1; ++p)
       for (int q = p + 1; q < m; ++q) {
-        cd* bp = &B[(size_t)p * m];
-        cd* bq = &B[(size_t)q * m];
-        double alpha = 0.0, beta = 0.0;
-        cd g(0.0, 0.0);
+        double* pr = &Bre[(size_t)p * m];
+        double* pi = &Bim[(size_t)p * m];
+        double* qr = &Bre[(size_t)q * m];
+        double* qi = &Bim[(size_t)q * m];
+        double alpha = 0.0, beta = 0.0, gr = 0.0, gi = 0.0;  // |b_p|^2, |b_q|^2, b_p^H b_q
         for (int r = 0; r < m; ++r) {
-          alpha += std::norm(bp[r]);
-          beta += std::norm(bq[r]);
-          g += std::conj(bp[r]) * bq[r];
+          alpha += pr[r] * pr[r] + pi[r] * pi[r];
+          beta += qr[r] * qr[r] + qi[r] * qi[r];
+          gr += pr[r] * qr[r] + pi[r] * qi[r];
+          gi += pr[r] * qi[r] - pi[r] * qr[r];
         }
-        const double ag = std::abs(g);
+        const double ag = std::sqrt(gr * gr + gi * gi);
         if (ag == 0.0 || ag <= DBL_EPSILON * std::sqrt(alpha * beta)) continue;
         rotated = true;
-        const cd ph = g / ag;  // b_q e^{-i phi} makes the coupling real
+        const double phr = gr / ag, phi = -gi / ag;  // conj(g) / |g|: b_q e^{-i phi} makes the coupling real
         const double zeta = (beta - alpha) / (2.0 * ag);
         const double t = std::copysign(1.0, zeta) / (std::fabs(zeta) + std::sqrt(1.0 + zeta * zeta));
         const double c = 1.0 / std::sqrt(1.0 + t * t), s = c * t;
         for (int r = 0; r < m; ++r) {
-          const cd x = bp[r], y = bq[r] * std::conj(ph);
-          bp[r] = c * x - s * y;
-          bq[r] = s * x + c * y;
+          const double xr = pr[r], xi = pi[r];
+          const double yr = qr[r] * phr - qi[r] * phi, yi = qr[r] * phi + qi[r] * phr;
+          pr[r] = c * xr - s * yr;
+          pi[r] = c * xi - s * yi;
+          qr[r] = s * xr + c * yr;
+          qi[r] = s * xi + c * yi;
         }
       }
   }
   std::vector<double> nrm(m);
   for (int c = 0; c < m; ++c) {
     double s2 = 0.0;
-    for (int r = 0; r < m; ++r) s2 += std::norm(B[(size_t)c * m + r]);
+    for (int r = 0; r < m; ++r) s2 += Bre[(size_t)c * m + r] * Bre[(size_t)c * m + r] + Bim[(size_t)c * m + r] * Bim[(size_t)c * m + r];
     nrm[c] = std::sqrt(s2);
   }
   std::vector<int> order(m);
@@ -219,10 +230,8 @@ int small_svd_left(int m, const double2* a_in, double* sigma, double2* U) {
     const int c = order[k];
     sigma[k] = nrm[c];
     const double inv = nrm[c] > 0.0 ? 1.0 / nrm[c] : 0.0;
-    for (int r = 0; r < m; ++r) {
-      const cd u = B[(size_t)c * m + r] * inv;
-      U[(size_t)r * m + k] = make_double2(u.real(), u.imag());
-    }
+    for (int r = 0; r < m; ++r)
+      U[(size_t)r * m + k] = make_double2(Bre[(size_t)c * m + r] * inv, Bim[(size_t)c * m + r] * inv);
   }
   return SSQCD_OK;
 }
