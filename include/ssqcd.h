@@ -161,7 +161,9 @@ typedef struct {
   double ms_k_stencil;      /* stencil q = K p with the (p, q) partials and alpha */
   double ms_k_seed;         /* seed update r -= alpha q, shift scalars, freezing  */
   double ms_k_scalars;      /* seed direction p = r + beta p                      */
-  double ms_k_update;       /* fused multi-shift update                           */
+  double ms_k_update;       /* fused multi-shift update (update form), or the
+                               shift-scalar kernel beside the chain (Krylov-basis
+                               form: opts.basis)                                  */
   long long timed_shift_updates; /* (source, shift) updates in the timed iterations */
   int    basis;           /* 1: moments from the stored seed residuals; 2: began
                              so and switched to shift-vector updates at the
