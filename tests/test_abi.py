@@ -79,3 +79,30 @@ def test_argument_errors(ss):
         ss.create_lattice((4, 4, 0, 4), 0.1)
     with pytest.raises(ss.SsqcdError):
         ss.create_lattice((4, 4, 4, 4), 0.1, bc_t=0)
+
+
+def test_struct_layouts_match_the_header(ss, tmp_path):
+    # the ctypes mirrors of ssqcd_opts / ssqcd_stats against a C compiler's
+    # view of include/ssqcd.h (sizes and every field offset)
+    import os
+    import shutil
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "ssqcd.h"', "int main(void) {"]
+    for cname, py in (("ssqcd_opts", ss.Opts), ("ssqcd_stats", ss.Stats)):
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f'printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", inc, str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    c_side = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for cname, py in (("ssqcd_opts", ss.Opts), ("ssqcd_stats", ss.Stats)):
+        assert c_side[(cname, "size")] == ctypes.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert c_side[(cname, f)] == getattr(py, f).offset, (cname, f)
