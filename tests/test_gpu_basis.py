@@ -127,3 +127,29 @@ def test_basis_eigenpairs_full_size_match_update_form():
     good1, good0 = e1[r1 <= 1e-8], e0[r0 <= 1e-8]
     assert len(good1) == len(good0) >= 12
     assert np.max(np.abs(good1 - good0)) <= 1e-12 * np.max(np.abs(good0))
+
+
+def test_switch_to_updates_float_float(case):
+    # the same switch with float-float residuals and shift vectors (SSQCD_DF)
+    ss, U, v, iv, ref, bound = case
+    lat = ss.create_lattice(DIMS, KAPPA, BC, precision=ss.DF)
+    ss.upload_gauge(lat, U)
+    n = 12 * synthetic.volume(DIMS)
+    block = 16 * L * n * 16
+    s, st = ss.ss_moments(lat, iv, N, M, v, beta=BETA, nprime=NPRIME, basis=1, basis_max_bytes=2.5 * block)
+    assert st["basis"] == 2
+    _check_moments(s, ref, bound * 32.0, v)
+
+
+def test_zero_source_has_zero_moments(case):
+    # a zero source starts frozen: no residual of it enters, its moments are 0
+    ss, U, v, iv, ref, bound = case
+    lat = ss.create_lattice(DIMS, KAPPA, BC)
+    ss.upload_gauge(lat, U)
+    v2 = v.copy()
+    v2[1] = 0.0
+    s, st = ss.ss_moments(lat, iv, N, M, v2, beta=BETA, nprime=NPRIME)
+    assert st["basis"] == 1
+    assert np.all(s[1] == 0.0)
+    for k in range(M):
+        assert np.linalg.norm(s[0, k] - ref[0, k]) <= bound[k] * np.linalg.norm(v[0])
