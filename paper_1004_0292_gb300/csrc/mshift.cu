@@ -436,16 +436,21 @@ cg_stencil_kernel(Control c, int L, int par, Geometry g, Op op, double sigma, co
   __syncthreads();
   if (!s_last) return;
   __threadfence();
-  // warp w sums the partials of sources w, w + kWarps, ... in a fixed order
+  // warp w sums the partials of sources w, w + kWarps, ... in a fixed order,
+  // eight loads in flight a lane (this tail runs on one SM while the rest
+  // of the GPU waits for alpha)
   for (int ls = w; ls < L; ls += kWarps) {
-    double a0 = 0.0, a1 = 0.0;
-    int b = lane;
-    for (; b + 32 < nbw; b += 64) {
-      a0 += __ldcg(c.partial + (size_t)ls * nbw + b);
-      a1 += __ldcg(c.partial + (size_t)ls * nbw + b + 32);
+    double a = 0.0;
+    for (int b0 = lane; b0 < nbw; b0 += 32 * 8) {
+      double t[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int b = b0 + 32 * i;
+        t[i] = b < nbw ? __ldcg(c.partial + (size_t)ls * nbw + b) : 0.0;
+      }
+      a += ((t[0] + t[1]) + (t[2] + t[3])) + ((t[4] + t[5]) + (t[6] + t[7]));
     }
-    if (b < nbw) a0 += __ldcg(c.partial + (size_t)ls * nbw + b);
-    const double a = warp_sum(a0 + a1);
+    a = warp_sum(a);
     if (lane == 0) sums[ls] = a;
   }
   __syncthreads();
