@@ -237,7 +237,11 @@ def run_ours(args):
     # moments from the stored residuals: 8 flop per complex FMA, M moments x
     # (iterations + 1) residuals x n elements x L sources
     comb_flops = 8 * w["M"] * (plain[-1]["iterations"] + 1) * n * w["L"]
-    update_form = None if args.no_update_form else run_update_form(step, stream, flush, args, n, world)
+    update_form = None
+    if not args.no_update_form:
+        update_form = run_update_form(step, stream, flush, args, n, world)
+        update_form["float_float_shift_vectors"] = run_dfshift_update(ss, w, U_d, src_d, stream, flush, args, n,
+                                                                      world, peaks)
 
     # ---- end to end through the C ABI with host buffers ----
     e2e = None
@@ -409,6 +413,43 @@ def run_update_form(step, stream, flush, args, n, world):
                               "achieved_tflops": tf, "frac_fp64_peak": tf / FP64_PEAK_TFLOPS if tf else None,
                               "avg_launch_us": 1e3 * ms_upd / it, "traffic": UPDATE_FP64_TRAFFIC_ALL_LIVE,
                               "traffic_note": "one launch with all 128 shift vectors live; algorithmic 402.7 MB"}}
+
+
+def run_dfshift_update(ss, w, U_d, src_d, stream, flush, args, n, world, peaks):
+    """The update form with float-float shift vectors (SSQCD_FP64_DFSHIFT): its
+    shift update, the TMA-fed kernel, is the HBM-bound kernel of the path
+    (64 B per element-shift read and written)."""
+    lat = ss.create_lattice(w["dims"], w["kappa"], w["bc_t"], precision=ss.FP64_DFSHIFT, stream=stream)
+    ss.upload_gauge(lat, U_d)
+
+    def step(**kw):
+        res = ss.ss_solve(lat, w["interval"], w["N"], w["M"], src_d, beta=w["beta"], nprime=w["nprime"],
+                          tol=w["tol"])
+        if res.status != ss.OK:
+            raise RuntimeError(f"solve failed with status {res.status}: {res.error}")
+        ev, _, rs, st = ss.ss_eigpairs(res, want_vectors=False)
+        return ev, rs, st
+
+    for _ in range(args.warmup):
+        step()
+    times, counts, plain, _ = timed_steps(step, flush, stream, args.steps)
+    ms, pairs = reduce_job(float(sum(times)), float(sum(counts)), world, "cuda")
+    ss.set_kernel_timing(True)
+    _, _, stats, _ = timed_steps(step, flush, stream, KERNEL_TIMING_STEPS)
+    ss.set_kernel_timing(False)
+    del lat
+    ms_upd = sum(s["ms_k_update"] for s in stats)
+    units = sum(s["timed_shift_updates"] for s in stats) * n
+    it = max(1, sum(s["launches_update"] for s in stats))
+    gbs = UPDATE_BYTES_PER_UNIT * units / (ms_upd / 1e3) / 1e9 if ms_upd > 0 else None
+    return {"value": pairs / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / args.steps,
+            "cg_us_per_iteration": 1e3 * plain[-1]["ms_cg"] / max(1, plain[-1]["iterations"]),
+            "update_kernel": {"kernel": "cg_update_tma_kernel (fused multi-shift update, float-float, bulk-copy fed)",
+                              "bound": "hbm", "achieved_gbs": gbs, "peak_gbs": peaks["hbm_gbs"],
+                              "frac": gbs / peaks["hbm_gbs"] if gbs else None, "avg_launch_us": 1e3 * ms_upd / it,
+                              "traffic": UPDATE_TMA_TRAFFIC_ALL_LIVE,
+                              "note": "in the loop, beside the next iteration's stencil; algorithmic 64 B per "
+                                      "element-shift"}}
 
 
 STENCIL_LARGE = dict(dims=(16, 16, 16, 32), kappa=0.135, eps=0.5, gauge_seed=4, rhs=8, reps=20)
