@@ -292,11 +292,11 @@ namespace {
 // left singular vectors of S whose singular value exceeds rank_tol times the
 // largest (the paper leaves the orthogonalisation open).  Returns r, Q [r][n].
 int orthonormalise(const double2* S, int m, long long n, double rank_tol, DevBuf& Q, int& r, DevBuf& tmp,
-                   DevBuf& scratch, cudaStream_t st) {
+                   DevBuf& scratch, cudaStream_t st, const cudaEvent_t* ready = nullptr, int group = 0) {
   DevBuf Rd, Cd;
   SS_TRY(Rd.alloc(sizeof(double2) * m * m));
   SS_TRY(tmp.alloc(sizeof(double2) * n * m));
-  SS_TRY(cgs2(S, m, n, tmp.as<double2>(), Rd.as<double2>(), scratch, st));
+  SS_TRY(cgs2(S, m, n, tmp.as<double2>(), Rd.as<double2>(), scratch, st, ready, group));
   std::vector<double2> R((size_t)m * m), U((size_t)m * m);
   std::vector<double> sig(m);
   SS_CUDA(cudaMemcpyAsync(R.data(), Rd.p, sizeof(double2) * m * m, cudaMemcpyDeviceToHost, st));
@@ -327,11 +327,12 @@ namespace {
 // residuals.  Appends to evals / resid and returns X in `X`.
 int rayleigh_ritz_window(ssqcd_lattice lat, const double2* S, int m, double rank_tol, bool refine, double lo,
                          double hi, bool hi_open, std::vector<double>& evals, std::vector<double>& resid, DevBuf& X,
-                         int& cnt, int& rank, DevBuf& scratch, cudaStream_t st) {
+                         int& cnt, int& rank, DevBuf& scratch, cudaStream_t st, const cudaEvent_t* ready = nullptr,
+                         int group = 0) {
   const long long n = 12LL * lat->g.V;
   DevBuf Q, tmp, AQ, Gd;
   int r = 0;
-  SS_TRY(orthonormalise(S, m, n, rank_tol, Q, r, tmp, scratch, st));
+  SS_TRY(orthonormalise(S, m, n, rank_tol, Q, r, tmp, scratch, st, ready, group));
   tmp.release();
   rank = r;
   SS_TRY(AQ.alloc(sizeof(double2) * n * r));
@@ -668,17 +669,53 @@ int extract_eigenpairs(ssqcd_lattice lat, const SolvePlan& P, DevBuf& yd, Krylov
   const int m = MM * L;
   std::vector<DevBuf> Xk(K);
   std::vector<int> cntk(K, 0);
+  // Moments from the stored residuals and Rayleigh-Ritz overlap: the last
+  // source's moments form on a side stream, and the CGS2 of the basis waits
+  // per source, so it orthogonalises the other sources' moments meanwhile.  The moment
+  // scratch stays alive, and st waits for every side event, until the end.
+  struct Overlap {
+    cudaStream_t side = nullptr;
+    std::vector<cudaEvent_t> ev;
+    cudaStream_t st = nullptr;
+    ~Overlap() {
+      if (st != nullptr && !ev.empty()) cudaStreamWaitEvent(st, ev.back(), 0);  // error paths: st after the side work
+      for (auto e : ev) cudaEventDestroy(e);
+      if (side) cudaStreamDestroy(side);
+    }
+  } ov;
+  DevBuf mscratch;
+  const bool overlap = kb.S > 0 && !P.hankel && L > 1;
+  if (overlap) {
+    SS_CUDA(cudaStreamCreateWithFlags(&ov.side, cudaStreamNonBlocking));
+    ov.ev.resize(L);
+    for (auto& e : ov.ev) SS_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    ov.st = st;
+  }
+  cudaEvent_t e_mom = nullptr;  // the end of the last window's moments (side stream when overlapped)
+  struct EvOne {
+    cudaEvent_t* e;
+    ~EvOne() {
+      if (*e) cudaEventDestroy(*e);
+    }
+  } ev_mom{&e_mom};
   for (int k = 0; k < K; ++k) {
     // moments of window k (Eq. 2), S = [L][MM][n]
     SS_TRY(S.alloc(sizeof(double2) * n * m));
-    if (kb.S > 0)
+    if (overlap)
+      SS_TRY(basis_moments(kb, P.coefk[k].data(), MM, S.as<double2>(), mscratch, st, ov.side, ov.ev.data()));
+    else if (kb.S > 0)
       SS_TRY(basis_moments(kb, P.coefk[k].data(), MM, S.as<double2>(), scratch, st));
     else
       SS_TRY(moments_device(yd.as<double2>(), NU, MM, L, n, P.coefk[k].data(), S.as<double2>(), scratch, st));
     if (k == K - 1) {
-      cudaEventRecord(e1, st);
-      yd.release();
-      kb.release();
+      if (overlap) {
+        SS_CUDA(cudaEventCreate(&e_mom));
+        SS_CUDA(cudaEventRecord(e_mom, ov.side));
+      } else {
+        cudaEventRecord(e1, st);
+        yd.release();
+        kb.release();
+      }
     }
     // Rayleigh-Ritz (or the Hankel pencil) and acceptance in the window's core
     const double lo = (K == 1) ? a : a + k * core;
@@ -694,7 +731,9 @@ int extract_eigenpairs(ssqcd_lattice lat, const SolvePlan& P, DevBuf& yd, Krylov
       continue;
     }
     SS_TRY(rayleigh_ritz_window(lat, S.as<double2>(), m, P.o.rank_tol, P.o.refine != 0, lo, hi, k < K - 1,
-                                res->evals, res->residuals, Xk[k], cntk[k], rank, scratch, st));
+                                res->evals, res->residuals, Xk[k], cntk[k], rank, scratch, st,
+                                overlap ? ov.ev.data() : nullptr, MM));
+    if (k == K - 1 && overlap) kb.release();  // st has waited for every source's moments
     res->stats.rank += rank;
     res->stats.n_ritz += rank;
     res->stats.matvecs_rr += rank + cntk[k];
@@ -736,9 +775,12 @@ int extract_eigenpairs(ssqcd_lattice lat, const SolvePlan& P, DevBuf& yd, Krylov
   }
   cudaEventRecord(e2, st);
   cudaEventSynchronize(e2);
+  // overlapped: moments up to the last source's combination (side stream),
+  // Rayleigh-Ritz from there on (its start ran beside the moments)
+  const cudaEvent_t e_mid = e_mom != nullptr ? e_mom : e1;
   float ms1 = 0.f, ms2 = 0.f;
-  cudaEventElapsedTime(&ms1, e0, e1);
-  cudaEventElapsedTime(&ms2, e1, e2);
+  cudaEventElapsedTime(&ms1, e0, e_mid);
+  cudaEventElapsedTime(&ms2, e_mid, e2);
   res->stats.ms_moments = ms1;
   res->stats.ms_rr = ms2;
   return SSQCD_OK;

@@ -5,6 +5,8 @@
 // All reductions are two-stage with a fixed order (per-block partial sums,
 // then one pass over the partials in block order), so results do not depend
 // on scheduling.
+#include <algorithm>
+
 #include "internal.h"
 
 namespace ssqcd {
@@ -520,7 +522,8 @@ int gram(const double2* X, int mx, const double2* Y, int my, long long n, double
 }
 
 
-int cgs2(const double2* S, int m, long long n, double2* Q, double2* R, DevBuf& scratch, cudaStream_t s) {
+int cgs2(const double2* S, int m, long long n, double2* Q, double2* R, DevBuf& scratch, cudaStream_t s,
+         const cudaEvent_t* group_ready, int group) {
   if (m > kCgsMaxCols) return fail(SSQCD_ERR_ARG, "CGS2 of more than 128 columns");
   if (m <= 0 || n <= 0) return SSQCD_OK;
   const long long nbl = (n + kRedBlock - 1) / kRedBlock;  // one element per thread
@@ -538,19 +541,36 @@ int cgs2(const double2* S, int m, long long n, double2* Q, double2* R, DevBuf& s
               reinterpret_cast<unsigned*>(base + o_t)};
   SS_CUDA(cudaMemsetAsync(st.ticket, 0, sizeof(unsigned), s));
   SS_CUDA(cudaMemsetAsync(R, 0, sizeof(double2) * m * m, s));
-  SS_CUDA(cudaMemcpyAsync(Q, S, sizeof(double2) * n * m, cudaMemcpyDeviceToDevice, s));
+  // the columns enter Q as they are first needed; with group_ready, group g
+  // (columns [g group, (g + 1) group)) waits for its event first, so the
+  // orthogonalisation can start while later columns are still being formed
+  if (group_ready == nullptr || group <= 0) group = m;
+  int copied = 0;  // columns [0, copied) are in Q
+  auto need = [&](int j) -> int {
+    while (copied <= j) {
+      const int g = copied / group, c1 = std::min(m, copied + group);
+      if (group_ready != nullptr && group_ready[g] != nullptr) SS_CUDA(cudaStreamWaitEvent(s, group_ready[g], 0));
+      SS_CUDA(cudaMemcpyAsync(Q + (size_t)copied * n, S + (size_t)copied * n, sizeof(double2) * n * (c1 - copied),
+                              cudaMemcpyDeviceToDevice, s));
+      copied = c1;
+    }
+    return SSQCD_OK;
+  };
   auto step = [&](int j, int mode) {
     cgs2_step_kernel<<<nb, kRedBlock, 0, s>>>(st, Q, n, m, j, mode, R);
     count_launches(1);
   };
+  SS_TRY(need(0));
   step(0, kStart);    // nu_0 (column 0 has nothing to project on)
   if (m > 1) {
     // column 0's partials for column 1 (pass 1) come from a kSubNext on
     // column 0 with nothing to subtract
+    SS_TRY(need(1));
     step(0, kSubNext);
   }
   for (int j = 1; j < m; ++j) {
     step(j, kSubProj);  // pass 1 subtraction, pass 2 partials
+    if (j + 1 < m) SS_TRY(need(j + 1));
     step(j, kSubNext);  // pass 2 subtraction, nu_j, pass 1 partials of column j + 1
   }
   step(0, kFinal);

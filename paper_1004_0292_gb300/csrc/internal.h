@@ -153,7 +153,10 @@ int gram(const double2* X, int mx, const double2* Y, int my, long long n, double
 int combine(const double2* S, int ms, long long n, const double2* C, int mc, double2* Q, cudaStream_t s);
 // CGS2 QR of the m vectors S (device): Q [m][n] with orthonormal (or zero)
 // vectors and R (m x m row-major, device, upper triangular), S = Q R.
-int cgs2(const double2* S, int m, long long n, double2* Q, double2* R, DevBuf& scratch, cudaStream_t s);
+// group_ready (optional): events after which column groups of `group`
+// columns of S are complete (the orthogonalisation waits per group)
+int cgs2(const double2* S, int m, long long n, double2* Q, double2* R, DevBuf& scratch, cudaStream_t s,
+         const cudaEvent_t* group_ready = nullptr, int group = 0);
 int col_residual_norms(const double2* AX, const double2* X, const double* theta, int m, long long n,
                        double* out, DevBuf& scratch, cudaStream_t s);
 int convert_f64_to_f32(const double2* in, float2* out, long long n, cudaStream_t s);
@@ -206,8 +209,13 @@ struct KrylovBasis {
   void release();
 };
 // s_hat [L][M][n] = sum_s (sum_j coef[j][m] gam[l][j][s]) r_s; coef_host [N][M]
+// With side and src_ready (L events): sources 0 .. L-2 on st, the last one on
+// the side stream, each source followed by its event, so that the
+// orthogonalisation of the first sources' moments overlaps the combination
+// of the last (scratch must then stay allocated until st has waited for
+// every event).
 int basis_moments(const KrylovBasis& b, const double2* coef_host, int M, double2* s_hat, DevBuf& scratch,
-                  cudaStream_t st);
+                  cudaStream_t st, cudaStream_t side = nullptr, const cudaEvent_t* src_ready = nullptr);
 
 // Solves for L sources already packed on device (v: [L][12][V]); y out
 // [L][N][12][V] (device, FP64).  iters/xi: host arrays [L*N] (may be null).

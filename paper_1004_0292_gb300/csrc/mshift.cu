@@ -1508,10 +1508,10 @@ constexpr int kCombThreads = 64;
 template <typename VR, typename VO>
 __global__ void __launch_bounds__(kCombThreads, 2)
 basis_combine_kernel(char* const* __restrict__ tab, long long n, int L, const double2* __restrict__ C, int O, int S,
-                     const int* __restrict__ count, VO* __restrict__ out) {
+                     const int* __restrict__ count, VO* __restrict__ out, int l0) {
   __shared__ double s_wr[kCombTile][kCombOut], s_wi[kCombTile][kCombOut], s_ws[kCombTile][kCombOut];
   __shared__ const VR* s_p[kCombTile];
-  const int l = blockIdx.y, o0 = blockIdx.z * kCombOut;
+  const int l = blockIdx.y + l0, o0 = blockIdx.z * kCombOut;
   const int no = min(kCombOut, O - o0);
   const int Sl = count[l];
   const long long e = blockIdx.x * (long long)kCombThreads + threadIdx.x;
@@ -1564,10 +1564,10 @@ basis_combine_kernel(char* const* __restrict__ tab, long long n, int L, const do
 // sees the per-tile conversions.
 __global__ void __launch_bounds__(kCombThreads, 2)
 basis_combine_df_kernel(char* const* __restrict__ tab, long long n, int L, const double2* __restrict__ C, int O, int S,
-                        const int* __restrict__ count, double2* __restrict__ out) {
+                        const int* __restrict__ count, double2* __restrict__ out, int l0) {
   __shared__ float4 s_w[kCombTile][kCombOut];
   __shared__ const float4* s_p[kCombTile];
-  const int l = blockIdx.y, o0 = blockIdx.z * kCombOut;
+  const int l = blockIdx.y + l0, o0 = blockIdx.z * kCombOut;
   const int no = min(kCombOut, O - o0);
   const int Sl = count[l];
   const long long e = blockIdx.x * (long long)kCombThreads + threadIdx.x;
@@ -1612,11 +1612,13 @@ basis_combine_df_kernel(char* const* __restrict__ tab, long long n, int L, const
     for (int o = 0; o < no; ++o) out[((size_t)l * O + o0 + o) * n + e] = accd[o];
 }
 
+// sources [l0, l0 + nl) of L (all by default)
 template <typename VR, typename VO>
 int launch_combine(char* const* tab, long long n, int L, const double2* C, int O, int S, const int* count, VO* out,
-                   cudaStream_t st) {
-  const dim3 grid((unsigned)((n + kCombThreads - 1) / kCombThreads), L, (O + kCombOut - 1) / kCombOut);
-  basis_combine_kernel<VR, VO><<<grid, kCombThreads, 0, st>>>(tab, n, L, C, O, S, count, out);
+                   cudaStream_t st, int l0 = 0, int nl = -1) {
+  if (nl < 0) nl = L - l0;
+  const dim3 grid((unsigned)((n + kCombThreads - 1) / kCombThreads), nl, (O + kCombOut - 1) / kCombOut);
+  basis_combine_kernel<VR, VO><<<grid, kCombThreads, 0, st>>>(tab, n, L, C, O, S, count, out, l0);
   SS_CHECK_LAUNCH();
   count_launches(1);
   return SSQCD_OK;
@@ -2581,7 +2583,7 @@ void KrylovBasis::release() {
 }
 
 int basis_moments(const KrylovBasis& b, const double2* coef_host, int M, double2* s_hat, DevBuf& scratch,
-                  cudaStream_t st) {
+                  cudaStream_t st, cudaStream_t side, const cudaEvent_t* src_ready) {
   const int N = b.N, L = b.L, S = b.S;
   const size_t w_bytes = (sizeof(double2) * (size_t)N * M + 255) / 256 * 256;
   SS_TRY(scratch.alloc(w_bytes + sizeof(double2) * (size_t)L * M * S));
@@ -2592,15 +2594,27 @@ int basis_moments(const KrylovBasis& b, const double2* coef_host, int M, double2
   basis_window_kernel<<<(unsigned)((cnt + 255) / 256), 256, 0, st>>>(b.gam.as<double2>(), W, N, M, L, S, G);
   SS_CHECK_LAUNCH();
   count_launches(1);
-  if (b.df) {
-    const dim3 grid((unsigned)((b.n + kCombThreads - 1) / kCombThreads), L, (M + kCombOut - 1) / kCombOut);
-    basis_combine_df_kernel<<<grid, kCombThreads, 0, st>>>(b.tab.as<char*>(), b.n, L, G, M, S, b.count.as<int>(),
-                                                           s_hat);
-    SS_CHECK_LAUNCH();
-    count_launches(1);
-    return SSQCD_OK;
-  }
-  return launch_combine<double2, double2>(b.tab.as<char*>(), b.n, L, G, M, S, b.count.as<int>(), s_hat, st);
+  auto one = [&](int l0, int nl, cudaStream_t s) -> int {
+    if (b.df) {
+      const dim3 grid((unsigned)((b.n + kCombThreads - 1) / kCombThreads), nl, (M + kCombOut - 1) / kCombOut);
+      basis_combine_df_kernel<<<grid, kCombThreads, 0, s>>>(b.tab.as<char*>(), b.n, L, G, M, S, b.count.as<int>(),
+                                                            s_hat, l0);
+      SS_CHECK_LAUNCH();
+      count_launches(1);
+      return SSQCD_OK;
+    }
+    return launch_combine<double2, double2>(b.tab.as<char*>(), b.n, L, G, M, S, b.count.as<int>(), s_hat, s, l0,
+                                            nl);
+  };
+  if (side == nullptr || src_ready == nullptr || L == 1) return one(0, L, st);
+  // sources 0 .. L-2 in one launch on st (the orthogonalisation of their
+  // moments follows in stream order), the last one on the side stream
+  SS_TRY(one(0, L - 1, st));
+  for (int l = 0; l < L - 1; ++l) SS_CUDA(cudaEventRecord(src_ready[l], st));
+  SS_CUDA(cudaStreamWaitEvent(side, src_ready[0], 0));  // G and W are on st before
+  SS_TRY(one(L - 1, 1, side));
+  SS_CUDA(cudaEventRecord(src_ready[L - 1], side));
+  return SSQCD_OK;
 }
 
 }  // namespace ssqcd
