@@ -19,8 +19,10 @@
 // A shift stops ("freezes") once |xi_{k+1}| ||r_{k+1}|| <= tol ||v|| (the
 // paper's stopping rule ||r_j|| / ||v|| <= tol, Section 3 and Section 4).
 //
-// One iteration = three kernels, each finishing its reduction in its last
-// block (fixed summation order, no host round trip):
+// Two forms of the loop; every kernel finishes its reduction in its last
+// block (fixed summation order, no host round trip).
+//
+// Update form (opts.basis = 0; the path of ssqcd_shifted_cg): per iteration
 //   A. stencil q = K p for every source with block partials of (p, q); the
 //      last block forms alpha_k = (r, r) / (p, q) (breakdown check);
 //   B. seed update r -= alpha q with partials of ||r||^2; meanwhile the
@@ -29,16 +31,23 @@
 //      block forms (r_{k+1}, r_{k+1}), beta_k, the coefficients a_j, b_j and
 //      the freeze test, and writes per source the ordered list of shifts to
 //      update;
-//   C. fused update: for every listed shift y_j += a_j p-hat_j,
-//      p-hat_j = r + b_j p-hat_j, then p = r + beta p.
+//   P. seed direction p = r + beta p;
+//   C. fused update, on a side stream beside A, B, P of the next iteration:
+//      for every listed shift y_j += a_j p-hat_j, p-hat_j = r + b_j p-hat_j.
+// Krylov-basis form (default for FP64 and float-float solves): A, B, P as
+// above, B writing r_{k+1} into a stored slot, and S (the shift scalars:
+// xi_{k+1}, a_j, b_j into per-iteration records, the freeze test) on the
+// side stream; the shift vectors are never formed -- see "Krylov-basis form"
+// below.
 // (A two-kernel form that obtains ||r_{k+1}||^2 from (r, r) - 2 alpha (r, q)
 // + alpha^2 (q, q) was tried and rejected: on the indefinite seed the
 // residual can drop by many orders in one step, the three terms cancel, and
 // shifts froze on a wrong residual estimate.)
-// Every piece of state has a single writer per iteration (a last block), so
-// nothing needs double buffering.  Kernel A skips when no shift is live; the
-// host replays a CUDA graph of 16 iterations and polls the live count between
-// replays.  All reductions have a fixed order: runs are bit-reproducible.
+// Every piece of state has a single writer per iteration; what a side-stream
+// kernel reads is double buffered by iteration parity.  Kernel A skips when
+// no shift is live; the host replays a CUDA graph of 16 iterations and polls
+// the live count between replays.  All reductions have a fixed order: runs
+// are bit-reproducible.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
