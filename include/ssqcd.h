@@ -314,12 +314,15 @@ void ssqcd_result_destroy(ssqcd_result res);
  * ssqcd_ss_solve, on any lattice), driven by one host thread.  A submitted
  * request waits in a FIFO; ssqcd_server_progress admits requests from its
  * head while the estimated device memory of the running ones (dominated by
- * the N x L shift vectors) stays within the budget, runs every admitted
- * request on its own stream with its shifted-CG chunks enqueued ahead, so
- * the kernels of all running requests interleave on the device, and
- * finishes each request whose shifts have all frozen (moments, extraction,
- * memory freed).  A request's arithmetic does not depend on the others:
- * its result is the same alone and in the mix.  Not a part of the paper. */
+ * the N x L shift vectors, or by the stored seed residuals up to the
+ * request's cap -- the cap ssqcd_ss_solve would use, so that the result is
+ * the same; a request that does not fit the budget with it runs the update
+ * form) stays within the budget, runs every admitted request on its own
+ * stream with its shifted-CG chunks enqueued ahead, so the kernels of all
+ * running requests interleave on the device, and finishes each request
+ * whose shifts have all frozen (moments, extraction, memory freed).  A
+ * request's arithmetic does not depend on the others: its result is the
+ * same alone and in the mix.  Not a part of the paper. */
 typedef struct ssqcd_server_s* ssqcd_server;
 
 #define SSQCD_REQ_QUEUED  0
