@@ -247,21 +247,25 @@ int ssqcd_moments(ssqcd_lattice lat, int N, int M, int L, const double* w, const
                   const double* y, double* s_hat, int on_device);
 
 /* Allocation-free variant of ssqcd_moments for callers that cannot allocate
- * device memory when they need the moments -- for example code running while
- * a CUDA graph is being captured, programs that hand all device memory to
- * their own pool up front, or allocation-free real-time loops.  The paper has
- * no counterpart; it computes the same s_hat[l][k] = sum_j w_j zeta_j^k
- * y[l][j] as ssqcd_moments.
+ * device memory when they need the moments -- programs that hand all
+ * device memory to their own pool or arena up front (a framework's caching
+ * allocator, a solver embedded in a larger simulation), or loops that must
+ * run within a fixed memory budget.  The paper has no counterpart; it
+ * computes the same s_hat[l][k] = sum_j w_j zeta_j^k y[l][j] as
+ * ssqcd_moments.
  * y: device, [L][N][n] complex128; s_hat: device, [L][M][n] complex128
  * (any element order, the same for both; n = 12 V for spinor fields);
- * w, zeta: host, [N] complex128; work is issued on cuda_stream and the call
+ * w, zeta: host, [N] complex128, read during the call and passed to the
+ * device as kernel parameters; work is issued on cuda_stream and the call
  * does not wait for it.  No cudaMalloc/cudaFree or allocating library call:
  * the only scratch, the N x M coefficient table, lives in a fixed 64 KiB
  * device array held by every GPU that loads the library until exit, so
  * N * M <= 4096 and N <= 256 (else SSQCD_ERR_ARG).  The first call on a
- * device looks up that array's device address (cudaGetSymbolAddress); make
- * that first call before any stream capture.  All calls share the array:
- * calls that overlap on the GPU (different streams, no ordering) race. */
+ * device looks up that array's device address (cudaGetSymbolAddress) with
+ * the device current and caches it for the process; do not call again on a
+ * device whose context was destroyed (cudaDeviceReset).  All calls share
+ * the array: calls that overlap on the GPU (different streams, no
+ * ordering) race. */
 int ssqcd_moments_noalloc(int N, int M, int L, long long n, const double* w, const double* zeta,
                           const double* y, double* s_hat, void* cuda_stream);
 
@@ -374,7 +378,8 @@ void ssqcd_server_destroy(ssqcd_server srv);
  * complex128, host; only the lower triangle is read): evals[m] ascending,
  * evecs[m][m] row-major with eigenvector k in column k (may be NULL).  This
  * is the small eigenproblem of the Rayleigh-Ritz step (Section 2.1);
- * Householder reduction to real tridiagonal form, then implicit QL. */
+ * Householder reduction to real tridiagonal form, then implicit symmetric
+ * QR steps with Wilkinson shifts. */
 int ssqcd_small_eigh(int m, const double* a, double* evals, double* evecs);
 
 /* ---- diagnostics ------------------------------------------------------------------------- */

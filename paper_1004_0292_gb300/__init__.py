@@ -277,15 +277,22 @@ def moments_noalloc(w, zeta, y, M, stream=None):
     """Allocation-free moments: y (L, N, ...) complex128 CUDA tensor ->
     s_hat (L, M, ...) (Eq. 2).  Uses the library's fixed device scratch
     (N * M <= 4096); returns a new tensor allocated here by torch, the
-    library itself allocates nothing."""
+    library itself allocates nothing.  Raises ValueError when y, w and zeta
+    do not agree on N."""
     import torch
     w = np.ascontiguousarray(w, dtype=np.complex128)
     zeta = np.ascontiguousarray(zeta, dtype=np.complex128)
     N = len(w)
     if not (_is_torch(y) and y.is_cuda and y.is_contiguous() and y.dtype == torch.complex128):
         raise ValueError("y must be a contiguous complex128 CUDA tensor")
+    if zeta.shape != (N,) or w.shape != (N,):
+        raise ValueError("w and zeta must be 1-D arrays of the same length N")
+    if y.dim() < 3 or y.shape[1] != N:
+        raise ValueError("y must have shape (L, N, ...) with N = len(w)")
     L = y.shape[0]
-    n = y.numel() // (L * N)
+    n = int(np.prod(y.shape[2:]))
+    if L < 1 or n < 1 or y.numel() != L * N * n:
+        raise ValueError("y must be a non-empty (L, N, ...) tensor")
     s = torch.empty((L, M) + tuple(y.shape[2:]), dtype=torch.complex128, device=y.device)
     st = _stream_handle(stream if stream is not None else torch.cuda.current_stream())
     _check(lib().ssqcd_moments_noalloc(N, int(M), L, n, w.ctypes.data, zeta.ctypes.data, y.data_ptr(),

@@ -4,8 +4,8 @@
 //
 // Method: Householder reflections reduce A to a Hermitian tridiagonal T
 // (A = Q T Q^H); a diagonal unitary D makes T real (T' = D^H T D with
-// off-diagonals |e_k|); the implicit QL algorithm with Wilkinson shifts
-// diagonalises T' = Z Lambda Z^T with plane rotations; the eigenvectors of A
+// off-diagonals |e_k|); implicit symmetric QR steps with Wilkinson shifts
+// diagonalise T' = Z Lambda Z^T with plane rotations; the eigenvectors of A
 // are Q D Z.  O(m^3); m <= 256 here.
 #include <algorithm>
 #include <cfloat>
@@ -21,55 +21,64 @@ namespace {
 
 using cd = std::complex<double>;
 
-// Implicit QL on a real symmetric tridiagonal matrix: d[0..n) diagonal,
-// e[i] couples i and i+1 (e[n-1] is workspace).  Z (n x n, row-major) is
-// multiplied on the right by every rotation.
-int tridiagonal_ql(int n, std::vector<double>& d, std::vector<double>& e, std::vector<double>& Z) {
-  for (int l = 0; l < n; ++l) {
-    int sweeps = 0;
-    for (;;) {
-      int m = l;
-      for (; m < n - 1; ++m) {
-        const double scale = std::fabs(d[m]) + std::fabs(d[m + 1]);
-        if (std::fabs(e[m]) <= DBL_EPSILON * scale) break;
+// Implicit symmetric QR with Wilkinson shifts on a real symmetric
+// tridiagonal matrix (the textbook "implicit shifted QR step", Golub & Van
+// Loan, Matrix Computations, Sec. 8.3): d[0..n) diagonal, e[i] couples i and
+// i + 1.  Each step works on the lowest block [lo, hi] that is still
+// coupled: the shift mu is the eigenvalue of its trailing 2x2 block nearer
+// its last diagonal entry; a plane rotation of rows/columns lo, lo + 1 is
+// chosen from (d[lo] - mu, e[lo]), and the bulge it creates below the
+// sub-diagonal is chased down the block by rotations of (k, k + 1).  The
+// columns of Z (n x n, row-major) receive every rotation, so Z T_final Z^T
+// stays equal to the input.  Couplings below eps (|d_i| + |d_i+1|) are set
+// to zero.
+int tridiagonal_qr(int n, std::vector<double>& d, std::vector<double>& e, std::vector<double>& Z) {
+  auto rotate_cols = [&](int k, double c, double s) {
+    for (int r = 0; r < n; ++r) {
+      double* zr = &Z[(size_t)r * n];
+      const double a = zr[k], b = zr[k + 1];
+      zr[k] = c * a + s * b;
+      zr[k + 1] = c * b - s * a;
+    }
+  };
+  int steps = 0;
+  int hi = n - 1;
+  while (hi > 0) {
+    // deflate converged couplings at the bottom
+    if (std::fabs(e[hi - 1]) <= DBL_EPSILON * (std::fabs(d[hi - 1]) + std::fabs(d[hi]))) {
+      e[hi - 1] = 0.0;
+      --hi;
+      continue;
+    }
+    // top of the coupled block ending at hi
+    int lo = hi - 1;
+    while (lo > 0 && std::fabs(e[lo - 1]) > DBL_EPSILON * (std::fabs(d[lo - 1]) + std::fabs(d[lo]))) --lo;
+    if (lo > 0) e[lo - 1] = 0.0;
+    if (++steps > 60 * n) return -1;
+    // Wilkinson shift from the trailing 2x2 block [[d[hi-1], b], [b, d[hi]]]
+    const double b = e[hi - 1];
+    const double half = 0.5 * (d[hi - 1] - d[hi]);
+    const double root = std::hypot(half, b);
+    const double mu = d[hi] - b * b / (half + (half >= 0.0 ? root : -root));
+    // first rotation from the shifted leading column, then chase the bulge
+    double x = d[lo] - mu, z = e[lo];
+    for (int k = lo; k < hi; ++k) {
+      const double r = std::hypot(x, z);
+      const double c = r > 0.0 ? x / r : 1.0, s = r > 0.0 ? z / r : 0.0;
+      if (k > lo) e[k - 1] = r;  // the bulge (k + 1, k - 1) is annihilated
+      // rotate the 2x2 block of rows/columns k, k + 1
+      const double a = d[k], f = e[k], g = d[k + 1];
+      const double cs = c * s, c2 = c * c, s2 = s * s;
+      d[k] = c2 * a + 2.0 * cs * f + s2 * g;
+      d[k + 1] = s2 * a - 2.0 * cs * f + c2 * g;
+      e[k] = cs * (g - a) + (c2 - s2) * f;
+      rotate_cols(k, c, s);
+      if (k + 1 < hi) {
+        // coupling (k + 2, k + 1) splits into a new bulge (k + 2, k)
+        x = e[k];
+        z = s * e[k + 1];
+        e[k + 1] = c * e[k + 1];
       }
-      if (m == l) break;
-      if (++sweeps > 300) return -1;
-      // Wilkinson shift from the 2x2 block at l; g holds d[m] - shift
-      double g = (d[l + 1] - d[l]) / (2.0 * e[l]);
-      double r = std::hypot(g, 1.0);
-      g = d[m] - d[l] + e[l] / (g + std::copysign(r, g));
-      double s = 1.0, c = 1.0, p = 0.0;
-      int i = m - 1;
-      bool split = false;
-      for (; i >= l; --i) {
-        const double f = s * e[i];
-        const double b = c * e[i];
-        r = std::hypot(f, g);
-        e[i + 1] = r;
-        if (r == 0.0) {  // the sweep splits: restart from the top
-          d[i + 1] -= p;
-          e[m] = 0.0;
-          split = true;
-          break;
-        }
-        s = f / r;
-        c = g / r;
-        g = d[i + 1] - p;
-        r = (d[i] - g) * s + 2.0 * c * b;
-        p = s * r;
-        d[i + 1] = g + p;
-        g = c * r - b;
-        for (int k = 0; k < n; ++k) {
-          const double z1 = Z[(size_t)k * n + i + 1], z0 = Z[(size_t)k * n + i];
-          Z[(size_t)k * n + i + 1] = s * z0 + c * z1;
-          Z[(size_t)k * n + i] = c * z0 - s * z1;
-        }
-      }
-      if (split) continue;
-      d[l] -= p;
-      e[l] = g;
-      e[m] = 0.0;
     }
   }
   return 0;
@@ -150,7 +159,7 @@ int small_eigh(int m, const double2* a_in, double* evals, double2* evecs) {
   }
   std::vector<double> Z((size_t)m * m, 0.0);
   for (int i = 0; i < m; ++i) Z[(size_t)i * m + i] = 1.0;
-  if (tridiagonal_ql(m, d, e, Z) != 0) return fail(SSQCD_ERR_NOCONV, "small_eigh: QL did not converge");
+  if (tridiagonal_qr(m, d, e, Z) != 0) return fail(SSQCD_ERR_NOCONV, "small_eigh: QR did not converge");
   std::vector<int> order(m);
   std::iota(order.begin(), order.end(), 0);
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return d[a] < d[b]; });

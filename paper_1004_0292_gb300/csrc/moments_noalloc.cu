@@ -2,20 +2,25 @@
 // with c_jk = w_j zeta_j^k, for callers that cannot allocate device memory.
 //
 // Some callers cannot call cudaMalloc at the point where they need the
-// moments: code running while a CUDA graph is being captured (a cudaMalloc
-// there breaks the capture), programs that hand all device memory to their
-// own pool or arena up front, and allocation-free real-time loops.  This
-// entry point takes device pointers for the input and the output and keeps
-// its only scratch -- the N x M coefficient table -- in a fixed file-scope
-// device array, so a call allocates nothing.
+// moments: programs that hand all device memory to their own pool or arena
+// up front (a framework's caching allocator, an embedded solver inside a
+// larger simulation), and allocation-free loops with fixed memory budgets.
+// This entry point takes device pointers for the input and the output and
+// keeps its only scratch -- the N x M coefficient table -- in a fixed
+// file-scope device array, so a call allocates nothing.
+//
+// The weights and nodes reach the device by value, as kernel parameters (at
+// most 256 of each: 8 KiB of parameters); a first kernel forms the table
+// c_jk = w_j zeta_j^k in the device array, a second one forms the moments.
+// No host buffer outlives the call and nothing is copied from host memory.
 //
 // The array holds at most kMaxCoef = 4096 complex coefficients (64 KiB), so
 // N * M <= 4096 (and N <= 256); every GPU that loads this library holds it
 // until the process exits.  All calls share the one array, which keeps the
 // last call's table: each call overwrites the N * M entries it uses before
-// its kernel reads them, so nothing has to start at zero, but calls whose
-// copies and kernels overlap on the GPU (different streams, no ordering
-// between them) race on the table.  Calls on one stream are ordered.
+// its second kernel reads them, so nothing has to start at zero, but calls
+// whose kernels overlap on the GPU (different streams, no ordering between
+// them) race on the table.  Calls on one stream are ordered.
 #include <mutex>
 #include <vector>
 
@@ -33,7 +38,10 @@ static __device__ __align__(256) double2 g_moment_coef[kMaxCoef];
 
 // In host code g_moment_coef is only a host-side stand-in, not a device
 // address; the device address comes from cudaGetSymbolAddress, once per
-// device, with that device current.
+// device and process, with that device current (the first call on a
+// device).  The cached address belongs to that device's primary context: a
+// process that destroys the context (cudaDeviceReset) must not call this
+// entry point on that device again.
 std::mutex g_setup_mutex;
 double2* g_coef_ptr[kMaxDevices] = {nullptr};
 
@@ -51,6 +59,27 @@ int coef_table(int dev, double2** out) {
 }
 
 constexpr int kCols = 8;  // output vectors per thread
+
+// Weights and nodes of one call, passed by value as a kernel parameter.
+struct NodeSet {
+  double2 w[kMaxNoallocShifts];
+  double2 zeta[kMaxNoallocShifts];
+};
+
+// coef[j * M + k] = w_j zeta_j^k, one thread per node j (powers by repeated
+// multiplication, k ascending).
+__global__ void moment_coef_kernel(const NodeSet ns, int N, int M, double2* __restrict__ coef) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= N) return;
+  const double2 w = ns.w[j], a = ns.zeta[j];
+  double zr = 1.0, zi = 0.0;
+  for (int k = 0; k < M; ++k) {
+    coef[j * M + k] = make_double2(w.x * zr - w.y * zi, w.x * zi + w.y * zr);
+    const double nr = zr * a.x - zi * a.y, ni = zr * a.y + zi * a.x;
+    zr = nr;
+    zi = ni;
+  }
+}
 
 // s_hat[l][c] (n complex) = sum_j y[l][j] coef[j * M + c]; blockIdx.z = l.
 // The coefficient columns of this block are staged in shared memory.
@@ -101,21 +130,16 @@ extern "C" int ssqcd_moments_noalloc(int N, int M, int L, long long n, const dou
   SS_CUDA(cudaGetDevice(&dev));
   double2* table = nullptr;
   SS_TRY(coef_table(dev, &table));
-  // c_jk = w_j zeta_j^k (host), then one copy into the device table
-  double2 coef[kMaxCoef];
+  // c_jk = w_j zeta_j^k, formed on the device from the nodes passed by value
+  NodeSet ns;
   for (int j = 0; j < N; ++j) {
-    double zr = 1.0, zi = 0.0;
-    for (int k = 0; k < M; ++k) {
-      const double wr = w[2 * j], wi = w[2 * j + 1];
-      coef[j * M + k] = make_double2(wr * zr - wi * zi, wr * zi + wi * zr);
-      const double ar = zeta[2 * j], ai = zeta[2 * j + 1];
-      const double nr = zr * ar - zi * ai, ni = zr * ai + zi * ar;
-      zr = nr;
-      zi = ni;
-    }
+    ns.w[j] = make_double2(w[2 * j], w[2 * j + 1]);
+    ns.zeta[j] = make_double2(zeta[2 * j], zeta[2 * j + 1]);
   }
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
-  SS_CUDA(cudaMemcpyAsync(table, coef, sizeof(double2) * N * M, cudaMemcpyHostToDevice, st));
+  moment_coef_kernel<<<(N + 63) / 64, 64, 0, st>>>(ns, N, M, table);
+  count_launches(1);
+  SS_CHECK_LAUNCH();
   const int cy = (M + kCols - 1) / kCols;
   long long bx = (n + 255) / 256;
   const long long cap = (4LL * 152 + (long long)cy * L - 1) / ((long long)cy * L);

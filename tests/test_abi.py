@@ -106,3 +106,17 @@ def test_struct_layouts_match_the_header(ss, tmp_path):
         assert c_side[(cname, "size")] == ctypes.sizeof(py), cname
         for f, _ in py._fields_:
             assert c_side[(cname, f)] == getattr(py, f).offset, (cname, f)
+
+
+def test_small_eigh_clustered_and_large(ss):
+    # the Rayleigh-Ritz sizes (m up to M L = 128 and beyond) with tight
+    # eigenvalue clusters, as the projected matrices of a window have
+    g = synthetic.rng(9)
+    for m, spread in ((128, 1e-9), (200, 1e-3), (96, 0.0)):
+        d = np.concatenate([0.1 + spread * g.standard_normal(m // 2), g.standard_normal(m - m // 2)])
+        q, _ = np.linalg.qr(g.standard_normal((m, m)) + 1j * g.standard_normal((m, m)))
+        a = q @ np.diag(d) @ q.conj().T
+        ev, vec = ss.small_eigh(a)
+        assert np.max(np.abs(ev - np.sort(d))) <= 1e-13 * max(1.0, np.max(np.abs(d)))
+        assert np.allclose(vec.conj().T @ vec, np.eye(m), atol=1e-12)
+        assert np.max(np.abs(a @ vec - vec * ev[None, :])) <= 1e-12 * max(1.0, np.max(np.abs(d)))

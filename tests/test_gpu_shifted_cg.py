@@ -105,3 +105,37 @@ def test_moments_match_oracle(ss):
         scale = np.sum(np.abs(w)[:, None] * np.abs(zeta)[:, None] ** np.arange(M)[None, :], axis=0)
         for k in range(M):
             assert np.max(np.abs(s[l, k] - ref[k])) <= 1e-14 * scale[k] * np.max(np.abs(y)) * 8
+
+
+@pytest.mark.parametrize("prec", ["FP64", "DF"])
+def test_seed_breakdown_returns_status(ss, prec):
+    """The seed matrix K = sigma I - A with sigma = 0 (Section 4) is
+    indefinite, so CG on it can break down.  Free field (U = 1), periodic
+    time, kappa = 1/16: the constant spinor with colour-0 components in spin 0
+    (gamma5 = +1) and spin 2 (gamma5 = -1) is a sum of a +lambda and a -lambda
+    eigenvector of equal norm (lambda = 1 - 8 kappa = 1/2), so (v, K v) = 0
+    exactly in binary arithmetic, at the first iteration.  Built on the
+    host; the solve must return SSQCD_ERR_BREAKDOWN (no fault, no hang)."""
+    dims, kappa, bc = (4, 4, 4, 4), 1.0 / 16.0, +1
+    U = synthetic.unit_gauge(dims)
+    V = synthetic.volume(dims)
+    v = np.zeros((1, V, 4, 3), dtype=np.complex128)
+    v[0, :, 0, 0] = 1.0
+    v[0, :, 2, 0] = 1.0
+    Av = wilson.apply_H(U, v[0], kappa, dims, bc)
+    assert np.vdot(v[0], Av) == 0.0
+    assert np.allclose(Av[:, 0, 0], 0.5) and np.allclose(Av[:, 2, 0], -0.5)
+    with pytest.raises(oscg.Breakdown):
+        oscg.shifted_cg(lambda x: wilson.apply_H(U, x, kappa, dims, bc), v[0],
+                        contour.line_nodes(0.5, 0.05, 0.3, 8), tol=1e-12)
+    lat = ss.create_lattice(dims, kappa, bc, precision=getattr(ss, prec))
+    ss.upload_gauge(lat, U)
+    z = contour.line_nodes(0.5, 0.05, 0.3, 8)
+    code, *_ = ss.shifted_cg(lat, z, v, tol=1e-12, precision=getattr(ss, prec))
+    assert code == ss.ERR_BREAKDOWN
+    res = ss.ss_solve(lat, (0.45, 0.55), 8, 4, v, beta=0.3, nprime=4)
+    assert res.status == ss.ERR_BREAKDOWN
+    # the context stays usable: a regular solve afterwards succeeds
+    w = synthetic.gaussian_sources(dims, 1, seed=5)
+    code, *_ = ss.shifted_cg(lat, z, w, tol=1e-10, precision=getattr(ss, prec))
+    assert code == ss.OK
