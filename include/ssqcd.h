@@ -129,6 +129,15 @@ typedef struct {
                              reaches it forms y_j and p-hat_j from the stored
                              residuals and continues with the per-iteration
                              updates (the same eigenpairs, other rounding)     */
+  int    source_block;    /* 0 (default): all L sources in one shifted-CG run.
+                             B with 0 < B < L: the sources run in blocks of B,
+                             one shifted-CG run per block, each block's moments
+                             formed before the next block starts (the seed
+                             recurrences of different sources are independent,
+                             so the moments are the same); only B sources'
+                             stored residuals or shift vectors are held at a
+                             time -- what lets the stored-residual form of a
+                             large lattice fit the device memory            */
 } ssqcd_opts;
 
 /* Counters of one solve.  Times are device milliseconds between CUDA events. */
@@ -291,6 +300,22 @@ void ssqcd_default_opts(ssqcd_opts* opts);
  * SSQCD_ERR_ARG/OOM, so its stats can be read). */
 int ssqcd_ss_solve(ssqcd_lattice lat, const double interval[2], int N, int M, int L,
                    const ssqcd_opts* opts, ssqcd_result* out);
+
+/* Several windows out of one shifted-CG run: K intervals
+ * intervals[k] = [a_k, b_k] (host, [K][2] doubles, any positions, e.g. on both
+ * sides of the spectral gap around zero), each with its own quadrature
+ * points placed as in ssqcd_ss_solve with one window (same N, N', beta and
+ * path from opts) -- Section 3's windows, which the paper solves one after
+ * another.  The points of all windows (exact duplicates merged) go into one
+ * seed recurrence per source (Section 2.2: one Krylov space serves every
+ * shift); each window then has its own moments s_hat_k, k < M (Eq. 2),
+ * Rayleigh-Ritz (or Hankel) extraction, and accepts the Ritz values in its
+ * own [a_k, b_k].  The result holds the accepted pairs of all windows sorted
+ * by eigenvalue; stats.points counts the distinct points and stats.gamma /
+ * stats.rho give the first window.  opts.windows must be 0 or 1.  Errors as
+ * ssqcd_ss_solve. */
+int ssqcd_ss_solve_windows(ssqcd_lattice lat, int K, const double* intervals, int N, int M, int L,
+                           const ssqcd_opts* opts, ssqcd_result* out);
 
 /* The filtered block of one window without the extraction: the shifted CG
  * of ssqcd_ss_solve (same options, same quadrature points, the same choice

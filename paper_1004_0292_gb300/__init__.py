@@ -24,7 +24,7 @@ __all__ = [
     "OK", "ERR_ARG", "ERR_OOM", "ERR_BREAKDOWN", "ERR_NOCONV", "ERR_CUDA",
     "FP64", "MIXED", "MIXED_F32LINKS", "FP64_SHIFT32", "FP64_DFSHIFT", "DF", "EXTRACT_RR", "EXTRACT_HANKEL", "PATH_LINES", "PATH_CIRCLE", "SsqcdError",
     "library_path", "lib", "Server", "time_stencil", "create_lattice", "upload_gauge", "apply_H", "apply_H_mixed",
-    "contour", "shifted_cg", "moments", "moments_noalloc", "ss_solve", "ss_eigpairs", "small_eigh",
+    "contour", "shifted_cg", "moments", "moments_noalloc", "ss_solve", "ss_solve_windows", "ss_eigpairs", "small_eigh",
     "kernel_launches", "set_kernel_timing", "Lattice", "Result", "Opts", "Stats",
 ]
 
@@ -52,7 +52,7 @@ class Opts(C.Structure):
         ("sigma", C.c_double), ("max_iter", C.c_int), ("rank_tol", C.c_double),
         ("sources", C.c_void_p), ("sources_on_device", C.c_int), ("reliable_every", C.c_int),
         ("windows", C.c_int), ("extract", C.c_int), ("hankel_tol", C.c_double), ("refine", C.c_int),
-        ("basis", C.c_int), ("basis_max_bytes", C.c_double),
+        ("basis", C.c_int), ("basis_max_bytes", C.c_double), ("source_block", C.c_int),
     ]
 
 
@@ -104,6 +104,7 @@ def lib():
         "ssqcd_moments": (i, [vp, i, i, i, vp, vp, vp, vp, i]),
         "ssqcd_default_opts": (None, [vp]),
         "ssqcd_ss_solve": (i, [vp, vp, i, i, i, vp, vp]),
+        "ssqcd_ss_solve_windows": (i, [vp, i, vp, i, i, i, vp, vp]),
         "ssqcd_ss_moments": (i, [vp, vp, i, i, i, vp, vp, i, vp]),
         "ssqcd_ss_eigpairs": (i, [vp, vp, vp, vp, vp, vp]),
         "ssqcd_result_destroy": (None, [vp]),
@@ -300,11 +301,8 @@ def moments_noalloc(w, zeta, y, M, stream=None):
     return s
 
 
-def ss_solve(lat: Lattice, interval, N, M, sources, beta=0.3, nprime=0, tol=1e-12, sigma=0.0, max_iter=100000,
-             rank_tol=1e-14, path=PATH_LINES, reliable_every=0, windows=1, extract=0,
-             hankel_tol=1e-12, refine=0, basis=1, basis_max_bytes=0.0) -> Result:
-    """Run the solver; returns a Result (check ``status``).  ``basis`` / ``basis_max_bytes``: moments
-    from the stored seed residuals (FP64 and DF lattices; see ssqcd_opts)."""
+def _solve_opts(lat, sources, beta, nprime, tol, sigma, max_iter, rank_tol, path, reliable_every, windows, extract,
+                hankel_tol, refine, basis, basis_max_bytes, source_block):
     L = int(np.prod(sources.shape)) // lat.n
     o = Opts()
     lib().ssqcd_default_opts(C.byref(o))
@@ -315,9 +313,38 @@ def ss_solve(lat: Lattice, interval, N, M, sources, beta=0.3, nprime=0, tol=1e-1
     o.windows = int(windows)
     o.extract, o.hankel_tol, o.refine = int(extract), float(hankel_tol), int(refine)
     o.basis, o.basis_max_bytes = int(basis), float(basis_max_bytes)
+    o.source_block = int(source_block)
+    return L, o, keep
+
+
+def ss_solve(lat: Lattice, interval, N, M, sources, beta=0.3, nprime=0, tol=1e-12, sigma=0.0, max_iter=100000,
+             rank_tol=1e-14, path=PATH_LINES, reliable_every=0, windows=1, extract=0,
+             hankel_tol=1e-12, refine=0, basis=1, basis_max_bytes=0.0, source_block=0) -> Result:
+    """Run the solver; returns a Result (check ``status``).  ``basis`` / ``basis_max_bytes``: moments
+    from the stored seed residuals (FP64 and DF lattices; see ssqcd_opts); ``source_block``: sources
+    per shifted-CG run."""
+    L, o, keep = _solve_opts(lat, sources, beta, nprime, tol, sigma, max_iter, rank_tol, path, reliable_every,
+                             windows, extract, hankel_tol, refine, basis, basis_max_bytes, source_block)
     iv = (C.c_double * 2)(float(interval[0]), float(interval[1]))
     h = C.c_void_p()
     code = lib().ssqcd_ss_solve(lat.handle, iv, int(N), int(M), L, C.byref(o), C.byref(h))
+    if not h.value:
+        _check(code)
+    err = lib().ssqcd_last_error().decode() if code != OK else ""
+    return Result(h, code, lat, err)
+
+
+def ss_solve_windows(lat: Lattice, intervals, N, M, sources, beta=0.3, nprime=0, tol=1e-12, sigma=0.0,
+                     max_iter=100000, rank_tol=1e-14, path=PATH_LINES, extract=0, hankel_tol=1e-12, refine=0,
+                     basis=1, basis_max_bytes=0.0, source_block=0) -> Result:
+    """Several windows [(a_k, b_k), ...] out of one shifted-CG run (ssqcd_ss_solve_windows)."""
+    iv_list = [float(x) for ab in intervals for x in ab]
+    K = len(iv_list) // 2
+    L, o, keep = _solve_opts(lat, sources, beta, nprime, tol, sigma, max_iter, rank_tol, path, 0, 1, extract,
+                             hankel_tol, refine, basis, basis_max_bytes, source_block)
+    iv = (C.c_double * (2 * K))(*iv_list)
+    h = C.c_void_p()
+    code = lib().ssqcd_ss_solve_windows(lat.handle, K, iv, int(N), int(M), L, C.byref(o), C.byref(h))
     if not h.value:
         _check(code)
     err = lib().ssqcd_last_error().decode() if code != OK else ""

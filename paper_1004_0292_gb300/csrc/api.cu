@@ -33,6 +33,10 @@ struct SolvePlan {
   int N = 0, M = 0, L = 0, K = 1, MM = 0, NU = 0;
   bool hankel = false;
   double a = 0.0, b = 0.0, core = 0.0, gamma0 = 0.0, rho = 0.0;
+  // per window: centre, radius, accepted interval [lo, hi] (hi_open: the
+  // upper end belongs to the next window)
+  std::vector<double> gam, rad, lo, hi;
+  std::vector<char> hi_open;
   std::vector<double2> zu;                   // union of the windows' points
   std::vector<std::vector<double2>> coefk;   // per window: [NU][MM] moment coefficients
 };
@@ -282,6 +286,7 @@ extern "C" void ssqcd_default_opts(ssqcd_opts* o) {
   o->refine = 0;
   o->basis = 1;
   o->basis_max_bytes = 0.0;
+  o->source_block = 0;
 }
 
 namespace {
@@ -620,6 +625,101 @@ int plan_solve(const double interval[2], int N, int M, int L, const ssqcd_opts* 
   P->rho = rho;
   P->zu.swap(zu);
   P->coefk.swap(coefk);
+  P->gam.resize(K);
+  P->rad.assign(K, rho);
+  P->lo.resize(K);
+  P->hi.resize(K);
+  P->hi_open.resize(K);
+  for (int k = 0; k < K; ++k) {
+    P->gam[k] = gamma0 + k * core;
+    P->lo[k] = (K == 1) ? a : a + k * core;
+    P->hi[k] = (K == 1) ? b : (k == K - 1 ? b : a + (k + 1) * core);
+    P->hi_open[k] = k < K - 1;
+  }
+  return SSQCD_OK;
+}
+
+// A list of K windows [a_k, b_k] (any positions, the same N, N', beta and
+// path): each window gets its own centre and radius as in plan_solve with
+// one window; the union of the points is the concatenation of the windows'
+// points with exact duplicates merged (windows laid out on a common grid
+// share them, as in Section 3), and every window's moment coefficients sit
+// at its own points of the union.  One shifted-CG run then serves all
+// windows; each window accepts the Ritz values in its own [a_k, b_k].
+int plan_windows(int K, const double* iv, int N, int M, int L, const ssqcd_opts* opts_in, SolvePlan* P) {
+  if (K < 1 || iv == nullptr) return fail(SSQCD_ERR_ARG, "need K >= 1 windows");
+  std::vector<std::vector<double2>> zk(K), wk(K);
+  std::vector<double> gam(K), rad(K);
+  SolvePlan one;
+  for (int k = 0; k < K; ++k) {
+    ssqcd_opts o;
+    ssqcd_default_opts(&o);
+    if (opts_in) o = *opts_in;
+    o.windows = 1;
+    SS_TRY(plan_solve(iv + 2 * k, N, M, L, &o, &one));
+    gam[k] = one.gamma0;
+    rad[k] = one.rho;
+    zk[k] = one.zu;
+    wk[k].resize(N);
+    // the window's own coefficients: column m of point j is w_j zeta_j^m
+    for (int j = 0; j < N; ++j) wk[k][j] = one.coefk[0][(size_t)j * one.MM];
+  }
+  P->o = one.o;
+  P->N = N;
+  P->M = M;
+  P->L = L;
+  P->K = K;
+  P->MM = one.MM;
+  P->hankel = one.hankel;
+  P->a = iv[0];
+  P->b = iv[1];
+  P->core = iv[1] - iv[0];
+  P->gamma0 = gam[0];
+  P->rho = rad[0];
+  P->gam = gam;
+  P->rad = rad;
+  P->lo.resize(K);
+  P->hi.resize(K);
+  P->hi_open.assign(K, 0);
+  for (int k = 0; k < K; ++k) {
+    P->lo[k] = iv[2 * k];
+    P->hi[k] = iv[2 * k + 1];
+  }
+  // union with exact duplicates merged
+  std::vector<double2> zu;
+  std::vector<std::vector<int>> at(K, std::vector<int>(N));
+  for (int k = 0; k < K; ++k)
+    for (int j = 0; j < N; ++j) {
+      const double2 z = zk[k][j];
+      int u = -1;
+      for (int q = 0; q < (int)zu.size(); ++q)
+        if (zu[q].x == z.x && zu[q].y == z.y) {
+          u = q;
+          break;
+        }
+      if (u < 0) {
+        u = (int)zu.size();
+        zu.push_back(z);
+      }
+      at[k][j] = u;
+    }
+  const int NU = (int)zu.size(), MM = P->MM;
+  std::vector<std::vector<double2>> coefk(K, std::vector<double2>((size_t)NU * MM, make_double2(0.0, 0.0)));
+  for (int k = 0; k < K; ++k)
+    for (int j = 0; j < N; ++j) {
+      const double zr0 = (zk[k][j].x - gam[k]) / rad[k], zi0 = zk[k][j].y / rad[k];
+      const double2 w = wk[k][j];
+      double zr = 1.0, zi = 0.0;
+      for (int m = 0; m < MM; ++m) {
+        coefk[k][(size_t)at[k][j] * MM + m] = make_double2(w.x * zr - w.y * zi, w.x * zi + w.y * zr);
+        const double nr = zr * zr0 - zi * zi0, ni = zr * zi0 + zi * zr0;
+        zr = nr;
+        zi = ni;
+      }
+    }
+  P->NU = NU;
+  P->zu.swap(zu);
+  P->coefk.swap(coefk);
   return SSQCD_OK;
 }
 
@@ -647,10 +747,9 @@ void fill_cg_stats(const ShiftedCGOut& cg, const std::vector<int>& iters, ssqcd_
 // is filled; released once the last window's moments exist); vd: the
 // sources [L][n].  All device work on st.
 int extract_eigenpairs(ssqcd_lattice lat, const SolvePlan& P, DevBuf& yd, KrylovBasis& kb, DevBuf& vd,
-                       ssqcd_result_s* res, cudaStream_t st) {
+                       ssqcd_result_s* res, cudaStream_t st, std::vector<DevBuf>* Spre = nullptr) {
   const long long n = 12LL * lat->g.V;
   const int K = P.K, L = P.L, MM = P.MM, M = P.M, NU = P.NU;
-  const double a = P.a, b = P.b, core = P.core, rho = P.rho;
   res->stats.gamma = P.gamma0;
   res->stats.rho = P.rho;
   res->stats.points = NU;
@@ -684,7 +783,7 @@ int extract_eigenpairs(ssqcd_lattice lat, const SolvePlan& P, DevBuf& yd, Krylov
     }
   } ov;
   DevBuf mscratch;
-  const bool overlap = kb.S > 0 && !P.hankel && L > 1;
+  const bool overlap = Spre == nullptr && kb.S > 0 && !P.hankel && L > 1;
   if (overlap) {
     SS_CUDA(cudaStreamCreateWithFlags(&ov.side, cudaStreamNonBlocking));
     ov.ev.resize(L);
@@ -699,7 +798,12 @@ int extract_eigenpairs(ssqcd_lattice lat, const SolvePlan& P, DevBuf& yd, Krylov
     }
   } ev_mom{&e_mom};
   for (int k = 0; k < K; ++k) {
-    // moments of window k (Eq. 2), S = [L][MM][n]
+    // moments of window k (Eq. 2), S = [L][MM][n] (formed here, or given)
+    if (Spre != nullptr) {
+      S.release();
+      S.swap((*Spre)[k]);  // window k's moments, freed with S
+      if (k == K - 1) cudaEventRecord(e1, st);
+    } else {
     SS_TRY(S.alloc(sizeof(double2) * n * m));
     if (overlap)
       SS_TRY(basis_moments(kb, P.coefk[k].data(), MM, S.as<double2>(), mscratch, st, ov.side, ov.ev.data()));
@@ -717,20 +821,21 @@ int extract_eigenpairs(ssqcd_lattice lat, const SolvePlan& P, DevBuf& yd, Krylov
         kb.release();
       }
     }
+    }
     // Rayleigh-Ritz (or the Hankel pencil) and acceptance in the window's core
-    const double lo = (K == 1) ? a : a + k * core;
-    const double hi = (K == 1) ? b : (k == K - 1 ? b : a + (k + 1) * core);
+    const double lo = P.lo[k], hi = P.hi[k];
+    const bool hi_open = P.hi_open[k] != 0;
     int rank = 0;
     if (P.hankel) {
       const size_t before = res->evals.size();
-      SS_TRY(hankel_window(vd.as<double2>(), L, S.as<double2>(), M, n, P.o.hankel_tol, P.gamma0 + k * core, rho, lo,
-                           hi, k < K - 1, res->evals, res->residuals, rank, scratch, st));
+      SS_TRY(hankel_window(vd.as<double2>(), L, S.as<double2>(), M, n, P.o.hankel_tol, P.gam[k], P.rad[k], lo,
+                           hi, hi_open, res->evals, res->residuals, rank, scratch, st));
       cntk[k] = (int)(res->evals.size() - before);
       res->stats.rank += rank;
       res->stats.n_ritz += rank;
       continue;
     }
-    SS_TRY(rayleigh_ritz_window(lat, S.as<double2>(), m, P.o.rank_tol, P.o.refine != 0, lo, hi, k < K - 1,
+    SS_TRY(rayleigh_ritz_window(lat, S.as<double2>(), m, P.o.rank_tol, P.o.refine != 0, lo, hi, hi_open,
                                 res->evals, res->residuals, Xk[k], cntk[k], rank, scratch, st,
                                 overlap ? ov.ev.data() : nullptr, MM));
     if (k == K - 1 && overlap) kb.release();  // st has waited for every source's moments
@@ -788,21 +893,38 @@ int extract_eigenpairs(ssqcd_lattice lat, const SolvePlan& P, DevBuf& yd, Krylov
 
 }  // namespace
 
-extern "C" int ssqcd_ss_solve(ssqcd_lattice lat, const double interval[2], int N, int M, int L,
-                              const ssqcd_opts* opts_in, ssqcd_result* out) {
-  if (out == nullptr) return fail(SSQCD_ERR_ARG, "NULL result pointer");
-  *out = nullptr;
-  SS_TRY(check_lattice(lat, true));
-  SolvePlan P;
-  SS_TRY(plan_solve(interval, N, M, L, opts_in, &P));
+namespace {
+
+void add_cg_stats(const ShiftedCGOut& b, ShiftedCGOut* acc) {
+  acc->seed_iters = std::max(acc->seed_iters, b.seed_iters);
+  acc->reliable_updates += b.reliable_updates;
+  acc->ms += b.ms;
+  acc->shift_updates += b.shift_updates;
+  acc->timed = acc->timed || b.timed;
+  acc->launches_update += b.launches_update;
+  acc->timed_units += b.timed_units;
+  for (int i = 0; i < 4; ++i) acc->ms_k[i] += b.ms_k[i];
+  acc->basis = std::max(acc->basis, b.basis);
+  acc->basis_bytes = std::max(acc->basis_bytes, b.basis_bytes);
+}
+
+// A planned solve: shifted CG over the union of the windows' points, the
+// moments and the extraction.  With opts.source_block = B (0 < B < L) the
+// sources run in blocks of B, one shifted-CG run per block (the seed
+// recurrences of different sources never interact), and each block's
+// moments of every window are formed before the next block starts, so the
+// stored seed residuals of only B sources are held at a time.
+int run_solve(ssqcd_lattice lat, const SolvePlan& P, ssqcd_result* out) {
+  const int L = P.L, NU = P.NU, K = P.K, MM = P.MM;
+  const long long n = 12LL * lat->g.V;
   auto* res = new (std::nothrow) ssqcd_result_s();
   if (!res) return fail(SSQCD_ERR_OOM, "host allocation failed");
   res->stream = lat->stream;
   res->V = lat->g.V;
-  res->n = 12LL * lat->g.V;
+  res->n = n;
   res->stats.gamma = P.gamma0;
   res->stats.rho = P.rho;
-  res->stats.points = P.NU;
+  res->stats.points = NU;
   cudaStream_t st = lat->stream;
   // sources -> device layout
   DevBuf vd, yd;
@@ -812,18 +934,97 @@ extern "C" int ssqcd_ss_solve(ssqcd_lattice lat, const double interval[2], int N
     delete res;
     return s1;
   }
-  // shifted CG over the union of the quadrature points (one seed recurrence)
+  const int B = (P.o.source_block > 0 && P.o.source_block < L) ? P.o.source_block : L;
+  std::vector<int> iters((size_t)NU * L);
+  if (B == L) {
+    // shifted CG over the union of the quadrature points (one seed recurrence per source)
+    ShiftedCGOut cg;
+    s1 = shifted_cg_solve(lat, NU, P.zu.data(), L, vd.as<double2>(), P.o.sigma, P.o.tol, P.o.max_iter,
+                          lat->precision, P.o.reliable_every,
+                          basis_cap_for(lat->precision, P.o.basis, P.o.basis_max_bytes, n, NU, L), yd, &kb,
+                          iters.data(), &cg);
+    fill_cg_stats(cg, iters, &res->stats);
+    *out = res;  // a result handle even on failure, so its stats can be read
+    if (s1 != SSQCD_OK) return s1;
+    if (!P.hankel) vd.release();
+    return extract_eigenpairs(lat, P, yd, kb, vd, res, st);
+  }
+  // source blocks: every window's moments [L][MM][n], filled block by block
+  std::vector<DevBuf> Sk(K);
+  *out = res;
+  for (int k = 0; k < K; ++k) SS_TRY(Sk[k].alloc(sizeof(double2) * n * MM * L));
   ShiftedCGOut cg;
-  std::vector<int> iters((size_t)P.NU * L);
-  s1 = shifted_cg_solve(lat, P.NU, P.zu.data(), L, vd.as<double2>(), P.o.sigma, P.o.tol, P.o.max_iter,
-                        lat->precision, P.o.reliable_every,
-                        basis_cap_for(lat->precision, P.o.basis, P.o.basis_max_bytes, 12LL * lat->g.V, P.NU, L), yd, &kb,
-                        iters.data(), &cg);
-  fill_cg_stats(cg, iters, &res->stats);
-  *out = res;  // a result handle even on failure, so its stats can be read
-  if (s1 != SSQCD_OK) return s1;
+  cudaEvent_t m0 = nullptr, m1 = nullptr;
+  struct Evs {
+    cudaEvent_t* a;
+    cudaEvent_t* b;
+    ~Evs() {
+      if (*a) cudaEventDestroy(*a);
+      if (*b) cudaEventDestroy(*b);
+    }
+  } evs{&m0, &m1};
+  SS_CUDA(cudaEventCreate(&m0));
+  SS_CUDA(cudaEventCreate(&m1));
+  float ms_mom = 0.f;
+  for (int l0 = 0; l0 < L; l0 += B) {
+    const int Lb = std::min(B, L - l0);
+    ShiftedCGOut cgb;
+    DevBuf scratch;
+    s1 = shifted_cg_solve(lat, NU, P.zu.data(), Lb, vd.as<double2>() + (size_t)l0 * n, P.o.sigma, P.o.tol,
+                          P.o.max_iter, lat->precision, P.o.reliable_every,
+                          basis_cap_for(lat->precision, P.o.basis, P.o.basis_max_bytes, n, NU, Lb), yd, &kb,
+                          iters.data() + (size_t)l0 * NU, &cgb);
+    add_cg_stats(cgb, &cg);
+    fill_cg_stats(cg, iters, &res->stats);
+    if (s1 != SSQCD_OK) return s1;
+    SS_CUDA(cudaEventRecord(m0, st));
+    for (int k = 0; k < K; ++k) {
+      double2* dst = Sk[k].as<double2>() + (size_t)l0 * MM * n;
+      if (kb.S > 0)
+        SS_TRY(basis_moments(kb, P.coefk[k].data(), MM, dst, scratch, st));
+      else
+        SS_TRY(moments_device(yd.as<double2>(), NU, MM, Lb, n, P.coefk[k].data(), dst, scratch, st));
+    }
+    SS_CUDA(cudaEventRecord(m1, st));
+    SS_CUDA(cudaEventSynchronize(m1));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, m0, m1);
+    ms_mom += ms;
+    yd.release();
+    kb.release();
+  }
   if (!P.hankel) vd.release();
-  return extract_eigenpairs(lat, P, yd, kb, vd, res, st);
+  s1 = extract_eigenpairs(lat, P, yd, kb, vd, res, st, &Sk);
+  res->stats.ms_moments += ms_mom;
+  return s1;
+}
+
+}  // namespace
+
+extern "C" int ssqcd_ss_solve(ssqcd_lattice lat, const double interval[2], int N, int M, int L,
+                              const ssqcd_opts* opts_in, ssqcd_result* out) {
+  if (out == nullptr) return fail(SSQCD_ERR_ARG, "NULL result pointer");
+  *out = nullptr;
+  SS_TRY(check_lattice(lat, true));
+  SolvePlan P;
+  SS_TRY(plan_solve(interval, N, M, L, opts_in, &P));
+  return run_solve(lat, P, out);
+}
+
+extern "C" int ssqcd_ss_solve_windows(ssqcd_lattice lat, int K, const double* intervals, int N, int M, int L,
+                                      const ssqcd_opts* opts_in, ssqcd_result* out) {
+  if (out == nullptr) return fail(SSQCD_ERR_ARG, "NULL result pointer");
+  *out = nullptr;
+  SS_TRY(check_lattice(lat, true));
+  if (opts_in != nullptr && opts_in->windows > 1)
+    return fail(SSQCD_ERR_ARG, "ssqcd_ss_solve_windows: opts.windows must be 0 or 1 (the list gives the windows)");
+  if (K < 1 || intervals == nullptr) return fail(SSQCD_ERR_ARG, "ssqcd_ss_solve_windows: need K >= 1 intervals");
+  for (int k = 0; k < K; ++k)
+    if (!(intervals[2 * k + 1] > intervals[2 * k]))
+      return fail(SSQCD_ERR_ARG, "ssqcd_ss_solve_windows: every interval needs b > a");
+  SolvePlan P;
+  SS_TRY(plan_windows(K, intervals, N, M, L, opts_in, &P));
+  return run_solve(lat, P, out);
 }
 
 extern "C" int ssqcd_ss_moments(ssqcd_lattice lat, const double interval[2], int N, int M, int L,
