@@ -138,6 +138,13 @@ typedef struct {
                              stored residuals or shift vectors are held at a
                              time -- what lets the stored-residual form of a
                              large lattice fit the device memory            */
+  double converged_tol;   /* residual bound of stats.n_converged; 1e-8.  The
+                             paper accepts Ritz values by position (Section 3),
+                             so an accepted pair can be a spurious Ritz value of
+                             the filtered noise (residual ~0.5 when M L exceeds
+                             the eigenvalue count); ssqcd_ss_eigpairs returns
+                             every accepted pair with its residual, and
+                             n_converged counts those at or below this bound */
 } ssqcd_opts;
 
 /* Counters of one solve.  Times are device milliseconds between CUDA events. */
@@ -178,6 +185,9 @@ typedef struct {
                              so and switched to shift-vector updates at the
                              memory cap; 0: shift-vector updates throughout    */
   double basis_bytes;     /* device memory the stored residuals took at most  */
+  int    n_converged;     /* accepted pairs with residual <= opts.converged_tol
+                             (Rayleigh-Ritz only; the Hankel extraction has no
+                             residuals and reports 0)                         */
 } ssqcd_stats;
 
 /* ---- lattice / operator ---------------------------------------------------- */

@@ -53,6 +53,7 @@ class Opts(C.Structure):
         ("sources", C.c_void_p), ("sources_on_device", C.c_int), ("reliable_every", C.c_int),
         ("windows", C.c_int), ("extract", C.c_int), ("hankel_tol", C.c_double), ("refine", C.c_int),
         ("basis", C.c_int), ("basis_max_bytes", C.c_double), ("source_block", C.c_int),
+        ("converged_tol", C.c_double),
     ]
 
 
@@ -65,6 +66,7 @@ class Stats(C.Structure):
         ("timed", C.c_int), ("launches_update", C.c_int), ("ms_k_stencil", C.c_double),
         ("ms_k_seed", C.c_double), ("ms_k_scalars", C.c_double), ("ms_k_update", C.c_double),
         ("timed_shift_updates", C.c_longlong), ("basis", C.c_int), ("basis_bytes", C.c_double),
+        ("n_converged", C.c_int),
     ]
 
     def as_dict(self):

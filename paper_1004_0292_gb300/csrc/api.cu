@@ -287,6 +287,7 @@ extern "C" void ssqcd_default_opts(ssqcd_opts* o) {
   o->basis = 1;
   o->basis_max_bytes = 0.0;
   o->source_block = 0;
+  o->converged_tol = 1e-8;
 }
 
 namespace {
@@ -847,6 +848,9 @@ int extract_eigenpairs(ssqcd_lattice lat, const SolvePlan& P, DevBuf& yd, Krylov
   int cnt = 0;
   for (int k = 0; k < K; ++k) cnt += cntk[k];
   res->stats.n_accepted = cnt;
+  res->stats.n_converged = 0;
+  for (double r : res->residuals)
+    if (r <= P.o.converged_tol) ++res->stats.n_converged;
   if (P.hankel) {  // eigenvalues only: sort them
     std::sort(res->evals.begin(), res->evals.end());
   } else if (cnt > 0) {

@@ -21,6 +21,8 @@
 
 #include <cuda_runtime.h>
 
+#include "pair32.cuh"
+
 namespace ssqcd {
 namespace ff {
 
@@ -176,6 +178,127 @@ __device__ __forceinline__ cff cfma(cff c, cff u, cff v) {
   const float2 r_ = fma2(c.x, c.z, u.x, u.z, v.x, v.z, -u.y, -u.w, v.y, v.w);
   const float2 i_ = fma2(c.y, c.w, u.x, u.z, v.y, v.w, u.y, u.w, v.x, v.z);
   return make_float4(r_.x, i_.x, r_.y, i_.y);
+}
+
+// ---- complex float-float on register pairs -------------------------------------------
+// A complex float-float value {re.hi, im.hi, re.lo, im.lo} is two register
+// pairs: (re.hi, im.hi) and (re.lo, im.lo).  The real and imaginary parts of
+// cadd, csub and the three-term complex dot products above run the same
+// sequence of FP32 operations on different data, so they run here as one
+// sequence of paired instructions (pair32.cuh), lane 0 the real part and
+// lane 1 the imaginary part.  Every lane rounds exactly as the scalar code
+// above does, in the same order: the results are bit-identical, with half
+// the instructions.
+
+__device__ __forceinline__ void p_two_sum(f32x2_t a, f32x2_t b, f32x2_t& s, f32x2_t& e) {
+  s = ::ssqcd::add2(a, b);
+  const f32x2_t bb = ::ssqcd::sub2(s, a);
+  e = ::ssqcd::add2(::ssqcd::sub2(a, ::ssqcd::sub2(s, bb)), ::ssqcd::sub2(b, bb));
+}
+__device__ __forceinline__ void p_fast_two_sum(f32x2_t a, f32x2_t b, f32x2_t& s, f32x2_t& e) {
+  s = ::ssqcd::add2(a, b);
+  e = ::ssqcd::sub2(b, ::ssqcd::sub2(s, a));
+}
+__device__ __forceinline__ f32x2_t hi2(cff z) { return pk2(z.x, z.y); }
+__device__ __forceinline__ f32x2_t lo2(cff z) { return pk2(z.z, z.w); }
+__device__ __forceinline__ cff make2(f32x2_t h, f32x2_t l) {
+  const float2 a = upk2(h), b = upk2(l);
+  return make_float4(a.x, a.y, b.x, b.y);
+}
+// a + b and a - b (lane-wise float-float add of the real and imaginary parts)
+__device__ __forceinline__ cff p_cadd(cff a, cff b) {
+  f32x2_t s, e, h, l;
+  p_two_sum(hi2(a), hi2(b), s, e);
+  e = ::ssqcd::add2(e, ::ssqcd::add2(lo2(a), lo2(b)));
+  p_fast_two_sum(s, e, h, l);
+  return make2(h, l);
+}
+__device__ __forceinline__ cff p_csub(cff a, cff b) { return p_cadd(a, cneg(b)); }
+
+// sum_i A_i B_i over K paired float-float factors (hi and lo pairs), the
+// operation sequence of dot<K> in each lane
+template <int K>
+__device__ __forceinline__ cff p_dot(const f32x2_t (&ah)[K], const f32x2_t (&al)[K], const f32x2_t (&bh)[K],
+                                     const f32x2_t (&bl)[K]) {
+  f32x2_t s = ::ssqcd::mul2(ah[0], bh[0]);
+  f32x2_t lo = ::ssqcd::fma2(ah[0], bh[0], neg2(s));
+  lo = ::ssqcd::fma2(ah[0], bl[0], lo);
+  lo = ::ssqcd::fma2(al[0], bh[0], lo);
+#pragma unroll
+  for (int i = 1; i < K; ++i) {
+    const f32x2_t p = ::ssqcd::mul2(ah[i], bh[i]);
+    const f32x2_t e = ::ssqcd::fma2(ah[i], bh[i], neg2(p));
+    f32x2_t t;
+    p_two_sum(s, p, s, t);
+    lo = ::ssqcd::add2(lo, ::ssqcd::add2(e, t));
+    lo = ::ssqcd::fma2(ah[i], bl[i], lo);
+    lo = ::ssqcd::fma2(al[i], bh[i], lo);
+  }
+  f32x2_t h, l;
+  p_fast_two_sum(s, lo, h, l);
+  return make2(h, l);
+}
+
+// cdot3 / cdot3_conj on pairs: term 2b pairs (re u_b, re u_b) with
+// (re h_b, im h_b), term 2b + 1 pairs (-im u_b, im u_b) (conj: (im u_b,
+// -im u_b)) with (im h_b, re h_b) -- the factors of dot<6> in cdot3 for the
+// real part (lane 0) and the imaginary part (lane 1).
+template <bool CONJ>
+__device__ __forceinline__ cff p_cdot3_impl(cff u0, cff u1, cff u2, cff h0, cff h1, cff h2) {
+  const cff u[3] = {u0, u1, u2}, h[3] = {h0, h1, h2};
+  f32x2_t ah[6], al[6], bh[6], bl[6];
+#pragma unroll
+  for (int b = 0; b < 3; ++b) {
+    const float sg = CONJ ? 1.f : -1.f;
+    ah[2 * b] = pk2(u[b].x, u[b].x);
+    al[2 * b] = pk2(u[b].z, u[b].z);
+    ah[2 * b + 1] = pk2(sg * u[b].y, -sg * u[b].y);
+    al[2 * b + 1] = pk2(sg * u[b].w, -sg * u[b].w);
+    bh[2 * b] = hi2(h[b]);
+    bl[2 * b] = lo2(h[b]);
+    bh[2 * b + 1] = swap2(hi2(h[b]));
+    bl[2 * b + 1] = swap2(lo2(h[b]));
+  }
+  return p_dot<6>(ah, al, bh, bl);
+}
+__device__ __forceinline__ cff p_cdot3(cff u0, cff u1, cff u2, cff h0, cff h1, cff h2) {
+  return p_cdot3_impl<false>(u0, u1, u2, h0, h1, h2);
+}
+__device__ __forceinline__ cff p_cdot3_conj(cff u0, cff u1, cff u2, cff h0, cff h1, cff h2) {
+  return p_cdot3_impl<true>(u0, u1, u2, h0, h1, h2);
+}
+
+// c + u v for complex float-float c, v and a coefficient u given as its four
+// pairs U = {(u.re.hi, u.re.hi), (u.re.lo, u.re.lo), (-u.im.hi, u.im.hi),
+// (-u.im.lo, u.im.lo)} (p_coef): the operation sequence of cfma in each lane.
+struct PCoef {
+  f32x2_t a1h, a1l, a2h, a2l;
+};
+__device__ __forceinline__ PCoef p_coef(cff u) {
+  return PCoef{pk2(u.x, u.x), pk2(u.z, u.z), pk2(-u.y, u.y), pk2(-u.w, u.w)};
+}
+// v's pairs: (re.hi, im.hi), (re.lo, im.lo) and the same swapped
+struct PVal {
+  f32x2_t h, l, hs, ls;
+};
+__device__ __forceinline__ PVal p_val(cff v) {
+  const f32x2_t h = hi2(v), l = lo2(v);
+  return PVal{h, l, swap2(h), swap2(l)};
+}
+__device__ __forceinline__ void p_cfma(f32x2_t& ch, f32x2_t& cl, const PCoef& u, const PVal& v) {
+  const f32x2_t p1 = ::ssqcd::mul2(u.a1h, v.h);
+  const f32x2_t e1 = ::ssqcd::fma2(u.a1h, v.h, neg2(p1));
+  const f32x2_t p2 = ::ssqcd::mul2(u.a2h, v.hs);
+  const f32x2_t e2 = ::ssqcd::fma2(u.a2h, v.hs, neg2(p2));
+  f32x2_t s1, t1, s2, t2;
+  p_two_sum(ch, p1, s1, t1);
+  p_two_sum(s1, p2, s2, t2);
+  f32x2_t lo = ::ssqcd::add2(::ssqcd::add2(cl, ::ssqcd::add2(e1, e2)), ::ssqcd::add2(t1, t2));
+  lo = ::ssqcd::fma2(u.a1h, v.l, lo);
+  lo = ::ssqcd::fma2(u.a1l, v.h, lo);
+  lo = ::ssqcd::fma2(u.a2h, v.ls, lo);
+  lo = ::ssqcd::fma2(u.a2l, v.hs, lo);
+  p_fast_two_sum(s2, lo, ch, cl);
 }
 
 // Nearest float-float to an FP64 complex (hi = fl32(x), lo = fl32(x - hi);

@@ -1570,11 +1570,15 @@ basis_combine_kernel(char* const* __restrict__ tab, long long n, int L, const do
 // pairs once per tile), then the tile's sums enter FP64 accumulators, so at
 // most kCombTile terms share a float-float sum (rounding ~kCombTile 2^-48 of
 // their magnitudes, against the residuals' own 2^-48).  The FP64 pipe only
-// sees the per-tile conversions.
+// sees the per-tile conversions.  The complex float-float multiply-adds run
+// on register pairs (real and imaginary part in one paired instruction,
+// floatfloat.cuh p_cfma), in the operation order of ff::cfma.
 __global__ void __launch_bounds__(kCombThreads, 2)
 basis_combine_df_kernel(char* const* __restrict__ tab, long long n, int L, const double2* __restrict__ C, int O, int S,
                         const int* __restrict__ count, double2* __restrict__ out, int l0) {
-  __shared__ float4 s_w[kCombTile][kCombOut];
+  // coefficients as the four register pairs of ff::p_cfma (real part in lane
+  // 0, imaginary part in lane 1: one paired instruction for both)
+  __shared__ ff::PCoef s_w[kCombTile][kCombOut];
   __shared__ const float4* s_p[kCombTile];
   const int l = blockIdx.y + l0, o0 = blockIdx.z * kCombOut;
   const int no = min(kCombOut, O - o0);
@@ -1590,7 +1594,7 @@ basis_combine_df_kernel(char* const* __restrict__ tab, long long n, int L, const
     for (int t = threadIdx.x; t < kCombTile * kCombOut; t += kCombThreads) {
       const int ss = t / kCombOut, oo = t % kCombOut;
       const double2 c = (ss < ns && oo < no) ? C[((size_t)l * O + o0 + oo) * S + s0 + ss] : make_double2(0.0, 0.0);
-      s_w[ss][oo] = ff::from_double2(c);
+      s_w[ss][oo] = ff::p_coef(ff::from_double2(c));
     }
     if (threadIdx.x < kCombTile) {
       const int s = s0 + threadIdx.x;
@@ -1600,18 +1604,18 @@ basis_combine_df_kernel(char* const* __restrict__ tab, long long n, int L, const
     }
     __syncthreads();
     if (e < n) {
-      ff::cff acc[kCombOut];
+      f32x2_t ah[kCombOut], al[kCombOut];
 #pragma unroll
-      for (int o = 0; o < kCombOut; ++o) acc[o] = make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int o = 0; o < kCombOut; ++o) ah[o] = al[o] = 0ull;
 #pragma unroll 2
       for (int ss = 0; ss < ns; ++ss) {
-        const float4 x = s_p[ss][e];
+        const ff::PVal x = ff::p_val(s_p[ss][e]);
 #pragma unroll
-        for (int o = 0; o < kCombOut; ++o) acc[o] = ff::cfma(acc[o], s_w[ss][o], x);
+        for (int o = 0; o < kCombOut; ++o) ff::p_cfma(ah[o], al[o], s_w[ss][o], x);
       }
 #pragma unroll
       for (int o = 0; o < kCombOut; ++o) {
-        const double2 t = ff::to_double2(acc[o]);
+        const double2 t = ff::to_double2(ff::make2(ah[o], al[o]));
         accd[o].x += t.x;
         accd[o].y += t.y;
       }

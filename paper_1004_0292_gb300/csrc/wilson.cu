@@ -10,6 +10,8 @@
 // 192 B (out) + 576 B (links, shared by the rhs) of compulsory traffic.
 // FP32 spinors with FP16 (or FP32) 12-parameter links: HBM-bound; 96 B in,
 // 96 B out, 96 (192) B links per site.
+#include <cstdlib>
+
 #include "wilson_core.cuh"
 #include "wilson_df.cuh"
 
@@ -17,6 +19,16 @@ namespace ssqcd {
 namespace {
 
 using namespace wcore;
+
+// blocks an SM of the all-rhs FP32 stencil (register cap 65536 / (128 x
+// MinB)): 4 (128 registers) by default, 3 (170) with SSQCD_MRHS_MINB=3
+int mrhs_min_blocks() {
+  static const int v = [] {
+    const char* e = std::getenv("SSQCD_MRHS_MINB");
+    return (e != nullptr && std::atoi(e) == 3) ? 3 : 4;
+  }();
+  return v;
+}
 
 template <int BLOCK>
 __device__ __forceinline__ double block_sum(double v, double* sh) {
@@ -105,6 +117,22 @@ wilson32_kernel(Geometry g, LK lk, const float2* __restrict__ in_all,
   }
 }
 
+// FP32 spinors, all rhs of 32 sites a block (see mrhs_block): warp w takes
+// direction w, its links are loaded once for every rhs.  MinB blocks an SM.
+template <typename LK, int MinB>
+__global__ void __launch_bounds__(128, MinB)
+wilson32m_kernel(Geometry g, LK lk, const float2* __restrict__ in_all, float2* __restrict__ out_all, int nrhs,
+                 float c0, float c1, float* __restrict__ dot_partial) {
+  __shared__ float2 sh[12 * 4 * 32];
+  __shared__ float shred[4];
+  switch (threadIdx.x >> 5) {
+    case 0: mrhs_block<0>(g, lk, in_all, out_all, nrhs, c0, c1, sh, shred, dot_partial); break;
+    case 1: mrhs_block<1>(g, lk, in_all, out_all, nrhs, c0, c1, sh, shred, dot_partial); break;
+    case 2: mrhs_block<2>(g, lk, in_all, out_all, nrhs, c0, c1, sh, shred, dot_partial); break;
+    default: mrhs_block<3>(g, lk, in_all, out_all, nrhs, c0, c1, sh, shred, dot_partial); break;
+  }
+}
+
 // Float-float stencil (SSQCD_DF): out = c0 in + c1 A in with float-float
 // spinors and links; see wilson_df.cuh.
 __global__ void __launch_bounds__(kStencilThreadsDF)
@@ -182,9 +210,31 @@ int wilson64(const Geometry& g, const double2* u, const double2* in, double2* ou
   return SSQCD_OK;
 }
 
+int wilson32_blocks(const Geometry& g) { return (g.V + 31) / 32; }
+
 int wilson32(const Geometry& g, const void* links, int link_bits, const float2* in, float2* out, int nrhs, float c0,
              float c1, float* dot_partial, const int* skip_if_zero, cudaStream_t s) {
   if (nrhs <= 0) return SSQCD_OK;
+  if (skip_if_zero == nullptr) {
+    // all rhs of a block of sites: links loaded once for every rhs
+    const int nb = wilson32_blocks(g);
+    const LinksF16 l16{static_cast<const uint2*>(links), g.V};
+    const LinksF32 l32{static_cast<const float4*>(links), g.V};
+    if (mrhs_min_blocks() == 3) {
+      if (link_bits == 16)
+        wilson32m_kernel<LinksF16, 3><<<nb, 128, 0, s>>>(g, l16, in, out, nrhs, c0, c1, dot_partial);
+      else
+        wilson32m_kernel<LinksF32, 3><<<nb, 128, 0, s>>>(g, l32, in, out, nrhs, c0, c1, dot_partial);
+    } else {
+      if (link_bits == 16)
+        wilson32m_kernel<LinksF16, 4><<<nb, 128, 0, s>>>(g, l16, in, out, nrhs, c0, c1, dot_partial);
+      else
+        wilson32m_kernel<LinksF32, 4><<<nb, 128, 0, s>>>(g, l32, in, out, nrhs, c0, c1, dot_partial);
+    }
+    count_launches(1);
+    SS_CHECK_LAUNCH();
+    return SSQCD_OK;
+  }
   dim3 grid((g.V + kSiteThreads - 1) / kSiteThreads, nrhs);
   if (link_bits == 16)
     wilson32_kernel<<<grid, kSiteThreads, 0, s>>>(g, LinksF16{static_cast<const uint2*>(links), g.V}, in, out, c0, c1,

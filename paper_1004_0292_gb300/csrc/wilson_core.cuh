@@ -23,6 +23,7 @@
 #pragma once
 
 #include "internal.h"
+#include "pair32.cuh"
 
 namespace ssqcd {
 namespace wcore {
@@ -577,6 +578,189 @@ __device__ __forceinline__ void block_hops32(const LK& lk, const float2* __restr
     }
   }
   reduce_dirs(acc, sh, acc_out);
+}
+
+// ---- FP32, many right-hand sides a block ----------------------------------------------
+// The FP32 stencil with 12-parameter links is bound by HBM only if its
+// instruction count per site and rhs stays below ~1100 (the issue rate of
+// 152 SMs against the 1632 compulsory bytes of a site with eight rhs).  The
+// one-thread-per-site form above spends ~3000: every rhs rebuilds the third
+// link row and recomputes the neighbour addresses.  Here a block covers 32
+// sites for every rhs: warp w takes direction mu = w (forward and backward
+// hop) for the 32 sites, loads and rebuilds its two links once, keeps them
+// in registers pre-packed for paired FP32 arithmetic, and then loops over
+// the rhs.  Per rhs the four directions' sums meet in shared memory and warp
+// w finishes spinor components 3w..3w+2.
+//
+// Paired arithmetic: Blackwell executes fma/add/sub.rn.f32x2 on a register
+// pair as one instruction (two lanes of FP32).  A complex multiply-add
+// acc += u h is then two paired FMAs,
+//   acc += (u.x, u.x) (h.x, h.y) + (-u.y, u.y) (h.y, h.x),
+// with the link pairs (u.x, u.x), (-u.y, u.y) formed once per thread (they
+// serve every rhs) and the swapped half-spinor (h.y, h.x) once per hop; the
+// 72 FP32 FMAs of a hop's link product become 36 paired ones.
+// unit (+1, -1, +i, -i) times z, as a pair
+__device__ __forceinline__ f32x2_t unit2(int code, f32x2_t z) {
+  const float2 v = upk2(z);
+  switch (code) {
+    case P1: return z;
+    case M1: return pk2(-v.x, -v.y);
+    case PI: return pk2(-v.y, v.x);
+    default: return pk2(v.y, -v.x);
+  }
+}
+
+// A link rebuilt from its 12 parameters, packed for the paired products:
+// a[e] = (u.x, u.x), b[e] = (-u.y, u.y) for element e = 3 row + column of U
+// (forward hop, U h) or of U^H (backward hop, U^H h: element (a, b) of U^H
+// is conj(U_ba), so b holds (u.y, -u.y) of U_ba).
+struct PackedLink {
+  f32x2_t a[9], b[9];
+};
+
+template <typename LK>
+__device__ __forceinline__ void load_packed(const LK& lk, int mu, int site, bool dagger, PackedLink& P) {
+  Link32 L;
+  lk.load(mu, site, L);
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const float2 u = dagger ? L.e[c][r] : L.e[r][c];
+      const float uy = dagger ? -u.y : u.y;
+      P.a[3 * r + c] = pk2(u.x, u.x);
+      P.b[3 * r + c] = pk2(-uy, uy);
+    }
+}
+
+// wv[a] = sum_b M_ab h_b for the packed link M, with hs[b] = (h_b.y, h_b.x)
+__device__ __forceinline__ void link_mul2(const PackedLink& P, const f32x2_t (&h)[3], const f32x2_t (&hs)[3],
+                                          f32x2_t (&wv)[3]) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    f32x2_t t = mul2(P.a[3 * a], h[0]);
+    t = fma2(P.b[3 * a], hs[0], t);
+    t = fma2(P.a[3 * a + 1], h[1], t);
+    t = fma2(P.b[3 * a + 1], hs[1], t);
+    t = fma2(P.a[3 * a + 2], h[2], t);
+    t = fma2(P.b[3 * a + 2], hs[2], t);
+    wv[a] = t;
+  }
+}
+
+// One hop of direction MU (DIR = +1 forward, -1 backward) for right-hand
+// side `in`, neighbour nb, accumulated into acc[12] (FIRST: set instead of
+// add).  Forward: h = psi_u - B psi_l, lower part -B^H wv; backward:
+// h = psi_u + B psi_l, lower part +B^H wv; an antiperiodic t wrap negates h.
+template <int MU, int DIR, bool FIRST>
+__device__ __forceinline__ void hop_mrhs(const PackedLink& P, const float2* __restrict__ in, int nb, int V,
+                                         bool negate, f32x2_t (&acc)[12]) {
+  using S = Spin<MU>;
+  f32x2_t h[2][3], hs[2][3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const float2 u0 = __ldg(in + (0 * 3 + a) * V + nb);
+    const float2 u1 = __ldg(in + (1 * 3 + a) * V + nb);
+    const float2 l0 = __ldg(in + ((2 + S::bcol0) * 3 + a) * V + nb);
+    const float2 l1 = __ldg(in + ((2 + S::bcol1) * 3 + a) * V + nb);
+    const f32x2_t bl0 = unit2(S::bcode0, pk2(l0.x, l0.y)), bl1 = unit2(S::bcode1, pk2(l1.x, l1.y));
+    f32x2_t h0 = DIR > 0 ? sub2(pk2(u0.x, u0.y), bl0) : add2(pk2(u0.x, u0.y), bl0);
+    f32x2_t h1 = DIR > 0 ? sub2(pk2(u1.x, u1.y), bl1) : add2(pk2(u1.x, u1.y), bl1);
+    if (MU == 3 && negate) {
+      h0 = unit2(M1, h0);
+      h1 = unit2(M1, h1);
+    }
+    h[0][a] = h0;
+    h[1][a] = h1;
+    hs[0][a] = swap2(h0);
+    hs[1][a] = swap2(h1);
+  }
+  f32x2_t wv[2][3];
+  link_mul2(P, h[0], hs[0], wv[0]);
+  link_mul2(P, h[1], hs[1], wv[1]);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const f32x2_t lo0 = unit2(S::hcode0, wv[S::hcol0][a]), lo1 = unit2(S::hcode1, wv[S::hcol1][a]);
+    if (FIRST) {
+      acc[0 * 3 + a] = wv[0][a];
+      acc[1 * 3 + a] = wv[1][a];
+      acc[2 * 3 + a] = DIR > 0 ? unit2(M1, lo0) : lo0;
+      acc[3 * 3 + a] = DIR > 0 ? unit2(M1, lo1) : lo1;
+    } else {
+      acc[0 * 3 + a] = add2(acc[0 * 3 + a], wv[0][a]);
+      acc[1 * 3 + a] = add2(acc[1 * 3 + a], wv[1][a]);
+      acc[2 * 3 + a] = DIR > 0 ? sub2(acc[2 * 3 + a], lo0) : add2(acc[2 * 3 + a], lo0);
+      acc[3 * 3 + a] = DIR > 0 ? sub2(acc[3 * 3 + a], lo1) : add2(acc[3 * 3 + a], lo1);
+    }
+  }
+}
+
+// out_r = c0 in_r + c1 A in_r for the rhs r = 0..nrhs-1 of 32 sites
+// (block of 128 threads, warp w = direction MU = w); dot_partial (optional):
+// per rhs the block's share of Re <in_r, out_r> at dot_partial[r * gridDim.x
+// + blockIdx.x].  sh: 12 x 4 x 32 float2.
+template <int MU, typename LK>
+__device__ __forceinline__ void mrhs_block(const Geometry& g, const LK& lk, const float2* __restrict__ in_all,
+                                           float2* __restrict__ out_all, int nrhs, float c0, float c1,
+                                           float2* sh, float* shred, float* __restrict__ dot_partial) {
+  const int lane = threadIdx.x & 31;
+  const int s = blockIdx.x * 32 + lane;
+  const int V = g.V;
+  const bool act = s < V;
+  PackedLink Pf, Pb;
+  int nbf = 0, nbb = 0;
+  bool wf = false, wb = false;
+  if (act) {
+    const Coords c = site_coords(s, g);
+    nbf = neighbour<MU, +1>(s, c, g, wf);
+    nbb = neighbour<MU, -1>(s, c, g, wb);
+    load_packed(lk, MU, s, false, Pf);
+    load_packed(lk, MU, nbb, true, Pb);
+  }
+  const bool negf = wf && g.bc_t < 0, negb = wb && g.bc_t < 0;
+  const float mk = -(float)g.kappa;
+  const float sg = MU < 2 ? c1 : -c1;  // gamma5 on spin MU of components 3 MU .. 3 MU + 2
+  for (int r = 0; r < nrhs; ++r) {
+    const float2* in = in_all + (size_t)r * 12 * V;
+    f32x2_t acc[12];
+    if (act) {
+      hop_mrhs<MU, +1, true>(Pf, in, nbf, V, negf, acc);
+      hop_mrhs<MU, -1, false>(Pb, in, nbb, V, negb, acc);
+    } else {
+#pragma unroll
+      for (int i = 0; i < 12; ++i) acc[i] = 0ull;
+    }
+#pragma unroll
+    for (int i = 0; i < 12; ++i) sh[(i * 4 + MU) * 32 + lane] = upk2(acc[i]);
+    __syncthreads();
+    float dot = 0.f;
+    if (act) {
+      float2* out = out_all + (size_t)r * 12 * V;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const int i = 3 * MU + k;
+        const f32x2_t d = add2(add2(pk2(sh[(i * 4 + 0) * 32 + lane].x, sh[(i * 4 + 0) * 32 + lane].y),
+                                    pk2(sh[(i * 4 + 1) * 32 + lane].x, sh[(i * 4 + 1) * 32 + lane].y)),
+                               add2(pk2(sh[(i * 4 + 2) * 32 + lane].x, sh[(i * 4 + 2) * 32 + lane].y),
+                                    pk2(sh[(i * 4 + 3) * 32 + lane].x, sh[(i * 4 + 3) * 32 + lane].y)));
+        const float2 dv = upk2(d);
+        const float2 p = __ldg(in + i * V + s);
+        float2 o;
+        o.x = fmaf(sg, fmaf(mk, dv.x, p.x), c0 * p.x);
+        o.y = fmaf(sg, fmaf(mk, dv.y, p.y), c0 * p.y);
+        out[i * V + s] = o;
+        dot = fmaf(p.x, o.x, fmaf(p.y, o.y, dot));
+      }
+    }
+    if (dot_partial != nullptr) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) dot += __shfl_down_sync(0xffffffffu, dot, o);
+      if (lane == 0) shred[MU] = dot;
+    }
+    __syncthreads();
+    if (dot_partial != nullptr && threadIdx.x == 0)
+      dot_partial[(size_t)r * gridDim.x + blockIdx.x] = (shred[0] + shred[1]) + (shred[2] + shred[3]);
+  }
 }
 
 }  // namespace wcore

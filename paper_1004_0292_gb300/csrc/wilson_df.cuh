@@ -30,7 +30,9 @@ struct LinksDF {
 // B_mu^H).  Against two hops per warp with a 12-component accumulator this
 // holds half the registers per thread, so more warps hide the latency of
 // the float-float chains, and stays balanced next to the concurrent
-// shift-update kernel.
+// shift-update kernel.  The complex float-float operations run on register
+// pairs (real and imaginary part in the two lanes of one paired
+// instruction, floatfloat.cuh), bit-identical to the scalar form.
 constexpr int kStencilThreadsDF = 256;
 
 template <int MU, int DIR>
@@ -48,11 +50,11 @@ __device__ __forceinline__ void hop_one_df(const LinksDF& lk, const float4* __re
     const float4 l0 = __ldg(in + ((2 + S::bcol0) * 3 + a) * V + nb);
     const float4 l1 = __ldg(in + ((2 + S::bcol1) * 3 + a) * V + nb);
     if (DIR > 0) {  // (1 - gamma_mu): h = psi_u - B psi_l
-      h[0][a] = ff::csub(u0, ff::unit_mul(S::bcode0, l0));
-      h[1][a] = ff::csub(u1, ff::unit_mul(S::bcode1, l1));
+      h[0][a] = ff::p_csub(u0, ff::unit_mul(S::bcode0, l0));
+      h[1][a] = ff::p_csub(u1, ff::unit_mul(S::bcode1, l1));
     } else {  // (1 + gamma_mu): h = psi_u + B psi_l
-      h[0][a] = ff::cadd(u0, ff::unit_mul(S::bcode0, l0));
-      h[1][a] = ff::cadd(u1, ff::unit_mul(S::bcode1, l1));
+      h[0][a] = ff::p_cadd(u0, ff::unit_mul(S::bcode0, l0));
+      h[1][a] = ff::p_cadd(u1, ff::unit_mul(S::bcode1, l1));
     }
   }
   if (MU == 3 && w && g.bc_t < 0) {
@@ -66,12 +68,12 @@ __device__ __forceinline__ void hop_one_df(const LinksDF& lk, const float4* __re
   for (int a = 0; a < 3; ++a) {
     if (DIR > 0) {  // U_mu(x) h: row a
       const float4 ua0 = lk.get(MU, a, 0, s), ua1 = lk.get(MU, a, 1, s), ua2 = lk.get(MU, a, 2, s);
-      out[(0 * 3 + a) * 32] = ff::cdot3(ua0, ua1, ua2, h[0][0], h[0][1], h[0][2]);
-      out[(1 * 3 + a) * 32] = ff::cdot3(ua0, ua1, ua2, h[1][0], h[1][1], h[1][2]);
+      out[(0 * 3 + a) * 32] = ff::p_cdot3(ua0, ua1, ua2, h[0][0], h[0][1], h[0][2]);
+      out[(1 * 3 + a) * 32] = ff::p_cdot3(ua0, ua1, ua2, h[1][0], h[1][1], h[1][2]);
     } else {  // U_mu(x - mu)^H h: column a, conjugated
       const float4 u0a = lk.get(MU, 0, a, nb), u1a = lk.get(MU, 1, a, nb), u2a = lk.get(MU, 2, a, nb);
-      out[(0 * 3 + a) * 32] = ff::cdot3_conj(u0a, u1a, u2a, h[0][0], h[0][1], h[0][2]);
-      out[(1 * 3 + a) * 32] = ff::cdot3_conj(u0a, u1a, u2a, h[1][0], h[1][1], h[1][2]);
+      out[(0 * 3 + a) * 32] = ff::p_cdot3_conj(u0a, u1a, u2a, h[0][0], h[0][1], h[0][2]);
+      out[(1 * 3 + a) * 32] = ff::p_cdot3_conj(u0a, u1a, u2a, h[1][0], h[1][1], h[1][2]);
     }
   }
 }
@@ -90,7 +92,7 @@ __device__ __forceinline__ float4 hop_sum_df(const float4* __restrict__ sh, int 
   if (sp < 2) {
     acc = base[(0 * 6 + sp * 3 + a) * 32];
 #pragma unroll
-    for (int hp = 1; hp < 8; ++hp) acc = ff::cadd(acc, base[(hp * 6 + sp * 3 + a) * 32]);
+    for (int hp = 1; hp < 8; ++hp) acc = ff::p_cadd(acc, base[(hp * 6 + sp * 3 + a) * 32]);
   } else {
     const int rr = sp - 2;
 #pragma unroll
@@ -100,7 +102,7 @@ __device__ __forceinline__ float4 hop_sum_df(const float4* __restrict__ sh, int 
       const int col = rr == 0 ? hcol[0][mu] : hcol[1][mu];
       const int code = rr == 0 ? hcode[0][mu] : hcode[1][mu];
       const float4 t = ff::unit_mul(fwd ? (code ^ 1) : code, base[(hp * 6 + col * 3 + a) * 32]);
-      acc = hp == 0 ? t : ff::cadd(acc, t);
+      acc = hp == 0 ? t : ff::p_cadd(acc, t);
     }
   }
   return acc;

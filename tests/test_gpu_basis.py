@@ -110,8 +110,8 @@ def test_switch_to_updates_at_the_memory_cap(case):
 def test_basis_eigenpairs_full_size_match_update_form():
     import torch
     ss = gpu_module()
-    w = bench.WORKLOAD
-    U, src = bench.make_inputs(0)
+    w = bench.CONFIG2
+    U, src = bench.make_inputs(0, bench.CONFIG2)
     lat = ss.create_lattice(w["dims"], w["kappa"], w["bc_t"], stream=torch.cuda.Stream())
     ss.upload_gauge(lat, U)
     out = {}

@@ -107,8 +107,8 @@ def test_dfshift_eigenpairs_full_size(ss):
     # the 8^4 workload (N = 32, L = 4, M = 8, beta 0.6) on a side stream with
     # graph replay, as the benchmark runs it
     import torch
-    w = bench.WORKLOAD
-    U, src = bench.make_inputs(0)
+    w = bench.CONFIG2
+    U, src = bench.make_inputs(0, bench.CONFIG2)
     lat = ss.create_lattice(w["dims"], w["kappa"], w["bc_t"], precision=ss.FP64_DFSHIFT,
                             stream=torch.cuda.Stream())
     ss.upload_gauge(lat, U)
@@ -198,8 +198,8 @@ def test_df_eigenpairs_config1(ss):
 
 def test_df_eigenpairs_full_size(ss):
     import torch
-    w = bench.WORKLOAD
-    U, src = bench.make_inputs(0)
+    w = bench.CONFIG2
+    U, src = bench.make_inputs(0, bench.CONFIG2)
     lat = ss.create_lattice(w["dims"], w["kappa"], w["bc_t"], precision=ss.DF, stream=torch.cuda.Stream())
     ss.upload_gauge(lat, U)
     res = ss.ss_solve(lat, w["interval"], w["N"], w["M"], src, beta=w["beta"], nprime=w["nprime"], tol=w["tol"])
@@ -224,8 +224,8 @@ def test_refined_ritz_vectors_full_size(ss, precision):
     # residuals, and the spurious value itself (whose refined vector would
     # duplicate its neighbour) is dropped.
     import torch
-    w = bench.WORKLOAD
-    U, src = bench.make_inputs(0)
+    w = bench.CONFIG2
+    U, src = bench.make_inputs(0, bench.CONFIG2)
     lat = ss.create_lattice(w["dims"], w["kappa"], w["bc_t"], precision=getattr(ss, precision),
                             stream=torch.cuda.Stream())
     ss.upload_gauge(lat, U)

@@ -24,8 +24,8 @@ GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "windows.json")
 def setup():
     import torch
     ss = gpu_module()
-    w = bench.WORKLOAD
-    U, src = bench.make_inputs(0)
+    w = bench.CONFIG2
+    U, src = bench.make_inputs(0, bench.CONFIG2)
     stream = torch.cuda.Stream()
     lat = ss.create_lattice(w["dims"], w["kappa"], w["bc_t"], stream=stream)
     ss.upload_gauge(lat, U)

@@ -31,8 +31,8 @@ def setup():
     ss.upload_gauge(lat4, U4)
     lat4df = ss.create_lattice(dims4, 0.13, -1, precision=ss.DF, stream=stream)
     ss.upload_gauge(lat4df, U4)
-    w = bench.WORKLOAD
-    U8, src8 = bench.make_inputs(0)
+    w = bench.CONFIG2
+    U8, src8 = bench.make_inputs(0, bench.CONFIG2)
     lat8 = ss.create_lattice(w["dims"], w["kappa"], w["bc_t"], precision=ss.FP64_DFSHIFT, stream=stream)
     ss.upload_gauge(lat8, U8)
     reqs = [

@@ -78,9 +78,11 @@ def test_hankel_extraction_config1(ss):
     exact = _reference_spectrum("haar_4x4x4x4_k0.13_s1")
     exact = np.sort(exact[(exact >= c["interval"][0]) & (exact <= c["interval"][1])])
     assert len(ev) == len(exact) == 8
-    # the oracle's Hankel extraction of this case reaches 1.5e-5 (its own
-    # moments, shifted CG at tol 1e-12); the bar leaves a factor ~7
-    assert np.max(np.abs(ev - exact) / exact) <= 1e-4
+    # the oracle's Hankel extraction of this case reaches 1.51e-5 (its own
+    # moments, shifted CG at tol 1e-12), the conditioning of the Hankel matrix
+    # (smallest kept eigenvalue ~1.4e-11 of the largest); the GPU reduction
+    # (Hermitian eigendecomposition of H) reaches the same
+    assert np.max(np.abs(ev - exact) / exact) <= 2e-5
     # the oracle's Hankel extraction on its own shifted-CG moments
     from oracle import contour, hankel, moments, shifted_cg, wilson
     a, b = c["interval"]
@@ -96,6 +98,8 @@ def test_hankel_extraction_config1(ss):
     lam_o = g + r * hankel.block_hankel_eigs(src.reshape(c["L"], -1).T, S, rank_tol=1e-12)
     lam_o = np.sort(lam_o[(np.abs(lam_o.imag) < 1e-6) & (lam_o.real >= a) & (lam_o.real <= b)].real)
     assert len(lam_o) == 8
-    assert np.max(np.abs(ev - lam_o) / lam_o) <= 1e-4
+    # the two reductions of (nearly) the same moments agree far below their
+    # common error against the exact spectrum
+    assert np.max(np.abs(ev - lam_o) / lam_o) <= 1e-8
     with pytest.raises(Exception):
         ss.ss_eigpairs(res, want_vectors=True)

@@ -91,3 +91,21 @@ def test_mixed_stencil_matches_oracle_on_fp16_links(ss, dims, kind, bc):
     # and the FP16 links perturb the true operator by ~2^-11 relative
     ref = wilson.apply_H(U, psi, kappa, dims, bc)
     assert np.linalg.norm(got - ref) <= 2e-3 * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("dims,nrhs,bc", [((16, 16, 16, 32), 8, -1), ((5, 3, 4, 6), 3, 1), ((33, 1, 2, 2), 1, -1)])
+def test_mixed_stencil_all_rhs_kernel(ss, dims, nrhs, bc):
+    """The FP32 stencil that applies every rhs of a block of 32 sites with
+    the block's links loaded once (paired FP32 arithmetic): every rhs against
+    the oracle on the FP16-rounded links, at the 16^3 x 32 size of the
+    stencil measurement with 8 rhs, an odd lattice, and a ragged last block
+    (V = 132 = 4 x 32 + 4)."""
+    kappa = 0.135
+    U = synthetic.gauge_field(dims, "smooth", seed=5, eps=0.5)
+    psi = synthetic.gaussian_sources(dims, nrhs, seed=6)
+    lat = ss.create_lattice(dims, kappa, bc, precision=ss.MIXED)
+    ss.upload_gauge(lat, U)
+    got = ss.apply_H_mixed(lat, psi)
+    ref16 = wilson.apply_H(fp16_rounded_links(U), psi, kappa, dims, bc)
+    for r in range(nrhs):
+        assert np.max(np.abs(got[r] - ref16[r])) <= 2e-6 * np.max(np.abs(ref16[r]))

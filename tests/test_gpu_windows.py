@@ -79,6 +79,7 @@ def test_window_list_one_seed_run_matches_separate_windows(setup):
     assert len(exact) == 16 and len(ev) == 16
     assert np.max(np.abs(ev - exact) / np.abs(exact)) <= 1e-10
     assert np.max(rs) <= 1e-8
+    assert st["n_converged"] == 16 == st["n_accepted"]
     sep = []
     for a, b in wins:
         r1 = ss.ss_solve(lat, (a, b), N, M, src, beta=0.3, nprime=Np)
