@@ -337,10 +337,11 @@ def run_ours(args):
     if not args.no_serving:
         stencil_large = run_stencil_large(ss, stream, peaks)
 
-    serving = None
+    serving = serving_large = None
     if not args.no_serving:
         U8, _ = make_inputs(rank, CONFIG2)
         serving = run_serving(ss, stream, U8, seed=17 + rank)
+        serving_large = run_serving_large(ss, stream, U, src, U8, seed=23 + rank)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -389,7 +390,7 @@ def run_ours(args):
                                         "timed_iterations": it_tot, "rhs": Lb},
             "e2e": e2e, "cpu_baseline": cpu, "clocks": clk, "gpu_launches": int(launches), "mixed": mixed,
             "mixed_fp32_fp16": config2.pop("fp32_fp16") if config2 else None,
-            "config2": config2, "serving": serving, "stencil_large": stencil_large,
+            "config2": config2, "serving": serving, "serving_16x32": serving_large, "stencil_large": stencil_large,
         }
         print(json.dumps(out), flush=True)
     if world > 1:
@@ -530,6 +531,11 @@ def run_stencil_large(ss, stream, peaks):
         gbs = byts / (ms / 1e3) / 1e9
         out[name] = {"us_per_call": 1e3 * ms, "hbm_gbs": gbs, "hbm_frac": gbs / peaks["hbm_gbs"],
                      "tflops": STENCIL_FLOP_PER_SITE * V * c["rhs"] / (ms / 1e3) / 1e12}
+        if prec in (ss.MIXED, ss.MIXED_F32LINKS):
+            v, us = ss.stencil_tuning(lat, c["rhs"])
+            out[name]["variant"] = {"chosen": v, "us_per_variant": us,
+                                    "variants": ["all rhs of 32 sites a block, 4 blocks/SM", "same, 3 blocks/SM",
+                                                 "thread per site and rhs pair, 4 blocks/SM", "same, 3 blocks/SM"]}
         del lat
     return out
 
@@ -599,8 +605,10 @@ def run_serving(ss, stream, U8, seed=17):
                 continue
             _, _, rs, _ = ss.ss_eigpairs(res, want_vectors=False)
             pairs += int(np.sum(rs <= RES_TOL))
+        deferred = srv.deferred()
         srv.close()
         return {"eigenpairs_per_s": pairs / (t_end - arrive[0]), "eigenpairs": pairs, "failed": failed,
+                "waited_on_memory": deferred,
                 "latency_ms": {"p50": float(np.percentile(lat_ms, 50)), "p99": float(np.percentile(lat_ms, 99))},
                 "span_s": t_end - arrive[0]}
 
@@ -640,6 +648,91 @@ def _host_cores():
         return max([i.get("num_threads", 1) for i in info] + [1])
     except Exception:
         return os.cpu_count() or 1
+
+
+SERVING_LARGE = dict(rate_per_s=20.0, budget_bytes=220e9, n_small=6)
+
+
+def run_serving_large(ss, stream, U3, src3, U8, seed=23):
+    """The scheduler with the headline lattice resident: requests on the
+    16^3 x 32 field (the headline's two windows, and its positive window
+    alone; L = 8 in source blocks of two, 128 GB of stored residuals a block)
+    mixed with small 8^4 and 4^4 requests, Poisson arrivals (mean 20/s,
+    seeded), and a 220 GB memory budget, so that the large requests cannot
+    run together and admission defers them.  Plain FP64 and float-float
+    lattices.  Reports p50/p99 latency, eigenpairs/s at residual <= 1e-8 over
+    the span, and how many requests waited on memory."""
+    import torch
+
+    import synthetic
+    w, w8 = WORKLOAD, CONFIG2
+    dims4 = (4, 4, 4, 4)
+    U4 = synthetic.gauge_field(dims4, "haar", seed=1)
+    rng = np.random.default_rng(seed)
+    plan = [("16", [list(x) for x in w["windows"]], src3), ("16", [list(w["windows"][1])], src3)]
+    for i in range(SERVING_LARGE["n_small"]):
+        if i % 2 == 0:
+            plan.append(("8", [list(w8["interval"])], synthetic.gaussian_sources(w8["dims"], 4, seed=7000 + i)))
+        else:
+            plan.append(("4", [[0.374, 0.3930]], synthetic.gaussian_sources(dims4, 3, seed=7100 + i)))
+    order = rng.permutation(len(plan))
+    plan = [plan[i] for i in order]
+    arrive = np.cumsum(rng.exponential(1.0 / SERVING_LARGE["rate_per_s"], len(plan)))
+    kw = {"16": dict(N=w["N"], M=w["M"], beta=w["beta"], nprime=w["nprime"], source_block=w["source_block"],
+                     basis_max_bytes=w["basis_max_bytes"]),
+          "8": dict(N=w8["N"], M=w8["M"], beta=w8["beta"], nprime=w8["nprime"]),
+          "4": dict(N=16, M=8, beta=0.3, nprime=14)}
+    out = {"requests": len(plan), "arrivals": f"Poisson, mean {SERVING_LARGE['rate_per_s']}/s, seed {seed}",
+           "budget_bytes": SERVING_LARGE["budget_bytes"],
+           "mix": "2 on the 16^3x32 headline field (both windows; the positive window), L=8 in blocks of 2; "
+                  "3 on the 8^4 field (L=4, N=32); 3 on the 4^4 Haar field (L=3, N=16)"}
+    for name, prec in (("plain_fp64", ss.FP64), ("mixed", ss.DF)):
+        lats = {"16": ss.create_lattice(w["dims"], w["kappa"], w["bc_t"], precision=prec, stream=stream),
+                "8": ss.create_lattice(w8["dims"], w8["kappa"], w8["bc_t"], precision=prec, stream=stream),
+                "4": ss.create_lattice(dims4, 0.13, -1, precision=prec, stream=stream)}
+        ss.upload_gauge(lats["16"], U3)
+        ss.upload_gauge(lats["8"], U8)
+        ss.upload_gauge(lats["4"], U4)
+        torch.cuda.synchronize()
+        srv = ss.Server(memory_budget=int(SERVING_LARGE["budget_bytes"]))
+        ids, t0, nxt = [], time.perf_counter(), 0
+        while True:
+            now = time.perf_counter() - t0
+            while nxt < len(plan) and arrive[nxt] <= now:
+                key, wins, src = plan[nxt]
+                k = dict(kw[key])
+                N, M = k.pop("N"), k.pop("M")
+                ids.append((key, srv.submit_windows(lats[key], wins, N, M, src, **k)))
+                nxt += 1
+            q, r, f = srv.counts()
+            if nxt == len(plan) and q == 0 and r == 0:
+                break
+            if r > 0 or q > 0:
+                srv.progress(wait=(nxt == len(plan) or arrive[nxt] - now > 0.002))
+            else:
+                time.sleep(max(0.0, arrive[nxt] - now))
+        t_end = time.perf_counter() - t0
+        lat_ms, pairs, failed, per = [], 0, 0, {}
+        for key, i in ids:
+            state, ms = srv.status(i)
+            lat_ms.append(ms)
+            res = srv.take(i)
+            if res.status != ss.OK:
+                failed += 1
+                continue
+            _, _, rs, _ = ss.ss_eigpairs(res, want_vectors=False)
+            good = int(np.sum(rs <= RES_TOL))
+            pairs += good
+            per.setdefault(key, []).append({"latency_ms": ms, "eigenpairs": good})
+        deferred = srv.deferred()
+        srv.close()
+        out[name] = {"eigenpairs_per_s": pairs / (t_end - arrive[0]), "eigenpairs": pairs, "failed": failed,
+                     "waited_on_memory": deferred, "span_s": t_end - arrive[0],
+                     "latency_ms": {"p50": float(np.percentile(lat_ms, 50)), "p99": float(np.percentile(lat_ms, 99))},
+                     "per_lattice": per}
+        del lats
+    out["mixed_vs_plain"] = out["mixed"]["eigenpairs_per_s"] / out["plain_fp64"]["eigenpairs_per_s"]
+    return out
 
 
 def cpu_baseline(budget_s=20.0, gpu_iterations=None, pairs=48, sample_iters=None):

@@ -380,6 +380,14 @@ int ssqcd_server_create(size_t memory_budget, ssqcd_server* out);
 int ssqcd_server_submit(ssqcd_server srv, ssqcd_lattice lat, const double interval[2], int N, int M,
                         int L, const ssqcd_opts* opts, long long* id);
 
+/* Queue a request for several windows out of one shifted-CG run; arguments
+ * as ssqcd_ss_solve_windows.  With opts.source_block = B < L the request
+ * runs its sources in blocks of B, one shifted-CG run after another (its
+ * admission estimate counts one block's shift vectors or stored residuals
+ * and the moments of all L sources).  Errors as ssqcd_server_submit. */
+int ssqcd_server_submit_windows(ssqcd_server srv, ssqcd_lattice lat, int K, const double* intervals, int N, int M,
+                                int L, const ssqcd_opts* opts, long long* id);
+
 /* Admit, advance and finish requests.  wait = 0 never blocks on the device
  * (returns at once when all running work is still in flight); wait = 1
  * blocks until at least one running request could move.  *completed (may be
@@ -400,6 +408,10 @@ int ssqcd_server_take(ssqcd_server srv, long long id, ssqcd_result* out);
 /* Device bytes the scheduler reserves for a request while it runs (its
  * admission estimate). */
 int ssqcd_server_request_bytes(ssqcd_server srv, long long id, size_t* bytes);
+
+/* Requests so far that waited at the head of the queue because the running
+ * requests' memory left no room for them (each counted once). */
+int ssqcd_server_deferred(ssqcd_server srv, long long* requests);
 
 /* Number of requests queued, running and finished (not yet taken). */
 int ssqcd_server_counts(ssqcd_server srv, int* queued, int* running, int* finished);
@@ -428,6 +440,26 @@ const char* ssqcd_last_error(void);
  * CUDA events on the lattice stream.  *ms_per_call receives the mean time of
  * one application (all nrhs fields). */
 int ssqcd_time_stencil(ssqcd_lattice lat, int nrhs, int reps, double* ms_per_call);
+
+/* The FP32 stencil of the mixed precisions (ssqcd_apply_H_mixed,
+ * ssqcd_time_stencil) has four variants: 0/1 -- every rhs of a block of 32
+ * sites, warp w applying direction w with its two links loaded once for all
+ * rhs, at 4/3 blocks an SM; 2/3 -- one thread per site and pair of rhs, all
+ * eight hops, at 4/3 blocks an SM.  By default (-1) the first application
+ * for a given lattice volume, rhs count and link storage times every variant
+ * (three launches each, CUDA events on the lattice stream, skipped while the
+ * stream is being captured) and keeps the fastest for that key.
+ * ssqcd_set_stencil_variant(v) forces variant v (0..3) for later calls in
+ * this process, or returns to tuning (-1); SSQCD_ERR_ARG otherwise.  Not a
+ * part of the paper: the paper's operator (Section 4) is the same in every
+ * variant. */
+int ssqcd_set_stencil_variant(int variant);
+
+/* The tuning recorded for this lattice (created with SSQCD_MIXED or
+ * SSQCD_MIXED_F32LINKS) and nrhs: *variant the chosen variant, us[4] (may be
+ * NULL) the measured microseconds per application of each.  SSQCD_ERR_ARG
+ * if nothing was tuned for that key yet. */
+int ssqcd_stencil_tuning(ssqcd_lattice lat, int nrhs, int* variant, double* us);
 
 /* Kernel launches issued by this process so far (all entry points). */
 long long ssqcd_kernel_launches(void);

@@ -25,7 +25,7 @@ __all__ = [
     "FP64", "MIXED", "MIXED_F32LINKS", "FP64_SHIFT32", "FP64_DFSHIFT", "DF", "EXTRACT_RR", "EXTRACT_HANKEL", "PATH_LINES", "PATH_CIRCLE", "SsqcdError",
     "library_path", "lib", "Server", "time_stencil", "create_lattice", "upload_gauge", "apply_H", "apply_H_mixed",
     "contour", "shifted_cg", "moments", "moments_noalloc", "ss_solve", "ss_solve_windows", "ss_eigpairs", "small_eigh",
-    "kernel_launches", "set_kernel_timing", "Lattice", "Result", "Opts", "Stats",
+    "kernel_launches", "set_kernel_timing", "set_stencil_variant", "stencil_tuning", "Lattice", "Result", "Opts", "Stats",
 ]
 
 OK, ERR_ARG, ERR_OOM, ERR_BREAKDOWN, ERR_NOCONV, ERR_CUDA = 0, 1, 2, 3, 4, 5
@@ -94,10 +94,12 @@ def lib():
         "ssqcd_apply_H_mixed": (i, [vp, vp, vp, i, i]),
         "ssqcd_server_create": (i, [C.c_size_t, vp]),
         "ssqcd_server_submit": (i, [vp, vp, vp, i, i, i, vp, vp]),
+        "ssqcd_server_submit_windows": (i, [vp, vp, i, vp, i, i, i, vp, vp]),
         "ssqcd_server_progress": (i, [vp, i, vp]),
         "ssqcd_server_status": (i, [vp, C.c_longlong, vp, vp]),
         "ssqcd_server_take": (i, [vp, C.c_longlong, vp]),
         "ssqcd_server_counts": (i, [vp, vp, vp, vp]),
+        "ssqcd_server_deferred": (i, [vp, vp]),
         "ssqcd_server_request_bytes": (i, [vp, C.c_longlong, vp]),
         "ssqcd_server_destroy": (None, [vp]),
         "ssqcd_lattice_destroy": (None, [vp]),
@@ -115,6 +117,8 @@ def lib():
         "ssqcd_kernel_launches": (C.c_longlong, []),
         "ssqcd_time_stencil": (i, [vp, i, i, vp]),
         "ssqcd_set_kernel_timing": (i, [i]),
+        "ssqcd_set_stencil_variant": (i, [i]),
+        "ssqcd_stencil_tuning": (i, [vp, i, vp, vp]),
         "ssqcd_moments_noalloc": (i, [i, i, i, C.c_longlong, vp, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
@@ -417,6 +421,20 @@ class Server:
         self._lats[rid.value] = lat
         return rid.value
 
+    def submit_windows(self, lat: Lattice, intervals, N, M, sources, beta=0.3, nprime=0, tol=1e-12, sigma=0.0,
+                       max_iter=100000, rank_tol=1e-14, path=PATH_LINES, extract=0, hankel_tol=1e-12, refine=0,
+                       basis=1, basis_max_bytes=0.0, source_block=0):
+        iv_list = [float(x) for ab in intervals for x in ab]
+        K = len(iv_list) // 2
+        L, o, keep = _solve_opts(lat, sources, beta, nprime, tol, sigma, max_iter, rank_tol, path, 0, 1, extract,
+                                 hankel_tol, refine, basis, basis_max_bytes, source_block)
+        iv = (C.c_double * (2 * K))(*iv_list)
+        rid = C.c_longlong(0)
+        _check(lib().ssqcd_server_submit_windows(self.handle, lat.handle, K, iv, int(N), int(M), L, C.byref(o),
+                                                 C.byref(rid)))
+        self._lats[rid.value] = lat
+        return rid.value
+
     def progress(self, wait=False) -> int:
         n = C.c_int(0)
         _check(lib().ssqcd_server_progress(self.handle, 1 if wait else 0, C.byref(n)))
@@ -437,6 +455,12 @@ class Server:
         q, r, f = C.c_int(0), C.c_int(0), C.c_int(0)
         _check(lib().ssqcd_server_counts(self.handle, C.byref(q), C.byref(r), C.byref(f)))
         return q.value, r.value, f.value
+
+    def deferred(self) -> int:
+        """Requests that waited at the head of the queue for memory."""
+        n = C.c_longlong(0)
+        _check(lib().ssqcd_server_deferred(self.handle, C.byref(n)))
+        return n.value
 
     def take(self, rid) -> "Result":
         h = C.c_void_p()
@@ -474,6 +498,19 @@ def time_stencil(lat: Lattice, nrhs: int, reps: int = 20) -> float:
     ms = C.c_double(0.0)
     _check(lib().ssqcd_time_stencil(lat.handle, int(nrhs), int(reps), C.byref(ms)))
     return ms.value
+
+
+def set_stencil_variant(variant: int):
+    """Force FP32 stencil variant 0..3, or -1 to tune per lattice size and rhs count."""
+    _check(lib().ssqcd_set_stencil_variant(int(variant)))
+
+
+def stencil_tuning(lat: Lattice, nrhs: int):
+    """(chosen variant, microseconds per application of each variant) recorded for lat and nrhs."""
+    v = C.c_int(0)
+    us = (C.c_double * 4)()
+    _check(lib().ssqcd_stencil_tuning(lat.handle, int(nrhs), C.byref(v), us))
+    return v.value, list(us)
 
 
 def kernel_launches() -> int:

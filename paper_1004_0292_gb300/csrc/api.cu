@@ -1090,6 +1090,7 @@ struct ServerRequest {
   size_t est_bytes = 0;
   int state = SSQCD_REQ_QUEUED;
   int status = SSQCD_OK;
+  bool waited_on_memory = false;
   std::string error;
   std::chrono::steady_clock::time_point t_submit, t_done;
   cudaStream_t stream = nullptr;
@@ -1098,6 +1099,14 @@ struct ServerRequest {
   std::unique_ptr<CgRunBase> run;
   KrylovBasis basis;
   ssqcd_result_s* res = nullptr;
+  // source blocks (opts.source_block): the first source of the running
+  // block, the block size, every window's moments [L][MM][n] filled block by
+  // block, and the shifted-CG counters so far
+  int blk0 = 0, B = 0;
+  std::vector<DevBuf> Sk;
+  ShiftedCGOut cg_acc;
+  std::vector<int> iters;
+  float ms_mom = 0.f;
 
   ~ServerRequest() {
     run.reset();
@@ -1115,6 +1124,7 @@ struct ssqcd_server_s {
   size_t budget = 0;
   size_t running_bytes = 0;
   int running = 0;
+  long long deferred = 0;  // requests that waited at the head of the queue for memory
   long long next_id = 1;
   std::deque<long long> queue;
   std::map<long long, std::unique_ptr<ServerRequest>> reqs;
@@ -1177,9 +1187,16 @@ int request_start(ssqcd_server_s* srv, ServerRequest& r) {
     SS_CUDA(cudaMemcpyAsync(stage.p, r.src.data(), bytes, cudaMemcpyHostToDevice, r.stream));
     SS_TRY(pack_spinors(stage.as<double2>(), r.vd.as<double2>(), L, V, r.stream));
   }
+  r.iters.assign((size_t)r.P.NU * r.P.L, 0);
+  if (r.B < r.P.L) {
+    AllocStream scope(r.stream);
+    std::vector<DevBuf> sk(r.P.K);
+    r.Sk.swap(sk);
+    for (auto& b : r.Sk) SS_TRY(b.alloc(sizeof(double2) * 12 * (size_t)lat->g.V * r.P.MM * r.P.L));
+  }
   std::unique_ptr<CgRunBase> run;
-  SS_TRY(make_cg_run(lat, r.P.NU, r.P.zu.data(), r.P.L, r.vd.as<double2>(), r.P.o.sigma, r.P.o.tol, r.P.o.max_iter,
-                     lat->precision, r.P.o.reliable_every, r.basis_cap, r.stream, &run));
+  SS_TRY(make_cg_run(lat, r.P.NU, r.P.zu.data(), std::min(r.B, r.P.L), r.vd.as<double2>(), r.P.o.sigma, r.P.o.tol,
+                     r.P.o.max_iter, lat->precision, r.P.o.reliable_every, r.basis_cap, r.stream, &run));
   r.run = std::move(run);
   srv->running_bytes += r.est_bytes;
   srv->running += 1;
@@ -1188,8 +1205,92 @@ int request_start(ssqcd_server_s* srv, ServerRequest& r) {
   return SSQCD_OK;
 }
 
-int request_complete(ssqcd_server_s* srv, ServerRequest& r) {
+// A source block's run has ended: its moments of every window into r.Sk,
+// then the next block's run (returns with *more = true) or, after the last
+// block, nothing (*more = false; the caller extracts).
+int request_next_block(ServerRequest& r, bool* more) {
   ssqcd_lattice lat = r.lat;
+  const long long n = 12LL * lat->g.V;
+  const int Lb = std::min(r.B, r.P.L - r.blk0);
+  DevBuf yd;
+  ShiftedCGOut cg;
+  SS_TRY(r.run->finish(yd, r.iters.data() + (size_t)r.blk0 * r.P.NU, nullptr, &cg));
+  r.run->take_basis(&r.basis);
+  r.run.reset();
+  add_cg_stats(cg, &r.cg_acc);
+  {
+    AllocStream scope(r.stream);
+    DevBuf scratch;
+    cudaEvent_t m0 = nullptr, m1 = nullptr;
+    SS_CUDA(cudaEventCreate(&m0));
+    SS_CUDA(cudaEventCreate(&m1));
+    cudaEventRecord(m0, r.stream);
+    int st1 = SSQCD_OK;
+    for (int k = 0; k < r.P.K && st1 == SSQCD_OK; ++k) {
+      double2* dst = r.Sk[k].as<double2>() + (size_t)r.blk0 * r.P.MM * n;
+      st1 = r.basis.S > 0 ? basis_moments(r.basis, r.P.coefk[k].data(), r.P.MM, dst, scratch, r.stream)
+                          : moments_device(yd.as<double2>(), r.P.NU, r.P.MM, Lb, n, r.P.coefk[k].data(), dst, scratch,
+                                           r.stream);
+    }
+    cudaEventRecord(m1, r.stream);
+    cudaEventSynchronize(m1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, m0, m1);
+    r.ms_mom += ms;
+    cudaEventDestroy(m0);
+    cudaEventDestroy(m1);
+    SS_TRY(st1);
+    yd.release();
+    r.basis.release();
+  }
+  r.blk0 += Lb;
+  *more = r.blk0 < r.P.L;
+  if (!*more) return SSQCD_OK;
+  std::unique_ptr<CgRunBase> run;
+  SS_TRY(make_cg_run(lat, r.P.NU, r.P.zu.data(), std::min(r.B, r.P.L - r.blk0), r.vd.as<double2>() + (size_t)r.blk0 * n,
+                     r.P.o.sigma, r.P.o.tol, r.P.o.max_iter, lat->precision, r.P.o.reliable_every, r.basis_cap,
+                     r.stream, &run));
+  r.run = std::move(run);
+  for (int i = 0; i < kServerChunksAhead; ++i) SS_TRY(r.run->launch());
+  return SSQCD_OK;
+}
+
+// A request whose (last) shifted-CG run has ended: moments, extraction,
+// memory freed.  With source blocks left, starts the next block instead and
+// sets *still_running.
+int request_complete(ssqcd_server_s* srv, ServerRequest& r, bool* still_running = nullptr) {
+  ssqcd_lattice lat = r.lat;
+  if (still_running) *still_running = false;
+  if (r.B < r.P.L) {
+    bool more = false;
+    SS_TRY(request_next_block(r, &more));
+    if (more) {
+      if (still_running) *still_running = true;
+      return SSQCD_OK;
+    }
+    auto* res = new (std::nothrow) ssqcd_result_s();
+    if (!res) return fail(SSQCD_ERR_OOM, "host allocation failed");
+    r.res = res;
+    res->V = lat->g.V;
+    res->n = 12LL * lat->g.V;
+    fill_cg_stats(r.cg_acc, r.iters, &res->stats);
+    if (!r.P.hankel) r.vd.release();
+    DevBuf yd;
+    {
+      AllocStream scope(r.stream);
+      SS_TRY(extract_eigenpairs(lat, r.P, yd, r.basis, r.vd, res, r.stream, &r.Sk));
+    }
+    res->stats.ms_moments += r.ms_mom;
+    r.vd.release();
+    r.Sk.clear();
+    SS_CUDA(cudaStreamSynchronize(r.stream));
+    res->stream = lat->stream;
+    srv->running_bytes -= r.est_bytes;
+    srv->running -= 1;
+    r.state = SSQCD_REQ_DONE;
+    r.t_done = std::chrono::steady_clock::now();
+    return SSQCD_OK;
+  }
   auto* res = new (std::nothrow) ssqcd_result_s();
   if (!res) return fail(SSQCD_ERR_OOM, "host allocation failed");
   r.res = res;
@@ -1236,15 +1337,18 @@ extern "C" int ssqcd_server_create(size_t memory_budget, ssqcd_server* out) {
   return SSQCD_OK;
 }
 
-extern "C" int ssqcd_server_submit(ssqcd_server srv, ssqcd_lattice lat, const double interval[2], int N, int M,
-                                   int L, const ssqcd_opts* opts, long long* id) {
-  if (srv == nullptr || id == nullptr) return fail(SSQCD_ERR_ARG, "NULL server or id");
-  SS_TRY(check_lattice(lat, true));
-  auto r = std::make_unique<ServerRequest>();
-  SS_TRY(plan_solve(interval, N, M, L, opts, &r->P));
+namespace {
+
+int server_enqueue(ssqcd_server srv, ssqcd_lattice lat, std::unique_ptr<ServerRequest> r, int L, long long* id) {
   r->lat = lat;
-  r->basis_cap = request_basis_cap(lat, r->P, srv->budget);
-  r->est_bytes = estimate_request_bytes(lat, r->P, r->basis_cap);
+  r->B = (r->P.o.source_block > 0 && r->P.o.source_block < L) ? r->P.o.source_block : L;
+  // a source block holds the shift vectors / stored residuals of B sources
+  // and the moments of all L
+  SolvePlan Pb = r->P;
+  Pb.L = r->B;
+  r->basis_cap = request_basis_cap(lat, Pb, srv->budget);
+  r->est_bytes = estimate_request_bytes(lat, Pb, r->basis_cap);
+  if (r->B < L) r->est_bytes += sizeof(double2) * 12 * (size_t)lat->g.V * r->P.MM * L * r->P.K;
   if (r->est_bytes > srv->budget)
     return fail(SSQCD_ERR_OOM, "request needs more device memory than the server budget");
   const size_t nd = 2ull * 12 * lat->g.V * L;  // doubles
@@ -1262,6 +1366,32 @@ extern "C" int ssqcd_server_submit(ssqcd_server srv, ssqcd_lattice lat, const do
   return SSQCD_OK;
 }
 
+}  // namespace
+
+extern "C" int ssqcd_server_submit(ssqcd_server srv, ssqcd_lattice lat, const double interval[2], int N, int M,
+                                   int L, const ssqcd_opts* opts, long long* id) {
+  if (srv == nullptr || id == nullptr) return fail(SSQCD_ERR_ARG, "NULL server or id");
+  SS_TRY(check_lattice(lat, true));
+  auto r = std::make_unique<ServerRequest>();
+  SS_TRY(plan_solve(interval, N, M, L, opts, &r->P));
+  return server_enqueue(srv, lat, std::move(r), L, id);
+}
+
+extern "C" int ssqcd_server_submit_windows(ssqcd_server srv, ssqcd_lattice lat, int K, const double* intervals, int N,
+                                           int M, int L, const ssqcd_opts* opts, long long* id) {
+  if (srv == nullptr || id == nullptr) return fail(SSQCD_ERR_ARG, "NULL server or id");
+  SS_TRY(check_lattice(lat, true));
+  if (opts != nullptr && opts->windows > 1)
+    return fail(SSQCD_ERR_ARG, "ssqcd_server_submit_windows: opts.windows must be 0 or 1");
+  if (K < 1 || intervals == nullptr) return fail(SSQCD_ERR_ARG, "ssqcd_server_submit_windows: need K >= 1 intervals");
+  for (int k = 0; k < K; ++k)
+    if (!(intervals[2 * k + 1] > intervals[2 * k]))
+      return fail(SSQCD_ERR_ARG, "ssqcd_server_submit_windows: every interval needs b > a");
+  auto r = std::make_unique<ServerRequest>();
+  SS_TRY(plan_windows(K, intervals, N, M, L, opts, &r->P));
+  return server_enqueue(srv, lat, std::move(r), L, id);
+}
+
 extern "C" int ssqcd_server_progress(ssqcd_server srv, int wait, int* completed) {
   if (srv == nullptr) return fail(SSQCD_ERR_ARG, "NULL server");
   int done = 0;
@@ -1273,7 +1403,13 @@ extern "C" int ssqcd_server_progress(ssqcd_server srv, int wait, int* completed)
       continue;
     }
     ServerRequest& r = *it->second;
-    if (srv->running > 0 && srv->running_bytes + r.est_bytes > srv->budget) break;
+    if (srv->running > 0 && srv->running_bytes + r.est_bytes > srv->budget) {
+      if (!r.waited_on_memory) {
+        r.waited_on_memory = true;
+        ++srv->deferred;
+      }
+      break;
+    }
     srv->queue.pop_front();
     const int s1 = request_start(srv, r);
     if (s1 != SSQCD_OK) {
@@ -1303,8 +1439,14 @@ extern "C" int ssqcd_server_progress(ssqcd_server srv, int wait, int* completed)
       }
       moved = true;
       if (state == CgRunBase::kPollDone) {
-        s1 = request_complete(srv, r);
-        if (s1 != SSQCD_OK) request_fail(srv, r, s1);
+        bool again = false;
+        s1 = request_complete(srv, r, &again);
+        if (s1 != SSQCD_OK) {
+          request_fail(srv, r, s1);
+          ++done;
+          break;
+        }
+        if (again) continue;  // the next source block is running
         ++done;
         break;
       }
@@ -1327,9 +1469,14 @@ extern "C" int ssqcd_server_progress(ssqcd_server srv, int wait, int* completed)
       request_fail(srv, r, s1);
       ++done;
     } else if (state == CgRunBase::kPollDone) {
-      s1 = request_complete(srv, r);
-      if (s1 != SSQCD_OK) request_fail(srv, r, s1);
-      ++done;
+      bool again = false;
+      s1 = request_complete(srv, r, &again);
+      if (s1 != SSQCD_OK) {
+        request_fail(srv, r, s1);
+        ++done;
+      } else if (!again) {
+        ++done;
+      }
     } else {
       while (r.run->in_flight() < kServerChunksAhead)
         if ((s1 = r.run->launch()) != SSQCD_OK) {
@@ -1340,6 +1487,12 @@ extern "C" int ssqcd_server_progress(ssqcd_server srv, int wait, int* completed)
     }
   }
   if (completed) *completed = done;
+  return SSQCD_OK;
+}
+
+extern "C" int ssqcd_server_deferred(ssqcd_server srv, long long* requests) {
+  if (srv == nullptr || requests == nullptr) return fail(SSQCD_ERR_ARG, "NULL server or output");
+  *requests = srv->deferred;
   return SSQCD_OK;
 }
 
@@ -1400,6 +1553,19 @@ extern "C" int ssqcd_server_counts(ssqcd_server srv, int* queued, int* running, 
 extern "C" void ssqcd_server_destroy(ssqcd_server srv) {
   if (!srv) return;
   delete srv;  // requests finish their device work and free their memory
+}
+
+extern "C" int ssqcd_set_stencil_variant(int variant) { return set_fp32_stencil_variant(variant); }
+
+extern "C" int ssqcd_stencil_tuning(ssqcd_lattice lat, int nrhs, int* variant, double* us) {
+  SS_TRY(check_lattice(lat, false));
+  if (!is_mixed(lat->precision)) return fail(SSQCD_ERR_ARG, "ssqcd_stencil_tuning: the lattice has no FP32 stencil");
+  if (variant == nullptr || nrhs < 1) return fail(SSQCD_ERR_ARG, "ssqcd_stencil_tuning: bad arguments");
+  float t[4];
+  SS_TRY(fp32_stencil_tuning(lat->g.V, nrhs, lat->precision == SSQCD_MIXED ? 16 : 32, variant, t));
+  if (us != nullptr)
+    for (int v = 0; v < 4; ++v) us[v] = t[v];
+  return SSQCD_OK;
 }
 
 extern "C" int ssqcd_time_stencil(ssqcd_lattice lat, int nrhs, int reps, double* ms_per_call) {

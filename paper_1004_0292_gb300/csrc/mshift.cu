@@ -1573,26 +1573,27 @@ basis_combine_kernel(char* const* __restrict__ tab, long long n, int L, const do
 // sees the per-tile conversions.  The complex float-float multiply-adds run
 // on register pairs (real and imaginary part in one paired instruction,
 // floatfloat.cuh p_cfma), in the operation order of ff::cfma.
+template <int OUT>
 __global__ void __launch_bounds__(kCombThreads, 2)
 basis_combine_df_kernel(char* const* __restrict__ tab, long long n, int L, const double2* __restrict__ C, int O, int S,
                         const int* __restrict__ count, double2* __restrict__ out, int l0) {
   // coefficients as the four register pairs of ff::p_cfma (real part in lane
   // 0, imaginary part in lane 1: one paired instruction for both)
-  __shared__ ff::PCoef s_w[kCombTile][kCombOut];
+  __shared__ ff::PCoef s_w[kCombTile][OUT];
   __shared__ const float4* s_p[kCombTile];
-  const int l = blockIdx.y + l0, o0 = blockIdx.z * kCombOut;
-  const int no = min(kCombOut, O - o0);
+  const int l = blockIdx.y + l0, o0 = blockIdx.z * OUT;
+  const int no = min(OUT, O - o0);
   const int Sl = count[l];
   const long long e = blockIdx.x * (long long)kCombThreads + threadIdx.x;
   const long long Ln = (long long)L * n;
-  double2 accd[kCombOut];
+  double2 accd[OUT];
 #pragma unroll
-  for (int o = 0; o < kCombOut; ++o) accd[o] = make_double2(0.0, 0.0);
+  for (int o = 0; o < OUT; ++o) accd[o] = make_double2(0.0, 0.0);
   for (int s0 = 0; s0 < Sl; s0 += kCombTile) {
     const int ns = min(kCombTile, Sl - s0);
     __syncthreads();
-    for (int t = threadIdx.x; t < kCombTile * kCombOut; t += kCombThreads) {
-      const int ss = t / kCombOut, oo = t % kCombOut;
+    for (int t = threadIdx.x; t < kCombTile * OUT; t += kCombThreads) {
+      const int ss = t / OUT, oo = t % OUT;
       const double2 c = (ss < ns && oo < no) ? C[((size_t)l * O + o0 + oo) * S + s0 + ss] : make_double2(0.0, 0.0);
       s_w[ss][oo] = ff::p_coef(ff::from_double2(c));
     }
@@ -1604,17 +1605,17 @@ basis_combine_df_kernel(char* const* __restrict__ tab, long long n, int L, const
     }
     __syncthreads();
     if (e < n) {
-      f32x2_t ah[kCombOut], al[kCombOut];
+      f32x2_t ah[OUT], al[OUT];
 #pragma unroll
-      for (int o = 0; o < kCombOut; ++o) ah[o] = al[o] = 0ull;
+      for (int o = 0; o < OUT; ++o) ah[o] = al[o] = 0ull;
 #pragma unroll 2
       for (int ss = 0; ss < ns; ++ss) {
         const ff::PVal x = ff::p_val(s_p[ss][e]);
 #pragma unroll
-        for (int o = 0; o < kCombOut; ++o) ff::p_cfma(ah[o], al[o], s_w[ss][o], x);
+        for (int o = 0; o < OUT; ++o) ff::p_cfma(ah[o], al[o], s_w[ss][o], x);
       }
 #pragma unroll
-      for (int o = 0; o < kCombOut; ++o) {
+      for (int o = 0; o < OUT; ++o) {
         const double2 t = ff::to_double2(ff::make2(ah[o], al[o]));
         accd[o].x += t.x;
         accd[o].y += t.y;
@@ -1700,16 +1701,24 @@ bool balanced_stencil() {
   return v;
 }
 
-// Blocks per source of kernel P (it strides): two blocks an SM over all
+// Resident blocks an SM the seed kernels B and P aim at (256 threads each,
+// striding over their source): 2 for lattices whose vectors sit in L2 (8^4
+// x 4: the last block's reduction, not bandwidth, sets their time), 8 when
+// the L vectors hold more than 2^21 elements and the kernels stream from
+// HBM (more loads in flight).
+long long seed_blocks_per_sm(long long n, int L) { return n * L > (1LL << 21) ? 8 : 2; }
+
+// Blocks per source of kernel P (it strides): seed_blocks_per_sm over all
 // sources by default (8^4 x 4: 50.3 against 50.6 us an iteration with one
-// element per thread); SSQCD_P_BLOCKS sets the cap for tuning runs.
+// element per thread and two blocks an SM); SSQCD_P_BLOCKS sets the cap for
+// tuning runs.
 unsigned p_blocks(long long n, int L) {
   static const long long env = [] {
     const char* e = std::getenv("SSQCD_P_BLOCKS");
     const long long v = e ? std::atoll(e) : 0;
     return v > 0 ? v : 0LL;
   }();
-  const long long cap = env > 0 ? env : (152LL * 2 + L - 1) / L;
+  const long long cap = env > 0 ? env : (152LL * seed_blocks_per_sm(n, L) + L - 1) / L;
   long long b = (n + kUpdBlock - 1) / kUpdBlock;
   if (b > cap) b = cap;
   return (unsigned)(b < 1 ? 1 : b);
@@ -1722,7 +1731,7 @@ int seed_blocks(long long n, int L) {
     return (v >= 1 && v <= 64) ? v : 2;  // measured (8^4 x 4, stored-residual loop): 2 -> 51.9, 4 -> 53.3 us an iteration
   }();
   long long b = (n + (long long)ept * kSeedBlock - 1) / ((long long)ept * kSeedBlock);
-  const long long cap = (152LL * 2 + L - 1) / L;
+  const long long cap = (152LL * seed_blocks_per_sm(n, L) + L - 1) / L;
   if (b > cap) b = cap;
   return (int)(b < 1 ? 1 : b);
 }
@@ -2609,9 +2618,21 @@ int basis_moments(const KrylovBasis& b, const double2* coef_host, int M, double2
   count_launches(1);
   auto one = [&](int l0, int nl, cudaStream_t s) -> int {
     if (b.df) {
-      const dim3 grid((unsigned)((b.n + kCombThreads - 1) / kCombThreads), nl, (M + kCombOut - 1) / kCombOut);
-      basis_combine_df_kernel<<<grid, kCombThreads, 0, s>>>(b.tab.as<char*>(), b.n, L, G, M, S, b.count.as<int>(),
-                                                            s_hat, l0);
+      // outputs a thread accumulates: 8 (default) or 4 (SSQCD_COMB_DF_OUT=4:
+      // fewer registers, more resident warps, the residuals read twice as often)
+      static const int out_df = [] {
+        const char* e = std::getenv("SSQCD_COMB_DF_OUT");
+        return (e != nullptr && std::atoi(e) == 4) ? 4 : 8;
+      }();
+      if (out_df == 4) {
+        const dim3 grid((unsigned)((b.n + kCombThreads - 1) / kCombThreads), nl, (M + 3) / 4);
+        basis_combine_df_kernel<4><<<grid, kCombThreads, 0, s>>>(b.tab.as<char*>(), b.n, L, G, M, S,
+                                                                 b.count.as<int>(), s_hat, l0);
+      } else {
+        const dim3 grid((unsigned)((b.n + kCombThreads - 1) / kCombThreads), nl, (M + 7) / 8);
+        basis_combine_df_kernel<8><<<grid, kCombThreads, 0, s>>>(b.tab.as<char*>(), b.n, L, G, M, S,
+                                                                 b.count.as<int>(), s_hat, l0);
+      }
       SS_CHECK_LAUNCH();
       count_launches(1);
       return SSQCD_OK;

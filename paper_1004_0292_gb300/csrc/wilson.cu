@@ -10,7 +10,11 @@
 // 192 B (out) + 576 B (links, shared by the rhs) of compulsory traffic.
 // FP32 spinors with FP16 (or FP32) 12-parameter links: HBM-bound; 96 B in,
 // 96 B out, 96 (192) B links per site.
+#include <atomic>
 #include <cstdlib>
+#include <map>
+#include <mutex>
+#include <tuple>
 
 #include "wilson_core.cuh"
 #include "wilson_df.cuh"
@@ -20,15 +24,8 @@ namespace {
 
 using namespace wcore;
 
-// blocks an SM of the all-rhs FP32 stencil (register cap 65536 / (128 x
-// MinB)): 4 (128 registers) by default, 3 (170) with SSQCD_MRHS_MINB=3
-int mrhs_min_blocks() {
-  static const int v = [] {
-    const char* e = std::getenv("SSQCD_MRHS_MINB");
-    return (e != nullptr && std::atoi(e) == 3) ? 3 : 4;
-  }();
-  return v;
-}
+// ---- the FP32 stencil variants and their autotuner ----------------------------------
+// (see fp32_variant below)
 
 template <int BLOCK>
 __device__ __forceinline__ double block_sum(double v, double* sh) {
@@ -123,13 +120,46 @@ template <typename LK, int MinB>
 __global__ void __launch_bounds__(128, MinB)
 wilson32m_kernel(Geometry g, LK lk, const float2* __restrict__ in_all, float2* __restrict__ out_all, int nrhs,
                  float c0, float c1, float* __restrict__ dot_partial) {
-  __shared__ float2 sh[12 * 4 * 32];
-  __shared__ float shred[4];
+  __shared__ float2 sh[2 * 12 * 4 * 32];
+  __shared__ float shred[2 * 4];
   switch (threadIdx.x >> 5) {
     case 0: mrhs_block<0>(g, lk, in_all, out_all, nrhs, c0, c1, sh, shred, dot_partial); break;
     case 1: mrhs_block<1>(g, lk, in_all, out_all, nrhs, c0, c1, sh, shred, dot_partial); break;
     case 2: mrhs_block<2>(g, lk, in_all, out_all, nrhs, c0, c1, sh, shred, dot_partial); break;
     default: mrhs_block<3>(g, lk, in_all, out_all, nrhs, c0, c1, sh, shred, dot_partial); break;
+  }
+}
+
+// FP32 spinors, one thread per site and pair of rhs (see site_hops_pair);
+// blockIdx.y = rhs pair; an odd last rhs is computed twice, stored once.
+template <typename LK, int MinB>
+__global__ void __launch_bounds__(128, MinB)
+wilson32p_kernel(Geometry g, LK lk, const float2* __restrict__ in_all, float2* __restrict__ out_all, int nrhs,
+                 float c0, float c1) {
+  const int s = blockIdx.x * 128 + threadIdx.x;
+  const int V = g.V;
+  if (s >= V) return;
+  const int r0 = 2 * blockIdx.y, r1 = min(r0 + 1, nrhs - 1);
+  const float2* in0 = in_all + (size_t)r0 * 12 * V;
+  const float2* in1 = in_all + (size_t)r1 * 12 * V;
+  f32x2_t acc0[12], acc1[12];
+  site_hops_pair(lk, in0, in1, s, g, acc0, acc1);
+  const float mk = -(float)g.kappa;
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    if (q == 1 && r1 == r0) break;
+    const float2* in = q ? in1 : in0;
+    float2* out = out_all + (size_t)(q ? r1 : r0) * 12 * V;
+#pragma unroll
+    for (int i = 0; i < 12; ++i) {
+      const float sg = i < 6 ? c1 : -c1;
+      const float2 p = __ldg(in + i * V + s);
+      const float2 d = upk2(q ? acc1[i] : acc0[i]);
+      float2 o;
+      o.x = fmaf(sg, fmaf(mk, d.x, p.x), c0 * p.x);
+      o.y = fmaf(sg, fmaf(mk, d.y, p.y), c0 * p.y);
+      out[i * V + s] = o;
+    }
   }
 }
 
@@ -210,27 +240,127 @@ int wilson64(const Geometry& g, const double2* u, const double2* in, double2* ou
   return SSQCD_OK;
 }
 
+namespace {
+using namespace wcore;
+
+// Four variants of the FP32 stencil with 12-parameter links (kernels below):
+//   0: all rhs of 32 sites a block (wilson32m), 4 blocks an SM (128 registers)
+//   1: the same at 3 blocks an SM (170 registers)
+//   2: one thread per site and rhs pair (wilson32p), 4 blocks an SM
+//   3: the same at 3 blocks an SM
+// Which is fastest depends on the lattice volume, the number of rhs and the
+// link storage, so the first application for a (V, nrhs, link bits) key
+// times each variant (three launches each, CUDA events on the caller's
+// stream) and records the fastest; later applications with that key use it.
+// Variants 2-3 give no (in, out) partials, so callers that want them tune
+// among 0-1 only.  ssqcd_set_stencil_variant forces one variant
+// (tests, measurements), ssqcd_stencil_tuning reports the choice of a key.
+constexpr int kFp32Variants = 4;
+
+struct TuneEntry {
+  int variant;
+  float us[kFp32Variants];
+};
+std::mutex g_tune_mutex;
+std::map<std::tuple<int, int, int, int>, TuneEntry> g_tune;
+std::atomic<int> g_variant_override{-1};
+
+template <typename LK>
+void launch_fp32_variant(int v, const Geometry& g, const LK& lk, const float2* in, float2* out, int nrhs, float c0,
+                         float c1, float* dot_partial, cudaStream_t s) {
+  if (v <= 1) {
+    const int nb = (g.V + 31) / 32;
+    if (v == 0)
+      wilson32m_kernel<LK, 4><<<nb, 128, 0, s>>>(g, lk, in, out, nrhs, c0, c1, dot_partial);
+    else
+      wilson32m_kernel<LK, 3><<<nb, 128, 0, s>>>(g, lk, in, out, nrhs, c0, c1, dot_partial);
+  } else {
+    const dim3 grid((g.V + 127) / 128, (nrhs + 1) / 2);
+    if (v == 2)
+      wilson32p_kernel<LK, 4><<<grid, 128, 0, s>>>(g, lk, in, out, nrhs, c0, c1);
+    else
+      wilson32p_kernel<LK, 3><<<grid, 128, 0, s>>>(g, lk, in, out, nrhs, c0, c1);
+  }
+}
+
+// the variant for this key: forced, recorded, or tuned now (when the
+// stream is not being captured; a capturing caller gets variant 0 untimed)
+template <typename LK>
+int fp32_variant(const Geometry& g, const LK& lk, int bits, const float2* in, float2* out, int nrhs, float c0,
+                 float c1, float* dot_partial, cudaStream_t s) {
+  const int forced = g_variant_override.load();
+  if (forced >= 0) return (dot_partial != nullptr && forced >= 2) ? 0 : forced;
+  const auto key = std::make_tuple(g.V, nrhs, bits, dot_partial != nullptr ? 1 : 0);
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) return it->second.variant;
+  }
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return 0;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return 0;
+  }
+  TuneEntry t{0, {0.f, 0.f, 0.f, 0.f}};
+  const int nv = dot_partial != nullptr ? 2 : kFp32Variants;
+  float best = 0.f;
+  for (int v = 0; v < nv; ++v) {
+    launch_fp32_variant(v, g, lk, in, out, nrhs, c0, c1, dot_partial, s);  // warm-up
+    cudaEventRecord(e0, s);
+    for (int k = 0; k < 3; ++k) launch_fp32_variant(v, g, lk, in, out, nrhs, c0, c1, dot_partial, s);
+    cudaEventRecord(e1, s);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    t.us[v] = 1e3f * ms / 3.f;
+    if (v == 0 || t.us[v] < best) {
+      best = t.us[v];
+      t.variant = v;
+    }
+  }
+  count_launches(4LL * nv);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (cudaGetLastError() != cudaSuccess) return 0;
+  std::lock_guard<std::mutex> lock(g_tune_mutex);
+  g_tune[key] = t;
+  return t.variant;
+}
+
+}  // namespace
+
 int wilson32_blocks(const Geometry& g) { return (g.V + 31) / 32; }
+
+int set_fp32_stencil_variant(int v) {
+  if (v < -1 || v >= kFp32Variants) return fail(SSQCD_ERR_ARG, "stencil variant must be -1 (tuned) or 0..3");
+  g_variant_override.store(v);
+  return SSQCD_OK;
+}
+
+int fp32_stencil_tuning(int V, int nrhs, int link_bits, int* variant, float* us) {
+  std::lock_guard<std::mutex> lock(g_tune_mutex);
+  auto it = g_tune.find(std::make_tuple(V, nrhs, link_bits, 0));
+  if (it == g_tune.end()) return fail(SSQCD_ERR_ARG, "no tuning recorded for this lattice size, rhs count and links");
+  *variant = it->second.variant;
+  for (int v = 0; v < kFp32Variants; ++v) us[v] = it->second.us[v];
+  return SSQCD_OK;
+}
 
 int wilson32(const Geometry& g, const void* links, int link_bits, const float2* in, float2* out, int nrhs, float c0,
              float c1, float* dot_partial, const int* skip_if_zero, cudaStream_t s) {
   if (nrhs <= 0) return SSQCD_OK;
   if (skip_if_zero == nullptr) {
-    // all rhs of a block of sites: links loaded once for every rhs
-    const int nb = wilson32_blocks(g);
+    // the tuned all-rhs variants: links loaded once for several rhs
     const LinksF16 l16{static_cast<const uint2*>(links), g.V};
     const LinksF32 l32{static_cast<const float4*>(links), g.V};
-    if (mrhs_min_blocks() == 3) {
-      if (link_bits == 16)
-        wilson32m_kernel<LinksF16, 3><<<nb, 128, 0, s>>>(g, l16, in, out, nrhs, c0, c1, dot_partial);
-      else
-        wilson32m_kernel<LinksF32, 3><<<nb, 128, 0, s>>>(g, l32, in, out, nrhs, c0, c1, dot_partial);
-    } else {
-      if (link_bits == 16)
-        wilson32m_kernel<LinksF16, 4><<<nb, 128, 0, s>>>(g, l16, in, out, nrhs, c0, c1, dot_partial);
-      else
-        wilson32m_kernel<LinksF32, 4><<<nb, 128, 0, s>>>(g, l32, in, out, nrhs, c0, c1, dot_partial);
-    }
+    if (link_bits == 16)
+      launch_fp32_variant(fp32_variant(g, l16, 16, in, out, nrhs, c0, c1, dot_partial, s), g, l16, in, out, nrhs, c0,
+                          c1, dot_partial, s);
+    else
+      launch_fp32_variant(fp32_variant(g, l32, 32, in, out, nrhs, c0, c1, dot_partial, s), g, l32, in, out, nrhs, c0,
+                          c1, dot_partial, s);
     count_launches(1);
     SS_CHECK_LAUNCH();
     return SSQCD_OK;

@@ -698,11 +698,15 @@ __device__ __forceinline__ void hop_mrhs(const PackedLink& P, const float2* __re
 // out_r = c0 in_r + c1 A in_r for the rhs r = 0..nrhs-1 of 32 sites
 // (block of 128 threads, warp w = direction MU = w); dot_partial (optional):
 // per rhs the block's share of Re <in_r, out_r> at dot_partial[r * gridDim.x
-// + blockIdx.x].  sh: 12 x 4 x 32 float2.
+// + blockIdx.x].  sh: 2 x 12 x 4 x 32 float2 and shred: 2 x 4 floats, double
+// buffered by rhs parity, so one barrier per rhs separates the four
+// directions' partial sums from their combination (a buffer is rewritten two
+// rhs later, after the next barrier, by which every warp has finished
+// reading it).
 template <int MU, typename LK>
 __device__ __forceinline__ void mrhs_block(const Geometry& g, const LK& lk, const float2* __restrict__ in_all,
                                            float2* __restrict__ out_all, int nrhs, float c0, float c1,
-                                           float2* sh, float* shred, float* __restrict__ dot_partial) {
+                                           float2* sh2, float* shred2, float* __restrict__ dot_partial) {
   const int lane = threadIdx.x & 31;
   const int s = blockIdx.x * 32 + lane;
   const int V = g.V;
@@ -721,6 +725,8 @@ __device__ __forceinline__ void mrhs_block(const Geometry& g, const LK& lk, cons
   const float mk = -(float)g.kappa;
   const float sg = MU < 2 ? c1 : -c1;  // gamma5 on spin MU of components 3 MU .. 3 MU + 2
   for (int r = 0; r < nrhs; ++r) {
+    float2* sh = sh2 + (r & 1) * (12 * 4 * 32);
+    float* shred = shred2 + (r & 1) * 4;
     const float2* in = in_all + (size_t)r * 12 * V;
     f32x2_t acc[12];
     if (act) {
@@ -733,17 +739,19 @@ __device__ __forceinline__ void mrhs_block(const Geometry& g, const LK& lk, cons
 #pragma unroll
     for (int i = 0; i < 12; ++i) sh[(i * 4 + MU) * 32 + lane] = upk2(acc[i]);
     __syncthreads();
+    if (dot_partial != nullptr && r > 0 && threadIdx.x == 0) {
+      const float* pr = shred2 + ((r - 1) & 1) * 4;
+      dot_partial[(size_t)(r - 1) * gridDim.x + blockIdx.x] = (pr[0] + pr[1]) + (pr[2] + pr[3]);
+    }
     float dot = 0.f;
     if (act) {
       float2* out = out_all + (size_t)r * 12 * V;
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
         const int i = 3 * MU + k;
-        const f32x2_t d = add2(add2(pk2(sh[(i * 4 + 0) * 32 + lane].x, sh[(i * 4 + 0) * 32 + lane].y),
-                                    pk2(sh[(i * 4 + 1) * 32 + lane].x, sh[(i * 4 + 1) * 32 + lane].y)),
-                               add2(pk2(sh[(i * 4 + 2) * 32 + lane].x, sh[(i * 4 + 2) * 32 + lane].y),
-                                    pk2(sh[(i * 4 + 3) * 32 + lane].x, sh[(i * 4 + 3) * 32 + lane].y)));
-        const float2 dv = upk2(d);
+        const float2 e0 = sh[(i * 4 + 0) * 32 + lane], e1 = sh[(i * 4 + 1) * 32 + lane];
+        const float2 e2 = sh[(i * 4 + 2) * 32 + lane], e3 = sh[(i * 4 + 3) * 32 + lane];
+        const float2 dv = upk2(add2(add2(pk2(e0.x, e0.y), pk2(e1.x, e1.y)), add2(pk2(e2.x, e2.y), pk2(e3.x, e3.y))));
         const float2 p = __ldg(in + i * V + s);
         float2 o;
         o.x = fmaf(sg, fmaf(mk, dv.x, p.x), c0 * p.x);
@@ -757,10 +765,52 @@ __device__ __forceinline__ void mrhs_block(const Geometry& g, const LK& lk, cons
       for (int o = 16; o > 0; o >>= 1) dot += __shfl_down_sync(0xffffffffu, dot, o);
       if (lane == 0) shred[MU] = dot;
     }
-    __syncthreads();
-    if (dot_partial != nullptr && threadIdx.x == 0)
-      dot_partial[(size_t)r * gridDim.x + blockIdx.x] = (shred[0] + shred[1]) + (shred[2] + shred[3]);
   }
+  if (dot_partial != nullptr) {
+    __syncthreads();
+    if (threadIdx.x == 0 && nrhs > 0) {
+      const float* pr = shred2 + ((nrhs - 1) & 1) * 4;
+      dot_partial[(size_t)(nrhs - 1) * gridDim.x + blockIdx.x] = (pr[0] + pr[1]) + (pr[2] + pr[3]);
+    }
+  }
+}
+
+// ---- FP32, one thread per site and rhs pair ------------------------------------------
+// Without the block's cross-warp sum: a thread applies all eight hops of its
+// site to two rhs at once, so every link is loaded and rebuilt once for two
+// rhs, the neighbour indices once for both, and there is no barrier.  The
+// 2 x 12 accumulators and the hop's packed link stay in registers.
+template <int MU, int DIR, typename LK>
+__device__ __forceinline__ void hop_pair(const LK& lk, const float2* __restrict__ in0,
+                                         const float2* __restrict__ in1, int s, const Coords& c, const Geometry& g,
+                                         bool first, f32x2_t (&acc0)[12], f32x2_t (&acc1)[12]) {
+  bool w;
+  const int nb = neighbour<MU, DIR>(s, c, g, w);
+  PackedLink P;
+  load_packed(lk, MU, DIR > 0 ? s : nb, DIR < 0, P);
+  const bool neg = MU == 3 && w && g.bc_t < 0;
+  if (first) {
+    hop_mrhs<MU, DIR, true>(P, in0, nb, g.V, neg, acc0);
+    hop_mrhs<MU, DIR, true>(P, in1, nb, g.V, neg, acc1);
+  } else {
+    hop_mrhs<MU, DIR, false>(P, in0, nb, g.V, neg, acc0);
+    hop_mrhs<MU, DIR, false>(P, in1, nb, g.V, neg, acc1);
+  }
+}
+
+template <typename LK>
+__device__ __forceinline__ void site_hops_pair(const LK& lk, const float2* __restrict__ in0,
+                                               const float2* __restrict__ in1, int s, const Geometry& g,
+                                               f32x2_t (&acc0)[12], f32x2_t (&acc1)[12]) {
+  const Coords c = site_coords(s, g);
+  hop_pair<0, +1>(lk, in0, in1, s, c, g, true, acc0, acc1);
+  hop_pair<0, -1>(lk, in0, in1, s, c, g, false, acc0, acc1);
+  hop_pair<1, +1>(lk, in0, in1, s, c, g, false, acc0, acc1);
+  hop_pair<1, -1>(lk, in0, in1, s, c, g, false, acc0, acc1);
+  hop_pair<2, +1>(lk, in0, in1, s, c, g, false, acc0, acc1);
+  hop_pair<2, -1>(lk, in0, in1, s, c, g, false, acc0, acc1);
+  hop_pair<3, +1>(lk, in0, in1, s, c, g, false, acc0, acc1);
+  hop_pair<3, -1>(lk, in0, in1, s, c, g, false, acc0, acc1);
 }
 
 }  // namespace wcore

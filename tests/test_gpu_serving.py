@@ -93,6 +93,10 @@ def test_admission_keeps_running_requests_within_the_budget(setup):
     seen = _drain(ss, srv, ids, budget=budget, est=dict(zip(ids, est)))
     big = ids[int(np.argmax(est))]
     assert all(r == [big] for r in seen if big in r)  # the largest always ran alone
+    # admission deferred requests on memory (the first one runs at once, the
+    # others queue while it holds the budget), and their results below are
+    # still bit-identical to the solo runs
+    assert srv.deferred() >= 1
     for i, (ev0, rs0, _) in zip(ids, alone):
         res = srv.take(i)
         ev, _, rs, _ = ss.ss_eigpairs(res, want_vectors=False)
@@ -108,4 +112,32 @@ def test_request_above_the_budget_is_refused(setup):
         srv.submit(lat, iv, N, M, src, **kw)
     assert e.value.code == ss.ERR_OOM
     assert srv.counts() == (0, 0, 0)
+    srv.close()
+
+
+def test_window_list_request_with_source_blocks(setup):
+    """A request for two windows (one on each side of the gap) whose sources
+    run in blocks of one: the scheduler chains the blocks' shifted-CG runs
+    and forms the moments block by block; the result is bit-identical to
+    ssqcd_ss_solve_windows with the same blocks, alone and next to other
+    requests."""
+    ss, reqs, alone = setup
+    lat4 = reqs[0][0]
+    src = synthetic.gaussian_sources((4, 4, 4, 4), 3, seed=103)
+    wins = [(-0.3932, -0.3785), (0.374, 0.3930)]
+    res = ss.ss_solve_windows(lat4, wins, 16, 8, src, beta=0.3, nprime=14, source_block=1)
+    assert res.status == ss.OK, res.error
+    ev0, _, rs0, st0 = ss.ss_eigpairs(res, want_vectors=False)
+    assert len(ev0) == 16 and np.max(rs0) <= 1e-8
+    srv = ss.Server()
+    rid = srv.submit_windows(lat4, wins, 16, 8, src, beta=0.3, nprime=14, source_block=1)
+    others = [srv.submit(lat, iv, N, M, s, **kw) for lat, iv, N, M, s, kw in reqs[:2]]
+    _drain(ss, srv, [rid] + others)
+    out = srv.take(rid)
+    assert out.status == ss.OK, out.error
+    ev, _, rs, st = ss.ss_eigpairs(out, want_vectors=False)
+    assert np.array_equal(ev, ev0) and np.array_equal(rs, rs0)
+    assert st["iterations"] == st0["iterations"]
+    for i in others:
+        assert srv.take(i).status == ss.OK
     srv.close()

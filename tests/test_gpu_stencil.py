@@ -105,7 +105,20 @@ def test_mixed_stencil_all_rhs_kernel(ss, dims, nrhs, bc):
     psi = synthetic.gaussian_sources(dims, nrhs, seed=6)
     lat = ss.create_lattice(dims, kappa, bc, precision=ss.MIXED)
     ss.upload_gauge(lat, U)
-    got = ss.apply_H_mixed(lat, psi)
     ref16 = wilson.apply_H(fp16_rounded_links(U), psi, kappa, dims, bc)
-    for r in range(nrhs):
-        assert np.max(np.abs(got[r] - ref16[r])) <= 2e-6 * np.max(np.abs(ref16[r]))
+    try:
+        for variant in (0, 1, 2, 3):
+            ss.set_stencil_variant(variant)
+            got = ss.apply_H_mixed(lat, psi)
+            for r in range(nrhs):
+                assert np.max(np.abs(got[r] - ref16[r])) <= 2e-6 * np.max(np.abs(ref16[r])), (variant, r)
+    finally:
+        ss.set_stencil_variant(-1)
+    # the autotuner: the first tuned application times every variant and
+    # keeps the fastest; the result is the same operator
+    got = ss.apply_H_mixed(lat, psi)
+    chosen, us = ss.stencil_tuning(lat, nrhs)
+    assert chosen in (0, 1, 2, 3) and all(t > 0 for t in us) and us[chosen] == min(us)
+    assert np.max(np.abs(got - ref16)) <= 2e-6 * np.max(np.abs(ref16))
+    with pytest.raises(ss.SsqcdError):
+        ss.set_stencil_variant(7)
