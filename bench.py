@@ -535,7 +535,9 @@ def run_stencil_large(ss, stream, peaks):
             v, us = ss.stencil_tuning(lat, c["rhs"])
             out[name]["variant"] = {"chosen": v, "us_per_variant": us,
                                     "variants": ["all rhs of 32 sites a block, 4 blocks/SM", "same, 3 blocks/SM",
-                                                 "thread per site and rhs pair, 4 blocks/SM", "same, 3 blocks/SM"]}
+                                                 "thread per site and rhs pair, 4 blocks/SM", "same, 3 blocks/SM",
+                                                 "thread per site and rhs pair, the two rhs in the paired lanes, "
+                                                 "4 blocks/SM", "same, 3 blocks/SM"]}
         del lat
     return out
 

@@ -442,22 +442,26 @@ const char* ssqcd_last_error(void);
 int ssqcd_time_stencil(ssqcd_lattice lat, int nrhs, int reps, double* ms_per_call);
 
 /* The FP32 stencil of the mixed precisions (ssqcd_apply_H_mixed,
- * ssqcd_time_stencil) has four variants: 0/1 -- every rhs of a block of 32
+ * ssqcd_time_stencil) has six variants: 0/1 -- every rhs of a block of 32
  * sites, warp w applying direction w with its two links loaded once for all
  * rhs, at 4/3 blocks an SM; 2/3 -- one thread per site and pair of rhs, all
- * eight hops, at 4/3 blocks an SM.  By default (-1) the first application
- * for a given lattice volume, rhs count and link storage times every variant
- * (three launches each, CUDA events on the lattice stream, skipped while the
- * stream is being captured) and keeps the fastest for that key.
- * ssqcd_set_stencil_variant(v) forces variant v (0..3) for later calls in
- * this process, or returns to tuning (-1); SSQCD_ERR_ARG otherwise.  Not a
- * part of the paper: the paper's operator (Section 4) is the same in every
- * variant. */
+ * eight hops, at 4/3 blocks an SM; 4/5 -- the same with the two rhs in the
+ * two lanes of the paired FP32 instructions (rhs-pair layout, converted
+ * around the kernel; even nrhs only), at 4/3 blocks an SM.  By default (-1)
+ * the first application for a given lattice volume, rhs count and link
+ * storage times every variant (three launches each, CUDA events on the
+ * lattice stream, skipped while the stream is being captured) and keeps the
+ * fastest for that key; ssqcd_time_stencil times the chosen kernel alone.
+ * ssqcd_set_stencil_variant(v) forces variant v (0..5; 4-5 fall back to 2-3
+ * for an odd nrhs) for later calls in this process, or returns to tuning
+ * (-1); SSQCD_ERR_ARG otherwise.  Not a part of the paper: the paper's
+ * operator (Section 4) is the same in every variant. */
 int ssqcd_set_stencil_variant(int variant);
 
 /* The tuning recorded for this lattice (created with SSQCD_MIXED or
- * SSQCD_MIXED_F32LINKS) and nrhs: *variant the chosen variant, us[4] (may be
- * NULL) the measured microseconds per application of each.  SSQCD_ERR_ARG
+ * SSQCD_MIXED_F32LINKS) and nrhs: *variant the chosen variant, us[6] (may be
+ * NULL) the measured microseconds per application of each (0 for a variant
+ * not timed).  SSQCD_ERR_ARG
  * if nothing was tuned for that key yet. */
 int ssqcd_stencil_tuning(ssqcd_lattice lat, int nrhs, int* variant, double* us);
 

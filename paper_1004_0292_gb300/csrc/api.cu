@@ -1561,10 +1561,10 @@ extern "C" int ssqcd_stencil_tuning(ssqcd_lattice lat, int nrhs, int* variant, d
   SS_TRY(check_lattice(lat, false));
   if (!is_mixed(lat->precision)) return fail(SSQCD_ERR_ARG, "ssqcd_stencil_tuning: the lattice has no FP32 stencil");
   if (variant == nullptr || nrhs < 1) return fail(SSQCD_ERR_ARG, "ssqcd_stencil_tuning: bad arguments");
-  float t[4];
+  float t[6];
   SS_TRY(fp32_stencil_tuning(lat->g.V, nrhs, lat->precision == SSQCD_MIXED ? 16 : 32, variant, t));
   if (us != nullptr)
-    for (int v = 0; v < 4; ++v) us[v] = t[v];
+    for (int v = 0; v < 6; ++v) us[v] = t[v];
   return SSQCD_OK;
 }
 
@@ -1583,8 +1583,8 @@ extern "C" int ssqcd_time_stencil(ssqcd_lattice lat, int nrhs, int reps, double*
   auto once = [&]() -> int {
     if (mixed) {
       const bool f16 = lat->precision == SSQCD_MIXED;
-      return wilson32(lat->g, f16 ? lat->u16.p : lat->u32.p, f16 ? 16 : 32, a.as<float2>(), b.as<float2>(), nrhs,
-                      0.f, 1.f, nullptr, nullptr, st);
+      return wilson32_kernel_only(lat->g, f16 ? lat->u16.p : lat->u32.p, f16 ? 16 : 32, a.as<float2>(),
+                                  b.as<float2>(), nrhs, 0.f, 1.f, st);
     }
     if (df) return wilson_df(lat->g, lat->udf.as<float4>(), a.as<float4>(), b.as<float4>(), nrhs, 0.0, 1.0, st);
     return wilson64(lat->g, lat->u64.as<double2>(), a.as<double2>(), b.as<double2>(), nrhs, 0.0, 1.0, nullptr,

@@ -1701,11 +1701,10 @@ bool balanced_stencil() {
   return v;
 }
 
-// Resident blocks an SM the seed kernels B and P aim at (256 threads each,
-// striding over their source): 2 for lattices whose vectors sit in L2 (8^4
-// x 4: the last block's reduction, not bandwidth, sets their time), 8 when
-// the L vectors hold more than 2^21 elements and the kernels stream from
-// HBM (more loads in flight).
+// Resident blocks an SM the seed direction kernel P aims at (256 threads,
+// striding over its source): 2 for lattices whose vectors sit in L2 (8^4 x
+// 4), 8 when the L vectors hold more than 2^21 elements and P streams from
+// HBM (more loads in flight; 16^3 x 32 x 2 sources: 40 -> 32 us).
 long long seed_blocks_per_sm(long long n, int L) { return n * L > (1LL << 21) ? 8 : 2; }
 
 // Blocks per source of kernel P (it strides): seed_blocks_per_sm over all
@@ -1731,7 +1730,10 @@ int seed_blocks(long long n, int L) {
     return (v >= 1 && v <= 64) ? v : 2;  // measured (8^4 x 4, stored-residual loop): 2 -> 51.9, 4 -> 53.3 us an iteration
   }();
   long long b = (n + (long long)ept * kSeedBlock - 1) / ((long long)ept * kSeedBlock);
-  const long long cap = (152LL * seed_blocks_per_sm(n, L) + L - 1) / L;
+  // B ends in a last-block reduction over its blocks' partials: two blocks
+  // an SM at every size (16^3 x 32 x 2 sources: 62 us an iteration at two,
+  // 67 at eight)
+  const long long cap = (152LL * 2 + L - 1) / L;
   if (b > cap) b = cap;
   return (int)(b < 1 ? 1 : b);
 }

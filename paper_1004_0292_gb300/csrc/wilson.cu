@@ -163,6 +163,61 @@ wilson32p_kernel(Geometry g, LK lk, const float2* __restrict__ in_all, float2* _
   }
 }
 
+// FP32 spinors in the rhs-pair layout [npair][12][V] float4 (see hop_rp):
+// one thread per site and rhs pair (blockIdx.y).
+template <typename LK, int MinB>
+__global__ void __launch_bounds__(128, MinB)
+wilson32rp_kernel(Geometry g, LK lk, const float4* __restrict__ in_all, float4* __restrict__ out_all, float c0,
+                  float c1) {
+  const int s = blockIdx.x * 128 + threadIdx.x;
+  const int V = g.V;
+  if (s >= V) return;
+  const float4* in = in_all + (size_t)blockIdx.y * 12 * V;
+  float4* out = out_all + (size_t)blockIdx.y * 12 * V;
+  C2 acc[12];
+  const Coords c = site_coords(s, g);
+  hop_rp_site<0, +1>(lk, in, s, c, g, true, acc);
+  hop_rp_site<0, -1>(lk, in, s, c, g, false, acc);
+  hop_rp_site<1, +1>(lk, in, s, c, g, false, acc);
+  hop_rp_site<1, -1>(lk, in, s, c, g, false, acc);
+  hop_rp_site<2, +1>(lk, in, s, c, g, false, acc);
+  hop_rp_site<2, -1>(lk, in, s, c, g, false, acc);
+  hop_rp_site<3, +1>(lk, in, s, c, g, false, acc);
+  hop_rp_site<3, -1>(lk, in, s, c, g, false, acc);
+  const f32x2_t mk = pk2(-(float)g.kappa, -(float)g.kappa), cc0 = pk2(c0, c0);
+  const f32x2_t sgu = pk2(c1, c1), sgl = pk2(-c1, -c1);
+#pragma unroll
+  for (int i = 0; i < 12; ++i) {
+    const C2 p = c2_load(in + i * V + s);
+    // out = c0 p + c1 gamma5 (p - kappa D p)
+    const f32x2_t sg = i < 6 ? sgu : sgl;
+    const f32x2_t tre = fma2(mk, acc[i].re, p.re), tim = fma2(mk, acc[i].im, p.im);
+    const float2 ore = upk2(fma2(sg, tre, mul2(cc0, p.re))), oim = upk2(fma2(sg, tim, mul2(cc0, p.im)));
+    out[i * V + s] = make_float4(ore.x, ore.y, oim.x, oim.y);
+  }
+}
+
+// FP32 [nrhs][12][V] float2 <-> rhs pairs [npair][12][V] float4 (a missing
+// second rhs of the last pair reads as zero and is not written back)
+__global__ void to_rhs_pairs_kernel(const float2* __restrict__ a, float4* __restrict__ b, int nrhs, long long n12) {
+  const long long npn = (long long)((nrhs + 1) / 2) * n12;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < npn; e += (long long)gridDim.x * blockDim.x) {
+    const long long q = e / n12, k = e % n12;
+    const float2 x = a[(2 * q) * n12 + k];
+    const float2 y = (2 * q + 1 < nrhs) ? a[(2 * q + 1) * n12 + k] : make_float2(0.f, 0.f);
+    b[e] = make_float4(x.x, y.x, x.y, y.y);
+  }
+}
+__global__ void from_rhs_pairs_kernel(const float4* __restrict__ b, float2* __restrict__ a, int nrhs, long long n12) {
+  const long long npn = (long long)((nrhs + 1) / 2) * n12;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < npn; e += (long long)gridDim.x * blockDim.x) {
+    const long long q = e / n12, k = e % n12;
+    const float4 v = b[e];
+    a[(2 * q) * n12 + k] = make_float2(v.x, v.z);
+    if (2 * q + 1 < nrhs) a[(2 * q + 1) * n12 + k] = make_float2(v.y, v.w);
+  }
+}
+
 // Float-float stencil (SSQCD_DF): out = c0 in + c1 A in with float-float
 // spinors and links; see wilson_df.cuh.
 __global__ void __launch_bounds__(kStencilThreadsDF)
@@ -243,19 +298,25 @@ int wilson64(const Geometry& g, const double2* u, const double2* in, double2* ou
 namespace {
 using namespace wcore;
 
-// Four variants of the FP32 stencil with 12-parameter links (kernels below):
+// Six variants of the FP32 stencil with 12-parameter links (kernels above):
 //   0: all rhs of 32 sites a block (wilson32m), 4 blocks an SM (128 registers)
 //   1: the same at 3 blocks an SM (170 registers)
 //   2: one thread per site and rhs pair (wilson32p), 4 blocks an SM
 //   3: the same at 3 blocks an SM
+//   4: one thread per site and rhs pair, the two rhs in the lanes of the
+//      paired instructions (wilson32rp, rhs-pair layout), 4 blocks an SM
+//   5: the same at 3 blocks an SM
 // Which is fastest depends on the lattice volume, the number of rhs and the
 // link storage, so the first application for a (V, nrhs, link bits) key
 // times each variant (three launches each, CUDA events on the caller's
-// stream) and records the fastest; later applications with that key use it.
-// Variants 2-3 give no (in, out) partials, so callers that want them tune
-// among 0-1 only.  ssqcd_set_stencil_variant forces one variant
-// (tests, measurements), ssqcd_stencil_tuning reports the choice of a key.
-constexpr int kFp32Variants = 4;
+// stream; variants 4-5 only for an even nrhs, on the same buffers, which
+// then have the same size in the rhs-pair layout) and records the fastest;
+// later applications with that key use it (variants 4-5 convert to and from
+// the rhs-pair layout around the kernel).  Variants 2-5 give no (in, out)
+// partials, so callers that want them tune among 0-1 only.
+// ssqcd_set_stencil_variant forces one variant (tests, measurements),
+// ssqcd_stencil_tuning reports the choice of a key.
+constexpr int kFp32Variants = 6;
 
 struct TuneEntry {
   int variant;
@@ -274,12 +335,20 @@ void launch_fp32_variant(int v, const Geometry& g, const LK& lk, const float2* i
       wilson32m_kernel<LK, 4><<<nb, 128, 0, s>>>(g, lk, in, out, nrhs, c0, c1, dot_partial);
     else
       wilson32m_kernel<LK, 3><<<nb, 128, 0, s>>>(g, lk, in, out, nrhs, c0, c1, dot_partial);
-  } else {
+  } else if (v <= 3) {
     const dim3 grid((g.V + 127) / 128, (nrhs + 1) / 2);
     if (v == 2)
       wilson32p_kernel<LK, 4><<<grid, 128, 0, s>>>(g, lk, in, out, nrhs, c0, c1);
     else
       wilson32p_kernel<LK, 3><<<grid, 128, 0, s>>>(g, lk, in, out, nrhs, c0, c1);
+  } else {  // in, out in the rhs-pair layout
+    const dim3 grid((g.V + 127) / 128, (nrhs + 1) / 2);
+    const float4* a = reinterpret_cast<const float4*>(in);
+    float4* b = reinterpret_cast<float4*>(out);
+    if (v == 4)
+      wilson32rp_kernel<LK, 4><<<grid, 128, 0, s>>>(g, lk, a, b, c0, c1);
+    else
+      wilson32rp_kernel<LK, 3><<<grid, 128, 0, s>>>(g, lk, a, b, c0, c1);
   }
 }
 
@@ -289,7 +358,10 @@ template <typename LK>
 int fp32_variant(const Geometry& g, const LK& lk, int bits, const float2* in, float2* out, int nrhs, float c0,
                  float c1, float* dot_partial, cudaStream_t s) {
   const int forced = g_variant_override.load();
-  if (forced >= 0) return (dot_partial != nullptr && forced >= 2) ? 0 : forced;
+  if (forced >= 0) {
+    if (dot_partial != nullptr && forced >= 2) return 0;
+    return (forced >= 4 && nrhs % 2 != 0) ? forced - 2 : forced;
+  }
   const auto key = std::make_tuple(g.V, nrhs, bits, dot_partial != nullptr ? 1 : 0);
   {
     std::lock_guard<std::mutex> lock(g_tune_mutex);
@@ -303,8 +375,8 @@ int fp32_variant(const Geometry& g, const LK& lk, int bits, const float2* in, fl
     if (e0) cudaEventDestroy(e0);
     return 0;
   }
-  TuneEntry t{0, {0.f, 0.f, 0.f, 0.f}};
-  const int nv = dot_partial != nullptr ? 2 : kFp32Variants;
+  TuneEntry t{0, {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}};
+  const int nv = dot_partial != nullptr ? 2 : (nrhs % 2 == 0 ? kFp32Variants : 4);
   float best = 0.f;
   for (int v = 0; v < nv; ++v) {
     launch_fp32_variant(v, g, lk, in, out, nrhs, c0, c1, dot_partial, s);  // warm-up
@@ -334,8 +406,27 @@ int fp32_variant(const Geometry& g, const LK& lk, int bits, const float2* in, fl
 int wilson32_blocks(const Geometry& g) { return (g.V + 31) / 32; }
 
 int set_fp32_stencil_variant(int v) {
-  if (v < -1 || v >= kFp32Variants) return fail(SSQCD_ERR_ARG, "stencil variant must be -1 (tuned) or 0..3");
+  if (v < -1 || v >= kFp32Variants) return fail(SSQCD_ERR_ARG, "stencil variant must be -1 (tuned) or 0..5");
   g_variant_override.store(v);
+  return SSQCD_OK;
+}
+
+// The tuned variant's kernel alone on in, out (std layout buffers; an
+// rhs-pair variant runs on them as rhs-pair buffers of the same size), for
+// kernel timing.
+int wilson32_kernel_only(const Geometry& g, const void* links, int link_bits, const float2* in, float2* out, int nrhs,
+                         float c0, float c1, cudaStream_t s) {
+  if (nrhs <= 0) return SSQCD_OK;
+  const LinksF16 l16{static_cast<const uint2*>(links), g.V};
+  const LinksF32 l32{static_cast<const float4*>(links), g.V};
+  const int v = link_bits == 16 ? fp32_variant(g, l16, 16, in, out, nrhs, c0, c1, nullptr, s)
+                                : fp32_variant(g, l32, 32, in, out, nrhs, c0, c1, nullptr, s);
+  if (link_bits == 16)
+    launch_fp32_variant(v, g, l16, in, out, nrhs, c0, c1, nullptr, s);
+  else
+    launch_fp32_variant(v, g, l32, in, out, nrhs, c0, c1, nullptr, s);
+  count_launches(1);
+  SS_CHECK_LAUNCH();
   return SSQCD_OK;
 }
 
@@ -355,12 +446,30 @@ int wilson32(const Geometry& g, const void* links, int link_bits, const float2* 
     // the tuned all-rhs variants: links loaded once for several rhs
     const LinksF16 l16{static_cast<const uint2*>(links), g.V};
     const LinksF32 l32{static_cast<const float4*>(links), g.V};
+    const int v = link_bits == 16 ? fp32_variant(g, l16, 16, in, out, nrhs, c0, c1, dot_partial, s)
+                                  : fp32_variant(g, l32, 32, in, out, nrhs, c0, c1, dot_partial, s);
+    if (v >= 4) {
+      // the rhs-pair kernel between two layout conversions
+      const long long n12 = 12LL * g.V, np = (long long)((nrhs + 1) / 2) * n12;
+      DevBuf ta, tb;
+      SS_TRY(ta.alloc(sizeof(float4) * np));
+      SS_TRY(tb.alloc(sizeof(float4) * np));
+      to_rhs_pairs_kernel<<<grid_for(np, 256), 256, 0, s>>>(in, ta.as<float4>(), nrhs, n12);
+      const float2* a = reinterpret_cast<const float2*>(ta.p);
+      float2* b = reinterpret_cast<float2*>(tb.p);
+      if (link_bits == 16)
+        launch_fp32_variant(v, g, l16, a, b, nrhs, c0, c1, nullptr, s);
+      else
+        launch_fp32_variant(v, g, l32, a, b, nrhs, c0, c1, nullptr, s);
+      from_rhs_pairs_kernel<<<grid_for(np, 256), 256, 0, s>>>(tb.as<float4>(), out, nrhs, n12);
+      count_launches(3);
+      SS_CHECK_LAUNCH();
+      return SSQCD_OK;
+    }
     if (link_bits == 16)
-      launch_fp32_variant(fp32_variant(g, l16, 16, in, out, nrhs, c0, c1, dot_partial, s), g, l16, in, out, nrhs, c0,
-                          c1, dot_partial, s);
+      launch_fp32_variant(v, g, l16, in, out, nrhs, c0, c1, dot_partial, s);
     else
-      launch_fp32_variant(fp32_variant(g, l32, 32, in, out, nrhs, c0, c1, dot_partial, s), g, l32, in, out, nrhs, c0,
-                          c1, dot_partial, s);
+      launch_fp32_variant(v, g, l32, in, out, nrhs, c0, c1, dot_partial, s);
     count_launches(1);
     SS_CHECK_LAUNCH();
     return SSQCD_OK;

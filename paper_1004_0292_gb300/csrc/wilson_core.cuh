@@ -813,5 +813,125 @@ __device__ __forceinline__ void site_hops_pair(const LK& lk, const float2* __res
   hop_pair<3, -1>(lk, in0, in1, s, c, g, false, acc0, acc1);
 }
 
+// ---- FP32, two rhs in the lanes of the paired instructions ------------------------------
+// Layout "rhs pairs": rhs 2q and 2q + 1 interleaved, [npair][12][V] float4
+// = (re_{2q}, re_{2q+1}, im_{2q}, im_{2q+1}), so the real parts of the two
+// rhs form one register pair and the imaginary parts another.  A complex
+// number times a link element u is then four paired FMAs for two rhs with
+// the broadcast pairs (u.x, u.x), (u.y, u.y), (-u.y, -u.y), and a factor
+// +-1 or +-i (the spin projection and reconstruction) only chooses which
+// pair and which sign: no lane swaps.  A thread covers one site and one rhs
+// pair: 12 16-byte loads per neighbour, 72 paired FMAs per hop for two rhs.
+struct C2 {
+  f32x2_t re, im;
+};
+
+__device__ __forceinline__ C2 c2_load(const float4* __restrict__ p) {
+  const float4 v = __ldg(p);
+  return C2{pk2(v.x, v.y), pk2(v.z, v.w)};
+}
+// z + code * w (code +1, -1, +i, -i)
+__device__ __forceinline__ C2 c2_add_unit(const C2& z, int code, const C2& w) {
+  switch (code) {
+    case P1: return C2{add2(z.re, w.re), add2(z.im, w.im)};
+    case M1: return C2{sub2(z.re, w.re), sub2(z.im, w.im)};
+    case PI: return C2{sub2(z.re, w.im), add2(z.im, w.re)};  // + i w = (-w.im, w.re)
+    default: return C2{add2(z.re, w.im), sub2(z.im, w.re)};  // - i w = (w.im, -w.re)
+  }
+}
+__device__ __forceinline__ C2 c2_neg(const C2& z) { return C2{neg2(z.re), neg2(z.im)}; }
+
+// A link rebuilt from its 12 parameters as broadcast pairs: x[e] = (u.x,
+// u.x), y[e] = (u.y, u.y), ny[e] = (-u.y, -u.y) for element e = 3 row +
+// column of U (dagger = false) or of U^H (true; conj folds into the signs).
+struct BcastLink {
+  f32x2_t x[9], y[9], ny[9];
+};
+template <typename LK>
+__device__ __forceinline__ void load_bcast(const LK& lk, int mu, int site, bool dagger, BcastLink& B) {
+  Link32 L;
+  lk.load(mu, site, L);
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const float2 u = dagger ? L.e[c][r] : L.e[r][c];
+      const float uy = dagger ? -u.y : u.y;
+      B.x[3 * r + c] = pk2(u.x, u.x);
+      B.y[3 * r + c] = pk2(uy, uy);
+      B.ny[3 * r + c] = pk2(-uy, -uy);
+    }
+}
+// row a of the link times h: sum_b M_ab h_b for both rhs
+__device__ __forceinline__ C2 c2_row(const BcastLink& B, int a, const C2 (&h)[3]) {
+  f32x2_t re = mul2(B.x[3 * a], h[0].re), im = mul2(B.x[3 * a], h[0].im);
+  re = fma2(B.ny[3 * a], h[0].im, re);
+  im = fma2(B.y[3 * a], h[0].re, im);
+#pragma unroll
+  for (int b = 1; b < 3; ++b) {
+    re = fma2(B.x[3 * a + b], h[b].re, re);
+    im = fma2(B.x[3 * a + b], h[b].im, im);
+    re = fma2(B.ny[3 * a + b], h[b].im, re);
+    im = fma2(B.y[3 * a + b], h[b].re, im);
+  }
+  return C2{re, im};
+}
+
+// One hop (DIR +1: U_mu(x) psi(x + mu), h = psi_u - B psi_l, lower -B^H wv;
+// DIR -1: U_mu(x - mu)^H psi(x - mu), h = psi_u + B psi_l, lower +B^H wv)
+// of one rhs pair into acc[12] (FIRST: set instead of add).
+template <int MU, int DIR, bool FIRST>
+__device__ __forceinline__ void hop_rp(const BcastLink& B, const float4* __restrict__ in, int nb, int V, bool negate,
+                                       C2 (&acc)[12]) {
+  using S = Spin<MU>;
+  C2 h[2][3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const C2 u0 = c2_load(in + (0 * 3 + a) * V + nb);
+    const C2 u1 = c2_load(in + (1 * 3 + a) * V + nb);
+    const C2 l0 = c2_load(in + ((2 + S::bcol0) * 3 + a) * V + nb);
+    const C2 l1 = c2_load(in + ((2 + S::bcol1) * 3 + a) * V + nb);
+    // forward subtracts B psi_l: the code with its sign flipped (P1 <-> M1, PI <-> MI)
+    h[0][a] = c2_add_unit(u0, DIR > 0 ? (S::bcode0 ^ 1) : S::bcode0, l0);
+    h[1][a] = c2_add_unit(u1, DIR > 0 ? (S::bcode1 ^ 1) : S::bcode1, l1);
+    if (MU == 3 && negate) {
+      h[0][a] = c2_neg(h[0][a]);
+      h[1][a] = c2_neg(h[1][a]);
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const C2 w0 = c2_row(B, a, h[0]), w1 = c2_row(B, a, h[1]);
+    const C2 wt0 = S::hcol0 == 0 ? w0 : w1, wt1 = S::hcol1 == 0 ? w0 : w1;
+    const int c0 = DIR > 0 ? (S::hcode0 ^ 1) : S::hcode0, c1 = DIR > 0 ? (S::hcode1 ^ 1) : S::hcode1;
+    if (FIRST) {
+      acc[0 * 3 + a] = w0;
+      acc[1 * 3 + a] = w1;
+      const C2 zero{0ull, 0ull};
+      acc[2 * 3 + a] = c2_add_unit(zero, c0, wt0);
+      acc[3 * 3 + a] = c2_add_unit(zero, c1, wt1);
+    } else {
+      acc[0 * 3 + a] = c2_add_unit(acc[0 * 3 + a], P1, w0);
+      acc[1 * 3 + a] = c2_add_unit(acc[1 * 3 + a], P1, w1);
+      acc[2 * 3 + a] = c2_add_unit(acc[2 * 3 + a], c0, wt0);
+      acc[3 * 3 + a] = c2_add_unit(acc[3 * 3 + a], c1, wt1);
+    }
+  }
+}
+
+template <int MU, int DIR, typename LK>
+__device__ __forceinline__ void hop_rp_site(const LK& lk, const float4* __restrict__ in, int s, const Coords& c,
+                                            const Geometry& g, bool first, C2 (&acc)[12]) {
+  bool w;
+  const int nb = neighbour<MU, DIR>(s, c, g, w);
+  BcastLink B;
+  load_bcast(lk, MU, DIR > 0 ? s : nb, DIR < 0, B);
+  const bool neg = MU == 3 && w && g.bc_t < 0;
+  if (first)
+    hop_rp<MU, DIR, true>(B, in, nb, g.V, neg, acc);
+  else
+    hop_rp<MU, DIR, false>(B, in, nb, g.V, neg, acc);
+}
+
 }  // namespace wcore
 }  // namespace ssqcd
