@@ -811,6 +811,8 @@ def cpu_baseline(budget_s=20.0, gpu_iterations=None, pairs=48, sample_iters=None
     t_rr = t_app[0] * (m / m_s) + (t_rr_all - t_app[0]) * (m / m_s) ** 2
     oracle_iters = _oracle_iterations()
     iters = oracle_iters if oracle_iters is not None else gpu_iterations
+    if iters is None:
+        raise RuntimeError("no iteration count: tests/golden/config3_iterations.json is missing")
     K = len(w["windows"])
     t_step = t_iter * iters * w["L"] + t_mom * K * w["L"] + t_rr * K
     return {"value": pairs / t_step, "unit": UNIT, "cores": int(_host_cores()), "kind": "oracle",
@@ -845,6 +847,10 @@ def run_reference(args):
     world, rank, local = _dist()
     if rank != 0:
         return
+    if _oracle_iterations() is None:
+        print(json.dumps({"impl": "reference", "unavailable": "the oracle's iteration count of this workload "
+                          "(tests/golden/config3_iterations.json) is missing"}), flush=True)
+        return
     vals = []
     for i in range(args.warmup + args.steps):
         cb = cpu_baseline(budget_s=args.cpu_budget / 2, sample_iters=2)
@@ -867,6 +873,9 @@ def run_reference(args):
                          "iterations_from": vals[-1]["iterations_from"], "extrapolated": True},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "config1_full_solve": c1,
+        "ms_per_step_note": "the extrapolated full step of the oracle on this workload; each of the "
+                            f"{args.warmup + args.steps} steps of this run timed a bounded sample of it (about "
+                            f"{args.cpu_budget / 2:.0f} s of host work)",
     }
     print(json.dumps(out), flush=True)
 
