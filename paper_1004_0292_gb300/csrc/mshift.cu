@@ -1626,108 +1626,6 @@ basis_combine_df_kernel(char* const* __restrict__ tab, long long n, int L, const
     for (int o = 0; o < no; ++o) out[((size_t)l * O + o0 + o) * n + e] = accd[o];
 }
 
-// The combination of float-float residuals on both pipes at once: the
-// float-float form above keeps the FP32 pipes busy and leaves the FP64
-// pipe idle, and the FP64 form (three FP64 FMAs a term) is bound by the
-// FP64 pipe.  The two are separate units of the SM, so one grid interleaves
-// the two roles block by block: of every kRolePeriod consecutive 64-element
-// tiles, kFp64Tiles are combined in FP64 (the residual converted to FP64,
-// the three-multiplication products of basis_combine_kernel) and the rest in
-// float-float (p_cfma, tile sums into FP64).  Every SM then runs blocks of
-// both roles side by side.  Per element the arithmetic is exactly that of
-// one of the two kernels; the moments are the same to the float-float
-// rounding (~2^-48 relative per term).
-constexpr int kRolePeriod = 3;
-constexpr int kFp64Tiles = 1;
-
-// one role of basis_combine_two_pipe_kernel over this block's 64 elements
-template <bool FP64>
-__device__ __forceinline__ void combine_role(char* const* __restrict__ tab, long long n, int L,
-                                             const double2* __restrict__ C, int O, int S, int Sl, int l, int o0,
-                                             int no, long long e, double2* __restrict__ out) {
-  __shared__ ff::PCoef s_w[FP64 ? 1 : kCombTile][kCombOut];
-  __shared__ double s_wr[FP64 ? kCombTile : 1][kCombOut], s_wi[FP64 ? kCombTile : 1][kCombOut],
-      s_ws[FP64 ? kCombTile : 1][kCombOut];
-  __shared__ const float4* s_p[kCombTile];
-  const long long Ln = (long long)L * n;
-  double2 accd[kCombOut];  // float-float role: tile sums in FP64
-  double a1[kCombOut], a2[kCombOut], a3[kCombOut];  // FP64 role: the three real sums
-#pragma unroll
-  for (int o = 0; o < kCombOut; ++o) {
-    if (FP64)
-      a1[o] = a2[o] = a3[o] = 0.0;
-    else
-      accd[o] = make_double2(0.0, 0.0);
-  }
-  for (int s0 = 0; s0 < Sl; s0 += kCombTile) {
-    const int ns = min(kCombTile, Sl - s0);
-    __syncthreads();
-    for (int t = threadIdx.x; t < kCombTile * kCombOut; t += kCombThreads) {
-      const int ss = t / kCombOut, oo = t % kCombOut;
-      const double2 c = (ss < ns && oo < no) ? C[((size_t)l * O + o0 + oo) * S + s0 + ss] : make_double2(0.0, 0.0);
-      if (FP64) {
-        s_wr[ss][oo] = c.x;
-        s_wi[ss][oo] = c.y;
-        s_ws[ss][oo] = c.x + c.y;
-      } else {
-        s_w[ss][oo] = ff::p_coef(ff::from_double2(c));
-      }
-    }
-    if (threadIdx.x < kCombTile) {
-      const int s = s0 + threadIdx.x;
-      s_p[threadIdx.x] = threadIdx.x < ns ? reinterpret_cast<const float4*>(tab[s >> kBasisLog]) +
-                                                (long long)(s & (kBasisBlock - 1)) * Ln + (long long)l * n
-                                          : nullptr;
-    }
-    __syncthreads();
-    if (e >= n) continue;
-    if (FP64) {
-#pragma unroll 4
-      for (int ss = 0; ss < ns; ++ss) {
-        const double2 x = ff::to_double2(s_p[ss][e]);
-        const double xs = x.x + x.y;
-#pragma unroll
-        for (int o = 0; o < kCombOut; ++o) {
-          a1[o] = fma(s_wr[ss][o], x.x, a1[o]);
-          a2[o] = fma(s_wi[ss][o], x.y, a2[o]);
-          a3[o] = fma(s_ws[ss][o], xs, a3[o]);
-        }
-      }
-    } else {
-      f32x2_t ah[kCombOut], al[kCombOut];
-#pragma unroll
-      for (int o = 0; o < kCombOut; ++o) ah[o] = al[o] = 0ull;
-#pragma unroll 2
-      for (int ss = 0; ss < ns; ++ss) {
-        const ff::PVal x = ff::p_val(s_p[ss][e]);
-#pragma unroll
-        for (int o = 0; o < kCombOut; ++o) ff::p_cfma(ah[o], al[o], s_w[ss][o], x);
-      }
-#pragma unroll
-      for (int o = 0; o < kCombOut; ++o) {
-        const double2 t = ff::to_double2(ff::make2(ah[o], al[o]));
-        accd[o].x += t.x;
-        accd[o].y += t.y;
-      }
-    }
-  }
-  if (e < n)
-    for (int o = 0; o < no; ++o)
-      out[((size_t)l * O + o0 + o) * n + e] = FP64 ? make_double2(a1[o] - a2[o], (a3[o] - a1[o]) - a2[o]) : accd[o];
-}
-
-__global__ void __launch_bounds__(kCombThreads, 2)
-basis_combine_two_pipe_kernel(char* const* __restrict__ tab, long long n, int L, const double2* __restrict__ C, int O,
-                              int S, const int* __restrict__ count, double2* __restrict__ out, int l0) {
-  const int l = blockIdx.y + l0, o0 = blockIdx.z * kCombOut;
-  const int no = min(kCombOut, O - o0);
-  const long long e = blockIdx.x * (long long)kCombThreads + threadIdx.x;
-  if ((blockIdx.x % kRolePeriod) < kFp64Tiles)
-    combine_role<true>(tab, n, L, C, O, S, count[l], l, o0, no, e, out);
-  else
-    combine_role<false>(tab, n, L, C, O, S, count[l], l, o0, no, e, out);
-}
-
 // sources [l0, l0 + nl) of L (all by default)
 template <typename VR, typename VO>
 int launch_combine(char* const* tab, long long n, int L, const double2* C, int O, int S, const int* count, VO* out,
@@ -2728,16 +2626,7 @@ int basis_moments(const KrylovBasis& b, const double2* coef_host, int M, double2
         const char* e = std::getenv("SSQCD_COMB_DF_OUT");
         return (e != nullptr && std::atoi(e) == 4) ? 4 : 8;
       }();
-      // both pipes (default), or the FP32 pipes alone (SSQCD_COMB_TWO_PIPE=0)
-      static const bool two_pipe = [] {
-        const char* e = std::getenv("SSQCD_COMB_TWO_PIPE");
-        return !(e != nullptr && std::atoi(e) == 0);
-      }();
-      if (two_pipe) {
-        const dim3 grid((unsigned)((b.n + kCombThreads - 1) / kCombThreads), nl, (M + kCombOut - 1) / kCombOut);
-        basis_combine_two_pipe_kernel<<<grid, kCombThreads, 0, s>>>(b.tab.as<char*>(), b.n, L, G, M, S,
-                                                                    b.count.as<int>(), s_hat, l0);
-      } else if (out_df == 4) {
+      if (out_df == 4) {
         const dim3 grid((unsigned)((b.n + kCombThreads - 1) / kCombThreads), nl, (M + 3) / 4);
         basis_combine_df_kernel<4><<<grid, kCombThreads, 0, s>>>(b.tab.as<char*>(), b.n, L, G, M, S,
                                                                  b.count.as<int>(), s_hat, l0);
