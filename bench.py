@@ -540,7 +540,10 @@ def run_stencil_large(ss, stream, peaks):
         out[name] = {"us_per_call": 1e3 * ms, "hbm_gbs": gbs, "hbm_frac": gbs / peaks["hbm_gbs"],
                      "tflops": STENCIL_FLOP_PER_SITE * V * c["rhs"] / (ms / 1e3) / 1e12}
         if prec in (ss.MIXED, ss.MIXED_F32LINKS):
-            v, us = ss.stencil_tuning(lat, c["rhs"])
+            try:
+                v, us = ss.stencil_tuning(lat, c["rhs"])
+            except ss.SsqcdError:  # a forced variant: nothing tuned
+                v, us = None, None
             out[name]["variant"] = {"chosen": v, "us_per_variant": us,
                                     "variants": ["all rhs of 32 sites a block, 4 blocks/SM", "same, 3 blocks/SM",
                                                  "thread per site and rhs pair, 4 blocks/SM", "same, 3 blocks/SM",
@@ -940,6 +943,7 @@ def run_only(args):
     torch.cuda.set_stream(stream)
     peaks = _measured_peaks()
     if args.only == "stencil_large":
+        ss.set_stencil_variant(args.stencil_variant)
         out = run_stencil_large(ss, stream, peaks)
     elif args.only.startswith("beta_study"):
         out = run_beta_study(ss, stream, big=args.only.endswith("16x32"))
@@ -963,6 +967,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end (host buffers) leg")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--cpu-budget", type=float, default=30.0)
+    ap.add_argument("--stencil-variant", type=int, default=-1,
+                    help="FP32 stencil variant for stencil_large (0..5; -1: the autotuner's choice)")
     ap.add_argument("--only", choices=["stencil_large", "config2", "beta_study", "beta_study_16x32"], default=None,
                     help="run one secondary leg alone and print its JSON (profiling runs)")
     args = ap.parse_args()
