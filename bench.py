@@ -93,14 +93,10 @@ STENCIL_FP64_TRAFFIC = 5.565952e6  # ncu: dram read 5.565952 MB, write 0 per lau
 # a launch are 64 x 128 x 49152 = 402.7 MB -- part of y / p-hat stays in L2).
 # Null them when the kernel changes.
 # DRAM traffic of one launch of basis_combine_kernel on the headline workload
-# (one window, one block of 2 sources, 2499 stored residuals, 16 moments in
-# two groups of 8 that each read the residuals): scaled from the ncu capture
-# of the same kernel on the 8^4 workload (dram read 2.406 GB + write 24.4 MB
-# for 767 residuals x 4 sources x 49152 elements and 8 moments: 16.0 B read
-# per residual element and group of 8, the moments written once), since the
-# headline's 128 GB of residuals cannot be captured with every section:
-# 2 x 2499 x 2 x 1572864 x 16 B + 16 x 2 x 1572864 x 16 B.
-COMBINE_TRAFFIC = 2 * 2499 * 2 * 1572864 * 16.0 + 16 * 2 * 1572864 * 16.0
+# (one window, one block of 2 sources, 2499 stored residuals, 16 moments,
+# real coefficients) from a one-pass ncu capture (dram__bytes_read.sum
+# 123.875 GB + dram__bytes_write.sum 0.814 GB); None once the kernel changes.
+COMBINE_TRAFFIC = 123875257344.0 + 814184960.0
 UPDATE_FP64_TRAFFIC_ALL_LIVE = (204.503552 + 139.793408) * 1e6
 UPDATE_TMA_TRAFFIC_ALL_LIVE = (204.504320 + 139.588352) * 1e6
 
@@ -207,11 +203,14 @@ def windows_step(ss, lat, src, w, want_vectors=False):
 
 
 def moments_flops(w, st, n):
-    """Algorithmic FP64 flops of the moment combination of one solve: 8 per
-    complex multiply-add, (windows x M) moments x (slots = iterations + 1)
-    stored residuals x n elements x L sources (each block's slot count is
-    bounded by the largest, stats.iterations)."""
-    return 8 * len(w["windows"]) * w["M"] * (st["iterations"] + 1) * n * w["L"]
+    """Algorithmic FP64 flops of the moment combination of one solve:
+    (windows x M) moments x (slots = iterations + 1) stored residuals x n
+    complex elements x L sources (each block's slot count is bounded by the
+    largest, stats.iterations), times 4 per term when the coefficients are
+    real (stats.real_moments: a real times a complex number, 2 FMA) and 8
+    when they are complex (a complex multiply-add)."""
+    per = 4 if st.get("real_moments") else 8
+    return per * len(w["windows"]) * w["M"] * (st["iterations"] + 1) * n * w["L"]
 
 
 def run_ours(args):
@@ -377,12 +376,14 @@ def run_ours(args):
                           "whose other kernels are the small coefficient recurrences)",
                 "bound": "alu", "achieved": mom_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": mom_tf / FP64_PEAK_TFLOPS, "traffic": COMBINE_TRAFFIC,
-                "traffic_note": "bytes per launch (one window, one source block), scaled from the ncu capture on "
-                                "the 8^4 workload (profiles/combine_fp64_8x8x8x8.md); algorithmic (each residual "
-                                "read once per launch) is half: the 16 moments are two groups of 8",
+                "traffic_note": "bytes per launch (one window, one block of 2 sources: each residual read "
+                                "once, 2 x 2499 x 1572864 x 16 B = 125.8 GB, and 32 moments written, 0.8 GB; "
+                                "profiles/combine_fp64_16x16x16x32.md)",
                 "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (no FP64 entry in "
                                "MEASURED_PEAKS.json)",
-                "flop_count": "8 per complex multiply-add (the kernel issues 3 real multiplications per product)",
+                "flop_count": ("4 per term: real coefficients (conjugate-pair points), a real times a complex "
+                               "residual element, 2 FMA" if last.get("real_moments") else
+                               "8 per complex multiply-add (the kernel issues 3 real multiplications per product)"),
                 "phase_ms": last["ms_moments"], "fraction_of_step": last["ms_moments"] / (total_ms / args.steps),
             },
             "stencil": {

@@ -188,6 +188,14 @@ typedef struct {
   int    n_converged;     /* accepted pairs with residual <= opts.converged_tol
                              (Rayleigh-Ritz only; the Hankel extraction has no
                              residuals and reports 0)                         */
+  int    real_moments;    /* 1: the moments were combined from the stored seed
+                             residuals with real coefficients -- the points
+                             and weights come in conjugate pairs (line pairs
+                             about a real centre, Section 3), the seed's CG
+                             scalars are real, so each pair's coefficients
+                             are conjugate and sum to a real number; 0: complex
+                             coefficients (circle points, shift-vector updates,
+                             or SSQCD_REAL_MOMENTS=0 in the environment)      */
 } ssqcd_stats;
 
 /* ---- lattice / operator ---------------------------------------------------- */

@@ -66,7 +66,7 @@ class Stats(C.Structure):
         ("timed", C.c_int), ("launches_update", C.c_int), ("ms_k_stencil", C.c_double),
         ("ms_k_seed", C.c_double), ("ms_k_scalars", C.c_double), ("ms_k_update", C.c_double),
         ("timed_shift_updates", C.c_longlong), ("basis", C.c_int), ("basis_bytes", C.c_double),
-        ("n_converged", C.c_int),
+        ("n_converged", C.c_int), ("real_moments", C.c_int),
     ]
 
     def as_dict(self):

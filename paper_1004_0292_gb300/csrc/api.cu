@@ -39,6 +39,9 @@ struct SolvePlan {
   std::vector<char> hi_open;
   std::vector<double2> zu;                   // union of the windows' points
   std::vector<std::vector<double2>> coefk;   // per window: [NU][MM] moment coefficients
+  // every point's conjugate is a point, with conjugate coefficients in every
+  // window: the moments are real combinations of the seed residuals
+  bool real_moments = false;
 };
 
 }  // namespace
@@ -549,6 +552,35 @@ namespace {
 
 // Everything of a solve that does not touch the device: windows, nodes,
 // the union of the windows' points and the moment coefficients.
+// True when the union of the points is closed under conjugation (exactly:
+// the line pairs of a real centre are built that way) and every window's
+// coefficient of the conjugate point is the conjugate of the point's own, to
+// within 1e-12 of the largest coefficient of that moment.  The moment
+// sum_j c_j x_j over such a set then has real coefficients in the Krylov
+// basis of the seed residuals (x of conj z has the conjugate coefficients).
+bool conjugate_closed(const std::vector<double2>& zu, const std::vector<std::vector<double2>>& coefk, int MM) {
+  const int NU = (int)zu.size();
+  std::vector<int> partner(NU, -1);
+  for (int u = 0; u < NU; ++u) {
+    for (int q = 0; q < NU; ++q)
+      if (zu[q].x == zu[u].x && zu[q].y == -zu[u].y) {
+        partner[u] = q;
+        break;
+      }
+    if (partner[u] < 0) return false;
+  }
+  for (const auto& c : coefk)
+    for (int m = 0; m < MM; ++m) {
+      double big = 0.0;
+      for (int u = 0; u < NU; ++u) big = std::max(big, std::hypot(c[(size_t)u * MM + m].x, c[(size_t)u * MM + m].y));
+      for (int u = 0; u < NU; ++u) {
+        const double2 a = c[(size_t)u * MM + m], b = c[(size_t)partner[u] * MM + m];
+        if (std::hypot(a.x - b.x, a.y + b.y) > 1e-12 * big) return false;
+      }
+    }
+  return true;
+}
+
 int plan_solve(const double interval[2], int N, int M, int L, const ssqcd_opts* opts_in, SolvePlan* P) {
   if (interval == nullptr || !(interval[1] > interval[0])) return fail(SSQCD_ERR_ARG, "interval must have b > a");
   if (N < 1 || M < 1 || L < 1) return fail(SSQCD_ERR_ARG, "N, M, L must be >= 1");
@@ -626,6 +658,7 @@ int plan_solve(const double interval[2], int N, int M, int L, const ssqcd_opts* 
   P->rho = rho;
   P->zu.swap(zu);
   P->coefk.swap(coefk);
+  P->real_moments = conjugate_closed(P->zu, P->coefk, MM);
   P->gam.resize(K);
   P->rad.assign(K, rho);
   P->lo.resize(K);
@@ -721,10 +754,12 @@ int plan_windows(int K, const double* iv, int N, int M, int L, const ssqcd_opts*
   P->NU = NU;
   P->zu.swap(zu);
   P->coefk.swap(coefk);
+  P->real_moments = conjugate_closed(P->zu, P->coefk, MM);
   return SSQCD_OK;
 }
 
-void fill_cg_stats(const ShiftedCGOut& cg, const std::vector<int>& iters, ssqcd_stats* st) {
+// plan_real: the plan's points are conjugate-closed (SolvePlan::real_moments)
+void fill_cg_stats(const ShiftedCGOut& cg, const std::vector<int>& iters, ssqcd_stats* st, bool plan_real = false) {
   st->iterations = cg.seed_iters;
   st->reliable_updates = cg.reliable_updates;
   st->ms_cg = cg.ms;
@@ -739,6 +774,7 @@ void fill_cg_stats(const ShiftedCGOut& cg, const std::vector<int>& iters, ssqcd_
   st->timed_shift_updates = cg.timed_units;
   st->basis = cg.basis;
   st->basis_bytes = cg.basis_bytes;
+  st->real_moments = (plan_real && real_moments_enabled() && cg.basis == 1) ? 1 : 0;
 }
 
 // After the shifted CG: per window the moments (Eq. 2) and Rayleigh-Ritz (or
@@ -807,9 +843,10 @@ int extract_eigenpairs(ssqcd_lattice lat, const SolvePlan& P, DevBuf& yd, Krylov
     } else {
     SS_TRY(S.alloc(sizeof(double2) * n * m));
     if (overlap)
-      SS_TRY(basis_moments(kb, P.coefk[k].data(), MM, S.as<double2>(), mscratch, st, ov.side, ov.ev.data()));
+      SS_TRY(basis_moments(kb, P.coefk[k].data(), MM, S.as<double2>(), mscratch, st, ov.side, ov.ev.data(),
+                           P.real_moments));
     else if (kb.S > 0)
-      SS_TRY(basis_moments(kb, P.coefk[k].data(), MM, S.as<double2>(), scratch, st));
+      SS_TRY(basis_moments(kb, P.coefk[k].data(), MM, S.as<double2>(), scratch, st, nullptr, nullptr, P.real_moments));
     else
       SS_TRY(moments_device(yd.as<double2>(), NU, MM, L, n, P.coefk[k].data(), S.as<double2>(), scratch, st));
     if (k == K - 1) {
@@ -947,7 +984,7 @@ int run_solve(ssqcd_lattice lat, const SolvePlan& P, ssqcd_result* out) {
                           lat->precision, P.o.reliable_every,
                           basis_cap_for(lat->precision, P.o.basis, P.o.basis_max_bytes, n, NU, L), yd, &kb,
                           iters.data(), &cg);
-    fill_cg_stats(cg, iters, &res->stats);
+    fill_cg_stats(cg, iters, &res->stats, P.real_moments);
     *out = res;  // a result handle even on failure, so its stats can be read
     if (s1 != SSQCD_OK) return s1;
     if (!P.hankel) vd.release();
@@ -979,13 +1016,13 @@ int run_solve(ssqcd_lattice lat, const SolvePlan& P, ssqcd_result* out) {
                           basis_cap_for(lat->precision, P.o.basis, P.o.basis_max_bytes, n, NU, Lb), yd, &kb,
                           iters.data() + (size_t)l0 * NU, &cgb);
     add_cg_stats(cgb, &cg);
-    fill_cg_stats(cg, iters, &res->stats);
+    fill_cg_stats(cg, iters, &res->stats, P.real_moments);
     if (s1 != SSQCD_OK) return s1;
     SS_CUDA(cudaEventRecord(m0, st));
     for (int k = 0; k < K; ++k) {
       double2* dst = Sk[k].as<double2>() + (size_t)l0 * MM * n;
       if (kb.S > 0)
-        SS_TRY(basis_moments(kb, P.coefk[k].data(), MM, dst, scratch, st));
+        SS_TRY(basis_moments(kb, P.coefk[k].data(), MM, dst, scratch, st, nullptr, nullptr, P.real_moments));
       else
         SS_TRY(moments_device(yd.as<double2>(), NU, MM, Lb, n, P.coefk[k].data(), dst, scratch, st));
     }
@@ -1050,7 +1087,8 @@ extern "C" int ssqcd_ss_moments(ssqcd_lattice lat, const double interval[2], int
                         iters.data(), &cg));
   SS_TRY(S.alloc(sizeof(double2) * n * P.MM * L));
   if (kb.S > 0)
-    SS_TRY(basis_moments(kb, P.coefk[0].data(), P.MM, S.as<double2>(), scratch, st));
+    SS_TRY(basis_moments(kb, P.coefk[0].data(), P.MM, S.as<double2>(), scratch, st, nullptr, nullptr,
+                         P.real_moments));
   else
     SS_TRY(moments_device(yd.as<double2>(), P.NU, P.MM, L, n, P.coefk[0].data(), S.as<double2>(), scratch, st));
   // the first M of the MM moments of each source
@@ -1062,7 +1100,7 @@ extern "C" int ssqcd_ss_moments(ssqcd_lattice lat, const double interval[2], int
   SS_CUDA(cudaStreamSynchronize(st));
   if (stats) {
     *stats = ssqcd_stats{};
-    fill_cg_stats(cg, iters, stats);
+    fill_cg_stats(cg, iters, stats, P.real_moments);
   }
   return SSQCD_OK;
 }
@@ -1228,7 +1266,8 @@ int request_next_block(ServerRequest& r, bool* more) {
     int st1 = SSQCD_OK;
     for (int k = 0; k < r.P.K && st1 == SSQCD_OK; ++k) {
       double2* dst = r.Sk[k].as<double2>() + (size_t)r.blk0 * r.P.MM * n;
-      st1 = r.basis.S > 0 ? basis_moments(r.basis, r.P.coefk[k].data(), r.P.MM, dst, scratch, r.stream)
+      st1 = r.basis.S > 0 ? basis_moments(r.basis, r.P.coefk[k].data(), r.P.MM, dst, scratch, r.stream, nullptr,
+                                            nullptr, r.P.real_moments)
                           : moments_device(yd.as<double2>(), r.P.NU, r.P.MM, Lb, n, r.P.coefk[k].data(), dst, scratch,
                                            r.stream);
     }
@@ -1273,7 +1312,7 @@ int request_complete(ssqcd_server_s* srv, ServerRequest& r, bool* still_running 
     r.res = res;
     res->V = lat->g.V;
     res->n = 12LL * lat->g.V;
-    fill_cg_stats(r.cg_acc, r.iters, &res->stats);
+    fill_cg_stats(r.cg_acc, r.iters, &res->stats, r.P.real_moments);
     if (!r.P.hankel) r.vd.release();
     DevBuf yd;
     {
@@ -1301,7 +1340,7 @@ int request_complete(ssqcd_server_s* srv, ServerRequest& r, bool* still_running 
   std::vector<int> iters((size_t)r.P.NU * r.P.L);
   SS_TRY(r.run->finish(yd, iters.data(), nullptr, &cg));
   r.run->take_basis(&r.basis);
-  fill_cg_stats(cg, iters, &res->stats);
+  fill_cg_stats(cg, iters, &res->stats, r.P.real_moments);
   r.run.reset();
   if (!r.P.hankel) r.vd.release();
   {

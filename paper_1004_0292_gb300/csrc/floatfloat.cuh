@@ -301,6 +301,21 @@ __device__ __forceinline__ void p_cfma(f32x2_t& ch, f32x2_t& cl, const PCoef& u,
   p_fast_two_sum(s2, lo, ch, cl);
 }
 
+// c + u v for a REAL float-float coefficient u, given as the pairs
+// (u.hi, u.hi) and (u.lo, u.lo), and a complex float-float v: the real and
+// imaginary parts are two independent float-float multiply-adds, one in
+// each lane (the operation order of ff::fma1 on each part).
+__device__ __forceinline__ void p_rfma(f32x2_t& ch, f32x2_t& cl, f32x2_t uh, f32x2_t ul, const PVal& v) {
+  const f32x2_t p = ::ssqcd::mul2(uh, v.h);
+  const f32x2_t e = ::ssqcd::fma2(uh, v.h, neg2(p));
+  f32x2_t s, t;
+  p_two_sum(ch, p, s, t);
+  f32x2_t lo = ::ssqcd::add2(cl, ::ssqcd::add2(e, t));
+  lo = ::ssqcd::fma2(uh, v.l, lo);
+  lo = ::ssqcd::fma2(ul, v.h, lo);
+  p_fast_two_sum(s, lo, ch, cl);
+}
+
 // Nearest float-float to an FP64 complex (hi = fl32(x), lo = fl32(x - hi);
 // x - hi is exact in FP64).
 __device__ __forceinline__ cff from_double2(double2 x) {

@@ -218,9 +218,15 @@ struct KrylovBasis {
 // the side stream, each source followed by its event, so that the
 // orthogonalisation of the first sources' moments overlaps the combination
 // of the last (scratch must then stay allocated until st has waited for
-// every event).
+// every event).  real_coef: the coefficients' points and weights come in
+// conjugate pairs, so the combined coefficients are real and only their
+// real parts are applied (half the FP64 work of complex coefficients).
 int basis_moments(const KrylovBasis& b, const double2* coef_host, int M, double2* s_hat, DevBuf& scratch,
-                  cudaStream_t st, cudaStream_t side = nullptr, const cudaEvent_t* src_ready = nullptr);
+                  cudaStream_t st, cudaStream_t side = nullptr, const cudaEvent_t* src_ready = nullptr,
+                  bool real_coef = false);
+// false when the environment sets SSQCD_REAL_MOMENTS=0 (complex coefficients
+// throughout, for comparison)
+bool real_moments_enabled();
 
 // Solves for L sources already packed on device (v: [L][12][V]); y out
 // [L][N][12][V] (device, FP64).  iters/xi: host arrays [L*N] (may be null).

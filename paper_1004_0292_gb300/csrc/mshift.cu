@@ -1514,29 +1514,41 @@ constexpr int kCombTile = 32;
 // threads, ~20 an SM, against 768 of 256 filling 2.5 waves of 2 an SM)
 constexpr int kCombThreads = 64;
 
-template <typename VR, typename VO, int OUT>
+// RC (real coefficients): only Re C is used, 2 FMA a term (Re and Im of the
+// residual times the real coefficient).  The moments of a contour whose
+// points and weights come in conjugate pairs (z, w), (conj z, conj w) have
+// real coefficients: the seed's CG scalars are real (Hermitian A, real seed
+// shift), so each shift's Krylov coefficients are rational functions of the
+// shift with real coefficients, the pair's coefficients are conjugate, and
+// the two terms of a pair sum to twice the real part.  Im C is then rounding
+// noise of the sum over the points and is dropped.
+template <typename VR, typename VO, int OUT, bool RC>
 __global__ void __launch_bounds__(kCombThreads, 2)
 basis_combine_kernel(char* const* __restrict__ tab, long long n, int L, const double2* __restrict__ C, int O, int S,
                      const int* __restrict__ count, VO* __restrict__ out, int l0) {
-  __shared__ double s_wr[kCombTile][OUT], s_wi[kCombTile][OUT], s_ws[kCombTile][OUT];
+  __shared__ double s_w[RC ? 1 : 3][kCombTile][OUT];
   __shared__ const VR* s_p[kCombTile];
   const int l = blockIdx.y + l0, o0 = blockIdx.z * OUT;
   const int no = min(OUT, O - o0);
   const int Sl = count[l];
   const long long e = blockIdx.x * (long long)kCombThreads + threadIdx.x;
   const long long Ln = (long long)L * n;
-  double a1[OUT], a2[OUT], a3[OUT];
+  double a1[OUT], a2[OUT], a3[RC ? 1 : OUT];
 #pragma unroll
-  for (int o = 0; o < OUT; ++o) a1[o] = a2[o] = a3[o] = 0.0;
+  for (int o = 0; o < OUT; ++o) a1[o] = a2[o] = 0.0;
+#pragma unroll
+  for (int o = 0; o < (RC ? 1 : OUT); ++o) a3[o] = 0.0;
   for (int s0 = 0; s0 < Sl; s0 += kCombTile) {
     const int ns = min(kCombTile, Sl - s0);
     __syncthreads();
     for (int t = threadIdx.x; t < kCombTile * OUT; t += kCombThreads) {
       const int ss = t / OUT, oo = t % OUT;
       const double2 c = (ss < ns && oo < no) ? C[((size_t)l * O + o0 + oo) * S + s0 + ss] : make_double2(0.0, 0.0);
-      s_wr[ss][oo] = c.x;
-      s_wi[ss][oo] = c.y;
-      s_ws[ss][oo] = c.x + c.y;
+      s_w[0][ss][oo] = c.x;
+      if (!RC) {
+        s_w[RC ? 0 : 1][ss][oo] = c.y;
+        s_w[RC ? 0 : 2][ss][oo] = c.x + c.y;
+      }
     }
     if (threadIdx.x < kCombTile) {
       const int s = s0 + threadIdx.x;
@@ -1549,12 +1561,20 @@ basis_combine_kernel(char* const* __restrict__ tab, long long n, int L, const do
 #pragma unroll 4
       for (int ss = 0; ss < ns; ++ss) {
         const double2 x = to_d2(s_p[ss][e]);
-        const double xs = x.x + x.y;
+        if (RC) {
 #pragma unroll
-        for (int o = 0; o < OUT; ++o) {
-          a1[o] = fma(s_wr[ss][o], x.x, a1[o]);
-          a2[o] = fma(s_wi[ss][o], x.y, a2[o]);
-          a3[o] = fma(s_ws[ss][o], xs, a3[o]);
+          for (int o = 0; o < OUT; ++o) {
+            a1[o] = fma(s_w[0][ss][o], x.x, a1[o]);
+            a2[o] = fma(s_w[0][ss][o], x.y, a2[o]);
+          }
+        } else {
+          const double xs = x.x + x.y;
+#pragma unroll
+          for (int o = 0; o < OUT; ++o) {
+            a1[o] = fma(s_w[0][ss][o], x.x, a1[o]);
+            a2[o] = fma(s_w[RC ? 0 : 1][ss][o], x.y, a2[o]);
+            a3[RC ? 0 : o] = fma(s_w[RC ? 0 : 2][ss][o], xs, a3[RC ? 0 : o]);
+          }
         }
       }
     }
@@ -1563,7 +1583,8 @@ basis_combine_kernel(char* const* __restrict__ tab, long long n, int L, const do
 #pragma unroll
     for (int o = 0; o < OUT; ++o)
       if (o < no)
-        put_out(out[((size_t)l * O + o0 + o) * n + e], make_double2(a1[o] - a2[o], (a3[o] - a1[o]) - a2[o]));
+        put_out(out[((size_t)l * O + o0 + o) * n + e],
+                RC ? make_double2(a1[o], a2[o]) : make_double2(a1[o] - a2[o], (a3[RC ? 0 : o] - a1[o]) - a2[o]));
   }
 }
 
@@ -1575,14 +1596,18 @@ basis_combine_kernel(char* const* __restrict__ tab, long long n, int L, const do
 // their magnitudes, against the residuals' own 2^-48).  The FP64 pipe only
 // sees the per-tile conversions.  The complex float-float multiply-adds run
 // on register pairs (real and imaginary part in one paired instruction,
-// floatfloat.cuh p_cfma), in the operation order of ff::cfma.
-template <int OUT>
+// floatfloat.cuh p_cfma), in the operation order of ff::cfma.  RC: real
+// coefficients (as in basis_combine_kernel), one float-float multiply-add a
+// part, both parts in one paired instruction (ff::p_rfma).
+template <int OUT, bool RC>
 __global__ void __launch_bounds__(kCombThreads, 2)
 basis_combine_df_kernel(char* const* __restrict__ tab, long long n, int L, const double2* __restrict__ C, int O, int S,
                         const int* __restrict__ count, double2* __restrict__ out, int l0) {
   // coefficients as the four register pairs of ff::p_cfma (real part in lane
-  // 0, imaginary part in lane 1: one paired instruction for both)
-  __shared__ ff::PCoef s_w[kCombTile][OUT];
+  // 0, imaginary part in lane 1: one paired instruction for both); RC: the
+  // pairs (hi, hi) and (lo, lo) of the real coefficient
+  __shared__ ff::PCoef s_w[RC ? 1 : kCombTile][OUT];
+  __shared__ f32x2_t s_rh[RC ? kCombTile : 1][OUT], s_rl[RC ? kCombTile : 1][OUT];
   __shared__ const float4* s_p[kCombTile];
   const int l = blockIdx.y + l0, o0 = blockIdx.z * OUT;
   const int no = min(OUT, O - o0);
@@ -1598,7 +1623,13 @@ basis_combine_df_kernel(char* const* __restrict__ tab, long long n, int L, const
     for (int t = threadIdx.x; t < kCombTile * OUT; t += kCombThreads) {
       const int ss = t / OUT, oo = t % OUT;
       const double2 c = (ss < ns && oo < no) ? C[((size_t)l * O + o0 + oo) * S + s0 + ss] : make_double2(0.0, 0.0);
-      s_w[ss][oo] = ff::p_coef(ff::from_double2(c));
+      if (RC) {
+        const float2 r = ff::split(c.x);
+        s_rh[RC ? ss : 0][oo] = pk2(r.x, r.x);
+        s_rl[RC ? ss : 0][oo] = pk2(r.y, r.y);
+      } else {
+        s_w[RC ? 0 : ss][oo] = ff::p_coef(ff::from_double2(c));
+      }
     }
     if (threadIdx.x < kCombTile) {
       const int s = s0 + threadIdx.x;
@@ -1614,8 +1645,13 @@ basis_combine_df_kernel(char* const* __restrict__ tab, long long n, int L, const
 #pragma unroll 2
       for (int ss = 0; ss < ns; ++ss) {
         const ff::PVal x = ff::p_val(s_p[ss][e]);
+        if (RC) {
 #pragma unroll
-        for (int o = 0; o < OUT; ++o) ff::p_cfma(ah[o], al[o], s_w[ss][o], x);
+          for (int o = 0; o < OUT; ++o) ff::p_rfma(ah[o], al[o], s_rh[RC ? ss : 0][o], s_rl[RC ? ss : 0][o], x);
+        } else {
+#pragma unroll
+          for (int o = 0; o < OUT; ++o) ff::p_cfma(ah[o], al[o], s_w[RC ? 0 : ss][o], x);
+        }
       }
 #pragma unroll
       for (int o = 0; o < OUT; ++o) {
@@ -1629,10 +1665,10 @@ basis_combine_df_kernel(char* const* __restrict__ tab, long long n, int L, const
     for (int o = 0; o < no; ++o) out[((size_t)l * O + o0 + o) * n + e] = accd[o];
 }
 
-// sources [l0, l0 + nl) of L (all by default)
+// sources [l0, l0 + nl) of L (all by default); rc: real coefficients
 template <typename VR, typename VO>
 int launch_combine(char* const* tab, long long n, int L, const double2* C, int O, int S, const int* count, VO* out,
-                   cudaStream_t st, int l0 = 0, int nl = -1) {
+                   cudaStream_t st, int l0 = 0, int nl = -1, bool rc = false) {
   if (nl < 0) nl = L - l0;
   // outputs a thread accumulates: 16 when there are at least 16 (a
   // 16-moment window reads the residuals once instead of twice, 48
@@ -1642,13 +1678,16 @@ int launch_combine(char* const* tab, long long n, int L, const double2* C, int O
     const char* e = std::getenv("SSQCD_COMB_OUT");
     return (e != nullptr && std::atoi(e) == 8) ? 8 : 16;
   }();
-  if (out_per_thread == 16 && O >= 16) {
-    const dim3 grid((unsigned)((n + kCombThreads - 1) / kCombThreads), nl, (O + 15) / 16);
-    basis_combine_kernel<VR, VO, 16><<<grid, kCombThreads, 0, st>>>(tab, n, L, C, O, S, count, out, l0);
-  } else {
-    const dim3 grid((unsigned)((n + kCombThreads - 1) / kCombThreads), nl, (O + kCombOut - 1) / kCombOut);
-    basis_combine_kernel<VR, VO, kCombOut><<<grid, kCombThreads, 0, st>>>(tab, n, L, C, O, S, count, out, l0);
-  }
+  const int per = (out_per_thread == 16 && O >= 16) ? 16 : kCombOut;
+  const dim3 grid((unsigned)((n + kCombThreads - 1) / kCombThreads), nl, (O + per - 1) / per);
+  if (per == 16 && rc)
+    basis_combine_kernel<VR, VO, 16, true><<<grid, kCombThreads, 0, st>>>(tab, n, L, C, O, S, count, out, l0);
+  else if (per == 16)
+    basis_combine_kernel<VR, VO, 16, false><<<grid, kCombThreads, 0, st>>>(tab, n, L, C, O, S, count, out, l0);
+  else if (rc)
+    basis_combine_kernel<VR, VO, kCombOut, true><<<grid, kCombThreads, 0, st>>>(tab, n, L, C, O, S, count, out, l0);
+  else
+    basis_combine_kernel<VR, VO, kCombOut, false><<<grid, kCombThreads, 0, st>>>(tab, n, L, C, O, S, count, out, l0);
   SS_CHECK_LAUNCH();
   count_launches(1);
   return SSQCD_OK;
@@ -2622,8 +2661,17 @@ void KrylovBasis::release() {
   S = 0;
 }
 
+bool real_moments_enabled() {
+  // SSQCD_REAL_MOMENTS=0 keeps the complex combination, for comparison
+  static const bool on = [] {
+    const char* e = std::getenv("SSQCD_REAL_MOMENTS");
+    return !(e != nullptr && std::atoi(e) == 0);
+  }();
+  return on;
+}
+
 int basis_moments(const KrylovBasis& b, const double2* coef_host, int M, double2* s_hat, DevBuf& scratch,
-                  cudaStream_t st, cudaStream_t side, const cudaEvent_t* src_ready) {
+                  cudaStream_t st, cudaStream_t side, const cudaEvent_t* src_ready, bool real_coef) {
   const int N = b.N, L = b.L, S = b.S;
   const size_t w_bytes = (sizeof(double2) * (size_t)N * M + 255) / 256 * 256;
   SS_TRY(scratch.alloc(w_bytes + sizeof(double2) * (size_t)L * M * S));
@@ -2634,6 +2682,7 @@ int basis_moments(const KrylovBasis& b, const double2* coef_host, int M, double2
   basis_window_kernel<<<(unsigned)((cnt + 255) / 256), 256, 0, st>>>(b.gam.as<double2>(), W, N, M, L, S, G);
   SS_CHECK_LAUNCH();
   count_launches(1);
+  const bool rc = real_coef && real_moments_enabled();
   auto one = [&](int l0, int nl, cudaStream_t s) -> int {
     if (b.df) {
       // outputs a thread accumulates: 8 (default) or 4 (SSQCD_COMB_DF_OUT=4:
@@ -2642,21 +2691,24 @@ int basis_moments(const KrylovBasis& b, const double2* coef_host, int M, double2
         const char* e = std::getenv("SSQCD_COMB_DF_OUT");
         return (e != nullptr && std::atoi(e) == 4) ? 4 : 8;
       }();
-      if (out_df == 4) {
-        const dim3 grid((unsigned)((b.n + kCombThreads - 1) / kCombThreads), nl, (M + 3) / 4);
-        basis_combine_df_kernel<4><<<grid, kCombThreads, 0, s>>>(b.tab.as<char*>(), b.n, L, G, M, S,
-                                                                 b.count.as<int>(), s_hat, l0);
-      } else {
-        const dim3 grid((unsigned)((b.n + kCombThreads - 1) / kCombThreads), nl, (M + 7) / 8);
-        basis_combine_df_kernel<8><<<grid, kCombThreads, 0, s>>>(b.tab.as<char*>(), b.n, L, G, M, S,
-                                                                 b.count.as<int>(), s_hat, l0);
-      }
+      const int per = out_df;
+      const dim3 grid((unsigned)((b.n + kCombThreads - 1) / kCombThreads), nl, (M + per - 1) / per);
+      char* const* tab = b.tab.as<char*>();
+      const int* count = b.count.as<int>();
+      if (per == 4 && rc)
+        basis_combine_df_kernel<4, true><<<grid, kCombThreads, 0, s>>>(tab, b.n, L, G, M, S, count, s_hat, l0);
+      else if (per == 4)
+        basis_combine_df_kernel<4, false><<<grid, kCombThreads, 0, s>>>(tab, b.n, L, G, M, S, count, s_hat, l0);
+      else if (rc)
+        basis_combine_df_kernel<8, true><<<grid, kCombThreads, 0, s>>>(tab, b.n, L, G, M, S, count, s_hat, l0);
+      else
+        basis_combine_df_kernel<8, false><<<grid, kCombThreads, 0, s>>>(tab, b.n, L, G, M, S, count, s_hat, l0);
       SS_CHECK_LAUNCH();
       count_launches(1);
       return SSQCD_OK;
     }
     return launch_combine<double2, double2>(b.tab.as<char*>(), b.n, L, G, M, S, b.count.as<int>(), s_hat, s, l0,
-                                            nl);
+                                            nl, rc);
   };
   if (side == nullptr || src_ready == nullptr || L == 1) return one(0, L, st);
   // sources 0 .. L-2 in one launch on st (the orthogonalisation of their

@@ -87,3 +87,31 @@ def test_a_frozen_shift_stops_contributing():
         assert np.all(c[j, Kj:] == 0)
         assert abs(c[j, Kj - 1]) > 0
     assert len(set(int(i) for i in out["iters"])) > 1  # the shifts freeze at different iterations
+
+
+def test_moment_coefficients_are_real_on_a_conjugate_closed_contour():
+    # The line pair of a real centre (Section 3) holds each point's conjugate,
+    # with the conjugate weight; the seed's CG scalars are real (Hermitian A,
+    # real seed shift), so the coefficient of r_s in s_hat_k is real and the
+    # moments are the real parts' combination.  Off the real axis (a complex
+    # centre) the coefficients are not real.
+    A, v, z, gamma, rho = _case()
+    M = 6
+    zeta = contour.normalise(z, gamma, rho)
+    w = contour.weights_closed_form(zeta)
+    out = shifted_cg.shifted_cg(A, v, z, tol=1e-12, history=True)
+    R = np.array(out["hist_r"])
+    c = _coefficients(out, len(z))
+    ref = omoments.moments(out["y"], w, zeta, M)
+    for k in range(M):
+        Gk = np.sum((w * zeta ** k)[:, None] * c, axis=0)
+        big = np.sum(np.abs((w * zeta ** k)[:, None] * c), axis=0)
+        assert np.all(np.abs(Gk.imag) <= 1e-13 * np.max(big))
+        s_k = np.tensordot(Gk.real, R, axes=1)
+        scale = np.sum(np.abs(w) * np.abs(zeta) ** k) * np.max(np.linalg.norm(out["y"].reshape(len(z), -1), axis=1))
+        assert np.linalg.norm(s_k - ref[k]) <= 1e-13 * scale
+    zc = z + 0.05j * rho
+    outc = shifted_cg.shifted_cg(A, v, zc, tol=1e-12, history=True)
+    cc = _coefficients(outc, len(zc))
+    Gc = np.sum((w * zeta ** 1)[:, None] * cc, axis=0)
+    assert np.max(np.abs(Gc.imag)) > 1e-3 * np.max(np.abs(Gc))
