@@ -10,13 +10,14 @@ Rayleigh-Ritz, acceptance, eigenpair readback):
   on the two sides of the spectral gap around zero, [-0.1095, -0.0765] and
   [0.0769, 0.1081], N = 32 points each (64 shifts in one seed recurrence,
   beta = 0.3, N' = 20); each window holds the two lowest eigenvalue
-  clusters of its sign, 48 eigenpairs in all.  The sources run in blocks of
-  two (opts.source_block) so that the stored seed residuals of a block fit
-  the device memory; FP64 throughout ("plain").
+  clusters of its sign, 48 eigenpairs in all.  The sources run one at a
+  time (opts.source_block = 1), two such runs side by side on their own
+  streams (opts.block_streams = 2), so that the stored seed residuals of the
+  two fit the device memory; FP64 throughout ("plain").
 
 ``value`` counts accepted eigenpairs with residual <= 1e-8 per second of
 device time (inputs resident, CUDA events on the library's stream; the
-stored residuals, 128 GB a block, are far larger than L2).  ``e2e`` is the
+stored residuals, 63 GB a source, are far larger than L2).  ``e2e`` is the
 same metric with host inputs (gauge field and sources copied in,
 eigenvectors copied out) timed on the host.  Under torchrun every rank
 solves an independent replica (its own sources): the path has no data
@@ -61,7 +62,7 @@ WORKLOAD = dict(
     name="16^3x32 smooth eps=0.5 kappa=0.135 L=8 M=16 two windows x N=32 (64 shifts) beta=0.3 FP64",
     dims=(16, 16, 16, 32), kappa=0.135, bc_t=-1, kind="smooth", gauge_seed=4, eps=0.5,
     L=8, src_seed=300, windows=((-0.1095, -0.0765), (0.0769, 0.1081)), N=32, M=16, beta=0.3, nprime=20,
-    tol=1e-12, source_block=2, basis_max_bytes=160e9,
+    tol=1e-12, source_block=1, block_streams=2, basis_max_bytes=160e9,
 )
 
 CONFIG2 = dict(
@@ -195,7 +196,8 @@ def make_inputs(rank=0, w=None):
 def windows_step(ss, lat, src, w, want_vectors=False):
     """One solve of the headline workload: (evals, residuals, stats[, evecs])."""
     res = ss.ss_solve_windows(lat, w["windows"], w["N"], w["M"], src, beta=w["beta"], nprime=w["nprime"],
-                              tol=w["tol"], source_block=w["source_block"], basis_max_bytes=w["basis_max_bytes"])
+                              tol=w["tol"], source_block=w["source_block"], basis_max_bytes=w["basis_max_bytes"],
+                              block_streams=w.get("block_streams", 1))
     if res.status != ss.OK:
         raise RuntimeError(f"solve failed with status {res.status}: {res.error}")
     ev, vec, rs, st = ss.ss_eigpairs(res, want_vectors=want_vectors)
@@ -260,8 +262,10 @@ def run_ours(args):
     # per-kernel device times: a separate step with the library's sampled
     # kernel timing on (its event nodes slow the loop a little, so they stay
     # out of the timed steps above)
+    # (one run at a time there, so that each kernel's events see only its own run)
+    w_kt = dict(w, block_streams=1)
     ss.set_kernel_timing(True)
-    _, _, stats, _ = timed_steps(step, flush, stream, KERNEL_TIMING_STEPS)
+    _, _, stats, _ = timed_steps(lambda: windows_step(ss, lat, src_d, w_kt), flush, stream, KERNEL_TIMING_STEPS)
     ss.set_kernel_timing(False)
 
     # ---- roofline of the dominant kernel: the FP64 moment combination ----
@@ -272,6 +276,8 @@ def run_ours(args):
     it_tot = sum(s["launches_update"] for s in stats)
     ms_sten = sum(s["ms_k_stencil"] for s in stats)
     Lb = w["source_block"]
+    # shifted-CG runs one after another: groups of block_streams runs of Lb sources side by side
+    n_groups = -(-w["L"] // (Lb * w.get("block_streams", 1)))
     sten_flops = it_tot * V * Lb * STENCIL_FLOP_PER_SITE
     sten_bytes = it_tot * V * (Lb * 2 * 192 + 576)
     sten_tf = sten_flops / (ms_sten / 1e3) / 1e12 if ms_sten > 0 else None
@@ -313,7 +319,8 @@ def run_ours(args):
         t_m, c_m, p_m, res_m = timed_steps(step_m, flush, stream, args.steps)
         r_m = [float(np.max(rs[rs <= RES_TOL])) if np.any(rs <= RES_TOL) else None for rs in res_m]
         ss.set_kernel_timing(True)
-        _, _, s_m, _ = timed_steps(step_m, flush, stream, KERNEL_TIMING_STEPS)
+        _, _, s_m, _ = timed_steps(lambda: windows_step(ss, lat_m, src_d, dict(w, block_streams=1)), flush, stream,
+                                   KERNEL_TIMING_STEPS)
         ss.set_kernel_timing(False)
         ms_m, pairs_m = reduce_job(float(sum(t_m)), float(sum(c_m)), world, "cuda")
         value_m = pairs_m / (ms_m / 1e3)
@@ -325,7 +332,7 @@ def run_ours(args):
             "vs_plain_fp64": value_m / value, "eigenpairs_per_step": c_m[-1],
             "max_accepted_residual": r_m[-1], "iterations_per_step": p_m[-1]["iterations"],
             "phase_ms": {"cg": p_m[-1]["ms_cg"], "moments": p_m[-1]["ms_moments"], "rr": p_m[-1]["ms_rr"]},
-            "cg_us_per_iteration": 1e3 * p_m[-1]["ms_cg"] / max(1, p_m[-1]["iterations"]) / (w["L"] // Lb),
+            "cg_us_per_iteration": 1e3 * p_m[-1]["ms_cg"] / max(1, p_m[-1]["iterations"]) / n_groups,
             "kernel_us_per_iteration": {"stencil": 1e3 * sum(x["ms_k_stencil"] for x in s_m) / it_m,
                                         "seed_update": 1e3 * sum(x["ms_k_seed"] for x in s_m) / it_m,
                                         "seed_direction": 1e3 * sum(x["ms_k_scalars"] for x in s_m) / it_m,
@@ -360,16 +367,18 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded smooth SU(3) links, Gaussian sources)",
             "config": {"workload": w["name"], "lattice": list(w["dims"]), "kappa": w["kappa"],
-                       "sources": w["L"], "source_block": w["source_block"], "windows": [list(x) for x in w["windows"]],
+                       "sources": w["L"], "source_block": w["source_block"],
+                       "block_streams": w.get("block_streams", 1), "windows": [list(x) for x in w["windows"]],
                        "quad_points_per_window": w["N"], "shifts": w["N"] * len(w["windows"]), "moments": w["M"],
                        "beta": w["beta"], "nprime": w["nprime"], "tol": w["tol"],
                        "parallelism": f"replicas x{world}",
-                       "l2": "inputs larger than L2 (stored residuals 128 GB per source block) and a 256 MB "
+                       "l2": "inputs larger than L2 (stored residuals 63 GB per source, two sources resident) and a 256 MB "
                              "flush write between steps"},
             "eigenpairs_per_step": counts[-1], "max_accepted_residual": r_p[-1],
             "iterations_per_step": last["iterations"],
             "latency_ms": {"p50": float(np.percentile(lat_sorted, 50)), "p99": float(np.percentile(lat_sorted, 99))},
             "phase_ms": {"cg": last["ms_cg"], "moments": last["ms_moments"], "rr": last["ms_rr"]},
+            "cg_us_per_iteration": 1e3 * last["ms_cg"] / max(1, last["iterations"]) / n_groups,
             "stored_residual_bytes_per_block": last["basis_bytes"],
             "roofline": {
                 "kernel": "basis_combine_kernel (moments from the stored seed residuals, FP64; the moments phase, "

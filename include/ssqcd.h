@@ -145,6 +145,14 @@ typedef struct {
                              the eigenvalue count); ssqcd_ss_eigpairs returns
                              every accepted pair with its residual, and
                              n_converged counts those at or below this bound */
+  int    block_streams;   /* with source blocks: how many blocks' shifted-CG runs
+                             proceed at once, each on its own stream (default
+                             1: one after another).  The runs share only the
+                             links, so the latency-bound seed kernels of one
+                             run fill the gaps of the other's stencil; the
+                             stored residuals of that many blocks are held at
+                             once (basis_max_bytes is split between them) and
+                             every source's arithmetic is unchanged        */
 } ssqcd_opts;
 
 /* Counters of one solve.  Times are device milliseconds between CUDA events. */

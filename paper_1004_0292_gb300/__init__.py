@@ -53,7 +53,7 @@ class Opts(C.Structure):
         ("sources", C.c_void_p), ("sources_on_device", C.c_int), ("reliable_every", C.c_int),
         ("windows", C.c_int), ("extract", C.c_int), ("hankel_tol", C.c_double), ("refine", C.c_int),
         ("basis", C.c_int), ("basis_max_bytes", C.c_double), ("source_block", C.c_int),
-        ("converged_tol", C.c_double),
+        ("converged_tol", C.c_double), ("block_streams", C.c_int),
     ]
 
 
@@ -308,7 +308,7 @@ def moments_noalloc(w, zeta, y, M, stream=None):
 
 
 def _solve_opts(lat, sources, beta, nprime, tol, sigma, max_iter, rank_tol, path, reliable_every, windows, extract,
-                hankel_tol, refine, basis, basis_max_bytes, source_block):
+                hankel_tol, refine, basis, basis_max_bytes, source_block, block_streams=1):
     L = int(np.prod(sources.shape)) // lat.n
     o = Opts()
     lib().ssqcd_default_opts(C.byref(o))
@@ -320,17 +320,19 @@ def _solve_opts(lat, sources, beta, nprime, tol, sigma, max_iter, rank_tol, path
     o.extract, o.hankel_tol, o.refine = int(extract), float(hankel_tol), int(refine)
     o.basis, o.basis_max_bytes = int(basis), float(basis_max_bytes)
     o.source_block = int(source_block)
+    o.block_streams = int(block_streams)
     return L, o, keep
 
 
 def ss_solve(lat: Lattice, interval, N, M, sources, beta=0.3, nprime=0, tol=1e-12, sigma=0.0, max_iter=100000,
              rank_tol=1e-14, path=PATH_LINES, reliable_every=0, windows=1, extract=0,
-             hankel_tol=1e-12, refine=0, basis=1, basis_max_bytes=0.0, source_block=0) -> Result:
+             hankel_tol=1e-12, refine=0, basis=1, basis_max_bytes=0.0, source_block=0, block_streams=1) -> Result:
     """Run the solver; returns a Result (check ``status``).  ``basis`` / ``basis_max_bytes``: moments
     from the stored seed residuals (FP64 and DF lattices; see ssqcd_opts); ``source_block``: sources
-    per shifted-CG run."""
+    per shifted-CG run; ``block_streams``: source blocks whose runs proceed at once."""
     L, o, keep = _solve_opts(lat, sources, beta, nprime, tol, sigma, max_iter, rank_tol, path, reliable_every,
-                             windows, extract, hankel_tol, refine, basis, basis_max_bytes, source_block)
+                             windows, extract, hankel_tol, refine, basis, basis_max_bytes, source_block,
+                             block_streams)
     iv = (C.c_double * 2)(float(interval[0]), float(interval[1]))
     h = C.c_void_p()
     code = lib().ssqcd_ss_solve(lat.handle, iv, int(N), int(M), L, C.byref(o), C.byref(h))
@@ -342,12 +344,12 @@ def ss_solve(lat: Lattice, interval, N, M, sources, beta=0.3, nprime=0, tol=1e-1
 
 def ss_solve_windows(lat: Lattice, intervals, N, M, sources, beta=0.3, nprime=0, tol=1e-12, sigma=0.0,
                      max_iter=100000, rank_tol=1e-14, path=PATH_LINES, extract=0, hankel_tol=1e-12, refine=0,
-                     basis=1, basis_max_bytes=0.0, source_block=0) -> Result:
+                     basis=1, basis_max_bytes=0.0, source_block=0, block_streams=1) -> Result:
     """Several windows [(a_k, b_k), ...] out of one shifted-CG run (ssqcd_ss_solve_windows)."""
     iv_list = [float(x) for ab in intervals for x in ab]
     K = len(iv_list) // 2
     L, o, keep = _solve_opts(lat, sources, beta, nprime, tol, sigma, max_iter, rank_tol, path, 0, 1, extract,
-                             hankel_tol, refine, basis, basis_max_bytes, source_block)
+                             hankel_tol, refine, basis, basis_max_bytes, source_block, block_streams)
     iv = (C.c_double * (2 * K))(*iv_list)
     h = C.c_void_p()
     code = lib().ssqcd_ss_solve_windows(lat.handle, K, iv, int(N), int(M), L, C.byref(o), C.byref(h))

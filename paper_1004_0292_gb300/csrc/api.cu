@@ -291,6 +291,7 @@ extern "C" void ssqcd_default_opts(ssqcd_opts* o) {
   o->basis_max_bytes = 0.0;
   o->source_block = 0;
   o->converged_tol = 1e-8;
+  o->block_streams = 1;
 }
 
 namespace {
@@ -330,6 +331,125 @@ int orthonormalise(const double2* S, int m, long long n, double rank_tol, DevBuf
 
 namespace {
 
+// Ritz values in [lo, hi] (hi_open: the upper end belongs to the next
+// window) out of theta.
+std::vector<int> accepted(const std::vector<double>& theta, double lo, double hi, bool hi_open) {
+  std::vector<int> acc;
+  for (int c = 0; c < (int)theta.size(); ++c)
+    if (theta[c] >= lo && (hi_open ? theta[c] < hi : theta[c] <= hi)) acc.push_back(c);
+  return acc;
+}
+
+// X (cnt vectors of n, device), A X and ||A x - theta x|| for the accepted
+// pairs; appends the eigenvalues and residuals.
+int finish_ritz(ssqcd_lattice lat, const double2* B, int nb, const std::vector<double2>& Cx,
+                const std::vector<double>& ev, std::vector<double>& evals, std::vector<double>& resid, DevBuf& X,
+                DevBuf& scratch, cudaStream_t st) {
+  const long long n = 12LL * lat->g.V;
+  const int cnt = (int)ev.size();
+  std::vector<double> rs(cnt);
+  DevBuf Wd, AX, th, rn;
+  SS_TRY(Wd.alloc(sizeof(double2) * nb * cnt));
+  SS_CUDA(cudaMemcpyAsync(Wd.p, Cx.data(), sizeof(double2) * nb * cnt, cudaMemcpyHostToDevice, st));
+  SS_TRY(X.alloc(sizeof(double2) * n * cnt));
+  SS_TRY(combine(B, nb, n, Wd.as<double2>(), cnt, X.as<double2>(), st));
+  SS_TRY(AX.alloc(sizeof(double2) * n * cnt));
+  SS_TRY(wilson64(lat->g, lat->u64.as<double2>(), X.as<double2>(), AX.as<double2>(), cnt, 0.0, 1.0, nullptr,
+                  nullptr, st));
+  SS_TRY(th.alloc(sizeof(double) * cnt));
+  SS_TRY(rn.alloc(sizeof(double) * cnt));
+  SS_CUDA(cudaMemcpyAsync(th.p, ev.data(), sizeof(double) * cnt, cudaMemcpyHostToDevice, st));
+  SS_TRY(col_residual_norms(AX.as<double2>(), X.as<double2>(), th.as<double>(), cnt, n, rn.as<double>(), scratch,
+                            st));
+  SS_CUDA(cudaMemcpyAsync(rs.data(), rn.p, sizeof(double) * cnt, cudaMemcpyDeviceToHost, st));
+  SS_CUDA(cudaStreamSynchronize(st));
+  evals.insert(evals.end(), ev.begin(), ev.end());
+  resid.insert(resid.end(), rs.begin(), rs.end());
+  return SSQCD_OK;
+}
+
+// Rayleigh-Ritz for one window with the projection kept implicit: the CGS2
+// basis T of S (m columns, orthonormal or zero, S = T R) is used as it is,
+// and the rank cut of the SVD R = U Sigma V^H enters only the small
+// matrices: with U_r the left singular vectors above rank_tol, the
+// orthonormal basis is T U_r, so (T U_r)^H A (T U_r) = U_r^H (T^H A T) U_r
+// and a Ritz vector is T U_r w.  The same Ritz pairs as forming T U_r first,
+// without that n x m x r combination; T^H A T is Hermitian, so only its
+// upper tiles are formed.
+int rayleigh_ritz_projected(ssqcd_lattice lat, const double2* S, int m, double rank_tol, double lo, double hi,
+                            bool hi_open, std::vector<double>& evals, std::vector<double>& resid, DevBuf& X,
+                            int& cnt, int& rank, DevBuf& scratch, cudaStream_t st, const cudaEvent_t* ready,
+                            int group) {
+  const long long n = 12LL * lat->g.V;
+  DevBuf T, AT, Gd, Rd;
+  SS_TRY(T.alloc(sizeof(double2) * n * m));
+  SS_TRY(Rd.alloc(sizeof(double2) * m * m));
+  SS_TRY(cgs2(S, m, n, T.as<double2>(), Rd.as<double2>(), scratch, st, ready, group));
+  std::vector<double2> R((size_t)m * m), U((size_t)m * m);
+  SS_CUDA(cudaMemcpyAsync(R.data(), Rd.p, sizeof(double2) * m * m, cudaMemcpyDeviceToHost, st));
+  SS_CUDA(cudaStreamSynchronize(st));
+  std::vector<double> sig(m);
+  SS_TRY(small_svd_left(m, R.data(), sig.data(), U.data()));
+  if (!(sig[0] > 0.0)) return fail(SSQCD_ERR_ARG, "moment block is zero");
+  int r = 0;
+  while (r < m && sig[r] > rank_tol * sig[0]) ++r;
+  rank = r;
+  SS_TRY(AT.alloc(sizeof(double2) * n * m));
+  SS_TRY(wilson64(lat->g, lat->u64.as<double2>(), T.as<double2>(), AT.as<double2>(), m, 0.0, 1.0, nullptr, nullptr,
+                  st));
+  SS_TRY(Gd.alloc(sizeof(double2) * m * m));
+  SS_TRY(gram(T.as<double2>(), m, AT.as<double2>(), m, n, Gd.as<double2>(), scratch, st, true));
+  std::vector<double2> G((size_t)m * m);
+  SS_CUDA(cudaMemcpyAsync(G.data(), Gd.p, sizeof(double2) * m * m, cudaMemcpyDeviceToHost, st));
+  SS_CUDA(cudaStreamSynchronize(st));
+  AT.release();
+  auto g_full = [&](int i, int j) {  // Hermitian T^H A T from its upper triangle
+    return i <= j ? G[(size_t)i * m + j] : make_double2(G[(size_t)j * m + i].x, -G[(size_t)j * m + i].y);
+  };
+  // GU = G U_r (m x r), then At = U_r^H GU (r x r; small_eigh reads the lower triangle)
+  std::vector<double2> GU((size_t)m * r), At((size_t)r * r), W((size_t)r * r);
+  for (int i = 0; i < m; ++i)
+    for (int c = 0; c < r; ++c) {
+      double re = 0.0, im = 0.0;
+      for (int j = 0; j < m; ++j) {
+        const double2 g = g_full(i, j), u = U[(size_t)j * m + c];
+        re += g.x * u.x - g.y * u.y;
+        im += g.x * u.y + g.y * u.x;
+      }
+      GU[(size_t)i * r + c] = make_double2(re, im);
+    }
+  for (int a = 0; a < r; ++a)
+    for (int c = 0; c <= a; ++c) {
+      double re = 0.0, im = 0.0;
+      for (int i = 0; i < m; ++i) {
+        const double2 u = U[(size_t)i * m + a], g = GU[(size_t)i * r + c];  // conj(u) g
+        re += u.x * g.x + u.y * g.y;
+        im += u.x * g.y - u.y * g.x;
+      }
+      At[(size_t)a * r + c] = make_double2(re, im);
+    }
+  std::vector<double> theta(r);
+  SS_TRY(small_eigh(r, At.data(), theta.data(), W.data()));
+  const std::vector<int> acc = accepted(theta, lo, hi, hi_open);
+  cnt = (int)acc.size();
+  if (cnt == 0) return SSQCD_OK;
+  // Ritz vectors T (U_r w): coefficients Cx = U_r W_acc (m x cnt)
+  std::vector<double2> Cx((size_t)m * cnt);
+  std::vector<double> ev(cnt);
+  for (int c = 0; c < cnt; ++c) ev[c] = theta[acc[c]];
+  for (int i = 0; i < m; ++i)
+    for (int c = 0; c < cnt; ++c) {
+      double re = 0.0, im = 0.0;
+      for (int k = 0; k < r; ++k) {
+        const double2 u = U[(size_t)i * m + k], w = W[(size_t)k * r + acc[c]];
+        re += u.x * w.x - u.y * w.y;
+        im += u.x * w.y + u.y * w.x;
+      }
+      Cx[(size_t)i * cnt + c] = make_double2(re, im);
+    }
+  return finish_ritz(lat, T.as<double2>(), m, Cx, ev, evals, resid, X, scratch, st);
+}
+
 // Rayleigh-Ritz for one window: orthonormal basis of S (m vectors), Ritz
 // pairs of A on it, acceptance of the Ritz values in [lo, hi] (hi_open: the
 // upper end belongs to the next window), eigenvectors X (device, [cnt][n]),
@@ -339,6 +459,9 @@ int rayleigh_ritz_window(ssqcd_lattice lat, const double2* S, int m, double rank
                          int& cnt, int& rank, DevBuf& scratch, cudaStream_t st, const cudaEvent_t* ready = nullptr,
                          int group = 0) {
   const long long n = 12LL * lat->g.V;
+  if (!refine)
+    return rayleigh_ritz_projected(lat, S, m, rank_tol, lo, hi, hi_open, evals, resid, X, cnt, rank, scratch, st,
+                                   ready, group);
   DevBuf Q, tmp, AQ, Gd;
   int r = 0;
   SS_TRY(orthonormalise(S, m, n, rank_tol, Q, r, tmp, scratch, st, ready, group));
@@ -839,7 +962,9 @@ int extract_eigenpairs(ssqcd_lattice lat, const SolvePlan& P, DevBuf& yd, Krylov
     if (Spre != nullptr) {
       S.release();
       S.swap((*Spre)[k]);  // window k's moments, freed with S
-      if (k == K - 1) cudaEventRecord(e1, st);
+      // every window's moments are formed already: the extraction of all
+      // of them is Rayleigh-Ritz time
+      if (k == 0) cudaEventRecord(e1, st);
     } else {
     SS_TRY(S.alloc(sizeof(double2) * n * m));
     if (overlap)
@@ -955,6 +1080,40 @@ void add_cg_stats(const ShiftedCGOut& b, ShiftedCGOut* acc) {
 // recurrences of different sources never interact), and each block's
 // moments of every window are formed before the next block starts, so the
 // stored seed residuals of only B sources are held at a time.
+// Drive several shifted-CG runs (each on its own stream) to the end
+// together: two chunks in flight per run, the runs polled in turn.  Returns
+// the first status other than OK (a run that breaks down or does not
+// converge ends; the others go on).
+int drive_runs(const std::vector<CgRunBase*>& runs) {
+  const int nr = (int)runs.size();
+  std::vector<char> done(nr, 0);
+  int first = SSQCD_OK, live = nr;
+  auto end_run = [&](int i, int status) {
+    done[i] = 1;
+    --live;
+    if (first == SSQCD_OK) first = status;
+  };
+  for (int i = 0; i < nr; ++i) {
+    int status = runs[i]->launch();
+    if (status == SSQCD_OK) status = runs[i]->launch();
+    if (status != SSQCD_OK) end_run(i, status);
+  }
+  while (live > 0) {
+    for (int i = 0; i < nr; ++i) {
+      if (done[i]) continue;
+      int state = 0;
+      int status = runs[i]->poll(true, &state);
+      if (status == SSQCD_OK && state == CgRunBase::kPollDone) {
+        end_run(i, SSQCD_OK);
+        continue;
+      }
+      if (status == SSQCD_OK) status = runs[i]->launch();
+      if (status != SSQCD_OK) end_run(i, status);
+    }
+  }
+  return first;
+}
+
 int run_solve(ssqcd_lattice lat, const SolvePlan& P, ssqcd_result* out) {
   const int L = P.L, NU = P.NU, K = P.K, MM = P.MM;
   const long long n = 12LL * lat->g.V;
@@ -1007,32 +1166,92 @@ int run_solve(ssqcd_lattice lat, const SolvePlan& P, ssqcd_result* out) {
   SS_CUDA(cudaEventCreate(&m0));
   SS_CUDA(cudaEventCreate(&m1));
   float ms_mom = 0.f;
-  for (int l0 = 0; l0 < L; l0 += B) {
-    const int Lb = std::min(B, L - l0);
-    ShiftedCGOut cgb;
-    DevBuf scratch;
-    s1 = shifted_cg_solve(lat, NU, P.zu.data(), Lb, vd.as<double2>() + (size_t)l0 * n, P.o.sigma, P.o.tol,
-                          P.o.max_iter, lat->precision, P.o.reliable_every,
-                          basis_cap_for(lat->precision, P.o.basis, P.o.basis_max_bytes, n, NU, Lb), yd, &kb,
-                          iters.data() + (size_t)l0 * NU, &cgb);
-    add_cg_stats(cgb, &cg);
+  // G blocks at a time (opts.block_streams), each shifted-CG run on its own
+  // stream: the runs share nothing but the links, so while one run's stencil
+  // fills the GPU the other's latency-bound seed kernels and grid reductions
+  // run beside it.  The stored residuals of all G runs are held at once
+  // (basis_max_bytes is split between them).
+  const int nblocks = (L + B - 1) / B;
+  const int G = std::max(1, std::min(P.o.block_streams, nblocks));
+  std::vector<cudaStream_t> streams(G, st);
+  std::vector<cudaEvent_t> evj(G, nullptr);
+  cudaEvent_t fork = nullptr, c0 = nullptr, c1 = nullptr;
+  struct StreamsEvs {
+    std::vector<cudaStream_t>* s;
+    std::vector<cudaEvent_t>* e;
+    cudaEvent_t* f[3];
+    ~StreamsEvs() {
+      for (size_t i = 1; i < s->size(); ++i)
+        if ((*s)[i]) cudaStreamDestroy((*s)[i]);
+      for (auto ev : *e)
+        if (ev) cudaEventDestroy(ev);
+      for (auto* ev : f)
+        if (*ev) cudaEventDestroy(*ev);
+    }
+  } sev{&streams, &evj, {&fork, &c0, &c1}};
+  for (int g = 1; g < G; ++g) {
+    streams[g] = nullptr;
+    SS_CUDA(cudaStreamCreateWithFlags(&streams[g], cudaStreamNonBlocking));
+  }
+  for (int g = 0; g < G; ++g) SS_CUDA(cudaEventCreateWithFlags(&evj[g], cudaEventDisableTiming));
+  SS_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+  SS_CUDA(cudaEventCreate(&c0));
+  SS_CUDA(cudaEventCreate(&c1));
+  for (int b0 = 0; b0 < nblocks; b0 += G) {
+    const int gn = std::min(G, nblocks - b0);
+    std::vector<std::unique_ptr<CgRunBase>> runs(gn);
+    std::vector<DevBuf> ys(gn);
+    std::vector<KrylovBasis> kbs(gn);
+    SS_CUDA(cudaEventRecord(c0, st));
+    SS_CUDA(cudaEventRecord(fork, st));  // the sources are on st
+    for (int g = 0; g < gn; ++g) {
+      const int l0 = (b0 + g) * B, Lb = std::min(B, L - l0);
+      if (streams[g] != st) SS_CUDA(cudaStreamWaitEvent(streams[g], fork, 0));
+      const double cap = basis_cap_for(lat->precision, P.o.basis, P.o.basis_max_bytes, n, NU, Lb) / gn;
+      SS_TRY(make_cg_run(lat, NU, P.zu.data(), Lb, vd.as<double2>() + (size_t)l0 * n, P.o.sigma, P.o.tol,
+                         P.o.max_iter, lat->precision, P.o.reliable_every, cap, streams[g], &runs[g]));
+    }
+    std::vector<CgRunBase*> rp(gn);
+    for (int g = 0; g < gn; ++g) rp[g] = runs[g].get();
+    s1 = drive_runs(rp);
+    if (s1 != SSQCD_OK && s1 != SSQCD_ERR_BREAKDOWN && s1 != SSQCD_ERR_NOCONV) return s1;
+    const double ms_before = cg.ms;
+    for (int g = 0; g < gn; ++g) {
+      const int l0 = (b0 + g) * B;
+      ShiftedCGOut cgb;
+      SS_TRY(runs[g]->finish(ys[g], iters.data() + (size_t)l0 * NU, nullptr, &cgb));
+      runs[g]->take_basis(&kbs[g]);
+      add_cg_stats(cgb, &cg);
+      SS_CUDA(cudaEventRecord(evj[g], streams[g]));
+      SS_CUDA(cudaStreamWaitEvent(st, evj[g], 0));
+    }
+    SS_CUDA(cudaEventRecord(c1, st));
+    SS_CUDA(cudaEventSynchronize(c1));
+    if (gn > 1) {  // the runs overlap: the group's span, not the sum of the runs' times
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, c0, c1);
+      cg.ms = ms_before + ms;
+    }
     fill_cg_stats(cg, iters, &res->stats, P.real_moments);
     if (s1 != SSQCD_OK) return s1;
+    runs.clear();
+    DevBuf scratch;
     SS_CUDA(cudaEventRecord(m0, st));
-    for (int k = 0; k < K; ++k) {
-      double2* dst = Sk[k].as<double2>() + (size_t)l0 * MM * n;
-      if (kb.S > 0)
-        SS_TRY(basis_moments(kb, P.coefk[k].data(), MM, dst, scratch, st, nullptr, nullptr, P.real_moments));
-      else
-        SS_TRY(moments_device(yd.as<double2>(), NU, MM, Lb, n, P.coefk[k].data(), dst, scratch, st));
+    for (int g = 0; g < gn; ++g) {
+      const int l0 = (b0 + g) * B, Lb = std::min(B, L - l0);
+      for (int k = 0; k < K; ++k) {
+        double2* dst = Sk[k].as<double2>() + (size_t)l0 * MM * n;
+        if (kbs[g].S > 0)
+          SS_TRY(basis_moments(kbs[g], P.coefk[k].data(), MM, dst, scratch, st, nullptr, nullptr, P.real_moments));
+        else
+          SS_TRY(moments_device(ys[g].as<double2>(), NU, MM, Lb, n, P.coefk[k].data(), dst, scratch, st));
+      }
     }
     SS_CUDA(cudaEventRecord(m1, st));
     SS_CUDA(cudaEventSynchronize(m1));
     float ms = 0.f;
     cudaEventElapsedTime(&ms, m0, m1);
     ms_mom += ms;
-    yd.release();
-    kb.release();
   }
   if (!P.hankel) vd.release();
   s1 = extract_eigenpairs(lat, P, yd, kb, vd, res, st, &Sk);

@@ -101,9 +101,11 @@ constexpr int kGE = 32;     // elements per shared-memory stage
 
 __global__ void __launch_bounds__(256)
 gram_partial_kernel(const double2* __restrict__ X, int mx, const double2* __restrict__ Y, int my, long long n,
-                    long long chunk, double2* __restrict__ partial) {
+                    long long chunk, double2* __restrict__ partial, int herm) {
   __shared__ double2 sx[kGE][kGT + 1];
   __shared__ double2 sy[kGE][kGT + 1];
+  // herm: G is Hermitian, only the tiles on and above the diagonal
+  if (herm && blockIdx.x > blockIdx.y) return;
   const int a0 = blockIdx.x * kGT, b0 = blockIdx.y * kGT;
   const int split = blockIdx.z;
   const long long e_begin = split * chunk;
@@ -151,11 +153,15 @@ gram_partial_kernel(const double2* __restrict__ X, int mx, const double2* __rest
     }
 }
 
-__global__ void gram_reduce_kernel(const double2* __restrict__ partial, int nsplit, int count,
+__global__ void gram_reduce_kernel(const double2* __restrict__ partial, int nsplit, int count, int my, int herm,
                                    double2* __restrict__ G) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= count) return;
   double2 acc = make_double2(0.0, 0.0);
+  if (herm && (i / my) / kGT > (i % my) / kGT) {  // a tile below the diagonal: not computed
+    G[i] = acc;
+    return;
+  }
   for (int sp = 0; sp < nsplit; ++sp) {
     const double2 v = partial[(long long)sp * count + i];
     acc.x += v.x;
@@ -264,18 +270,20 @@ __global__ void f32_to_f64_kernel(const float2* __restrict__ in, double2* __rest
 //              registers) and ||u||^2; the last block forms nu_j^2 first
 // and kStart gives column 0's norm; a column whose norm fell below 1e-15 of
 // its original is dependent: Q_j = 0, R[j][j] = 0 and c_j = 0 from then on.
-// Per thread: one element (the grid covers n); the projections in tiles of
-// kPT columns, reduced by halving warp exchanges and one pass over the warps.
+// Per thread: kCE elements, kCE x kPT loads in flight (the grid covers n);
+// the projections in tiles of kPT columns, each tile's 2 kPT sums over the
+// thread's elements reduced by halving warp exchanges and one pass over the
+// warps, so the reduction's FP64 additions are spread over kCE elements
+// (one element a thread spent ~2 additions a column and element on them,
+// against 8 FP64 operations of projection).
 enum CgsMode : int { kStart = 0, kSubProj = 1, kSubNext = 2, kFinal = 3 };
 
-// Warp sums of 16 values at once by halving exchanges: at the step with
-// offset O a lane keeps one half of its values and adds the partner's copy of
-// that half, so the four steps take 8 + 4 + 2 + 1 additions and one more
-// pairs the lanes: 16 FP64 additions a lane instead of 16 x 5 for separate
-// shuffle trees (FP64 issues at 1/64 of the FP32 rate here).  On return lane
-// L holds the warp total of value (L >> 1) & 15.
+// Warp sums of 8 values at once by halving exchanges: at the step with offset
+// O a lane keeps one half of its values and adds the partner's copy of that
+// half (4 + 2 + 1 additions), then two exchanges over the low lane bits.  On
+// return lane L holds the warp total of value (L >> 2) & 7.
 template <int O, int HALF>
-__device__ __forceinline__ void halve_step(double (&v)[16], int lane) {
+__device__ __forceinline__ void halve_step8(double (&v)[8], int lane) {
   const bool up = (lane & O) != 0;
 #pragma unroll
   for (int i = 0; i < HALF; ++i) {
@@ -284,15 +292,16 @@ __device__ __forceinline__ void halve_step(double (&v)[16], int lane) {
     v[i] = keep + __shfl_xor_sync(0xffffffffu, send, O);
   }
 }
-__device__ __forceinline__ double warp_reduce16(double (&v)[16]) {
+__device__ __forceinline__ double warp_reduce8(double (&v)[8]) {
   const int lane = threadIdx.x & 31;
-  halve_step<16, 8>(v, lane);
-  halve_step<8, 4>(v, lane);
-  halve_step<4, 2>(v, lane);
-  halve_step<2, 1>(v, lane);
-  return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+  halve_step8<16, 4>(v, lane);
+  halve_step8<8, 2>(v, lane);
+  halve_step8<4, 1>(v, lane);
+  double t = v[0] + __shfl_xor_sync(0xffffffffu, v[0], 2);
+  return t + __shfl_xor_sync(0xffffffffu, t, 1);
 }
-constexpr int kPT = 8;
+constexpr int kPT = 4;
+constexpr int kCE = 4;
 constexpr int kCgsMaxCols = 128;
 
 struct CgsState {
@@ -314,60 +323,85 @@ cgs2_step_kernel(CgsState st, double2* __restrict__ Q, long long n, int m, int j
   __shared__ bool s_last;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int nb = gridDim.x;
-  const long long e = blockIdx.x * (long long)kRedBlock + threadIdx.x;
-  const bool in = e < n;
+  long long ei[kCE];
+  bool in[kCE];
+#pragma unroll
+  for (int i = 0; i < kCE; ++i) {
+    ei[i] = blockIdx.x * (long long)(kRedBlock * kCE) + i * kRedBlock + threadIdx.x;
+    in[i] = ei[i] < n;
+  }
   if (mode == kFinal) {  // Q_a = v_a / nu_a for every column
-    for (int a = 0; a < m; ++a)
-      if (in) {
-        const double s = st.inv_nu[a];
-        double2 x = Q[(long long)a * n + e];
-        Q[(long long)a * n + e] = make_double2(x.x * s, x.y * s);
-      }
+    for (int a = 0; a < m; ++a) {
+      const double s = st.inv_nu[a];
+#pragma unroll
+      for (int i = 0; i < kCE; ++i)
+        if (in[i]) {
+          double2 x = Q[(long long)a * n + ei[i]];
+          Q[(long long)a * n + ei[i]] = make_double2(x.x * s, x.y * s);
+        }
+    }
     return;
   }
-  // 1. the subtraction w -= sum_a v_a c_a on column j (kPT loads in flight)
-  double2 x = make_double2(0.0, 0.0);
-  if (in) x = Q[(long long)j * n + e];
+  // 1. the subtraction w -= sum_a v_a c_a on column j
+  double2 x[kCE];
+#pragma unroll
+  for (int i = 0; i < kCE; ++i) x[i] = in[i] ? Q[(long long)j * n + ei[i]] : make_double2(0.0, 0.0);
   if (mode == kSubProj || mode == kSubNext) {
     for (int a = threadIdx.x; a < j; a += kRedBlock) s_c[a] = st.c[a];
     __syncthreads();
-    if (in) {
-      for (int a0 = 0; a0 < j; a0 += kPT) {
-        double2 q[kPT];
+    for (int a0 = 0; a0 < j; a0 += kPT) {
+      double2 q[kPT][kCE];
 #pragma unroll
-        for (int c = 0; c < kPT; ++c) q[c] = a0 + c < j ? Q[(long long)(a0 + c) * n + e] : make_double2(0.0, 0.0);
+      for (int c = 0; c < kPT; ++c)
 #pragma unroll
-        for (int c = 0; c < kPT; ++c) {
-          if (a0 + c < j) {
-            const double2 h = s_c[a0 + c];
-            x.x -= q[c].x * h.x - q[c].y * h.y;
-            x.y -= q[c].x * h.y + q[c].y * h.x;
+        for (int i = 0; i < kCE; ++i)
+          q[c][i] = (a0 + c < j && in[i]) ? Q[(long long)(a0 + c) * n + ei[i]] : make_double2(0.0, 0.0);
+#pragma unroll
+      for (int c = 0; c < kPT; ++c) {
+        if (a0 + c < j) {
+          const double2 h = s_c[a0 + c];
+#pragma unroll
+          for (int i = 0; i < kCE; ++i) {
+            x[i].x -= q[c][i].x * h.x - q[c][i].y * h.y;
+            x[i].y -= q[c][i].x * h.y + q[c][i].y * h.x;
           }
         }
       }
-      Q[(long long)j * n + e] = x;
     }
+#pragma unroll
+    for (int i = 0; i < kCE; ++i)
+      if (in[i]) Q[(long long)j * n + ei[i]] = x[i];
   }
   // 2. partials: projections of column jp on its first np columns, norms
   const int jp = mode == kSubNext ? j + 1 : j;
   const bool next = mode == kSubNext && jp < m;
   const int np = mode == kSubProj ? j : (next ? jp : 0);
-  double2 y = x;  // the vector being projected
-  if (next) y = in ? Q[(long long)jp * n + e] : make_double2(0.0, 0.0);
+  double2 y[kCE];  // the vector being projected
+#pragma unroll
+  for (int i = 0; i < kCE; ++i) y[i] = next ? (in[i] ? Q[(long long)jp * n + ei[i]] : make_double2(0.0, 0.0)) : x[i];
   for (int a0 = 0; a0 < np; a0 += kPT) {
-    double acc[2 * kPT];  // re, im of conj(v_a) y for kPT columns
+    double2 q[kPT][kCE];
 #pragma unroll
     for (int c = 0; c < kPT; ++c) {
-      acc[2 * c] = acc[2 * c + 1] = 0.0;
       const int a = a0 + c;
-      if (in && a < np) {
-        const double2 q = (next && a == j) ? x : Q[(long long)a * n + e];
-        acc[2 * c] = fma(q.x, y.x, q.y * y.y);
-        acc[2 * c + 1] = fma(q.x, y.y, -q.y * y.x);
-      }
+#pragma unroll
+      for (int i = 0; i < kCE; ++i)
+        q[c][i] = (a < np && in[i]) ? ((next && a == j) ? x[i] : Q[(long long)a * n + ei[i]]) : make_double2(0.0, 0.0);
     }
-    const double t = warp_reduce16(acc);
-    if ((lane & 1) == 0) s_red[w][lane >> 1] = t;
+    double acc[2 * kPT];  // re, im of sum over the thread's elements of conj(v_a) y
+#pragma unroll
+    for (int c = 0; c < kPT; ++c) {
+      double re = 0.0, im = 0.0;
+#pragma unroll
+      for (int i = 0; i < kCE; ++i) {
+        re = fma(q[c][i].x, y[i].x, fma(q[c][i].y, y[i].y, re));
+        im = fma(q[c][i].x, y[i].y, fma(-q[c][i].y, y[i].x, im));
+      }
+      acc[2 * c] = re;
+      acc[2 * c + 1] = im;
+    }
+    const double t = warp_reduce8(acc);
+    if ((lane & 3) == 0) s_red[w][lane >> 2] = t;
     __syncthreads();
     if (threadIdx.x < 2 * kPT && a0 + (int)threadIdx.x / 2 < np) {
       double u = s_red[0][threadIdx.x];
@@ -381,8 +415,12 @@ cgs2_step_kernel(CgsState st, double2* __restrict__ Q, long long n, int m, int j
   // column: also ||u||^2
   const bool norm_w = mode == kStart || mode == kSubNext;
   if (norm_w || next) {
-    double v0 = in ? fma(x.x, x.x, x.y * x.y) : 0.0;
-    double v1 = (next && in) ? fma(y.x, y.x, y.y * y.y) : 0.0;
+    double v0 = 0.0, v1 = 0.0;
+#pragma unroll
+    for (int i = 0; i < kCE; ++i) {
+      v0 = fma(x[i].x, x[i].x, fma(x[i].y, x[i].y, v0));
+      if (next) v1 = fma(y[i].x, y[i].x, fma(y[i].y, y[i].y, v1));
+    }
     v0 = warp_sum(v0);
     v1 = warp_sum(v1);
     if (lane == 0) {
@@ -438,9 +476,9 @@ cgs2_step_kernel(CgsState st, double2* __restrict__ Q, long long n, int m, int j
         }
       }
     }
-    const double t = warp_reduce16(acc);
-    const int a = a0 + (lane >> 2), comp = (lane >> 1) & 1;
-    if ((lane & 1) == 0 && a < np) {
+    const double t = warp_reduce8(acc);
+    const int a = a0 + (lane >> 3), comp = (lane >> 2) & 1;
+    if ((lane & 3) == 0 && a < np) {
       // v_a^H y: subtraction coefficient / nu_a^2, R entry / nu_a
       const double i2 = __ldcg(st.inv_nu2 + a), i1 = __ldcg(st.inv_nu + a);
       reinterpret_cast<double*>(st.c)[2 * a + comp] = t * i2;
@@ -499,11 +537,13 @@ int sum_partials(const double* partial, int nvec, int nblocks, double* out, cuda
 }
 
 int gram(const double2* X, int mx, const double2* Y, int my, long long n, double2* G, DevBuf& scratch,
-         cudaStream_t s) {
+         cudaStream_t s, bool herm) {
   if (mx <= 0 || my <= 0) return SSQCD_OK;
+  if (herm && mx != my) return fail(SSQCD_ERR_ARG, "gram: a Hermitian product needs mx == my");
   const int ta = (mx + kGT - 1) / kGT, tb = (my + kGT - 1) / kGT;
+  const int tiles = herm ? ta * (ta + 1) / 2 : ta * tb;
   // enough splits to give every SM a few blocks
-  long long nsplit = (4LL * 152 + ta * tb - 1) / (ta * tb);
+  long long nsplit = (4LL * 152 + tiles - 1) / tiles;
   const long long min_chunk = 256;
   if (nsplit * min_chunk > n) nsplit = (n + min_chunk - 1) / min_chunk;
   if (nsplit < 1) nsplit = 1;
@@ -512,10 +552,11 @@ int gram(const double2* X, int mx, const double2* Y, int my, long long n, double
   nsplit = (n + chunk - 1) / chunk;
   SS_TRY(scratch.alloc(sizeof(double2) * nsplit * mx * my));
   gram_partial_kernel<<<dim3(ta, tb, (unsigned)nsplit), 256, 0, s>>>(X, mx, Y, my, n, chunk,
-                                                                      scratch.as<double2>());
+                                                                      scratch.as<double2>(), herm ? 1 : 0);
   SS_CHECK_LAUNCH();
   const int count = mx * my;
-  gram_reduce_kernel<<<grid_for(count, 256), 256, 0, s>>>(scratch.as<double2>(), (int)nsplit, count, G);
+  gram_reduce_kernel<<<grid_for(count, 256), 256, 0, s>>>(scratch.as<double2>(), (int)nsplit, count, my,
+                                                           herm ? 1 : 0, G);
   count_launches(2);
   SS_CHECK_LAUNCH();
   return SSQCD_OK;
@@ -526,7 +567,7 @@ int cgs2(const double2* S, int m, long long n, double2* Q, double2* R, DevBuf& s
          const cudaEvent_t* group_ready, int group) {
   if (m > kCgsMaxCols) return fail(SSQCD_ERR_ARG, "CGS2 of more than 128 columns");
   if (m <= 0 || n <= 0) return SSQCD_OK;
-  const long long nbl = (n + kRedBlock - 1) / kRedBlock;  // one element per thread
+  const long long nbl = (n + kRedBlock * kCE - 1) / (kRedBlock * kCE);  // kCE elements a thread
   if (nbl > (1LL << 30)) return fail(SSQCD_ERR_ARG, "CGS2 vectors too long");
   const int nb = (int)nbl;
   const size_t o_part = 0, o_np = o_part + sizeof(double2) * (size_t)kCgsMaxCols * nb,

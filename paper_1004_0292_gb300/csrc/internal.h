@@ -153,8 +153,12 @@ int pack_gauge32(const double2* u64dev, void* u32, int V, cudaStream_t s);
 // reductions / dense block ops in FP64 (blas.cu)
 int norm2_partials(const double2* x, int nvec, long long n, double* partial, int nblocks, cudaStream_t s);
 int sum_partials(const double* partial, int nvec, int nblocks, double* out, cudaStream_t s);
+// G = X^H Y (mx x my row-major, device).  herm: X^H Y is Hermitian (mx ==
+// my, e.g. Q^H A Q): only the 32 x 32 tiles on and above the diagonal are
+// formed, the others are left zero (the upper triangle is always complete)
 int gram(const double2* X, int mx, const double2* Y, int my, long long n, double2* G, DevBuf& scratch,
-         cudaStream_t s);
+         cudaStream_t s, bool herm = false);
+// Q[c] = sum_a S[a] C[a][c] (C ms x mc row-major, device)
 int combine(const double2* S, int ms, long long n, const double2* C, int mc, double2* Q, cudaStream_t s);
 // CGS2 QR of the m vectors S (device): Q [m][n] with orthonormal (or zero)
 // vectors and R (m x m row-major, device, upper triangular), S = Q R.

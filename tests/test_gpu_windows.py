@@ -96,6 +96,14 @@ def test_window_list_one_seed_run_matches_separate_windows(setup):
     assert len(eb) == 16
     assert np.max(np.abs(eb - ev) / np.abs(ev)) <= 1e-11
     assert np.max(rb) <= 1e-8
+    # the blocks' runs side by side on their own streams (block_streams):
+    # every source's arithmetic is the same, so the result is bit-identical
+    for bs in (2, 3):
+        res_s = ss.ss_solve_windows(lat, wins, N, M, src, beta=0.3, nprime=Np, source_block=1, block_streams=bs)
+        assert res_s.status == ss.OK, res_s.error
+        es, _, rss, sts = ss.ss_eigpairs(res_s, want_vectors=False)
+        assert np.array_equal(es, eb) and np.array_equal(rss, rb)
+        assert sts["iterations"] == stb["iterations"]
 
 
 def test_window_list_rejects_bad_intervals(setup):
