@@ -340,19 +340,14 @@ std::vector<int> accepted(const std::vector<double>& theta, double lo, double hi
   return acc;
 }
 
-// X (cnt vectors of n, device), A X and ||A x - theta x|| for the accepted
-// pairs; appends the eigenvalues and residuals.
-int finish_ritz(ssqcd_lattice lat, const double2* B, int nb, const std::vector<double2>& Cx,
-                const std::vector<double>& ev, std::vector<double>& evals, std::vector<double>& resid, DevBuf& X,
-                DevBuf& scratch, cudaStream_t st) {
+// A X and ||A x - theta x|| for the accepted pairs, X (cnt vectors of n,
+// device, FP64) formed by the caller; appends the eigenvalues and residuals.
+int finish_ritz(ssqcd_lattice lat, const DevBuf& X, const std::vector<double>& ev, std::vector<double>& evals,
+                std::vector<double>& resid, DevBuf& scratch, cudaStream_t st) {
   const long long n = 12LL * lat->g.V;
   const int cnt = (int)ev.size();
   std::vector<double> rs(cnt);
-  DevBuf Wd, AX, th, rn;
-  SS_TRY(Wd.alloc(sizeof(double2) * nb * cnt));
-  SS_CUDA(cudaMemcpyAsync(Wd.p, Cx.data(), sizeof(double2) * nb * cnt, cudaMemcpyHostToDevice, st));
-  SS_TRY(X.alloc(sizeof(double2) * n * cnt));
-  SS_TRY(combine(B, nb, n, Wd.as<double2>(), cnt, X.as<double2>(), st));
+  DevBuf AX, th, rn;
   SS_TRY(AX.alloc(sizeof(double2) * n * cnt));
   SS_TRY(wilson64(lat->g, lat->u64.as<double2>(), X.as<double2>(), AX.as<double2>(), cnt, 0.0, 1.0, nullptr,
                   nullptr, st));
@@ -381,25 +376,46 @@ int rayleigh_ritz_projected(ssqcd_lattice lat, const double2* S, int m, double r
                             int& cnt, int& rank, DevBuf& scratch, cudaStream_t st, const cudaEvent_t* ready,
                             int group) {
   const long long n = 12LL * lat->g.V;
-  DevBuf T, AT, Gd, Rd;
-  SS_TRY(T.alloc(sizeof(double2) * n * m));
+  // SSQCD_DF solves: the basis, A T and the products in float-float on the
+  // FP32 pipes (blas_df.cu); the eigenvectors and their residuals in FP64
+  const bool df = lat->precision == SSQCD_DF;
+  DevBuf T, AT, Gd, Rd, gs;
+  SS_TRY(T.alloc(sizeof(double2) * n * m));  // a float-float element takes 16 B too
   SS_TRY(Rd.alloc(sizeof(double2) * m * m));
-  SS_TRY(cgs2(S, m, n, T.as<double2>(), Rd.as<double2>(), scratch, st, ready, group));
-  std::vector<double2> R((size_t)m * m), U((size_t)m * m);
+  if (df) {
+    if (ready != nullptr && group > 0)  // the conversion reads every column
+      for (int g = 0; g * group < m; ++g)
+        if (ready[g] != nullptr) SS_CUDA(cudaStreamWaitEvent(st, ready[g], 0));
+    DevBuf Sdf;
+    SS_TRY(Sdf.alloc(sizeof(float4) * n * m));
+    SS_TRY(convert_f64_to_df(S, Sdf.as<float4>(), n * m, st));
+    SS_TRY(cgs2_df(Sdf.as<float4>(), m, n, T.as<float4>(), Rd.as<double2>(), scratch, st));
+  } else {
+    SS_TRY(cgs2(S, m, n, T.as<double2>(), Rd.as<double2>(), scratch, st, ready, group));
+  }
+  std::vector<double2> R((size_t)m * m), U((size_t)m * m), G((size_t)m * m);
   SS_CUDA(cudaMemcpyAsync(R.data(), Rd.p, sizeof(double2) * m * m, cudaMemcpyDeviceToHost, st));
-  SS_CUDA(cudaStreamSynchronize(st));
+  // A T and T^H A T do not depend on the rank cut: they run on the device
+  // while the host takes the SVD of R
+  SS_TRY(AT.alloc(sizeof(double2) * n * m));
+  SS_TRY(Gd.alloc(sizeof(double2) * m * m));
+  if (df) {
+    SS_TRY(ensure_df_links(lat));
+    SS_TRY(wilson_df(lat->g, lat->udf.as<float4>(), T.as<float4>(), AT.as<float4>(), m, 0.0, 1.0, st));
+    SS_TRY(gram_df(T.as<float4>(), m, AT.as<float4>(), m, n, Gd.as<double2>(), gs, st, true));
+  } else {
+    SS_TRY(wilson64(lat->g, lat->u64.as<double2>(), T.as<double2>(), AT.as<double2>(), m, 0.0, 1.0, nullptr,
+                    nullptr, st));
+    SS_TRY(gram(T.as<double2>(), m, AT.as<double2>(), m, n, Gd.as<double2>(), gs, st, true));
+  }
+  // (a copy to pageable host memory returns when it is complete: R is
+  // here, and G is read after the SVD)
   std::vector<double> sig(m);
   SS_TRY(small_svd_left(m, R.data(), sig.data(), U.data()));
   if (!(sig[0] > 0.0)) return fail(SSQCD_ERR_ARG, "moment block is zero");
   int r = 0;
   while (r < m && sig[r] > rank_tol * sig[0]) ++r;
   rank = r;
-  SS_TRY(AT.alloc(sizeof(double2) * n * m));
-  SS_TRY(wilson64(lat->g, lat->u64.as<double2>(), T.as<double2>(), AT.as<double2>(), m, 0.0, 1.0, nullptr, nullptr,
-                  st));
-  SS_TRY(Gd.alloc(sizeof(double2) * m * m));
-  SS_TRY(gram(T.as<double2>(), m, AT.as<double2>(), m, n, Gd.as<double2>(), scratch, st, true));
-  std::vector<double2> G((size_t)m * m);
   SS_CUDA(cudaMemcpyAsync(G.data(), Gd.p, sizeof(double2) * m * m, cudaMemcpyDeviceToHost, st));
   SS_CUDA(cudaStreamSynchronize(st));
   AT.release();
@@ -447,7 +463,15 @@ int rayleigh_ritz_projected(ssqcd_lattice lat, const double2* S, int m, double r
       }
       Cx[(size_t)i * cnt + c] = make_double2(re, im);
     }
-  return finish_ritz(lat, T.as<double2>(), m, Cx, ev, evals, resid, X, scratch, st);
+  DevBuf Wd;
+  SS_TRY(Wd.alloc(sizeof(double2) * m * cnt));
+  SS_CUDA(cudaMemcpyAsync(Wd.p, Cx.data(), sizeof(double2) * m * cnt, cudaMemcpyHostToDevice, st));
+  SS_TRY(X.alloc(sizeof(double2) * n * cnt));
+  if (df)
+    SS_TRY(combine_df(T.as<float4>(), m, n, Wd.as<double2>(), cnt, X.as<double2>(), st));
+  else
+    SS_TRY(combine(T.as<double2>(), m, n, Wd.as<double2>(), cnt, X.as<double2>(), st));
+  return finish_ritz(lat, X, ev, evals, resid, scratch, st);
 }
 
 // Rayleigh-Ritz for one window: orthonormal basis of S (m vectors), Ritz

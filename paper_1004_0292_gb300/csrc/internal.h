@@ -166,6 +166,13 @@ int combine(const double2* S, int ms, long long n, const double2* C, int mc, dou
 // columns of S are complete (the orthogonalisation waits per group)
 int cgs2(const double2* S, int m, long long n, double2* Q, double2* R, DevBuf& scratch, cudaStream_t s,
          const cudaEvent_t* group_ready = nullptr, int group = 0);
+// Float-float forms of cgs2, gram and combine (blas_df.cu) for SSQCD_DF
+// solves: S, Q, X (gram), T: complex float-float vectors [m][n] (float4);
+// R, G: FP64 (m x m row-major, device); combine_df writes X in FP64.
+int cgs2_df(const float4* S, int m, long long n, float4* Q, double2* R, DevBuf& scratch, cudaStream_t s);
+int gram_df(const float4* X, int mx, const float4* Y, int my, long long n, double2* G, DevBuf& scratch,
+            cudaStream_t s, bool herm = false);
+int combine_df(const float4* T, int ms, long long n, const double2* C, int mc, double2* X, cudaStream_t s);
 int col_residual_norms(const double2* AX, const double2* X, const double* theta, int m, long long n,
                        double* out, DevBuf& scratch, cudaStream_t s);
 int convert_f64_to_f32(const double2* in, float2* out, long long n, cudaStream_t s);
