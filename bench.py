@@ -24,8 +24,9 @@ solves an independent replica (its own sources): the path has no data
 exchange, so scaling is weak and there is no collective on the data path.
 
 ``mixed`` reports the same metric on the same workload for the solve
-precision SSQCD_DF (float-float links, stencil, seed vectors and stored
-residuals on the FP32 pipes; FP64 recurrence scalars, Rayleigh-Ritz), with
+precision SSQCD_DF (float-float links, stencil, seed vectors, stored
+residuals and the Rayleigh-Ritz basis on the FP32 pipes; FP64 recurrence
+scalars, eigenvectors and residuals), with
 its ratio to the plain FP64 value.  ``mixed_fp32_fp16`` records the FP32
 stencil / FP16-link form, which cannot reach the residual bar (it runs on
 the 8^4 workload, where it converges).  ``config2`` repeats the plain and
@@ -85,9 +86,9 @@ UPDATE_BYTES_PER_UNIT = 64
 # + 24 = 888 FP64 instructions; counted as 1368 flop/site/rhs (FMA = 2); bytes:
 # spinor in 192 B + out 192 B + links 576 B (shared by the rhs) per site.
 STENCIL_FLOP_PER_SITE = 1368
-# DRAM traffic of one launch of the FP64 stencil kernel (cg_stencil_kernel<Stencil64>,
-# 4 rhs, 8^4) from an ncu capture; None until captured for the current kernel.
-STENCIL_FP64_TRAFFIC = 5.565952e6  # ncu: dram read 5.565952 MB, write 0 per launch
+# DRAM traffic of one launch of the FP64 stencil kernel (cg_stencil_kernel<Stencil64h>,
+# 1 rhs, 16^3 x 32) from a one-pass ncu capture; None until captured for the current kernel.
+STENCIL_FP64_TRAFFIC = 102877184.0 + 11855872.0  # ncu: dram read 102.88 MB + write 11.86 MB
 # DRAM traffic of one launch of each update kernel with all 128 (source,
 # shift) pairs live on this workload (ncu dram__bytes_read.sum +
 # dram__bytes_write.sum, one capture per kernel; the algorithmic bytes of such
@@ -327,7 +328,8 @@ def run_ours(args):
         it_m = max(1, sum(x["launches_update"] for x in s_m))
         mixed = {
             "precision": "SSQCD_DF: float-float (FP32 pair, 48-bit significand) links, stencil, seed vectors and "
-                         "stored residuals on the FP32 pipes; FP64 recurrence scalars and Rayleigh-Ritz",
+                         "stored residuals, and the Rayleigh-Ritz basis and products, on the FP32 pipes; FP64 "
+                         "recurrence scalars, eigenvectors and residuals",
             "value": value_m, "unit": UNIT, "ms_per_step": ms_m / args.steps,
             "vs_plain_fp64": value_m / value, "eigenpairs_per_step": c_m[-1],
             "max_accepted_residual": r_m[-1], "iterations_per_step": p_m[-1]["iterations"],
@@ -381,26 +383,36 @@ def run_ours(args):
             "cg_us_per_iteration": 1e3 * last["ms_cg"] / max(1, last["iterations"]) / n_groups,
             "stored_residual_bytes_per_block": last["basis_bytes"],
             "roofline": {
+                "kernel": "cg_stencil_kernel<Stencil64h> (q = K p with the (p, q) partials, FP64, 16 sites a block; "
+                          "the step's dominant kernel: 2 x L x iterations launches)",
+                "bound": "alu", "achieved": sten_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": sten_tf / FP64_PEAK_TFLOPS if sten_tf else None, "traffic": STENCIL_FP64_TRAFFIC,
+                "traffic_note": "dram read + write of one launch (1 rhs, 16^3 x 32) from a one-pass ncu capture "
+                                "(profiles/launches_fp64_16x16x16x32_headline.md); algorithmic 192 + 192 + 576 B a "
+                                "site = 125.8 MB",
+                "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (no FP64 entry in "
+                               "MEASURED_PEAKS.json)",
+                "flop_count": "1368 a site and rhs (the Wilson hop's 1320 plus gamma5 and the diagonal; FMA = 2); "
+                              "~910 FP64 instructions, so 0.75 of the flop peak is the instruction-issue bound",
+                "avg_launch_us": 1e3 * ms_sten / max(1, it_tot), "rhs_per_launch": Lb,
+                "hbm_achieved_gbs": sten_bytes / (ms_sten / 1e3) / 1e9 if ms_sten > 0 else None,
+                "launch_time_source": "a separate step with the library's kernel timing on (one run at a time): "
+                                      "CUDA events on the launching stream, one 16-iteration chunk in four",
+                "share_of_step": (ms_sten / max(1, it_tot) * last["iterations"] * w["L"] / Lb)
+                                 / (total_ms / args.steps),
+            },
+            "moments_roofline": {
                 "kernel": "basis_combine_kernel (moments from the stored seed residuals, FP64; the moments phase, "
                           "whose other kernels are the small coefficient recurrences)",
                 "bound": "alu", "achieved": mom_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": mom_tf / FP64_PEAK_TFLOPS, "traffic": COMBINE_TRAFFIC,
                 "traffic_note": "bytes per launch (one window, one block of 2 sources: each residual read "
                                 "once, 2 x 2499 x 1572864 x 16 B = 125.8 GB, and 32 moments written, 0.8 GB; "
-                                "profiles/combine_fp64_16x16x16x32.md)",
-                "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (no FP64 entry in "
-                               "MEASURED_PEAKS.json)",
+                                "profiles/combine_fp64_16x16x16x32.md); the headline runs one source a launch",
                 "flop_count": ("4 per term: real coefficients (conjugate-pair points), a real times a complex "
                                "residual element, 2 FMA" if last.get("real_moments") else
                                "8 per complex multiply-add (the kernel issues 3 real multiplications per product)"),
                 "phase_ms": last["ms_moments"], "fraction_of_step": last["ms_moments"] / (total_ms / args.steps),
-            },
-            "stencil": {
-                "kernel": "cg_stencil_kernel<Stencil64h> (q = K p with the (p, q) partials, FP64, 16 sites a block)",
-                "bound": "alu", "achieved_tflops": sten_tf, "frac": sten_tf / FP64_PEAK_TFLOPS if sten_tf else None,
-                "hbm_achieved_gbs": sten_bytes / (ms_sten / 1e3) / 1e9 if ms_sten > 0 else None,
-                "avg_launch_us": 1e3 * ms_sten / max(1, it_tot), "rhs_per_launch": Lb,
-                "note": "separate step with the library kernel timing on: CUDA events on one 16-iteration chunk in four",
             },
             "kernel_us_per_iteration": {"stencil": 1e3 * ms_sten / max(1, it_tot),
                                         "seed_update": 1e3 * sum(s["ms_k_seed"] for s in stats) / max(1, it_tot),
@@ -462,7 +474,7 @@ def run_config2(ss, stream, flush, args, world, peaks):
             ms_sten = sum(s["ms_k_stencil"] for s in stats)
             tf = it_tot * V * w["L"] * STENCIL_FLOP_PER_SITE / (ms_sten / 1e3) / 1e12
             ent["stencil"] = {"kernel": "cg_stencil_kernel<Stencil64h>", "bound": "alu", "achieved_tflops": tf,
-                              "frac": tf / FP64_PEAK_TFLOPS, "traffic": STENCIL_FP64_TRAFFIC,
+                              "frac": tf / FP64_PEAK_TFLOPS, "traffic": None,
                               "avg_launch_us": 1e3 * ms_sten / max(1, it_tot)}
             ent["kernel_us_per_iteration"] = {
                 "stencil": 1e3 * ms_sten / max(1, it_tot),

@@ -60,8 +60,10 @@ extern "C" {
                                    float-float (hi + lo FP32 pair, 48-bit
                                    significand) updated on the FP32 pipes      */
 #define SSQCD_DF           5    /* links, stencil, seed and shift vectors all in
-                                   float-float on the FP32 pipes; recurrence
-                                   scalars, moments and Rayleigh-Ritz in FP64  */
+                                   float-float on the FP32 pipes, and so are
+                                   the Rayleigh-Ritz basis (CGS2), A T and the
+                                   projected matrix; recurrence scalars, moment
+                                   sums, eigenvectors and residuals in FP64    */
 
 /* ---- eigenvalue extraction from the moments ---------------------------------- */
 #define SSQCD_EXTRACT_RR     0  /* Rayleigh-Ritz on span(S_hat) (Section 2.1): eigenpairs
