@@ -954,6 +954,123 @@ def run_beta_study(ss, stream, big=False):
     return {"workload": w["name"], "rows": rows}
 
 
+# 48 requests over three lattice sizes (the batched workload): seeded smooth
+# fields, each lattice's lowest positive eigenvalue cluster (12 eigenvalues,
+# located with the solver on a tiled scan of [0.03, 0.15]); a request with
+# L = 1 takes one of three sub-windows of its cluster (3-5 eigenvalues, ends
+# in gaps), L = 4 or 8 the whole cluster.
+BATCHED = dict(
+    lattices={
+        "8": dict(dims=(8, 8, 8, 8), kappa=0.125, eps=0.3, seed=2, full=(0.105, 0.120),
+                  subs=((0.1095, 0.1123), (0.1123, 0.1146), (0.1146, 0.1170))),
+        "12": dict(dims=(12, 12, 12, 12), kappa=0.13, eps=0.4, seed=5, full=(0.0850, 0.0915),
+                   subs=((0.0855, 0.0877), (0.0877, 0.08868), (0.08868, 0.0910))),
+        "16": dict(dims=(16, 16, 16, 16), kappa=0.135, eps=0.5, seed=6, full=(0.0885, 0.0940),
+                   subs=((0.0895, 0.09108), (0.09108, 0.09164), (0.09164, 0.0930))),
+    },
+    n_requests=48, sources=(1, 4, 8), points=(16, 32, 64), M=8, beta=0.3, nprime={16: 10, 32: 20, 64: 40},
+    budget_bytes=200e9, solo_checks=6,
+)
+
+
+def batched_plan(n_requests, seed=29):
+    """The request list of the batched workload: (lattice key, interval, N, L,
+    source seed, source_block, basis_max_bytes), lattices in turn, L and N
+    drawn (seeded)."""
+    rng = np.random.default_rng(seed)
+    keys = list(BATCHED["lattices"])
+    plan = []
+    for i in range(n_requests):
+        key = keys[i % len(keys)]
+        lt = BATCHED["lattices"][key]
+        L = int(rng.choice(BATCHED["sources"]))
+        N = int(rng.choice(BATCHED["points"]))
+        iv = lt["subs"][int(rng.integers(3))] if L == 1 else lt["full"]
+        # stored residuals: ~1000 / 1300 / 5000 iterations of 0.8 / 4.0 / 12.6 MB
+        # a source on 8^4 / 12^4 / 16^4; the 16^4 runs go one source at a time
+        # (63 GB each), and the caps keep every run in the stored-residual form
+        sb = 1 if key == "16" and L > 1 else 0
+        cap = {"8": 0.0, "12": 6e9 * L, "16": 70e9}[key]
+        plan.append((key, iv, N, L, 7000 + i, sb, cap))
+    return plan
+
+
+def run_batched_uneven(ss, stream, n_requests=None, solo_checks=None):
+    """The batched workload through the request scheduler: all requests
+    submitted at once, each on its own stream with its own CUDA graphs, under
+    a 200 GB memory budget; FP64 and float-float lattices.  Reports
+    eigenpairs/s at residual <= 1e-8 over the span, p50/p99 latency and the
+    requests that waited on memory, and checks that the first few requests'
+    eigenvalues equal their solo runs (one request at a time) bit for bit."""
+    import torch
+
+    import synthetic
+    cfg = BATCHED
+    n_requests = cfg["n_requests"] if n_requests is None else n_requests
+    solo_checks = cfg["solo_checks"] if solo_checks is None else solo_checks
+    plan = batched_plan(n_requests)
+    fields = {k: synthetic.gauge_field(v["dims"], "smooth", seed=v["seed"], eps=v["eps"])
+              for k, v in cfg["lattices"].items()}
+    out = {"requests": n_requests, "arrivals": "all at once",
+           "mix": "8^4 (kappa 0.125, eps 0.3), 12^4 (0.13, 0.4), 16^4 (0.135, 0.5) in turn; L in {1, 4, 8}, "
+                  "N in {16, 32, 64}, M 8; L = 1 on a 3-5 eigenvalue sub-window, else the 12-eigenvalue cluster",
+           "budget_bytes": cfg["budget_bytes"],
+           "launch": "per-request streams and CUDA graphs through the scheduler (no single launch across "
+                     "lattices)"}
+
+    def submit(srv, lats, item):
+        key, iv, N, L, sseed, sb, cap = item
+        lt = cfg["lattices"][key]
+        src = torch.from_numpy(synthetic.gaussian_sources(lt["dims"], L, seed=sseed)).cuda()
+        return srv.submit_windows(lats[key], [iv], N, cfg["M"], src, beta=cfg["beta"], nprime=cfg["nprime"][N],
+                                  source_block=sb, basis_max_bytes=cap)
+
+    def serve(lats, items):
+        srv = ss.Server(int(cfg["budget_bytes"]))
+        t0 = time.perf_counter()
+        ids = [submit(srv, lats, it) for it in items]
+        while True:
+            q, r, f = srv.counts()
+            if q == 0 and r == 0:
+                break
+            srv.progress(wait=True)
+        span = time.perf_counter() - t0
+        lat_ms, pairs, failed, evs = [], 0, 0, []
+        for i in ids:
+            _, ms = srv.status(i)
+            lat_ms.append(ms)
+            res = srv.take(i)
+            if res.status != ss.OK:
+                failed += 1
+                evs.append(None)
+                continue
+            ev, _, rs, _ = ss.ss_eigpairs(res, want_vectors=False)
+            pairs += int(np.sum(rs <= RES_TOL))
+            evs.append((ev, rs))
+        deferred = srv.deferred()
+        srv.close()
+        return {"eigenpairs_per_s": pairs / span, "eigenpairs": pairs, "failed": failed,
+                "waited_on_memory": deferred, "span_s": span,
+                "latency_ms": {"p50": float(np.percentile(lat_ms, 50)), "p99": float(np.percentile(lat_ms, 99))}}, evs
+
+    for name, prec in (("plain_fp64", ss.FP64), ("mixed", ss.DF)):
+        lats = {}
+        for k, v in cfg["lattices"].items():
+            lats[k] = ss.create_lattice(v["dims"], v["kappa"], -1, precision=prec, stream=stream)
+            ss.upload_gauge(lats[k], fields[k])
+        res, evs = serve(lats, plan)
+        same = 0
+        for j in range(min(solo_checks, len(plan))):
+            _, evs1 = serve(lats, [plan[j]])
+            a, b = evs[j], evs1[0]
+            same += int(a is not None and b is not None and np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]))
+        res["solo_identical"] = f"{same} of {min(solo_checks, len(plan))}"
+        out[name] = res
+        del lats
+    out["mixed_vs_plain"] = out["mixed"]["eigenpairs_per_s"] / out["plain_fp64"]["eigenpairs_per_s"]
+    return out
+
+
 def run_only(args):
     """One secondary leg alone (the commands of the committed ncu captures)."""
     import torch
@@ -967,6 +1084,8 @@ def run_only(args):
     if args.only == "stencil_large":
         ss.set_stencil_variant(args.stencil_variant)
         out = run_stencil_large(ss, stream, peaks)
+    elif args.only == "batched_uneven":
+        out = run_batched_uneven(ss, stream)
     elif args.only.startswith("beta_study"):
         out = run_beta_study(ss, stream, big=args.only.endswith("16x32"))
     else:
@@ -991,7 +1110,8 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=30.0)
     ap.add_argument("--stencil-variant", type=int, default=-1,
                     help="FP32 stencil variant for stencil_large (0..5; -1: the autotuner's choice)")
-    ap.add_argument("--only", choices=["stencil_large", "config2", "beta_study", "beta_study_16x32"], default=None,
+    ap.add_argument("--only", choices=["stencil_large", "config2", "beta_study", "beta_study_16x32", "batched_uneven"],
+                    default=None,
                     help="run one secondary leg alone and print its JSON (profiling runs)")
     args = ap.parse_args()
     if args.only is not None:

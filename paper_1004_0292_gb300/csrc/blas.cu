@@ -6,6 +6,7 @@
 // then one pass over the partials in block order), so results do not depend
 // on scheduling.
 #include <algorithm>
+#include <mutex>
 
 #include "internal.h"
 
@@ -626,8 +627,14 @@ int combine(const double2* S, int ms, long long n, const double2* C, int mc, dou
   const long long cap = (4LL * 152 + cy - 1) / cy;
   if (bx > cap) bx = cap;
   const size_t shm = sizeof(double2) * ms * kCC;
-  if (shm > 48 * 1024) {
-    SS_CUDA(cudaFuncSetAttribute(combine_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+  if (shm > 48 * 1024) {  // raised only: concurrent solves share the kernel's attribute
+    static std::mutex mu;
+    static size_t set = 0;
+    std::lock_guard<std::mutex> lock(mu);
+    if (shm > set) {
+      SS_CUDA(cudaFuncSetAttribute(combine_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+      set = shm;
+    }
   }
   combine_kernel<<<dim3((unsigned)bx, cy), 256, shm, s>>>(S, ms, n, C, mc, Q);
   count_launches(1);

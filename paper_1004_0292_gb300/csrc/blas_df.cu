@@ -12,6 +12,7 @@
 // only sees those per-chain conversions.  The reductions have a fixed order
 // (block partials, then one pass over them in block order).
 #include <algorithm>
+#include <mutex>
 
 #include "floatfloat.cuh"
 #include "internal.h"
@@ -469,8 +470,14 @@ int combine_df(const float4* T, int ms, long long n, const double2* C, int mc, d
   const long long cap = (4LL * 152 + cy - 1) / cy;
   if (bx > cap) bx = cap;
   const size_t shm = sizeof(ff::PCoef) * ms * kCCd;
-  if (shm > 48 * 1024) {
-    SS_CUDA(cudaFuncSetAttribute(combine_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+  if (shm > 48 * 1024) {  // raised only: concurrent solves share the kernel's attribute
+    static std::mutex mu;
+    static size_t set = 0;
+    std::lock_guard<std::mutex> lock(mu);
+    if (shm > set) {
+      SS_CUDA(cudaFuncSetAttribute(combine_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+      set = shm;
+    }
   }
   combine_df_kernel<<<dim3((unsigned)bx, cy), 256, shm, s>>>(T, ms, n, C, mc, X);
   count_launches(1);

@@ -53,6 +53,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <memory>
+#include <mutex>
 #include <new>
 #include <type_traits>
 #include <utility>
@@ -1863,10 +1864,19 @@ int update_stall_test() {
   return v;
 }
 
+// The shared-memory limit is an attribute of the kernel, shared by every run
+// of the process: it is only ever raised, so that a run with fewer shifts
+// does not lower it below what a concurrent run's launches need (the
+// scheduler's requests run side by side).
 template <typename RT>
 int prepare_update_tma(int NL, int L) {
+  static std::mutex mu;
+  static size_t set = 0;
   const size_t smem = tma_smem_bytes(NL, L);
+  std::lock_guard<std::mutex> lock(mu);
+  if (smem <= set) return SSQCD_OK;
   SS_CUDA(cudaFuncSetAttribute(cg_update_tma_kernel<RT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  set = smem;
   return SSQCD_OK;
 }
 

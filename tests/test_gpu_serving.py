@@ -141,3 +141,53 @@ def test_window_list_request_with_source_blocks(setup):
     for i in others:
         assert srv.take(i).status == ss.OK
     srv.close()
+
+
+def test_update_form_requests_with_different_shift_counts_side_by_side(setup):
+    """Two requests whose float-float shift vectors are updated by the
+    TMA-fed kernel (its shared memory grows with N x L), the one with fewer
+    shifts admitted second: the kernel's shared-memory limit is shared by the
+    process, so the second request must not lower it below the first one's
+    need.  Both finish and equal their solo runs bit for bit."""
+    ss, reqs, alone = setup
+    lat8 = reqs[3][0]
+    w = bench.CONFIG2
+    _, src8 = bench.make_inputs(0, bench.CONFIG2)
+    items = [(w["N"], src8), (16, src8[:1])]
+    solo = []
+    for N, src in items:
+        res = ss.ss_solve(lat8, w["interval"], N, w["M"], src, beta=w["beta"], nprime=min(w["nprime"], N))
+        assert res.status == ss.OK, res.error
+        ev, _, rs, _ = ss.ss_eigpairs(res, want_vectors=False)
+        solo.append((ev, rs))
+    srv = ss.Server()
+    ids = [srv.submit(lat8, w["interval"], N, w["M"], src, beta=w["beta"], nprime=min(w["nprime"], N))
+           for N, src in items]
+    _drain(ss, srv, ids)
+    for i, (ev0, rs0) in zip(ids, solo):
+        out = srv.take(i)
+        assert out.status == ss.OK, out.error
+        ev, _, rs, _ = ss.ss_eigpairs(out, want_vectors=False)
+        assert np.array_equal(ev, ev0) and np.array_equal(rs, rs0)
+    srv.close()
+
+
+def test_batched_uneven_requests_match_their_solo_runs():
+    """The batched workload's first six requests (8^4, 12^4 and 16^4 fields,
+    each with its own window, L and N) submitted at once through the
+    scheduler, in FP64 and float-float: none fails, each request's
+    eigenvalues and residuals equal its solo run bit for bit, and each
+    cluster window's converged eigenvalues lie in its interval."""
+    ss = gpu_module()
+    import torch
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    try:
+        out = bench.run_batched_uneven(ss, stream, n_requests=6, solo_checks=6)
+    finally:
+        torch.cuda.set_stream(torch.cuda.default_stream())
+    for arm in ("plain_fp64", "mixed"):
+        r = out[arm]
+        assert r["failed"] == 0
+        assert r["solo_identical"] == "6 of 6"
+        assert r["eigenpairs"] >= 12
