@@ -31,7 +31,11 @@ its ratio to the plain FP64 value.  ``mixed_fp32_fp16`` records the FP32
 stencil / FP16-link form, which cannot reach the residual bar (it runs on
 the 8^4 workload, where it converges).  ``config2`` repeats the plain and
 float-float measurements on the 8^4 workload (kappa 0.125, L = 4, N = 32,
-M = 8, 12 eigenpairs), whose data fit in L2.
+M = 8, 12 eigenpairs), whose data fit in L2.  ``serving``,
+``serving_16x32`` and ``batched_uneven`` drive the library's request
+scheduler: Poisson arrivals on small resident lattices, the headline
+lattice resident beside small ones under a memory budget, and 48 uneven
+requests over 8^4 / 12^4 / 16^4 lattices submitted at once.
 
 ``--impl reference`` times the FP64 numpy oracle on the host cores on a
 bounded sample of the same workload (shifted-CG iterations of one source
@@ -350,11 +354,12 @@ def run_ours(args):
     if not args.no_serving:
         stencil_large = run_stencil_large(ss, stream, peaks)
 
-    serving = serving_large = None
+    serving = serving_large = batched = None
     if not args.no_serving:
         U8, _ = make_inputs(rank, CONFIG2)
         serving = run_serving(ss, stream, U8, seed=17 + rank)
         serving_large = run_serving_large(ss, stream, U, src, U8, seed=23 + rank)
+        batched = run_batched_uneven(ss, stream)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -420,7 +425,8 @@ def run_ours(args):
                                         "timed_iterations": it_tot, "rhs": Lb},
             "e2e": e2e, "cpu_baseline": cpu, "clocks": clk, "gpu_launches": int(launches), "mixed": mixed,
             "mixed_fp32_fp16": config2.pop("fp32_fp16") if config2 else None,
-            "config2": config2, "serving": serving, "serving_16x32": serving_large, "stencil_large": stencil_large,
+            "config2": config2, "serving": serving, "serving_16x32": serving_large, "batched_uneven": batched,
+            "stencil_large": stencil_large,
         }
         print(json.dumps(out), flush=True)
     if world > 1:
