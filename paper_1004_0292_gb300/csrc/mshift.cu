@@ -1590,26 +1590,38 @@ basis_combine_kernel(char* const* __restrict__ tab, long long n, int L, const do
 }
 
 // The same combination for float-float residuals (SSQCD_DF runs), on the
-// FP32 pipes: within a tile of kCombTile slots each output accumulates
-// c += w r in float-float (the FP64 coefficients split into float-float
-// pairs once per tile), then the tile's sums enter FP64 accumulators, so at
-// most kCombTile terms share a float-float sum (rounding ~kCombTile 2^-48 of
-// their magnitudes, against the residuals' own 2^-48).  The FP64 pipe only
-// sees the per-tile conversions.  The complex float-float multiply-adds run
-// on register pairs (real and imaginary part in one paired instruction,
-// floatfloat.cuh p_cfma), in the operation order of ff::cfma.  RC: real
-// coefficients (as in basis_combine_kernel), one float-float multiply-add a
-// part, both parts in one paired instruction (ff::p_rfma).
-template <int OUT, bool RC>
+// FP32 pipes: within a tile of TILE slots each output accumulates c += w r
+// in float-float, then the tile's sums enter FP64 accumulators, so at most
+// TILE terms share a float-float sum (rounding ~TILE 2^-48 of their
+// magnitudes, against the residuals' own 2^-48).  The FP64 pipe (1/64 of the
+// FP32 rate) only sees the per-tile conversions, but every warp reaches them
+// at once after the tile's barrier, so they are kept rare: real coefficients
+// (RC, as in basis_combine_kernel) take tiles of 128 slots and come as
+// float-float pairs from coef_real_to_ff_kernel (one FP64 split per
+// coefficient and solve, not per block); complex ones tiles of kCombTile,
+// split per tile.  The complex float-float multiply-adds run on register
+// pairs (real and imaginary part in one paired instruction, floatfloat.cuh
+// p_cfma), in the operation order of ff::cfma; RC: one float-float
+// multiply-add a part, both parts in one paired instruction (ff::p_rfma).
+constexpr int kCombTileRC = 128;
+
+// cr[i] = (hi, lo) of Re c[i] as float-float
+__global__ void coef_real_to_ff_kernel(const double2* __restrict__ c, long long count, float2* __restrict__ cr) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < count) cr[i] = ff::split(c[i].x);
+}
+
+template <int OUT, bool RC, int TILE>
 __global__ void __launch_bounds__(kCombThreads, 2)
-basis_combine_df_kernel(char* const* __restrict__ tab, long long n, int L, const double2* __restrict__ C, int O, int S,
-                        const int* __restrict__ count, double2* __restrict__ out, int l0) {
+basis_combine_df_kernel(char* const* __restrict__ tab, long long n, int L, const double2* __restrict__ C,
+                        const float2* __restrict__ Cr, int O, int S, const int* __restrict__ count,
+                        double2* __restrict__ out, int l0) {
   // coefficients as the four register pairs of ff::p_cfma (real part in lane
   // 0, imaginary part in lane 1: one paired instruction for both); RC: the
   // pairs (hi, hi) and (lo, lo) of the real coefficient
-  __shared__ ff::PCoef s_w[RC ? 1 : kCombTile][OUT];
-  __shared__ f32x2_t s_rh[RC ? kCombTile : 1][OUT], s_rl[RC ? kCombTile : 1][OUT];
-  __shared__ const float4* s_p[kCombTile];
+  __shared__ ff::PCoef s_w[RC ? 1 : TILE][OUT];
+  __shared__ f32x2_t s_rh[RC ? TILE : 1][OUT], s_rl[RC ? TILE : 1][OUT];
+  __shared__ const float4* s_p[TILE];
   const int l = blockIdx.y + l0, o0 = blockIdx.z * OUT;
   const int no = min(OUT, O - o0);
   const int Sl = count[l];
@@ -1618,25 +1630,25 @@ basis_combine_df_kernel(char* const* __restrict__ tab, long long n, int L, const
   double2 accd[OUT];
 #pragma unroll
   for (int o = 0; o < OUT; ++o) accd[o] = make_double2(0.0, 0.0);
-  for (int s0 = 0; s0 < Sl; s0 += kCombTile) {
-    const int ns = min(kCombTile, Sl - s0);
+  for (int s0 = 0; s0 < Sl; s0 += TILE) {
+    const int ns = min(TILE, Sl - s0);
     __syncthreads();
-    for (int t = threadIdx.x; t < kCombTile * OUT; t += kCombThreads) {
+    for (int t = threadIdx.x; t < TILE * OUT; t += kCombThreads) {
       const int ss = t / OUT, oo = t % OUT;
-      const double2 c = (ss < ns && oo < no) ? C[((size_t)l * O + o0 + oo) * S + s0 + ss] : make_double2(0.0, 0.0);
       if (RC) {
-        const float2 r = ff::split(c.x);
+        const float2 r = (ss < ns && oo < no) ? Cr[((size_t)l * O + o0 + oo) * S + s0 + ss] : make_float2(0.f, 0.f);
         s_rh[RC ? ss : 0][oo] = pk2(r.x, r.x);
         s_rl[RC ? ss : 0][oo] = pk2(r.y, r.y);
       } else {
+        const double2 c = (ss < ns && oo < no) ? C[((size_t)l * O + o0 + oo) * S + s0 + ss] : make_double2(0.0, 0.0);
         s_w[RC ? 0 : ss][oo] = ff::p_coef(ff::from_double2(c));
       }
     }
-    if (threadIdx.x < kCombTile) {
-      const int s = s0 + threadIdx.x;
-      s_p[threadIdx.x] = threadIdx.x < ns ? reinterpret_cast<const float4*>(tab[s >> kBasisLog]) +
-                                                (long long)(s & (kBasisBlock - 1)) * Ln + (long long)l * n
-                                          : nullptr;
+    for (int t = threadIdx.x; t < TILE; t += kCombThreads) {
+      const int s = s0 + t;
+      s_p[t] = t < ns ? reinterpret_cast<const float4*>(tab[s >> kBasisLog]) + (long long)(s & (kBasisBlock - 1)) * Ln +
+                            (long long)l * n
+                      : nullptr;
     }
     __syncthreads();
     if (e < n) {
@@ -2690,15 +2702,22 @@ int basis_moments(const KrylovBasis& b, const double2* coef_host, int M, double2
                   cudaStream_t st, cudaStream_t side, const cudaEvent_t* src_ready, bool real_coef) {
   const int N = b.N, L = b.L, S = b.S;
   const size_t w_bytes = (sizeof(double2) * (size_t)N * M + 255) / 256 * 256;
-  SS_TRY(scratch.alloc(w_bytes + sizeof(double2) * (size_t)L * M * S));
+  const long long cnt = (long long)L * M * S;
+  // W, G and (float-float residuals) Re G as float-float pairs
+  SS_TRY(scratch.alloc(w_bytes + sizeof(double2) * (size_t)cnt + (b.df ? sizeof(float2) * (size_t)cnt : 0)));
   double2* W = scratch.as<double2>();
   double2* G = reinterpret_cast<double2*>(scratch.as<char>() + w_bytes);
+  float2* Gr = reinterpret_cast<float2*>(G + cnt);
   SS_CUDA(cudaMemcpyAsync(W, coef_host, sizeof(double2) * (size_t)N * M, cudaMemcpyHostToDevice, st));
-  const long long cnt = (long long)L * M * S;
   basis_window_kernel<<<(unsigned)((cnt + 255) / 256), 256, 0, st>>>(b.gam.as<double2>(), W, N, M, L, S, G);
   SS_CHECK_LAUNCH();
   count_launches(1);
   const bool rc = real_coef && real_moments_enabled();
+  if (b.df && rc) {
+    coef_real_to_ff_kernel<<<(unsigned)((cnt + 255) / 256), 256, 0, st>>>(G, cnt, Gr);
+    SS_CHECK_LAUNCH();
+    count_launches(1);
+  }
   auto one = [&](int l0, int nl, cudaStream_t s) -> int {
     if (b.df) {
       // outputs a thread accumulates: 8 (default) or 4 (SSQCD_COMB_DF_OUT=4:
@@ -2711,14 +2730,26 @@ int basis_moments(const KrylovBasis& b, const double2* coef_host, int M, double2
       const dim3 grid((unsigned)((b.n + kCombThreads - 1) / kCombThreads), nl, (M + per - 1) / per);
       char* const* tab = b.tab.as<char*>();
       const int* count = b.count.as<int>();
+      // SSQCD_COMB_DF_TILE=32: real coefficients in tiles of 32 (comparison runs)
+      static const bool tile32 = [] {
+        const char* e = std::getenv("SSQCD_COMB_DF_TILE");
+        return e != nullptr && std::atoi(e) == 32;
+      }();
       if (per == 4 && rc)
-        basis_combine_df_kernel<4, true><<<grid, kCombThreads, 0, s>>>(tab, b.n, L, G, M, S, count, s_hat, l0);
+        basis_combine_df_kernel<4, true, kCombTileRC>
+            <<<grid, kCombThreads, 0, s>>>(tab, b.n, L, G, Gr, M, S, count, s_hat, l0);
       else if (per == 4)
-        basis_combine_df_kernel<4, false><<<grid, kCombThreads, 0, s>>>(tab, b.n, L, G, M, S, count, s_hat, l0);
+        basis_combine_df_kernel<4, false, kCombTile>
+            <<<grid, kCombThreads, 0, s>>>(tab, b.n, L, G, Gr, M, S, count, s_hat, l0);
+      else if (rc && tile32)
+        basis_combine_df_kernel<8, true, kCombTile>
+            <<<grid, kCombThreads, 0, s>>>(tab, b.n, L, G, Gr, M, S, count, s_hat, l0);
       else if (rc)
-        basis_combine_df_kernel<8, true><<<grid, kCombThreads, 0, s>>>(tab, b.n, L, G, M, S, count, s_hat, l0);
+        basis_combine_df_kernel<8, true, kCombTileRC>
+            <<<grid, kCombThreads, 0, s>>>(tab, b.n, L, G, Gr, M, S, count, s_hat, l0);
       else
-        basis_combine_df_kernel<8, false><<<grid, kCombThreads, 0, s>>>(tab, b.n, L, G, M, S, count, s_hat, l0);
+        basis_combine_df_kernel<8, false, kCombTile>
+            <<<grid, kCombThreads, 0, s>>>(tab, b.n, L, G, Gr, M, S, count, s_hat, l0);
       SS_CHECK_LAUNCH();
       count_launches(1);
       return SSQCD_OK;
