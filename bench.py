@@ -576,7 +576,9 @@ def run_stencil_large(ss, stream, peaks):
                                     "variants": ["all rhs of 32 sites a block, 4 blocks/SM", "same, 3 blocks/SM",
                                                  "thread per site and rhs pair, 4 blocks/SM", "same, 3 blocks/SM",
                                                  "thread per site and rhs pair, the two rhs in the paired lanes, "
-                                                 "4 blocks/SM", "same, 3 blocks/SM"]}
+                                                 "4 blocks/SM", "same, 3 blocks/SM",
+                                                 "the same with the x-y plane and its y-halo staged in shared "
+                                                 "memory, 4 blocks/SM", "same, 3 blocks/SM"]}
         del lat
     return out
 
@@ -1115,7 +1117,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--cpu-budget", type=float, default=30.0)
     ap.add_argument("--stencil-variant", type=int, default=-1,
-                    help="FP32 stencil variant for stencil_large (0..5; -1: the autotuner's choice)")
+                    help="FP32 stencil variant for stencil_large (0..7; -1: the autotuner's choice)")
     ap.add_argument("--only", choices=["stencil_large", "config2", "beta_study", "beta_study_16x32", "batched_uneven"],
                     default=None,
                     help="run one secondary leg alone and print its JSON (profiling runs)")

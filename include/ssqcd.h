@@ -470,14 +470,15 @@ int ssqcd_time_stencil(ssqcd_lattice lat, int nrhs, int reps, double* ms_per_cal
  * storage times every variant (three launches each, CUDA events on the
  * lattice stream, skipped while the stream is being captured) and keeps the
  * fastest for that key; ssqcd_time_stencil times the chosen kernel alone.
- * ssqcd_set_stencil_variant(v) forces variant v (0..5; 4-5 fall back to 2-3
- * for an odd nrhs) for later calls in this process, or returns to tuning
- * (-1); SSQCD_ERR_ARG otherwise.  Not a part of the paper: the paper's
+ * ssqcd_set_stencil_variant(v) forces variant v (0..7; 4-7 fall back to 2-3
+ * for an odd nrhs, 6-7 to 4-5 where the lattice's X does not divide 128 or
+ * 128 / X does not divide Y) for later calls in this process, or returns to
+ * tuning (-1); SSQCD_ERR_ARG otherwise.  Not a part of the paper: the paper's
  * operator (Section 4) is the same in every variant. */
 int ssqcd_set_stencil_variant(int variant);
 
 /* The tuning recorded for this lattice (created with SSQCD_MIXED or
- * SSQCD_MIXED_F32LINKS) and nrhs: *variant the chosen variant, us[6] (may be
+ * SSQCD_MIXED_F32LINKS) and nrhs: *variant the chosen variant, us[8] (may be
  * NULL) the measured microseconds per application of each (0 for a variant
  * not timed).  SSQCD_ERR_ARG
  * if nothing was tuned for that key yet. */

@@ -503,14 +503,14 @@ def time_stencil(lat: Lattice, nrhs: int, reps: int = 20) -> float:
 
 
 def set_stencil_variant(variant: int):
-    """Force FP32 stencil variant 0..5, or -1 to tune per lattice size and rhs count."""
+    """Force FP32 stencil variant 0..7, or -1 to tune per lattice size and rhs count."""
     _check(lib().ssqcd_set_stencil_variant(int(variant)))
 
 
 def stencil_tuning(lat: Lattice, nrhs: int):
     """(chosen variant, microseconds per application of each variant) recorded for lat and nrhs."""
     v = C.c_int(0)
-    us = (C.c_double * 6)()
+    us = (C.c_double * 8)()
     _check(lib().ssqcd_stencil_tuning(lat.handle, int(nrhs), C.byref(v), us))
     return v.value, list(us)
 

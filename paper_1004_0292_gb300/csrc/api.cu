@@ -1843,10 +1843,10 @@ extern "C" int ssqcd_stencil_tuning(ssqcd_lattice lat, int nrhs, int* variant, d
   SS_TRY(check_lattice(lat, false));
   if (!is_mixed(lat->precision)) return fail(SSQCD_ERR_ARG, "ssqcd_stencil_tuning: the lattice has no FP32 stencil");
   if (variant == nullptr || nrhs < 1) return fail(SSQCD_ERR_ARG, "ssqcd_stencil_tuning: bad arguments");
-  float t[6];
+  float t[8];
   SS_TRY(fp32_stencil_tuning(lat->g.V, nrhs, lat->precision == SSQCD_MIXED ? 16 : 32, variant, t));
   if (us != nullptr)
-    for (int v = 0; v < 6; ++v) us[v] = t[v];
+    for (int v = 0; v < 8; ++v) us[v] = t[v];
   return SSQCD_OK;
 }
 

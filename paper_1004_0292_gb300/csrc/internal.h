@@ -138,7 +138,7 @@ int wilson32(const Geometry& g, const void* links, int link_bits, const float2* 
 int pack_gauge16(const double2* u64dev, void* u16, int V, cudaStream_t s);
 // FP32 stencil variants (wilson.cu): -1 tuned per (V, nrhs, link bits), 0..3 forced
 int set_fp32_stencil_variant(int v);
-int fp32_stencil_tuning(int V, int nrhs, int link_bits, int* variant, float* us);  // us[6]
+int fp32_stencil_tuning(int V, int nrhs, int link_bits, int* variant, float* us);  // us[8]
 int wilson32_kernel_only(const Geometry& g, const void* links, int link_bits, const float2* in, float2* out, int nrhs,
                          float c0, float c1, cudaStream_t s);
 int wilson_df(const Geometry& g, const float4* u, const float4* in, float4* out, int nrhs, double c0, double c1,

@@ -197,6 +197,68 @@ wilson32rp_kernel(Geometry g, LK lk, const float4* __restrict__ in_all, float4* 
   }
 }
 
+// The rhs-pair kernel with its x-y plane staged in shared memory: a block of
+// 128 threads covers 128 consecutive sites, i.e. 128 / X full x-lines of one
+// (z, t) plane (applicable when X divides 128 and 128 / X divides Y); the
+// block's own spinors and the two neighbouring y-rows are copied into a
+// shared tile first, so the x and y hops read their neighbours there (~30
+// cycles instead of a global load each) and only the z and t hops go to
+// global memory -- first, so that their loads overlap the staging.
+// Tile rows r = 0 .. R + 1: row 0 is y0 - 1, rows 1..R the block's own,
+// row R + 1 is y0 + R (periodic in y); element (r, x) at r X + x.
+template <typename LK, int MinB>
+__global__ void __launch_bounds__(128, MinB)
+wilson32rs_kernel(Geometry g, LK lk, const float4* __restrict__ in_all, float4* __restrict__ out_all, float c0,
+                  float c1) {
+  extern __shared__ float4 tile[];
+  const int X = g.X, Y = g.Y, V = g.V;
+  const int R = 128 / X, stride = (R + 2) * X;
+  const int s0 = blockIdx.x * 128, s = s0 + threadIdx.x;
+  const float4* in = in_all + (size_t)blockIdx.y * 12 * V;
+  float4* out = out_all + (size_t)blockIdx.y * 12 * V;
+  const int plane = s0 / (X * Y), y0 = (s0 / X) % Y;  // the block's (z, t) plane and first row
+#pragma unroll
+  for (int comp = 0; comp < 12; ++comp) tile[comp * stride + X + threadIdx.x] = __ldg(in + comp * V + s);
+  if ((int)threadIdx.x < 2 * X) {
+    const bool lo = (int)threadIdx.x < X;
+    const int xx = (int)threadIdx.x - (lo ? 0 : X);
+    const int yy = lo ? (y0 + Y - 1) % Y : (y0 + R) % Y;
+    const int site = xx + X * (yy + Y * plane);
+    const int r = lo ? 0 : R + 1;
+#pragma unroll
+    for (int comp = 0; comp < 12; ++comp) tile[comp * stride + r * X + xx] = __ldg(in + comp * V + site);
+  }
+  C2 acc[12];
+  const Coords c = site_coords(s, g);
+  // z and t hops from global memory while the tile fills
+  hop_rp_site<2, +1>(lk, in, s, c, g, true, acc);
+  hop_rp_site<2, -1>(lk, in, s, c, g, false, acc);
+  hop_rp_site<3, +1>(lk, in, s, c, g, false, acc);
+  hop_rp_site<3, -1>(lk, in, s, c, g, false, acc);
+  __syncthreads();
+  const int r = 1 + (c.y - y0);
+  const int xp = c.x + 1 == X ? 0 : c.x + 1, xm = c.x == 0 ? X - 1 : c.x - 1;
+  hop_rp_tile<0, +1>(lk, tile, stride, r * X + xp, s, c, g, false, acc);
+  hop_rp_tile<0, -1>(lk, tile, stride, r * X + xm, s, c, g, false, acc);
+  hop_rp_tile<1, +1>(lk, tile, stride, (r + 1) * X + c.x, s, c, g, false, acc);
+  hop_rp_tile<1, -1>(lk, tile, stride, (r - 1) * X + c.x, s, c, g, false, acc);
+  const f32x2_t mk = pk2(-(float)g.kappa, -(float)g.kappa), cc0 = pk2(c0, c0);
+  const f32x2_t sgu = pk2(c1, c1), sgl = pk2(-c1, -c1);
+#pragma unroll
+  for (int i = 0; i < 12; ++i) {
+    const float4 pv = tile[i * stride + X + threadIdx.x];
+    const C2 p{pk2(pv.x, pv.y), pk2(pv.z, pv.w)};
+    const f32x2_t sg = i < 6 ? sgu : sgl;
+    const f32x2_t tre = fma2(mk, acc[i].re, p.re), tim = fma2(mk, acc[i].im, p.im);
+    const float2 ore = upk2(fma2(sg, tre, mul2(cc0, p.re))), oim = upk2(fma2(sg, tim, mul2(cc0, p.im)));
+    out[i * V + s] = make_float4(ore.x, ore.y, oim.x, oim.y);
+  }
+}
+
+// the staged kernel applies: X divides 128 and 128 / X divides Y
+bool rs_applicable(const Geometry& g) { return g.X >= 1 && 128 % g.X == 0 && g.Y % (128 / g.X) == 0; }
+size_t rs_smem(const Geometry& g) { return sizeof(float4) * 12 * (128 + 2 * g.X); }
+
 // FP32 [nrhs][12][V] float2 <-> rhs pairs [npair][12][V] float4 (a missing
 // second rhs of the last pair reads as zero and is not written back)
 __global__ void to_rhs_pairs_kernel(const float2* __restrict__ a, float4* __restrict__ b, int nrhs, long long n12) {
@@ -306,17 +368,21 @@ using namespace wcore;
 //   4: one thread per site and rhs pair, the two rhs in the lanes of the
 //      paired instructions (wilson32rp, rhs-pair layout), 4 blocks an SM
 //   5: the same at 3 blocks an SM
+//   6: variant 4 with the block's x-y plane and its y-halo staged in shared
+//      memory (wilson32rs: the x and y hops read the tile), 4 blocks an SM;
+//      only where X divides 128 and 128 / X divides Y
+//   7: the same at 3 blocks an SM
 // Which is fastest depends on the lattice volume, the number of rhs and the
 // link storage, so the first application for a (V, nrhs, link bits) key
 // times each variant (three launches each, CUDA events on the caller's
-// stream; variants 4-5 only for an even nrhs, on the same buffers, which
+// stream; variants 4-7 only for an even nrhs, on the same buffers, which
 // then have the same size in the rhs-pair layout) and records the fastest;
-// later applications with that key use it (variants 4-5 convert to and from
-// the rhs-pair layout around the kernel).  Variants 2-5 give no (in, out)
+// later applications with that key use it (variants 4-7 convert to and from
+// the rhs-pair layout around the kernel).  Variants 2-7 give no (in, out)
 // partials, so callers that want them tune among 0-1 only.
 // ssqcd_set_stencil_variant forces one variant (tests, measurements),
 // ssqcd_stencil_tuning reports the choice of a key.
-constexpr int kFp32Variants = 6;
+constexpr int kFp32Variants = 8;
 
 struct TuneEntry {
   int variant;
@@ -347,9 +413,21 @@ void launch_fp32_variant(int v, const Geometry& g, const LK& lk, const float2* i
     float4* b = reinterpret_cast<float4*>(out);
     if (v == 4)
       wilson32rp_kernel<LK, 4><<<grid, 128, 0, s>>>(g, lk, a, b, c0, c1);
-    else
+    else if (v == 5)
       wilson32rp_kernel<LK, 3><<<grid, 128, 0, s>>>(g, lk, a, b, c0, c1);
+    else if (v == 6)
+      wilson32rs_kernel<LK, 4><<<grid, 128, rs_smem(g), s>>>(g, lk, a, b, c0, c1);
+    else
+      wilson32rs_kernel<LK, 3><<<grid, 128, rs_smem(g), s>>>(g, lk, a, b, c0, c1);
   }
+}
+
+// a forced variant where it applies: 4-7 need an even nrhs (else 2-3), 6-7
+// the tile geometry (else 4-5)
+int applicable_variant(int v, const Geometry& g, int nrhs) {
+  if (v >= 6 && !rs_applicable(g)) v -= 2;
+  if (v >= 4 && nrhs % 2 != 0) v = 2 + (v % 2);
+  return v;
 }
 
 // the variant for this key: forced, recorded, or tuned now (when the
@@ -360,7 +438,7 @@ int fp32_variant(const Geometry& g, const LK& lk, int bits, const float2* in, fl
   const int forced = g_variant_override.load();
   if (forced >= 0) {
     if (dot_partial != nullptr && forced >= 2) return 0;
-    return (forced >= 4 && nrhs % 2 != 0) ? forced - 2 : forced;
+    return applicable_variant(forced, g, nrhs);
   }
   const auto key = std::make_tuple(g.V, nrhs, bits, dot_partial != nullptr ? 1 : 0);
   {
@@ -375,8 +453,8 @@ int fp32_variant(const Geometry& g, const LK& lk, int bits, const float2* in, fl
     if (e0) cudaEventDestroy(e0);
     return 0;
   }
-  TuneEntry t{0, {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}};
-  const int nv = dot_partial != nullptr ? 2 : (nrhs % 2 == 0 ? kFp32Variants : 4);
+  TuneEntry t{0, {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f}};
+  const int nv = dot_partial != nullptr ? 2 : (nrhs % 2 == 0 ? (rs_applicable(g) ? kFp32Variants : 6) : 4);
   float best = 0.f;
   for (int v = 0; v < nv; ++v) {
     launch_fp32_variant(v, g, lk, in, out, nrhs, c0, c1, dot_partial, s);  // warm-up
@@ -406,7 +484,7 @@ int fp32_variant(const Geometry& g, const LK& lk, int bits, const float2* in, fl
 int wilson32_blocks(const Geometry& g) { return (g.V + 31) / 32; }
 
 int set_fp32_stencil_variant(int v) {
-  if (v < -1 || v >= kFp32Variants) return fail(SSQCD_ERR_ARG, "stencil variant must be -1 (tuned) or 0..5");
+  if (v < -1 || v >= kFp32Variants) return fail(SSQCD_ERR_ARG, "stencil variant must be -1 (tuned) or 0..7");
   g_variant_override.store(v);
   return SSQCD_OK;
 }

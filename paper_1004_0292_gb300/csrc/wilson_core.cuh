@@ -877,20 +877,36 @@ __device__ __forceinline__ C2 c2_row(const BcastLink& B, int a, const C2 (&h)[3]
   return C2{re, im};
 }
 
+// Where a hop reads its neighbour's components: global memory (component
+// comp of site nb at in + comp V + nb) or a shared-memory tile (sh + comp
+// stride + idx).
+struct SrcGlobal {
+  const float4* __restrict__ in;
+  int V, nb;
+  __device__ __forceinline__ C2 operator()(int comp) const { return c2_load(in + comp * V + nb); }
+};
+struct SrcShared {
+  const float4* sh;
+  int stride, idx;
+  __device__ __forceinline__ C2 operator()(int comp) const {
+    const float4 v = sh[comp * stride + idx];
+    return C2{pk2(v.x, v.y), pk2(v.z, v.w)};
+  }
+};
+
 // One hop (DIR +1: U_mu(x) psi(x + mu), h = psi_u - B psi_l, lower -B^H wv;
 // DIR -1: U_mu(x - mu)^H psi(x - mu), h = psi_u + B psi_l, lower +B^H wv)
 // of one rhs pair into acc[12] (FIRST: set instead of add).
-template <int MU, int DIR, bool FIRST>
-__device__ __forceinline__ void hop_rp(const BcastLink& B, const float4* __restrict__ in, int nb, int V, bool negate,
-                                       C2 (&acc)[12]) {
+template <int MU, int DIR, bool FIRST, typename SRC>
+__device__ __forceinline__ void hop_rp(const BcastLink& B, const SRC& src, bool negate, C2 (&acc)[12]) {
   using S = Spin<MU>;
   C2 h[2][3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    const C2 u0 = c2_load(in + (0 * 3 + a) * V + nb);
-    const C2 u1 = c2_load(in + (1 * 3 + a) * V + nb);
-    const C2 l0 = c2_load(in + ((2 + S::bcol0) * 3 + a) * V + nb);
-    const C2 l1 = c2_load(in + ((2 + S::bcol1) * 3 + a) * V + nb);
+    const C2 u0 = src(0 * 3 + a);
+    const C2 u1 = src(1 * 3 + a);
+    const C2 l0 = src((2 + S::bcol0) * 3 + a);
+    const C2 l1 = src((2 + S::bcol1) * 3 + a);
     // forward subtracts B psi_l: the code with its sign flipped (P1 <-> M1, PI <-> MI)
     h[0][a] = c2_add_unit(u0, DIR > 0 ? (S::bcode0 ^ 1) : S::bcode0, l0);
     h[1][a] = c2_add_unit(u1, DIR > 0 ? (S::bcode1 ^ 1) : S::bcode1, l1);
@@ -927,10 +943,28 @@ __device__ __forceinline__ void hop_rp_site(const LK& lk, const float4* __restri
   BcastLink B;
   load_bcast(lk, MU, DIR > 0 ? s : nb, DIR < 0, B);
   const bool neg = MU == 3 && w && g.bc_t < 0;
+  const SrcGlobal src{in, g.V, nb};
   if (first)
-    hop_rp<MU, DIR, true>(B, in, nb, g.V, neg, acc);
+    hop_rp<MU, DIR, true>(B, src, neg, acc);
   else
-    hop_rp<MU, DIR, false>(B, in, nb, g.V, neg, acc);
+    hop_rp<MU, DIR, false>(B, src, neg, acc);
+}
+
+// The same hop with the neighbour's spinor read from a shared-memory tile
+// (directions x and y only: no boundary sign).
+template <int MU, int DIR, typename LK>
+__device__ __forceinline__ void hop_rp_tile(const LK& lk, const float4* sh, int stride, int idx, int s,
+                                            const Coords& c, const Geometry& g, bool first, C2 (&acc)[12]) {
+  static_assert(MU < 2, "tile hops are the x and y directions");
+  bool w;
+  const int nb = neighbour<MU, DIR>(s, c, g, w);
+  BcastLink B;
+  load_bcast(lk, MU, DIR > 0 ? s : nb, DIR < 0, B);
+  const SrcShared src{sh, stride, idx};
+  if (first)
+    hop_rp<MU, DIR, true>(B, src, false, acc);
+  else
+    hop_rp<MU, DIR, false>(B, src, false, acc);
 }
 
 }  // namespace wcore

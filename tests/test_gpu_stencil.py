@@ -96,12 +96,13 @@ def test_mixed_stencil_matches_oracle_on_fp16_links(ss, dims, kind, bc):
 @pytest.mark.parametrize("dims,nrhs,bc", [((16, 16, 16, 32), 8, -1), ((5, 3, 4, 6), 3, 1), ((33, 1, 2, 2), 1, -1)])
 def test_mixed_stencil_all_rhs_kernel(ss, dims, nrhs, bc):
     """The FP32 stencil variants that share each link load among several
-    rhs (paired FP32 arithmetic; the rhs-pair variants 4-5 with two rhs in
-    the lanes, between layout conversions): every variant and every rhs
-    against the oracle on the FP16-rounded links, at the 16^3 x 32 size of
-    the stencil measurement with 8 rhs, an odd lattice with an odd rhs count
-    (variants 4-5 fall back to 2-3), and a ragged last block (V = 132 =
-    4 x 32 + 4)."""
+    rhs (paired FP32 arithmetic; the rhs-pair variants 4-7 with two rhs in
+    the lanes, between layout conversions, 6-7 with the x-y plane staged in
+    shared memory): every variant and every rhs against the oracle on the
+    FP16-rounded links, at the 16^3 x 32 size of the stencil measurement
+    with 8 rhs (8 x-lines of 16 a tile), an odd lattice with an odd rhs
+    count (variants 4-7 fall back to 2-3), and a ragged last block (V = 132
+    = 4 x 32 + 4, where 6-7 fall back to 4-5)."""
     kappa = 0.135
     U = synthetic.gauge_field(dims, "smooth", seed=5, eps=0.5)
     psi = synthetic.gaussian_sources(dims, nrhs, seed=6)
@@ -109,7 +110,7 @@ def test_mixed_stencil_all_rhs_kernel(ss, dims, nrhs, bc):
     ss.upload_gauge(lat, U)
     ref16 = wilson.apply_H(fp16_rounded_links(U), psi, kappa, dims, bc)
     try:
-        for variant in (0, 1, 2, 3, 4, 5):
+        for variant in (0, 1, 2, 3, 4, 5, 6, 7):
             ss.set_stencil_variant(variant)
             got = ss.apply_H_mixed(lat, psi)
             for r in range(nrhs):
@@ -121,8 +122,9 @@ def test_mixed_stencil_all_rhs_kernel(ss, dims, nrhs, bc):
     got = ss.apply_H_mixed(lat, psi)
     chosen, us = ss.stencil_tuning(lat, nrhs)
     timed = [t for t in us if t > 0]
-    assert len(timed) == (6 if nrhs % 2 == 0 else 4)
-    assert 0 <= chosen <= 5 and us[chosen] == min(timed)
+    tiled = 128 % dims[0] == 0 and dims[1] % (128 // dims[0]) == 0
+    assert len(timed) == ((8 if tiled else 6) if nrhs % 2 == 0 else 4)
+    assert 0 <= chosen <= 7 and us[chosen] == min(timed)
     assert np.max(np.abs(got - ref16)) <= 2e-6 * np.max(np.abs(ref16))
     with pytest.raises(ss.SsqcdError):
-        ss.set_stencil_variant(7)
+        ss.set_stencil_variant(8)
