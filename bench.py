@@ -344,6 +344,19 @@ def run_ours(args):
                                         "seed_direction": 1e3 * sum(x["ms_k_scalars"] for x in s_m) / it_m,
                                         "timed_iterations": it_m},
         }
+        # the float-float arm's dominant kernel: its stencil (one rhs a launch)
+        sten_us_m = 1e3 * sum(x["ms_k_stencil"] for x in s_m) / it_m
+        sten_gbs_m = V * (Lb * 2 * 192 + 576) / (sten_us_m * 1e-6) / 1e9 if sten_us_m > 0 else None
+        mixed["stencil"] = {
+            "kernel": "cg_stencil_kernel<StencilDF<4>> (q = K p in float-float with the (p, q) partials; 32 "
+                      "sites and 8 warps, one hop each, a block)",
+            "bound": "FP32 issue and latency (float-float chains; the FP32 pipes run at 64x the FP64 rate)",
+            "avg_launch_us": sten_us_m, "rhs_per_launch": Lb, "hbm_achieved_gbs": sten_gbs_m,
+            "hbm_frac": sten_gbs_m / peaks["hbm_gbs"] if sten_gbs_m else None,
+            "note": "algorithmic bytes 192 in + 192 out + 576 links (float-float, 16 B a complex element) a "
+                    "site; profiles/stencil_floatfloat_16x16x16x32.md",
+            "share_of_step": (sten_us_m * p_m[-1]["iterations"] * w["L"] / Lb) / 1e3 / (ms_m / args.steps),
+        }
         del lat_m
 
     config2 = None
