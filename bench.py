@@ -559,14 +559,15 @@ def run_update_form(step, stream, flush, args, n, world):
 STENCIL_LARGE = dict(dims=(16, 16, 16, 32), kappa=0.135, eps=0.5, gauge_seed=4, rhs=8, reps=20)
 
 
-def run_stencil_large(ss, stream, peaks):
+def run_stencil_large(ss, stream, peaks, rhs=None):
     """The stencil alone on the mixed-path lattice shape (16^3 x 32, 8
-    right-hand sides, smooth links eps 0.5, kappa 0.135) where its data no
-    longer fits in L2: FP64, float-float and FP32 spinors with FP16 / FP32
-    12-parameter links.  Algorithmic bytes per application: spinors in and
-    out for every rhs plus the links once (shared by the rhs)."""
+    right-hand sides unless ``rhs`` says otherwise, smooth links eps 0.5,
+    kappa 0.135) where its data no longer fits in L2: FP64, float-float and
+    FP32 spinors with FP16 / FP32 12-parameter links.  Algorithmic bytes per
+    application: spinors in and out for every rhs plus the links once
+    (shared by the rhs)."""
     import synthetic
-    c = STENCIL_LARGE
+    c = dict(STENCIL_LARGE) if rhs is None else dict(STENCIL_LARGE, rhs=int(rhs))
     U = synthetic.gauge_field(c["dims"], "smooth", seed=c["gauge_seed"], eps=c["eps"])
     V = int(np.prod(c["dims"]))
     out = {"lattice": "x".join(map(str, c["dims"])), "rhs": c["rhs"],
@@ -1104,7 +1105,7 @@ def run_only(args):
     peaks = _measured_peaks()
     if args.only == "stencil_large":
         ss.set_stencil_variant(args.stencil_variant)
-        out = run_stencil_large(ss, stream, peaks)
+        out = run_stencil_large(ss, stream, peaks, rhs=args.stencil_rhs)
     elif args.only == "batched_uneven":
         out = run_batched_uneven(ss, stream)
     elif args.only.startswith("beta_study"):
@@ -1129,6 +1130,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end (host buffers) leg")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--cpu-budget", type=float, default=30.0)
+    ap.add_argument("--stencil-rhs", type=int, default=None, help="right-hand sides of stencil_large (default 8)")
     ap.add_argument("--stencil-variant", type=int, default=-1,
                     help="FP32 stencil variant for stencil_large (0..7; -1: the autotuner's choice)")
     ap.add_argument("--only", choices=["stencil_large", "config2", "beta_study", "beta_study_16x32", "batched_uneven"],

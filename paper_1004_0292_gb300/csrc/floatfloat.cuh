@@ -243,13 +243,13 @@ __device__ __forceinline__ cff p_dot(const f32x2_t (&ah)[K], const f32x2_t (&al)
 // (re h_b, im h_b), term 2b + 1 pairs (-im u_b, im u_b) (conj: (im u_b,
 // -im u_b)) with (im h_b, re h_b) -- the factors of dot<6> in cdot3 for the
 // real part (lane 0) and the imaginary part (lane 1).
-template <bool CONJ>
-__device__ __forceinline__ cff p_cdot3_impl(cff u0, cff u1, cff u2, cff h0, cff h1, cff h2) {
+// sg = -1: sum_b u_b h_b; sg = +1: sum_b conj(u_b) h_b (the direction of
+// a hop may pick the sign at run time: the operations are the same)
+__device__ __forceinline__ cff p_cdot3_sg(cff u0, cff u1, cff u2, cff h0, cff h1, cff h2, float sg) {
   const cff u[3] = {u0, u1, u2}, h[3] = {h0, h1, h2};
   f32x2_t ah[6], al[6], bh[6], bl[6];
 #pragma unroll
   for (int b = 0; b < 3; ++b) {
-    const float sg = CONJ ? 1.f : -1.f;
     ah[2 * b] = pk2(u[b].x, u[b].x);
     al[2 * b] = pk2(u[b].z, u[b].z);
     ah[2 * b + 1] = pk2(sg * u[b].y, -sg * u[b].y);
@@ -262,10 +262,10 @@ __device__ __forceinline__ cff p_cdot3_impl(cff u0, cff u1, cff u2, cff h0, cff 
   return p_dot<6>(ah, al, bh, bl);
 }
 __device__ __forceinline__ cff p_cdot3(cff u0, cff u1, cff u2, cff h0, cff h1, cff h2) {
-  return p_cdot3_impl<false>(u0, u1, u2, h0, h1, h2);
+  return p_cdot3_sg(u0, u1, u2, h0, h1, h2, -1.f);
 }
 __device__ __forceinline__ cff p_cdot3_conj(cff u0, cff u1, cff u2, cff h0, cff h1, cff h2) {
-  return p_cdot3_impl<true>(u0, u1, u2, h0, h1, h2);
+  return p_cdot3_sg(u0, u1, u2, h0, h1, h2, 1.f);
 }
 
 // c + u v for complex float-float c, v and a coefficient u given as its four

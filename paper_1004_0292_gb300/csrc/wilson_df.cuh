@@ -35,46 +35,56 @@ struct LinksDF {
 // instruction, floatfloat.cuh), bit-identical to the scalar form.
 constexpr int kStencilThreadsDF = 256;
 
-template <int MU, int DIR>
-__device__ __forceinline__ void hop_one_df(const LinksDF& lk, const float4* __restrict__ in, int s, const Coords& c,
-                                           const Geometry& g, float4* __restrict__ out) {
-  using S = Spin<MU>;
+// One hop of warp 2 mu + d at site s: h = (1 -/+ gamma_mu) psi(x +/- mu) in
+// the two-spinor form h_r = psi_r + c_r psi_{bcol_r} (c_r the unit factor
+// of B_mu's row r, negated on the forward hop: exact), then U_mu(x) h by
+// rows (forward) or U_mu(x - mu)^H h by conjugated columns (backward).  The
+// direction is a run-time value, so the eight warps of a block share one
+// instruction stream: with a compile-time copy per direction the kernel's
+// code outgrew the instruction cache and warps waited on instruction fetch
+// ("no instruction" the first stall reason in ncu, 6.4 cycles per issue at
+// one rhs).
+__device__ __forceinline__ void hop_one_df_rt(const LinksDF& lk, const float4* __restrict__ in, int s,
+                                              const Coords& c, const Geometry& g, int mu, bool fwd,
+                                              float4* __restrict__ out) {
   const int V = g.V;
-  bool w;
-  const int nb = neighbour<MU, DIR>(s, c, g, w);
+  const int coord = mu == 0 ? c.x : mu == 1 ? c.y : mu == 2 ? c.z : c.t;
+  const int ext = mu == 0 ? g.X : mu == 1 ? g.Y : mu == 2 ? g.Z : g.T;
+  const int st = mu == 0 ? 1 : mu == 1 ? g.X : mu == 2 ? g.X * g.Y : g.X * g.Y * g.Z;
+  const bool wrap = fwd ? coord == ext - 1 : coord == 0;
+  const int nb = fwd ? (wrap ? s - (ext - 1) * st : s + st) : (wrap ? s + (ext - 1) * st : s - st);
+  // Spin<mu>: lower-spin column and unit factor of B_mu's two rows
+  constexpr int bcol[4] = {Spin<0>::bcol0, Spin<1>::bcol0, Spin<2>::bcol0, Spin<3>::bcol0};
+  constexpr int bcode[2][4] = {{Spin<0>::bcode0, Spin<1>::bcode0, Spin<2>::bcode0, Spin<3>::bcode0},
+                               {Spin<0>::bcode1, Spin<1>::bcode1, Spin<2>::bcode1, Spin<3>::bcode1}};
+  const int bcol0 = bcol[mu], bcol1 = 1 - bcol0;
+  const int bc0 = bcode[0][mu], bc1 = bcode[1][mu];
+  // (1 - gamma_mu): h = psi_u - B psi_l, the unit factor's sign flipped
+  const int code0 = fwd ? (bc0 ^ 1) : bc0, code1 = fwd ? (bc1 ^ 1) : bc1;
+  const bool negate = mu == 3 && wrap && g.bc_t < 0;
   float4 h[2][3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     const float4 u0 = __ldg(in + (0 * 3 + a) * V + nb);
     const float4 u1 = __ldg(in + (1 * 3 + a) * V + nb);
-    const float4 l0 = __ldg(in + ((2 + S::bcol0) * 3 + a) * V + nb);
-    const float4 l1 = __ldg(in + ((2 + S::bcol1) * 3 + a) * V + nb);
-    if (DIR > 0) {  // (1 - gamma_mu): h = psi_u - B psi_l
-      h[0][a] = ff::p_csub(u0, ff::unit_mul(S::bcode0, l0));
-      h[1][a] = ff::p_csub(u1, ff::unit_mul(S::bcode1, l1));
-    } else {  // (1 + gamma_mu): h = psi_u + B psi_l
-      h[0][a] = ff::p_cadd(u0, ff::unit_mul(S::bcode0, l0));
-      h[1][a] = ff::p_cadd(u1, ff::unit_mul(S::bcode1, l1));
-    }
-  }
-  if (MU == 3 && w && g.bc_t < 0) {
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
+    const float4 l0 = __ldg(in + ((2 + bcol0) * 3 + a) * V + nb);
+    const float4 l1 = __ldg(in + ((2 + bcol1) * 3 + a) * V + nb);
+    h[0][a] = ff::p_cadd(u0, ff::unit_mul(code0, l0));
+    h[1][a] = ff::p_cadd(u1, ff::unit_mul(code1, l1));
+    if (negate) {
       h[0][a] = ff::cneg(h[0][a]);
       h[1][a] = ff::cneg(h[1][a]);
     }
   }
+  const float sg = fwd ? -1.f : 1.f;  // conjugated link columns on the backward hop
+  const int ls = fwd ? s : nb;
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    if (DIR > 0) {  // U_mu(x) h: row a
-      const float4 ua0 = lk.get(MU, a, 0, s), ua1 = lk.get(MU, a, 1, s), ua2 = lk.get(MU, a, 2, s);
-      out[(0 * 3 + a) * 32] = ff::p_cdot3(ua0, ua1, ua2, h[0][0], h[0][1], h[0][2]);
-      out[(1 * 3 + a) * 32] = ff::p_cdot3(ua0, ua1, ua2, h[1][0], h[1][1], h[1][2]);
-    } else {  // U_mu(x - mu)^H h: column a, conjugated
-      const float4 u0a = lk.get(MU, 0, a, nb), u1a = lk.get(MU, 1, a, nb), u2a = lk.get(MU, 2, a, nb);
-      out[(0 * 3 + a) * 32] = ff::p_cdot3_conj(u0a, u1a, u2a, h[0][0], h[0][1], h[0][2]);
-      out[(1 * 3 + a) * 32] = ff::p_cdot3_conj(u0a, u1a, u2a, h[1][0], h[1][1], h[1][2]);
-    }
+    const float4 w0 = lk.get(mu, fwd ? a : 0, fwd ? 0 : a, ls);
+    const float4 w1 = lk.get(mu, fwd ? a : 1, fwd ? 1 : a, ls);
+    const float4 w2 = lk.get(mu, fwd ? a : 2, fwd ? 2 : a, ls);
+    out[(0 * 3 + a) * 32] = ff::p_cdot3_sg(w0, w1, w2, h[0][0], h[0][1], h[0][2], sg);
+    out[(1 * 3 + a) * 32] = ff::p_cdot3_sg(w0, w1, w2, h[1][0], h[1][1], h[1][2], sg);
   }
 }
 
@@ -116,16 +126,7 @@ __device__ __forceinline__ void block_hops_df8(const LinksDF& lk, const float4* 
   float4* out = sh + (size_t)w * 6 * 32 + lane;
   if (s < g.V) {
     const Coords c = site_coords(s, g);
-    switch (w) {
-      case 0: hop_one_df<0, +1>(lk, in, s, c, g, out); break;
-      case 1: hop_one_df<0, -1>(lk, in, s, c, g, out); break;
-      case 2: hop_one_df<1, +1>(lk, in, s, c, g, out); break;
-      case 3: hop_one_df<1, -1>(lk, in, s, c, g, out); break;
-      case 4: hop_one_df<2, +1>(lk, in, s, c, g, out); break;
-      case 5: hop_one_df<2, -1>(lk, in, s, c, g, out); break;
-      case 6: hop_one_df<3, +1>(lk, in, s, c, g, out); break;
-      default: hop_one_df<3, -1>(lk, in, s, c, g, out); break;
-    }
+    hop_one_df_rt(lk, in, s, c, g, w >> 1, (w & 1) == 0, out);  // warp 2 mu + d: direction mu, d = 0 forward
   } else {
 #pragma unroll
     for (int k = 0; k < 6; ++k) out[k * 32] = make_float4(0.f, 0.f, 0.f, 0.f);
