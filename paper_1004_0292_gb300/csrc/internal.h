@@ -239,6 +239,17 @@ int basis_moments(const KrylovBasis& b, const double2* coef_host, int M, double2
 // throughout, for comparison)
 bool real_moments_enabled();
 
+// The moment combination on the tensor cores (combine_tc.cu): FP64 residuals
+// (tab: the basis block table, 2^basis_log slots a block, [slot][L][n]),
+// real coefficients C[l][o][s] (.x), O <= 16 outputs, out[l][o][n] for the
+// sources l0 .. l0 + nl - 1; work: combine_tc_work_bytes(nl, S) bytes.
+// Synchronises st (reads the kernel's error word).
+bool combine_tc_enabled();
+bool combine_tc_applicable(long long n, int O, int S);
+size_t combine_tc_work_bytes(int nl, int S);
+int combine_tc(char* const* tab, int basis_log, long long n, int L, const double2* C, int O, int S,
+               const int* count, double2* out, int l0, int nl, void* work, cudaStream_t st);
+
 // Solves for L sources already packed on device (v: [L][12][V]); y out
 // [L][N][12][V] (device, FP64).  iters/xi: host arrays [L*N] (may be null).
 // A resumable shifted-CG run (mshift.cu): see CgRun there.

@@ -2703,16 +2703,22 @@ int basis_moments(const KrylovBasis& b, const double2* coef_host, int M, double2
   const int N = b.N, L = b.L, S = b.S;
   const size_t w_bytes = (sizeof(double2) * (size_t)N * M + 255) / 256 * 256;
   const long long cnt = (long long)L * M * S;
+  const bool rc = real_coef && real_moments_enabled();
+  // FP64 residuals with real coefficients: the tensor-core combination
+  // (unless SSQCD_MOMENTS_TC=0), one source a launch, each with its work space
+  const bool tc = !b.df && rc && combine_tc_enabled() && combine_tc_applicable(b.n, M, S);
+  const size_t g_bytes = (sizeof(double2) * (size_t)cnt + (b.df ? sizeof(float2) * (size_t)cnt : 0) + 255) / 256 * 256;
+  const size_t tc_src = tc ? (combine_tc_work_bytes(1, S) + 255) / 256 * 256 : 0;
   // W, G and (float-float residuals) Re G as float-float pairs
-  SS_TRY(scratch.alloc(w_bytes + sizeof(double2) * (size_t)cnt + (b.df ? sizeof(float2) * (size_t)cnt : 0)));
+  SS_TRY(scratch.alloc(w_bytes + g_bytes + tc_src * (size_t)L));
   double2* W = scratch.as<double2>();
   double2* G = reinterpret_cast<double2*>(scratch.as<char>() + w_bytes);
   float2* Gr = reinterpret_cast<float2*>(G + cnt);
+  char* tcw = scratch.as<char>() + w_bytes + g_bytes;
   SS_CUDA(cudaMemcpyAsync(W, coef_host, sizeof(double2) * (size_t)N * M, cudaMemcpyHostToDevice, st));
   basis_window_kernel<<<(unsigned)((cnt + 255) / 256), 256, 0, st>>>(b.gam.as<double2>(), W, N, M, L, S, G);
   SS_CHECK_LAUNCH();
   count_launches(1);
-  const bool rc = real_coef && real_moments_enabled();
   if (b.df && rc) {
     coef_real_to_ff_kernel<<<(unsigned)((cnt + 255) / 256), 256, 0, st>>>(G, cnt, Gr);
     SS_CHECK_LAUNCH();
@@ -2752,6 +2758,12 @@ int basis_moments(const KrylovBasis& b, const double2* coef_host, int M, double2
             <<<grid, kCombThreads, 0, s>>>(tab, b.n, L, G, Gr, M, S, count, s_hat, l0);
       SS_CHECK_LAUNCH();
       count_launches(1);
+      return SSQCD_OK;
+    }
+    if (tc) {
+      for (int l = l0; l < l0 + nl; ++l)
+        SS_TRY(combine_tc(b.tab.as<char*>(), kBasisLog, b.n, L, G, M, S, b.count.as<int>(), s_hat, l, 1,
+                          tcw + tc_src * (size_t)l, s));
       return SSQCD_OK;
     }
     return launch_combine<double2, double2>(b.tab.as<char*>(), b.n, L, G, M, S, b.count.as<int>(), s_hat, s, l0,
