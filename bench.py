@@ -220,6 +220,45 @@ def moments_flops(w, st, n):
     return per * len(w["windows"]) * w["M"] * (st["iterations"] + 1) * n * w["L"]
 
 
+def moments_roofline(w, st, n, mom_tf, step_ms, peaks):
+    """Roofline line of the moment combination.  With real coefficients and
+    FP64 residuals it runs on the tensor cores (combine_tc_kernel, unless
+    SSQCD_MOMENTS_TC=0): exact bf16 slices, so its roof is reading the
+    stored residuals once (16 B a complex element and slot, each window);
+    the phase also holds the scale pass, which reads them once more a
+    window.  Otherwise the FP64-pipe kernel, bound by the FP64 rate."""
+    tc = bool(st.get("real_moments")) and os.environ.get("SSQCD_MOMENTS_TC", "1") != "0"
+    if tc:
+        nbytes = 16.0 * len(w["windows"]) * (st["iterations"] + 1) * n * w["L"]
+        gbs = nbytes / (st["ms_moments"] / 1e3) / 1e9
+        return {
+            "kernel": "combine_tc_kernel (moments on the tensor cores: the FP64 residuals and real coefficients "
+                      "cut exactly into seven 8-bit bf16 slices, 28 slice-pair tcgen05.mma into tensor memory, "
+                      "exact integer sums; with its scale pass, one read of the residuals more)",
+            "bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": gbs / peaks["hbm_gbs"], "traffic": None,
+            "traffic_note": "no ncu capture of this kernel; algorithmic bytes: each stored residual read once "
+                            "a window (windows x slots x n x 16 B a source)",
+            "fp64_equivalent_tflops": mom_tf,
+            "fp64_equivalent_note": "4 flop a term (real coefficient times complex element) over the phase time, "
+                                    "against the FP64 pipe's 1.259 TFLOP/s",
+            "phase_ms": st["ms_moments"], "fraction_of_step": st["ms_moments"] / step_ms,
+        }
+    return {
+        "kernel": "basis_combine_kernel (moments from the stored seed residuals, FP64; the moments phase, "
+                  "whose other kernels are the small coefficient recurrences)",
+        "bound": "alu", "achieved": mom_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+        "frac": mom_tf / FP64_PEAK_TFLOPS, "traffic": COMBINE_TRAFFIC,
+        "traffic_note": "bytes per launch (one window, one block of 2 sources: each residual read "
+                        "once, 2 x 2499 x 1572864 x 16 B = 125.8 GB, and 32 moments written, 0.8 GB; "
+                        "profiles/combine_fp64_16x16x16x32.md); the headline runs one source a launch",
+        "flop_count": ("4 per term: real coefficients (conjugate-pair points), a real times a complex "
+                       "residual element, 2 FMA" if st.get("real_moments") else
+                       "8 per complex multiply-add (the kernel issues 3 real multiplications per product)"),
+        "phase_ms": st["ms_moments"], "fraction_of_step": st["ms_moments"] / step_ms,
+    }
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -273,7 +312,7 @@ def run_ours(args):
     _, _, stats, _ = timed_steps(lambda: windows_step(ss, lat, src_d, w_kt), flush, stream, KERNEL_TIMING_STEPS)
     ss.set_kernel_timing(False)
 
-    # ---- roofline of the dominant kernel: the FP64 moment combination ----
+    # ---- rooflines: the moment combination and the stencil ----
     last = plain[-1]
     mflops = moments_flops(w, last, n)
     mom_tf = mflops / (last["ms_moments"] / 1e3) / 1e12
@@ -419,19 +458,7 @@ def run_ours(args):
                 "share_of_step": (ms_sten / max(1, it_tot) * last["iterations"] * w["L"] / Lb)
                                  / (total_ms / args.steps),
             },
-            "moments_roofline": {
-                "kernel": "basis_combine_kernel (moments from the stored seed residuals, FP64; the moments phase, "
-                          "whose other kernels are the small coefficient recurrences)",
-                "bound": "alu", "achieved": mom_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": mom_tf / FP64_PEAK_TFLOPS, "traffic": COMBINE_TRAFFIC,
-                "traffic_note": "bytes per launch (one window, one block of 2 sources: each residual read "
-                                "once, 2 x 2499 x 1572864 x 16 B = 125.8 GB, and 32 moments written, 0.8 GB; "
-                                "profiles/combine_fp64_16x16x16x32.md); the headline runs one source a launch",
-                "flop_count": ("4 per term: real coefficients (conjugate-pair points), a real times a complex "
-                               "residual element, 2 FMA" if last.get("real_moments") else
-                               "8 per complex multiply-add (the kernel issues 3 real multiplications per product)"),
-                "phase_ms": last["ms_moments"], "fraction_of_step": last["ms_moments"] / (total_ms / args.steps),
-            },
+            "moments_roofline": moments_roofline(w, last, n, mom_tf, total_ms / args.steps, peaks),
             "kernel_us_per_iteration": {"stencil": 1e3 * ms_sten / max(1, it_tot),
                                         "seed_update": 1e3 * sum(s["ms_k_seed"] for s in stats) / max(1, it_tot),
                                         "seed_direction": 1e3 * sum(s["ms_k_scalars"] for s in stats) / max(1, it_tot),
