@@ -205,7 +205,15 @@ typedef struct {
                              scalars are real, so each pair's coefficients
                              are conjugate and sum to a real number; 0: complex
                              coefficients (circle points, shift-vector updates,
-                             or SSQCD_REAL_MOMENTS=0 in the environment)      */
+                             or SSQCD_REAL_MOMENTS=0 in the environment).
+                             With real coefficients and FP64 residuals the
+                             combination runs on the tensor cores: residuals
+                             and coefficients are split exactly into seven
+                             8-bit bf16 slices on power-of-two grids and the
+                             slice products summed exactly, so the moments
+                             lie within 2^-56 of the operand scales of the
+                             FP64 sum (SSQCD_MOMENTS_TC=0 in the environment:
+                             the FP64-pipe combination instead)              */
 } ssqcd_stats;
 
 /* ---- lattice / operator ---------------------------------------------------- */
