@@ -5,6 +5,7 @@
 // copy of the same integer arithmetic (the 56-bit fixed-point digits, the
 // exact slice-pair sums, the same final FP64 combination), and lie within a
 // few units of 2^-52 of the long-double sum.  Prints "checks: passed".
+// With --time it times the combination on a half-size headline window.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -206,8 +207,68 @@ static int run_check(const Case& c) {
   return nbad == 0 && worst < 1e-13 ? 0 : 1;
 }
 
-int main() {
+// --time: one window of the headline size (2502 slots of 786,432 complex
+// elements, 31.5 GB, 16 moments), best of three after a warm-up
+__global__ void fill_kernel(double* p, long long count, unsigned long long seed, double scale) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count; i += (long long)gridDim.x * blockDim.x) {
+    unsigned long long z = (i + 1) * 0x9E3779B97F4A7C15ull ^ seed;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    p[i] = scale * ((double)(z >> 11) * (1.0 / 9007199254740992.0) - 0.5);
+  }
+}
+
+static int run_timing(long long n, int S) {
+  const int nblk = (S + kBlk - 1) / kBlk;
+  std::vector<char*> blocks(nblk);
+  for (int b = 0; b < nblk; ++b) {
+    if (cudaMalloc(&blocks[b], (size_t)kBlk * n * 16) != cudaSuccess) {
+      printf("timing: allocation failed\n");
+      return 2;
+    }
+    fill_kernel<<<1024, 256>>>(reinterpret_cast<double*>(blocks[b]), (long long)kBlk * 2 * n, b, std::pow(10.0, -8.0 * b / nblk));
+  }
+  char** tab;
+  cudaMalloc(&tab, sizeof(char*) * nblk);
+  cudaMemcpy(tab, blocks.data(), sizeof(char*) * nblk, cudaMemcpyHostToDevice);
+  std::vector<double2> Ch((size_t)16 * S);
+  for (auto& v : Ch) v = make_double2(urand() - 0.5, 0.0);
+  double2 *Cd, *out;
+  int* count;
+  cudaMalloc(&Cd, sizeof(double2) * Ch.size());
+  cudaMemcpy(Cd, Ch.data(), sizeof(double2) * Ch.size(), cudaMemcpyHostToDevice);
+  cudaMalloc(&count, sizeof(int));
+  cudaMemcpy(count, &S, sizeof(int), cudaMemcpyHostToDevice);
+  cudaMalloc(&out, sizeof(double2) * 16 * n);
+  void* work;
+  cudaMalloc(&work, ssqcd::combine_tc_work_bytes(1, S));
+  cudaStream_t st;
+  cudaStreamCreate(&st);
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  int rc = ssqcd::combine_tc(tab, kLog, n, 1, Cd, 16, S, count, out, 0, 1, work, st);  // warm-up
+  float best = 1e30f;
+  for (int it = 0; it < 3 && rc == 0; ++it) {
+    cudaEventRecord(e0, st);
+    rc = ssqcd::combine_tc(tab, kLog, n, 1, Cd, 16, S, count, out, 0, 1, work, st);
+    cudaEventRecord(e1, st);
+    cudaEventSynchronize(e1);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    best = std::fmin(best, ms);
+  }
+  const double gb = (double)S * n * 16 / 1e9;
+  printf("timing n=%lld S=%d (%.1f GB of residuals): status %d, %.2f ms (incl. scale pass and host sync), %.0f GB/s\n",
+         n, S, gb, rc, best, gb / (best / 1e3));
+  for (auto b : blocks) cudaFree(b);
+  return rc;
+}
+
+int main(int argc, char** argv) {
   cudaFree(0);
+  if (argc > 1 && std::strcmp(argv[1], "--time") == 0) return run_timing(786432, 2502);
   int bad = 0;
   bad |= run_check(Case{64 * 40, 1, 300, 16, 300, 0});
   bad |= run_check(Case{64 * 20, 3, 48, 5, 37, 1});
