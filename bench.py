@@ -13,7 +13,10 @@ Rayleigh-Ritz, acceptance, eigenpair readback):
   clusters of its sign, 48 eigenpairs in all.  The sources run one at a
   time (opts.source_block = 1), two such runs side by side on their own
   streams (opts.block_streams = 2), so that the stored seed residuals of the
-  two fit the device memory; FP64 throughout ("plain").
+  two fit the device memory; FP64 throughout ("plain"), the moment
+  combination on the tensor cores through an exact bf16 splitting of the
+  FP64 operands (as accurate as the FP64 sum; SSQCD_MOMENTS_TC=0 runs it
+  on the FP64 pipe).
 
 ``value`` counts accepted eigenpairs with residual <= 1e-8 per second of
 device time (inputs resident, CUDA events on the library's stream; the
