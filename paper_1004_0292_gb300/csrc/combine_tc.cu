@@ -254,18 +254,29 @@ __global__ void tc_maxabs_kernel(char* const* __restrict__ tab, int basis_log, l
   if (s >= count[l]) return;
   const double2* r = reinterpret_cast<const double2*>(slot_ptr(tab, basis_log, n, L, l, s));
   double m = 0.0;
+  bool bad = false;  // a NaN or infinity (fmax would drop a NaN)
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
     const double2 v = r[e];
+    bad |= !isfinite(v.x) || !isfinite(v.y);
     m = fmax(m, fmax(fabs(v.x), fabs(v.y)));
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  bad = __any_sync(0xffffffffu, bad);
   __shared__ double wm[32];
-  if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = m;
+  __shared__ int wb[32];
+  if ((threadIdx.x & 31) == 0) {
+    wm[threadIdx.x >> 5] = m;
+    wb[threadIdx.x >> 5] = bad ? 1 : 0;
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
-    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, wm[w]);
-    atomicMax(mx + (size_t)lz * S + s, (unsigned long long)__double_as_longlong(m));
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+      m = fmax(m, wm[w]);
+      bad |= wb[w] != 0;
+    }
+    // a non-finite element marks the slot with +infinity (above every finite bit pattern)
+    atomicMax(mx + (size_t)lz * S + s, bad ? 0x7FF0000000000000ull : (unsigned long long)__double_as_longlong(m));
   }
 }
 
@@ -277,26 +288,46 @@ __device__ __forceinline__ int exp_above(double x) {
 }
 
 // e[l'][s] (slot scales) and sig[l'][o] = 2^g_o >= max_s |C[l][o][s] 2^e_s|;
-// one block of 256 threads per (source, output)
+// one block of 256 threads per (source, output).  A non-finite residual
+// element or coefficient makes sig NaN, so that the outputs of that source
+// come out NaN as the FP64 sum's would (the slices themselves stay finite).
 __global__ void tc_scales_kernel(const unsigned long long* __restrict__ mx, const double2* __restrict__ C, int O,
                                  int S, int l0, const int* __restrict__ count, int* __restrict__ eslot,
                                  double* __restrict__ sig) {
   const int lz = blockIdx.x / kOut, o = blockIdx.x % kOut, l = l0 + lz;
   const int cnt = count[l];
   double m = 0.0;
+  bool bad = false;
   for (int s = threadIdx.x; s < cnt; s += blockDim.x) {
-    const int e = exp_above(__longlong_as_double((long long)mx[(size_t)lz * S + s]));
+    const double ms = __longlong_as_double((long long)mx[(size_t)lz * S + s]);
+    const bool fin = isfinite(ms);
+    const int e = fin ? exp_above(ms) : 0;
+    bad |= !fin;
     if (o == 0) eslot[(size_t)lz * S + s] = e;
-    if (o < O) m = fmax(m, fabs(ldexp(C[((size_t)l * O + o) * S + s].x, e)));
+    if (o < O) {
+      const double c = C[((size_t)l * O + o) * S + s].x;
+      bad |= !isfinite(c);
+      if (isfinite(c)) m = fmax(m, fabs(ldexp(c, e)));
+    }
   }
 #pragma unroll
   for (int d = 16; d > 0; d >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, d));
+  bad = __any_sync(0xffffffffu, bad);
   __shared__ double wm[32];
-  if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = m;
+  __shared__ int wb[32];
+  if ((threadIdx.x & 31) == 0) {
+    wm[threadIdx.x >> 5] = m;
+    wb[threadIdx.x >> 5] = bad ? 1 : 0;
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
-    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, wm[w]);
-    sig[(size_t)lz * kOut + o] = ldexp(1.0, exp_above(m));
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+      m = fmax(m, wm[w]);
+      bad |= wb[w] != 0;
+    }
+    // every output of the source: a bad slot of this source poisons them all
+    sig[(size_t)lz * kOut + o] = (bad || !isfinite(m)) ? __longlong_as_double(0x7FF8000000000000ll)
+                                                       : ldexp(1.0, exp_above(m));
   }
 }
 

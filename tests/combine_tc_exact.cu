@@ -4,7 +4,8 @@
 // random real coefficients; the device result must equal, bit for bit, a CPU
 // copy of the same integer arithmetic (the 56-bit fixed-point digits, the
 // exact slice-pair sums, the same final FP64 combination), and lie within a
-// few units of 2^-52 of the long-double sum.  Prints "checks: passed".
+// few units of 2^-52 of the long-double sum; a NaN in a residual must make
+// the outputs of its source NaN.  Prints "checks: passed".
 // With --time it times the combination on a half-size headline window.
 #include <cuda_runtime.h>
 
@@ -207,6 +208,50 @@ static int run_check(const Case& c) {
   return nbad == 0 && worst < 1e-13 ? 0 : 1;
 }
 
+// A NaN in one element of one slot: every output of that source is NaN
+// (the tensor-core path marks the source through its scales; the FP64 sum
+// would give NaN in the rows that element reaches).
+static int run_nan_check() {
+  const long long n = 64 * 4;
+  const int S = 32, cnt = 20, O = 16;
+  std::vector<double> h((size_t)2 * n * 16);
+  for (auto& v : h) v = urand() - 0.5;
+  std::vector<char*> blocks(2);
+  for (int b = 0; b < 2; ++b) {
+    if (cudaMalloc(&blocks[b], (size_t)16 * n * 16) != cudaSuccess) return 2;
+    cudaMemcpy(blocks[b], h.data(), (size_t)16 * n * 16, cudaMemcpyHostToDevice);
+  }
+  const double nan = std::nan("");
+  cudaMemcpy(reinterpret_cast<double*>(blocks[0] + (size_t)3 * n * 16) + 77, &nan, 8, cudaMemcpyHostToDevice);
+  char** tab;
+  cudaMalloc(&tab, sizeof(char*) * 2);
+  cudaMemcpy(tab, blocks.data(), sizeof(char*) * 2, cudaMemcpyHostToDevice);
+  std::vector<double2> Ch((size_t)O * S);
+  for (auto& v : Ch) v = make_double2(urand() - 0.5, 0.0);
+  double2 *Cd, *out;
+  int* count;
+  cudaMalloc(&Cd, sizeof(double2) * Ch.size());
+  cudaMemcpy(Cd, Ch.data(), sizeof(double2) * Ch.size(), cudaMemcpyHostToDevice);
+  cudaMalloc(&count, sizeof(int));
+  cudaMemcpy(count, &cnt, sizeof(int), cudaMemcpyHostToDevice);
+  cudaMalloc(&out, sizeof(double2) * O * n);
+  void* work;
+  cudaMalloc(&work, ssqcd::combine_tc_work_bytes(1, S));
+  const int rc = ssqcd::combine_tc(tab, kLog, n, 1, Cd, O, S, count, out, 0, 1, work, 0);
+  std::vector<double> g((size_t)O * 2 * n);
+  cudaMemcpy(g.data(), out, sizeof(double) * g.size(), cudaMemcpyDeviceToHost);
+  long long finite = 0;
+  for (double v : g) finite += std::isnan(v) ? 0 : 1;
+  printf("nan case: status %d, %lld of %lld outputs not NaN\n", rc, finite, (long long)g.size());
+  for (auto b : blocks) cudaFree(b);
+  cudaFree(tab);
+  cudaFree(Cd);
+  cudaFree(out);
+  cudaFree(count);
+  cudaFree(work);
+  return rc == 0 && finite == 0 ? 0 : 1;
+}
+
 // --time: one window of the headline size (2502 slots of 786,432 complex
 // elements, 31.5 GB, 16 moments), best of three after a warm-up
 __global__ void fill_kernel(double* p, long long count, unsigned long long seed, double scale) {
@@ -273,6 +318,7 @@ int main(int argc, char** argv) {
   bad |= run_check(Case{64 * 40, 1, 300, 16, 300, 0});
   bad |= run_check(Case{64 * 20, 3, 48, 5, 37, 1});
   bad |= run_check(Case{64 * 8, 1, 16, 16, 1, 0});
+  bad |= run_nan_check();
   printf("checks: %s\n", bad ? "FAILED" : "passed");
   return bad ? 1 : 0;
 }
